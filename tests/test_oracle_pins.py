@@ -1,0 +1,365 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself or with a retyped copy of its
+formulas: each check uses LAPACK (numpy / scipy), a closed form, an
+invariant, brute force on a tiny case, or values printed in the paper.
+"""
+
+import itertools
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.stats as sst
+
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _sign_fixed_qr(c):
+    q, r = np.linalg.qr(c)
+    s = np.sign(np.diag(r))
+    s[s == 0] = 1.0
+    return q * s, (r.T * s).T
+
+
+# --------------------------------------------------------------------------
+# Random numbers (Psi, Alg. 1 step 1)
+# --------------------------------------------------------------------------
+
+def test_philox_known_answers(oracle_lib):
+    """Philox-4x32-10 against the generator authors' known-answer vectors."""
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for row in rows:
+        vals = [int(v, 16) for v in row]
+        assert oracle_lib.philox4x32_10(vals[0:4], vals[4:6]) == vals[6:10]
+
+
+def test_gaussian_is_standard_normal(oracle_lib):
+    """Box-Muller output: N(0, 1) by a KS test, finite everywhere, and
+    streams / seeds give different draws."""
+    z = oracle_lib.gauss_matrix(7, 0, 40000, 5).ravel()
+    assert np.all(np.isfinite(z))
+    assert abs(z.mean()) < 0.02 and abs(z.var() - 1.0) < 0.02
+    assert sst.kstest(z, "norm").pvalue > 1e-3
+    z1 = oracle_lib.gauss_matrix(7, 1, 100, 5)
+    z2 = oracle_lib.gauss_matrix(8, 0, 100, 5)
+    assert not np.allclose(z1, z.reshape(40000, 5)[:100])
+    assert not np.allclose(z2, z.reshape(40000, 5)[:100])
+    # the matrix routine is the entry routine laid out row-major
+    assert oracle_lib.gauss_entry(7, 0, 3, 4) == z.reshape(40000, 5)[3, 4]
+
+
+# --------------------------------------------------------------------------
+# Thin QR (Sec. 3.1, C1 = Q1 R1, C2 = Q2 R2)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m,l,cond", [(50, 12, 1.0), (200, 60, 1e6), (17, 17, 10.0), (300, 1, 1.0)])
+def test_qr_matches_lapack(oracle_lib, m, l, cond):
+    rng = np.random.default_rng(m + l)
+    u = synth.haar(rng, m, l)
+    v = synth.haar(rng, l, l)
+    c = (u * np.logspace(0, -np.log10(cond), l)) @ v.T
+    q, r = oracle_lib.qr(c)
+    qn, rn = _sign_fixed_qr(c)
+    assert np.allclose(np.triu(r), r, atol=0)
+    assert np.all(np.diag(r) >= 0)
+    assert np.linalg.norm(q.T @ q - np.eye(l)) < 1e-13 * l
+    assert _rel(q @ r, c) < 1e-14
+    assert _rel(r, rn) < 1e-13
+    assert np.linalg.norm(q - qn) < 1e-13 * cond
+
+
+def test_qr_rank_deficient_still_orthonormal(oracle_lib):
+    """Householder QR stays backward stable on an exactly rank-deficient C."""
+    rng = np.random.default_rng(3)
+    c = rng.standard_normal((80, 4)) @ rng.standard_normal((4, 10))
+    q, r = oracle_lib.qr(c)
+    assert np.linalg.norm(q.T @ q - np.eye(10)) < 1e-13
+    assert _rel(q @ r, c) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# QRCP of D (eq. 8)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("l,seed", [(5, 0), (15, 1), (60, 2), (110, 3)])
+def test_qrcp_matches_lapack_dgeqp3(oracle_lib, l, seed):
+    """On a tie-free matrix the pivot order and R agree with LAPACK's xGEQP3."""
+    rng = np.random.default_rng(seed)
+    d = rng.standard_normal((l, l)) * np.logspace(0, -3, l)
+    qt, rt, perm = oracle_lib.qrcp(d)
+    qs, rs, ps = sla.qr(d, pivoting=True)
+    s = np.sign(np.diag(rs))
+    assert np.array_equal(perm, ps)
+    assert _rel(rt, (rs.T * s).T) < 1e-12
+    assert np.linalg.norm(qt - qs * s) < 1e-11
+    assert _rel(qt @ rt, d[:, perm]) < 1e-14
+    assert np.linalg.norm(qt.T @ qt - np.eye(l)) < 1e-13 * l
+
+
+@pytest.mark.parametrize("l,seed", list(itertools.product([2, 3, 4, 6], [0, 1, 2])))
+def test_qrcp_pivots_brute_force(oracle_lib, l, seed):
+    """Each pivot is the remaining column of largest residual norm after
+    projecting out the columns already chosen (computed by least squares)."""
+    rng = np.random.default_rng(100 * l + seed)
+    d = rng.standard_normal((l, l))
+    _, _, perm = oracle_lib.qrcp(d)
+    chosen = []
+    for j in range(l):
+        best, best_c = -1.0, None
+        for c in range(l):
+            if c in chosen:
+                continue
+            if chosen:
+                basis = d[:, chosen]
+                coef, *_ = np.linalg.lstsq(basis, d[:, c], rcond=None)
+                res = np.linalg.norm(d[:, c] - basis @ coef)
+            else:
+                res = np.linalg.norm(d[:, c])
+            if res > best + 1e-12:
+                best, best_c = res, c
+        assert perm[j] == best_c
+        chosen.append(best_c)
+
+
+def test_qrcp_rank_revealing_inequalities(oracle_lib):
+    """|R_jj| >= ||R(j:i, i)|| for every i > j, so diag(R) is non-increasing."""
+    rng = np.random.default_rng(5)
+    d = synth.haar(rng, 30, 30) @ np.diag(np.logspace(0, -8, 30)) @ synth.haar(rng, 30, 30).T
+    _, rt, _ = oracle_lib.qrcp(d)
+    for j in range(30):
+        for i in range(j + 1, 30):
+            assert rt[j, j] >= np.linalg.norm(rt[j:i + 1, i]) * (1 - 1e-12)
+    assert np.all(np.diff(np.diag(rt)) <= 1e-15)
+
+
+def test_qrcp_ties_take_lowest_index(oracle_lib):
+    """Two columns of identical norm: the lower index is chosen first."""
+    d = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 0.5]])
+    _, rt, perm = oracle_lib.qrcp(d)
+    assert list(perm) == [0, 1, 2]
+    d2 = d[:, [2, 1, 0]]
+    _, _, perm2 = oracle_lib.qrcp(d2)
+    assert list(perm2) == [1, 2, 0]
+
+
+# --------------------------------------------------------------------------
+# CoR-UTV (Alg. 1, eqs. 4-9)
+# --------------------------------------------------------------------------
+
+def _approx(o):
+    return o["U"] @ o["T"] @ o["V"].T
+
+
+@pytest.mark.parametrize("m,n,rank,k,p,q", [(300, 200, 10, 10, 5, 0), (200, 300, 8, 8, 4, 1),
+                                            (150, 150, 20, 20, 0, 2), (400, 120, 5, 10, 10, 1)])
+def test_exact_rank_is_reproduced(oracle_lib, m, n, rank, k, p, q):
+    """A of exact rank <= ell is reproduced to rounding (Sec. 3.1)."""
+    f = synth.exact_rank_case(m, n, rank, k, p, q, seed=m + n)
+    o = oracle_lib.corutv(f.a, k, p, q, synth.gaussian_psi(n, k + p, seed=1))
+    assert _rel(_approx(o), f.a) < 1e-13
+
+
+def _moderate_case(m=240, n=180, seed=4, decay=0.7):
+    sigma = decay ** np.arange(min(m, n))
+    return synth.spectrum_matrix(m, n, sigma, 0.0, seed), sigma
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_closed_form_projection(oracle_lib, q):
+    """U T V^T = Q1 Q1^T A Q2 Q2^T with Q1 = orth(A (A^T A)^q Psi) and
+    Q2 = orth(A^T Q1), both obtained here with LAPACK QR and no
+    re-orthonormalisation."""
+    # slow decay keeps the LAPACK-side Krylov product well conditioned:
+    # sigma_1 / sigma_12 = 0.9^-11 ~ 3.1, so kappa ~ 3.1^(2q+1) <= 3e2
+    a, _ = _moderate_case(decay=0.9)
+    k, p = 8, 4
+    psi = synth.gaussian_psi(a.shape[1], k + p, seed=2)
+    o = oracle_lib.corutv(a, k, p, q, psi)
+    kry = a @ psi
+    for _ in range(q):
+        kry = a @ (a.T @ kry)
+    q1, _ = _sign_fixed_qr(kry)
+    q2, _ = _sign_fixed_qr(a.T @ q1)
+    assert np.linalg.norm(o["Q1"] - q1) < 1e-11
+    assert np.linalg.norm(o["Q2"] - q2) < 1e-11
+    assert _rel(_approx(o), q1 @ (q1.T @ a @ q2) @ q2.T) < 1e-12
+
+
+def test_d_equals_r2_transpose(oracle_lib):
+    """With C2 = A^T Q1 = Q2 R2, eq. 7 gives D = Q1^T A Q2 = R2^T exactly."""
+    a, _ = _moderate_case(seed=9)
+    o = oracle_lib.corutv(a, 8, 4, 1, synth.gaussian_psi(a.shape[1], 12, seed=3))
+    _, r2 = _sign_fixed_qr(a.T @ o["Q1"])
+    assert _rel(o["D"], r2.T) < 1e-12
+
+
+def test_factor_structure(oracle_lib):
+    """U, V orthonormal; T upper with non-negative, non-increasing diagonal;
+    sigma(T) = sigma(D); V = Q2 P; U = Q1 Qt."""
+    f = synth.factor_c1()
+    psi = synth.gaussian_psi(f.n, f.ell, seed=0)
+    o = oracle_lib.corutv(f.a, f.k, f.p, f.q, psi)
+    u, t, v = o["U"], o["T"], o["V"]
+    l = f.ell
+    assert np.linalg.norm(u.T @ u - np.eye(l)) < 10 * l * 2.2e-16
+    assert np.linalg.norm(v.T @ v - np.eye(l)) < 10 * l * 2.2e-16
+    assert np.all(np.tril(t, -1) == 0)
+    dg = np.diag(t)
+    assert np.all(dg >= 0) and np.all(np.diff(dg) <= 1e-15)
+    assert np.allclose(np.linalg.svd(t, compute_uv=False), np.linalg.svd(o["D"], compute_uv=False),
+                       rtol=1e-12, atol=1e-14)
+    assert np.array_equal(v, o["Q2"][:, o["perm"]])
+    qt, _, _ = sla.qr(o["D"], pivoting=True)  # only used for the span check below
+    assert _rel(u @ u.T @ o["Q1"], o["Q1"]) < 1e-13
+    del qt
+
+
+def test_c1_reveals_rank_and_singular_values(oracle_lib):
+    """1000 x 1000, exact rank 10 + 1e-6 noise: diag(T) has the gap after
+    k = 10, and its first 10 entries bracket sigma_i within the q = 0 sketch
+    accuracy (Sec. 5.1)."""
+    f = synth.factor_c1()
+    o = oracle_lib.corutv(f.a, f.k, f.p, f.q, synth.gaussian_psi(f.n, f.ell, seed=0))
+    dg = np.diag(o["T"])
+    assert dg[9] / dg[10] > 1e4
+    sv = np.linalg.svd(o["T"], compute_uv=False)
+    assert np.allclose(sv[:10], f.sigma, rtol=1e-6)
+
+
+@pytest.mark.parametrize("q", [0, 2])
+def test_error_versus_truncated_svd(oracle_lib, q):
+    """||A - U T V^T||_F >= sqrt(sum_{i>ell} sigma_i^2) (eq. 3); with q = 2 it
+    is within a few per cent of that optimum (Sec. 5.2)."""
+    m, n = 300, 250
+    sigma = 1.0 / np.arange(1, 251) ** 1.0
+    a = synth.spectrum_matrix(m, n, sigma, 0.0, 11)
+    k, p = 20, 5
+    o = oracle_lib.corutv(a, k, p, q, synth.gaussian_psi(n, k + p, seed=5))
+    err = np.linalg.norm(a - _approx(o))
+    sv = np.linalg.svd(a, compute_uv=False)
+    opt = np.sqrt(np.sum(sv[k + p:] ** 2))
+    assert err >= opt * (1 - 1e-12)
+    if q == 2:
+        assert err <= 1.05 * opt
+    else:
+        assert err <= 3.0 * opt
+    # rank-k truncation U(:,1:k) T(1:k,:) V^T against the rank-k optimum
+    ek = np.linalg.norm(a - o["U"][:, :k] @ o["T"][:k, :] @ o["V"].T)
+    assert ek >= np.sqrt(np.sum(sv[k:] ** 2)) * (1 - 1e-12)
+
+
+def test_literal_and_reorthonormalised_forms_agree(oracle_lib):
+    """Algorithm 1 as printed and the re-orthonormalised loop give the same
+    factorisation in exact arithmetic; on a well-conditioned case they agree
+    to rounding amplified by the growth of (A^T A)^q."""
+    a, _ = _moderate_case(seed=21, decay=0.9)
+    psi = synth.gaussian_psi(a.shape[1], 12, seed=6)
+    for q in (0, 1, 2):
+        o1 = oracle_lib.corutv(a, 8, 4, q, psi, literal=False)
+        o2 = oracle_lib.corutv(a, 8, 4, q, psi, literal=True)
+        assert _rel(_approx(o1), _approx(o2)) < 1e-11
+        assert np.linalg.norm(o1["Q1"] - o2["Q1"]) < 1e-10
+
+
+def test_seeded_psi_equals_injected_psi(oracle_lib):
+    a, _ = _moderate_case(seed=2)
+    psi = oracle_lib.gauss_matrix(42, 3, a.shape[1], 12)
+    o1 = oracle_lib.corutv(a, 8, 4, 1, psi)
+    o2 = oracle_lib.corutv(a, 8, 4, 1, None, seed=42, stream=3)
+    assert np.array_equal(o1["T"], o2["T"]) and np.array_equal(o1["U"], o2["U"])
+
+
+def test_invalid_arguments_rejected(oracle_lib):
+    a = np.ones((10, 8))
+    with pytest.raises(oracle_lib.OracleError):
+        oracle_lib.corutv(a, 5, 3, 0)   # ell = 8 = min(m, n)
+    with pytest.raises(oracle_lib.OracleError):
+        oracle_lib.corutv(a, 0, 3, 0)
+
+
+# --------------------------------------------------------------------------
+# Robust PCA (Sec. 4, Alg. 2; Sec. 5.3)
+# --------------------------------------------------------------------------
+
+def test_shrink_operator(oracle_lib):
+    x = np.array([-3.0, -1.0, -0.5, 0.0, 0.5, 1.0, 2.5])
+    out = oracle_lib.shrink(x, 1.0)
+    assert np.array_equal(out, np.array([-2.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.5]))
+    assert np.array_equal(oracle_lib.shrink(x, 0.0), x)
+
+
+def test_norm2_matches_lapack(oracle_lib):
+    rng = np.random.default_rng(0)
+    mat = rng.standard_normal((120, 80))
+    assert abs(oracle_lib.norm2(mat) - np.linalg.norm(mat, 2)) < 1e-10 * np.linalg.norm(mat, 2)
+
+
+def _table1_rows():
+    return [ln.split() for ln in open(os.path.join(GOLDEN, "table1_alm_corutv.txt"))
+            if ln.strip() and not ln.startswith("#")]
+
+
+def _run_table1(oracle_lib, n):
+    row = [r for r in _table1_rows() if int(r[0]) == n][0]
+    pr = synth.rpca_table1(n, seed=0)
+    assert pr.rank == int(row[1]) and int(np.count_nonzero(pr.s_true)) == int(row[2])
+    d = oracle_lib.rpca_defaults(pr.m_obs)
+    o = oracle_lib.rpca(pr.m_obs, pr.rank, d["lam"], d["mu0"], d["mu_bar"], d["rho"], d["tol"], 50)
+    return row, pr, o
+
+
+def test_table1_n1000_recovery(oracle_lib):
+    """Table 1, n = 1000: exact rank 50, ||S*||_0 = 5e4 on the true support,
+    12 iterations, zeta below the 1e-5 stopping threshold."""
+    row, pr, o = _run_table1(oracle_lib, 1000)
+    assert o["rank"] == int(row[3])
+    assert int(np.count_nonzero(o["S"])) == int(row[4])
+    assert np.array_equal(o["S"] != 0, pr.s_true != 0)
+    assert o["iters"] == int(row[5])
+    assert o["zeta"] < 1e-5
+    # zeta as defined in Sec. 5.3, recomputed from the outputs
+    zeta = np.linalg.norm(pr.m_obs - o["L"] - o["S"]) / np.linalg.norm(pr.m_obs)
+    assert abs(zeta - o["zeta"]) < 1e-3 * o["zeta"]
+    assert np.linalg.matrix_rank(o["L"], tol=1e-6 * np.linalg.norm(o["L"], 2)) == int(row[3])
+
+
+@pytest.mark.slow
+def test_table1_n2000_recovery(oracle_lib):
+    row, pr, o = _run_table1(oracle_lib, 2000)
+    assert o["rank"] == int(row[3])
+    assert int(np.count_nonzero(o["S"])) == int(row[4])
+    assert o["iters"] == int(row[5])
+    assert o["zeta"] < 1e-5
+
+
+def test_rpca_mu_schedule_and_histories(oracle_lib):
+    """mu_j = min(rho^j mu0, mu_bar) (continuation with a cap); r_j is the
+    number of diag(T) above 1/mu_j, so never above ell = 2k."""
+    pr = synth.rpca_problem(240, 120, 4, 0.05, "pm", seed=3, amplitude=20.0)
+    mu0 = 1.25 / np.linalg.norm(pr.m_obs, 2)
+    mu_bar = 40 * mu0
+    o = oracle_lib.rpca(pr.m_obs, 4, 1 / np.sqrt(240), mu0, mu_bar, 1.6, 1e-9, 20)
+    j = np.arange(o["iters"])
+    assert np.allclose(o["mu_hist"], np.minimum(mu0 * 1.6 ** j, mu_bar), rtol=1e-12)
+    assert np.all(o["rank_hist"] <= 8)
+    assert o["iters"] == 20 or o["zeta"] < 1e-9
+
+
+def test_rpca_c4_shape_small(oracle_lib):
+    """The 4800 x 1200 workload's recipe at 1/10 size (rank 5, 10 % of
+    U[-50, 50] outliers): rank and support recovered."""
+    pr = synth.rpca_problem(480, 120, 5, 0.10, "uniform", seed=0, amplitude=50.0)
+    d = oracle_lib.rpca_defaults(pr.m_obs)
+    o = oracle_lib.rpca(pr.m_obs, 5, d["lam"], d["mu0"], d["mu_bar"], d["rho"], 1e-5, 50)
+    assert o["rank"] == 5 and o["zeta"] < 1e-5
+    assert _rel(o["L"], pr.l_true) < 1e-3
