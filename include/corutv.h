@@ -1,0 +1,201 @@
+/*
+ * corutv.h -- C ABI of libcorutv, a single-GPU (sm_103a) implementation of
+ * Compressed Randomized UTV (CoR-UTV) with the power method and of the
+ * ALM-CoRUTV robust-PCA solver (Kaloorazi & de Lamare, "Study of Compressed
+ * Randomized UTV Decompositions for Low-Rank Matrix Approximations in Data
+ * Science").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are row-major; `ld*` is the row stride in elements (>= columns).
+ *  - A pointer argument may be host or device memory; the library asks the
+ *    CUDA runtime which. All pointers of one call must be in the same space,
+ *    except `opts->psi`, which may be either.
+ *  - Device-pointer calls are stream-ordered on the context's stream
+ *    (corutv_set_stream) and return once enqueued; corutv_sync waits and
+ *    reports any status raised on the device. Host-pointer calls copy in,
+ *    compute, copy out and synchronise before returning.
+ *  - Inputs are borrowed and never written. Outputs are caller-owned. The
+ *    context owns its workspace and streams.
+ *  - Errors are reported only through the returned status; nothing aborts or
+ *    exits. corutv_last_error gives a one-line message for the calling thread.
+ *  - ell = k + p must satisfy 1 <= k <= ell < min(m, n) and ell <= 128
+ *    (Sec. 3.1: "an integer k <= ell < min{m, n}"); q >= 0.
+ *  - Every step of every call runs in this library's CUDA kernels; there is
+ *    no CPU fallback. Without a usable GPU, corutv_create returns CORUTV_ECUDA.
+ */
+#ifndef CORUTV_H
+#define CORUTV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CORUTV_OK = 0,
+    CORUTV_EINVAL = 1,      /* bad argument or unsupported combination */
+    CORUTV_ENOMEM = 2,      /* device memory or the context's budget exhausted */
+    CORUTV_ECUDA = 3,       /* a CUDA runtime / driver call failed */
+    CORUTV_EPENDING = 4,    /* corutv_poll: the request has not finished */
+    CORUTV_ETIMEDOUT = 5,   /* corutv_poll: timeout elapsed; or a device wait gave up */
+    CORUTV_ENOTCONV = 6,    /* corutv_rpca: max_iter reached with zeta >= tol */
+    CORUTV_EBREAKDOWN = 7   /* Cholesky of a sketch Gram failed even after the shift */
+} corutv_status;
+
+/* Element type of A / M and of every floating-point output of the call. */
+typedef enum { CORUTV_F64 = 0, CORUTV_F32 = 1 } corutv_dtype;
+
+/* Arithmetic of the 2q+2 sketch / power products A X and A^T Y.
+ * F64: FP64 FMA. F32: FP32 FMA. TF32 / BF16: tensor cores (tcgen05) with FP32
+ * accumulation; BF16 first writes a bf16 copy of A. The projection D of
+ * eq. 7 always runs in FP64 (dtype F64) or FP32 (dtype F32); the Gram
+ * Cholesky factorisations and the pivoted QR of D always run in FP64. */
+typedef enum { CORUTV_P_F64 = 0, CORUTV_P_F32 = 1, CORUTV_P_TF32 = 2, CORUTV_P_BF16 = 3 } corutv_prec;
+
+typedef struct {
+    int64_t k;            /* target rank */
+    int64_t p;            /* oversampling; ell = k + p */
+    int64_t q;            /* power iterations (Algorithm 1 runs its loop q+1 times) */
+    int32_t sketch_prec;  /* corutv_prec */
+    int32_t d_mode;       /* 0: exact D = Q1^T A Q2 (eq. 7); other values rejected */
+    uint64_t seed;        /* Philox-4x32-10 key for Psi when psi == NULL */
+    uint32_t stream;      /* Philox counter word 2 (independent draws per call) */
+    uint32_t reserved;
+    const double* psi;    /* optional n x ell row-major FP64 Gaussian test matrix */
+} corutv_opts;
+
+typedef struct corutv_ctx corutv_ctx;
+
+/* Create a context on CUDA device `device`. mem_budget_bytes caps the
+ * device workspace the context may hold (0 = 90 % of the free memory at
+ * creation). max_slots caps how many serving requests are resident at once
+ * (<= 0 selects 8). */
+corutv_status corutv_create(corutv_ctx** out, int device, size_t mem_budget_bytes, int max_slots);
+
+/* Waits for outstanding work, frees all device memory of the context. */
+corutv_status corutv_destroy(corutv_ctx* ctx);
+
+/* Message of the last failing call made by this thread; never NULL. */
+const char* corutv_last_error(const corutv_ctx* ctx);
+
+/* Use `cuda_stream` (a cudaStream_t, may be NULL for the legacy stream) for
+ * subsequent stream-ordered calls. The caller keeps the stream alive. */
+corutv_status corutv_set_stream(corutv_ctx* ctx, void* cuda_stream);
+
+/* Wait for all work enqueued on the context's stream; returns the first
+ * device-side status raised since the previous corutv_sync
+ * (CORUTV_EBREAKDOWN, CORUTV_ETIMEDOUT) or a CUDA error. */
+corutv_status corutv_sync(corutv_ctx* ctx);
+
+/* CoR-UTV with power method (Algorithm 1; eqs. 4-9):
+ *   Psi (n x ell, Gaussian) -> for i = 0..q: C1 = A X, Q1 = qr(C1),
+ *   C2 = A^T Q1, X = qr(C2) (i < q) -> Q2 = qr(C2) -> D = Q1^T A Q2 ->
+ *   D P = Qt Rt (column-pivoted QR) -> U = Q1 Qt, T = Rt, V = Q2 P.
+ * Each sketch is re-orthonormalised before its next use (CholeskyQR2); in
+ * exact arithmetic this gives the same Q1, Q2 as the printed loop.
+ * A: m x n (lda). U: m x ell (ldu), T: ell x ell upper triangular (row
+ * stride ell, strictly lower part written as 0, diag >= 0 and
+ * non-increasing), V: n x ell (ldv), perm: ell int32, the 0-based column of
+ * D placed at position j. U, V, perm may be NULL; T may not. */
+corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, int64_t m, int64_t n,
+                            int64_t lda, const corutv_opts* opts, void* U, int64_t ldu, void* T,
+                            void* V, int64_t ldv, int32_t* perm);
+
+/* ALM-CoRUTV (Algorithm 2; eq. 13): M = L + S by inexact augmented
+ * Lagrange multipliers with the CoR-UTV thresholding operator
+ * C_delta(B) = U(:,1:r) T(1:r,:) V^T, r = #{i : T_ii > delta}, and the
+ * shrinkage S_delta(x) = sgn(x) max(|x| - delta, 0) (Sec. 4). opts->k is the
+ * rank guess; the low-rank step uses ell = 2k and q = 1 (Sec. 5.3) and a
+ * fresh Psi per iteration (Philox stream opts->stream + j + 1).
+ * Y_0 = S_0 = 0; mu_{j+1} = min(rho mu_j, mu_bar); stop after the first
+ * iteration with zeta = ||M - L - S||_F / ||M||_F < tol or after max_iter.
+ * Parameters <= 0 select: lambda = 1/sqrt(max(m, n)), mu0 = 1.25/||M||_2
+ * (estimated on the device by 50 power iterations), rho = 1.6,
+ * mu_bar = 1e7 mu0, tol = 1e-5, max_iter = 100.
+ * L, S: m x n with row stride n. iters, zeta, rank: optional outputs (host
+ * pointers), valid after the call (device calls synchronise at the end).
+ * Returns CORUTV_ENOTCONV if max_iter was reached with zeta >= tol. */
+corutv_status corutv_rpca(corutv_ctx* ctx, corutv_dtype dtype, const void* M, int64_t m, int64_t n,
+                          int64_t ldm, const corutv_opts* opts, double lambda, double mu0,
+                          double mu_bar, double rho, double tol, int max_iter, void* L, void* S,
+                          int* iters, double* zeta, int* rank);
+
+/* ---- serving: asynchronous factorisations with continuous admission ---- */
+typedef struct {
+    corutv_dtype dtype;
+    const void* A;
+    int64_t m, n, lda;
+    corutv_opts opts;
+    void *U, *T, *V;
+    int64_t ldu, ldv;
+    int32_t* perm;
+} corutv_request;
+
+/* Queue one corutv_factor request; the descriptor is copied, the buffers
+ * are borrowed until corutv_poll returns something other than
+ * CORUTV_EPENDING. Requests are admitted in arrival order as slots and
+ * workspace memory free up, and run concurrently on the device. Returns
+ * CORUTV_ENOMEM only if the request could never fit the budget. */
+corutv_status corutv_submit(corutv_ctx* ctx, const corutv_request* req, uint64_t* ticket);
+
+/* Wait up to timeout_us (0 = do not wait, < 0 = forever) for a ticket.
+ * CORUTV_EPENDING / CORUTV_ETIMEDOUT while unfinished; otherwise the
+ * request's own status, with latency_s (optional) = completion - submit. */
+corutv_status corutv_poll(corutv_ctx* ctx, uint64_t ticket, int64_t timeout_us, double* latency_s);
+
+/* ---- per-stage device timers and launch counter --------------------------
+ * Not part of the method: instrumentation for roofline measurements. With
+ * profiling enabled, corutv_factor / corutv_rpca record a CUDA event pair on
+ * the context's stream around every kernel of a stage:
+ *   CORUTV_STAGE_SKETCH  the 2q+2 sketch / power products (eqs. 4, 5)
+ *   CORUTV_STAGE_PROJECT the product W = A Q2 of the projection (eq. 7)
+ *   CORUTV_STAGE_ORTH    each thin QR (CholeskyQR2), all of its kernels
+ *   CORUTV_STAGE_QRCP    the pivoted QR of D (eq. 8)
+ *   CORUTV_STAGE_FACTOR  one whole factorisation (Algorithm 1)
+ * corutv_profile_read synchronises the stream and returns the summed
+ * duration (ms) and the number of timed intervals of `stage`, and, for
+ * CORUTV_STAGE_ALL, the number of kernels this library launched (in any
+ * context) since profiling was last enabled. Enabling resets all counters. */
+enum { CORUTV_STAGE_SKETCH = 0, CORUTV_STAGE_PROJECT = 1, CORUTV_STAGE_ORTH = 2, CORUTV_STAGE_QRCP = 3,
+       CORUTV_STAGE_FACTOR = 4, CORUTV_STAGE_COUNT = 5, CORUTV_STAGE_ALL = -1 };
+corutv_status corutv_profile_enable(corutv_ctx* ctx, int enable);
+corutv_status corutv_profile_read(corutv_ctx* ctx, int stage, double* total_ms, int64_t* count);
+
+/* ---- single steps of Algorithm 1, for testing and composition ----------
+ * Device pointers only, stream-ordered on the context's stream. */
+
+/* Step 1: psi[i*ldpsi + j] = N(0,1) draw for entry (i, j) of the n x ell
+ * test matrix: Philox-4x32-10 with counter (i, j, stream, 0) and key
+ * (seed_lo, seed_hi); the four words give two 53-bit uniforms
+ * u1 in (0,1], u2 in [0,1); z = sqrt(-2 ln u1) cos(2 pi u2). FP64 output. */
+corutv_status corutv_gaussian(corutv_ctx* ctx, uint64_t seed, uint32_t stream, int64_t n, int64_t ell,
+                              double* psi, int64_t ldpsi);
+
+/* Eq. 4 / eq. 5 / the first half of eq. 7: C = A X (trans = 0, X n x ell,
+ * C m x ell) or C = A^T X (trans = 1, X m x ell, C n x ell) in arithmetic
+ * `prec`. A has element type dtype; X and C are FP64. */
+corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec prec, int trans,
+                            const void* A, int64_t m, int64_t n, int64_t lda, const double* X,
+                            int64_t ldx, int64_t ell, double* C, int64_t ldc);
+
+/* Sec. 3.1 "C = Q R": thin QR of the rows x ell FP64 matrix C (rows >= ell)
+ * by CholeskyQR2 (Gram in FP64, Cholesky in FP64, shifted once if the
+ * first Gram is not numerically positive definite). Q: rows x ell (ldq),
+ * R: ell x ell upper (optional), diag(R) > 0. */
+corutv_status corutv_orth(corutv_ctx* ctx, const double* C, int64_t rows, int64_t ell, int64_t ldc,
+                          double* Q, int64_t ldq, double* R);
+
+/* Eq. 8: D P = Qt Rt for the ell x ell FP64 matrix D (row stride ell), one
+ * thread block, FP64, Businger-Golub pivoting on recomputed column norms
+ * (lowest index on ties), diag(Rt) >= 0. Qt, Rt: ell x ell. */
+corutv_status corutv_qrcp(corutv_ctx* ctx, const double* D, int64_t ell, double* Qt, double* Rt,
+                          int32_t* perm);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CORUTV_H */

@@ -68,6 +68,8 @@ def _bind(path):
                                    ctypes.c_uint32]
     lib.or_gauss_entry.restype = ctypes.c_double
     lib.or_gauss_matrix.argtypes = [ctypes.c_uint64, ctypes.c_uint32, i64, i64, dp]
+    lib.or_gemm_ax.argtypes = [i64, i64, i64, dp, i64, dp, dp]
+    lib.or_gemm_aty.argtypes = [i64, i64, i64, dp, i64, dp, dp]
     lib.or_qr.argtypes = [i64, i64, dp, i64, dp, dp]
     lib.or_qrcp.argtypes = [i64, dp, dp, dp, ip]
     lib.or_corutv.argtypes = [dp, i64, i64, i64, i64, i64, i64, dp, ctypes.c_uint64,
@@ -153,6 +155,24 @@ def gauss_entry(seed: int, stream: int, i: int, j: int) -> float:
 def gauss_matrix(seed: int, stream: int, n: int, ell: int) -> np.ndarray:
     out = np.empty((n, ell))
     _load().or_gauss_matrix(seed, stream, n, ell, _dp(out))
+    return out
+
+
+def gemm_ax(a: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """C = A X (eq. 4)."""
+    a, x = _f64(a), _f64(x)
+    m, n = a.shape
+    out = np.empty((m, x.shape[1]))
+    _load().or_gemm_ax(m, n, x.shape[1], _dp(a), n, _dp(x), _dp(out))
+    return out
+
+
+def gemm_aty(a: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """C = A^T Y (eq. 5)."""
+    a, y = _f64(a), _f64(y)
+    m, n = a.shape
+    out = np.empty((n, y.shape[1]))
+    _load().or_gemm_aty(m, n, y.shape[1], _dp(a), n, _dp(y), _dp(out))
     return out
 
 

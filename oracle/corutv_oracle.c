@@ -137,6 +137,16 @@ static void mm_xy(int64_t m, int64_t p, int64_t l, const double* x, const double
     }
 }
 
+void or_gemm_ax(int64_t m, int64_t n, int64_t l, const double* a, int64_t lda, const double* x,
+               double* c) {
+    mm_ax(m, n, l, a, lda, x, c);
+}
+
+void or_gemm_aty(int64_t m, int64_t n, int64_t l, const double* a, int64_t lda, const double* y,
+                 double* c) {
+    mm_aty(m, n, l, a, lda, y, c);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Householder reflections (Golub & Van Loan, Sec. 5.1).                    */
 /* For the column x = w[r0.., col] of the row-major work array w (stride    */

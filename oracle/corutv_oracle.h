@@ -37,6 +37,13 @@ double or_gauss_entry(uint64_t seed, uint32_t stream, uint32_t i, uint32_t j);
 /* psi[i*ell + j] = or_gauss_entry(seed, stream, i, j) for an n x ell matrix. */
 void or_gauss_matrix(uint64_t seed, uint32_t stream, int64_t n, int64_t ell, double* psi);
 
+/* Plain products of eqs. 4-5: C (m x l) = A X with A m x n (row stride lda)
+ * and X n x l; C (n x l) = A^T Y with Y m x l. Ascending summation order. */
+void or_gemm_ax(int64_t m, int64_t n, int64_t l, const double* a, int64_t lda, const double* x,
+               double* c);
+void or_gemm_aty(int64_t m, int64_t n, int64_t l, const double* a, int64_t lda, const double* y,
+                 double* c);
+
 /* Thin Householder QR of the m x l matrix C (m >= l): C = Q R, Q m x l with
  * orthonormal columns, R l x l upper triangular with diag(R) >= 0. */
 int or_qr(int64_t m, int64_t l, const double* c, int64_t ldc, double* q, double* r);

@@ -1,0 +1,1228 @@
+// C ABI of libcorutv (include/corutv.h): context, workspace, the CoR-UTV
+// pipeline of Algorithm 1, the ALM-CoRUTV loop of Algorithm 2 and the
+// serving queue. Host code only orchestrates; every arithmetic step runs in
+// the kernels of k_*.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/corutv.h"
+#include "internal.cuh"
+#include "tc.cuh"
+
+using namespace corutv;
+
+namespace {
+std::atomic<long long> g_launches{0};
+}  // namespace
+
+void corutv::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+// Per-stage CUDA event timers of one context (see corutv_profile_enable).
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> open;
+    double ms[CORUTV_STAGE_COUNT] = {0};
+    long long count[CORUTV_STAGE_COUNT] = {0};
+    long long launch_base = 0;
+
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    int begin(int stage, cudaStream_t st) {
+        if (!on) return -1;
+        cudaEvent_t a = get(), b = get();
+        cudaEventRecord(a, st);
+        open.push_back({stage, {a, b}});
+        return (int)open.size() - 1;
+    }
+    void end(int token, cudaStream_t st) {
+        if (token < 0) return;
+        cudaEventRecord(open[token].second.second, st);
+    }
+    // requires the stream to have been synchronised
+    void collect() {
+        for (auto& r : open) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, r.second.first, r.second.second) == cudaSuccess) {
+                ms[r.first] += t;
+                count[r.first] += 1;
+            } else {
+                cudaGetLastError();
+            }
+            pool.push_back(r.second.first);
+            pool.push_back(r.second.second);
+        }
+        open.clear();
+    }
+    void reset() {
+        for (int i = 0; i < CORUTV_STAGE_COUNT; ++i) {
+            ms[i] = 0;
+            count[i] = 0;
+        }
+        launch_base = g_launches.load();
+    }
+    ~Profiler() {
+        for (auto& r : open) pool.push_back(r.second.first), pool.push_back(r.second.second);
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+struct ProfScope {
+    Profiler* p;
+    int tok;
+    cudaStream_t st;
+    ProfScope(Profiler* p_, int stage, cudaStream_t s) : p(p_), tok(p_ ? p_->begin(stage, s) : -1), st(s) {}
+    ~ProfScope() {
+        if (p) p->end(tok, st);
+    }
+};
+
+thread_local std::string g_last_error = "no error";
+
+corutv_status fail(corutv_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define CK(expr)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(CORUTV_ECUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                  \
+    } while (0)
+
+#define CKS(expr)                          \
+    do {                                   \
+        corutv_status s_ = (expr);         \
+        if (s_ != CORUTV_OK) return s_;    \
+    } while (0)
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// Bump allocator over one device buffer; the same code measures (base ==
+// nullptr) and carves.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+    template <typename T>
+    T* take(int64_t count) {
+        const size_t bytes = (size_t)round_up((int64_t)(count * (int64_t)sizeof(T)), 256);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+struct DeviceBuffer {
+    void* ptr = nullptr;
+    size_t cap = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Plan and buffers of one factorisation.
+// ---------------------------------------------------------------------------
+struct FactorPlan {
+    int64_t m, n, lda, k, p, q, ell, ellp, ldm, ldn;
+    ElemType ta;
+    corutv_prec prec;
+    ElemType tcomp;   // element type of the B operand of the sketch products
+    ElemType tdproj;  // arithmetic of the projection pass (eq. 7)
+    bool tensor;      // sketch products on tcgen05
+    int sp_ax, sp_aty, sp_w, gs_m, gs_n;
+    int64_t part_elems;
+    int num_sms;
+};
+
+struct FactorBufs {
+    double *x, *c1, *q1, *c2, *q2, *w, *tmp, *gpart, *g, *r, *d, *qt, *rt, *upanel, *zpanel;
+    void *xc, *q1c, *q2c, *part;
+    void* abf;        // bf16 copy of A for CORUTV_P_BF16
+    int *perm, *skip;
+};
+
+corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64_t lda, int64_t k,
+                        int64_t p, int64_t q, corutv_prec prec, int num_sms) {
+    pl.m = m; pl.n = n; pl.lda = lda; pl.k = k; pl.p = p; pl.q = q;
+    pl.ell = k + p;
+    pl.ta = ta;
+    pl.prec = prec;
+    pl.num_sms = num_sms;
+    if (m < 1 || n < 1 || k < 1 || p < 0 || q < 0)
+        return fail(CORUTV_EINVAL, "invalid sizes m=%lld n=%lld k=%lld p=%lld q=%lld", (long long)m,
+                    (long long)n, (long long)k, (long long)p, (long long)q);
+    if (pl.ell >= std::min(m, n))
+        return fail(CORUTV_EINVAL, "ell = k + p = %lld must be < min(m, n) = %lld", (long long)pl.ell,
+                    (long long)std::min(m, n));
+    if (pl.ell > 128) return fail(CORUTV_EINVAL, "ell = %lld exceeds the supported maximum 128", (long long)pl.ell);
+    if (lda < n) return fail(CORUTV_EINVAL, "lda = %lld < n = %lld", (long long)lda, (long long)n);
+    if (prec < CORUTV_P_F64 || prec > CORUTV_P_BF16) return fail(CORUTV_EINVAL, "unknown sketch precision %d", (int)prec);
+    pl.tensor = (prec == CORUTV_P_TF32 || prec == CORUTV_P_BF16);
+    if (prec == CORUTV_P_TF32 && ta != T_F32)
+        return fail(CORUTV_EINVAL, "TF32 sketches need FP32 input (dtype CORUTV_F32)");
+    pl.ellp = pl.tensor ? round_up(pl.ell, 16) : pl.ell;
+    pl.ldm = round_up(m, 64);
+    pl.ldn = round_up(n, 64);
+    pl.tcomp = pl.tensor ? (prec == CORUTV_P_BF16 ? T_BF16 : T_F32) : (prec == CORUTV_P_F64 ? T_F64 : T_F32);
+    pl.tdproj = (ta == T_F64) ? T_F64 : T_F32;
+    pl.sp_ax = gemm_simt_splits(m, n, num_sms);
+    pl.sp_aty = gemm_simt_splits(n, m, num_sms);
+    pl.sp_w = pl.sp_ax;
+    pl.gs_m = gemm_simt_splits(pl.ell, m, num_sms);
+    pl.gs_n = gemm_simt_splits(pl.ell, n, num_sms);
+    int64_t part = std::max((int64_t)pl.sp_ax * pl.ellp * pl.ldm, (int64_t)pl.sp_aty * pl.ellp * pl.ldn);
+    if (pl.tensor) part = std::max(part, tc_partial_elems(pl.m, pl.n, pl.ellp, pl.ldm, pl.ldn, num_sms));
+    pl.part_elems = part;
+    return CORUTV_OK;
+}
+
+template <typename C>
+void carve_factor(C& cv, const FactorPlan& pl, FactorBufs& b) {
+    const int64_t pm = pl.ellp * pl.ldm, pn = pl.ellp * pl.ldn, ll = pl.ellp * pl.ellp;
+    const int es_c = elem_size(pl.tcomp), es_d = elem_size(pl.tdproj);
+    b.x = cv.template take<double>(pn);
+    b.c1 = cv.template take<double>(pm);
+    b.q1 = cv.template take<double>(pm);
+    b.c2 = cv.template take<double>(pn);
+    b.q2 = cv.template take<double>(pn);
+    b.w = cv.template take<double>(pm);
+    b.upanel = cv.template take<double>(pm);
+    b.zpanel = cv.template take<double>(pn);
+    b.tmp = cv.template take<double>(std::max(pm, pn));
+    b.gpart = cv.template take<double>((int64_t)std::max(pl.gs_m, pl.gs_n) * ll);
+    b.g = cv.template take<double>(ll);
+    b.r = cv.template take<double>(ll);
+    b.d = cv.template take<double>(ll);
+    b.qt = cv.template take<double>(ll);
+    b.rt = cv.template take<double>(ll);
+    b.xc = cv.template take<char>(pn * es_c);
+    b.q1c = cv.template take<char>(pm * es_c);
+    b.q2c = cv.template take<char>(pn * es_d);
+    b.part = cv.template take<char>(pl.part_elems * std::max(8, std::max(es_c, es_d)));
+    b.abf = pl.prec == CORUTV_P_BF16 ? cv.template take<char>(pl.m * round_up(pl.n, 8) * 2) : nullptr;
+    b.perm = cv.template take<int>(pl.ellp);
+    b.skip = cv.template take<int>(8);
+}
+
+size_t factor_bytes(const FactorPlan& pl) {
+    Carver cv(nullptr);
+    FactorBufs b;
+    carve_factor(cv, pl, b);
+    return cv.off;
+}
+
+struct Exec {
+    cudaStream_t st;
+    int* flags;
+    const int* cancel;
+    int num_sms;
+    Profiler* prof = nullptr;
+};
+
+// C = A X (am = A_ROWS, R = m, K = n) or A^T Y (am = A_COLS, R = n, K = m) on SIMT cores.
+corutv_status sketch_simt(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, AMode am,
+                          const void* a, ElemType ta, const void* bop, ElemType tc, double* out,
+                          int64_t ldout) {
+    const int64_t R = am == A_ROWS ? pl.m : pl.n;
+    const int64_t K = am == A_ROWS ? pl.n : pl.m;
+    const int splits = am == A_ROWS ? pl.sp_ax : pl.sp_aty;
+    const int64_t ldb = am == A_ROWS ? pl.ldn : pl.ldm;
+    GemmArgs g{am, B_PANEL, O_PANEL, ta, tc, a, pl.lda, bop, ldb, b.part, ldout, pl.ellp * ldout,
+               R, K, pl.ell, splits, ex.cancel};
+    {
+        ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
+        CK(launch_gemm_simt(g, ex.st));
+    }
+    CK(launch_reduce_splits(b.part, tc, splits, pl.ellp * ldout, out, ldout, R, pl.ell, ldout, ex.cancel,
+                            ex.st));
+    return CORUTV_OK;
+}
+
+// G = X^T Y (ell x ell, FP64) for two FP64 panels of `len` rows.
+corutv_status gram(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, const double* x,
+                   int64_t ldx, const double* y, int64_t ldy, int64_t len, double* out,
+                   const int* cancel) {
+    const int gs = gemm_simt_splits(pl.ell, len, ex.num_sms);
+    const int64_t ll = pl.ell * pl.ell;
+    GemmArgs g{A_PANEL_T, B_PANEL, O_ROWMAJ, T_F64, T_F64, x, ldx, y, ldy, b.gpart, pl.ell, ll,
+               pl.ell, len, pl.ell, gs, cancel};
+    CK(launch_gemm_simt(g, ex.st));
+    CK(launch_reduce_splits(b.gpart, T_F64, gs, ll, out, pl.ell, pl.ell, pl.ell, pl.ell, cancel, ex.st));
+    return CORUTV_OK;
+}
+
+// Thin QR of the FP64 panel c (len x ell) by CholeskyQR2, with one more
+// pass when the first Gram needed the shift (shifted CholeskyQR3).
+// Writes the FP64 panel q and, if qc != nullptr, a copy of type tqc.
+corutv_status orth(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, const double* c,
+                   int64_t ld, int64_t len, double* q, void* qc, ElemType tqc, double* r_out) {
+    const int64_t ell = pl.ell;
+    ProfScope ps(ex.prof, CORUTV_STAGE_ORTH, ex.st);
+    // pass 1
+    CKS(gram(ex, pl, b, c, ld, c, ld, len, b.g, ex.cancel));
+    CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, b.skip, ex.cancel, ex.st));
+    CK(launch_trsm_rows(c, ld, len, ell, b.r, T_F64, b.tmp, ld, nullptr, T_F64, 0, ex.cancel, ex.st));
+    // pass 1b, only after a shifted pass 1
+    CKS(gram(ex, pl, b, b.tmp, ld, b.tmp, ld, len, b.g, b.skip));
+    CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, nullptr, b.skip, ex.st));
+    CK(launch_trsm_rows(b.tmp, ld, len, ell, b.r, T_F64, b.tmp, ld, nullptr, T_F64, 0, b.skip, ex.st));
+    // pass 2
+    CKS(gram(ex, pl, b, b.tmp, ld, b.tmp, ld, len, b.g, ex.cancel));
+    CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, nullptr, ex.cancel, ex.st));
+    CK(launch_trsm_rows(b.tmp, ld, len, ell, b.r, T_F64, q, ld, qc, tqc, ld, ex.cancel, ex.st));
+    (void)r_out;
+    return CORUTV_OK;
+}
+
+// Algorithm 1 on device data; leaves Q1, Q2, D, Qt, Rt, perm in the buffers.
+// psi_dev: optional n x ell row-major FP64 test matrix.
+corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, const void* a,
+                         const double* psi_dev, uint64_t seed, uint32_t sid) {
+    const int64_t m = pl.m, n = pl.n, ell = pl.ell;
+    ProfScope ps_all(ex.prof, CORUTV_STAGE_FACTOR, ex.st);
+    // Step 1: X = Psi (panel n x ellp, padding columns zero)
+    if (psi_dev) CK(launch_rowmajor_to_panel(psi_dev, ell, n, ell, pl.ellp, b.x, pl.ldn, ex.st));
+    else CK(launch_gaussian_panel(seed, sid, n, ell, pl.ellp, b.x, pl.ldn, ex.cancel, ex.st));
+    if (pl.tensor) {
+        CK(launch_panel_convert(b.x, pl.ldn, n, pl.ellp, b.xc, pl.tcomp, pl.ldn, ex.cancel, ex.st));
+        if (pl.prec == CORUTV_P_BF16)
+            CK(launch_cast_bf16(a, pl.ta, m, n, pl.lda, b.abf, round_up(n, 8), ex.cancel, ex.st));
+    } else {
+        CK(launch_panel_convert(b.x, pl.ldn, n, ell, b.xc, pl.tcomp, pl.ldn, ex.cancel, ex.st));
+    }
+    const int64_t ldabf = round_up(n, 8);
+    for (int64_t it = 0; it <= pl.q; ++it) {
+        // eq. 4: C1 = A X
+        if (pl.tensor) {
+            const void* aop = pl.prec == CORUTV_P_BF16 ? b.abf : a;
+            const int64_t lda_op = pl.prec == CORUTV_P_BF16 ? ldabf : pl.lda;
+            ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
+            CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, /*trans=*/0, b.xc, pl.ldn, ell, pl.ellp, b.part,
+                                b.c1, pl.ldm, ex.num_sms, ex.flags, ex.cancel, ex.st));
+        } else {
+            CKS(sketch_simt(ex, pl, b, A_ROWS, a, pl.ta, b.xc, pl.tcomp, b.c1, pl.ldm));
+        }
+        CKS(orth(ex, pl, b, b.c1, pl.ldm, m, b.q1, b.q1c, pl.tcomp, nullptr));
+        // eq. 5 (with C1 -> Q1): C2 = A^T Q1
+        if (pl.tensor) {
+            const void* aop = pl.prec == CORUTV_P_BF16 ? b.abf : a;
+            const int64_t lda_op = pl.prec == CORUTV_P_BF16 ? ldabf : pl.lda;
+            ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
+            CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, /*trans=*/1, b.q1c, pl.ldm, ell, pl.ellp, b.part,
+                                b.c2, pl.ldn, ex.num_sms, ex.flags, ex.cancel, ex.st));
+        } else {
+            CKS(sketch_simt(ex, pl, b, A_COLS, a, pl.ta, b.q1c, pl.tcomp, b.c2, pl.ldn));
+        }
+        if (it < pl.q) CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.x, b.xc, pl.tcomp, nullptr));
+    }
+    // Q2 = qr(C2), with a copy in the projection's arithmetic
+    CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.q2, b.q2c, pl.tdproj, nullptr));
+    // eq. 7: W = A Q2 (FP64 or FP32 from the original A), D = Q1^T W (FP64)
+    {
+        GemmArgs g{A_ROWS, B_PANEL, O_PANEL, pl.ta, pl.tdproj, a, pl.lda, b.q2c, pl.ldn, b.part, pl.ldm,
+                   pl.ellp * pl.ldm, m, n, ell, pl.sp_w, ex.cancel};
+        {
+            ProfScope ps(ex.prof, CORUTV_STAGE_PROJECT, ex.st);
+            CK(launch_gemm_simt(g, ex.st));
+        }
+        CK(launch_reduce_splits(b.part, pl.tdproj, pl.sp_w, pl.ellp * pl.ldm, b.w, pl.ldm, m, ell, pl.ldm,
+                                ex.cancel, ex.st));
+    }
+    CKS(gram(ex, pl, b, b.q1, pl.ldm, b.w, pl.ldm, m, b.d, ex.cancel));
+    // eq. 8: D P = Qt Rt
+    {
+        ProfScope ps(ex.prof, CORUTV_STAGE_QRCP, ex.st);
+        CK(launch_qrcp(b.d, ell, b.qt, b.rt, b.perm, ex.cancel, ex.st));
+    }
+    return CORUTV_OK;
+}
+
+// Eq. 9 into caller buffers (device): U = Q1 Qt, T = Rt, V = Q2 P, perm.
+corutv_status emit_user(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, ElemType tout, void* u,
+                        int64_t ldu, void* t, void* v, int64_t ldv, int32_t* perm) {
+    const int64_t ell = pl.ell;
+    if (u) {
+        GemmArgs g{A_PANEL, B_SMALL, O_ROWMAJ, T_F64, tout, b.q1, pl.ldm, nullptr, ell, u, ldu, 0,
+                   pl.m, ell, ell, 1, ex.cancel};
+        // the B operand must have the compute type: Qt in FP64, or converted for FP32
+        if (tout == T_F64) {
+            g.b = b.qt;
+        } else {
+            CK(launch_copy_small(b.qt, ell, b.g, T_F32, ex.cancel, ex.st));  // b.g reused as FP32 scratch
+            g.b = b.g;
+        }
+        CK(launch_gemm_simt(g, ex.st));
+    }
+    CK(launch_copy_small(b.rt, ell, t, tout, ex.cancel, ex.st));
+    if (v) CK(launch_gather_v(b.q2, pl.ldn, pl.n, ell, b.perm, v, tout, ldv, ex.cancel, ex.st));
+    if (perm) CK(cudaMemcpyAsync(perm, b.perm, sizeof(int32_t) * ell, cudaMemcpyDeviceToDevice, ex.st));
+    return CORUTV_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct ServingSlot {
+    cudaStream_t st = nullptr;
+    DeviceBuffer ws;
+    int* flags = nullptr;   // device
+    int* hflags = nullptr;  // pinned host mirror
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    uint64_t ticket = 0;
+    int32_t* perm_host = nullptr;
+};
+
+struct PendingReq {
+    uint64_t ticket;
+    corutv_request req;
+    std::chrono::steady_clock::time_point t0;
+    size_t bytes;
+    bool host;
+};
+
+struct ReqResult {
+    bool done = false;
+    corutv_status status = CORUTV_EPENDING;
+    double latency = 0.0;
+    std::chrono::steady_clock::time_point t0;
+};
+
+struct corutv_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t budget = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::mutex call_mu;
+    DeviceBuffer ws;
+    int* flags = nullptr;
+    Profiler prof;
+    // serving
+    int max_slots = 8;
+    std::vector<ServingSlot> slots;
+    std::mutex smu;
+    std::condition_variable scv;
+    std::deque<PendingReq> queue;
+    std::map<uint64_t, ReqResult> results;
+    std::thread worker;
+    bool stop = false;
+    bool worker_started = false;
+    uint64_t next_ticket = 1;
+    size_t serving_bytes = 0;
+};
+
+namespace {
+
+corutv_status ensure_ws(corutv_ctx* ctx, DeviceBuffer& buf, size_t bytes, cudaStream_t st) {
+    if (buf.cap >= bytes) return CORUTV_OK;
+    if (bytes > ctx->budget)
+        return fail(CORUTV_ENOMEM, "workspace of %zu bytes exceeds the context budget %zu", bytes, ctx->budget);
+    if (buf.ptr) {
+        CK(cudaStreamSynchronize(st));
+        CK(cudaFree(buf.ptr));
+        buf.ptr = nullptr;
+        buf.cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&buf.ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        buf.ptr = nullptr;
+        return fail(CORUTV_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    buf.cap = bytes;
+    return CORUTV_OK;
+}
+
+corutv_status check_ctx(const corutv_ctx* ctx) {
+    if (!ctx) return fail(CORUTV_EINVAL, "null context");
+    return CORUTV_OK;
+}
+
+corutv_status read_flags(corutv_ctx* ctx, int* hf) {
+    CK(cudaMemcpyAsync(hf, ctx->flags, sizeof(int) * FLAG_COUNT, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return CORUTV_OK;
+}
+
+corutv_status flags_status(const int* hf) {
+    if (hf[FLAG_BREAKDOWN]) return fail(CORUTV_EBREAKDOWN, "Cholesky of a sketch Gram matrix broke down");
+    if (hf[FLAG_TIMEOUT]) return fail(CORUTV_ETIMEDOUT, "a bounded device wait gave up");
+    return CORUTV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+corutv_status corutv_create(corutv_ctx** out, int device, size_t mem_budget_bytes, int max_slots) {
+    if (!out) return fail(CORUTV_EINVAL, "out is NULL");
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        return fail(CORUTV_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
+    }
+    if (device < 0 || device >= count) return fail(CORUTV_EINVAL, "device %d out of range [0, %d)", device, count);
+    DeviceGuard guard(device);
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, device));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(CORUTV_ECUDA, "device %d is sm_%d%d; this library is built for sm_103a only", device,
+                    prop.major, prop.minor);
+    auto* ctx = new corutv_ctx();
+    ctx->device = device;
+    ctx->num_sms = prop.multiProcessorCount;
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    ctx->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)(0.9 * (double)free_b);
+    ctx->max_slots = max_slots > 0 ? max_slots : 8;
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete ctx;
+        return fail(CORUTV_ECUDA, "cudaStreamCreate failed");
+    }
+    ctx->own_stream = true;
+    if (cudaMalloc(&ctx->flags, sizeof(int) * FLAG_COUNT) != cudaSuccess ||
+        cudaMemset(ctx->flags, 0, sizeof(int) * FLAG_COUNT) != cudaSuccess) {
+        cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return fail(CORUTV_ENOMEM, "cannot allocate the status words");
+    }
+    *out = ctx;
+    return CORUTV_OK;
+}
+
+corutv_status corutv_destroy(corutv_ctx* ctx) {
+    if (!ctx) return CORUTV_OK;
+    DeviceGuard guard(ctx->device);
+    if (ctx->worker_started) {
+        {
+            std::lock_guard<std::mutex> lk(ctx->smu);
+            ctx->stop = true;
+        }
+        ctx->scv.notify_all();
+        ctx->worker.join();
+    }
+    for (auto& s : ctx->slots) {
+        if (s.st) cudaStreamSynchronize(s.st);
+        if (s.ws.ptr) cudaFree(s.ws.ptr);
+        if (s.flags) cudaFree(s.flags);
+        if (s.hflags) cudaFreeHost(s.hflags);
+        if (s.done) cudaEventDestroy(s.done);
+        if (s.st) cudaStreamDestroy(s.st);
+    }
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->ws.ptr) cudaFree(ctx->ws.ptr);
+    if (ctx->flags) cudaFree(ctx->flags);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return CORUTV_OK;
+}
+
+const char* corutv_last_error(const corutv_ctx* ctx) {
+    (void)ctx;
+    return g_last_error.c_str();
+}
+
+corutv_status corutv_set_stream(corutv_ctx* ctx, void* cuda_stream) {
+    CKS(check_ctx(ctx));
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    DeviceGuard guard(ctx->device);
+    if (ctx->own_stream) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaStreamDestroy(ctx->stream));
+        ctx->own_stream = false;
+    }
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    return CORUTV_OK;
+}
+
+corutv_status corutv_sync(corutv_ctx* ctx) {
+    CKS(check_ctx(ctx));
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    DeviceGuard guard(ctx->device);
+    int hf[FLAG_COUNT];
+    CKS(read_flags(ctx, hf));
+    CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int) * FLAG_COUNT, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return flags_status(hf);
+}
+
+corutv_status corutv_profile_enable(corutv_ctx* ctx, int enable) {
+    CKS(check_ctx(ctx));
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    DeviceGuard guard(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->prof.collect();
+    ctx->prof.reset();
+    ctx->prof.on = enable != 0;
+    return CORUTV_OK;
+}
+
+corutv_status corutv_profile_read(corutv_ctx* ctx, int stage, double* total_ms, int64_t* count) {
+    CKS(check_ctx(ctx));
+    if (stage < CORUTV_STAGE_ALL || stage >= CORUTV_STAGE_COUNT) return fail(CORUTV_EINVAL, "unknown stage %d", stage);
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    DeviceGuard guard(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->prof.collect();
+    if (stage == CORUTV_STAGE_ALL) {
+        if (total_ms) *total_ms = 0.0;
+        if (count) *count = g_launches.load() - ctx->prof.launch_base;
+    } else {
+        if (total_ms) *total_ms = ctx->prof.ms[stage];
+        if (count) *count = ctx->prof.count[stage];
+    }
+    return CORUTV_OK;
+}
+
+corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, int64_t m, int64_t n,
+                            int64_t lda, const corutv_opts* opts, void* U, int64_t ldu, void* T, void* V,
+                            int64_t ldv, int32_t* perm) {
+    CKS(check_ctx(ctx));
+    if (!A || !opts || !T) return fail(CORUTV_EINVAL, "A, opts and T must not be NULL");
+    if (dtype != CORUTV_F64 && dtype != CORUTV_F32) return fail(CORUTV_EINVAL, "unknown dtype %d", (int)dtype);
+    if (opts->d_mode != 0) return fail(CORUTV_EINVAL, "d_mode %d is not supported (0 = exact D)", opts->d_mode);
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    DeviceGuard guard(ctx->device);
+    const ElemType ta = dtype == CORUTV_F64 ? T_F64 : T_F32;
+    const int es = elem_size(ta);
+    FactorPlan pl;
+    CKS(make_plan(pl, ta, m, n, lda, opts->k, opts->p, opts->q, (corutv_prec)opts->sketch_prec, ctx->num_sms));
+    const int64_t ell = pl.ell;
+    if (U && ldu < ell) return fail(CORUTV_EINVAL, "ldu < ell");
+    if (V && ldv < ell) return fail(CORUTV_EINVAL, "ldv < ell");
+    const bool dev = is_device_ptr(A);
+    if ((U && is_device_ptr(U) != dev) || is_device_ptr(T) != dev || (V && is_device_ptr(V) != dev) ||
+        (perm && is_device_ptr(perm) != dev))
+        return fail(CORUTV_EINVAL, "A and the outputs must all be host or all be device memory");
+    const bool psi_dev = opts->psi && is_device_ptr(opts->psi);
+    // workspace: factor buffers + staging for host calls / host psi
+    size_t bytes = factor_bytes(pl);
+    Carver extra_measure(nullptr);
+    if (!dev) {
+        extra_measure.take<char>(m * n * es);
+        extra_measure.take<char>(m * ell * es);
+        extra_measure.take<char>(n * ell * es);
+        extra_measure.take<char>(ell * ell * es);
+        extra_measure.take<int>(ell);
+    }
+    if (opts->psi && !psi_dev) extra_measure.take<double>(n * ell);
+    CKS(ensure_ws(ctx, ctx->ws, bytes + extra_measure.off, ctx->stream));
+    Carver cv(ctx->ws.ptr);
+    FactorBufs b;
+    carve_factor(cv, pl, b);
+    const void* a_dev = A;
+    void *u_dev = U, *t_dev = T, *v_dev = V;
+    int32_t* perm_dev = perm;
+    int64_t ldu_dev = ldu, ldv_dev = ldv;
+    if (!dev) {
+        void* as = cv.take<char>(m * n * es);
+        u_dev = U ? cv.take<char>(m * ell * es) : nullptr;
+        v_dev = V ? cv.take<char>(n * ell * es) : nullptr;
+        t_dev = cv.take<char>(ell * ell * es);
+        perm_dev = perm ? cv.take<int>(ell) : nullptr;
+        if (!U) cv.take<char>(m * ell * es);
+        if (!V) cv.take<char>(n * ell * es);
+        if (!perm) cv.take<int>(ell);
+        CK(cudaMemcpy2DAsync(as, n * es, A, lda * es, n * es, m, cudaMemcpyHostToDevice, ctx->stream));
+        a_dev = as;
+        ldu_dev = ell;
+        ldv_dev = ell;
+        pl.lda = n;
+    }
+    const double* psi = nullptr;
+    if (opts->psi) {
+        if (psi_dev) {
+            psi = opts->psi;
+        } else {
+            double* ps = cv.take<double>(n * ell);
+            CK(cudaMemcpyAsync(ps, opts->psi, sizeof(double) * n * ell, cudaMemcpyHostToDevice, ctx->stream));
+            psi = ps;
+        }
+    }
+    Exec ex{ctx->stream, ctx->flags, nullptr, ctx->num_sms, &ctx->prof};
+    CKS(run_factor(ex, pl, b, a_dev, psi, opts->seed, opts->stream));
+    CKS(emit_user(ex, pl, b, ta, u_dev, ldu_dev, t_dev, v_dev, ldv_dev, perm_dev));
+    if (!dev) {
+        if (U) CK(cudaMemcpy2DAsync(U, ldu * es, u_dev, ell * es, ell * es, m, cudaMemcpyDeviceToHost, ctx->stream));
+        if (V) CK(cudaMemcpy2DAsync(V, ldv * es, v_dev, ell * es, ell * es, n, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(T, t_dev, ell * ell * es, cudaMemcpyDeviceToHost, ctx->stream));
+        if (perm) CK(cudaMemcpyAsync(perm, perm_dev, sizeof(int32_t) * ell, cudaMemcpyDeviceToHost, ctx->stream));
+        int hf[FLAG_COUNT];
+        CKS(read_flags(ctx, hf));
+        CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int) * FLAG_COUNT, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return flags_status(hf);
+    }
+    CK(cudaGetLastError());
+    return CORUTV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Single steps.
+// ---------------------------------------------------------------------------
+corutv_status corutv_gaussian(corutv_ctx* ctx, uint64_t seed, uint32_t stream, int64_t n, int64_t ell,
+                              double* psi, int64_t ldpsi) {
+    CKS(check_ctx(ctx));
+    if (!psi || n < 1 || ell < 1 || ldpsi < ell) return fail(CORUTV_EINVAL, "bad gaussian arguments");
+    if (!is_device_ptr(psi)) return fail(CORUTV_EINVAL, "psi must be device memory");
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    DeviceGuard guard(ctx->device);
+    CK(launch_gaussian_rowmajor(seed, stream, n, ell, psi, ldpsi, ctx->stream));
+    return CORUTV_OK;
+}
+
+corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec prec, int trans, const void* A,
+                            int64_t m, int64_t n, int64_t lda, const double* X, int64_t ldx, int64_t ell,
+                            double* C, int64_t ldc) {
+    CKS(check_ctx(ctx));
+    if (!A || !X || !C) return fail(CORUTV_EINVAL, "null pointer");
+    if (!is_device_ptr(A) || !is_device_ptr(X) || !is_device_ptr(C))
+        return fail(CORUTV_EINVAL, "corutv_sketch takes device pointers only");
+    const int64_t xrows = trans ? m : n, crows = trans ? n : m;
+    if (ell < 1 || ell > 128 || ldx < ell || ldc < ell || lda < n || m < 1 || n < 1)
+        return fail(CORUTV_EINVAL, "bad sketch sizes");
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    DeviceGuard guard(ctx->device);
+    const ElemType ta = dtype == CORUTV_F64 ? T_F64 : T_F32;
+    FactorPlan pl;
+    // plan with k = ell, p = 0, q = 0; sizes m, n need ell < min(m, n) only for the full pipeline
+    pl.m = m; pl.n = n; pl.lda = lda; pl.k = ell; pl.p = 0; pl.q = 0; pl.ell = ell; pl.ta = ta; pl.prec = prec;
+    pl.num_sms = ctx->num_sms;
+    pl.tensor = (prec == CORUTV_P_TF32 || prec == CORUTV_P_BF16);
+    if (prec == CORUTV_P_TF32 && ta != T_F32) return fail(CORUTV_EINVAL, "TF32 needs FP32 input");
+    pl.ellp = pl.tensor ? round_up(ell, 16) : ell;
+    pl.ldm = round_up(m, 64);
+    pl.ldn = round_up(n, 64);
+    pl.tcomp = pl.tensor ? (prec == CORUTV_P_BF16 ? T_BF16 : T_F32) : (prec == CORUTV_P_F64 ? T_F64 : T_F32);
+    pl.tdproj = pl.tcomp;
+    pl.sp_ax = gemm_simt_splits(m, n, ctx->num_sms);
+    pl.sp_aty = gemm_simt_splits(n, m, ctx->num_sms);
+    pl.sp_w = pl.sp_ax;
+    pl.gs_m = pl.gs_n = 1;
+    pl.part_elems = std::max((int64_t)pl.sp_ax * pl.ellp * pl.ldm, (int64_t)pl.sp_aty * pl.ellp * pl.ldn);
+    if (pl.tensor) pl.part_elems = std::max(pl.part_elems, tc_partial_elems(m, n, pl.ellp, pl.ldm, pl.ldn, ctx->num_sms));
+    const int64_t ldxp = trans ? pl.ldm : pl.ldn, ldcp = trans ? pl.ldn : pl.ldm;
+    Carver measure(nullptr);
+    measure.take<double>(pl.ellp * ldxp);
+    measure.take<char>(pl.ellp * ldxp * 8);
+    measure.take<double>(pl.ellp * ldcp);
+    measure.take<char>(pl.part_elems * 8);
+    if (prec == CORUTV_P_BF16) measure.take<char>(m * round_up(n, 8) * 2);
+    CKS(ensure_ws(ctx, ctx->ws, measure.off, ctx->stream));
+    Carver cv(ctx->ws.ptr);
+    double* xp = cv.take<double>(pl.ellp * ldxp);
+    void* xc = cv.take<char>(pl.ellp * ldxp * 8);
+    double* cp = cv.take<double>(pl.ellp * ldcp);
+    FactorBufs b{};
+    b.part = cv.take<char>(pl.part_elems * 8);
+    b.abf = prec == CORUTV_P_BF16 ? cv.take<char>(m * round_up(n, 8) * 2) : nullptr;
+    CK(launch_rowmajor_to_panel(X, ldx, xrows, ell, pl.ellp, xp, ldxp, ctx->stream));
+    CK(launch_panel_convert(xp, ldxp, xrows, pl.ellp, xc, pl.tcomp, ldxp, nullptr, ctx->stream));
+    Exec ex{ctx->stream, ctx->flags, nullptr, ctx->num_sms};
+    if (pl.tensor) {
+        const void* aop = A;
+        int64_t lda_op = lda;
+        if (prec == CORUTV_P_BF16) {
+            CK(launch_cast_bf16(A, ta, m, n, lda, b.abf, round_up(n, 8), nullptr, ctx->stream));
+            aop = b.abf;
+            lda_op = round_up(n, 8);
+        }
+        CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, trans, xc, ldxp, ell, pl.ellp, b.part, cp, ldcp,
+                            ctx->num_sms, ctx->flags, nullptr, ctx->stream));
+    } else {
+        CKS(sketch_simt(ex, pl, b, trans ? A_COLS : A_ROWS, A, ta, xc, pl.tcomp, cp, ldcp));
+    }
+    CK(launch_panel_to_rowmajor(cp, ldcp, crows, ell, C, T_F64, ldc, nullptr, ctx->stream));
+    return CORUTV_OK;
+}
+
+corutv_status corutv_orth(corutv_ctx* ctx, const double* C, int64_t rows, int64_t ell, int64_t ldc, double* Q,
+                          int64_t ldq, double* R) {
+    CKS(check_ctx(ctx));
+    if (!C || !Q) return fail(CORUTV_EINVAL, "null pointer");
+    if (!is_device_ptr(C) || !is_device_ptr(Q) || (R && !is_device_ptr(R)))
+        return fail(CORUTV_EINVAL, "corutv_orth takes device pointers only");
+    if (ell < 1 || ell > 128 || rows < ell || ldc < ell || ldq < ell) return fail(CORUTV_EINVAL, "bad orth sizes");
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    DeviceGuard guard(ctx->device);
+    FactorPlan pl{};
+    pl.ell = ell; pl.ellp = ell; pl.m = rows; pl.ldm = round_up(rows, 64);
+    pl.gs_m = gemm_simt_splits(ell, rows, ctx->num_sms);
+    pl.gs_n = pl.gs_m;
+    const int64_t pm = ell * pl.ldm;
+    Carver measure(nullptr);
+    measure.take<double>(pm);
+    measure.take<double>(pm);
+    measure.take<double>(pm);
+    measure.take<double>((int64_t)pl.gs_m * ell * ell);
+    measure.take<double>(ell * ell);
+    measure.take<double>(ell * ell);
+    measure.take<int>(8);
+    CKS(ensure_ws(ctx, ctx->ws, measure.off, ctx->stream));
+    Carver cv(ctx->ws.ptr);
+    double* cp = cv.take<double>(pm);
+    double* qp = cv.take<double>(pm);
+    FactorBufs b{};
+    b.tmp = cv.take<double>(pm);
+    b.gpart = cv.take<double>((int64_t)pl.gs_m * ell * ell);
+    b.g = cv.take<double>(ell * ell);
+    b.r = cv.take<double>(ell * ell);
+    b.skip = cv.take<int>(8);
+    CK(launch_rowmajor_to_panel(C, ldc, rows, ell, ell, cp, pl.ldm, ctx->stream));
+    Exec ex{ctx->stream, ctx->flags, nullptr, ctx->num_sms};
+    CKS(orth(ex, pl, b, cp, pl.ldm, rows, qp, nullptr, T_F64, nullptr));
+    CK(launch_panel_to_rowmajor(qp, pl.ldm, rows, ell, Q, T_F64, ldq, nullptr, ctx->stream));
+    if (R) {
+        // R of C = Q R: R = Q^T C (exact in exact arithmetic; upper triangular)
+        CKS(gram(ex, pl, b, qp, pl.ldm, cp, pl.ldm, rows, b.g, nullptr));
+        CK(cudaMemcpyAsync(R, b.g, sizeof(double) * ell * ell, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    return CORUTV_OK;
+}
+
+corutv_status corutv_qrcp(corutv_ctx* ctx, const double* D, int64_t ell, double* Qt, double* Rt, int32_t* perm) {
+    CKS(check_ctx(ctx));
+    if (!D || !Qt || !Rt || !perm) return fail(CORUTV_EINVAL, "null pointer");
+    if (!is_device_ptr(D) || !is_device_ptr(Qt) || !is_device_ptr(Rt) || !is_device_ptr(perm))
+        return fail(CORUTV_EINVAL, "corutv_qrcp takes device pointers only");
+    if (ell < 1 || ell > 128) return fail(CORUTV_EINVAL, "ell must be in [1, 128]");
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    DeviceGuard guard(ctx->device);
+    CK(launch_qrcp(D, ell, Qt, Rt, perm, nullptr, ctx->stream));
+    return CORUTV_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// ALM-CoRUTV
+// ---------------------------------------------------------------------------
+namespace {
+
+corutv_status normest(corutv_ctx* ctx, const FactorPlan& pl, const FactorBufs& b, const void* mat,
+                      ElemType tm, int64_t ldm_user, double* out_norm2) {
+    const int64_t m = pl.m, n = pl.n;
+    double* v = b.x;    // n x 1 panel
+    double* u = b.c1;   // m x 1 panel
+    double* w = b.c2;   // n x 1 panel
+    double* lam = b.g;  // scalar
+    CK(launch_vec_fill(v, n, 1.0 / std::sqrt((double)n), ctx->stream));
+    const int spm = gemm_simt_splits(m, n, ctx->num_sms), spn = gemm_simt_splits(n, m, ctx->num_sms);
+    for (int it = 0; it < 50; ++it) {
+        GemmArgs g1{A_ROWS, B_PANEL, O_PANEL, tm, T_F64, mat, ldm_user, v, pl.ldn, b.part, pl.ldm, pl.ldm,
+                    m, n, 1, spm, nullptr};
+        CK(launch_gemm_simt(g1, ctx->stream));
+        CK(launch_reduce_splits(b.part, T_F64, spm, pl.ldm, u, pl.ldm, m, 1, pl.ldm, nullptr, ctx->stream));
+        GemmArgs g2{A_COLS, B_PANEL, O_PANEL, tm, T_F64, mat, ldm_user, u, pl.ldm, b.part, pl.ldn, pl.ldn,
+                    n, m, 1, spn, nullptr};
+        CK(launch_gemm_simt(g2, ctx->stream));
+        CK(launch_reduce_splits(b.part, T_F64, spn, pl.ldn, w, pl.ldn, n, 1, pl.ldn, nullptr, ctx->stream));
+        CK(launch_vec_normalize(w, v, n, lam, ctx->stream));
+    }
+    double h = 0.0;
+    CK(cudaMemcpyAsync(&h, lam, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *out_norm2 = std::sqrt(h);
+    return CORUTV_OK;
+}
+
+}  // namespace
+
+extern "C" corutv_status corutv_rpca(corutv_ctx* ctx, corutv_dtype dtype, const void* M, int64_t m, int64_t n,
+                                     int64_t ldm, const corutv_opts* opts, double lambda, double mu0,
+                                     double mu_bar, double rho, double tol, int max_iter, void* L, void* S,
+                                     int* iters, double* zeta, int* rank) {
+    CKS(check_ctx(ctx));
+    if (!M || !opts || !L || !S) return fail(CORUTV_EINVAL, "M, opts, L and S must not be NULL");
+    if (dtype != CORUTV_F64 && dtype != CORUTV_F32) return fail(CORUTV_EINVAL, "unknown dtype");
+    const int64_t k = opts->k;
+    if (k < 1 || 2 * k > 64) return fail(CORUTV_EINVAL, "rank guess k must be in [1, 32] (ell = 2k <= 64)");
+    if (ldm < n) return fail(CORUTV_EINVAL, "ldm < n");
+    const bool dev = is_device_ptr(M);
+    if (is_device_ptr(L) != dev || is_device_ptr(S) != dev)
+        return fail(CORUTV_EINVAL, "M, L and S must all be host or all be device memory");
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    DeviceGuard guard(ctx->device);
+    const ElemType tm = dtype == CORUTV_F64 ? T_F64 : T_F32;
+    const int es = elem_size(tm);
+    corutv_prec prec = (corutv_prec)opts->sketch_prec;
+    if (prec != CORUTV_P_F64 && prec != CORUTV_P_F32 && prec != CORUTV_P_TF32 && prec != CORUTV_P_BF16)
+        return fail(CORUTV_EINVAL, "unknown sketch precision");
+    if (max_iter <= 0) max_iter = 100;
+    if (tol <= 0) tol = 1e-5;
+    if (rho <= 0) rho = 1.6;
+    if (lambda <= 0) lambda = 1.0 / std::sqrt((double)std::max(m, n));
+    FactorPlan pl;
+    CKS(make_plan(pl, tm, m, n, n, k, k, 1, prec, ctx->num_sms));
+    const int64_t mn = m * n;
+    const int nup = rpca_update_blocks(m, n);
+    size_t bytes = factor_bytes(pl);
+    Carver measure(nullptr);
+    measure.take<char>(mn * es);  // Y
+    measure.take<char>(mn * es);  // B
+    measure.take<double>(std::max(nup, 1184));  // residual partials
+    measure.take<double>(1184);  // ||M||_F partials
+    measure.take<double>(max_iter);
+    measure.take<int>(4);
+    if (!dev) {
+        measure.take<char>(mn * es);  // M
+        measure.take<char>(mn * es);  // L
+        measure.take<char>(mn * es);  // S
+    }
+    CKS(ensure_ws(ctx, ctx->ws, bytes + measure.off, ctx->stream));
+    Carver cv(ctx->ws.ptr);
+    FactorBufs b;
+    carve_factor(cv, pl, b);
+    void* y = cv.take<char>(mn * es);
+    void* bmat = cv.take<char>(mn * es);
+    double* res_part = cv.take<double>(std::max(nup, 1184));
+    double* fro_part = cv.take<double>(1184);
+    double* zhist = cv.take<double>(max_iter);
+    int* rank_dev = cv.take<int>(4);
+    const void* m_dev = M;
+    int64_t ldm_dev = ldm;
+    void *l_dev = L, *s_dev = S;
+    if (!dev) {
+        void* ms = cv.take<char>(mn * es);
+        l_dev = cv.take<char>(mn * es);
+        s_dev = cv.take<char>(mn * es);
+        CK(cudaMemcpy2DAsync(ms, n * es, M, ldm * es, n * es, m, cudaMemcpyHostToDevice, ctx->stream));
+        m_dev = ms;
+        ldm_dev = n;
+    }
+    CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int) * FLAG_COUNT, ctx->stream));
+    CK(cudaMemsetAsync(rank_dev, 0, sizeof(int) * 4, ctx->stream));
+    int nfro = 0;
+    CK(launch_rpca_init(m_dev, tm, ldm_dev, m, n, static_cast<float*>(s_dev), static_cast<float*>(y),
+                        static_cast<float*>(bmat), static_cast<double*>(s_dev), static_cast<double*>(y),
+                        static_cast<double*>(bmat), fro_part, &nfro, ctx->stream));
+    if (mu0 <= 0) {
+        double nrm = 0.0;
+        CKS(normest(ctx, pl, b, m_dev, tm, ldm_dev, &nrm));
+        if (!(nrm > 0)) return fail(CORUTV_EINVAL, "M has zero spectral norm");
+        mu0 = 1.25 / nrm;
+    }
+    if (mu_bar <= 0) mu_bar = 1e7 * mu0;
+    std::vector<double> mus(max_iter + 1);
+    mus[0] = mu0;
+    for (int j = 1; j <= max_iter; ++j) mus[j] = std::min(rho * mus[j - 1], mu_bar);
+    const int* done = ctx->flags + FLAG_RPCA_DONE;
+    Exec ex{ctx->stream, ctx->flags, done, ctx->num_sms, &ctx->prof};
+    for (int j = 0; j < max_iter; ++j) {
+        // L_{j+1} = C_{1/mu_j}(B_j): CoR-UTV of B_j with ell = 2k, q = 1, fresh Psi
+        CKS(run_factor(ex, pl, b, bmat, nullptr, opts->seed, opts->stream + (uint32_t)j + 1u));
+        GemmArgs gu{A_PANEL, B_SMALL, O_PANEL, T_F64, T_F64, b.q1, pl.ldm, b.qt, pl.ell, b.upanel, pl.ldm, 0,
+                    m, pl.ell, pl.ell, 1, done};
+        CK(launch_gemm_simt(gu, ctx->stream));
+        CK(launch_rpca_rank_z(b.rt, b.q2, pl.ldn, b.perm, n, pl.ell, 1.0 / mus[j], rank_dev, b.zpanel, pl.ldn,
+                              done, ctx->stream));
+        RpcaIterArgs ua{m_dev, tm, ldm_dev, m, n,
+                        static_cast<float*>(s_dev), static_cast<float*>(y), static_cast<float*>(bmat),
+                        static_cast<double*>(s_dev), static_cast<double*>(y), static_cast<double*>(bmat),
+                        b.upanel, pl.ldm, b.zpanel, pl.ldn, pl.ell, rank_dev, mus[j], mus[j + 1], lambda,
+                        res_part, done};
+        int nparts = 0;
+        CK(launch_rpca_update(ua, &nparts, ctx->stream));
+        CK(launch_rpca_finish_iter(res_part, nparts, fro_part, nfro, tol, j, zhist, ctx->flags, rank_dev,
+                                   ctx->stream));
+    }
+    CK(launch_rpca_reconstruct(b.upanel, pl.ldm, b.zpanel, pl.ldn, rank_dev, pl.ell, m, n, l_dev, tm, n,
+                               ctx->stream));
+    int hf[FLAG_COUNT];
+    CKS(read_flags(ctx, hf));
+    const int it_done = hf[FLAG_RPCA_ITERS];
+    double z_last = 0.0;
+    if (it_done > 0)
+        CK(cudaMemcpyAsync(&z_last, zhist + (it_done - 1), sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (!dev) {
+        CK(cudaMemcpyAsync(L, l_dev, mn * es, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(S, s_dev, mn * es, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int) * FLAG_COUNT, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (iters) *iters = it_done;
+    if (zeta) *zeta = z_last;
+    if (rank) *rank = hf[FLAG_RPCA_RANK];
+    CKS(flags_status(hf));
+    if (!hf[FLAG_RPCA_DONE]) return fail(CORUTV_ENOTCONV, "ALM-CoRUTV reached max_iter=%d with zeta=%.3e", max_iter, z_last);
+    return CORUTV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Serving: a dispatcher thread admits queued requests into slots (each with
+// its own stream, workspace and status words) as slots and memory free up;
+// admitted requests run concurrently on the device.
+// ---------------------------------------------------------------------------
+namespace {
+
+size_t request_bytes(const corutv_request& r, bool host, int num_sms, FactorPlan* plan_out, corutv_status* st) {
+    FactorPlan pl;
+    const ElemType ta = r.dtype == CORUTV_F64 ? T_F64 : T_F32;
+    *st = make_plan(pl, ta, r.m, r.n, host ? r.n : r.lda, r.opts.k, r.opts.p, r.opts.q,
+                    (corutv_prec)r.opts.sketch_prec, num_sms);
+    if (*st != CORUTV_OK) return 0;
+    size_t bytes = factor_bytes(pl);
+    const int es = elem_size(ta);
+    const int64_t ell = pl.ell;
+    if (host) {
+        Carver c(nullptr);
+        c.take<char>(r.m * r.n * es);
+        c.take<char>(r.m * ell * es);
+        c.take<char>(r.n * ell * es);
+        c.take<char>(ell * ell * es);
+        c.take<int>(ell);
+        bytes += c.off;
+    }
+    if (r.opts.psi) bytes += (size_t)round_up(r.n * ell * 8, 256);
+    if (plan_out) *plan_out = pl;
+    return bytes;
+}
+
+corutv_status launch_request(corutv_ctx* ctx, ServingSlot& s, const PendingReq& pr) {
+    const corutv_request& r = pr.req;
+    FactorPlan pl;
+    corutv_status st;
+    request_bytes(r, pr.host, ctx->num_sms, &pl, &st);
+    if (st != CORUTV_OK) return st;
+    const ElemType ta = r.dtype == CORUTV_F64 ? T_F64 : T_F32;
+    const int es = elem_size(ta);
+    const int64_t m = r.m, n = r.n, ell = pl.ell;
+    Carver cv(s.ws.ptr);
+    FactorBufs b;
+    carve_factor(cv, pl, b);
+    const void* a_dev = r.A;
+    void *u_dev = r.U, *t_dev = r.T, *v_dev = r.V;
+    int32_t* perm_dev = r.perm;
+    int64_t ldu = r.ldu, ldv = r.ldv;
+    if (pr.host) {
+        void* as = cv.take<char>(m * n * es);
+        u_dev = cv.take<char>(m * ell * es);
+        v_dev = cv.take<char>(n * ell * es);
+        t_dev = cv.take<char>(ell * ell * es);
+        perm_dev = cv.take<int>(ell);
+        CK(cudaMemcpy2DAsync(as, n * es, r.A, r.lda * es, n * es, m, cudaMemcpyHostToDevice, s.st));
+        a_dev = as;
+        ldu = ell;
+        ldv = ell;
+    }
+    const double* psi = nullptr;
+    if (r.opts.psi) {
+        double* ps = cv.take<double>(n * ell);
+        CK(cudaMemcpyAsync(ps, r.opts.psi, sizeof(double) * n * ell, cudaMemcpyDefault, s.st));
+        psi = ps;
+    }
+    CK(cudaMemsetAsync(s.flags, 0, sizeof(int) * FLAG_COUNT, s.st));
+    Exec ex{s.st, s.flags, nullptr, ctx->num_sms};
+    CKS(run_factor(ex, pl, b, a_dev, psi, r.opts.seed, r.opts.stream));
+    CKS(emit_user(ex, pl, b, ta, r.U ? u_dev : nullptr, ldu, t_dev, r.V ? v_dev : nullptr, ldv,
+                  r.perm ? perm_dev : nullptr));
+    if (pr.host) {
+        if (r.U) CK(cudaMemcpy2DAsync(r.U, r.ldu * es, u_dev, ell * es, ell * es, m, cudaMemcpyDeviceToHost, s.st));
+        if (r.V) CK(cudaMemcpy2DAsync(r.V, r.ldv * es, v_dev, ell * es, ell * es, n, cudaMemcpyDeviceToHost, s.st));
+        CK(cudaMemcpyAsync(r.T, t_dev, ell * ell * es, cudaMemcpyDeviceToHost, s.st));
+        if (r.perm) CK(cudaMemcpyAsync(r.perm, perm_dev, sizeof(int32_t) * ell, cudaMemcpyDeviceToHost, s.st));
+    }
+    CK(cudaMemcpyAsync(s.hflags, s.flags, sizeof(int) * FLAG_COUNT, cudaMemcpyDeviceToHost, s.st));
+    CK(cudaEventRecord(s.done, s.st));
+    return CORUTV_OK;
+}
+
+void finish_slot(corutv_ctx* ctx, ServingSlot& s, corutv_status st) {
+    auto it = ctx->results.find(s.ticket);
+    if (it != ctx->results.end()) {
+        it->second.done = true;
+        it->second.status = st;
+        it->second.latency =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - it->second.t0).count();
+    }
+    s.busy = false;
+}
+
+void worker_main(corutv_ctx* ctx) {
+    DeviceGuard guard(ctx->device);
+    std::unique_lock<std::mutex> lk(ctx->smu);
+    while (true) {
+        bool progressed = false;
+        // retire
+        for (auto& s : ctx->slots) {
+            if (!s.busy) continue;
+            const cudaError_t q = cudaEventQuery(s.done);
+            if (q == cudaSuccess) {
+                corutv_status st = CORUTV_OK;
+                if (s.hflags[FLAG_BREAKDOWN]) st = CORUTV_EBREAKDOWN;
+                else if (s.hflags[FLAG_TIMEOUT]) st = CORUTV_ETIMEDOUT;
+                finish_slot(ctx, s, st);
+                progressed = true;
+            } else if (q != cudaErrorNotReady) {
+                cudaGetLastError();
+                finish_slot(ctx, s, CORUTV_ECUDA);
+                progressed = true;
+            }
+        }
+        // admit in arrival order
+        while (!ctx->queue.empty()) {
+            PendingReq& head = ctx->queue.front();
+            ServingSlot* pick = nullptr;
+            for (auto& s : ctx->slots)
+                if (!s.busy && s.ws.cap >= head.bytes) { pick = &s; break; }
+            if (!pick) {
+                for (auto& s : ctx->slots) {
+                    if (s.busy) continue;
+                    if (ctx->serving_bytes - s.ws.cap + head.bytes <= ctx->budget) { pick = &s; break; }
+                }
+                if (pick) {
+                    // grow this idle slot's workspace (stream-ordered, no device-wide sync)
+                    if (pick->ws.ptr) {
+                        cudaFreeAsync(pick->ws.ptr, pick->st);
+                        ctx->serving_bytes -= pick->ws.cap;
+                        pick->ws.ptr = nullptr;
+                        pick->ws.cap = 0;
+                    }
+                    if (cudaMallocAsync(&pick->ws.ptr, head.bytes, pick->st) != cudaSuccess) {
+                        cudaGetLastError();
+                        pick->ws.ptr = nullptr;
+                        pick = nullptr;
+                    } else {
+                        pick->ws.cap = head.bytes;
+                        ctx->serving_bytes += head.bytes;
+                    }
+                }
+            }
+            if (!pick) break;
+            PendingReq pr = head;
+            ctx->queue.pop_front();
+            pick->busy = true;
+            pick->ticket = pr.ticket;
+            lk.unlock();
+            corutv_status st = launch_request(ctx, *pick, pr);
+            lk.lock();
+            if (st != CORUTV_OK) finish_slot(ctx, *pick, st);
+            progressed = true;
+        }
+        if (progressed) ctx->scv.notify_all();
+        if (ctx->stop) {
+            bool any_busy = false;
+            for (auto& s : ctx->slots) any_busy |= s.busy;
+            if (!any_busy) break;
+        }
+        ctx->scv.wait_for(lk, std::chrono::microseconds(progressed ? 0 : 20));
+    }
+}
+
+corutv_status start_worker(corutv_ctx* ctx) {
+    if (ctx->worker_started) return CORUTV_OK;
+    ctx->slots.resize(ctx->max_slots);
+    for (auto& s : ctx->slots) {
+        CK(cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking));
+        CK(cudaMalloc(&s.flags, sizeof(int) * FLAG_COUNT));
+        CK(cudaMallocHost(&s.hflags, sizeof(int) * FLAG_COUNT));
+        CK(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+    }
+    ctx->worker = std::thread(worker_main, ctx);
+    ctx->worker_started = true;
+    return CORUTV_OK;
+}
+
+}  // namespace
+
+extern "C" corutv_status corutv_submit(corutv_ctx* ctx, const corutv_request* req, uint64_t* ticket) {
+    CKS(check_ctx(ctx));
+    if (!req || !ticket || !req->A || !req->T) return fail(CORUTV_EINVAL, "req, ticket, A and T must not be NULL");
+    if (req->opts.d_mode != 0) return fail(CORUTV_EINVAL, "d_mode must be 0");
+    DeviceGuard guard(ctx->device);
+    const bool host = !is_device_ptr(req->A);
+    corutv_status st;
+    const size_t bytes = request_bytes(*req, host, ctx->num_sms, nullptr, &st);
+    if (st != CORUTV_OK) return st;
+    if (bytes > ctx->budget)
+        return fail(CORUTV_ENOMEM, "request needs %zu bytes of workspace, budget is %zu", bytes, ctx->budget);
+    std::lock_guard<std::mutex> lk(ctx->smu);
+    CKS(start_worker(ctx));
+    PendingReq pr{ctx->next_ticket++, *req, std::chrono::steady_clock::now(), bytes, host};
+    ReqResult rr;
+    rr.t0 = pr.t0;
+    ctx->results[pr.ticket] = rr;
+    ctx->queue.push_back(pr);
+    *ticket = pr.ticket;
+    ctx->scv.notify_all();
+    return CORUTV_OK;
+}
+
+extern "C" corutv_status corutv_poll(corutv_ctx* ctx, uint64_t ticket, int64_t timeout_us, double* latency_s) {
+    CKS(check_ctx(ctx));
+    std::unique_lock<std::mutex> lk(ctx->smu);
+    auto it = ctx->results.find(ticket);
+    if (it == ctx->results.end()) return fail(CORUTV_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    auto ready = [&] { return ctx->results[ticket].done; };
+    if (!ready()) {
+        if (timeout_us == 0) return CORUTV_EPENDING;
+        if (timeout_us < 0) ctx->scv.wait(lk, ready);
+        else if (!ctx->scv.wait_for(lk, std::chrono::microseconds(timeout_us), ready))
+            return fail(CORUTV_ETIMEDOUT, "ticket %llu not finished after %lld us", (unsigned long long)ticket,
+                        (long long)timeout_us);
+    }
+    ReqResult rr = ctx->results[ticket];
+    ctx->results.erase(ticket);
+    if (latency_s) *latency_s = rr.latency;
+    if (rr.status != CORUTV_OK && rr.status != CORUTV_EPENDING)
+        return fail(rr.status, "request %llu failed with status %d", (unsigned long long)ticket, (int)rr.status);
+    return rr.status;
+}

@@ -1,0 +1,154 @@
+// Internal declarations of libcorutv (not part of the public ABI).
+//
+// Layout conventions inside the library
+//  * "panel": a tall-skinny rows x ell matrix stored column-major, element
+//    (i, j) at p[j * ld + i], ld a multiple of 32 elements. Sketches C1, C2,
+//    the bases Q1, Q2 and the test matrix X all live in this layout, so the
+//    coalesced direction of every skinny product is the long one.
+//  * "small": an ell x ell matrix stored row-major with row stride ell.
+//  * user matrices (A, M, U, V, T, L, S) are row-major with a leading
+//    dimension, as in the public header.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+
+namespace corutv {
+
+// Device-side status words, one small array per context / request.
+enum FlagIndex {
+    FLAG_BREAKDOWN = 0,   // a Cholesky of a Gram matrix failed even after shifting
+    FLAG_SHIFTED = 1,     // count of Gram matrices that needed the shift
+    FLAG_TIMEOUT = 2,     // a bounded device wait gave up
+    FLAG_RPCA_DONE = 3,   // ALM loop converged: later iteration kernels exit at once
+    FLAG_RPCA_ITERS = 4,  // iterations executed
+    FLAG_RPCA_RANK = 5,   // r of the last executed iteration
+    FLAG_COUNT = 16
+};
+
+enum ElemType { T_F64 = 0, T_F32 = 1, T_BF16 = 2 };
+
+inline int elem_size(ElemType t) { return t == T_F64 ? 8 : (t == T_F32 ? 4 : 2); }
+
+// How the generic skinny product reads its "A" operand. The product is
+//   out[r][j] = sum_k Aop[k][r] * Bop[k][j],  r < R, k < K, j < L (L <= 128).
+enum AMode {
+    A_ROWS = 0,     // Aop[k][r] = A[r * lda + k]   : C = A X     (r = row of A)
+    A_COLS = 1,     // Aop[k][r] = A[k * lda + r]   : C = A^T Y   (r = column of A)
+    A_PANEL_T = 2,  // Aop[k][r] = P[r * ldp + k]   : G = X^T Y   (r = panel column)
+    A_PANEL = 3     // Aop[k][r] = P[k * ldp + r]   : Q = P B     (r = panel row)
+};
+enum BMode {
+    B_PANEL = 0,    // Bop[k][j] = Y[j * ldb + k]
+    B_SMALL = 1     // Bop[k][j] = Bm[k * ldb + j]
+};
+enum OMode {
+    O_PANEL = 0,    // out[j * ldo + r]  (+ split * split_stride)
+    O_ROWMAJ = 1    // out[r * ldo + j]  (+ split * split_stride)
+};
+
+struct GemmArgs {
+    AMode amode;
+    BMode bmode;
+    OMode omode;
+    ElemType ta;          // element type of A (F64 / F32)
+    ElemType tc;          // compute type = element type of B and of the output
+    const void* a;
+    int64_t lda;
+    const void* b;
+    int64_t ldb;
+    void* out;
+    int64_t ldo;
+    int64_t split_stride; // elements between split outputs
+    int64_t R, K, L;
+    int splits;           // K is cut into `splits` ranges, each written separately
+    const int* cancel;    // optional device flag: kernels return at once when set
+};
+
+// Counts every kernel launch issued by this library (instrumentation).
+void count_launch();
+
+// ---- launchers (all stream-ordered, never synchronising) ----------------
+cudaError_t launch_gemm_simt(const GemmArgs& g, cudaStream_t st);
+int gemm_simt_splits(int64_t R, int64_t K, int num_sms);
+
+// out[e] = sum_{s < splits} part[s * stride + e] over a rows x cols region
+// with leading dimension ld (panel: rows = R, cols = L; small: rows = L).
+cudaError_t launch_reduce_splits(const void* part, ElemType tpart, int splits, int64_t stride,
+                                 double* out, int64_t ld, int64_t rows, int64_t cols, int64_t ld_out,
+                                 const int* cancel, cudaStream_t st);
+
+cudaError_t launch_gaussian_panel(uint64_t seed, uint32_t stream_id, int64_t n, int64_t ell,
+                                  int64_t ellp, double* x, int64_t ldx, const int* cancel,
+                                  cudaStream_t st);
+cudaError_t launch_gaussian_rowmajor(uint64_t seed, uint32_t stream_id, int64_t n, int64_t ell,
+                                     double* psi, int64_t ld, cudaStream_t st);
+
+// Layout / type conversions.
+cudaError_t launch_rowmajor_to_panel(const double* src, int64_t lds, int64_t rows, int64_t cols,
+                                     int64_t colsp, double* dst, int64_t ldd, cudaStream_t st);
+cudaError_t launch_panel_convert(const double* src, int64_t lds, int64_t rows, int64_t cols,
+                                 void* dst, ElemType tdst, int64_t ldd, const int* cancel,
+                                 cudaStream_t st);
+cudaError_t launch_panel_to_rowmajor(const double* src, int64_t lds, int64_t rows, int64_t cols,
+                                     void* dst, ElemType tdst, int64_t ldd, const int* cancel,
+                                     cudaStream_t st);
+
+// CholeskyQR pieces (k_qr.cu).
+// R = chol(G) (upper, R^T R = G + shift I), FP64, one block; flags as above.
+// *skip_out (optional) is set to 0 when a shift was needed (so a third
+// CholeskyQR pass must run) and to 1 otherwise or when cancelled.
+cudaError_t launch_cholesky(const double* g, int64_t ell, int64_t rows, double* r, int* flags,
+                            int* skip_out, const int* cancel, cudaStream_t st);
+// Q = C R^{-1} row by row (forward substitution with R^T), compute type tc;
+// writes the FP64 panel q and, if qc != nullptr, a copy of type tqc.
+cudaError_t launch_trsm_rows(const double* c, int64_t ldc, int64_t rows, int64_t ell,
+                             const double* r, ElemType tc, double* q, int64_t ldq, void* qc,
+                             ElemType tqc, int64_t ldqc, const int* cancel, cudaStream_t st);
+// Column-pivoted QR of the small ell x ell FP64 matrix d (eq. 8), one block.
+cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, int* perm,
+                        const int* cancel, cudaStream_t st);
+// V[i][j] = Q2[perm[j]] (row-major output of type tv), T = Rt (type tt).
+cudaError_t launch_gather_v(const double* q2, int64_t ldq2, int64_t n, int64_t ell, const int* perm,
+                            void* v, ElemType tv, int64_t ldv, const int* cancel, cudaStream_t st);
+cudaError_t launch_copy_small(const double* src, int64_t ell, void* dst, ElemType tdst,
+                              const int* cancel, cudaStream_t st);
+
+// RPCA pieces (k_rpca.cu).
+struct RpcaIterArgs {
+    const void* m; ElemType tm; int64_t ldm;
+    int64_t rows, cols;
+    float* s; float* y; float* b;           // FP32 state (dtype F32)
+    double* s64; double* y64; double* b64;  // FP64 state (dtype F64)
+    const double* u; int64_t ldu;           // U panel (rows x ell)
+    const double* z; int64_t ldz;           // Z panel (cols x ell): Z = V T(1:r,:)^T
+    int64_t ell;
+    const int* rank;                        // device r
+    double mu, mu_next, lambda;
+    double* res_part;                       // per-block partial sums of residual^2
+    const int* cancel;
+};
+cudaError_t launch_rpca_init(const void* m, ElemType tm, int64_t ldm, int64_t rows, int64_t cols,
+                             float* s, float* y, float* b, double* s64, double* y64, double* b64,
+                             double* fro_part, int* nparts, cudaStream_t st);
+cudaError_t launch_rpca_rank_z(const double* rt, const double* vq2, int64_t ldv, const int* perm,
+                               int64_t cols, int64_t ell, double inv_mu, int* rank, double* z,
+                               int64_t ldz, const int* cancel, cudaStream_t st);
+cudaError_t launch_rpca_update(const RpcaIterArgs& a, int* nparts, cudaStream_t st);
+cudaError_t launch_rpca_finish_iter(const double* res_part, int nparts, const double* fro_part,
+                                    int nfro, double tol, int iter, double* zeta_hist,
+                                    int* flags, const int* rank, cudaStream_t st);
+cudaError_t launch_rpca_reconstruct(const double* u, int64_t ldu, const double* z, int64_t ldz,
+                                    const int* rank, int64_t ell, int64_t rows, int64_t cols,
+                                    void* lout, ElemType tl, int64_t ldl, cudaStream_t st);
+
+int rpca_update_blocks(int64_t rows, int64_t cols);
+
+// Power iteration helpers for the ||M||_2 estimate: v = value; v = w / ||w||
+// with ||w|| stored in *lam (one block).
+cudaError_t launch_vec_fill(double* v, int64_t n, double value, cudaStream_t st);
+cudaError_t launch_vec_normalize(const double* w, double* v, int64_t n, double* lam, cudaStream_t st);
+
+}  // namespace corutv

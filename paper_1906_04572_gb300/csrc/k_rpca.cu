@@ -1,0 +1,306 @@
+// ALM-CoRUTV iteration kernels (Algorithm 2, Sec. 4).
+//
+// One iteration j, given the CoR-UTV factors of B_j = M - S_j + Y_j / mu_j:
+//   r       = #{i : T_ii > 1/mu_j}                      (operator C_delta)
+//   Z       = V T(1:r,:)^T            (cols x ell, columns >= r zero)
+//   L_{j+1} = U Z^T  = U(:,1:r) T(1:r,:) V^T            (never stored per iteration)
+//   S_{j+1} = shrink(M - L_{j+1} + Y_j / mu_j, lambda / mu_j)
+//   Y_{j+1} = Y_j + mu_j (M - L_{j+1} - S_{j+1})
+//   B_{j+1} = M - S_{j+1} + Y_{j+1} / mu_{j+1}          (input of the next CoR-UTV)
+//   zeta_j  = ||M - L_{j+1} - S_{j+1}||_F / ||M||_F
+// The update is one fused pass over the m x n state (reads M, Y; writes S, Y, B)
+// that forms L_{j+1} on the fly from the rank-r factors.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace corutv {
+
+namespace {
+
+constexpr int kUpdCols = 128;   // threads per block = columns per tile
+constexpr int kUpdRows = 16;    // rows per tile
+constexpr int kMaxEll = 64;
+constexpr int kFinalThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    __syncthreads();
+    return s;  // valid in thread 0
+}
+
+template <typename TM>
+__device__ __forceinline__ double ld_m(const void* m, int64_t off) {
+    return (double)static_cast<const TM*>(m)[off];
+}
+
+// S = 0, Y = 0, B = M; per-block sum of M^2.
+template <typename TM, typename TS>
+__global__ void rpca_init_kernel(const TM* m, int64_t ldm, int64_t rows, int64_t cols, TS* s, TS* y,
+                                 TS* b, double* fro_part) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    const int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / cols, c = e % cols;
+        const double mv = (double)m[i * ldm + c];
+        s[e] = (TS)0;
+        y[e] = (TS)0;
+        b[e] = (TS)mv;
+        acc += mv * mv;
+    }
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) fro_part[blockIdx.x] = t;
+}
+
+// r = #{i : Rt_ii > inv_mu}; Z[i][s] = sum_h Q2[i][perm[h]] Rt[s][h] for s < r.
+__global__ void rank_z_kernel(const double* rt, const double* q2, int64_t ldq2, const int* perm,
+                              int64_t cols, int ell, double inv_mu, int* rank, double* z, int64_t ldz,
+                              const int* cancel) {
+    if (cancel && *cancel) return;
+    __shared__ double Rs[kMaxEll * kMaxEll];
+    __shared__ int ps[kMaxEll];
+    __shared__ int r_s;
+    for (int e = threadIdx.x; e < ell * ell; e += blockDim.x) Rs[e] = rt[e];
+    for (int e = threadIdx.x; e < ell; e += blockDim.x) ps[e] = perm[e];
+    if (threadIdx.x == 0) {
+        int r = 0;
+        for (int i = 0; i < ell; ++i)
+            if (rt[i * ell + i] > inv_mu) ++r;
+        r_s = r;
+        if (blockIdx.x == 0) *rank = r;
+    }
+    __syncthreads();
+    const int r = r_s;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cols) return;
+    double v[kMaxEll];
+#pragma unroll 4
+    for (int h = 0; h < ell; ++h) v[h] = q2[(int64_t)ps[h] * ldq2 + i];
+    for (int s = 0; s < ell; ++s) {
+        double acc = 0.0;
+        if (s < r)
+            for (int h = s; h < ell; ++h) acc += v[h] * Rs[s * ell + h];  // Rt upper triangular
+        z[(int64_t)s * ldz + i] = acc;
+    }
+}
+
+// Fused S / Y / B update over a tile of kUpdRows x kUpdCols elements.
+template <typename TM, typename TS>
+__global__ void __launch_bounds__(kUpdCols)
+rpca_update_kernel(const TM* m, int64_t ldm, int64_t rows, int64_t cols, TS* s, TS* y, TS* b,
+                   const double* u, int64_t ldu, const double* z, int64_t ldz, int ell, const int* rank,
+                   double mu, double mu_next, double lambda, double* res_part, const int* cancel) {
+    if (cancel && *cancel) return;
+    __shared__ double red[32];
+    __shared__ double Us[kUpdRows][kMaxEll];
+    const int r = *rank;
+    const int64_t i0 = (int64_t)blockIdx.y * kUpdRows;
+    const int64_t c = (int64_t)blockIdx.x * kUpdCols + threadIdx.x;
+    for (int e = threadIdx.x; e < kUpdRows * kMaxEll; e += blockDim.x) {
+        const int ii = e / kMaxEll, sidx = e % kMaxEll;
+        const int64_t i = i0 + ii;
+        Us[ii][sidx] = (i < rows && sidx < r) ? u[(int64_t)sidx * ldu + i] : 0.0;
+    }
+    double zc[kMaxEll];
+    if (c < cols) {
+#pragma unroll 4
+        for (int sidx = 0; sidx < ell; ++sidx) zc[sidx] = (sidx < r) ? z[(int64_t)sidx * ldz + c] : 0.0;
+    }
+    __syncthreads();
+    const double inv_mu = 1.0 / mu, inv_mu_next = 1.0 / mu_next, delta = lambda / mu;
+    double acc = 0.0;
+    if (c < cols) {
+        for (int ii = 0; ii < kUpdRows; ++ii) {
+            const int64_t i = i0 + ii;
+            if (i >= rows) break;
+            double l = 0.0;
+            for (int sidx = 0; sidx < r; ++sidx) l += Us[ii][sidx] * zc[sidx];
+            const int64_t e = i * cols + c;
+            const double mv = (double)m[i * ldm + c];
+            const double yv = (double)y[e];
+            const double x = mv - l + yv * inv_mu;
+            const double mag = fabs(x) - delta;
+            const double sv = mag > 0.0 ? copysign(mag, x) : 0.0;
+            const double res = mv - l - sv;
+            const double yn = yv + mu * res;
+            s[e] = (TS)sv;
+            y[e] = (TS)yn;
+            b[e] = (TS)(mv - sv + yn * inv_mu_next);
+            acc += res * res;
+        }
+    }
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) res_part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+// zeta_j and the convergence flag; one block, fixed summation order.
+__global__ void finish_iter_kernel(const double* res_part, int nparts, const double* fro_part, int nfro,
+                                   double tol, int iter, double* zeta_hist, int* flags, const int* rank) {
+    if (flags[FLAG_RPCA_DONE]) return;
+    __shared__ double red[32];
+    double a = 0.0, f = 0.0;
+    for (int e = threadIdx.x; e < nparts; e += blockDim.x) a += res_part[e];
+    for (int e = threadIdx.x; e < nfro; e += blockDim.x) f += fro_part[e];
+    const double ra = block_sum(a, red);
+    const double rf = block_sum(f, red);
+    if (threadIdx.x == 0) {
+        const double zeta = sqrt(ra) / sqrt(rf);
+        zeta_hist[iter] = zeta;
+        flags[FLAG_RPCA_ITERS] = iter + 1;
+        flags[FLAG_RPCA_RANK] = *rank;
+        if (zeta < tol) flags[FLAG_RPCA_DONE] = 1;
+    }
+}
+
+template <typename TL>
+__global__ void __launch_bounds__(kUpdCols)
+reconstruct_kernel(const double* u, int64_t ldu, const double* z, int64_t ldz, const int* rank, int ell,
+                   int64_t rows, int64_t cols, TL* lout, int64_t ldl) {
+    __shared__ double Us[kUpdRows][kMaxEll];
+    const int r = *rank;
+    const int64_t i0 = (int64_t)blockIdx.y * kUpdRows;
+    const int64_t c = (int64_t)blockIdx.x * kUpdCols + threadIdx.x;
+    for (int e = threadIdx.x; e < kUpdRows * kMaxEll; e += blockDim.x) {
+        const int ii = e / kMaxEll, sidx = e % kMaxEll;
+        const int64_t i = i0 + ii;
+        Us[ii][sidx] = (i < rows && sidx < r) ? u[(int64_t)sidx * ldu + i] : 0.0;
+    }
+    double zc[kMaxEll];
+    if (c < cols)
+        for (int sidx = 0; sidx < ell; ++sidx) zc[sidx] = (sidx < r) ? z[(int64_t)sidx * ldz + c] : 0.0;
+    __syncthreads();
+    if (c >= cols) return;
+    for (int ii = 0; ii < kUpdRows; ++ii) {
+        const int64_t i = i0 + ii;
+        if (i >= rows) break;
+        double l = 0.0;
+        for (int sidx = 0; sidx < r; ++sidx) l += Us[ii][sidx] * zc[sidx];
+        lout[i * ldl + c] = (TL)l;
+    }
+}
+
+int init_blocks(int64_t total) {
+    int64_t b = (total + 255) / 256;
+    if (b > 1184) b = 1184;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+__global__ void vec_fill_kernel(double* v, int64_t n, double value) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = value;
+}
+
+__global__ void vec_normalize_kernel(const double* w, double* v, int64_t n, double* lam) {
+    __shared__ double red[32];
+    __shared__ double nrm;
+    double a = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a += w[i] * w[i];
+    const double t = block_sum(a, red);
+    if (threadIdx.x == 0) {
+        nrm = sqrt(t);
+        *lam = nrm;
+    }
+    __syncthreads();
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v[i] = w[i] * inv;
+}
+
+}  // namespace
+
+cudaError_t launch_vec_fill(double* v, int64_t n, double value, cudaStream_t st) {
+    count_launch();
+    vec_fill_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(v, n, value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vec_normalize(const double* w, double* v, int64_t n, double* lam, cudaStream_t st) {
+    count_launch();
+    vec_normalize_kernel<<<1, 1024, 0, st>>>(w, v, n, lam);
+    return cudaGetLastError();
+}
+
+int rpca_update_blocks(int64_t rows, int64_t cols) {
+    return (int)(((cols + kUpdCols - 1) / kUpdCols) * ((rows + kUpdRows - 1) / kUpdRows));
+}
+
+cudaError_t launch_rpca_init(const void* m, ElemType tm, int64_t ldm, int64_t rows, int64_t cols,
+                             float* s, float* y, float* b, double* s64, double* y64, double* b64,
+                             double* fro_part, int* nparts, cudaStream_t st) {
+    const int blocks = init_blocks(rows * cols);
+    *nparts = blocks;
+    if (tm == T_F32) {
+        count_launch();
+        rpca_init_kernel<float, float><<<blocks, 256, 0, st>>>(static_cast<const float*>(m), ldm, rows, cols,
+                                                               s, y, b, fro_part);
+    } else {
+        count_launch();
+        rpca_init_kernel<double, double><<<blocks, 256, 0, st>>>(static_cast<const double*>(m), ldm, rows,
+                                                                 cols, s64, y64, b64, fro_part);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rpca_rank_z(const double* rt, const double* vq2, int64_t ldv, const int* perm,
+                               int64_t cols, int64_t ell, double inv_mu, int* rank, double* z,
+                               int64_t ldz, const int* cancel, cudaStream_t st) {
+    if (ell > kMaxEll) return cudaErrorInvalidValue;
+    const unsigned blocks = (unsigned)((cols + 127) / 128);
+    count_launch();
+    rank_z_kernel<<<blocks, 128, 0, st>>>(rt, vq2, ldv, perm, cols, (int)ell, inv_mu, rank, z, ldz, cancel);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rpca_update(const RpcaIterArgs& a, int* nparts, cudaStream_t st) {
+    if (a.ell > kMaxEll) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((a.cols + kUpdCols - 1) / kUpdCols), (unsigned)((a.rows + kUpdRows - 1) / kUpdRows));
+    *nparts = (int)(grid.x * grid.y);
+    if (a.tm == T_F32) {
+        count_launch();
+        rpca_update_kernel<float, float><<<grid, kUpdCols, 0, st>>>(
+            static_cast<const float*>(a.m), a.ldm, a.rows, a.cols, a.s, a.y, a.b, a.u, a.ldu, a.z, a.ldz,
+            (int)a.ell, a.rank, a.mu, a.mu_next, a.lambda, a.res_part, a.cancel);
+    } else {
+        count_launch();
+        rpca_update_kernel<double, double><<<grid, kUpdCols, 0, st>>>(
+            static_cast<const double*>(a.m), a.ldm, a.rows, a.cols, a.s64, a.y64, a.b64, a.u, a.ldu, a.z,
+            a.ldz, (int)a.ell, a.rank, a.mu, a.mu_next, a.lambda, a.res_part, a.cancel);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rpca_finish_iter(const double* res_part, int nparts, const double* fro_part,
+                                    int nfro, double tol, int iter, double* zeta_hist,
+                                    int* flags, const int* rank, cudaStream_t st) {
+    count_launch();
+    finish_iter_kernel<<<1, kFinalThreads, 0, st>>>(res_part, nparts, fro_part, nfro, tol, iter, zeta_hist,
+                                                    flags, rank);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rpca_reconstruct(const double* u, int64_t ldu, const double* z, int64_t ldz,
+                                    const int* rank, int64_t ell, int64_t rows, int64_t cols,
+                                    void* lout, ElemType tl, int64_t ldl, cudaStream_t st) {
+    if (ell > kMaxEll) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((cols + kUpdCols - 1) / kUpdCols), (unsigned)((rows + kUpdRows - 1) / kUpdRows));
+    if (tl == T_F32) {
+        count_launch();
+        reconstruct_kernel<float><<<grid, kUpdCols, 0, st>>>(u, ldu, z, ldz, rank, (int)ell, rows, cols,
+                                                             static_cast<float*>(lout), ldl);
+    } else {
+        count_launch();
+        reconstruct_kernel<double><<<grid, kUpdCols, 0, st>>>(u, ldu, z, ldz, rank, (int)ell, rows, cols,
+                                                              static_cast<double*>(lout), ldl);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace corutv

@@ -1,0 +1,384 @@
+// SIMT kernels of libcorutv:
+//  * the generic skinny product out = Aop^T Bop (FP64 or FP32 FMA) used for
+//    the FP64 / FP32 passes over A (eqs. 4, 5, 7), the Gram matrices of
+//    CholeskyQR, D = Q1^T W and U = Q1 Qt (eq. 9);
+//  * the fixed-order reduction of split-K partial products;
+//  * step 1 of Algorithm 1: the Philox-4x32-10 Gaussian test matrix;
+//  * layout / precision conversions of the tall-skinny panels.
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+
+namespace corutv {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kBM = 64;
+constexpr int kBK = 32;
+constexpr int kTM = 4;
+
+template <typename T>
+__device__ __forceinline__ T zero_of() { return T(0); }
+
+template <typename TO, typename TI>
+__device__ __forceinline__ TO cvt(TI v) { return static_cast<TO>(v); }
+template <>
+__device__ __forceinline__ float cvt<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <>
+__device__ __forceinline__ double cvt<double, __nv_bfloat16>(__nv_bfloat16 v) {
+    return (double)__bfloat162float(v);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, double>(double v) {
+    return __double2bfloat16(v);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, float>(float v) { return __float2bfloat16(v); }
+
+// out[r][j] = sum_k Aop[k][r] Bop[k][j] over the split's k range.
+// Tiles of kBM output rows x (16 TN) columns, kBK k per stage; 256 threads,
+// each owns kTM rows x TN columns (columns tx, tx+16, ... to avoid bank
+// conflicts on the B tile).
+template <typename TA, typename TC, int TN>
+__global__ void __launch_bounds__(kThreads) gemm_simt_kernel(GemmArgs g) {
+    if (g.cancel && *g.cancel) return;
+    constexpr int LP = 16 * TN;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TC* As = reinterpret_cast<TC*>(smem_raw);                 // [kBK][kBM + 1]
+    TC* Bs = As + kBK * (kBM + 1);                            // [kBK][LP + 1]
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t r0 = (int64_t)blockIdx.x * kBM;
+    const int split = blockIdx.y;
+    const int64_t kper = ((g.K + g.splits - 1) / g.splits + kBK - 1) / kBK * kBK;
+    const int64_t kbeg = (int64_t)split * kper;
+    const int64_t kend = (g.K < kbeg + kper) ? g.K : kbeg + kper;
+    const TA* A = static_cast<const TA*>(g.a);
+    const TC* B = static_cast<const TC*>(g.b);
+    const bool a_kfast = (g.amode == A_ROWS || g.amode == A_PANEL_T);
+
+    TC acc[kTM][TN];
+#pragma unroll
+    for (int i = 0; i < kTM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = zero_of<TC>();
+
+    for (int64_t k0 = kbeg; k0 < kend; k0 += kBK) {
+        for (int idx = tid; idx < kBM * kBK; idx += kThreads) {
+            int r, k;
+            if (a_kfast) { r = idx / kBK; k = idx % kBK; } else { k = idx / kBM; r = idx % kBM; }
+            const int64_t gr = r0 + r, gk = k0 + k;
+            TC v = zero_of<TC>();
+            if (gr < g.R && gk < kend) {
+                const int64_t off = a_kfast ? gr * g.lda + gk : gk * g.lda + gr;
+                v = cvt<TC>(A[off]);
+            }
+            As[k * (kBM + 1) + r] = v;
+        }
+        for (int idx = tid; idx < kBK * LP; idx += kThreads) {
+            int j, k;
+            if (g.bmode == B_PANEL) { j = idx / kBK; k = idx % kBK; } else { k = idx / LP; j = idx % LP; }
+            const int64_t gk = k0 + k;
+            TC v = zero_of<TC>();
+            if (j < g.L && gk < kend) v = (g.bmode == B_PANEL) ? B[j * g.ldb + gk] : B[gk * g.ldb + j];
+            Bs[k * (LP + 1) + j] = v;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < kBK; ++k) {
+            TC av[kTM], bv[TN];
+#pragma unroll
+            for (int i = 0; i < kTM; ++i) av[i] = As[k * (kBM + 1) + ty * kTM + i];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) bv[j] = Bs[k * (LP + 1) + tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < kTM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    TC* out = static_cast<TC*>(g.out) + (int64_t)split * g.split_stride;
+#pragma unroll
+    for (int i = 0; i < kTM; ++i) {
+        const int64_t r = r0 + ty * kTM + i;
+        if (r >= g.R) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int64_t c = tx + 16 * j;
+            if (c >= g.L) continue;
+            out[g.omode == O_PANEL ? c * g.ldo + r : r * g.ldo + c] = acc[i][j];
+        }
+    }
+}
+
+template <typename TA, typename TC, int TN>
+cudaError_t launch_tn(const GemmArgs& g, cudaStream_t st) {
+    const size_t smem = sizeof(TC) * (size_t)(kBK * (kBM + 1) + kBK * (16 * TN + 1));
+    static bool attr_set = false;  // per instantiation; benign race (idempotent)
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_simt_kernel<TA, TC, TN>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    dim3 grid((unsigned)((g.R + kBM - 1) / kBM), (unsigned)g.splits);
+    count_launch();
+    gemm_simt_kernel<TA, TC, TN><<<grid, kThreads, smem, st>>>(g);
+    return cudaGetLastError();
+}
+
+template <typename TA, typename TC>
+cudaError_t launch_types(const GemmArgs& g, cudaStream_t st) {
+    if (g.L <= 16) return launch_tn<TA, TC, 1>(g, st);
+    if (g.L <= 32) return launch_tn<TA, TC, 2>(g, st);
+    if (g.L <= 64) return launch_tn<TA, TC, 4>(g, st);
+    return launch_tn<TA, TC, 8>(g, st);
+}
+
+}  // namespace
+
+int gemm_simt_splits(int64_t R, int64_t K, int num_sms) {
+    const int64_t tiles = (R + kBM - 1) / kBM;
+    int64_t want = (2LL * num_sms + tiles - 1) / tiles;
+    const int64_t maxs = K / (4 * kBK) > 1 ? K / (4 * kBK) : 1;
+    if (want > maxs) want = maxs;
+    if (want < 1) want = 1;
+    if (want > 1024) want = 1024;
+    return (int)want;
+}
+
+cudaError_t launch_gemm_simt(const GemmArgs& g, cudaStream_t st) {
+    if (g.R <= 0 || g.L <= 0 || g.L > 128 || g.splits < 1) return cudaErrorInvalidValue;
+    if (g.ta == T_F64 && g.tc == T_F64) return launch_types<double, double>(g, st);
+    if (g.ta == T_F32 && g.tc == T_F32) return launch_types<float, float>(g, st);
+    if (g.ta == T_F32 && g.tc == T_F64) return launch_types<float, double>(g, st);
+    if (g.ta == T_F64 && g.tc == T_F32) return launch_types<double, float>(g, st);
+    return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-order reduction of split partials: out = sum_s part[s], s ascending.
+// Element (x, y) of the region is at y * ld + x.
+// ---------------------------------------------------------------------------
+namespace {
+template <typename TP>
+__global__ void reduce_splits_kernel(const TP* part, int splits, int64_t stride, double* out,
+                                     int64_t ld, int64_t rows, int64_t cols, int64_t ld_out,
+                                     const int* cancel) {
+    if (cancel && *cancel) return;
+    const int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t y = e / rows, x = e % rows;
+        const int64_t off = y * ld + x;
+        double s = 0.0;
+        for (int p = 0; p < splits; ++p) s += (double)part[(int64_t)p * stride + off];
+        out[y * ld_out + x] = s;
+    }
+}
+}  // namespace
+
+cudaError_t launch_reduce_splits(const void* part, ElemType tpart, int splits, int64_t stride,
+                                 double* out, int64_t ld, int64_t rows, int64_t cols, int64_t ld_out,
+                                 const int* cancel, cudaStream_t st) {
+    const int64_t total = rows * cols;
+    if (total <= 0) return cudaSuccess;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (tpart == T_F64) {
+        count_launch();
+        reduce_splits_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double*>(part), splits,
+                                                             stride, out, ld, rows, cols, ld_out, cancel);
+    } else {
+        count_launch();
+        reduce_splits_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(part), splits,
+                                                            stride, out, ld, rows, cols, ld_out, cancel);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Step 1 of Algorithm 1: Gaussian test matrix from Philox-4x32-10
+// (Salmon et al., SC'11) and the Box-Muller transform (cosine branch).
+// ---------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ void philox_4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        const uint32_t n0 = hi1 ^ c[1] ^ k0;
+        const uint32_t n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+__device__ __forceinline__ double gauss_at(uint64_t seed, uint32_t sid, uint32_t i, uint32_t j) {
+    uint32_t c[4] = {i, j, sid, 0u};
+    philox_4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint64_t a = ((((uint64_t)c[0]) << 32) | c[1]) >> 11;
+    const uint64_t b = ((((uint64_t)c[2]) << 32) | c[3]) >> 11;
+    const double scale = 1.0 / 9007199254740992.0;  // 2^-53
+    const double u1 = ((double)a + 1.0) * scale;
+    const double u2 = (double)b * scale;
+    return sqrt(-2.0 * log(u1)) * cos(6.283185307179586476925286766559 * u2);
+}
+
+__global__ void gaussian_panel_kernel(uint64_t seed, uint32_t sid, int64_t n, int64_t ell,
+                                      int64_t ellp, double* x, int64_t ldx, const int* cancel) {
+    if (cancel && *cancel) return;
+    const int64_t total = n * ellp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / n, i = e % n;
+        x[j * ldx + i] = (j < ell) ? gauss_at(seed, sid, (uint32_t)i, (uint32_t)j) : 0.0;
+    }
+}
+
+__global__ void gaussian_rowmajor_kernel(uint64_t seed, uint32_t sid, int64_t n, int64_t ell,
+                                         double* psi, int64_t ld) {
+    const int64_t total = n * ell;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / ell, j = e % ell;
+        psi[i * ld + j] = gauss_at(seed, sid, (uint32_t)i, (uint32_t)j);
+    }
+}
+
+int grid_for(int64_t total) {
+    int64_t b = (total + 255) / 256;
+    if (b > 8192) b = 8192;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+}  // namespace
+
+cudaError_t launch_gaussian_panel(uint64_t seed, uint32_t stream_id, int64_t n, int64_t ell,
+                                  int64_t ellp, double* x, int64_t ldx, const int* cancel,
+                                  cudaStream_t st) {
+    count_launch();
+    gaussian_panel_kernel<<<grid_for(n * ellp), 256, 0, st>>>(seed, stream_id, n, ell, ellp, x, ldx,
+                                                              cancel);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gaussian_rowmajor(uint64_t seed, uint32_t stream_id, int64_t n, int64_t ell,
+                                     double* psi, int64_t ld, cudaStream_t st) {
+    count_launch();
+    gaussian_rowmajor_kernel<<<grid_for(n * ell), 256, 0, st>>>(seed, stream_id, n, ell, psi, ld);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Layout conversions through 32 x 32 shared-memory tiles (both sides
+// coalesced).
+// ---------------------------------------------------------------------------
+namespace {
+// dst(row-major rows x cols) <- src(panel) or the reverse; `to_panel`
+// selects the direction. Padding columns [cols, colsp) of a panel output
+// are written as zero.
+template <typename TD>
+__global__ void transpose_kernel(const double* src, int64_t lds, int64_t rows, int64_t cols,
+                                 int64_t colsp, TD* dst, int64_t ldd, bool to_panel,
+                                 const int* cancel) {
+    if (cancel && *cancel) return;
+    __shared__ double tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int s = ty; s < 32; s += 8) {
+        double v = 0.0;
+        if (to_panel) {  // src row-major: (i0+s, j0+tx)
+            const int64_t i = i0 + s, j = j0 + tx;
+            if (i < rows && j < cols) v = src[i * lds + j];
+        } else {         // src panel: (i0+tx, j0+s)
+            const int64_t i = i0 + tx, j = j0 + s;
+            if (i < rows && j < cols) v = src[j * lds + i];
+        }
+        tile[s][tx] = v;
+    }
+    __syncthreads();
+    for (int s = ty; s < 32; s += 8) {
+        if (to_panel) {  // dst panel: (i0+tx, j0+s) = tile[tx][s]
+            const int64_t i = i0 + tx, j = j0 + s;
+            if (i < rows && j < colsp) dst[j * ldd + i] = cvt<TD>(tile[tx][s]);
+        } else {         // dst row-major: (i0+s, j0+tx) = tile[tx][s]
+            const int64_t i = i0 + s, j = j0 + tx;
+            if (i < rows && j < cols) dst[i * ldd + j] = cvt<TD>(tile[tx][s]);
+        }
+    }
+}
+
+template <typename TD>
+__global__ void panel_convert_kernel(const double* src, int64_t lds, int64_t rows, int64_t cols,
+                                     TD* dst, int64_t ldd, const int* cancel) {
+    if (cancel && *cancel) return;
+    const int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / rows, i = e % rows;
+        dst[j * ldd + i] = cvt<TD>(src[j * lds + i]);
+    }
+}
+}  // namespace
+
+cudaError_t launch_rowmajor_to_panel(const double* src, int64_t lds, int64_t rows, int64_t cols,
+                                     int64_t colsp, double* dst, int64_t ldd, cudaStream_t st) {
+    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((colsp + 31) / 32));
+    count_launch();
+    transpose_kernel<double><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, cols, colsp, dst, ldd, true,
+                                                           nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_panel_to_rowmajor(const double* src, int64_t lds, int64_t rows, int64_t cols,
+                                     void* dst, ElemType tdst, int64_t ldd, const int* cancel,
+                                     cudaStream_t st) {
+    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
+    if (tdst == T_F64) {
+        count_launch();
+        transpose_kernel<double><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, cols, cols,
+                                                               static_cast<double*>(dst), ldd, false,
+                                                               cancel);
+    } else {
+        count_launch();
+        transpose_kernel<float><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, cols, cols,
+                                                              static_cast<float*>(dst), ldd, false,
+                                                              cancel);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_panel_convert(const double* src, int64_t lds, int64_t rows, int64_t cols,
+                                 void* dst, ElemType tdst, int64_t ldd, const int* cancel,
+                                 cudaStream_t st) {
+    const int blocks = grid_for(rows * cols);
+    switch (tdst) {
+        case T_F64:
+            count_launch();
+            panel_convert_kernel<double><<<blocks, 256, 0, st>>>(src, lds, rows, cols,
+                                                                 static_cast<double*>(dst), ldd, cancel);
+            break;
+        case T_F32:
+            count_launch();
+            panel_convert_kernel<float><<<blocks, 256, 0, st>>>(src, lds, rows, cols,
+                                                                static_cast<float*>(dst), ldd, cancel);
+            break;
+        case T_BF16:
+            count_launch();
+            panel_convert_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(
+                src, lds, rows, cols, static_cast<__nv_bfloat16*>(dst), ldd, cancel);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace corutv

@@ -43,6 +43,7 @@ MUTANTS = [
 # the cheap pins (all but the n >= 1000 Table 1 runs)
 CHEAP = [
     (pins.test_philox_known_answers, ()),
+    (pins.test_products_match_blas, ()),
     (pins.test_gaussian_is_standard_normal, ()),
     (pins.test_qr_matches_lapack, (50, 12, 1.0)),
     (pins.test_qr_matches_lapack, (200, 60, 1e6)),

@@ -59,6 +59,19 @@ def test_gaussian_is_standard_normal(oracle_lib):
 
 
 # --------------------------------------------------------------------------
+# Products of eqs. 4-5
+# --------------------------------------------------------------------------
+
+def test_products_match_blas(oracle_lib):
+    rng = np.random.default_rng(0)
+    a = rng.standard_normal((70, 45))
+    x = rng.standard_normal((45, 7))
+    y = rng.standard_normal((70, 7))
+    assert np.allclose(oracle_lib.gemm_ax(a, x), a @ x, rtol=1e-13, atol=1e-13)
+    assert np.allclose(oracle_lib.gemm_aty(a, y), a.T @ y, rtol=1e-13, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
 # Thin QR (Sec. 3.1, C1 = Q1 R1, C2 = Q2 R2)
 # --------------------------------------------------------------------------
 
