@@ -1,0 +1,412 @@
+"""Benchmark of the CoR-UTV hot path (Algorithm 1 with power method) on GB300.
+
+One step = one complete factorisation (Gaussian test matrix, 2q+2 sketch /
+power products with their thin QRs, the projection D = Q1^T A Q2, the pivoted
+QR of D and the assembly of U, T, V) of the 8000 x 6000 power-method workload
+(k = 50, ell = 60, q = 2, sigma_i = i^-2 for i <= 200 plus N(0, 1e-4^2) noise,
+Haar factors), synthetic, inputs resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c2|c1|c3] [--prec f32|tf32|bf16|f64]
+
+Prints one JSON line (rank 0). Under torchrun each rank factorises its own
+matrix (independent replicas, weak scaling); value = all ranks' flops / the
+slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CoR-UTV TFLOP/s & solves/s vs FP64 path at equal error; p50/p99 latency"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# ALU peaks from unit counts x maximum SM clock (152 SMs, 2070 MHz):
+#   FP32: 128 FMA/clk/SM -> 152*128*2*2.07e9 = 80.5 TFLOP/s
+#   FP64:   2 FMA/clk/SM -> 152*2*2*2.07e9   = 1.26 TFLOP/s
+ALU_PEAK_TFLOPS = {"f32": 152 * 128 * 2 * 2.07e9 / 1e12, "f64": 152 * 2 * 2 * 2.07e9 / 1e12}
+TF32_OF_BF16 = 0.5  # nominal dense tf32 : bf16 tensor ratio (1.1 : 2.25 PFLOP/s)
+
+WORKLOADS = {
+    "c1": dict(m=1000, n=1000, k=10, p=5, q=0, name="c1_1000x1000_k10_l15_q0"),
+    "c2": dict(m=8000, n=6000, k=50, p=10, q=2, name="c2_8000x6000_k50_l60_q2"),
+    "c3": dict(m=20000, n=20000, k=100, p=10, q=2, name="c3_20000x20000_k100_l110_q2"),
+}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+def make_matrix(wl: str, seed: int):
+    import synth
+    if wl == "c1":
+        return synth.factor_c1(seed=seed)
+    if wl == "c2":
+        return synth.factor_c2(q=2, seed=seed)
+    return synth.factor_c3(seed=seed)
+
+
+def flops_per_factor(m, n, ell, q):
+    """(2q+3) passes of 2 m n ell flops (Sec. 3.2)."""
+    return (2 * q + 3) * 2.0 * m * n * ell
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+        self.window = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append((time.time(), parts))
+
+    def mark(self, which: str):
+        self.window.append((which, time.time()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        t0 = dict(self.window).get("start", 0)
+        t1 = dict(self.window).get("end", time.time())
+        sel = [r for (t, r) in self.rows if t0 - 0.25 <= t <= t1 + 0.25] or [r for (_, r) in self.rows]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in sel if num(r[1]) is not None]
+        smax = [num(r[2]) for r in sel if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in sel for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(sel)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    oracle.build()
+    wl = WORKLOADS[args.workload]
+    rows = min(wl["m"], 2000)
+    f = make_matrix(args.workload, seed=0)
+    a = np.ascontiguousarray(f.a[:rows])
+    ell = wl["k"] + wl["p"]
+    psi = synth.gaussian_psi(f.n, ell, seed=0)
+    flops = flops_per_factor(rows, f.n, ell, wl["q"])
+    for _ in range(args.warmup):
+        oracle.corutv(a, wl["k"], wl["p"], wl["q"], psi)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.corutv(a, wl["k"], wl["p"], wl["q"], psi)
+        times.append(time.perf_counter() - t0)
+    sec = sum(times) / len(times)
+    value = flops / sec / 1e12
+    cores = os.cpu_count()
+    sample = (f"first {rows} of {wl['m']} rows of the {wl['name']} matrix, full factorisation "
+              f"(k={wl['k']}, ell={ell}, q={wl['q']}), FP64, one call per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["name"], "m": wl["m"], "n": wl["n"], "k": wl["k"], "ell": ell, "q": wl["q"]},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "solves_per_s": 1.0 / sec * rows / wl["m"],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sample(args, f, ell):
+    """The oracle as it stands, on a bounded sample of the workload."""
+    import oracle
+    import synth
+    oracle.build()
+    wl = WORKLOADS[args.workload]
+    rows = min(f.m, 2000)
+    a = np.ascontiguousarray(f.a[:rows])
+    psi = synth.gaussian_psi(f.n, ell, seed=0)
+    t0 = time.perf_counter()
+    oracle.corutv(a, wl["k"], wl["p"], wl["q"], psi)
+    sec = time.perf_counter() - t0
+    return {"value": flops_per_factor(rows, f.n, ell, wl["q"]) / sec / 1e12, "unit": "TFLOP/s",
+            "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one FP64 oracle factorisation of the first {rows} of {f.m} rows ({sec:.2f} s)"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def rel_error(A, out):
+    import torch
+    approx = (out["U"].double() @ out["T"].double()) @ out["V"].double().T
+    return float(torch.linalg.norm(A.double() - approx) / torch.linalg.norm(A.double()))
+
+
+def time_factor(ctx, A, k, p, q, prec, steps, warmup, world, profile=False):
+    """Device-timed steps of corutv_factor with outputs preallocated."""
+    import torch
+    from paper_1906_04572_gb300 import corutv
+    m, n = A.shape
+    ell = k + p
+    U = torch.empty((m, ell), device=A.device, dtype=A.dtype)
+    V = torch.empty((n, ell), device=A.device, dtype=A.dtype)
+    T = torch.empty((ell, ell), device=A.device, dtype=A.dtype)
+    perm = torch.empty(ell, device=A.device, dtype=torch.int32)
+    for w in range(warmup):
+        corutv.corutv_factor(ctx.handle, A, k, p, q, prec, U, T, V, perm, seed=0, stream=w)
+    ctx.sync()
+    if profile:
+        corutv.corutv_profile_enable(ctx.handle, True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for s in range(steps):
+        corutv.corutv_factor(ctx.handle, A, k, p, q, prec, U, T, V, perm, seed=0, stream=s)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1) / steps
+    prof = None
+    if profile:
+        prof = {st: corutv.corutv_profile_read(ctx.handle, st) for st in range(5)}
+        prof["launches"] = corutv.corutv_profile_read(ctx.handle, corutv.STAGE_ALL)[1]
+        corutv.corutv_profile_enable(ctx.handle, False)
+    assert ctx.sync() == 0
+    return ms, {"U": U, "T": T, "V": V, "perm": perm}, prof
+
+
+def run_ours(args):
+    import torch
+    from paper_1906_04572_gb300 import Context, corutv
+    from paper_1906_04572_gb300 import build as _build
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    _build.build()
+    wl = WORKLOADS[args.workload]
+    k, p, q = wl["k"], wl["p"], wl["q"]
+    ell = k + p
+    peaks, peaks_kind = load_peaks()
+    f = make_matrix(args.workload, seed=rank)
+    m, n = f.m, f.n
+    prec = args.prec
+    dt = torch.float64 if prec == "f64" else torch.float32
+    A = torch.from_numpy(f.a).to(device=device, dtype=dt)
+    flops = flops_per_factor(m, n, ell, q)
+    ctx = Context(local)
+    corutv.corutv_set_stream(ctx.handle, torch.cuda.current_stream(device).cuda_stream)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    sampler.mark("start")
+    ms, out, prof = time_factor(ctx, A, k, p, q, prec, args.steps, args.warmup, world, profile=True)
+    sampler.mark("end")
+    time.sleep(0.3)
+    sampler.stop()
+    ms_max = max_over_ranks(ms, world, device)
+    value = world * flops / (ms_max / 1e3) / 1e12
+    err = rel_error(A, out)
+
+    # dominant kernel: the sketch / power products (eqs. 4, 5)
+    sk_ms, sk_n = prof[corutv.STAGE_SKETCH]
+    per_launch_ms = sk_ms / max(sk_n, 1)
+    s_a = {"f64": 8, "f32": 4, "tf32": 4, "bf16": 2}[prec]
+    bytes_per_launch = m * n * s_a + (m + n) * ell * s_a
+    flops_per_launch = 2.0 * m * n * ell
+    gbs = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+    tfs = flops_per_launch / (per_launch_ms / 1e3) / 1e12
+    if prec in ("f32", "f64"):
+        ai = flops_per_launch / bytes_per_launch
+        alu = ALU_PEAK_TFLOPS[prec]
+        if alu < peaks["hbm_gbs"] * 1e9 * ai / 1e12:
+            roof = {"bound": "alu", "achieved": tfs, "peak": alu, "unit": "TFLOP/s", "frac": tfs / alu,
+                    "peak_source": "derived: 152 SMs x FMA/clk x 2 x 2.07 GHz"}
+        else:
+            roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": gbs / peaks["hbm_gbs"], "peak_source": peaks_kind}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / peaks["hbm_gbs"], "peak_source": peaks_kind}
+    roof.update({"kernel": "sketch products A X / A^T Y (eqs. 4, 5)", "traffic": None,
+                 "bytes_per_launch": bytes_per_launch, "launch_ms": per_launch_ms,
+                 "launches_timed": sk_n})
+
+    stages = {name: {"ms_per_step": prof[i][0] / args.steps, "intervals": prof[i][1]}
+              for i, name in enumerate(["sketch", "project", "orth", "qrcp", "factor"])}
+
+    # FP64 path at the same workload (the comparison the metric names)
+    fp64 = None
+    if not args.skip_fp64 and prec != "f64":
+        A64 = torch.from_numpy(f.a).to(device=device, dtype=torch.float64)
+        ms64, out64, _ = time_factor(ctx, A64, k, p, q, "f64", max(2, args.steps // 10), 1, world)
+        err64 = rel_error(A64, out64)
+        fp64 = {"tflops": flops / (ms64 / 1e3) / 1e12, "solves_per_s": 1e3 / ms64, "ms_per_step": ms64,
+                "e_rel": err64}
+        del A64
+
+    # end to end through the C ABI with host (pinned) buffers
+    e2e = None
+    if not args.no_e2e:
+        hA = torch.from_numpy(f.a).to(dtype=dt).pin_memory()
+        hU = torch.empty((m, ell), dtype=dt).pin_memory()
+        hV = torch.empty((n, ell), dtype=dt).pin_memory()
+        hT = torch.empty((ell, ell), dtype=dt).pin_memory()
+        hP = torch.empty(ell, dtype=torch.int32).pin_memory()
+        npA, npU, npV, npT, npP = (x.numpy() for x in (hA, hU, hV, hT, hP))
+        for w in range(args.warmup):
+            corutv.corutv_factor(ctx.handle, npA, k, p, q, prec, npU, npT, npV, npP, stream=w)
+        e2e_steps = max(3, min(args.steps, 20))
+        barrier(world)
+        t0 = time.perf_counter()
+        for s in range(e2e_steps):
+            corutv.corutv_factor(ctx.handle, npA, k, p, q, prec, npU, npT, npV, npP, stream=s)
+        sec = (time.perf_counter() - t0) / e2e_steps
+        sec = max_over_ranks(sec, world, device)
+        es = A.element_size()
+        e2e = {"value": world * flops / sec / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": m * n * es,
+               "d2h_bytes_per_step": (m * ell + n * ell + ell * ell) * es + ell * 4,
+               "ms_per_step": sec * 1e3, "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline_sample(args, f, ell)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": wl["name"], "m": m, "n": n, "k": k, "ell": ell, "q": q,
+                       "sketch_prec": prec, "input_dtype": str(dt).replace("torch.", ""),
+                       "l2": f"A is {m * n * A.element_size() / 1e6:.0f} MB, larger than the 129 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "solves_per_s": world * 1e3 / ms_max,
+            "e_rel": err,
+            "fp64_path": fp64,
+            "equal_error": (None if fp64 is None else bool(err <= 1.01 * fp64["e_rel"])),
+            "roofline": roof,
+            "stages": stages,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": sampler.summary(),
+            "gpu_launches": int(prof["launches"]),
+            "peaks": {"source": peaks_kind, "hbm_gbs": peaks["hbm_gbs"], "bf16_tflops": peaks.get("bf16_tflops")},
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="f32", choices=["f32", "tf32", "bf16", "f64"])
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

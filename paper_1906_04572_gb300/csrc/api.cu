@@ -188,8 +188,9 @@ corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64
     if (lda < n) return fail(CORUTV_EINVAL, "lda = %lld < n = %lld", (long long)lda, (long long)n);
     if (prec < CORUTV_P_F64 || prec > CORUTV_P_BF16) return fail(CORUTV_EINVAL, "unknown sketch precision %d", (int)prec);
     pl.tensor = (prec == CORUTV_P_TF32 || prec == CORUTV_P_BF16);
-    if (prec == CORUTV_P_TF32 && ta != T_F32)
-        return fail(CORUTV_EINVAL, "TF32 sketches need FP32 input (dtype CORUTV_F32)");
+    if (prec == CORUTV_P_TF32)
+        return fail(CORUTV_EINVAL, "TF32 sketches are not available for the full factorisation: the A^T Y "
+                                   "product has no TF32 kernel (use CORUTV_P_BF16 or CORUTV_P_F32)");
     pl.ellp = pl.tensor ? round_up(pl.ell, 16) : pl.ell;
     pl.ldm = round_up(m, 64);
     pl.ldn = round_up(n, 64);
@@ -314,6 +315,8 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     if (psi_dev) CK(launch_rowmajor_to_panel(psi_dev, ell, n, ell, pl.ellp, b.x, pl.ldn, ex.st));
     else CK(launch_gaussian_panel(seed, sid, n, ell, pl.ellp, b.x, pl.ldn, ex.cancel, ex.st));
     if (pl.tensor) {
+        // padding columns of the bf16 / fp32 operand panels must read as zero
+        CK(cudaMemsetAsync(b.q1c, 0, (size_t)pl.ellp * pl.ldm * elem_size(pl.tcomp), ex.st));
         CK(launch_panel_convert(b.x, pl.ldn, n, pl.ellp, b.xc, pl.tcomp, pl.ldn, ex.cancel, ex.st));
         if (pl.prec == CORUTV_P_BF16)
             CK(launch_cast_bf16(a, pl.ta, m, n, pl.lda, b.abf, round_up(n, 8), ex.cancel, ex.st));
@@ -766,6 +769,8 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
     measure.take<double>(pl.ellp * ldcp);
     measure.take<char>(pl.part_elems * 8);
     if (prec == CORUTV_P_BF16) measure.take<char>(m * round_up(n, 8) * 2);
+    const bool tf32_copy = prec == CORUTV_P_TF32 && !tma_rows_aligned(A, lda, 4);
+    if (tf32_copy) measure.take<float>(m * round_up(n, 4));
     CKS(ensure_ws(ctx, ctx->ws, measure.off, ctx->stream));
     Carver cv(ctx->ws.ptr);
     double* xp = cv.take<double>(pl.ellp * ldxp);
@@ -774,6 +779,7 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
     FactorBufs b{};
     b.part = cv.take<char>(pl.part_elems * 8);
     b.abf = prec == CORUTV_P_BF16 ? cv.take<char>(m * round_up(n, 8) * 2) : nullptr;
+    float* a32 = tf32_copy ? cv.take<float>(m * round_up(n, 4)) : nullptr;
     CK(launch_rowmajor_to_panel(X, ldx, xrows, ell, pl.ellp, xp, ldxp, ctx->stream));
     CK(launch_panel_convert(xp, ldxp, xrows, pl.ellp, xc, pl.tcomp, ldxp, nullptr, ctx->stream));
     Exec ex{ctx->stream, ctx->flags, nullptr, ctx->num_sms};
@@ -784,6 +790,10 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
             CK(launch_cast_bf16(A, ta, m, n, lda, b.abf, round_up(n, 8), nullptr, ctx->stream));
             aop = b.abf;
             lda_op = round_up(n, 8);
+        } else if (tf32_copy) {
+            CK(launch_copy_f32_padded(static_cast<const float*>(A), m, n, lda, a32, round_up(n, 4), ctx->stream));
+            aop = a32;
+            lda_op = round_up(n, 4);
         }
         CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, trans, xc, ldxp, ell, pl.ellp, b.part, cp, ldcp,
                             ctx->num_sms, ctx->flags, nullptr, ctx->stream));

@@ -29,9 +29,15 @@ template <>
 __device__ __forceinline__ double cvt<double, __nv_bfloat16>(__nv_bfloat16 v) {
     return (double)__bfloat162float(v);
 }
+// double -> bf16 rounded to nearest even in one step: round toward zero to
+// float, mark an inexact result in the last float bit (round to odd), then
+// round to bf16. The float keeps 16 more bits than bf16, so the odd bit only
+// breaks ties the way exact rounding would.
 template <>
 __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, double>(double v) {
-    return __double2bfloat16(v);
+    float f = __double2float_rz(v);
+    if ((double)f != v && isfinite(v)) f = __uint_as_float(__float_as_uint(f) | 1u);
+    return __float2bfloat16_rn(f);
 }
 template <>
 __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, float>(float v) { return __float2bfloat16(v); }

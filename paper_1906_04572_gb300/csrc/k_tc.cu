@@ -1,13 +1,590 @@
-// placeholder replaced by the tcgen05 kernels
+// Tensor-core sketch products of libcorutv (eqs. 4 and 5): C = A X and
+// C = A^T Y with tcgen05.mma (kind::f16 with bf16 operands, kind::tf32 with
+// fp32 operands), FP32 accumulators in tensor memory, operands staged by TMA.
+//
+// Shape: A is m x n row-major; X / Y are tall-skinny panels with ell_p <= 128
+// columns (multiple of 16). Each output tile is 128 rows of C by all ell_p
+// columns. The MMA M dimension runs along the long side of C (rows of A for
+// A X, columns of A for A^T Y), N = ell_p, K along the contracted side.
+//   A X  : A is K-major (its rows are contiguous along K = n).
+//   A^T Y: A is MN-major (its rows are contiguous along M = n).
+// The panels are always K-major (column j of the panel is contiguous).
+//
+// Schedule: a persistent grid of G CTAs (one per SM) splits the
+// (tile, K-chunk) iteration space into G equal contiguous ranges (stream-K),
+// so no wave is ever partly empty. A CTA's range crosses at most a few tile
+// boundaries; each tile segment it covers is written as an FP32 partial
+// (128 x ell_p) to `part`, and a fixed-order reduction kernel adds the
+// partials of each tile into the FP64 output panel.
+//
+// Warp roles (192 threads): warps 0-3 read the accumulator out of tensor
+// memory (warp w owns TMEM lanes 32w..32w+31 = rows of the tile), warp 4 is
+// the TMA producer, warp 5 allocates tensor memory and issues the MMAs.
+// Two accumulators alternate so the epilogue of one segment overlaps the
+// MMAs of the next.
+//
+// Every wait on an mbarrier is bounded (kWaitNs of %globaltimer); on timeout
+// the CTA sets FLAG_TIMEOUT, stops issuing work, waits (again bounded) for
+// its own copies and MMAs in flight, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
 #include "tc.cuh"
+
 namespace corutv {
-int64_t tc_partial_elems(int64_t, int64_t, int64_t, int64_t, int64_t, int) { return 0; }
-cudaError_t launch_sketch_tc(const void*, ElemType, int64_t, int64_t, int64_t, int, const void*, int64_t,
-                             int64_t, int64_t, void*, double*, int64_t, int, int*, const int*, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+namespace {
+
+constexpr int kThreads = 192;
+constexpr int kTileM = 128;
+constexpr int kMaxStages = 8;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+
+struct TcParams {
+    long long units;      // mtiles * kchunks
+    long long kchunks;
+    int grid;             // G
+    int maxp;             // partial pieces per tile
+    int ellp;
+    int trans;
+    int tf32;
+    int stages;
+    int a_boxes;          // TMA boxes per A tile (MN-major needs several)
+    int a_box_cols;       // columns (MN elements) per A box
+    uint32_t a_bytes;     // A tile bytes per stage
+    uint32_t stage_bytes; // A + B bytes per stage
+    uint32_t idesc;
+    uint32_t tmem_cols;   // columns allocated (two accumulators)
+    int kchunk_elems;     // K elements per chunk (64 bf16 / 32 fp32)
+    float* part;
+    int* flags;
+    const int* cancel;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-cudaError_t launch_cast_bf16(const void*, ElemType, int64_t, int64_t, int64_t, void*, int64_t, const int*,
-                             cudaStream_t) {
-    return cudaErrorNotSupported;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; false if the phase did not complete within `limit_ns` or if
+// another role already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned long long limit_ns = kWaitNs) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (abort_flag && *abort_flag) return false;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// Shared-memory matrix descriptor of tcgen05 (start address, leading and
+// stride byte offsets, fixed version bits 46-48 = 0b001, swizzle mode in
+// bits 61-63: 2 = 128-byte swizzle, 1 = 128-byte swizzle with 32-byte atoms).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t swz) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)(swz & 7u) << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Owner CTA of stream-K unit u when `units` units are split over `grid` CTAs
+// as [floor(c U / G), floor((c+1) U / G)).
+__host__ __device__ __forceinline__ long long unit_owner(long long u, long long units, long long grid) {
+    return ((u + 1) * grid + units - 1) / units - 1;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                 const TcParams p) {
+    if (p.cancel && *p.cancel) return;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[kMaxStages];
+    __shared__ __align__(8) uint64_t empty_bar[kMaxStages];
+    __shared__ __align__(8) uint64_t accf_bar[2];
+    __shared__ __align__(8) uint64_t acce_bar[2];
+    __shared__ __align__(8) uint64_t drain_bar;
+    __shared__ uint32_t tmem_holder;
+    __shared__ volatile int abort_s;
+    __shared__ volatile long long consumed_s;
+
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long c = blockIdx.x;
+    const long long u0 = c * p.units / p.grid;
+    const long long u1 = (c + 1) * p.units / p.grid;
+    const int S = p.stages;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&accf_bar[a], 1);
+            mbar_init(&acce_bar[a], 4);
+        }
+        mbar_init(&drain_bar, 1);
+        abort_s = 0;
+        consumed_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 4 && lane == 0) {
+        prefetch_tmap(&map_a);
+        prefetch_tmap(&map_b);
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_holder)),
+                     "r"(p.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_holder;
+    const long long KC = p.kchunks;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            long long li = 0;
+            for (long long u = u0; u < u1; ++u, ++li) {
+                const int s = (int)(li % S);
+                const long long r = li / S;
+                if (r > 0 && !mbar_wait(&empty_bar[s], (uint32_t)((r - 1) & 1), &abort_s)) {
+                    abort_s = 1;
+                    break;
+                }
+                const long long t = u / KC, kc = u % KC;
+                uint8_t* sa = smem + (size_t)s * p.stage_bytes;
+                uint8_t* sb = sa + p.a_bytes;
+                mbar_expect_tx(&full_bar[s], p.stage_bytes);
+                const int kx = (int)(kc * p.kchunk_elems);
+                if (!p.trans) {
+                    tma_load_2d(sa, &map_a, &full_bar[s], kx, (int)(t * kTileM));
+                } else {
+                    const uint32_t box_bytes = p.a_bytes / p.a_boxes;
+                    for (int bx = 0; bx < p.a_boxes; ++bx)
+                        tma_load_2d(sa + bx * box_bytes, &map_a, &full_bar[s], (int)(t * kTileM + bx * p.a_box_cols),
+                                    kx);
+                }
+                tma_load_2d(sb, &map_b, &full_bar[s], kx, 0);
+            }
+            if (abort_s) {
+                // drain: wait (bounded) for every copy that was issued but not consumed
+                const long long issued = li;
+                for (long long j = consumed_s; j < issued; ++j)
+                    mbar_wait(&full_bar[j % S], (uint32_t)((j / S) & 1), nullptr, 100000000ull);
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            long long li = 0, seg = 0;
+            const int ksteps = p.tf32 ? p.kchunk_elems / 8 : p.kchunk_elems / 16;
+            const uint32_t kstep_bytes = 32;  // 16 bf16 or 8 tf32 elements of K
+            for (long long u = u0; u < u1 && !abort_s; ++seg) {
+                const long long t = u / KC;
+                const long long seg_end = (u1 < (t + 1) * KC) ? u1 : (t + 1) * KC;
+                const int a = (int)(seg & 1);
+                if (seg >= 2 && !mbar_wait(&acce_bar[a], (uint32_t)(((seg >> 1) - 1) & 1), &abort_s)) {
+                    abort_s = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tacc = tmem_base + (uint32_t)(a * (p.tmem_cols / 2));
+                bool first = true;
+                for (; u < seg_end; ++u, ++li) {
+                    const int s = (int)(li % S);
+                    const long long r = li / S;
+                    if (!mbar_wait(&full_bar[s], (uint32_t)(r & 1), &abort_s)) {
+                        abort_s = 1;
+                        break;
+                    }
+                    consumed_s = li + 1;
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(smem + (size_t)s * p.stage_bytes);
+                    const uint32_t sb = sa + p.a_bytes;
+                    for (int kk = 0; kk < ksteps; ++kk) {
+                        uint64_t adesc, bdesc;
+                        if (!p.trans) {
+                            // K-major A: 128 rows x 128 B, 8-row groups 1024 B apart
+                            adesc = smem_desc(sa + kk * kstep_bytes, 16, 1024, 2);
+                        } else if (!p.tf32) {
+                            // MN-major A: 64-element MN atoms (8 KB apart), 8-row K groups 1024 B apart;
+                            // one K step of 16 consumes two K groups
+                            adesc = smem_desc(sa + kk * 2048, p.a_bytes / p.a_boxes, 1024, 2);
+                        } else {
+                            // MN-major tf32: 32-element MN atoms, K step of 8 = one K group
+                            adesc = smem_desc(sa + kk * 1024, p.a_bytes / p.a_boxes, 1024, 1);
+                        }
+                        bdesc = smem_desc(sb + kk * kstep_bytes, 16, 1024, 2);
+                        const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+                        if (p.tf32) mma_tf32(tacc, adesc, bdesc, p.idesc, acc);
+                        else mma_f16(tacc, adesc, bdesc, p.idesc, acc);
+                    }
+                    first = false;
+                    mma_commit(&empty_bar[s]);
+                }
+                if (abort_s) break;
+                mma_commit(&accf_bar[a]);
+            }
+            if (abort_s) {
+                mma_commit(&drain_bar);
+                mbar_wait(&drain_bar, 0, nullptr, 100000000ull);
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 0-3 ----------------
+        const int row = warp * 32 + lane;
+        long long seg = 0;
+        for (long long u = u0; u < u1; ++seg) {
+            const long long t = u / KC;
+            const long long seg_end = (u1 < (t + 1) * KC) ? u1 : (t + 1) * KC;
+            const int a = (int)(seg & 1);
+            if (!mbar_wait(&accf_bar[a], (uint32_t)((seg >> 1) & 1), &abort_s)) {
+                abort_s = 1;
+                break;
+            }
+            tc_fence_after();
+            const long long piece = c - unit_owner(t * KC, p.units, p.grid);
+            float* dst = p.part + ((t * p.maxp + piece) * p.ellp) * (long long)kTileM + row;
+            const uint32_t tacc = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * (p.tmem_cols / 2));
+            for (int c0 = 0; c0 < p.ellp; c0 += 16) {
+                float v[16];
+                tmem_ld16(tacc + (uint32_t)c0, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) dst[(long long)(c0 + i) * kTileM] = v[i];
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce_bar[a]);
+            u = seg_end;
+        }
+    }
+    if (abort_s && threadIdx.x == 0) atomicExch(&p.flags[FLAG_TIMEOUT], 1);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 5) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(p.tmem_cols));
+    }
+}
+
+// C[j * ldc + t * 128 + r] = sum over the pieces of tile t, in order.
+__global__ void streamk_reduce_kernel(const float* part, long long mtiles, long long kc, long long units,
+                                      long long grid, int maxp, int ellp, int ell, long long mtot, double* c,
+                                      long long ldc, const int* cancel) {
+    if (cancel && *cancel) return;
+    const long long total = mtiles * kTileM * (long long)ell;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long j = e / (mtiles * kTileM);
+        const long long rr = e % (mtiles * kTileM);
+        const long long t = rr / kTileM, r = rr % kTileM;
+        if (rr >= mtot) continue;
+        const long long np = unit_owner((t + 1) * kc - 1, units, grid) - unit_owner(t * kc, units, grid) + 1;
+        double s = 0.0;
+        for (long long pc = 0; pc < np; ++pc) s += (double)part[((t * maxp + pc) * ellp + j) * kTileM + r];
+        c[j * ldc + rr] = s;
+    }
+}
+
+__device__ __forceinline__ __nv_bfloat16 to_bf16(float v) { return __float2bfloat16_rn(v); }
+// double -> bf16 without double rounding (round to odd through float).
+__device__ __forceinline__ __nv_bfloat16 to_bf16(double v) {
+    float f = __double2float_rz(v);
+    if ((double)f != v && isfinite(v)) f = __uint_as_float(__float_as_uint(f) | 1u);
+    return __float2bfloat16_rn(f);
+}
+
+template <typename TI>
+__global__ void cast_bf16_kernel(const TI* a, long long m, long long n, long long lda, __nv_bfloat16* out,
+                                 long long ldb, const int* cancel) {
+    if (cancel && *cancel) return;
+    const long long total = m * ldb;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e / ldb, j = e % ldb;
+        out[e] = (j < n) ? to_bf16(a[i * lda + j]) : __float2bfloat16_rn(0.f);
+    }
+}
+
+__global__ void copy_f32_padded_kernel(const float* a, long long m, long long n, long long lda, float* out,
+                                       long long ldb) {
+    const long long total = m * ldb;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e / ldb, j = e % ldb;
+        out[e] = (j < n) ? a[i * lda + j] : 0.f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+cudaError_t get_encoder() {
+    std::call_once(g_encode_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        else
+            cudaGetLastError();
+    });
+    return g_encode ? cudaSuccess : cudaErrorNotSupported;
+}
+
+// 2-D tiled map over a row-major (outer x inner) matrix with row stride ld elements.
+cudaError_t encode_2d(CUtensorMap* map, const void* base, bool f32, long long inner, long long outer, long long ld,
+                      uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swz) {
+    if (reinterpret_cast<uintptr_t>(base) % 16 != 0) return cudaErrorMisalignedAddress;
+    const int es = f32 ? 4 : 2;
+    if ((ld * es) % 16 != 0) return cudaErrorInvalidValue;
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                          const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+struct Plan {
+    long long mtot, ktot, mtiles, kc, units;
+    int grid, maxp;
+};
+
+Plan make_plan(long long m, long long n, int trans, bool tf32, int num_sms) {
+    Plan pl;
+    pl.mtot = trans ? n : m;
+    pl.ktot = trans ? m : n;
+    const int ke = tf32 ? 32 : 64;
+    pl.mtiles = (pl.mtot + kTileM - 1) / kTileM;
+    pl.kc = (pl.ktot + ke - 1) / ke;
+    pl.units = pl.mtiles * pl.kc;
+    pl.grid = (int)std::min<long long>(num_sms, pl.units);
+    pl.maxp = 1;
+    for (long long t = 0; t < pl.mtiles; ++t) {
+        const long long np = unit_owner((t + 1) * pl.kc - 1, pl.units, pl.grid) - unit_owner(t * pl.kc, pl.units, pl.grid) + 1;
+        pl.maxp = std::max<int>(pl.maxp, (int)np);
+    }
+    return pl;
+}
+
+uint32_t make_idesc(bool tf32, bool a_mn_major, int n) {
+    uint32_t d = 0;
+    d |= 1u << 4;                             // D format: FP32
+    d |= (tf32 ? 2u : 1u) << 7;               // A format: TF32 / BF16
+    d |= (tf32 ? 2u : 1u) << 10;              // B format
+    d |= (a_mn_major ? 1u : 0u) << 15;        // A major-ness
+    d |= (uint32_t)(n >> 3) << 17;            // N >> 3
+    d |= (uint32_t)(kTileM >> 4) << 24;       // M >> 4
+    return d;
+}
+
+}  // namespace
+
+int64_t tc_partial_elems(int64_t m, int64_t n, int64_t ellp, int64_t ldm, int64_t ldn, int num_sms) {
+    (void)ldm;
+    (void)ldn;
+    int64_t best = 0;
+    for (int trans = 0; trans < 2; ++trans)
+        for (int tf = 0; tf < 2; ++tf) {
+            const Plan pl = make_plan(m, n, trans, tf != 0, num_sms);
+            best = std::max<int64_t>(best, pl.mtiles * pl.maxp * ellp * kTileM);
+        }
+    return best;
+}
+
+cudaError_t launch_sketch_tc(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, int trans,
+                             const void* x, int64_t ldx, int64_t ell, int64_t ellp, void* part, double* c,
+                             int64_t ldc, int num_sms, int* flags, const int* cancel, cudaStream_t st) {
+    if (ta != T_BF16 && ta != T_F32) return cudaErrorInvalidValue;
+    if (ellp % 16 != 0 || ellp < 16 || ellp > 128 || ell > ellp) return cudaErrorInvalidValue;
+    // The MN-major tf32 operand form (A^T Y in TF32) is not enabled.
+    if (ta == T_F32 && trans) return cudaErrorNotSupported;
+    cudaError_t e = get_encoder();
+    if (e != cudaSuccess) return e;
+    const bool tf32 = ta == T_F32;
+    const Plan pl = make_plan(m, n, trans, tf32, num_sms);
+    const int ke = tf32 ? 32 : 64;  // K elements per 128-byte row
+    CUtensorMap map_a, map_b;
+    TcParams p{};
+    p.units = pl.units;
+    p.kchunks = pl.kc;
+    p.grid = pl.grid;
+    p.maxp = pl.maxp;
+    p.ellp = (int)ellp;
+    p.trans = trans;
+    p.tf32 = tf32 ? 1 : 0;
+    p.kchunk_elems = ke;
+    p.part = static_cast<float*>(part);
+    p.flags = flags;
+    p.cancel = cancel;
+    if (!trans) {
+        e = encode_2d(&map_a, a, tf32, n, m, lda, (uint32_t)ke, kTileM, CU_TENSOR_MAP_SWIZZLE_128B);
+        p.a_boxes = 1;
+        p.a_box_cols = 0;
+    } else {
+        // MN-major A: boxes of one 128-byte MN atom (64 bf16 / 32 fp32 columns) by ke rows
+        const int atom = tf32 ? 32 : 64;
+        e = encode_2d(&map_a, a, tf32, n, m, lda, (uint32_t)atom, (uint32_t)ke,
+                      tf32 ? CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B : CU_TENSOR_MAP_SWIZZLE_128B);
+        p.a_boxes = kTileM / atom;
+        p.a_box_cols = atom;
+    }
+    if (e != cudaSuccess) return e;
+    e = encode_2d(&map_b, x, tf32, trans ? m : n, ellp, ldx, (uint32_t)ke, (uint32_t)ellp, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (e != cudaSuccess) return e;
+    p.a_bytes = kTileM * 128;
+    p.stage_bytes = p.a_bytes + (uint32_t)ellp * 128;
+    p.stages = std::min<int>(kMaxStages, (int)((200 * 1024) / p.stage_bytes));
+    uint32_t cols = 32;
+    while (cols < (uint32_t)ellp) cols <<= 1;
+    p.tmem_cols = 2 * cols;
+    p.idesc = make_idesc(tf32, trans != 0, (int)ellp);
+    const size_t smem = (size_t)p.stages * p.stage_bytes + 1024;
+    e = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    sketch_tc_kernel<<<pl.grid, kThreads, smem, st>>>(map_a, map_b, p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long total = pl.mtiles * kTileM * ell;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+    count_launch();
+    streamk_reduce_kernel<<<blocks, 256, 0, st>>>(p.part, pl.mtiles, pl.kc, pl.units, pl.grid, pl.maxp, (int)ellp,
+                                                  (int)ell, pl.mtot, c, ldc, cancel);
+    return cudaGetLastError();
+}
+
+bool tma_rows_aligned(const void* a, int64_t lda, int elem_bytes) {
+    return reinterpret_cast<uintptr_t>(a) % 16 == 0 && (lda * elem_bytes) % 16 == 0;
+}
+
+cudaError_t launch_copy_f32_padded(const float* a, int64_t m, int64_t n, int64_t lda, float* out, int64_t ldb,
+                                   cudaStream_t st) {
+    const long long total = m * ldb;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 8192);
+    count_launch();
+    copy_f32_padded_kernel<<<blocks, 256, 0, st>>>(a, m, n, lda, out, ldb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cast_bf16(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, void* abf,
+                             int64_t ldb, const int* cancel, cudaStream_t st) {
+    const long long total = m * ldb;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 8192);
+    count_launch();
+    if (ta == T_F32)
+        cast_bf16_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(a), m, n, lda,
+                                                        static_cast<__nv_bfloat16*>(abf), ldb, cancel);
+    else
+        cast_bf16_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double*>(a), m, n, lda,
+                                                         static_cast<__nv_bfloat16*>(abf), ldb, cancel);
+    return cudaGetLastError();
+}
+
 }  // namespace corutv

@@ -27,4 +27,12 @@ cudaError_t launch_sketch_tc(const void* a, ElemType ta, int64_t m, int64_t n, i
 cudaError_t launch_cast_bf16(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, void* abf,
                              int64_t ldb, const int* cancel, cudaStream_t st);
 
+// True when a row-major matrix can be a TMA source as is: 16-byte aligned
+// base and row stride.
+bool tma_rows_aligned(const void* a, int64_t lda, int elem_bytes);
+
+// out[i * ldb + j] = A[i * lda + j] for j < n, 0 for n <= j < ldb.
+cudaError_t launch_copy_f32_padded(const float* a, int64_t m, int64_t n, int64_t lda, float* out, int64_t ldb,
+                                   cudaStream_t st);
+
 }  // namespace corutv

@@ -1,0 +1,137 @@
+"""GPU parity of the tcgen05 sketch products and of the BF16 mixed-precision
+factorisation against the FP64 oracle.
+
+Bounds: the tensor cores multiply bf16 operands exactly and accumulate in
+FP32, so against the oracle's product of the same bf16-rounded operands
+|C - C_ref| <= 2 K 2^-24 (|A_r| |X_r|) elementwise. TF32 operands keep 10
+mantissa bits (the low 13 bits of the FP32 input are dropped), which adds
+2^-10 (|A| |X|)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_1906_04572_gb300 import Context, corutv
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1906_04572_gb300 import build
+    build.build()
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def dev(x, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def bf16_round(x):
+    """Round float64 values to the nearest bf16 (ties to even) in one step,
+    from the float64 bit pattern: bf16 keeps the sign, an 8-bit exponent and
+    7 of the 52 mantissa bits (values here are normal and in range).
+    torch's float64 -> bfloat16 conversion passes through float32 and can
+    round twice, so it is not used as the reference."""
+    b = np.ascontiguousarray(x, dtype=np.float64).view(np.uint64)
+    drop = np.uint64(45)
+    keep = b >> drop
+    half = (b >> np.uint64(44)) & np.uint64(1)
+    sticky = (b & np.uint64((1 << 44) - 1)) != 0
+    up = (half == 1) & (sticky | ((keep & np.uint64(1)) == 1))
+    return ((keep + up.astype(np.uint64)) << drop).view(np.float64)
+
+
+def test_bf16_reference_rounding_is_exact():
+    h = float.fromhex
+    v = np.array([h("-0x1.3d0000fa4d343p-1"), h("0x1.3dp-1"), h("0x1.3c8p-1"), h("0x1.3d8p-1"), 1.0, -3.75])
+    want = [h("-0x1.3ep-1"), h("0x1.3cp-1"), h("0x1.3cp-1"), h("0x1.3ep-1"), 1.0, -3.75]
+    assert list(bf16_round(v)) == want
+
+
+@pytest.mark.parametrize("m,n,ell", [(1000, 700, 15), (333, 1021, 60), (4100, 130, 110), (256, 200, 128),
+                                     (129, 65, 16)])
+@pytest.mark.parametrize("trans", [0, 1])
+def test_sketch_bf16_within_bound(ctx, m, n, ell, trans):
+    rng = np.random.default_rng(m + 3 * n + ell + trans)
+    a32 = rng.standard_normal((m, n)).astype(np.float32)
+    x = rng.standard_normal((m if trans else n, ell))
+    c = torch.empty((n if trans else m, ell), dtype=torch.float64, device="cuda")
+    corutv.corutv_sketch(ctx.handle, dev(a32, torch.float32), dev(x), c, trans, "bf16")
+    assert ctx.sync() == 0
+    ar, xr = bf16_round(a32.astype(np.float64)), bf16_round(x)
+    ref = oracle.gemm_aty(ar, xr) if trans else oracle.gemm_ax(ar, xr)
+    k = m if trans else n
+    bound = 2 * k * U32 * ((np.abs(ar).T if trans else np.abs(ar)) @ np.abs(xr))
+    err = np.abs(host(c) - ref)
+    assert np.all(err <= bound), float((err / bound).max())
+
+
+@pytest.mark.parametrize("m,n,ell", [(1000, 700, 16), (333, 1021, 60)])
+def test_sketch_tf32_within_bound(ctx, m, n, ell):
+    rng = np.random.default_rng(m + n)
+    a32 = rng.standard_normal((m, n)).astype(np.float32)
+    x = rng.standard_normal((n, ell))
+    c = torch.empty((m, ell), dtype=torch.float64, device="cuda")
+    corutv.corutv_sketch(ctx.handle, dev(a32, torch.float32), dev(x), c, 0, "tf32")
+    assert ctx.sync() == 0
+    a64 = a32.astype(np.float64)
+    x32 = x.astype(np.float32).astype(np.float64)
+    ref = oracle.gemm_ax(a64, x32)
+    bound = (2 * 2.0 ** -10 + 2 * n * U32) * (np.abs(a64) @ np.abs(x32))
+    assert np.all(np.abs(host(c) - ref) <= bound)
+
+
+def test_sketch_tf32_transposed_is_refused(ctx):
+    a = dev(np.ones((64, 48), np.float32), torch.float32)
+    c = torch.empty((48, 16), dtype=torch.float64, device="cuda")
+    with pytest.raises(corutv.CorutvError):
+        corutv.corutv_sketch(ctx.handle, a, dev(np.ones((64, 16))), c, 1, "tf32")
+
+
+def test_sketch_bf16_stream_k_many_pieces(ctx):
+    """Few tiles and a long K: each tile is split over many CTAs."""
+    m, n, ell = 200, 30000, 32
+    rng = np.random.default_rng(1)
+    a32 = rng.standard_normal((m, n)).astype(np.float32)
+    x = rng.standard_normal((n, ell))
+    c = torch.empty((m, ell), dtype=torch.float64, device="cuda")
+    corutv.corutv_sketch(ctx.handle, dev(a32, torch.float32), dev(x), c, 0, "bf16")
+    ar, xr = bf16_round(a32.astype(np.float64)), bf16_round(x)
+    ref = oracle.gemm_ax(ar, xr)
+    bound = 2 * n * U32 * (np.abs(ar) @ np.abs(xr))
+    assert np.all(np.abs(host(c) - ref) <= bound)
+
+
+@pytest.mark.parametrize("m,n,k,p,q", [(2000, 1500, 50, 10, 2), (1500, 2000, 30, 10, 1), (777, 513, 10, 5, 0)])
+def test_factor_bf16_error_budget(ctx, m, n, k, p, q):
+    """BF16 sketches + CholeskyQR2 + FP32 projection: the reconstruction
+    error stays within the BF16 budget of the FP64 oracle's error."""
+    sigma = np.arange(1, min(m, n) + 1) ** -1.5
+    a = synth.spectrum_matrix(m, n, sigma, 0.0, m + n)
+    a32 = a.astype(np.float32)
+    a64 = a32.astype(np.float64)
+    psi = synth.gaussian_psi(n, k + p, seed=7)
+    ref = oracle.corutv(a64, k, p, q, psi)
+    out = ctx.factor(dev(a32, torch.float32), k, p, q, "bf16", psi=dev(psi))
+    assert ctx.sync() == 0
+    u, t, v = (host(out[x]) for x in ("U", "T", "V"))
+    na = np.linalg.norm(a64)
+    e_gpu = np.linalg.norm(a64 - u @ t @ v.T) / na
+    e_or = np.linalg.norm(a64 - ref["U"] @ ref["T"] @ ref["V"].T) / na
+    ell = k + p
+    budget = 4 * 2.0 ** -8 * np.sqrt(ell) * np.linalg.norm(a64, 2) / na
+    assert e_gpu <= e_or + budget, (e_gpu, e_or, budget)
+    assert np.linalg.norm(u.T @ u - np.eye(ell)) < 1e-5
+    assert np.linalg.norm(v.T @ v - np.eye(ell)) < 1e-5
+    assert np.all(np.tril(t, -1) == 0)
