@@ -194,6 +194,30 @@ corutv_status corutv_orth(corutv_ctx* ctx, const double* C, int64_t rows, int64_
 corutv_status corutv_qrcp(corutv_ctx* ctx, const double* D, int64_t ell, double* Qt, double* Rt,
                           int32_t* perm);
 
+/* ---- allocation-free thin QR --------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: a host framework that owns all device
+ * memory through its own pool, a real-time or certified process that forbids
+ * allocation after start-up, or a plug-in running inside another library's
+ * step. It computes exactly what corutv_orth computes (CholeskyQR2 with the
+ * shifted fallback pass) but takes no context, allocates nothing and keeps
+ * every temporary in one fixed 16 MiB device array owned by the library
+ * (every GPU that loads the library holds it until the process exits).
+ *   C: rows x ell (ldc), Q: rows x ell (ldq), R: ell x ell upper (optional),
+ *   info: optional device int, set to 1 if the Cholesky broke down even
+ *   after the shift, else 0; all device pointers; cuda_stream: the
+ *   cudaStream_t to enqueue on (NULL = legacy stream). Stream-ordered: it
+ *   returns once the work is enqueued.
+ * Limits: 1 <= ell <= 128, rows >= ell and round_up(rows, 64) * ell <= 524288
+ *   (e.g. 4096 x 128); larger problems return CORUTV_EINVAL before any work.
+ * The first call on each device looks up the fixed array's device address
+ *   (with that device current) and caches it; make that first call before
+ *   any stream capture. All calls share the array: calls that overlap on the
+ *   GPU race and corrupt each other's results, so order them on one stream.
+ * Errors: status only; corutv_last_error(NULL) gives the message. */
+corutv_status corutv_orth_noalloc(const double* C, int64_t rows, int64_t ell, int64_t ldc, double* Q,
+                                  int64_t ldq, double* R, int* info, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,8 @@ _SIGS = {
                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
     "corutv_qrcp": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                      ctypes.c_void_p], ctypes.c_int),
+    "corutv_orth_noalloc": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -295,6 +297,20 @@ def corutv_qrcp(ctx, D, Qt, Rt, perm) -> None:
     ell = D.shape[0]
     _use_torch_stream(ctx, D)
     _check(ctx, load().corutv_qrcp(ctx, _ptr(D), ell, _ptr(Qt), _ptr(Rt), _ptr(perm)))
+
+
+def corutv_orth_noalloc(C, Q, R=None, info=None, stream_handle=None) -> None:
+    """Thin QR like corutv_orth, for callers that cannot allocate device
+    memory: no context, no allocation, temporaries in the library's fixed
+    16 MiB device array. All tensors on the current CUDA device."""
+    rows, ell = C.shape
+    if stream_handle is None:
+        import torch
+        stream_handle = torch.cuda.current_stream(C.device).cuda_stream
+    st = load().corutv_orth_noalloc(_ptr(C), rows, ell, _rowmajor_ld(C), _ptr(Q), _rowmajor_ld(Q), _ptr(R),
+                                    _ptr(info), ctypes.c_void_p(stream_handle))
+    if st != OK:
+        raise CorutvError(st, load().corutv_last_error(None).decode())
 
 
 # --------------------------------------------------------------------------

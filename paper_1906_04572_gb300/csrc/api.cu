@@ -129,6 +129,12 @@ corutv_status fail(corutv_status st, const char* fmt, ...) {
 
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+}  // namespace
+
+void corutv::record_error(const char* msg) { g_last_error = msg; }
+
+namespace {
+
 // Bump allocator over one device buffer; the same code measures (base ==
 // nullptr) and carves.
 struct Carver {

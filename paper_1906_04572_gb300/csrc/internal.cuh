@@ -70,6 +70,9 @@ struct GemmArgs {
 // Counts every kernel launch issued by this library (instrumentation).
 void count_launch();
 
+// Sets the calling thread's message returned by corutv_last_error().
+void record_error(const char* msg);
+
 // ---- launchers (all stream-ordered, never synchronising) ----------------
 cudaError_t launch_gemm_simt(const GemmArgs& g, cudaStream_t st);
 int gemm_simt_splits(int64_t R, int64_t K, int num_sms);
