@@ -164,6 +164,7 @@ struct FactorPlan {
     corutv_prec prec;
     ElemType tcomp;   // element type of the B operand of the sketch products
     ElemType tdproj;  // arithmetic of the projection pass (eq. 7)
+    ElemType torth;   // arithmetic of the Gram products and triangular solves of the thin QRs
     bool tensor;      // sketch products on tcgen05
     int sp_ax, sp_aty, sp_w, gs_m, gs_n;
     int64_t part_elems;
@@ -202,6 +203,7 @@ corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64
     pl.ldn = round_up(n, 64);
     pl.tcomp = pl.tensor ? (prec == CORUTV_P_BF16 ? T_BF16 : T_F32) : (prec == CORUTV_P_F64 ? T_F64 : T_F32);
     pl.tdproj = (ta == T_F64) ? T_F64 : T_F32;
+    pl.torth = (prec == CORUTV_P_F64) ? T_F64 : T_F32;
     pl.sp_ax = gemm_simt_splits(m, n, num_sms);
     pl.sp_aty = gemm_simt_splits(n, m, num_sms);
     pl.sp_w = pl.sp_ax;
@@ -275,39 +277,49 @@ corutv_status sketch_simt(const Exec& ex, const FactorPlan& pl, const FactorBufs
     return CORUTV_OK;
 }
 
-// G = X^T Y (ell x ell, FP64) for two FP64 panels of `len` rows.
+// G = X^T Y (ell x ell, written as FP64) for two FP64 panels of `len` rows,
+// products and split sums in arithmetic tg (FP64, or FP32 on the mixed paths).
 corutv_status gram(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, const double* x,
                    int64_t ldx, const double* y, int64_t ldy, int64_t len, double* out,
-                   const int* cancel) {
+                   const int* cancel, ElemType tg = T_F64) {
     const int gs = gemm_simt_splits(pl.ell, len, ex.num_sms);
     const int64_t ll = pl.ell * pl.ell;
-    GemmArgs g{A_PANEL_T, B_PANEL, O_ROWMAJ, T_F64, T_F64, x, ldx, y, ldy, b.gpart, pl.ell, ll,
+    GemmArgs g{A_PANEL_T, B_PANEL, O_ROWMAJ, T_F64, tg, x, ldx, y, ldy, b.gpart, pl.ell, ll,
                pl.ell, len, pl.ell, gs, cancel};
+    g.tb = T_F64;
     CK(launch_gemm_simt(g, ex.st));
-    CK(launch_reduce_splits(b.gpart, T_F64, gs, ll, out, pl.ell, pl.ell, pl.ell, pl.ell, cancel, ex.st));
+    CK(launch_reduce_splits(b.gpart, tg, gs, ll, out, pl.ell, pl.ell, pl.ell, pl.ell, cancel, ex.st));
     return CORUTV_OK;
 }
 
-// Thin QR of the FP64 panel c (len x ell) by CholeskyQR2, with one more
-// pass when the first Gram needed the shift (shifted CholeskyQR3).
-// Writes the FP64 panel q and, if qc != nullptr, a copy of type tqc.
+// Thin QR of the FP64 panel c (len x ell) by CholeskyQR: `passes` = 2 gives
+// CholeskyQR2 (used for the bases Q1, Q2 that leave the power loop, and
+// everywhere on the FP64 path); `passes` = 1 is used for the intermediate
+// bases of the power iteration on the mixed paths, where only the span
+// matters. A pass whose Gram needed the shift is followed by one more pass
+// (shifted CholeskyQR3). Gram products and triangular solves run in
+// pl.torth; every Cholesky factorisation runs in FP64. Writes the FP64
+// panel q and, if qc != nullptr, a copy of type tqc.
 corutv_status orth(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, const double* c,
-                   int64_t ld, int64_t len, double* q, void* qc, ElemType tqc, double* r_out) {
+                   int64_t ld, int64_t len, double* q, void* qc, ElemType tqc, int passes = 2) {
     const int64_t ell = pl.ell;
+    const ElemType tw = pl.torth;
     ProfScope ps(ex.prof, CORUTV_STAGE_ORTH, ex.st);
+    double* p1 = passes == 1 ? q : b.tmp;
+    void* p1c = passes == 1 ? qc : nullptr;
     // pass 1
-    CKS(gram(ex, pl, b, c, ld, c, ld, len, b.g, ex.cancel));
+    CKS(gram(ex, pl, b, c, ld, c, ld, len, b.g, ex.cancel, tw));
     CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, b.skip, ex.cancel, ex.st));
-    CK(launch_trsm_rows(c, ld, len, ell, b.r, T_F64, b.tmp, ld, nullptr, T_F64, 0, ex.cancel, ex.st));
-    // pass 1b, only after a shifted pass 1
-    CKS(gram(ex, pl, b, b.tmp, ld, b.tmp, ld, len, b.g, b.skip));
+    CK(launch_trsm_rows(c, ld, len, ell, b.r, tw, p1, ld, p1c, tqc, ld, ex.cancel, ex.st));
+    // extra pass, only after a shifted pass 1
+    CKS(gram(ex, pl, b, p1, ld, p1, ld, len, b.g, b.skip, tw));
     CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, nullptr, b.skip, ex.st));
-    CK(launch_trsm_rows(b.tmp, ld, len, ell, b.r, T_F64, b.tmp, ld, nullptr, T_F64, 0, b.skip, ex.st));
+    CK(launch_trsm_rows(p1, ld, len, ell, b.r, tw, p1, ld, p1c, tqc, ld, b.skip, ex.st));
+    if (passes == 1) return CORUTV_OK;
     // pass 2
-    CKS(gram(ex, pl, b, b.tmp, ld, b.tmp, ld, len, b.g, ex.cancel));
+    CKS(gram(ex, pl, b, b.tmp, ld, b.tmp, ld, len, b.g, ex.cancel, tw));
     CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, nullptr, ex.cancel, ex.st));
-    CK(launch_trsm_rows(b.tmp, ld, len, ell, b.r, T_F64, q, ld, qc, tqc, ld, ex.cancel, ex.st));
-    (void)r_out;
+    CK(launch_trsm_rows(b.tmp, ld, len, ell, b.r, tw, q, ld, qc, tqc, ld, ex.cancel, ex.st));
     return CORUTV_OK;
 }
 
@@ -341,7 +353,8 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
         } else {
             CKS(sketch_simt(ex, pl, b, A_ROWS, a, pl.ta, b.xc, pl.tcomp, b.c1, pl.ldm));
         }
-        CKS(orth(ex, pl, b, b.c1, pl.ldm, m, b.q1, b.q1c, pl.tcomp, nullptr));
+        const int inner = (pl.prec == CORUTV_P_F64) ? 2 : 1;  // passes for the intermediate bases
+        CKS(orth(ex, pl, b, b.c1, pl.ldm, m, b.q1, b.q1c, pl.tcomp, it < pl.q ? inner : 2));
         // eq. 5 (with C1 -> Q1): C2 = A^T Q1
         if (pl.tensor) {
             const void* aop = pl.prec == CORUTV_P_BF16 ? b.abf : a;
@@ -352,10 +365,10 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
         } else {
             CKS(sketch_simt(ex, pl, b, A_COLS, a, pl.ta, b.q1c, pl.tcomp, b.c2, pl.ldn));
         }
-        if (it < pl.q) CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.x, b.xc, pl.tcomp, nullptr));
+        if (it < pl.q) CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.x, b.xc, pl.tcomp, inner));
     }
     // Q2 = qr(C2), with a copy in the projection's arithmetic
-    CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.q2, b.q2c, pl.tdproj, nullptr));
+    CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.q2, b.q2c, pl.tdproj, 2));
     // eq. 7: W = A Q2 (FP64 or FP32 from the original A), D = Q1^T W (FP64)
     {
         GemmArgs g{A_ROWS, B_PANEL, O_PANEL, pl.ta, pl.tdproj, a, pl.lda, b.q2c, pl.ldn, b.part, pl.ldm,
@@ -367,7 +380,7 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
         CK(launch_reduce_splits(b.part, pl.tdproj, pl.sp_w, pl.ellp * pl.ldm, b.w, pl.ldm, m, ell, pl.ldm,
                                 ex.cancel, ex.st));
     }
-    CKS(gram(ex, pl, b, b.q1, pl.ldm, b.w, pl.ldm, m, b.d, ex.cancel));
+    CKS(gram(ex, pl, b, b.q1, pl.ldm, b.w, pl.ldm, m, b.d, ex.cancel, pl.tdproj));
     // eq. 8: D P = Qt Rt
     {
         ProfScope ps(ex.prof, CORUTV_STAGE_QRCP, ex.st);
@@ -844,7 +857,8 @@ corutv_status corutv_orth(corutv_ctx* ctx, const double* C, int64_t rows, int64_
     b.skip = cv.take<int>(8);
     CK(launch_rowmajor_to_panel(C, ldc, rows, ell, ell, cp, pl.ldm, ctx->stream));
     Exec ex{ctx->stream, ctx->flags, nullptr, ctx->num_sms};
-    CKS(orth(ex, pl, b, cp, pl.ldm, rows, qp, nullptr, T_F64, nullptr));
+    pl.torth = T_F64;
+    CKS(orth(ex, pl, b, cp, pl.ldm, rows, qp, nullptr, T_F64, 2));
     CK(launch_panel_to_rowmajor(qp, pl.ldm, rows, ell, Q, T_F64, ldq, nullptr, ctx->stream));
     if (R) {
         // R of C = Q R: R = Q^T C (exact in exact arithmetic; upper triangular)

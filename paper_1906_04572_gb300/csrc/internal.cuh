@@ -28,7 +28,7 @@ enum FlagIndex {
     FLAG_COUNT = 16
 };
 
-enum ElemType { T_F64 = 0, T_F32 = 1, T_BF16 = 2 };
+enum ElemType { T_F64 = 0, T_F32 = 1, T_BF16 = 2, T_SAME = 3 };
 
 inline int elem_size(ElemType t) { return t == T_F64 ? 8 : (t == T_F32 ? 4 : 2); }
 
@@ -54,7 +54,7 @@ struct GemmArgs {
     BMode bmode;
     OMode omode;
     ElemType ta;          // element type of A (F64 / F32)
-    ElemType tc;          // compute type = element type of B and of the output
+    ElemType tc;          // compute type = element type of the output
     const void* a;
     int64_t lda;
     const void* b;
@@ -65,7 +65,11 @@ struct GemmArgs {
     int64_t R, K, L;
     int splits;           // K is cut into `splits` ranges, each written separately
     const int* cancel;    // optional device flag: kernels return at once when set
+    ElemType tb = T_SAME; // element type of B (T_SAME: the compute type)
 };
+
+// Number of SMs of the current device (cached per device).
+int device_sms();
 
 // Counts every kernel launch issued by this library (instrumentation).
 void count_launch();

@@ -15,54 +15,98 @@ namespace corutv {
 
 namespace {
 
-constexpr int kCholThreads = 256;
+// ---------------------------------------------------------------------------
+// FP64 reciprocal and reciprocal square root without the FP64 divide / sqrt
+// sequences (each several hundred cycles on this part): an FP32 estimate on
+// the operand scaled into FP32 range by a power of two, then two
+// Newton-Raphson steps in FP64, each squaring the relative error
+// (about 2^-23 -> 2^-46 -> 2^-92, so the result is within a few ulp).
+//   1/sqrt(x): y <- y (3/2 - (x/2) y^2)
+//   1/x      : y <- y + y (1 - x y)
+// For normal, finite, nonzero operands (1/sqrt: positive); others fall back
+// to the library operations.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double scale_pow2(double x, int k) {  // x * 2^k, k within the exponent range
+    return __hiloint2double(__double2hiint(x) + (k << 20), __double2loint(x));
+}
 
+__device__ __forceinline__ double rsqrt_nr(double x) {
+    const int ef = (__double2hiint(x) >> 20) & 0x7ff;
+    if (ef == 0 || ef == 0x7ff || x < 0.0) return 1.0 / sqrt(x);
+    const int k = (ef - 1023) >> 1;            // x = xs 2^(2k), xs in [1, 4)
+    const double xs = scale_pow2(x, -2 * k);
+    double y = (double)rsqrtf((float)xs);
+    const double hx = 0.5 * xs;
+    y = y * fma(-hx, y * y, 1.5);
+    y = y * fma(-hx, y * y, 1.5);
+    return scale_pow2(y, -k);
+}
+
+__device__ __forceinline__ double rcp_nr(double x) {
+    const int ef = (__double2hiint(x) >> 20) & 0x7ff;
+    if (ef == 0 || ef == 0x7ff) return 1.0 / x;
+    const int k = ef - 1023;                   // x = xs 2^k, |xs| in [1, 2)
+    const double xs = scale_pow2(x, -k);
+    double y = (double)__frcp_rn((float)xs);
+    y = fma(y, fma(-xs, y, 1.0), y);
+    y = fma(y, fma(-xs, y, 1.0), y);
+    return scale_pow2(y, -k);
+}
+
+constexpr int kCholThreads = 128;  // one warp per SM sub-partition (each has its own FP64 unit)
+
+// Right-looking Cholesky, upper factor, R^T R = G (+ shift I), one column at
+// a time: every warp derives 1/r_jj itself (no extra barrier), row j is
+// scaled, then the trailing upper triangle takes the rank-1 update with
+// rows spread over the four warps and columns over the lanes.
 // rows = number of rows of the matrix whose Gram is factorised (for the shift).
 __global__ void __launch_bounds__(kCholThreads)
 cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, int* skip_out,
                 const int* cancel) {
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nwarps = kCholThreads / 32;
     if (cancel && *cancel) {
         if (skip_out && tid == 0) *skip_out = 1;
         return;
     }
-    extern __shared__ double S[];  // ell x (ell + 1)
+    extern __shared__ double S[];  // ell x (ell + 1), upper triangle used
     const int ld = ell + 1;
-    __shared__ int fail;
     __shared__ double trace;
-    if (tid == 0) {
-        double t = 0.0;
-        for (int a = 0; a < ell; ++a) t += g[a * ell + a];
-        trace = t;
-    }
-    __syncthreads();
-    // shift s = 11 (rows ell + ell (ell + 1)) u ||C||_F^2 (u = 2^-53), then x100
-    const double u = 1.1102230246251565e-16;
-    const double base_shift = 11.0 * ((double)rows * ell + (double)ell * (ell + 1)) * u * trace;
     int attempt = 0;
+    bool fail = false;
     for (; attempt < 3; ++attempt) {
-        const double shift = attempt == 0 ? 0.0 : base_shift * (attempt == 1 ? 1.0 : 100.0);
+        double shift = 0.0;
+        if (attempt > 0) {
+            // shift s = 11 (rows ell + ell (ell + 1)) u ||C||_F^2 (u = 2^-53), then x100;
+            // ||C||_F^2 = trace(G), summed only when a shift is needed
+            if (tid == 0) {
+                double t = 0.0;
+                for (int a = 0; a < ell; ++a) t += g[a * ell + a];
+                trace = t;
+            }
+            __syncthreads();
+            const double u = 1.1102230246251565e-16;
+            shift = 11.0 * ((double)rows * ell + (double)ell * (ell + 1)) * u * trace * (attempt == 1 ? 1.0 : 100.0);
+        }
         for (int e = tid; e < ell * ell; e += kCholThreads) {
             const int a = e / ell, b = e % ell;
             S[a * ld + b] = g[a * ell + b] + (a == b ? shift : 0.0);
         }
-        if (tid == 0) fail = 0;
         __syncthreads();
+        fail = false;
         for (int j = 0; j < ell; ++j) {
-            if (tid == 0) {
-                const double d = S[j * ld + j];
-                if (!(d > 0.0) || !isfinite(d)) fail = 1;
-                else S[j * ld + j] = sqrt(d);
+            const double d = S[j * ld + j];  // same value in every thread
+            if (!(d > 0.0) || !isfinite(d)) {
+                fail = true;
+                break;
             }
+            const double y = rsqrt_nr(d);  // 1 / r_jj
+            for (int c = j + 1 + tid; c < ell; c += kCholThreads) S[j * ld + c] *= y;
             __syncthreads();
-            if (fail) break;
-            const double rjj = S[j * ld + j];
-            for (int c = j + 1 + tid; c < ell; c += kCholThreads) S[j * ld + c] /= rjj;
-            __syncthreads();
-            const int nt = ell - j - 1;
-            for (int e = tid; e < nt * nt; e += kCholThreads) {
-                const int a = j + 1 + e / nt, b = j + 1 + e % nt;
-                if (b >= a) S[a * ld + b] -= S[j * ld + a] * S[j * ld + b];
+            if (tid == 0) S[j * ld + j] = d * y;
+            for (int a = j + 1 + warp; a < ell; a += nwarps) {
+                const double sja = S[j * ld + a];
+                for (int c = a + lane; c < ell; c += 32) S[a * ld + c] -= sja * S[j * ld + c];
             }
             __syncthreads();
         }
@@ -92,8 +136,10 @@ __global__ void trsm_rows_kernel(const double* c, int64_t ldc, int64_t rows, int
     TC* Rs = reinterpret_cast<TC*>(smem_raw);   // ell x ell row-major
     const int nthr = blockDim.x;
     TC* Ts = Rs + ell * ell;                      // [ell][nthr]
+    TC* Rd = Ts + (size_t)ell * nthr;             // 1 / R[j][j]
     const int tid = threadIdx.x;
     for (int e = tid; e < ell * ell; e += nthr) Rs[e] = (TC)r[e];
+    for (int j = tid; j < ell; j += nthr) Rd[j] = (TC)(1.0 / r[j * ell + j]);
     const int64_t i = (int64_t)blockIdx.x * nthr + tid;
     if (i < rows)
         for (int j = 0; j < ell; ++j) Ts[j * nthr + tid] = (TC)c[j * ldc + i];
@@ -107,7 +153,7 @@ __global__ void trsm_rows_kernel(const double* c, int64_t ldc, int64_t rows, int
             s1 -= Ts[(t + 1) * nthr + tid] * Rs[(t + 1) * ell + j];
         }
         if (t < j) s0 -= Ts[t * nthr + tid] * Rs[t * ell + j];
-        Ts[j * nthr + tid] = (s0 + s1) / Rs[j * ell + j];
+        Ts[j * nthr + tid] = (s0 + s1) * Rd[j];
     }
     for (int j = 0; j < ell; ++j) {
         const TC v = Ts[j * nthr + tid];
@@ -116,13 +162,17 @@ __global__ void trsm_rows_kernel(const double* c, int64_t ldc, int64_t rows, int
     }
 }
 
+// Threads (= rows) per block: up to 256, bounded by shared memory. A row's
+// solve is a dependent chain, so larger blocks mainly serve to load R once
+// per 256 rows.
 template <typename TC>
-int trsm_threads(int ell) {
+int trsm_threads(int ell, int64_t rows) {
     const long budget = 200 * 1024;
-    long per = (budget - (long)ell * ell * (long)sizeof(TC)) / ((long)ell * (long)sizeof(TC));
+    long per = (budget - (long)ell * (ell + 1) * (long)sizeof(TC)) / ((long)ell * (long)sizeof(TC));
     per = per / 32 * 32;
     if (per > 256) per = 256;
     if (per < 32) per = 32;
+    (void)rows;
     return (int)per;
 }
 
@@ -130,8 +180,8 @@ template <typename TC, typename TQC>
 cudaError_t trsm_launch(const double* c, int64_t ldc, int64_t rows, int ell, const double* r,
                         double* q, int64_t ldq, TQC* qc, int64_t ldqc, const int* cancel,
                         cudaStream_t st) {
-    const int nthr = trsm_threads<TC>(ell);
-    const size_t smem = sizeof(TC) * ((size_t)ell * ell + (size_t)ell * nthr);
+    const int nthr = trsm_threads<TC>(ell, rows);
+    const size_t smem = sizeof(TC) * ((size_t)ell * ell + (size_t)ell * nthr + (size_t)ell);
     cudaError_t e = cudaFuncSetAttribute(trsm_rows_kernel<TC, TQC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -142,63 +192,112 @@ cudaError_t trsm_launch(const double* c, int64_t ldc, int64_t rows, int ell, con
 }
 
 // ---------------------------------------------------------------------------
-// QRCP of the small D (eq. 8). 256 threads = 8 warps.
+// QRCP of the small D (eq. 8), one block of four warps (one per SM
+// sub-partition, each with its own FP64 unit). W is column-major in shared
+// memory (column c at W + c * ldw, ldw odd so that lanes owning consecutive
+// columns hit distinct banks). Column-wise work (squared norms, reflector
+// dot products and updates) is split as lanes = columns, warps = quarters of
+// the active rows; partial sums meet in shared memory in warp order.
+// Pivot choice compares the non-negative squared norms through their bit
+// patterns (same order as the values), lowest index on ties.
 // ---------------------------------------------------------------------------
-constexpr int kQrcpThreads = 256;
+constexpr int kQrcpThreads = 128;
 constexpr int kQrcpWarps = kQrcpThreads / 32;
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+// rows [lo, hi) of the active range [j, ell) owned by warp w
+__device__ __forceinline__ void quarter(int j, int ell, int w, int& lo, int& hi) {
+    const int n = ell - j;
+    const int qn = (n + kQrcpWarps - 1) / kQrcpWarps;
+    lo = j + w * qn;
+    hi = min(ell, lo + qn);
+    if (lo > ell) lo = ell;
 }
 
-// Apply H = I - tau v v^T (v = [1; W[j+1:, j]]) to column c of W, rows j..ell-1.
-__device__ __forceinline__ void house_apply_col(double* W, int ld, int ell, int j, int c, double tau,
-                                                int lane) {
-    double dot = 0.0;
-    for (int i = j + 1 + lane; i < ell; i += 32) dot += W[i * ld + j] * W[i * ld + c];
-    dot = warp_sum(dot);
-    dot += W[j * ld + c];
-    const double f = tau * dot;
-    if (lane == 0) W[j * ld + c] -= f;
-    for (int i = j + 1 + lane; i < ell; i += 32) W[i * ld + c] -= f * W[i * ld + j];
+// Apply H_j = I - tau v v^T (v = [1; W[j][j+1:]]) to columns c0..ell-1, rows j..ell-1.
+__device__ void apply_reflector(double* W, int ldw, double* part, int j, int c0, int ell, double tau, int lane,
+                                int warp) {
+    const double* v = W + j * ldw;
+    int lo, hi;
+    quarter(j, ell, warp, lo, hi);
+    for (int cb = c0; cb < ell; cb += 32) {
+        const int c = cb + lane;
+        if (c < ell) {
+            const double* x = W + c * ldw;
+            double s0 = 0.0, s1 = 0.0;
+            int i = lo;
+            if (i == j && i < hi) { s0 = x[j]; ++i; }  // v[j] = 1
+            for (; i + 1 < hi; i += 2) {
+                s0 += v[i] * x[i];
+                s1 += v[i + 1] * x[i + 1];
+            }
+            if (i < hi) s0 += v[i] * x[i];
+            part[warp * 128 + (c - cb)] = s0 + s1;
+        }
+        __syncthreads();
+        if (c < ell) {
+            double dot = part[c - cb];
+            for (int w = 1; w < kQrcpWarps; ++w) dot += part[w * 128 + (c - cb)];
+            const double f = tau * dot;
+            double* x = W + c * ldw;
+            int i = lo;
+            if (i == j && i < hi) { x[j] -= f; ++i; }
+            for (; i < hi; ++i) x[i] -= f * v[i];
+        }
+        __syncthreads();
+    }
 }
 
 __global__ void __launch_bounds__(kQrcpThreads)
 qrcp_kernel(const double* d, int ell, double* qt, double* rt, int* perm, const int* cancel) {
     if (cancel && *cancel) return;
-    extern __shared__ double W[];  // ell x (ell + 1) row-major, then nrm[ell], tau[ell], sgn[ell]
-    const int ld = ell + 1;
-    double* nrm = W + ell * ld;
+    extern __shared__ double W[];  // ell columns of ldw doubles, then part, nrm, tau, sgn, perm
+    const int ldw = ell | 1;
+    double* part = W + ell * ldw;           // kQrcpWarps x 128
+    double* nrm = part + kQrcpWarps * 128;  // ell
     double* tau = nrm + ell;
     double* sgn = tau + ell;
     int* pv = reinterpret_cast<int*>(sgn + ell);
     __shared__ int piv_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int e = tid; e < ell * ell; e += kQrcpThreads) W[(e / ell) * ld + (e % ell)] = d[e];
+    for (int e = tid; e < ell * ell; e += kQrcpThreads) {
+        const int a = e / ell, b = e % ell;  // d row-major: entry (a, b) -> column b, row a
+        W[b * ldw + a] = d[e];
+    }
     for (int c = tid; c < ell; c += kQrcpThreads) pv[c] = c;
     __syncthreads();
     for (int j = 0; j < ell; ++j) {
-        // 1. recomputed residual norms of the trailing columns
-        for (int c = j + warp; c < ell; c += kQrcpWarps) {
-            double s = 0.0;
-            for (int i = j + lane; i < ell; i += 32) s += W[i * ld + c] * W[i * ld + c];
-            s = warp_sum(s);
-            if (lane == 0) nrm[c] = s;
+        int lo, hi;
+        quarter(j, ell, warp, lo, hi);
+        // 1. recomputed squared residual norms of columns j..ell-1
+        for (int cb = j; cb < ell; cb += 32) {
+            const int c = cb + lane;
+            if (c < ell) {
+                const double* x = W + c * ldw;
+                double s0 = 0.0, s1 = 0.0;
+                int i = lo;
+                for (; i + 1 < hi; i += 2) {
+                    s0 += x[i] * x[i];
+                    s1 += x[i + 1] * x[i + 1];
+                }
+                if (i < hi) s0 += x[i] * x[i];
+                part[warp * 128 + (c - j)] = s0 + s1;
+            }
         }
         __syncthreads();
-        // 2. pivot = argmax, lowest index on ties
+        // 2. pivot: warp 0 adds the quarters (warp order) and takes the argmax
         if (warp == 0) {
-            double best = -1.0;
+            long long best = -1;
             int bi = ell;
             for (int c = j + lane; c < ell; c += 32) {
-                const double v = nrm[c];
-                if (v > best) { best = v; bi = c; }
+                double s = part[c - j];
+                for (int w = 1; w < kQrcpWarps; ++w) s += part[w * 128 + (c - j)];
+                nrm[c] = s;
+                const long long key = __double_as_longlong(s);
+                if (key > best) { best = key; bi = c; }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
             }
@@ -206,69 +305,73 @@ qrcp_kernel(const double* d, int ell, double* qt, double* rt, int* perm, const i
         }
         __syncthreads();
         const int p = piv_s;
-        // 3. swap columns j and p
+        // 3. swap columns j and p (whole columns)
         if (p != j) {
             for (int i = tid; i < ell; i += kQrcpThreads) {
-                const double tmp = W[i * ld + j];
-                W[i * ld + j] = W[i * ld + p];
-                W[i * ld + p] = tmp;
+                const double t = W[j * ldw + i];
+                W[j * ldw + i] = W[p * ldw + i];
+                W[p * ldw + i] = t;
             }
             if (tid == 0) {
                 const int t = pv[j];
                 pv[j] = pv[p];
                 pv[p] = t;
+                const double tn = nrm[j];
+                nrm[j] = nrm[p];
+                nrm[p] = tn;
             }
+            __syncthreads();
         }
-        __syncthreads();
-        // 4. Householder reflector of column j (warp 0)
-        if (warp == 0) {
-            const double alpha = W[j * ld + j];
-            double x2 = 0.0;
-            for (int i = j + 1 + lane; i < ell; i += 32) x2 += W[i * ld + j] * W[i * ld + j];
-            x2 = warp_sum(x2);
+        // 4. reflector of column j from its squared norm s = alpha^2 + |x|^2:
+        //    beta = -sign(alpha) sqrt(s), tau = 1 - alpha / beta,
+        //    v[i] = x[i] / (alpha - beta); H = I when x is exactly zero.
+        {
+            double* x = W + j * ldw;
+            const double alpha = x[j];
+            const double s = nrm[j];
             double t = 0.0;
-            if (x2 > 0.0) {
-                const double nr = sqrt(alpha * alpha + x2);
+            if (s != alpha * alpha) {
+                const double y = rsqrt_nr(s);            // 1 / |column|
+                const double nr = s * y;
                 const double beta = alpha >= 0.0 ? -nr : nr;
-                t = (beta - alpha) / beta;
-                const double scale = 1.0 / (alpha - beta);
-                for (int i = j + 1 + lane; i < ell; i += 32) W[i * ld + j] *= scale;
-                if (lane == 0) W[j * ld + j] = beta;
+                const double inv_beta = alpha >= 0.0 ? -y : y;
+                t = fma(-alpha, inv_beta, 1.0);
+                const double scale = rcp_nr(alpha - beta);
+                for (int i = j + 1 + tid; i < ell; i += kQrcpThreads) x[i] *= scale;
+                __syncthreads();
+                if (tid == 0) x[j] = beta;
             }
-            if (lane == 0) tau[j] = t;
+            if (tid == 0) tau[j] = t;
+            __syncthreads();
         }
-        __syncthreads();
         // 5. apply it to the trailing columns
         const double tj = tau[j];
-        if (tj != 0.0)
-            for (int c = j + 1 + warp; c < ell; c += kQrcpWarps) house_apply_col(W, ld, ell, j, c, tj, lane);
-        __syncthreads();
+        if (tj != 0.0 && j + 1 < ell) apply_reflector(W, ldw, part, j, j + 1, ell, tj, lane, warp);
     }
     // Rt = upper(W) with diag(Rt) >= 0
-    for (int a = tid; a < ell; a += kQrcpThreads) sgn[a] = W[a * ld + a] < 0.0 ? -1.0 : 1.0;
+    for (int a = tid; a < ell; a += kQrcpThreads) sgn[a] = W[a * ldw + a] < 0.0 ? -1.0 : 1.0;
     __syncthreads();
     for (int e = tid; e < ell * ell; e += kQrcpThreads) {
         const int a = e / ell, b = e % ell;
-        rt[e] = (b >= a) ? sgn[a] * W[a * ld + b] : 0.0;
+        rt[e] = (b >= a) ? sgn[a] * W[b * ldw + a] : 0.0;
     }
     for (int c = tid; c < ell; c += kQrcpThreads) perm[c] = pv[c];
     __syncthreads();
-    // Qt = H_0 H_1 ... H_{ell-1} formed in place (backward accumulation)
+    // Qt = H_0 H_1 ... H_{ell-1}, accumulated backwards in place
     for (int j = ell - 1; j >= 0; --j) {
         const double tj = tau[j];
-        if (j < ell - 1 && tj != 0.0)
-            for (int c = j + 1 + warp; c < ell; c += kQrcpWarps) house_apply_col(W, ld, ell, j, c, tj, lane);
-        __syncthreads();
+        if (j < ell - 1 && tj != 0.0) apply_reflector(W, ldw, part, j, j + 1, ell, tj, lane, warp);
+        double* x = W + j * ldw;
         for (int i = tid; i < ell; i += kQrcpThreads) {
-            if (i > j) W[i * ld + j] *= -tj;
-            else if (i == j) W[j * ld + j] = 1.0 - tj;
-            else W[i * ld + j] = 0.0;
+            if (i > j) x[i] *= -tj;
+            else if (i == j) x[j] = 1.0 - tj;
+            else x[i] = 0.0;
         }
         __syncthreads();
     }
     for (int e = tid; e < ell * ell; e += kQrcpThreads) {
         const int a = e / ell, b = e % ell;
-        qt[e] = W[a * ld + b] * sgn[b];
+        qt[e] = W[b * ldw + a] * sgn[b];
     }
 }
 
@@ -337,7 +440,7 @@ cudaError_t launch_trsm_rows(const double* c, int64_t ldc, int64_t rows, int64_t
 
 cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, int* perm,
                         const int* cancel, cudaStream_t st) {
-    const size_t smem = sizeof(double) * ((size_t)ell * (ell + 1) + 3 * (size_t)ell) + sizeof(int) * ell;
+    const size_t smem = sizeof(double) * ((size_t)ell * (ell | 1) + 4 * 128 + 3 * (size_t)ell) + sizeof(int) * ell;
     cudaError_t e = cudaFuncSetAttribute(qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launch();

@@ -46,7 +46,7 @@ __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, float>(float v) { re
 // Tiles of kBM output rows x (16 TN) columns, kBK k per stage; 256 threads,
 // each owns kTM rows x TN columns (columns tx, tx+16, ... to avoid bank
 // conflicts on the B tile).
-template <typename TA, typename TC, int TN>
+template <typename TA, typename TB, typename TC, int TN>
 __global__ void __launch_bounds__(kThreads) gemm_simt_kernel(GemmArgs g) {
     if (g.cancel && *g.cancel) return;
     constexpr int LP = 16 * TN;
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kThreads) gemm_simt_kernel(GemmArgs g) {
     const int64_t kbeg = (int64_t)split * kper;
     const int64_t kend = (g.K < kbeg + kper) ? g.K : kbeg + kper;
     const TA* A = static_cast<const TA*>(g.a);
-    const TC* B = static_cast<const TC*>(g.b);
+    const TB* B = static_cast<const TB*>(g.b);
     const bool a_kfast = (g.amode == A_ROWS || g.amode == A_PANEL_T);
 
     TC acc[kTM][TN];
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kThreads) gemm_simt_kernel(GemmArgs g) {
             if (g.bmode == B_PANEL) { j = idx / kBK; k = idx % kBK; } else { k = idx / LP; j = idx % LP; }
             const int64_t gk = k0 + k;
             TC v = zero_of<TC>();
-            if (j < g.L && gk < kend) v = (g.bmode == B_PANEL) ? B[j * g.ldb + gk] : B[gk * g.ldb + j];
+            if (j < g.L && gk < kend) v = cvt<TC>((g.bmode == B_PANEL) ? B[j * g.ldb + gk] : B[gk * g.ldb + j]);
             Bs[k * (LP + 1) + j] = v;
         }
         __syncthreads();
@@ -119,28 +119,28 @@ __global__ void __launch_bounds__(kThreads) gemm_simt_kernel(GemmArgs g) {
     }
 }
 
-template <typename TA, typename TC, int TN>
+template <typename TA, typename TB, typename TC, int TN>
 cudaError_t launch_tn(const GemmArgs& g, cudaStream_t st) {
     const size_t smem = sizeof(TC) * (size_t)(kBK * (kBM + 1) + kBK * (16 * TN + 1));
     static bool attr_set = false;  // per instantiation; benign race (idempotent)
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_simt_kernel<TA, TC, TN>,
+        cudaError_t e = cudaFuncSetAttribute(gemm_simt_kernel<TA, TB, TC, TN>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     dim3 grid((unsigned)((g.R + kBM - 1) / kBM), (unsigned)g.splits);
     count_launch();
-    gemm_simt_kernel<TA, TC, TN><<<grid, kThreads, smem, st>>>(g);
+    gemm_simt_kernel<TA, TB, TC, TN><<<grid, kThreads, smem, st>>>(g);
     return cudaGetLastError();
 }
 
-template <typename TA, typename TC>
+template <typename TA, typename TB, typename TC>
 cudaError_t launch_types(const GemmArgs& g, cudaStream_t st) {
-    if (g.L <= 16) return launch_tn<TA, TC, 1>(g, st);
-    if (g.L <= 32) return launch_tn<TA, TC, 2>(g, st);
-    if (g.L <= 64) return launch_tn<TA, TC, 4>(g, st);
-    return launch_tn<TA, TC, 8>(g, st);
+    if (g.L <= 16) return launch_tn<TA, TB, TC, 1>(g, st);
+    if (g.L <= 32) return launch_tn<TA, TB, TC, 2>(g, st);
+    if (g.L <= 64) return launch_tn<TA, TB, TC, 4>(g, st);
+    return launch_tn<TA, TB, TC, 8>(g, st);
 }
 
 }  // namespace
@@ -148,7 +148,7 @@ cudaError_t launch_types(const GemmArgs& g, cudaStream_t st) {
 int gemm_simt_splits(int64_t R, int64_t K, int num_sms) {
     const int64_t tiles = (R + kBM - 1) / kBM;
     int64_t want = (2LL * num_sms + tiles - 1) / tiles;
-    const int64_t maxs = K / (4 * kBK) > 1 ? K / (4 * kBK) : 1;
+    const int64_t maxs = K / kBK > 1 ? K / kBK : 1;  // at least one k-stage per split
     if (want > maxs) want = maxs;
     if (want < 1) want = 1;
     if (want > 1024) want = 1024;
@@ -157,11 +157,25 @@ int gemm_simt_splits(int64_t R, int64_t K, int num_sms) {
 
 cudaError_t launch_gemm_simt(const GemmArgs& g, cudaStream_t st) {
     if (g.R <= 0 || g.L <= 0 || g.L > 128 || g.splits < 1) return cudaErrorInvalidValue;
-    if (g.ta == T_F64 && g.tc == T_F64) return launch_types<double, double>(g, st);
-    if (g.ta == T_F32 && g.tc == T_F32) return launch_types<float, float>(g, st);
-    if (g.ta == T_F32 && g.tc == T_F64) return launch_types<float, double>(g, st);
-    if (g.ta == T_F64 && g.tc == T_F32) return launch_types<double, float>(g, st);
+    const ElemType tb = g.tb == T_SAME ? g.tc : g.tb;
+    if (g.ta == T_F64 && tb == T_F64 && g.tc == T_F64) return launch_types<double, double, double>(g, st);
+    if (g.ta == T_F32 && tb == T_F32 && g.tc == T_F32) return launch_types<float, float, float>(g, st);
+    if (g.ta == T_F32 && tb == T_F64 && g.tc == T_F64) return launch_types<float, double, double>(g, st);
+    if (g.ta == T_F64 && tb == T_F32 && g.tc == T_F32) return launch_types<double, float, float>(g, st);
+    if (g.ta == T_F64 && tb == T_F64 && g.tc == T_F32) return launch_types<double, double, float>(g, st);
     return cudaErrorInvalidValue;
+}
+
+int device_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (!cached[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+        cached[dev] = v;
+    }
+    return cached[dev];
 }
 
 // ---------------------------------------------------------------------------
@@ -169,19 +183,42 @@ cudaError_t launch_gemm_simt(const GemmArgs& g, cudaStream_t st) {
 // Element (x, y) of the region is at y * ld + x.
 // ---------------------------------------------------------------------------
 namespace {
+// Block = 32 output elements x 8 split groups. Thread (x, g) adds the
+// partials g, g + 8, g + 16, ... of element x with four accumulators; the
+// eight group sums are then added in group order. The summation order depends
+// only on the split count, so results are reproducible.
+constexpr int kRedGroups = 8;
 template <typename TP>
-__global__ void reduce_splits_kernel(const TP* part, int splits, int64_t stride, double* out,
-                                     int64_t ld, int64_t rows, int64_t cols, int64_t ld_out,
-                                     const int* cancel) {
+__global__ void __launch_bounds__(32 * kRedGroups)
+reduce_splits_kernel(const TP* part, int splits, int64_t stride, double* out, int64_t ld, int64_t rows,
+                     int64_t cols, int64_t ld_out, const int* cancel) {
     if (cancel && *cancel) return;
+    __shared__ double red[kRedGroups][33];
+    const int tx = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int64_t total = rows * cols;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = (int64_t)blockIdx.x * 32 + tx;
+    double s = 0.0;
+    if (e < total) {
         const int64_t y = e / rows, x = e % rows;
-        const int64_t off = y * ld + x;
-        double s = 0.0;
-        for (int p = 0; p < splits; ++p) s += (double)part[(int64_t)p * stride + off];
-        out[y * ld_out + x] = s;
+        const TP* p = part + y * ld + x;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int q = g;
+        for (; q + 3 * kRedGroups < splits; q += 4 * kRedGroups) {
+            a0 += (double)p[(int64_t)q * stride];
+            a1 += (double)p[(int64_t)(q + kRedGroups) * stride];
+            a2 += (double)p[(int64_t)(q + 2 * kRedGroups) * stride];
+            a3 += (double)p[(int64_t)(q + 3 * kRedGroups) * stride];
+        }
+        for (; q < splits; q += kRedGroups) a0 += (double)p[(int64_t)q * stride];
+        s = (a0 + a1) + (a2 + a3);
+    }
+    red[g][tx] = s;
+    __syncthreads();
+    if (g == 0 && e < total) {
+        double t = red[0][tx];
+        for (int k = 1; k < kRedGroups; ++k) t += red[k][tx];
+        const int64_t y = e / rows, x = e % rows;
+        out[y * ld_out + x] = t;
     }
 }
 }  // namespace
@@ -191,16 +228,15 @@ cudaError_t launch_reduce_splits(const void* part, ElemType tpart, int splits, i
                                  const int* cancel, cudaStream_t st) {
     const int64_t total = rows * cols;
     if (total <= 0) return cudaSuccess;
-    int blocks = (int)((total + 255) / 256);
-    if (blocks > 4096) blocks = 4096;
+    const unsigned blocks = (unsigned)((total + 31) / 32);
     if (tpart == T_F64) {
         count_launch();
-        reduce_splits_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double*>(part), splits,
-                                                             stride, out, ld, rows, cols, ld_out, cancel);
+        reduce_splits_kernel<double><<<blocks, 32 * kRedGroups, 0, st>>>(static_cast<const double*>(part), splits,
+                                                                         stride, out, ld, rows, cols, ld_out, cancel);
     } else {
         count_launch();
-        reduce_splits_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(part), splits,
-                                                            stride, out, ld, rows, cols, ld_out, cancel);
+        reduce_splits_kernel<float><<<blocks, 32 * kRedGroups, 0, st>>>(static_cast<const float*>(part), splits,
+                                                                        stride, out, ld, rows, cols, ld_out, cancel);
     }
     return cudaGetLastError();
 }
@@ -383,6 +419,8 @@ cudaError_t launch_panel_convert(const double* src, int64_t lds, int64_t rows, i
             panel_convert_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(
                 src, lds, rows, cols, static_cast<__nv_bfloat16*>(dst), ldd, cancel);
             break;
+        default:
+            return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }

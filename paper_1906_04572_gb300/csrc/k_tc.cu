@@ -23,7 +23,8 @@
 // Two accumulators alternate so the epilogue of one segment overlaps the
 // MMAs of the next.
 //
-// Every wait on an mbarrier is bounded (kWaitNs of %globaltimer); on timeout
+// Every wait on an mbarrier is bounded (about kWaitNs, counted in SM clock
+// cycles); on timeout
 // the CTA sets FLAG_TIMEOUT, stops issuing work, waits (again bounded) for
 // its own copies and MMAs in flight, frees its tensor memory and returns.
 #include <cuda.h>
@@ -69,12 +70,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
@@ -100,16 +95,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait; false if the phase did not complete within `limit_ns` or if
-// another role already aborted.
+// Bounded wait; false if the phase did not complete within about `limit_ns`
+// (measured with the SM cycle counter at the 2.07 GHz maximum clock, checked
+// every 256 polls so the poll loop stays tight) or if another role aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                           unsigned long long limit_ns = kWaitNs) {
     if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    while (true) {
+    const long long limit_cycles = (long long)(limit_ns * 2.07);
+    const long long t0 = clock64();
+    for (uint32_t polls = 1;; ++polls) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (abort_flag && *abort_flag) return false;
-        if (global_ns() - t0 > limit_ns) return false;
+        if ((polls & 255u) == 0) {
+            if (abort_flag && *abort_flag) return false;
+            if (clock64() - t0 > limit_cycles) return false;
+        }
     }
 }
 
@@ -204,9 +203,9 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
 
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long c = blockIdx.x;
-    const long long u0 = c * p.units / p.grid;
-    const long long u1 = (c + 1) * p.units / p.grid;
+    const int c = blockIdx.x;
+    const int u0 = (int)((long long)c * p.units / p.grid);
+    const int u1 = (int)((long long)(c + 1) * p.units / p.grid);
     const int S = p.stages;
 
     if (threadIdx.x == 0) {
@@ -237,20 +236,18 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = tmem_holder;
-    const long long KC = p.kchunks;
+    const int KC = (int)p.kchunks;
 
     if (warp == 4) {
         if (lane == 0) {
             // ---------------- TMA producer ----------------
-            long long li = 0;
-            for (long long u = u0; u < u1; ++u, ++li) {
-                const int s = (int)(li % S);
-                const long long r = li / S;
+            int li = 0, s = 0, r = 0;       // unit index, stage, round (li = r S + s)
+            int t = u0 / KC, kc = u0 % KC;  // tile and K chunk of unit u
+            for (int u = u0; u < u1; ++u, ++li) {
                 if (r > 0 && !mbar_wait(&empty_bar[s], (uint32_t)((r - 1) & 1), &abort_s)) {
                     abort_s = 1;
                     break;
                 }
-                const long long t = u / KC, kc = u % KC;
                 uint8_t* sa = smem + (size_t)s * p.stage_bytes;
                 uint8_t* sb = sa + p.a_bytes;
                 mbar_expect_tx(&full_bar[s], p.stage_bytes);
@@ -264,24 +261,26 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                                     kx);
                 }
                 tma_load_2d(sb, &map_b, &full_bar[s], kx, 0);
+                if (++s == S) { s = 0; ++r; }
+                if (++kc == KC) { kc = 0; ++t; }
             }
             if (abort_s) {
                 // drain: wait (bounded) for every copy that was issued but not consumed
-                const long long issued = li;
-                for (long long j = consumed_s; j < issued; ++j)
+                const int issued = li;
+                for (int j = (int)consumed_s; j < issued; ++j)
                     mbar_wait(&full_bar[j % S], (uint32_t)((j / S) & 1), nullptr, 100000000ull);
             }
         }
     } else if (warp == 5) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            long long li = 0, seg = 0;
+            int li = 0, seg = 0, s = 0, r = 0;
             const int ksteps = p.tf32 ? p.kchunk_elems / 8 : p.kchunk_elems / 16;
             const uint32_t kstep_bytes = 32;  // 16 bf16 or 8 tf32 elements of K
-            for (long long u = u0; u < u1 && !abort_s; ++seg) {
-                const long long t = u / KC;
-                const long long seg_end = (u1 < (t + 1) * KC) ? u1 : (t + 1) * KC;
-                const int a = (int)(seg & 1);
+            for (int u = u0; u < u1 && !abort_s; ++seg) {
+                const int t = u / KC;
+                const int seg_end = (u1 < (t + 1) * KC) ? u1 : (t + 1) * KC;
+                const int a = seg & 1;
                 if (seg >= 2 && !mbar_wait(&acce_bar[a], (uint32_t)(((seg >> 1) - 1) & 1), &abort_s)) {
                     abort_s = 1;
                     break;
@@ -290,8 +289,6 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                 const uint32_t tacc = tmem_base + (uint32_t)(a * (p.tmem_cols / 2));
                 bool first = true;
                 for (; u < seg_end; ++u, ++li) {
-                    const int s = (int)(li % S);
-                    const long long r = li / S;
                     if (!mbar_wait(&full_bar[s], (uint32_t)(r & 1), &abort_s)) {
                         abort_s = 1;
                         break;
@@ -320,6 +317,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                     }
                     first = false;
                     mma_commit(&empty_bar[s]);
+                    if (++s == S) { s = 0; ++r; }
                 }
                 if (abort_s) break;
                 mma_commit(&accf_bar[a]);
@@ -332,18 +330,18 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
     } else {
         // ---------------- epilogue: warps 0-3 ----------------
         const int row = warp * 32 + lane;
-        long long seg = 0;
-        for (long long u = u0; u < u1; ++seg) {
-            const long long t = u / KC;
-            const long long seg_end = (u1 < (t + 1) * KC) ? u1 : (t + 1) * KC;
-            const int a = (int)(seg & 1);
+        int seg = 0;
+        for (int u = u0; u < u1; ++seg) {
+            const int t = u / KC;
+            const int seg_end = (u1 < (t + 1) * KC) ? u1 : (t + 1) * KC;
+            const int a = seg & 1;
             if (!mbar_wait(&accf_bar[a], (uint32_t)((seg >> 1) & 1), &abort_s)) {
                 abort_s = 1;
                 break;
             }
             tc_fence_after();
-            const long long piece = c - unit_owner(t * KC, p.units, p.grid);
-            float* dst = p.part + ((t * p.maxp + piece) * p.ellp) * (long long)kTileM + row;
+            const long long piece = c - unit_owner((long long)t * KC, p.units, p.grid);
+            float* dst = p.part + (((long long)t * p.maxp + piece) * p.ellp) * (long long)kTileM + row;
             const uint32_t tacc = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * (p.tmem_cols / 2));
             for (int c0 = 0; c0 < p.ellp; c0 += 16) {
                 float v[16];
@@ -393,15 +391,35 @@ __device__ __forceinline__ __nv_bfloat16 to_bf16(double v) {
     return __float2bfloat16_rn(f);
 }
 
+// One block row-segment per iteration: block b handles rows b, b + G, ...;
+// threads cover the row 4 elements at a time (float4 loads when the row start
+// is 16-byte aligned, 8-byte bf16x4 stores; ldb is a multiple of 8).
 template <typename TI>
 __global__ void cast_bf16_kernel(const TI* a, long long m, long long n, long long lda, __nv_bfloat16* out,
                                  long long ldb, const int* cancel) {
     if (cancel && *cancel) return;
-    const long long total = m * ldb;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long i = e / ldb, j = e % ldb;
-        out[e] = (j < n) ? to_bf16(a[i * lda + j]) : __float2bfloat16_rn(0.f);
+    for (long long i = blockIdx.x; i < m; i += gridDim.x) {
+        const TI* src = a + i * lda;
+        __nv_bfloat16* dst = out + i * ldb;
+        const bool vec = sizeof(TI) == 4 && (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+        for (long long j = 4LL * threadIdx.x; j < ldb; j += 4LL * blockDim.x) {
+            float v[4];
+            if (vec && j + 3 < n) {
+                const float4 f = *reinterpret_cast<const float4*>(src + j);
+                v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+                __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
+                __nv_bfloat162 hi = __floats2bfloat162_rn(v[2], v[3]);
+                uint2 pk;
+                pk.x = *reinterpret_cast<uint32_t*>(&lo);
+                pk.y = *reinterpret_cast<uint32_t*>(&hi);
+                *reinterpret_cast<uint2*>(dst + j) = pk;
+            } else {
+                for (int q = 0; q < 4; ++q) {
+                    const long long jj = j + q;
+                    if (jj < ldb) dst[jj] = (jj < n) ? to_bf16(src[jj]) : __float2bfloat16_rn(0.f);
+                }
+            }
+        }
     }
 }
 
@@ -575,8 +593,7 @@ cudaError_t launch_copy_f32_padded(const float* a, int64_t m, int64_t n, int64_t
 
 cudaError_t launch_cast_bf16(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, void* abf,
                              int64_t ldb, const int* cancel, cudaStream_t st) {
-    const long long total = m * ldb;
-    const int blocks = (int)std::min<long long>((total + 255) / 256, 8192);
+    const int blocks = (int)std::min<long long>(m, 16LL * 152);
     count_launch();
     if (ta == T_F32)
         cast_bf16_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(a), m, n, lda,
