@@ -51,9 +51,16 @@ typedef enum { CORUTV_F64 = 0, CORUTV_F32 = 1 } corutv_dtype;
 /* Arithmetic of the 2q+2 sketch / power products A X and A^T Y.
  * F64: FP64 FMA. F32: FP32 FMA. TF32 / BF16: tensor cores (tcgen05) with FP32
  * accumulation; BF16 first writes a bf16 copy of A. The projection D of
- * eq. 7 always runs in FP64 (dtype F64) or FP32 (dtype F32); the Gram
- * Cholesky factorisations and the pivoted QR of D always run in FP64. */
-typedef enum { CORUTV_P_F64 = 0, CORUTV_P_F32 = 1, CORUTV_P_TF32 = 2, CORUTV_P_BF16 = 3 } corutv_prec;
+ * eq. 7 always has FP32 accuracy (dtype F32) or runs in FP64 (dtype F64);
+ * with BF16 sketches and FP32 input it runs on the tensor cores with
+ * exact three-way bf16 splits of A and Q2 (see BF16X3). The Gram Cholesky
+ * factorisations and the pivoted QR of D always run in FP64.
+ * BF16X3 (corutv_sketch only, FP32 A, trans = 0): A X from the exact splits
+ * A = A_h + A_m + A_l, X = X_h + X_m + X_l into bf16 parts, all nine part
+ * products on the tensor cores with FP32 accumulation -- the rounding of an
+ * FP32 dot product at the memory traffic of 1.5 FP32 passes. */
+typedef enum { CORUTV_P_F64 = 0, CORUTV_P_F32 = 1, CORUTV_P_TF32 = 2, CORUTV_P_BF16 = 3,
+               CORUTV_P_BF16X3 = 4 } corutv_prec;
 
 typedef struct {
     int64_t k;            /* target rank */

@@ -19,8 +19,8 @@ LIB_PATH = os.path.join(_HERE, "lib", "libcorutv.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EPENDING, ETIMEDOUT, ENOTCONV, EBREAKDOWN = range(8)
 F64, F32 = 0, 1
-P_F64, P_F32, P_TF32, P_BF16 = 0, 1, 2, 3
-PREC_NAMES = {"f64": P_F64, "f32": P_F32, "tf32": P_TF32, "bf16": P_BF16}
+P_F64, P_F32, P_TF32, P_BF16, P_BF16X3 = 0, 1, 2, 3, 4
+PREC_NAMES = {"f64": P_F64, "f32": P_F32, "tf32": P_TF32, "bf16": P_BF16, "bf16x3": P_BF16X3}
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EPENDING", 5: "ETIMEDOUT",
                 6: "ENOTCONV", 7: "EBREAKDOWN"}
 

@@ -165,14 +165,18 @@ struct FactorPlan {
     ElemType tcomp;   // element type of the B operand of the sketch products
     ElemType tdproj;  // arithmetic of the projection pass (eq. 7)
     ElemType torth;   // arithmetic of the Gram products and triangular solves of the thin QRs
+    ElemType tp;      // element type of the tall-skinny panels (X, C1, Q1, C2, Q2, W)
     bool tensor;      // sketch products on tcgen05
+    bool split;       // projection by exact bf16 splits on tcgen05 (BF16 sketches, FP32 input)
+    int64_t seg;      // columns per segment of the bf16 copy of A ([A_h | A_m | A_l] when split)
     int sp_ax, sp_aty, sp_w, gs_m, gs_n;
     int64_t part_elems;
     int num_sms;
 };
 
 struct FactorBufs {
-    double *x, *c1, *q1, *c2, *q2, *w, *tmp, *gpart, *g, *r, *d, *qt, *rt, *upanel, *zpanel;
+    void *x, *c1, *q1, *c2, *q2, *w, *tmp;   // panels of type FactorPlan::tp
+    double *gpart, *g, *r, *d, *qt, *rt, *upanel, *zpanel;
     void *xc, *q1c, *q2c, *part;
     void* abf;        // bf16 copy of A for CORUTV_P_BF16
     int *perm, *skip;
@@ -195,6 +199,8 @@ corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64
     if (lda < n) return fail(CORUTV_EINVAL, "lda = %lld < n = %lld", (long long)lda, (long long)n);
     if (prec < CORUTV_P_F64 || prec > CORUTV_P_BF16) return fail(CORUTV_EINVAL, "unknown sketch precision %d", (int)prec);
     pl.tensor = (prec == CORUTV_P_TF32 || prec == CORUTV_P_BF16);
+    pl.split = prec == CORUTV_P_BF16 && ta == T_F32;
+    pl.seg = pl.split ? round_up(n, 64) : round_up(n, 8);
     if (prec == CORUTV_P_TF32)
         return fail(CORUTV_EINVAL, "TF32 sketches are not available for the full factorisation: the A^T Y "
                                    "product has no TF32 kernel (use CORUTV_P_BF16 or CORUTV_P_F32)");
@@ -204,6 +210,7 @@ corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64
     pl.tcomp = pl.tensor ? (prec == CORUTV_P_BF16 ? T_BF16 : T_F32) : (prec == CORUTV_P_F64 ? T_F64 : T_F32);
     pl.tdproj = (ta == T_F64) ? T_F64 : T_F32;
     pl.torth = (prec == CORUTV_P_F64) ? T_F64 : T_F32;
+    pl.tp = (ta == T_F32 && prec != CORUTV_P_F64) ? T_F32 : T_F64;
     pl.sp_ax = gemm_simt_splits(m, n, num_sms);
     pl.sp_aty = gemm_simt_splits(n, m, num_sms);
     pl.sp_w = pl.sp_ax;
@@ -218,16 +225,16 @@ corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64
 template <typename C>
 void carve_factor(C& cv, const FactorPlan& pl, FactorBufs& b) {
     const int64_t pm = pl.ellp * pl.ldm, pn = pl.ellp * pl.ldn, ll = pl.ellp * pl.ellp;
-    const int es_c = elem_size(pl.tcomp), es_d = elem_size(pl.tdproj);
-    b.x = cv.template take<double>(pn);
-    b.c1 = cv.template take<double>(pm);
-    b.q1 = cv.template take<double>(pm);
-    b.c2 = cv.template take<double>(pn);
-    b.q2 = cv.template take<double>(pn);
-    b.w = cv.template take<double>(pm);
+    const int es_c = elem_size(pl.tcomp), es_d = elem_size(pl.tdproj), es_p = elem_size(pl.tp);
+    b.x = cv.template take<char>(pn * es_p);
+    b.c1 = cv.template take<char>(pm * es_p);
+    b.q1 = cv.template take<char>(pm * es_p);
+    b.c2 = cv.template take<char>(pn * es_p);
+    b.q2 = cv.template take<char>(pn * es_p);
+    b.w = cv.template take<char>(pm * es_p);
+    b.tmp = cv.template take<char>(std::max(pm, pn) * es_p);
     b.upanel = cv.template take<double>(pm);
     b.zpanel = cv.template take<double>(pn);
-    b.tmp = cv.template take<double>(std::max(pm, pn));
     b.gpart = cv.template take<double>((int64_t)std::max(pl.gs_m, pl.gs_n) * ll);
     b.g = cv.template take<double>(ll);
     b.r = cv.template take<double>(ll);
@@ -236,9 +243,9 @@ void carve_factor(C& cv, const FactorPlan& pl, FactorBufs& b) {
     b.rt = cv.template take<double>(ll);
     b.xc = cv.template take<char>(pn * es_c);
     b.q1c = cv.template take<char>(pm * es_c);
-    b.q2c = cv.template take<char>(pn * es_d);
+    b.q2c = cv.template take<char>(pl.split ? 3 * pn * 2 : pn * es_d);
     b.part = cv.template take<char>(pl.part_elems * std::max(8, std::max(es_c, es_d)));
-    b.abf = pl.prec == CORUTV_P_BF16 ? cv.template take<char>(pl.m * round_up(pl.n, 8) * 2) : nullptr;
+    b.abf = pl.prec == CORUTV_P_BF16 ? cv.template take<char>(pl.m * (pl.split ? 3 : 1) * pl.seg * 2) : nullptr;
     b.perm = cv.template take<int>(pl.ellp);
     b.skip = cv.template take<int>(8);
 }
@@ -258,9 +265,10 @@ struct Exec {
     Profiler* prof = nullptr;
 };
 
-// C = A X (am = A_ROWS, R = m, K = n) or A^T Y (am = A_COLS, R = n, K = m) on SIMT cores.
+// C = A X (am = A_ROWS, R = m, K = n) or A^T Y (am = A_COLS, R = n, K = m) on
+// SIMT cores, written to the panel `out` (type pl.tp).
 corutv_status sketch_simt(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, AMode am,
-                          const void* a, ElemType ta, const void* bop, ElemType tc, double* out,
+                          const void* a, ElemType ta, const void* bop, ElemType tc, void* out,
                           int64_t ldout) {
     const int64_t R = am == A_ROWS ? pl.m : pl.n;
     const int64_t K = am == A_ROWS ? pl.n : pl.m;
@@ -272,54 +280,54 @@ corutv_status sketch_simt(const Exec& ex, const FactorPlan& pl, const FactorBufs
         ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
         CK(launch_gemm_simt(g, ex.st));
     }
-    CK(launch_reduce_splits(b.part, tc, splits, pl.ellp * ldout, out, ldout, R, pl.ell, ldout, ex.cancel,
+    CK(launch_reduce_splits(b.part, tc, splits, pl.ellp * ldout, out, pl.tp, ldout, R, pl.ell, ldout, ex.cancel,
                             ex.st));
     return CORUTV_OK;
 }
 
-// G = X^T Y (ell x ell, written as FP64) for two FP64 panels of `len` rows,
-// products and split sums in arithmetic tg (FP64, or FP32 on the mixed paths).
-corutv_status gram(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, const double* x,
-                   int64_t ldx, const double* y, int64_t ldy, int64_t len, double* out,
-                   const int* cancel, ElemType tg = T_F64) {
+// G = X^T Y (ell x ell, written as FP64) for two panels of type pl.tp and
+// `len` rows; products and split sums in arithmetic tg.
+corutv_status gram(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, const void* x,
+                   int64_t ldx, const void* y, int64_t ldy, int64_t len, double* out,
+                   const int* cancel, ElemType tg) {
     const int gs = gemm_simt_splits(pl.ell, len, ex.num_sms);
     const int64_t ll = pl.ell * pl.ell;
-    GemmArgs g{A_PANEL_T, B_PANEL, O_ROWMAJ, T_F64, tg, x, ldx, y, ldy, b.gpart, pl.ell, ll,
+    GemmArgs g{A_PANEL_T, B_PANEL, O_ROWMAJ, pl.tp, tg, x, ldx, y, ldy, b.gpart, pl.ell, ll,
                pl.ell, len, pl.ell, gs, cancel};
-    g.tb = T_F64;
+    g.tb = pl.tp;
     CK(launch_gemm_simt(g, ex.st));
-    CK(launch_reduce_splits(b.gpart, tg, gs, ll, out, pl.ell, pl.ell, pl.ell, pl.ell, cancel, ex.st));
+    CK(launch_reduce_splits(b.gpart, tg, gs, ll, out, T_F64, pl.ell, pl.ell, pl.ell, pl.ell, cancel, ex.st));
     return CORUTV_OK;
 }
 
-// Thin QR of the FP64 panel c (len x ell) by CholeskyQR: `passes` = 2 gives
-// CholeskyQR2 (used for the bases Q1, Q2 that leave the power loop, and
+// Thin QR of the panel c (len x ell, type pl.tp) by CholeskyQR: `passes` = 2
+// gives CholeskyQR2 (used for the bases Q1, Q2 that leave the power loop, and
 // everywhere on the FP64 path); `passes` = 1 is used for the intermediate
 // bases of the power iteration on the mixed paths, where only the span
 // matters. A pass whose Gram needed the shift is followed by one more pass
 // (shifted CholeskyQR3). Gram products and triangular solves run in
-// pl.torth; every Cholesky factorisation runs in FP64. Writes the FP64
-// panel q and, if qc != nullptr, a copy of type tqc.
-corutv_status orth(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, const double* c,
-                   int64_t ld, int64_t len, double* q, void* qc, ElemType tqc, int passes = 2) {
+// pl.torth; every Cholesky factorisation runs in FP64. Writes the panel q
+// (type pl.tp) and, if qc != nullptr, a copy of type tqc.
+corutv_status orth(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, const void* c,
+                   int64_t ld, int64_t len, void* q, void* qc, ElemType tqc, int passes = 2) {
     const int64_t ell = pl.ell;
-    const ElemType tw = pl.torth;
+    const ElemType tw = pl.torth, tp = pl.tp;
     ProfScope ps(ex.prof, CORUTV_STAGE_ORTH, ex.st);
-    double* p1 = passes == 1 ? q : b.tmp;
+    void* p1 = passes == 1 ? q : b.tmp;
     void* p1c = passes == 1 ? qc : nullptr;
     // pass 1
     CKS(gram(ex, pl, b, c, ld, c, ld, len, b.g, ex.cancel, tw));
     CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, b.skip, ex.cancel, ex.st));
-    CK(launch_trsm_rows(c, ld, len, ell, b.r, tw, p1, ld, p1c, tqc, ld, ex.cancel, ex.st));
+    CK(launch_trsm_rows(c, tp, ld, len, ell, b.r, tw, p1, ld, p1c, tqc, ld, ex.cancel, ex.st));
     // extra pass, only after a shifted pass 1
     CKS(gram(ex, pl, b, p1, ld, p1, ld, len, b.g, b.skip, tw));
     CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, nullptr, b.skip, ex.st));
-    CK(launch_trsm_rows(p1, ld, len, ell, b.r, tw, p1, ld, p1c, tqc, ld, b.skip, ex.st));
+    CK(launch_trsm_rows(p1, tp, ld, len, ell, b.r, tw, p1, ld, p1c, tqc, ld, b.skip, ex.st));
     if (passes == 1) return CORUTV_OK;
     // pass 2
     CKS(gram(ex, pl, b, b.tmp, ld, b.tmp, ld, len, b.g, ex.cancel, tw));
     CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, nullptr, ex.cancel, ex.st));
-    CK(launch_trsm_rows(b.tmp, ld, len, ell, b.r, tw, q, ld, qc, tqc, ld, ex.cancel, ex.st));
+    CK(launch_trsm_rows(b.tmp, tp, ld, len, ell, b.r, tw, q, ld, qc, tqc, ld, ex.cancel, ex.st));
     return CORUTV_OK;
 }
 
@@ -330,18 +338,20 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     const int64_t m = pl.m, n = pl.n, ell = pl.ell;
     ProfScope ps_all(ex.prof, CORUTV_STAGE_FACTOR, ex.st);
     // Step 1: X = Psi (panel n x ellp, padding columns zero)
-    if (psi_dev) CK(launch_rowmajor_to_panel(psi_dev, ell, n, ell, pl.ellp, b.x, pl.ldn, ex.st));
-    else CK(launch_gaussian_panel(seed, sid, n, ell, pl.ellp, b.x, pl.ldn, ex.cancel, ex.st));
+    if (psi_dev) CK(launch_rowmajor_to_panel(psi_dev, ell, n, ell, pl.ellp, b.x, pl.tp, pl.ldn, ex.st));
+    else CK(launch_gaussian_panel(seed, sid, n, ell, pl.ellp, b.x, pl.tp, pl.ldn, ex.cancel, ex.st));
     if (pl.tensor) {
         // padding columns of the bf16 / fp32 operand panels must read as zero
         CK(cudaMemsetAsync(b.q1c, 0, (size_t)pl.ellp * pl.ldm * elem_size(pl.tcomp), ex.st));
-        CK(launch_panel_convert(b.x, pl.ldn, n, pl.ellp, b.xc, pl.tcomp, pl.ldn, ex.cancel, ex.st));
-        if (pl.prec == CORUTV_P_BF16)
-            CK(launch_cast_bf16(a, pl.ta, m, n, pl.lda, b.abf, round_up(n, 8), ex.cancel, ex.st));
+        CK(launch_panel_convert(b.x, pl.tp, pl.ldn, n, pl.ellp, b.xc, pl.tcomp, pl.ldn, ex.cancel, ex.st));
+        if (pl.split)
+            CK(launch_cast_bf16_split(static_cast<const float*>(a), m, n, pl.lda, b.abf, pl.seg, ex.cancel, ex.st));
+        else if (pl.prec == CORUTV_P_BF16)
+            CK(launch_cast_bf16(a, pl.ta, m, n, pl.lda, b.abf, pl.seg, ex.cancel, ex.st));
     } else {
-        CK(launch_panel_convert(b.x, pl.ldn, n, ell, b.xc, pl.tcomp, pl.ldn, ex.cancel, ex.st));
+        CK(launch_panel_convert(b.x, pl.tp, pl.ldn, n, ell, b.xc, pl.tcomp, pl.ldn, ex.cancel, ex.st));
     }
-    const int64_t ldabf = round_up(n, 8);
+    const int64_t ldabf = (pl.split ? 3 : 1) * pl.seg;  // the sketches read the A_h segment
     for (int64_t it = 0; it <= pl.q; ++it) {
         // eq. 4: C1 = A X
         if (pl.tensor) {
@@ -349,7 +359,7 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
             const int64_t lda_op = pl.prec == CORUTV_P_BF16 ? ldabf : pl.lda;
             ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
             CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, /*trans=*/0, b.xc, pl.ldn, ell, pl.ellp, b.part,
-                                b.c1, pl.ldm, ex.num_sms, ex.flags, ex.cancel, ex.st));
+                                b.c1, pl.tp, pl.ldm, ex.num_sms, ex.flags, ex.cancel, ex.st));
         } else {
             CKS(sketch_simt(ex, pl, b, A_ROWS, a, pl.ta, b.xc, pl.tcomp, b.c1, pl.ldm));
         }
@@ -361,23 +371,29 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
             const int64_t lda_op = pl.prec == CORUTV_P_BF16 ? ldabf : pl.lda;
             ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
             CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, /*trans=*/1, b.q1c, pl.ldm, ell, pl.ellp, b.part,
-                                b.c2, pl.ldn, ex.num_sms, ex.flags, ex.cancel, ex.st));
+                                b.c2, pl.tp, pl.ldn, ex.num_sms, ex.flags, ex.cancel, ex.st));
         } else {
             CKS(sketch_simt(ex, pl, b, A_COLS, a, pl.ta, b.q1c, pl.tcomp, b.c2, pl.ldn));
         }
         if (it < pl.q) CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.x, b.xc, pl.tcomp, inner));
     }
     // Q2 = qr(C2), with a copy in the projection's arithmetic
-    CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.q2, b.q2c, pl.tdproj, 2));
-    // eq. 7: W = A Q2 (FP64 or FP32 from the original A), D = Q1^T W (FP64)
-    {
+    CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.q2, pl.split ? nullptr : b.q2c, pl.tdproj, 2));
+    // eq. 7: W = A Q2 (FP64, or FP32-accurate from the original A), D = Q1^T W
+    if (pl.split) {
+        CK(launch_split_panel(static_cast<const float*>(b.q2), pl.ldn, n, ell, pl.ellp, b.q2c, pl.ldn, ex.cancel,
+                              ex.st));
+        ProfScope ps(ex.prof, CORUTV_STAGE_PROJECT, ex.st);
+        CK(launch_project_split_tc(b.abf, m, n, pl.seg, b.q2c, pl.ldn, ell, pl.ellp, b.part, b.w, pl.tp, pl.ldm,
+                                   ex.num_sms, ex.flags, ex.cancel, ex.st));
+    } else {
         GemmArgs g{A_ROWS, B_PANEL, O_PANEL, pl.ta, pl.tdproj, a, pl.lda, b.q2c, pl.ldn, b.part, pl.ldm,
                    pl.ellp * pl.ldm, m, n, ell, pl.sp_w, ex.cancel};
         {
             ProfScope ps(ex.prof, CORUTV_STAGE_PROJECT, ex.st);
             CK(launch_gemm_simt(g, ex.st));
         }
-        CK(launch_reduce_splits(b.part, pl.tdproj, pl.sp_w, pl.ellp * pl.ldm, b.w, pl.ldm, m, ell, pl.ldm,
+        CK(launch_reduce_splits(b.part, pl.tdproj, pl.sp_w, pl.ellp * pl.ldm, b.w, pl.tp, pl.ldm, m, ell, pl.ldm,
                                 ex.cancel, ex.st));
     }
     CKS(gram(ex, pl, b, b.q1, pl.ldm, b.w, pl.ldm, m, b.d, ex.cancel, pl.tdproj));
@@ -394,7 +410,7 @@ corutv_status emit_user(const Exec& ex, const FactorPlan& pl, const FactorBufs& 
                         int64_t ldu, void* t, void* v, int64_t ldv, int32_t* perm) {
     const int64_t ell = pl.ell;
     if (u) {
-        GemmArgs g{A_PANEL, B_SMALL, O_ROWMAJ, T_F64, tout, b.q1, pl.ldm, nullptr, ell, u, ldu, 0,
+        GemmArgs g{A_PANEL, B_SMALL, O_ROWMAJ, pl.tp, tout, b.q1, pl.ldm, nullptr, ell, u, ldu, 0,
                    pl.m, ell, ell, 1, ex.cancel};
         // the B operand must have the compute type: Qt in FP64, or converted for FP32
         if (tout == T_F64) {
@@ -406,7 +422,7 @@ corutv_status emit_user(const Exec& ex, const FactorPlan& pl, const FactorBufs& 
         CK(launch_gemm_simt(g, ex.st));
     }
     CK(launch_copy_small(b.rt, ell, t, tout, ex.cancel, ex.st));
-    if (v) CK(launch_gather_v(b.q2, pl.ldn, pl.n, ell, b.perm, v, tout, ldv, ex.cancel, ex.st));
+    if (v) CK(launch_gather_v(b.q2, pl.tp, pl.ldn, pl.n, ell, b.perm, v, tout, ldv, ex.cancel, ex.st));
     if (perm) CK(cudaMemcpyAsync(perm, b.perm, sizeof(int32_t) * ell, cudaMemcpyDeviceToDevice, ex.st));
     return CORUTV_OK;
 }
@@ -764,6 +780,32 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
     std::lock_guard<std::mutex> lk(ctx->call_mu);
     DeviceGuard guard(ctx->device);
     const ElemType ta = dtype == CORUTV_F64 ? T_F64 : T_F32;
+    if ((int)prec == CORUTV_P_BF16X3) {
+        // FP32-accurate A X from exact bf16 splits (tensor cores)
+        if (ta != T_F32 || trans) return fail(CORUTV_EINVAL, "BF16X3 needs FP32 A and trans = 0");
+        const int64_t ellp = round_up(ell, 16), ldn = round_up(n, 64), ldm = round_up(m, 64), seg = round_up(n, 64);
+        const int64_t part_elems = tc_partial_elems(m, n, ellp, ldm, ldn, ctx->num_sms);
+        Carver measure(nullptr);
+        measure.take<float>(ellp * ldn);
+        measure.take<char>(3 * ellp * ldn * 2);
+        measure.take<double>(ellp * ldm);
+        measure.take<float>(part_elems);
+        measure.take<char>(m * 3 * seg * 2);
+        CKS(ensure_ws(ctx, ctx->ws, measure.off, ctx->stream));
+        Carver cv(ctx->ws.ptr);
+        float* xp = cv.take<float>(ellp * ldn);
+        void* x3 = cv.take<char>(3 * ellp * ldn * 2);
+        double* cp = cv.take<double>(ellp * ldm);
+        void* part = cv.take<float>(part_elems);
+        void* a3 = cv.take<char>(m * 3 * seg * 2);
+        CK(launch_rowmajor_to_panel(X, ldx, n, ell, ellp, xp, T_F32, ldn, ctx->stream));
+        CK(launch_split_panel(xp, ldn, n, ell, ellp, x3, ldn, nullptr, ctx->stream));
+        CK(launch_cast_bf16_split(static_cast<const float*>(A), m, n, lda, a3, seg, nullptr, ctx->stream));
+        CK(launch_project_split_tc(a3, m, n, seg, x3, ldn, ell, ellp, part, cp, T_F64, ldm, ctx->num_sms, ctx->flags,
+                                   nullptr, ctx->stream));
+        CK(launch_panel_to_rowmajor(cp, ldm, m, ell, C, T_F64, ldc, nullptr, ctx->stream));
+        return CORUTV_OK;
+    }
     FactorPlan pl;
     // plan with k = ell, p = 0, q = 0; sizes m, n need ell < min(m, n) only for the full pipeline
     pl.m = m; pl.n = n; pl.lda = lda; pl.k = ell; pl.p = 0; pl.q = 0; pl.ell = ell; pl.ta = ta; pl.prec = prec;
@@ -775,6 +817,7 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
     pl.ldn = round_up(n, 64);
     pl.tcomp = pl.tensor ? (prec == CORUTV_P_BF16 ? T_BF16 : T_F32) : (prec == CORUTV_P_F64 ? T_F64 : T_F32);
     pl.tdproj = pl.tcomp;
+    pl.tp = T_F64;
     pl.sp_ax = gemm_simt_splits(m, n, ctx->num_sms);
     pl.sp_aty = gemm_simt_splits(n, m, ctx->num_sms);
     pl.sp_w = pl.sp_ax;
@@ -799,8 +842,8 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
     b.part = cv.take<char>(pl.part_elems * 8);
     b.abf = prec == CORUTV_P_BF16 ? cv.take<char>(m * round_up(n, 8) * 2) : nullptr;
     float* a32 = tf32_copy ? cv.take<float>(m * round_up(n, 4)) : nullptr;
-    CK(launch_rowmajor_to_panel(X, ldx, xrows, ell, pl.ellp, xp, ldxp, ctx->stream));
-    CK(launch_panel_convert(xp, ldxp, xrows, pl.ellp, xc, pl.tcomp, ldxp, nullptr, ctx->stream));
+    CK(launch_rowmajor_to_panel(X, ldx, xrows, ell, pl.ellp, xp, T_F64, ldxp, ctx->stream));
+    CK(launch_panel_convert(xp, T_F64, ldxp, xrows, pl.ellp, xc, pl.tcomp, ldxp, nullptr, ctx->stream));
     Exec ex{ctx->stream, ctx->flags, nullptr, ctx->num_sms};
     if (pl.tensor) {
         const void* aop = A;
@@ -814,7 +857,7 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
             aop = a32;
             lda_op = round_up(n, 4);
         }
-        CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, trans, xc, ldxp, ell, pl.ellp, b.part, cp, ldcp,
+        CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, trans, xc, ldxp, ell, pl.ellp, b.part, cp, T_F64, ldcp,
                             ctx->num_sms, ctx->flags, nullptr, ctx->stream));
     } else {
         CKS(sketch_simt(ex, pl, b, trans ? A_COLS : A_ROWS, A, ta, xc, pl.tcomp, cp, ldcp));
@@ -855,14 +898,15 @@ corutv_status corutv_orth(corutv_ctx* ctx, const double* C, int64_t rows, int64_
     b.g = cv.take<double>(ell * ell);
     b.r = cv.take<double>(ell * ell);
     b.skip = cv.take<int>(8);
-    CK(launch_rowmajor_to_panel(C, ldc, rows, ell, ell, cp, pl.ldm, ctx->stream));
+    CK(launch_rowmajor_to_panel(C, ldc, rows, ell, ell, cp, T_F64, pl.ldm, ctx->stream));
     Exec ex{ctx->stream, ctx->flags, nullptr, ctx->num_sms};
     pl.torth = T_F64;
+    pl.tp = T_F64;
     CKS(orth(ex, pl, b, cp, pl.ldm, rows, qp, nullptr, T_F64, 2));
     CK(launch_panel_to_rowmajor(qp, pl.ldm, rows, ell, Q, T_F64, ldq, nullptr, ctx->stream));
     if (R) {
         // R of C = Q R: R = Q^T C (exact in exact arithmetic; upper triangular)
-        CKS(gram(ex, pl, b, qp, pl.ldm, cp, pl.ldm, rows, b.g, nullptr));
+        CKS(gram(ex, pl, b, qp, pl.ldm, cp, pl.ldm, rows, b.g, nullptr, T_F64));
         CK(cudaMemcpyAsync(R, b.g, sizeof(double) * ell * ell, cudaMemcpyDeviceToDevice, ctx->stream));
     }
     return CORUTV_OK;
@@ -890,21 +934,23 @@ namespace {
 corutv_status normest(corutv_ctx* ctx, const FactorPlan& pl, const FactorBufs& b, const void* mat,
                       ElemType tm, int64_t ldm_user, double* out_norm2) {
     const int64_t m = pl.m, n = pl.n;
-    double* v = b.x;    // n x 1 panel
-    double* u = b.c1;   // m x 1 panel
-    double* w = b.c2;   // n x 1 panel
-    double* lam = b.g;  // scalar
+    // FP64 vectors carved from the panel buffers (each holds at least ell >= 2
+    // panel columns, i.e. >= 2 x rows x 4 bytes)
+    double* v = static_cast<double*>(b.x);    // n
+    double* u = static_cast<double*>(b.c1);   // m
+    double* w = static_cast<double*>(b.c2);   // n
+    double* lam = b.g;                        // scalar
     CK(launch_vec_fill(v, n, 1.0 / std::sqrt((double)n), ctx->stream));
     const int spm = gemm_simt_splits(m, n, ctx->num_sms), spn = gemm_simt_splits(n, m, ctx->num_sms);
     for (int it = 0; it < 50; ++it) {
         GemmArgs g1{A_ROWS, B_PANEL, O_PANEL, tm, T_F64, mat, ldm_user, v, pl.ldn, b.part, pl.ldm, pl.ldm,
                     m, n, 1, spm, nullptr};
         CK(launch_gemm_simt(g1, ctx->stream));
-        CK(launch_reduce_splits(b.part, T_F64, spm, pl.ldm, u, pl.ldm, m, 1, pl.ldm, nullptr, ctx->stream));
+        CK(launch_reduce_splits(b.part, T_F64, spm, pl.ldm, u, T_F64, pl.ldm, m, 1, pl.ldm, nullptr, ctx->stream));
         GemmArgs g2{A_COLS, B_PANEL, O_PANEL, tm, T_F64, mat, ldm_user, u, pl.ldm, b.part, pl.ldn, pl.ldn,
                     n, m, 1, spn, nullptr};
         CK(launch_gemm_simt(g2, ctx->stream));
-        CK(launch_reduce_splits(b.part, T_F64, spn, pl.ldn, w, pl.ldn, n, 1, pl.ldn, nullptr, ctx->stream));
+        CK(launch_reduce_splits(b.part, T_F64, spn, pl.ldn, w, T_F64, pl.ldn, n, 1, pl.ldn, nullptr, ctx->stream));
         CK(launch_vec_normalize(w, v, n, lam, ctx->stream));
     }
     double h = 0.0;
@@ -999,11 +1045,11 @@ extern "C" corutv_status corutv_rpca(corutv_ctx* ctx, corutv_dtype dtype, const 
     for (int j = 0; j < max_iter; ++j) {
         // L_{j+1} = C_{1/mu_j}(B_j): CoR-UTV of B_j with ell = 2k, q = 1, fresh Psi
         CKS(run_factor(ex, pl, b, bmat, nullptr, opts->seed, opts->stream + (uint32_t)j + 1u));
-        GemmArgs gu{A_PANEL, B_SMALL, O_PANEL, T_F64, T_F64, b.q1, pl.ldm, b.qt, pl.ell, b.upanel, pl.ldm, 0,
+        GemmArgs gu{A_PANEL, B_SMALL, O_PANEL, pl.tp, T_F64, b.q1, pl.ldm, b.qt, pl.ell, b.upanel, pl.ldm, 0,
                     m, pl.ell, pl.ell, 1, done};
         CK(launch_gemm_simt(gu, ctx->stream));
-        CK(launch_rpca_rank_z(b.rt, b.q2, pl.ldn, b.perm, n, pl.ell, 1.0 / mus[j], rank_dev, b.zpanel, pl.ldn,
-                              done, ctx->stream));
+        CK(launch_rpca_rank_z(b.rt, b.q2, pl.tp, pl.ldn, b.perm, n, pl.ell, 1.0 / mus[j], rank_dev, b.zpanel,
+                              pl.ldn, done, ctx->stream));
         RpcaIterArgs ua{m_dev, tm, ldm_dev, m, n,
                         static_cast<float*>(s_dev), static_cast<float*>(y), static_cast<float*>(bmat),
                         static_cast<double*>(s_dev), static_cast<double*>(y), static_cast<double*>(bmat),

@@ -83,22 +83,21 @@ int gemm_simt_splits(int64_t R, int64_t K, int num_sms);
 
 // out[e] = sum_{s < splits} part[s * stride + e] over a rows x cols region
 // with leading dimension ld (panel: rows = R, cols = L; small: rows = L).
-cudaError_t launch_reduce_splits(const void* part, ElemType tpart, int splits, int64_t stride,
-                                 double* out, int64_t ld, int64_t rows, int64_t cols, int64_t ld_out,
+cudaError_t launch_reduce_splits(const void* part, ElemType tpart, int splits, int64_t stride, void* out,
+                                 ElemType tout, int64_t ld, int64_t rows, int64_t cols, int64_t ld_out,
                                  const int* cancel, cudaStream_t st);
 
 cudaError_t launch_gaussian_panel(uint64_t seed, uint32_t stream_id, int64_t n, int64_t ell,
-                                  int64_t ellp, double* x, int64_t ldx, const int* cancel,
+                                  int64_t ellp, void* x, ElemType tx, int64_t ldx, const int* cancel,
                                   cudaStream_t st);
 cudaError_t launch_gaussian_rowmajor(uint64_t seed, uint32_t stream_id, int64_t n, int64_t ell,
                                      double* psi, int64_t ld, cudaStream_t st);
 
 // Layout / type conversions.
 cudaError_t launch_rowmajor_to_panel(const double* src, int64_t lds, int64_t rows, int64_t cols,
-                                     int64_t colsp, double* dst, int64_t ldd, cudaStream_t st);
-cudaError_t launch_panel_convert(const double* src, int64_t lds, int64_t rows, int64_t cols,
-                                 void* dst, ElemType tdst, int64_t ldd, const int* cancel,
-                                 cudaStream_t st);
+                                     int64_t colsp, void* dst, ElemType tdst, int64_t ldd, cudaStream_t st);
+cudaError_t launch_panel_convert(const void* src, ElemType tsrc, int64_t lds, int64_t rows, int64_t cols,
+                                 void* dst, ElemType tdst, int64_t ldd, const int* cancel, cudaStream_t st);
 cudaError_t launch_panel_to_rowmajor(const double* src, int64_t lds, int64_t rows, int64_t cols,
                                      void* dst, ElemType tdst, int64_t ldd, const int* cancel,
                                      cudaStream_t st);
@@ -110,15 +109,16 @@ cudaError_t launch_panel_to_rowmajor(const double* src, int64_t lds, int64_t row
 cudaError_t launch_cholesky(const double* g, int64_t ell, int64_t rows, double* r, int* flags,
                             int* skip_out, const int* cancel, cudaStream_t st);
 // Q = C R^{-1} row by row (forward substitution with R^T), compute type tc;
-// writes the FP64 panel q and, if qc != nullptr, a copy of type tqc.
-cudaError_t launch_trsm_rows(const double* c, int64_t ldc, int64_t rows, int64_t ell,
-                             const double* r, ElemType tc, double* q, int64_t ldq, void* qc,
+// c and q are panels of type tp; if qc != nullptr a copy of type tqc is
+// written too.
+cudaError_t launch_trsm_rows(const void* c, ElemType tp, int64_t ldc, int64_t rows, int64_t ell,
+                             const double* r, ElemType tc, void* q, int64_t ldq, void* qc,
                              ElemType tqc, int64_t ldqc, const int* cancel, cudaStream_t st);
 // Column-pivoted QR of the small ell x ell FP64 matrix d (eq. 8), one block.
 cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, int* perm,
                         const int* cancel, cudaStream_t st);
-// V[i][j] = Q2[perm[j]] (row-major output of type tv), T = Rt (type tt).
-cudaError_t launch_gather_v(const double* q2, int64_t ldq2, int64_t n, int64_t ell, const int* perm,
+// V[i][j] = Q2[perm[j]] (Q2 a panel of type tq2; row-major output of type tv).
+cudaError_t launch_gather_v(const void* q2, ElemType tq2, int64_t ldq2, int64_t n, int64_t ell, const int* perm,
                             void* v, ElemType tv, int64_t ldv, const int* cancel, cudaStream_t st);
 cudaError_t launch_copy_small(const double* src, int64_t ell, void* dst, ElemType tdst,
                               const int* cancel, cudaStream_t st);
@@ -140,7 +140,7 @@ struct RpcaIterArgs {
 cudaError_t launch_rpca_init(const void* m, ElemType tm, int64_t ldm, int64_t rows, int64_t cols,
                              float* s, float* y, float* b, double* s64, double* y64, double* b64,
                              double* fro_part, int* nparts, cudaStream_t st);
-cudaError_t launch_rpca_rank_z(const double* rt, const double* vq2, int64_t ldv, const int* perm,
+cudaError_t launch_rpca_rank_z(const double* rt, const void* vq2, ElemType tq2, int64_t ldv, const int* perm,
                                int64_t cols, int64_t ell, double inv_mu, int* rank, double* z,
                                int64_t ldz, const int* cancel, cudaStream_t st);
 cudaError_t launch_rpca_update(const RpcaIterArgs& a, int* nparts, cudaStream_t st);

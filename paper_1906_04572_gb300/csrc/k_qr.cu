@@ -56,22 +56,34 @@ __device__ __forceinline__ double rcp_nr(double x) {
 constexpr int kCholThreads = 128;  // one warp per SM sub-partition (each has its own FP64 unit)
 
 // Right-looking Cholesky, upper factor, R^T R = G (+ shift I), one column at
-// a time: every warp derives 1/r_jj itself (no extra barrier), row j is
-// scaled, then the trailing upper triangle takes the rank-1 update with
-// rows spread over the four warps and columns over the lanes.
+// a time, with a one-step lookahead. The upper triangle is enumerated row by
+// row from the bottom row up, columns right to left (table `tri`), so the
+// trailing triangle of step j (rows > j) is a contiguous prefix of length
+// (ell-j-1)(ell-j)/2 whose last entry is the next pivot (j+1, j+1). Step j:
+// all threads scale row j by 1/r_jj (computed one step earlier); then warp 0
+// forms the next pivot d = G'(j+1,j+1) - r(j,j+1)^2, checks it and computes
+// 1/sqrt(d), while warps 1-3 apply the rank-1 update to the rest of the
+// prefix with every lane busy.
 // rows = number of rows of the matrix whose Gram is factorised (for the shift).
 __global__ void __launch_bounds__(kCholThreads)
 cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, int* skip_out,
                 const int* cancel) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int nwarps = kCholThreads / 32;
     if (cancel && *cancel) {
         if (skip_out && tid == 0) *skip_out = 1;
         return;
     }
-    extern __shared__ double S[];  // ell x (ell + 1), upper triangle used
+    extern __shared__ double S[];  // ell x (ell + 1) doubles, then the uint16 table
     const int ld = ell + 1;
-    __shared__ double trace;
+    unsigned short* tri = reinterpret_cast<unsigned short*>(S + (size_t)ell * ld);
+    __shared__ double trace, ynext;
+    __shared__ int fail_s;
+    // table: bottom-up rows; row a holds columns ell-1 .. a
+    for (int a = ell - 1 - tid; a >= 0; a -= kCholThreads) {
+        const int rb = ell - 1 - a;            // rows below the top of the enumeration
+        int e = rb * (rb + 1) / 2;
+        for (int c = ell - 1; c >= a; --c) tri[e++] = (unsigned short)((a << 8) | c);
+    }
     int attempt = 0;
     bool fail = false;
     for (; attempt < 3; ++attempt) {
@@ -92,23 +104,39 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
             const int a = e / ell, b = e % ell;
             S[a * ld + b] = g[a * ell + b] + (a == b ? shift : 0.0);
         }
+        if (tid == 0) {
+            const double d0 = g[0] + shift;
+            fail_s = !(d0 > 0.0) || !isfinite(d0);
+            ynext = fail_s ? 0.0 : rsqrt_nr(d0);
+        }
         __syncthreads();
-        fail = false;
-        for (int j = 0; j < ell; ++j) {
-            const double d = S[j * ld + j];  // same value in every thread
-            if (!(d > 0.0) || !isfinite(d)) {
-                fail = true;
-                break;
-            }
-            const double y = rsqrt_nr(d);  // 1 / r_jj
+        fail = fail_s != 0;
+        for (int j = 0; j < ell && !fail; ++j) {
+            const double y = ynext;  // 1 / r_jj
             for (int c = j + 1 + tid; c < ell; c += kCholThreads) S[j * ld + c] *= y;
+            if (tid == 0) S[j * ld + j] *= y;  // d_jj / sqrt(d_jj) = r_jj
             __syncthreads();
-            if (tid == 0) S[j * ld + j] = d * y;
-            for (int a = j + 1 + warp; a < ell; a += nwarps) {
-                const double sja = S[j * ld + a];
-                for (int c = a + lane; c < ell; c += 32) S[a * ld + c] -= sja * S[j * ld + c];
+            if (j + 1 < ell) {
+                if (warp == 0) {
+                    if (lane == 0) {
+                        const double s = S[j * ld + j + 1];
+                        const double d = fma(-s, s, S[(j + 1) * ld + j + 1]);
+                        S[(j + 1) * ld + j + 1] = d;
+                        const bool bad = !(d > 0.0) || !isfinite(d);
+                        if (bad) fail_s = 1;
+                        else ynext = rsqrt_nr(d);
+                    }
+                } else {
+                    const int len = (ell - j - 1) * (ell - j) / 2 - 1;  // prefix without (j+1, j+1)
+                    for (int e = tid - 32; e < len; e += kCholThreads - 32) {
+                        const int ac = tri[e];
+                        const int a = ac >> 8, c = ac & 0xff;
+                        S[a * ld + c] = fma(-S[j * ld + a], S[j * ld + c], S[a * ld + c]);
+                    }
+                }
             }
             __syncthreads();
+            fail = fail_s != 0;
         }
         if (!fail) break;
         __syncthreads();
@@ -128,9 +156,9 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
 }
 
 // Row i of Q solves q_i R = c_i (R upper): q_i[j] = (c_i[j] - sum_{t<j} q_i[t] R[t][j]) / R[j][j].
-template <typename TC, typename TQC>
-__global__ void trsm_rows_kernel(const double* c, int64_t ldc, int64_t rows, int ell, const double* r,
-                                 double* q, int64_t ldq, TQC* qc, int64_t ldqc, const int* cancel) {
+template <typename TI, typename TC, typename TQC>
+__global__ void trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* r,
+                                 TI* q, int64_t ldq, TQC* qc, int64_t ldqc, const int* cancel) {
     if (cancel && *cancel) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC* Rs = reinterpret_cast<TC*>(smem_raw);   // ell x ell row-major
@@ -157,7 +185,7 @@ __global__ void trsm_rows_kernel(const double* c, int64_t ldc, int64_t rows, int
     }
     for (int j = 0; j < ell; ++j) {
         const TC v = Ts[j * nthr + tid];
-        q[j * ldq + i] = (double)v;
+        q[j * ldq + i] = (TI)v;
         if (qc) qc[j * ldqc + i] = (TQC)v;
     }
 }
@@ -176,24 +204,37 @@ int trsm_threads(int ell, int64_t rows) {
     return (int)per;
 }
 
-template <typename TC, typename TQC>
-cudaError_t trsm_launch(const double* c, int64_t ldc, int64_t rows, int ell, const double* r,
-                        double* q, int64_t ldq, TQC* qc, int64_t ldqc, const int* cancel,
-                        cudaStream_t st) {
+template <typename TI, typename TC, typename TQC>
+cudaError_t trsm_launch(const void* c, int64_t ldc, int64_t rows, int ell, const double* r, void* q, int64_t ldq,
+                        void* qc, int64_t ldqc, const int* cancel, cudaStream_t st) {
     const int nthr = trsm_threads<TC>(ell, rows);
     const size_t smem = sizeof(TC) * ((size_t)ell * ell + (size_t)ell * nthr + (size_t)ell);
-    cudaError_t e = cudaFuncSetAttribute(trsm_rows_kernel<TC, TQC>,
+    cudaError_t e = cudaFuncSetAttribute(trsm_rows_kernel<TI, TC, TQC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((rows + nthr - 1) / nthr);
     count_launch();
-    trsm_rows_kernel<TC, TQC><<<blocks, nthr, smem, st>>>(c, ldc, rows, ell, r, q, ldq, qc, ldqc, cancel);
+    trsm_rows_kernel<TI, TC, TQC><<<blocks, nthr, smem, st>>>(static_cast<const TI*>(c), ldc, rows, ell, r,
+                                                              static_cast<TI*>(q), ldq, static_cast<TQC*>(qc),
+                                                              ldqc, cancel);
     return cudaGetLastError();
+}
+
+template <typename TI, typename TC>
+cudaError_t trsm_dispatch(const void* c, int64_t ldc, int64_t rows, int ell, const double* r, void* q,
+                          int64_t ldq, void* qc, ElemType tqc, int64_t ldqc, const int* cancel, cudaStream_t st) {
+    if (!qc) return trsm_launch<TI, TC, TI>(c, ldc, rows, ell, r, q, ldq, nullptr, 0, cancel, st);
+    switch (tqc) {
+        case T_F64: return trsm_launch<TI, TC, double>(c, ldc, rows, ell, r, q, ldq, qc, ldqc, cancel, st);
+        case T_F32: return trsm_launch<TI, TC, float>(c, ldc, rows, ell, r, q, ldq, qc, ldqc, cancel, st);
+        case T_BF16: return trsm_launch<TI, TC, __nv_bfloat16>(c, ldc, rows, ell, r, q, ldq, qc, ldqc, cancel, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // QRCP of the small D (eq. 8), one block of four warps (one per SM
-// sub-partition, each with its own FP64 unit). W is column-major in shared
+// sub-partition, each sub-partition with its own FP64 unit). W is column-major in shared
 // memory (column c at W + c * ldw, ldw odd so that lanes owning consecutive
 // columns hit distinct banks). Column-wise work (squared norms, reflector
 // dot products and updates) is split as lanes = columns, warps = quarters of
@@ -201,11 +242,11 @@ cudaError_t trsm_launch(const double* c, int64_t ldc, int64_t rows, int ell, con
 // Pivot choice compares the non-negative squared norms through their bit
 // patterns (same order as the values), lowest index on ties.
 // ---------------------------------------------------------------------------
-constexpr int kQrcpThreads = 128;
+constexpr int kQrcpThreads = 128;  // one warp per sub-partition (a second one per sub-partition measured slower)
 constexpr int kQrcpWarps = kQrcpThreads / 32;
 
-// rows [lo, hi) of the active range [j, ell) owned by warp w
-__device__ __forceinline__ void quarter(int j, int ell, int w, int& lo, int& hi) {
+// rows [lo, hi) of the active range [j, ell) owned by warp w (one of kQrcpWarps shares)
+__device__ __forceinline__ void row_share(int j, int ell, int w, int& lo, int& hi) {
     const int n = ell - j;
     const int qn = (n + kQrcpWarps - 1) / kQrcpWarps;
     lo = j + w * qn;
@@ -218,20 +259,22 @@ __device__ void apply_reflector(double* W, int ldw, double* part, int j, int c0,
                                 int warp) {
     const double* v = W + j * ldw;
     int lo, hi;
-    quarter(j, ell, warp, lo, hi);
+    row_share(j, ell, warp, lo, hi);
     for (int cb = c0; cb < ell; cb += 32) {
         const int c = cb + lane;
         if (c < ell) {
             const double* x = W + c * ldw;
-            double s0 = 0.0, s1 = 0.0;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
             int i = lo;
             if (i == j && i < hi) { s0 = x[j]; ++i; }  // v[j] = 1
-            for (; i + 1 < hi; i += 2) {
+            for (; i + 3 < hi; i += 4) {
                 s0 += v[i] * x[i];
                 s1 += v[i + 1] * x[i + 1];
+                s2 += v[i + 2] * x[i + 2];
+                s3 += v[i + 3] * x[i + 3];
             }
-            if (i < hi) s0 += v[i] * x[i];
-            part[warp * 128 + (c - cb)] = s0 + s1;
+            for (; i < hi; ++i) s0 += v[i] * x[i];
+            part[warp * 128 + (c - cb)] = (s0 + s1) + (s2 + s3);
         }
         __syncthreads();
         if (c < ell) {
@@ -267,24 +310,26 @@ qrcp_kernel(const double* d, int ell, double* qt, double* rt, int* perm, const i
     __syncthreads();
     for (int j = 0; j < ell; ++j) {
         int lo, hi;
-        quarter(j, ell, warp, lo, hi);
+        row_share(j, ell, warp, lo, hi);
         // 1. recomputed squared residual norms of columns j..ell-1
         for (int cb = j; cb < ell; cb += 32) {
             const int c = cb + lane;
             if (c < ell) {
                 const double* x = W + c * ldw;
-                double s0 = 0.0, s1 = 0.0;
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
                 int i = lo;
-                for (; i + 1 < hi; i += 2) {
+                for (; i + 3 < hi; i += 4) {
                     s0 += x[i] * x[i];
                     s1 += x[i + 1] * x[i + 1];
+                    s2 += x[i + 2] * x[i + 2];
+                    s3 += x[i + 3] * x[i + 3];
                 }
-                if (i < hi) s0 += x[i] * x[i];
-                part[warp * 128 + (c - j)] = s0 + s1;
+                for (; i < hi; ++i) s0 += x[i] * x[i];
+                part[warp * 128 + (c - j)] = (s0 + s1) + (s2 + s3);
             }
         }
         __syncthreads();
-        // 2. pivot: warp 0 adds the quarters (warp order) and takes the argmax
+        // 2. pivot: warp 0 adds the shares (warp order) and takes the argmax
         if (warp == 0) {
             long long best = -1;
             int bi = ell;
@@ -375,8 +420,8 @@ qrcp_kernel(const double* d, int ell, double* qt, double* rt, int* perm, const i
     }
 }
 
-template <typename TV>
-__global__ void gather_v_kernel(const double* q2, int64_t ldq2, int64_t n, int ell, const int* perm,
+template <typename TQ, typename TV>
+__global__ void gather_v_kernel(const TQ* q2, int64_t ldq2, int64_t n, int ell, const int* perm,
                                 TV* v, int64_t ldv, const int* cancel) {
     if (cancel && *cancel) return;
     __shared__ double tile[128][33];
@@ -385,7 +430,7 @@ __global__ void gather_v_kernel(const double* q2, int64_t ldq2, int64_t n, int e
     for (int e = tid; e < ell * 32; e += blockDim.x) {
         const int j = e / 32, ii = e % 32;
         const int64_t i = i0 + ii;
-        tile[j][ii] = (i < n) ? q2[(int64_t)perm[j] * ldq2 + i] : 0.0;
+        tile[j][ii] = (i < n) ? (double)q2[(int64_t)perm[j] * ldq2 + i] : 0.0;
     }
     __syncthreads();
     for (int e = tid; e < ell * 32; e += blockDim.x) {
@@ -406,7 +451,7 @@ __global__ void copy_small_kernel(const double* src, int n, TD* dst, const int* 
 
 cudaError_t launch_cholesky(const double* g, int64_t ell, int64_t rows, double* r, int* flags,
                                int* skip_out, const int* cancel, cudaStream_t st) {
-    const size_t smem = sizeof(double) * (size_t)ell * (ell + 1);
+    const size_t smem = sizeof(double) * (size_t)ell * (ell + 1) + sizeof(unsigned short) * (size_t)ell * (ell + 1) / 2;
     cudaError_t e = cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -415,32 +460,19 @@ cudaError_t launch_cholesky(const double* g, int64_t ell, int64_t rows, double* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_trsm_rows(const double* c, int64_t ldc, int64_t rows, int64_t ell,
-                             const double* r, ElemType tc, double* q, int64_t ldq, void* qc,
+cudaError_t launch_trsm_rows(const void* c, ElemType tp, int64_t ldc, int64_t rows, int64_t ell,
+                             const double* r, ElemType tc, void* q, int64_t ldq, void* qc,
                              ElemType tqc, int64_t ldqc, const int* cancel, cudaStream_t st) {
-    if (tc == T_F64) {
-        if (!qc || tqc == T_F64)
-            return trsm_launch<double, double>(c, ldc, rows, (int)ell, r, q, ldq, static_cast<double*>(qc),
-                                               ldqc, cancel, st);
-        if (tqc == T_F32)
-            return trsm_launch<double, float>(c, ldc, rows, (int)ell, r, q, ldq, static_cast<float*>(qc),
-                                              ldqc, cancel, st);
-        return trsm_launch<double, __nv_bfloat16>(c, ldc, rows, (int)ell, r, q, ldq,
-                                                  static_cast<__nv_bfloat16*>(qc), ldqc, cancel, st);
-    }
-    if (!qc || tqc == T_F32)
-        return trsm_launch<float, float>(c, ldc, rows, (int)ell, r, q, ldq, static_cast<float*>(qc), ldqc,
-                                         cancel, st);
-    if (tqc == T_F64)
-        return trsm_launch<float, double>(c, ldc, rows, (int)ell, r, q, ldq, static_cast<double*>(qc),
-                                          ldqc, cancel, st);
-    return trsm_launch<float, __nv_bfloat16>(c, ldc, rows, (int)ell, r, q, ldq,
-                                             static_cast<__nv_bfloat16*>(qc), ldqc, cancel, st);
+    const int l = (int)ell;
+    if (tp == T_F64 && tc == T_F64) return trsm_dispatch<double, double>(c, ldc, rows, l, r, q, ldq, qc, tqc, ldqc, cancel, st);
+    if (tp == T_F64 && tc == T_F32) return trsm_dispatch<double, float>(c, ldc, rows, l, r, q, ldq, qc, tqc, ldqc, cancel, st);
+    if (tp == T_F32 && tc == T_F32) return trsm_dispatch<float, float>(c, ldc, rows, l, r, q, ldq, qc, tqc, ldqc, cancel, st);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, int* perm,
                         const int* cancel, cudaStream_t st) {
-    const size_t smem = sizeof(double) * ((size_t)ell * (ell | 1) + 4 * 128 + 3 * (size_t)ell) + sizeof(int) * ell;
+    const size_t smem = sizeof(double) * ((size_t)ell * (ell | 1) + kQrcpWarps * 128 + 3 * (size_t)ell) + sizeof(int) * ell;
     cudaError_t e = cudaFuncSetAttribute(qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launch();
@@ -448,18 +480,22 @@ cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_v(const double* q2, int64_t ldq2, int64_t n, int64_t ell, const int* perm,
+cudaError_t launch_gather_v(const void* q2, ElemType tq2, int64_t ldq2, int64_t n, int64_t ell, const int* perm,
                             void* v, ElemType tv, int64_t ldv, const int* cancel, cudaStream_t st) {
     const unsigned blocks = (unsigned)((n + 31) / 32);
-    if (tv == T_F64) {
-        count_launch();
-        gather_v_kernel<double><<<blocks, 256, 0, st>>>(q2, ldq2, n, (int)ell, perm, static_cast<double*>(v),
-                                                        ldv, cancel);
-    } else {
-        count_launch();
-        gather_v_kernel<float><<<blocks, 256, 0, st>>>(q2, ldq2, n, (int)ell, perm, static_cast<float*>(v),
-                                                       ldv, cancel);
-    }
+    count_launch();
+    if (tq2 == T_F64 && tv == T_F64)
+        gather_v_kernel<double, double><<<blocks, 256, 0, st>>>(static_cast<const double*>(q2), ldq2, n, (int)ell,
+                                                                perm, static_cast<double*>(v), ldv, cancel);
+    else if (tq2 == T_F64)
+        gather_v_kernel<double, float><<<blocks, 256, 0, st>>>(static_cast<const double*>(q2), ldq2, n, (int)ell,
+                                                               perm, static_cast<float*>(v), ldv, cancel);
+    else if (tv == T_F64)
+        gather_v_kernel<float, double><<<blocks, 256, 0, st>>>(static_cast<const float*>(q2), ldq2, n, (int)ell,
+                                                               perm, static_cast<double*>(v), ldv, cancel);
+    else
+        gather_v_kernel<float, float><<<blocks, 256, 0, st>>>(static_cast<const float*>(q2), ldq2, n, (int)ell,
+                                                              perm, static_cast<float*>(v), ldv, cancel);
     return cudaGetLastError();
 }
 

@@ -61,7 +61,8 @@ __global__ void rpca_init_kernel(const TM* m, int64_t ldm, int64_t rows, int64_t
 }
 
 // r = #{i : Rt_ii > inv_mu}; Z[i][s] = sum_h Q2[i][perm[h]] Rt[s][h] for s < r.
-__global__ void rank_z_kernel(const double* rt, const double* q2, int64_t ldq2, const int* perm,
+template <typename TQ>
+__global__ void rank_z_kernel(const double* rt, const TQ* q2, int64_t ldq2, const int* perm,
                               int64_t cols, int ell, double inv_mu, int* rank, double* z, int64_t ldz,
                               const int* cancel) {
     if (cancel && *cancel) return;
@@ -83,7 +84,7 @@ __global__ void rank_z_kernel(const double* rt, const double* q2, int64_t ldq2, 
     if (i >= cols) return;
     double v[kMaxEll];
 #pragma unroll 4
-    for (int h = 0; h < ell; ++h) v[h] = q2[(int64_t)ps[h] * ldq2 + i];
+    for (int h = 0; h < ell; ++h) v[h] = (double)q2[(int64_t)ps[h] * ldq2 + i];
     for (int s = 0; s < ell; ++s) {
         double acc = 0.0;
         if (s < r)
@@ -249,13 +250,18 @@ cudaError_t launch_rpca_init(const void* m, ElemType tm, int64_t ldm, int64_t ro
     return cudaGetLastError();
 }
 
-cudaError_t launch_rpca_rank_z(const double* rt, const double* vq2, int64_t ldv, const int* perm,
+cudaError_t launch_rpca_rank_z(const double* rt, const void* vq2, ElemType tq2, int64_t ldv, const int* perm,
                                int64_t cols, int64_t ell, double inv_mu, int* rank, double* z,
                                int64_t ldz, const int* cancel, cudaStream_t st) {
     if (ell > kMaxEll) return cudaErrorInvalidValue;
     const unsigned blocks = (unsigned)((cols + 127) / 128);
     count_launch();
-    rank_z_kernel<<<blocks, 128, 0, st>>>(rt, vq2, ldv, perm, cols, (int)ell, inv_mu, rank, z, ldz, cancel);
+    if (tq2 == T_F64)
+        rank_z_kernel<double><<<blocks, 128, 0, st>>>(rt, static_cast<const double*>(vq2), ldv, perm, cols, (int)ell,
+                                                      inv_mu, rank, z, ldz, cancel);
+    else
+        rank_z_kernel<float><<<blocks, 128, 0, st>>>(rt, static_cast<const float*>(vq2), ldv, perm, cols, (int)ell,
+                                                     inv_mu, rank, z, ldz, cancel);
     return cudaGetLastError();
 }
 

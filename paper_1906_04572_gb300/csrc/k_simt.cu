@@ -188,9 +188,9 @@ namespace {
 // eight group sums are then added in group order. The summation order depends
 // only on the split count, so results are reproducible.
 constexpr int kRedGroups = 8;
-template <typename TP>
+template <typename TP, typename TO>
 __global__ void __launch_bounds__(32 * kRedGroups)
-reduce_splits_kernel(const TP* part, int splits, int64_t stride, double* out, int64_t ld, int64_t rows,
+reduce_splits_kernel(const TP* part, int splits, int64_t stride, TO* out, int64_t ld, int64_t rows,
                      int64_t cols, int64_t ld_out, const int* cancel) {
     if (cancel && *cancel) return;
     __shared__ double red[kRedGroups][33];
@@ -218,27 +218,31 @@ reduce_splits_kernel(const TP* part, int splits, int64_t stride, double* out, in
         double t = red[0][tx];
         for (int k = 1; k < kRedGroups; ++k) t += red[k][tx];
         const int64_t y = e / rows, x = e % rows;
-        out[y * ld_out + x] = t;
+        out[y * ld_out + x] = (TO)t;
     }
+}
+
+template <typename TP, typename TO>
+cudaError_t reduce_launch(const void* part, int splits, int64_t stride, void* out, int64_t ld, int64_t rows,
+                          int64_t cols, int64_t ld_out, const int* cancel, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((rows * cols + 31) / 32);
+    count_launch();
+    reduce_splits_kernel<TP, TO><<<blocks, 32 * kRedGroups, 0, st>>>(static_cast<const TP*>(part), splits, stride,
+                                                                     static_cast<TO*>(out), ld, rows, cols, ld_out,
+                                                                     cancel);
+    return cudaGetLastError();
 }
 }  // namespace
 
-cudaError_t launch_reduce_splits(const void* part, ElemType tpart, int splits, int64_t stride,
-                                 double* out, int64_t ld, int64_t rows, int64_t cols, int64_t ld_out,
+cudaError_t launch_reduce_splits(const void* part, ElemType tpart, int splits, int64_t stride, void* out,
+                                 ElemType tout, int64_t ld, int64_t rows, int64_t cols, int64_t ld_out,
                                  const int* cancel, cudaStream_t st) {
-    const int64_t total = rows * cols;
-    if (total <= 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((total + 31) / 32);
-    if (tpart == T_F64) {
-        count_launch();
-        reduce_splits_kernel<double><<<blocks, 32 * kRedGroups, 0, st>>>(static_cast<const double*>(part), splits,
-                                                                         stride, out, ld, rows, cols, ld_out, cancel);
-    } else {
-        count_launch();
-        reduce_splits_kernel<float><<<blocks, 32 * kRedGroups, 0, st>>>(static_cast<const float*>(part), splits,
-                                                                        stride, out, ld, rows, cols, ld_out, cancel);
-    }
-    return cudaGetLastError();
+    if (rows * cols <= 0) return cudaSuccess;
+    if (tpart == T_F64 && tout == T_F64) return reduce_launch<double, double>(part, splits, stride, out, ld, rows, cols, ld_out, cancel, st);
+    if (tpart == T_F32 && tout == T_F64) return reduce_launch<float, double>(part, splits, stride, out, ld, rows, cols, ld_out, cancel, st);
+    if (tpart == T_F32 && tout == T_F32) return reduce_launch<float, float>(part, splits, stride, out, ld, rows, cols, ld_out, cancel, st);
+    if (tpart == T_F64 && tout == T_F32) return reduce_launch<double, float>(part, splits, stride, out, ld, rows, cols, ld_out, cancel, st);
+    return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------
@@ -275,14 +279,15 @@ __device__ __forceinline__ double gauss_at(uint64_t seed, uint32_t sid, uint32_t
     return sqrt(-2.0 * log(u1)) * cos(6.283185307179586476925286766559 * u2);
 }
 
+template <typename TX>
 __global__ void gaussian_panel_kernel(uint64_t seed, uint32_t sid, int64_t n, int64_t ell,
-                                      int64_t ellp, double* x, int64_t ldx, const int* cancel) {
+                                      int64_t ellp, TX* x, int64_t ldx, const int* cancel) {
     if (cancel && *cancel) return;
     const int64_t total = n * ellp;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = e / n, i = e % n;
-        x[j * ldx + i] = (j < ell) ? gauss_at(seed, sid, (uint32_t)i, (uint32_t)j) : 0.0;
+        x[j * ldx + i] = (TX)((j < ell) ? gauss_at(seed, sid, (uint32_t)i, (uint32_t)j) : 0.0);
     }
 }
 
@@ -305,11 +310,15 @@ int grid_for(int64_t total) {
 }  // namespace
 
 cudaError_t launch_gaussian_panel(uint64_t seed, uint32_t stream_id, int64_t n, int64_t ell,
-                                  int64_t ellp, double* x, int64_t ldx, const int* cancel,
+                                  int64_t ellp, void* x, ElemType tx, int64_t ldx, const int* cancel,
                                   cudaStream_t st) {
     count_launch();
-    gaussian_panel_kernel<<<grid_for(n * ellp), 256, 0, st>>>(seed, stream_id, n, ell, ellp, x, ldx,
-                                                              cancel);
+    if (tx == T_F64)
+        gaussian_panel_kernel<double><<<grid_for(n * ellp), 256, 0, st>>>(seed, stream_id, n, ell, ellp,
+                                                                          static_cast<double*>(x), ldx, cancel);
+    else
+        gaussian_panel_kernel<float><<<grid_for(n * ellp), 256, 0, st>>>(seed, stream_id, n, ell, ellp,
+                                                                         static_cast<float*>(x), ldx, cancel);
     return cudaGetLastError();
 }
 
@@ -359,8 +368,8 @@ __global__ void transpose_kernel(const double* src, int64_t lds, int64_t rows, i
     }
 }
 
-template <typename TD>
-__global__ void panel_convert_kernel(const double* src, int64_t lds, int64_t rows, int64_t cols,
+template <typename TS, typename TD>
+__global__ void panel_convert_kernel(const TS* src, int64_t lds, int64_t rows, int64_t cols,
                                      TD* dst, int64_t ldd, const int* cancel) {
     if (cancel && *cancel) return;
     const int64_t total = rows * cols;
@@ -373,11 +382,15 @@ __global__ void panel_convert_kernel(const double* src, int64_t lds, int64_t row
 }  // namespace
 
 cudaError_t launch_rowmajor_to_panel(const double* src, int64_t lds, int64_t rows, int64_t cols,
-                                     int64_t colsp, double* dst, int64_t ldd, cudaStream_t st) {
+                                     int64_t colsp, void* dst, ElemType tdst, int64_t ldd, cudaStream_t st) {
     dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((colsp + 31) / 32));
     count_launch();
-    transpose_kernel<double><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, cols, colsp, dst, ldd, true,
-                                                           nullptr);
+    if (tdst == T_F64)
+        transpose_kernel<double><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, cols, colsp, static_cast<double*>(dst),
+                                                               ldd, true, nullptr);
+    else
+        transpose_kernel<float><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, cols, colsp, static_cast<float*>(dst),
+                                                              ldd, true, nullptr);
     return cudaGetLastError();
 }
 
@@ -399,30 +412,37 @@ cudaError_t launch_panel_to_rowmajor(const double* src, int64_t lds, int64_t row
     return cudaGetLastError();
 }
 
-cudaError_t launch_panel_convert(const double* src, int64_t lds, int64_t rows, int64_t cols,
-                                 void* dst, ElemType tdst, int64_t ldd, const int* cancel,
-                                 cudaStream_t st) {
+template <typename TS>
+cudaError_t panel_convert_from(const TS* src, int64_t lds, int64_t rows, int64_t cols, void* dst, ElemType tdst,
+                               int64_t ldd, const int* cancel, cudaStream_t st) {
     const int blocks = grid_for(rows * cols);
+    count_launch();
     switch (tdst) {
         case T_F64:
-            count_launch();
-            panel_convert_kernel<double><<<blocks, 256, 0, st>>>(src, lds, rows, cols,
-                                                                 static_cast<double*>(dst), ldd, cancel);
+            panel_convert_kernel<TS, double><<<blocks, 256, 0, st>>>(src, lds, rows, cols, static_cast<double*>(dst),
+                                                                     ldd, cancel);
             break;
         case T_F32:
-            count_launch();
-            panel_convert_kernel<float><<<blocks, 256, 0, st>>>(src, lds, rows, cols,
-                                                                static_cast<float*>(dst), ldd, cancel);
+            panel_convert_kernel<TS, float><<<blocks, 256, 0, st>>>(src, lds, rows, cols, static_cast<float*>(dst),
+                                                                    ldd, cancel);
             break;
         case T_BF16:
-            count_launch();
-            panel_convert_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(
+            panel_convert_kernel<TS, __nv_bfloat16><<<blocks, 256, 0, st>>>(
                 src, lds, rows, cols, static_cast<__nv_bfloat16*>(dst), ldd, cancel);
             break;
         default:
             return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_panel_convert(const void* src, ElemType tsrc, int64_t lds, int64_t rows, int64_t cols,
+                                 void* dst, ElemType tdst, int64_t ldd, const int* cancel, cudaStream_t st) {
+    if (tsrc == T_F64)
+        return panel_convert_from(static_cast<const double*>(src), lds, rows, cols, dst, tdst, ldd, cancel, st);
+    if (tsrc == T_F32)
+        return panel_convert_from(static_cast<const float*>(src), lds, rows, cols, dst, tdst, ldd, cancel, st);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace corutv

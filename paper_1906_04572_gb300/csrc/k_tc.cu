@@ -47,19 +47,27 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 struct TcParams {
     long long units;      // mtiles * kchunks
-    long long kchunks;
+    long long kchunks;    // K chunks per tile (kseg segments of kc_seg chunks)
+    int kc_seg;           // K chunks per segment
+    int seg_stride;       // A column offset between K segments (elements)
     int grid;             // G
     int maxp;             // partial pieces per tile
-    int ellp;
+    int ellp;             // output columns per tile
+    int nparts;           // B column groups added in the epilogue (1, or 3 for split products)
     int trans;
     int tf32;
     int stages;
     int a_boxes;          // TMA boxes per A tile (MN-major needs several)
     int a_box_cols;       // columns (MN elements) per A box
+    int b_boxes;          // TMA boxes per B tile
+    int b_box_rows;       // rows per B box
     uint32_t a_bytes;     // A tile bytes per stage
     uint32_t stage_bytes; // A + B bytes per stage
-    uint32_t idesc;
-    uint32_t tmem_cols;   // columns allocated (two accumulators)
+    uint32_t idesc0, idesc1;  // MMA N chunks: n0 columns, then n1 (0 = none)
+    int n0, n1;
+    int nacc;             // accumulators in tensor memory (2 = epilogue overlaps the next segment)
+    uint32_t acc_cols;    // tensor-memory columns per accumulator
+    uint32_t tmem_cols;   // columns allocated
     int kchunk_elems;     // K elements per chunk (64 bf16 / 32 fp32)
     float* part;
     int* flags;
@@ -251,16 +259,18 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                 uint8_t* sa = smem + (size_t)s * p.stage_bytes;
                 uint8_t* sb = sa + p.a_bytes;
                 mbar_expect_tx(&full_bar[s], p.stage_bytes);
-                const int kx = (int)(kc * p.kchunk_elems);
+                const int seg = kc / p.kc_seg, kk = kc - seg * p.kc_seg;
+                const int kx = kk * p.kchunk_elems;
                 if (!p.trans) {
-                    tma_load_2d(sa, &map_a, &full_bar[s], kx, (int)(t * kTileM));
+                    tma_load_2d(sa, &map_a, &full_bar[s], seg * p.seg_stride + kx, (int)(t * kTileM));
                 } else {
                     const uint32_t box_bytes = p.a_bytes / p.a_boxes;
                     for (int bx = 0; bx < p.a_boxes; ++bx)
                         tma_load_2d(sa + bx * box_bytes, &map_a, &full_bar[s], (int)(t * kTileM + bx * p.a_box_cols),
                                     kx);
                 }
-                tma_load_2d(sb, &map_b, &full_bar[s], kx, 0);
+                for (int bx = 0; bx < p.b_boxes; ++bx)
+                    tma_load_2d(sb + bx * p.b_box_rows * 128, &map_b, &full_bar[s], kx, bx * p.b_box_rows);
                 if (++s == S) { s = 0; ++r; }
                 if (++kc == KC) { kc = 0; ++t; }
             }
@@ -280,13 +290,13 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
             for (int u = u0; u < u1 && !abort_s; ++seg) {
                 const int t = u / KC;
                 const int seg_end = (u1 < (t + 1) * KC) ? u1 : (t + 1) * KC;
-                const int a = seg & 1;
-                if (seg >= 2 && !mbar_wait(&acce_bar[a], (uint32_t)(((seg >> 1) - 1) & 1), &abort_s)) {
+                const int a = seg % p.nacc, use = seg / p.nacc;
+                if (use >= 1 && !mbar_wait(&acce_bar[a], (uint32_t)((use - 1) & 1), &abort_s)) {
                     abort_s = 1;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t tacc = tmem_base + (uint32_t)(a * (p.tmem_cols / 2));
+                const uint32_t tacc = tmem_base + (uint32_t)a * p.acc_cols;
                 bool first = true;
                 for (; u < seg_end; ++u, ++li) {
                     if (!mbar_wait(&full_bar[s], (uint32_t)(r & 1), &abort_s)) {
@@ -312,8 +322,13 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                         }
                         bdesc = smem_desc(sb + kk * kstep_bytes, 16, 1024, 2);
                         const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-                        if (p.tf32) mma_tf32(tacc, adesc, bdesc, p.idesc, acc);
-                        else mma_f16(tacc, adesc, bdesc, p.idesc, acc);
+                        if (p.tf32) mma_tf32(tacc, adesc, bdesc, p.idesc0, acc);
+                        else mma_f16(tacc, adesc, bdesc, p.idesc0, acc);
+                        if (p.n1) {  // second N chunk: B rows n0.., accumulator columns n0..
+                            const uint64_t bdesc1 = smem_desc(sb + p.n0 * 128 + kk * kstep_bytes, 16, 1024, 2);
+                            if (p.tf32) mma_tf32(tacc + (uint32_t)p.n0, adesc, bdesc1, p.idesc1, acc);
+                            else mma_f16(tacc + (uint32_t)p.n0, adesc, bdesc1, p.idesc1, acc);
+                        }
                     }
                     first = false;
                     mma_commit(&empty_bar[s]);
@@ -334,18 +349,24 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
         for (int u = u0; u < u1; ++seg) {
             const int t = u / KC;
             const int seg_end = (u1 < (t + 1) * KC) ? u1 : (t + 1) * KC;
-            const int a = seg & 1;
-            if (!mbar_wait(&accf_bar[a], (uint32_t)((seg >> 1) & 1), &abort_s)) {
+            const int a = seg % p.nacc;
+            if (!mbar_wait(&accf_bar[a], (uint32_t)((seg / p.nacc) & 1), &abort_s)) {
                 abort_s = 1;
                 break;
             }
             tc_fence_after();
             const long long piece = c - unit_owner((long long)t * KC, p.units, p.grid);
             float* dst = p.part + (((long long)t * p.maxp + piece) * p.ellp) * (long long)kTileM + row;
-            const uint32_t tacc = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * (p.tmem_cols / 2));
+            const uint32_t tacc = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)a * p.acc_cols;
             for (int c0 = 0; c0 < p.ellp; c0 += 16) {
                 float v[16];
                 tmem_ld16(tacc + (uint32_t)c0, v);
+                for (int x = 1; x < p.nparts; ++x) {  // column groups of a split product, added in order
+                    float w[16];
+                    tmem_ld16(tacc + (uint32_t)(x * p.ellp + c0), w);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += w[i];
+                }
 #pragma unroll
                 for (int i = 0; i < 16; ++i) dst[(long long)(c0 + i) * kTileM] = v[i];
             }
@@ -365,8 +386,9 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
 }
 
 // C[j * ldc + t * 128 + r] = sum over the pieces of tile t, in order.
+template <typename TO>
 __global__ void streamk_reduce_kernel(const float* part, long long mtiles, long long kc, long long units,
-                                      long long grid, int maxp, int ellp, int ell, long long mtot, double* c,
+                                      long long grid, int maxp, int ellp, int ell, long long mtot, TO* c,
                                       long long ldc, const int* cancel) {
     if (cancel && *cancel) return;
     const long long total = mtiles * kTileM * (long long)ell;
@@ -379,7 +401,7 @@ __global__ void streamk_reduce_kernel(const float* part, long long mtiles, long 
         const long long np = unit_owner((t + 1) * kc - 1, units, grid) - unit_owner(t * kc, units, grid) + 1;
         double s = 0.0;
         for (long long pc = 0; pc < np; ++pc) s += (double)part[((t * maxp + pc) * ellp + j) * kTileM + r];
-        c[j * ldc + rr] = s;
+        c[j * ldc + rr] = (TO)s;
     }
 }
 
@@ -433,6 +455,60 @@ __global__ void copy_f32_padded_kernel(const float* a, long long m, long long n,
     }
 }
 
+// Exact three-way bf16 split of an FP32 value: a = h + m + l with h = bf16(a),
+// m = bf16(a - h), l = bf16(a - h - m); each difference is exact in FP32 and
+// the last one has at most 8 significant bits, so l is exact too (for
+// operands and parts in the normal range).
+__device__ __forceinline__ void split3(float a, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+    h = __float2bfloat16_rn(a);
+    const float r1 = a - __bfloat162float(h);
+    m = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(m);
+    l = __float2bfloat16_rn(r2);
+}
+
+// Rows of [A_h | A_m | A_l], each segment `seg` (multiple of 64) wide, zero
+// beyond column n. One block per row at a time, 4 columns per thread.
+__global__ void cast_bf16_split_kernel(const float* a, long long m, long long n, long long lda, __nv_bfloat16* out,
+                                       long long seg, const int* cancel) {
+    if (cancel && *cancel) return;
+    for (long long i = blockIdx.x; i < m; i += gridDim.x) {
+        const float* src = a + i * lda;
+        __nv_bfloat16* dst = out + i * 3 * seg;
+        const bool vec = (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+        for (long long j = 4LL * threadIdx.x; j < seg; j += 4LL * blockDim.x) {
+            float v[4];
+            if (vec && j + 3 < n) {
+                const float4 f = *reinterpret_cast<const float4*>(src + j);
+                v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+            } else {
+                for (int q = 0; q < 4; ++q) v[q] = (j + q < n) ? src[j + q] : 0.f;
+            }
+            __nv_bfloat16 h[4], md[4], lo[4];
+            for (int q = 0; q < 4; ++q) split3(v[q], h[q], md[q], lo[q]);
+            *reinterpret_cast<uint2*>(dst + j) = *reinterpret_cast<const uint2*>(h);
+            *reinterpret_cast<uint2*>(dst + seg + j) = *reinterpret_cast<const uint2*>(md);
+            *reinterpret_cast<uint2*>(dst + 2 * seg + j) = *reinterpret_cast<const uint2*>(lo);
+        }
+    }
+}
+
+// q3 column x * ellp + j = part x of panel column j (zero for ell <= j < ellp).
+__global__ void split_panel_kernel(const float* q, long long ldq, long long rows, int ell, int ellp,
+                                   __nv_bfloat16* q3, long long ldq3, const int* cancel) {
+    if (cancel && *cancel) return;
+    const long long total = rows * ellp;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long j = e / rows, i = e % rows;
+        __nv_bfloat16 h, md, lo;
+        split3(j < ell ? q[j * ldq + i] : 0.f, h, md, lo);
+        q3[j * ldq3 + i] = h;
+        q3[(ellp + j) * ldq3 + i] = md;
+        q3[(2 * ellp + j) * ldq3 + i] = lo;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -474,13 +550,14 @@ struct Plan {
     int grid, maxp;
 };
 
-Plan make_plan(long long m, long long n, int trans, bool tf32, int num_sms) {
+// kseg K segments of ktot_seg elements each (split products use 3).
+Plan make_plan(long long mtot, long long ktot_seg, int kseg, bool tf32, int num_sms) {
     Plan pl;
-    pl.mtot = trans ? n : m;
-    pl.ktot = trans ? m : n;
+    pl.mtot = mtot;
+    pl.ktot = ktot_seg;
     const int ke = tf32 ? 32 : 64;
     pl.mtiles = (pl.mtot + kTileM - 1) / kTileM;
-    pl.kc = (pl.ktot + ke - 1) / ke;
+    pl.kc = kseg * ((ktot_seg + ke - 1) / ke);
     pl.units = pl.mtiles * pl.kc;
     pl.grid = (int)std::min<long long>(num_sms, pl.units);
     pl.maxp = 1;
@@ -502,67 +579,58 @@ uint32_t make_idesc(bool tf32, bool a_mn_major, int n) {
     return d;
 }
 
-}  // namespace
-
-int64_t tc_partial_elems(int64_t m, int64_t n, int64_t ellp, int64_t ldm, int64_t ldn, int num_sms) {
-    (void)ldm;
-    (void)ldn;
-    int64_t best = 0;
-    for (int trans = 0; trans < 2; ++trans)
-        for (int tf = 0; tf < 2; ++tf) {
-            const Plan pl = make_plan(m, n, trans, tf != 0, num_sms);
-            best = std::max<int64_t>(best, pl.mtiles * pl.maxp * ellp * kTileM);
-        }
-    return best;
-}
-
-cudaError_t launch_sketch_tc(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, int trans,
-                             const void* x, int64_t ldx, int64_t ell, int64_t ellp, void* part, double* c,
-                             int64_t ldc, int num_sms, int* flags, const int* cancel, cudaStream_t st) {
-    if (ta != T_BF16 && ta != T_F32) return cudaErrorInvalidValue;
-    if (ellp % 16 != 0 || ellp < 16 || ellp > 128 || ell > ellp) return cudaErrorInvalidValue;
-    // The MN-major tf32 operand form (A^T Y in TF32) is not enabled.
-    if (ta == T_F32 && trans) return cudaErrorNotSupported;
-    cudaError_t e = get_encoder();
-    if (e != cudaSuccess) return e;
-    const bool tf32 = ta == T_F32;
-    const Plan pl = make_plan(m, n, trans, tf32, num_sms);
+// Shared launcher. A: rows x cols row-major (K-major for trans = 0, MN-major
+// for trans = 1) with `kseg` K segments `seg_stride` columns apart; B: panel
+// with nparts * ellp rows of the K-major operand (ldb); output: the panel c
+// (ell columns, type tcout) = sum over the nparts column groups.
+cudaError_t tc_launch(const void* a, bool tf32, long long mtot, long long ktot_seg, int kseg, long long seg_stride,
+                      const CUtensorMap& map_a, int a_boxes, int a_box_cols, const void* b, long long ldb,
+                      long long brows_k, int nparts, int trans, int64_t ell, int64_t ellp, void* part, void* c,
+                      ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel, cudaStream_t st) {
+    const Plan pl = make_plan(mtot, ktot_seg, kseg, tf32, num_sms);
     const int ke = tf32 ? 32 : 64;  // K elements per 128-byte row
-    CUtensorMap map_a, map_b;
+    const int nb = nparts * (int)ellp;
     TcParams p{};
     p.units = pl.units;
     p.kchunks = pl.kc;
+    p.kc_seg = (int)(pl.kc / kseg);
+    p.seg_stride = (int)seg_stride;
     p.grid = pl.grid;
     p.maxp = pl.maxp;
     p.ellp = (int)ellp;
+    p.nparts = nparts;
     p.trans = trans;
     p.tf32 = tf32 ? 1 : 0;
     p.kchunk_elems = ke;
     p.part = static_cast<float*>(part);
     p.flags = flags;
     p.cancel = cancel;
-    if (!trans) {
-        e = encode_2d(&map_a, a, tf32, n, m, lda, (uint32_t)ke, kTileM, CU_TENSOR_MAP_SWIZZLE_128B);
-        p.a_boxes = 1;
-        p.a_box_cols = 0;
+    p.a_boxes = a_boxes;
+    p.a_box_cols = a_box_cols;
+    p.b_boxes = nb > 256 ? 2 : 1;
+    p.b_box_rows = nb / p.b_boxes;
+    CUtensorMap map_b;
+    cudaError_t e = encode_2d(&map_b, b, tf32, brows_k, nb, ldb, (uint32_t)ke, (uint32_t)p.b_box_rows,
+                              CU_TENSOR_MAP_SWIZZLE_128B);
+    if (e != cudaSuccess) return e;
+    // MMA N chunks: one if nb <= 256, else two multiples of 16
+    if (nb <= 256) {
+        p.n0 = nb;
+        p.n1 = 0;
     } else {
-        // MN-major A: boxes of one 128-byte MN atom (64 bf16 / 32 fp32 columns) by ke rows
-        const int atom = tf32 ? 32 : 64;
-        e = encode_2d(&map_a, a, tf32, n, m, lda, (uint32_t)atom, (uint32_t)ke,
-                      tf32 ? CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B : CU_TENSOR_MAP_SWIZZLE_128B);
-        p.a_boxes = kTileM / atom;
-        p.a_box_cols = atom;
+        p.n0 = (nb / 2 + 15) / 16 * 16;
+        p.n1 = nb - p.n0;
     }
-    if (e != cudaSuccess) return e;
-    e = encode_2d(&map_b, x, tf32, trans ? m : n, ellp, ldx, (uint32_t)ke, (uint32_t)ellp, CU_TENSOR_MAP_SWIZZLE_128B);
-    if (e != cudaSuccess) return e;
+    p.idesc0 = make_idesc(tf32, trans != 0, p.n0);
+    p.idesc1 = p.n1 ? make_idesc(tf32, trans != 0, p.n1) : 0;
     p.a_bytes = kTileM * 128;
-    p.stage_bytes = p.a_bytes + (uint32_t)ellp * 128;
+    p.stage_bytes = p.a_bytes + (uint32_t)nb * 128;
     p.stages = std::min<int>(kMaxStages, (int)((200 * 1024) / p.stage_bytes));
     uint32_t cols = 32;
-    while (cols < (uint32_t)ellp) cols <<= 1;
-    p.tmem_cols = 2 * cols;
-    p.idesc = make_idesc(tf32, trans != 0, (int)ellp);
+    while (cols < (uint32_t)nb) cols <<= 1;
+    p.nacc = (2 * cols <= 512) ? 2 : 1;
+    p.acc_cols = cols;
+    p.tmem_cols = p.nacc * cols;
     const size_t smem = (size_t)p.stages * p.stage_bytes + 1024;
     e = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -573,9 +641,71 @@ cudaError_t launch_sketch_tc(const void* a, ElemType ta, int64_t m, int64_t n, i
     const long long total = pl.mtiles * kTileM * ell;
     const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
     count_launch();
-    streamk_reduce_kernel<<<blocks, 256, 0, st>>>(p.part, pl.mtiles, pl.kc, pl.units, pl.grid, pl.maxp, (int)ellp,
-                                                  (int)ell, pl.mtot, c, ldc, cancel);
+    if (tcout == T_F64)
+        streamk_reduce_kernel<double><<<blocks, 256, 0, st>>>(p.part, pl.mtiles, pl.kc, pl.units, pl.grid, pl.maxp,
+                                                              (int)ellp, (int)ell, pl.mtot, static_cast<double*>(c),
+                                                              ldc, cancel);
+    else
+        streamk_reduce_kernel<float><<<blocks, 256, 0, st>>>(p.part, pl.mtiles, pl.kc, pl.units, pl.grid, pl.maxp,
+                                                             (int)ellp, (int)ell, pl.mtot, static_cast<float*>(c),
+                                                             ldc, cancel);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+int64_t tc_partial_elems(int64_t m, int64_t n, int64_t ellp, int64_t ldm, int64_t ldn, int num_sms) {
+    (void)ldm;
+    (void)ldn;
+    int64_t best = 0;
+    for (int trans = 0; trans < 2; ++trans)
+        for (int tf = 0; tf < 2; ++tf)
+            for (int kseg : {1, 3}) {
+                const Plan pl = make_plan(trans ? n : m, trans ? m : n, kseg, tf != 0, num_sms);
+                best = std::max<int64_t>(best, pl.mtiles * pl.maxp * ellp * kTileM);
+            }
+    return best;
+}
+
+cudaError_t launch_sketch_tc(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, int trans,
+                             const void* x, int64_t ldx, int64_t ell, int64_t ellp, void* part, void* c,
+                             ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel,
+                             cudaStream_t st) {
+    if (ta != T_BF16 && ta != T_F32) return cudaErrorInvalidValue;
+    if (ellp % 16 != 0 || ellp < 16 || ellp > 128 || ell > ellp) return cudaErrorInvalidValue;
+    // The MN-major tf32 operand form (A^T Y in TF32) is not enabled.
+    if (ta == T_F32 && trans) return cudaErrorNotSupported;
+    cudaError_t e = get_encoder();
+    if (e != cudaSuccess) return e;
+    const bool tf32 = ta == T_F32;
+    const int ke = tf32 ? 32 : 64;
+    CUtensorMap map_a;
+    int a_boxes = 1, a_box_cols = 0;
+    if (!trans) {
+        e = encode_2d(&map_a, a, tf32, n, m, lda, (uint32_t)ke, kTileM, CU_TENSOR_MAP_SWIZZLE_128B);
+    } else {
+        // MN-major A: boxes of one 128-byte MN atom (64 bf16 columns) by ke rows
+        const int atom = 64;
+        e = encode_2d(&map_a, a, false, n, m, lda, (uint32_t)atom, (uint32_t)ke, CU_TENSOR_MAP_SWIZZLE_128B);
+        a_boxes = kTileM / atom;
+        a_box_cols = atom;
+    }
+    if (e != cudaSuccess) return e;
+    return tc_launch(a, tf32, trans ? n : m, trans ? m : n, 1, 0, map_a, a_boxes, a_box_cols, x, ldx, trans ? m : n,
+                     1, trans, ell, ellp, part, c, tcout, ldc, num_sms, flags, cancel, st);
+}
+
+cudaError_t launch_project_split_tc(const void* a3, int64_t m, int64_t n, int64_t seg, const void* q3, int64_t ldq,
+                                    int64_t ell, int64_t ellp, void* part, void* w, ElemType tw, int64_t ldw,
+                                    int num_sms, int* flags, const int* cancel, cudaStream_t st) {
+    if (ellp % 16 != 0 || ellp < 16 || ellp > 128 || ell > ellp || seg % 64 != 0) return cudaErrorInvalidValue;
+    cudaError_t e = get_encoder();
+    if (e != cudaSuccess) return e;
+    CUtensorMap map_a;
+    e = encode_2d(&map_a, a3, false, 3 * seg, m, 3 * seg, 64u, kTileM, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (e != cudaSuccess) return e;
+    return tc_launch(a3, false, m, n, 3, seg, map_a, 1, 0, q3, ldq, n, 3, 0, ell, ellp, part, w, tw, ldw, num_sms,
+                     flags, cancel, st);
 }
 
 bool tma_rows_aligned(const void* a, int64_t lda, int elem_bytes) {
@@ -588,6 +718,25 @@ cudaError_t launch_copy_f32_padded(const float* a, int64_t m, int64_t n, int64_t
     const int blocks = (int)std::min<long long>((total + 255) / 256, 8192);
     count_launch();
     copy_f32_padded_kernel<<<blocks, 256, 0, st>>>(a, m, n, lda, out, ldb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cast_bf16_split(const float* a, int64_t m, int64_t n, int64_t lda, void* a3, int64_t seg,
+                                   const int* cancel, cudaStream_t st) {
+    if (seg % 64 != 0 || seg < n) return cudaErrorInvalidValue;
+    const int blocks = (int)std::min<long long>(m, 16LL * 152);
+    count_launch();
+    cast_bf16_split_kernel<<<blocks, 256, 0, st>>>(a, m, n, lda, static_cast<__nv_bfloat16*>(a3), seg, cancel);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_panel(const float* q, int64_t ldq, int64_t rows, int64_t ell, int64_t ellp, void* q3,
+                               int64_t ldq3, const int* cancel, cudaStream_t st) {
+    const long long total = rows * ellp;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+    count_launch();
+    split_panel_kernel<<<blocks, 256, 0, st>>>(q, ldq, rows, (int)ell, (int)ellp, static_cast<__nv_bfloat16*>(q3),
+                                               ldq3, cancel);
     return cudaGetLastError();
 }
 

@@ -119,26 +119,26 @@ extern "C" corutv_status corutv_orth_noalloc(const double* C, int64_t rows, int6
                     ell, rows, ell, gs, cancel};
         cudaError_t ee = launch_gemm_simt(ga, st);
         if (ee != cudaSuccess) return ee;
-        return launch_reduce_splits(gpart, T_F64, gs, ll, g, ell, ell, ell, ell, cancel, st);
+        return launch_reduce_splits(gpart, T_F64, gs, ll, g, T_F64, ell, ell, ell, ell, cancel, st);
     };
 #define NA_CK(expr)                                                                       \
     do {                                                                                  \
         cudaError_t ee_ = (expr);                                                         \
         if (ee_ != cudaSuccess) return noalloc_fail(CORUTV_ECUDA, #expr " failed", ee_);  \
     } while (0)
-    NA_CK(launch_rowmajor_to_panel(C, ldc, rows, ell, ell, cp, ld, st));
+    NA_CK(launch_rowmajor_to_panel(C, ldc, rows, ell, ell, cp, T_F64, ld, st));
     // pass 1 (shifted when the Gram is not numerically positive definite)
     NA_CK(gram(cp, cp, nullptr));
     NA_CK(launch_cholesky(g, ell, rows, r, flags, skip, nullptr, st));
-    NA_CK(launch_trsm_rows(cp, ld, rows, ell, r, T_F64, tp, ld, nullptr, T_F64, 0, nullptr, st));
+    NA_CK(launch_trsm_rows(cp, T_F64, ld, rows, ell, r, T_F64, tp, ld, nullptr, T_F64, 0, nullptr, st));
     // pass 1b, only after a shifted pass 1
     NA_CK(gram(tp, tp, skip));
     NA_CK(launch_cholesky(g, ell, rows, r, flags, nullptr, skip, st));
-    NA_CK(launch_trsm_rows(tp, ld, rows, ell, r, T_F64, tp, ld, nullptr, T_F64, 0, skip, st));
+    NA_CK(launch_trsm_rows(tp, T_F64, ld, rows, ell, r, T_F64, tp, ld, nullptr, T_F64, 0, skip, st));
     // pass 2
     NA_CK(gram(tp, tp, nullptr));
     NA_CK(launch_cholesky(g, ell, rows, r, flags, nullptr, nullptr, st));
-    NA_CK(launch_trsm_rows(tp, ld, rows, ell, r, T_F64, qp, ld, nullptr, T_F64, 0, nullptr, st));
+    NA_CK(launch_trsm_rows(tp, T_F64, ld, rows, ell, r, T_F64, qp, ld, nullptr, T_F64, 0, nullptr, st));
     NA_CK(launch_panel_to_rowmajor(qp, ld, rows, ell, Q, T_F64, ldq, nullptr, st));
     if (R) {
         // R = Q^T C, upper triangular in exact arithmetic

@@ -17,10 +17,12 @@ int64_t tc_partial_elems(int64_t m, int64_t n, int64_t ellp, int64_t ldm, int64_
 // (T_BF16 -> kind::f16 with bf16 operands; T_F32 -> kind::tf32), row stride
 // lda (lda * elem_size a multiple of 16 bytes). X: panel of the same element
 // type with ellp columns (padding columns zero), ld ldx. FP32 accumulation;
-// C is written as FP64. `part` holds split partials.
+// C is written with element type tcout (FP64 or FP32). `part` holds split
+// partials.
 cudaError_t launch_sketch_tc(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, int trans,
-                             const void* x, int64_t ldx, int64_t ell, int64_t ellp, void* part, double* c,
-                             int64_t ldc, int num_sms, int* flags, const int* cancel, cudaStream_t st);
+                             const void* x, int64_t ldx, int64_t ell, int64_t ellp, void* part, void* c,
+                             ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel,
+                             cudaStream_t st);
 
 // abf[i * ldb + j] = bf16(A[i * lda + j]) (round to nearest even); columns
 // [n, ldb) are zero.
@@ -34,5 +36,21 @@ bool tma_rows_aligned(const void* a, int64_t lda, int elem_bytes);
 // out[i * ldb + j] = A[i * lda + j] for j < n, 0 for n <= j < ldb.
 cudaError_t launch_copy_f32_padded(const float* a, int64_t m, int64_t n, int64_t lda, float* out, int64_t ldb,
                                    cudaStream_t st);
+
+// FP32-accurate W = A Q on the tensor cores by exact three-way bf16 splits:
+// a3 holds rows [A_h | A_m | A_l] (each segment `seg` elements, seg a multiple
+// of 64, zero beyond n), q3 is a bf16 panel of 3 * ellp columns
+// [Q_h | Q_m | Q_l] (ld ldq). Products of bf16 parts are exact and
+// accumulate in FP32, so W = sum of the nine part products carries the
+// rounding of an FP32 dot product. W: panel (ell columns, type tw, ld ldw).
+cudaError_t launch_project_split_tc(const void* a3, int64_t m, int64_t n, int64_t seg, const void* q3, int64_t ldq,
+                                    int64_t ell, int64_t ellp, void* part, void* w, ElemType tw, int64_t ldw,
+                                    int num_sms, int* flags, const int* cancel, cudaStream_t st);
+// Writes a3 (rows of [A_h | A_m | A_l]) from FP32 A.
+cudaError_t launch_cast_bf16_split(const float* a, int64_t m, int64_t n, int64_t lda, void* a3, int64_t seg,
+                                   const int* cancel, cudaStream_t st);
+// Writes q3 = [Q_h | Q_m | Q_l] from an FP32 panel (ell valid columns of ellp).
+cudaError_t launch_split_panel(const float* q, int64_t ldq, int64_t rows, int64_t ell, int64_t ellp, void* q3,
+                               int64_t ldq3, const int* cancel, cudaStream_t st);
 
 }  // namespace corutv

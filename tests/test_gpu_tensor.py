@@ -92,6 +92,24 @@ def test_sketch_tf32_within_bound(ctx, m, n, ell):
     assert np.all(np.abs(host(c) - ref) <= bound)
 
 
+@pytest.mark.parametrize("m,n,ell", [(1000, 700, 60), (333, 1021, 110), (4100, 130, 16), (256, 64, 128)])
+def test_sketch_bf16x3_has_fp32_accuracy(ctx, m, n, ell):
+    """A X from exact three-way bf16 splits of A and X on the tensor cores:
+    within the rounding bound of an FP32 dot product (the SIMT FP32 bound)."""
+    rng = np.random.default_rng(m * 3 + n + ell)
+    a32 = rng.standard_normal((m, n)).astype(np.float32)
+    x = rng.standard_normal((n, ell))
+    c = torch.empty((m, ell), dtype=torch.float64, device="cuda")
+    corutv.corutv_sketch(ctx.handle, dev(a32, torch.float32), dev(x), c, 0, "bf16x3")
+    assert ctx.sync() == 0
+    a64 = a32.astype(np.float64)
+    x32 = x.astype(np.float32).astype(np.float64)
+    ref = oracle.gemm_ax(a64, x32)
+    bound = 2 * n * U32 * (np.abs(a64) @ np.abs(x32))
+    err = np.abs(host(c) - ref)
+    assert np.all(err <= bound), float((err / bound).max())
+
+
 def test_sketch_tf32_transposed_is_refused(ctx):
     a = dev(np.ones((64, 48), np.float32), torch.float32)
     c = torch.empty((48, 16), dtype=torch.float64, device="cuda")
