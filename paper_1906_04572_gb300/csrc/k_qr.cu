@@ -156,6 +156,11 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
 }
 
 // Row i of Q solves q_i R = c_i (R upper): q_i[j] = (c_i[j] - sum_{t<j} q_i[t] R[t][j]) / R[j][j].
+// Columns are solved in blocks of kTrsmB: the contributions of the columns
+// already solved go into kTrsmB independent accumulators (one shared load of
+// q_i[t] feeds all of them), then the small triangle inside the block is
+// finished in order. Row i is held in shared memory (one thread per row).
+constexpr int kTrsmB = 8;
 template <typename TI, typename TC, typename TQC>
 __global__ void trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* r,
                                  TI* q, int64_t ldq, TQC* qc, int64_t ldqc, const int* cancel) {
@@ -167,21 +172,35 @@ __global__ void trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell
     TC* Rd = Ts + (size_t)ell * nthr;             // 1 / R[j][j]
     const int tid = threadIdx.x;
     for (int e = tid; e < ell * ell; e += nthr) Rs[e] = (TC)r[e];
-    for (int j = tid; j < ell; j += nthr) Rd[j] = (TC)(1.0 / r[j * ell + j]);
+    for (int j = tid; j < ell; j += nthr) Rd[j] = (TC)1 / (TC)r[j * ell + j];
     const int64_t i = (int64_t)blockIdx.x * nthr + tid;
     if (i < rows)
         for (int j = 0; j < ell; ++j) Ts[j * nthr + tid] = (TC)c[j * ldc + i];
     __syncthreads();
     if (i >= rows) return;
-    for (int j = 0; j < ell; ++j) {
-        TC s0 = Ts[j * nthr + tid], s1 = 0;
-        int t = 0;
-        for (; t + 1 < j; t += 2) {
-            s0 -= Ts[t * nthr + tid] * Rs[t * ell + j];
-            s1 -= Ts[(t + 1) * nthr + tid] * Rs[(t + 1) * ell + j];
+    for (int j0 = 0; j0 < ell; j0 += kTrsmB) {
+        const int nb = min(kTrsmB, ell - j0);
+        TC acc[kTrsmB];
+#pragma unroll
+        for (int k = 0; k < kTrsmB; ++k) acc[k] = (k < nb) ? Ts[(j0 + k) * nthr + tid] : (TC)0;
+        for (int t = 0; t < j0; ++t) {
+            const TC qt = Ts[t * nthr + tid];
+            const TC* rrow = Rs + t * ell + j0;
+#pragma unroll
+            for (int k = 0; k < kTrsmB; ++k)
+                if (k < nb) acc[k] -= qt * rrow[k];
         }
-        if (t < j) s0 -= Ts[t * nthr + tid] * Rs[t * ell + j];
-        Ts[j * nthr + tid] = (s0 + s1) * Rd[j];
+#pragma unroll
+        for (int k = 0; k < kTrsmB; ++k) {
+            if (k >= nb) break;
+            TC s = acc[k];
+#pragma unroll
+            for (int kk = 0; kk < k; ++kk) s -= acc[kk] * Rs[(j0 + kk) * ell + j0 + k];
+            acc[k] = s * Rd[j0 + k];
+        }
+#pragma unroll
+        for (int k = 0; k < kTrsmB; ++k)
+            if (k < nb) Ts[(j0 + k) * nthr + tid] = acc[k];
     }
     for (int j = 0; j < ell; ++j) {
         const TC v = Ts[j * nthr + tid];
