@@ -43,6 +43,7 @@ namespace {
 constexpr int kThreads = 192;
 constexpr int kTileM = 128;
 constexpr int kMaxStages = 8;
+constexpr int kKSteps = 4;  // MMA K steps per 128-byte K chunk: 64 bf16 / 16, or 32 tf32 / 8
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 struct TcParams {
@@ -195,6 +196,7 @@ __host__ __device__ __forceinline__ long long unit_owner(long long u, long long 
     return ((u + 1) * grid + units - 1) / units - 1;
 }
 
+template <bool kTf32>
 __global__ void __launch_bounds__(kThreads, 1)
 sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                  const TcParams p) {
@@ -251,6 +253,8 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
             // ---------------- TMA producer ----------------
             int li = 0, s = 0, r = 0;       // unit index, stage, round (li = r S + s)
             int t = u0 / KC, kc = u0 % KC;  // tile and K chunk of unit u
+            int seg = kc / p.kc_seg, kk = kc - seg * p.kc_seg;  // K segment and chunk within it
+            const uint32_t box_bytes = p.a_bytes / p.a_boxes;
             for (int u = u0; u < u1; ++u, ++li) {
                 if (r > 0 && !mbar_wait(&empty_bar[s], (uint32_t)((r - 1) & 1), &abort_s)) {
                     abort_s = 1;
@@ -259,12 +263,10 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                 uint8_t* sa = smem + (size_t)s * p.stage_bytes;
                 uint8_t* sb = sa + p.a_bytes;
                 mbar_expect_tx(&full_bar[s], p.stage_bytes);
-                const int seg = kc / p.kc_seg, kk = kc - seg * p.kc_seg;
                 const int kx = kk * p.kchunk_elems;
                 if (!p.trans) {
                     tma_load_2d(sa, &map_a, &full_bar[s], seg * p.seg_stride + kx, (int)(t * kTileM));
                 } else {
-                    const uint32_t box_bytes = p.a_bytes / p.a_boxes;
                     for (int bx = 0; bx < p.a_boxes; ++bx)
                         tma_load_2d(sa + bx * box_bytes, &map_a, &full_bar[s], (int)(t * kTileM + bx * p.a_box_cols),
                                     kx);
@@ -272,7 +274,8 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                 for (int bx = 0; bx < p.b_boxes; ++bx)
                     tma_load_2d(sb + bx * p.b_box_rows * 128, &map_b, &full_bar[s], kx, bx * p.b_box_rows);
                 if (++s == S) { s = 0; ++r; }
-                if (++kc == KC) { kc = 0; ++t; }
+                if (++kk == p.kc_seg) { kk = 0; ++seg; }
+                if (++kc == KC) { kc = 0; ++t; seg = 0; kk = 0; }
             }
             if (abort_s) {
                 // drain: wait (bounded) for every copy that was issued but not consumed
@@ -284,9 +287,35 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
     } else if (warp == 5) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
+            // A single thread issues every MMA, so the issue loop must stay
+            // short: the shared-memory descriptors are built once, and per
+            // stage and per K step only their start-address field (bits
+            // 0-13, in 16-byte units; shared addresses stay below 256 KB so
+            // the field never carries into the next one) is advanced.
+            const uint32_t sbase = smem_u32(smem);
+            uint64_t a_desc0;
+            uint32_t a_kstep;
+            if (!p.trans) {
+                // K-major A: 128 rows x 128 B, 8-row groups 1024 B apart; a K step is 32 B along the row
+                a_desc0 = smem_desc(sbase, 16, 1024, 2);
+                a_kstep = 32u >> 4;
+            } else if (!kTf32) {
+                // MN-major A: 64-element MN atoms (a_bytes / a_boxes apart), 8-row K groups 1024 B
+                // apart; a K step of 16 consumes two K groups
+                a_desc0 = smem_desc(sbase, p.a_bytes / p.a_boxes, 1024, 2);
+                a_kstep = 2048u >> 4;
+            } else {
+                // MN-major tf32: 32-element MN atoms, a K step of 8 is one K group
+                a_desc0 = smem_desc(sbase, p.a_bytes / p.a_boxes, 1024, 1);
+                a_kstep = 1024u >> 4;
+            }
+            const uint64_t b_desc0 = smem_desc(sbase + p.a_bytes, 16, 1024, 2);
+            const uint32_t b_kstep = 32u >> 4;  // 16 bf16 or 8 tf32 elements of K
+            const uint32_t stage16 = p.stage_bytes >> 4;
+            const uint32_t n1_off = ((uint32_t)p.n0 * 128u) >> 4;
+            const uint32_t idesc0 = p.idesc0, idesc1 = p.idesc1;
+            const bool two_n = p.n1 != 0;
             int li = 0, seg = 0, s = 0, r = 0;
-            const int ksteps = p.tf32 ? p.kchunk_elems / 8 : p.kchunk_elems / 16;
-            const uint32_t kstep_bytes = 32;  // 16 bf16 or 8 tf32 elements of K
             for (int u = u0; u < u1 && !abort_s; ++seg) {
                 const int t = u / KC;
                 const int seg_end = (u1 < (t + 1) * KC) ? u1 : (t + 1) * KC;
@@ -305,29 +334,17 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                     }
                     consumed_s = li + 1;
                     tc_fence_after();
-                    const uint32_t sa = smem_u32(smem + (size_t)s * p.stage_bytes);
-                    const uint32_t sb = sa + p.a_bytes;
-                    for (int kk = 0; kk < ksteps; ++kk) {
-                        uint64_t adesc, bdesc;
-                        if (!p.trans) {
-                            // K-major A: 128 rows x 128 B, 8-row groups 1024 B apart
-                            adesc = smem_desc(sa + kk * kstep_bytes, 16, 1024, 2);
-                        } else if (!p.tf32) {
-                            // MN-major A: 64-element MN atoms (8 KB apart), 8-row K groups 1024 B apart;
-                            // one K step of 16 consumes two K groups
-                            adesc = smem_desc(sa + kk * 2048, p.a_bytes / p.a_boxes, 1024, 2);
-                        } else {
-                            // MN-major tf32: 32-element MN atoms, K step of 8 = one K group
-                            adesc = smem_desc(sa + kk * 1024, p.a_bytes / p.a_boxes, 1024, 1);
-                        }
-                        bdesc = smem_desc(sb + kk * kstep_bytes, 16, 1024, 2);
+                    const uint64_t ad = a_desc0 + (uint64_t)((uint32_t)s * stage16);
+                    const uint64_t bd = b_desc0 + (uint64_t)((uint32_t)s * stage16);
+#pragma unroll
+                    for (int kk = 0; kk < kKSteps; ++kk) {
                         const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-                        if (p.tf32) mma_tf32(tacc, adesc, bdesc, p.idesc0, acc);
-                        else mma_f16(tacc, adesc, bdesc, p.idesc0, acc);
-                        if (p.n1) {  // second N chunk: B rows n0.., accumulator columns n0..
-                            const uint64_t bdesc1 = smem_desc(sb + p.n0 * 128 + kk * kstep_bytes, 16, 1024, 2);
-                            if (p.tf32) mma_tf32(tacc + (uint32_t)p.n0, adesc, bdesc1, p.idesc1, acc);
-                            else mma_f16(tacc + (uint32_t)p.n0, adesc, bdesc1, p.idesc1, acc);
+                        const uint64_t adk = ad + (uint64_t)(kk * a_kstep), bdk = bd + (uint64_t)(kk * b_kstep);
+                        if (kTf32) mma_tf32(tacc, adk, bdk, idesc0, acc);
+                        else mma_f16(tacc, adk, bdk, idesc0, acc);
+                        if (two_n) {  // second N chunk: B rows n0.., accumulator columns n0..
+                            if (kTf32) mma_tf32(tacc + (uint32_t)p.n0, adk, bdk + n1_off, idesc1, acc);
+                            else mma_f16(tacc + (uint32_t)p.n0, adk, bdk + n1_off, idesc1, acc);
                         }
                     }
                     first = false;
@@ -632,10 +649,11 @@ cudaError_t tc_launch(const void* a, bool tf32, long long mtot, long long ktot_s
     p.acc_cols = cols;
     p.tmem_cols = p.nacc * cols;
     const size_t smem = (size_t)p.stages * p.stage_bytes + 1024;
-    e = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = tf32 ? sketch_tc_kernel<true> : sketch_tc_kernel<false>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launch();
-    sketch_tc_kernel<<<pl.grid, kThreads, smem, st>>>(map_a, map_b, p);
+    kern<<<pl.grid, kThreads, smem, st>>>(map_a, map_b, p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const long long total = pl.mtiles * kTileM * ell;
