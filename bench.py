@@ -397,7 +397,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default="f32", choices=["f32", "tf32", "bf16", "f64"])
+    ap.add_argument("--prec", default="bf16", choices=["f32", "tf32", "bf16", "f64"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -180,6 +180,7 @@ struct FactorBufs {
     void *xc, *q1c, *q2c, *part;
     void* abf;        // bf16 copy of A for CORUTV_P_BF16
     int *perm, *skip;
+    int* tcnt;        // per-tile counters of the tensor-core products
 };
 
 corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64_t lda, int64_t k,
@@ -248,6 +249,7 @@ void carve_factor(C& cv, const FactorPlan& pl, FactorBufs& b) {
     b.abf = pl.prec == CORUTV_P_BF16 ? cv.template take<char>(pl.m * (pl.split ? 3 : 1) * pl.seg * 2) : nullptr;
     b.perm = cv.template take<int>(pl.ellp);
     b.skip = cv.template take<int>(8);
+    b.tcnt = pl.tensor ? cv.template take<int>(tc_counter_elems(pl.m, pl.n)) : nullptr;
 }
 
 size_t factor_bytes(const FactorPlan& pl) {
@@ -343,6 +345,8 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     if (pl.tensor) {
         // padding columns of the bf16 / fp32 operand panels must read as zero
         CK(cudaMemsetAsync(b.q1c, 0, (size_t)pl.ellp * pl.ldm * elem_size(pl.tcomp), ex.st));
+        // the workspace is shared with other entry points: start the tile counters at zero
+        CK(cudaMemsetAsync(b.tcnt, 0, sizeof(int) * (size_t)tc_counter_elems(m, n), ex.st));
         CK(launch_panel_convert(b.x, pl.tp, pl.ldn, n, pl.ellp, b.xc, pl.tcomp, pl.ldn, ex.cancel, ex.st));
         if (pl.split)
             CK(launch_cast_bf16_split(static_cast<const float*>(a), m, n, pl.lda, b.abf, pl.seg, ex.cancel, ex.st));
@@ -359,7 +363,7 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
             const int64_t lda_op = pl.prec == CORUTV_P_BF16 ? ldabf : pl.lda;
             ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
             CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, /*trans=*/0, b.xc, pl.ldn, ell, pl.ellp, b.part,
-                                b.c1, pl.tp, pl.ldm, ex.num_sms, ex.flags, ex.cancel, ex.st));
+                                b.tcnt, b.c1, pl.tp, pl.ldm, ex.num_sms, ex.flags, ex.cancel, ex.st));
         } else {
             CKS(sketch_simt(ex, pl, b, A_ROWS, a, pl.ta, b.xc, pl.tcomp, b.c1, pl.ldm));
         }
@@ -371,7 +375,7 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
             const int64_t lda_op = pl.prec == CORUTV_P_BF16 ? ldabf : pl.lda;
             ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
             CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, /*trans=*/1, b.q1c, pl.ldm, ell, pl.ellp, b.part,
-                                b.c2, pl.tp, pl.ldn, ex.num_sms, ex.flags, ex.cancel, ex.st));
+                                b.tcnt, b.c2, pl.tp, pl.ldn, ex.num_sms, ex.flags, ex.cancel, ex.st));
         } else {
             CKS(sketch_simt(ex, pl, b, A_COLS, a, pl.ta, b.q1c, pl.tcomp, b.c2, pl.ldn));
         }
@@ -384,7 +388,8 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
         CK(launch_split_panel(static_cast<const float*>(b.q2), pl.ldn, n, ell, pl.ellp, b.q2c, pl.ldn, ex.cancel,
                               ex.st));
         ProfScope ps(ex.prof, CORUTV_STAGE_PROJECT, ex.st);
-        CK(launch_project_split_tc(b.abf, m, n, pl.seg, b.q2c, pl.ldn, ell, pl.ellp, b.part, b.w, pl.tp, pl.ldm,
+        CK(launch_project_split_tc(b.abf, m, n, pl.seg, b.q2c, pl.ldn, ell, pl.ellp, b.part, b.tcnt, b.w, pl.tp,
+                                   pl.ldm,
                                    ex.num_sms, ex.flags, ex.cancel, ex.st));
     } else {
         GemmArgs g{A_ROWS, B_PANEL, O_PANEL, pl.ta, pl.tdproj, a, pl.lda, b.q2c, pl.ldn, b.part, pl.ldm,
@@ -791,6 +796,7 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
         measure.take<double>(ellp * ldm);
         measure.take<float>(part_elems);
         measure.take<char>(m * 3 * seg * 2);
+        measure.take<int>(tc_counter_elems(m, n));
         CKS(ensure_ws(ctx, ctx->ws, measure.off, ctx->stream));
         Carver cv(ctx->ws.ptr);
         float* xp = cv.take<float>(ellp * ldn);
@@ -798,11 +804,13 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
         double* cp = cv.take<double>(ellp * ldm);
         void* part = cv.take<float>(part_elems);
         void* a3 = cv.take<char>(m * 3 * seg * 2);
+        int* tcnt = cv.take<int>(tc_counter_elems(m, n));
+        CK(cudaMemsetAsync(tcnt, 0, sizeof(int) * (size_t)tc_counter_elems(m, n), ctx->stream));
         CK(launch_rowmajor_to_panel(X, ldx, n, ell, ellp, xp, T_F32, ldn, ctx->stream));
         CK(launch_split_panel(xp, ldn, n, ell, ellp, x3, ldn, nullptr, ctx->stream));
         CK(launch_cast_bf16_split(static_cast<const float*>(A), m, n, lda, a3, seg, nullptr, ctx->stream));
-        CK(launch_project_split_tc(a3, m, n, seg, x3, ldn, ell, ellp, part, cp, T_F64, ldm, ctx->num_sms, ctx->flags,
-                                   nullptr, ctx->stream));
+        CK(launch_project_split_tc(a3, m, n, seg, x3, ldn, ell, ellp, part, tcnt, cp, T_F64, ldm, ctx->num_sms,
+                                   ctx->flags, nullptr, ctx->stream));
         CK(launch_panel_to_rowmajor(cp, ldm, m, ell, C, T_F64, ldc, nullptr, ctx->stream));
         return CORUTV_OK;
     }
@@ -833,6 +841,7 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
     if (prec == CORUTV_P_BF16) measure.take<char>(m * round_up(n, 8) * 2);
     const bool tf32_copy = prec == CORUTV_P_TF32 && !tma_rows_aligned(A, lda, 4);
     if (tf32_copy) measure.take<float>(m * round_up(n, 4));
+    if (pl.tensor) measure.take<int>(tc_counter_elems(m, n));
     CKS(ensure_ws(ctx, ctx->ws, measure.off, ctx->stream));
     Carver cv(ctx->ws.ptr);
     double* xp = cv.take<double>(pl.ellp * ldxp);
@@ -842,6 +851,8 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
     b.part = cv.take<char>(pl.part_elems * 8);
     b.abf = prec == CORUTV_P_BF16 ? cv.take<char>(m * round_up(n, 8) * 2) : nullptr;
     float* a32 = tf32_copy ? cv.take<float>(m * round_up(n, 4)) : nullptr;
+    b.tcnt = pl.tensor ? cv.take<int>(tc_counter_elems(m, n)) : nullptr;
+    if (pl.tensor) CK(cudaMemsetAsync(b.tcnt, 0, sizeof(int) * (size_t)tc_counter_elems(m, n), ctx->stream));
     CK(launch_rowmajor_to_panel(X, ldx, xrows, ell, pl.ellp, xp, T_F64, ldxp, ctx->stream));
     CK(launch_panel_convert(xp, T_F64, ldxp, xrows, pl.ellp, xc, pl.tcomp, ldxp, nullptr, ctx->stream));
     Exec ex{ctx->stream, ctx->flags, nullptr, ctx->num_sms};
@@ -857,7 +868,7 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
             aop = a32;
             lda_op = round_up(n, 4);
         }
-        CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, trans, xc, ldxp, ell, pl.ellp, b.part, cp, T_F64, ldcp,
+        CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, trans, xc, ldxp, ell, pl.ellp, b.part, b.tcnt, cp, T_F64, ldcp,
                             ctx->num_sms, ctx->flags, nullptr, ctx->stream));
     } else {
         CKS(sketch_simt(ex, pl, b, trans ? A_COLS : A_ROWS, A, ta, xc, pl.tcomp, cp, ldcp));

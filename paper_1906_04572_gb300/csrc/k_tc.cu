@@ -13,9 +13,11 @@
 // Schedule: a persistent grid of G CTAs (one per SM) splits the
 // (tile, K-chunk) iteration space into G equal contiguous ranges (stream-K),
 // so no wave is ever partly empty. A CTA's range crosses at most a few tile
-// boundaries; each tile segment it covers is written as an FP32 partial
-// (128 x ell_p) to `part`, and a fixed-order reduction kernel adds the
-// partials of each tile into the FP64 output panel.
+// boundaries. A tile covered by one CTA is written straight to the output
+// panel. Otherwise each CTA's segment of it is an FP32 partial (128 x ell_p)
+// in `part`; each finished piece bumps the tile's counter, and the CTA that
+// finishes last adds the tile's pieces in piece order (in FP32) and writes
+// the output, so the sum never depends on which CTA happened to finish last.
 //
 // Warp roles (192 threads): warps 0-3 read the accumulator out of tensor
 // memory (warp w owns TMEM lanes 32w..32w+31 = rows of the tile), warp 4 is
@@ -71,6 +73,12 @@ struct TcParams {
     uint32_t tmem_cols;   // columns allocated
     int kchunk_elems;     // K elements per chunk (64 bf16 / 32 fp32)
     float* part;
+    int* tile_cnt;        // per output tile: pieces finished (zero between launches)
+    void* out;            // output panel (FP64 or FP32)
+    int out_f64;
+    int ell;              // valid output columns
+    long long ldc;
+    long long mtot;       // valid output rows
     int* flags;
     const int* cancel;
 };
@@ -127,6 +135,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
             smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Untiled bulk copy global -> shared (16-byte aligned addresses, size a
+// multiple of 16), completing on `bar` with `bytes` of transaction count.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
 }
 
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
@@ -196,6 +213,67 @@ __host__ __device__ __forceinline__ long long unit_owner(long long u, long long 
     return ((u + 1) * grid + units - 1) / units - 1;
 }
 
+// Output row rg of a tile split over np pieces: out[j * ldc + rg] = the
+// pieces' FP32 partials added in piece order in FP32, for j < ell, then
+// converted once to the output type. The partials are FP32-accumulated
+// products, so adding a few of them in FP32 in a fixed order costs a few ulp,
+// below the error they already carry; an FP64 sum would add nothing but
+// FP64-pipe time (about 65 cycles per warp instruction on this GPU). All
+// loads of a 16-column chunk (up to four pieces at a time) are issued before
+// any add so their L2 latencies overlap.
+template <typename TO>
+__device__ __forceinline__ void reduce_pieces(const float* src, int np, int ellp, int ell, TO* out, long long ldc,
+                                              long long rg) {
+    for (int j0 = 0; j0 < ell; j0 += 16) {  // ellp is a multiple of 16, so j0 + 15 < ellp
+        float acc[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+        for (int pc0 = 0; pc0 < np; pc0 += 4) {
+            // unconditional loads (piece index clamped to a valid one) so that all
+            // 64 are issued back to back; pieces beyond np are not added
+            float v[4][16];
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                const float* sp = src + ((long long)min(pc0 + g, np - 1) * ellp + j0) * kTileM;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[g][i] = __ldcg(sp + i * kTileM);
+            }
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+                if (pc0 + g < np) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) acc[i] += v[g][i];
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (j0 + i < ell) out[(long long)(j0 + i) * ldc + rg] = (TO)acc[i];
+    }
+}
+
+// The same sum from pieces staged in shared memory (sp = row's element of
+// piece 0): 16 independent accumulators per chunk so the loads overlap.
+template <typename TO>
+__device__ __forceinline__ void sum_staged(const float* sp, int np, int ellp, int ell, TO* out, long long ldc,
+                                           long long rg) {
+    for (int j0 = 0; j0 < ell; j0 += 16) {
+        float acc[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+        for (int pc = 0; pc < np; ++pc) {
+            const float* q = sp + ((size_t)pc * ellp + j0) * kTileM;
+            float v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = q[i * kTileM];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i] += v[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (j0 + i < ell) out[(long long)(j0 + i) * ldc + rg] = (TO)acc[i];
+    }
+}
+
 template <bool kTf32>
 __global__ void __launch_bounds__(kThreads, 1)
 sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
@@ -207,6 +285,10 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
     __shared__ __align__(8) uint64_t accf_bar[2];
     __shared__ __align__(8) uint64_t acce_bar[2];
     __shared__ __align__(8) uint64_t drain_bar;
+    __shared__ __align__(8) uint64_t ep_bar[2];  // pieces stored (4 warps) / counter result ready
+    __shared__ __align__(8) uint64_t fix_bar;    // pieces staged into shared memory (last segment)
+    __shared__ volatile int last_s;
+    __shared__ volatile int fix_issued;
     __shared__ uint32_t tmem_holder;
     __shared__ volatile int abort_s;
     __shared__ volatile long long consumed_s;
@@ -228,6 +310,11 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
             mbar_init(&acce_bar[a], 4);
         }
         mbar_init(&drain_bar, 1);
+        mbar_init(&ep_bar[0], 4);
+        mbar_init(&ep_bar[1], 1);
+        mbar_init(&fix_bar, 1);
+        last_s = 0;
+        fix_issued = 0;
         abort_s = 0;
         consumed_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -362,7 +449,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
     } else {
         // ---------------- epilogue: warps 0-3 ----------------
         const int row = warp * 32 + lane;
-        int seg = 0;
+        int seg = 0, nsync = 0;
         for (int u = u0; u < u1; ++seg) {
             const int t = u / KC;
             const int seg_end = (u1 < (t + 1) * KC) ? u1 : (t + 1) * KC;
@@ -372,7 +459,11 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                 break;
             }
             tc_fence_after();
-            const long long piece = c - unit_owner((long long)t * KC, p.units, p.grid);
+            const long long first = unit_owner((long long)t * KC, p.units, p.grid);
+            const int np = (int)(unit_owner((long long)(t + 1) * KC - 1, p.units, p.grid) - first) + 1;
+            const long long piece = c - first;
+            const long long rg = (long long)t * kTileM + row;  // output row
+            const bool in_range = rg < p.mtot;
             float* dst = p.part + (((long long)t * p.maxp + piece) * p.ellp) * (long long)kTileM + row;
             const uint32_t tacc = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)a * p.acc_cols;
             for (int c0 = 0; c0 < p.ellp; c0 += 16) {
@@ -384,41 +475,87 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] += w[i];
                 }
+                if (np > 1) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) dst[(long long)(c0 + i) * kTileM] = v[i];
+                    for (int i = 0; i < 16; ++i) dst[(long long)(c0 + i) * kTileM] = v[i];
+                } else if (in_range) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        if (c0 + i >= p.ell) break;
+                        const long long o = (long long)(c0 + i) * p.ldc + rg;
+                        if (p.out_f64) static_cast<double*>(p.out)[o] = (double)v[i];
+                        else static_cast<float*>(p.out)[o] = v[i];
+                    }
+                }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce_bar[a]);
+            if (np > 1) {
+                // publish this piece, then count it; the CTA completing the count reduces the tile
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ep_bar[0]);
+                if (threadIdx.x == 0) {
+                    if (mbar_wait(&ep_bar[0], (uint32_t)(nsync & 1), &abort_s)) {
+                        const int done = atomicAdd(&p.tile_cnt[t], 1) + 1;
+                        last_s = done == np;
+                        if (done == np) p.tile_cnt[t] = 0;  // no other piece of this tile remains in this launch
+                    } else {
+                        abort_s = 1;
+                    }
+                    mbar_arrive(&ep_bar[1]);
+                }
+                if (!mbar_wait(&ep_bar[1], (uint32_t)(nsync & 1), &abort_s)) abort_s = 1;
+                ++nsync;
+                if (abort_s) break;
+                if (last_s) {
+                    const float* src = p.part + ((long long)t * p.maxp * p.ellp) * (long long)kTileM;
+                    const uint32_t piece_bytes = (uint32_t)p.ellp * kTileM * 4u;
+                    if (seg_end == u1 && (uint64_t)np * piece_bytes <= (uint64_t)p.stages * p.stage_bytes) {
+                        // Last segment: every MMA has completed and every copy was consumed,
+                        // so the operand ring is idle. Each piece is one contiguous block:
+                        // stage all of them with one bulk copy each (one round trip) and add
+                        // them from shared memory.
+                        if (threadIdx.x == 0) {
+                            __threadfence();
+                            asm volatile("fence.proxy.async.global;" ::: "memory");
+                            mbar_expect_tx(&fix_bar, (uint32_t)np * piece_bytes);
+                            for (int pc = 0; pc < np; ++pc)
+                                bulk_load(smem + (size_t)pc * piece_bytes, src + (long long)pc * p.ellp * kTileM,
+                                          piece_bytes, &fix_bar);
+                            fix_issued = 1;
+                        }
+                        if (!mbar_wait(&fix_bar, 0, &abort_s)) {
+                            abort_s = 1;
+                            break;
+                        }
+                        if (in_range) {
+                            const float* sp = reinterpret_cast<const float*>(smem) + row;
+                            if (p.out_f64) sum_staged<double>(sp, np, p.ellp, p.ell, static_cast<double*>(p.out), p.ldc, rg);
+                            else sum_staged<float>(sp, np, p.ellp, p.ell, static_cast<float*>(p.out), p.ldc, rg);
+                        }
+                    } else if (in_range) {
+                        __threadfence();
+                        if (p.out_f64)
+                            reduce_pieces<double>(src + row, np, p.ellp, p.ell, static_cast<double*>(p.out), p.ldc, rg);
+                        else
+                            reduce_pieces<float>(src + row, np, p.ellp, p.ell, static_cast<float*>(p.out), p.ldc, rg);
+                    }
+                }
+            }
             u = seg_end;
         }
     }
-    if (abort_s && threadIdx.x == 0) atomicExch(&p.flags[FLAG_TIMEOUT], 1);
+    if (abort_s && threadIdx.x == 0) {
+        atomicExch(&p.flags[FLAG_TIMEOUT], 1);
+        if (fix_issued) mbar_wait(&fix_bar, 0, nullptr, 100000000ull);  // staged copies in flight
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 5) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(p.tmem_cols));
-    }
-}
-
-// C[j * ldc + t * 128 + r] = sum over the pieces of tile t, in order.
-template <typename TO>
-__global__ void streamk_reduce_kernel(const float* part, long long mtiles, long long kc, long long units,
-                                      long long grid, int maxp, int ellp, int ell, long long mtot, TO* c,
-                                      long long ldc, const int* cancel) {
-    if (cancel && *cancel) return;
-    const long long total = mtiles * kTileM * (long long)ell;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long j = e / (mtiles * kTileM);
-        const long long rr = e % (mtiles * kTileM);
-        const long long t = rr / kTileM, r = rr % kTileM;
-        if (rr >= mtot) continue;
-        const long long np = unit_owner((t + 1) * kc - 1, units, grid) - unit_owner(t * kc, units, grid) + 1;
-        double s = 0.0;
-        for (long long pc = 0; pc < np; ++pc) s += (double)part[((t * maxp + pc) * ellp + j) * kTileM + r];
-        c[j * ldc + rr] = (TO)s;
     }
 }
 
@@ -602,7 +739,8 @@ uint32_t make_idesc(bool tf32, bool a_mn_major, int n) {
 // (ell columns, type tcout) = sum over the nparts column groups.
 cudaError_t tc_launch(const void* a, bool tf32, long long mtot, long long ktot_seg, int kseg, long long seg_stride,
                       const CUtensorMap& map_a, int a_boxes, int a_box_cols, const void* b, long long ldb,
-                      long long brows_k, int nparts, int trans, int64_t ell, int64_t ellp, void* part, void* c,
+                      long long brows_k, int nparts, int trans, int64_t ell, int64_t ellp, void* part,
+                      int* tile_cnt, void* c,
                       ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel, cudaStream_t st) {
     const Plan pl = make_plan(mtot, ktot_seg, kseg, tf32, num_sms);
     const int ke = tf32 ? 32 : 64;  // K elements per 128-byte row
@@ -620,6 +758,12 @@ cudaError_t tc_launch(const void* a, bool tf32, long long mtot, long long ktot_s
     p.tf32 = tf32 ? 1 : 0;
     p.kchunk_elems = ke;
     p.part = static_cast<float*>(part);
+    p.tile_cnt = tile_cnt;
+    p.out = c;
+    p.out_f64 = tcout == T_F64 ? 1 : 0;
+    p.ell = (int)ell;
+    p.ldc = ldc;
+    p.mtot = mtot;
     p.flags = flags;
     p.cancel = cancel;
     p.a_boxes = a_boxes;
@@ -654,23 +798,12 @@ cudaError_t tc_launch(const void* a, bool tf32, long long mtot, long long ktot_s
     if (e != cudaSuccess) return e;
     count_launch();
     kern<<<pl.grid, kThreads, smem, st>>>(map_a, map_b, p);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const long long total = pl.mtiles * kTileM * ell;
-    const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
-    count_launch();
-    if (tcout == T_F64)
-        streamk_reduce_kernel<double><<<blocks, 256, 0, st>>>(p.part, pl.mtiles, pl.kc, pl.units, pl.grid, pl.maxp,
-                                                              (int)ellp, (int)ell, pl.mtot, static_cast<double*>(c),
-                                                              ldc, cancel);
-    else
-        streamk_reduce_kernel<float><<<blocks, 256, 0, st>>>(p.part, pl.mtiles, pl.kc, pl.units, pl.grid, pl.maxp,
-                                                             (int)ellp, (int)ell, pl.mtot, static_cast<float*>(c),
-                                                             ldc, cancel);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+int64_t tc_counter_elems(int64_t m, int64_t n) { return (std::max(m, n) + kTileM - 1) / kTileM; }
 
 int64_t tc_partial_elems(int64_t m, int64_t n, int64_t ellp, int64_t ldm, int64_t ldn, int num_sms) {
     (void)ldm;
@@ -686,8 +819,8 @@ int64_t tc_partial_elems(int64_t m, int64_t n, int64_t ellp, int64_t ldm, int64_
 }
 
 cudaError_t launch_sketch_tc(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, int trans,
-                             const void* x, int64_t ldx, int64_t ell, int64_t ellp, void* part, void* c,
-                             ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel,
+                             const void* x, int64_t ldx, int64_t ell, int64_t ellp, void* part, int* tile_cnt,
+                             void* c, ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel,
                              cudaStream_t st) {
     if (ta != T_BF16 && ta != T_F32) return cudaErrorInvalidValue;
     if (ellp % 16 != 0 || ellp < 16 || ellp > 128 || ell > ellp) return cudaErrorInvalidValue;
@@ -710,20 +843,20 @@ cudaError_t launch_sketch_tc(const void* a, ElemType ta, int64_t m, int64_t n, i
     }
     if (e != cudaSuccess) return e;
     return tc_launch(a, tf32, trans ? n : m, trans ? m : n, 1, 0, map_a, a_boxes, a_box_cols, x, ldx, trans ? m : n,
-                     1, trans, ell, ellp, part, c, tcout, ldc, num_sms, flags, cancel, st);
+                     1, trans, ell, ellp, part, tile_cnt, c, tcout, ldc, num_sms, flags, cancel, st);
 }
 
 cudaError_t launch_project_split_tc(const void* a3, int64_t m, int64_t n, int64_t seg, const void* q3, int64_t ldq,
-                                    int64_t ell, int64_t ellp, void* part, void* w, ElemType tw, int64_t ldw,
-                                    int num_sms, int* flags, const int* cancel, cudaStream_t st) {
+                                    int64_t ell, int64_t ellp, void* part, int* tile_cnt, void* w, ElemType tw,
+                                    int64_t ldw, int num_sms, int* flags, const int* cancel, cudaStream_t st) {
     if (ellp % 16 != 0 || ellp < 16 || ellp > 128 || ell > ellp || seg % 64 != 0) return cudaErrorInvalidValue;
     cudaError_t e = get_encoder();
     if (e != cudaSuccess) return e;
     CUtensorMap map_a;
     e = encode_2d(&map_a, a3, false, 3 * seg, m, 3 * seg, 64u, kTileM, CU_TENSOR_MAP_SWIZZLE_128B);
     if (e != cudaSuccess) return e;
-    return tc_launch(a3, false, m, n, 3, seg, map_a, 1, 0, q3, ldq, n, 3, 0, ell, ellp, part, w, tw, ldw, num_sms,
-                     flags, cancel, st);
+    return tc_launch(a3, false, m, n, 3, seg, map_a, 1, 0, q3, ldq, n, 3, 0, ell, ellp, part, tile_cnt, w, tw, ldw,
+                     num_sms, flags, cancel, st);
 }
 
 bool tma_rows_aligned(const void* a, int64_t lda, int elem_bytes) {

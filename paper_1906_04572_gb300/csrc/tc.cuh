@@ -11,6 +11,10 @@ namespace corutv {
 // Elements of split-K partial storage the tensor-core products may use
 // (FP32 elements; the caller provides at least this many).
 int64_t tc_partial_elems(int64_t m, int64_t n, int64_t ellp, int64_t ldm, int64_t ldn, int num_sms);
+// Per-tile completion counters the products need (int elements). They must
+// be zero before the first product; every product leaves them zero again
+// (unless it timed out).
+int64_t tc_counter_elems(int64_t m, int64_t n);
 
 // C = A X (trans = 0; C: m x ell panel with ld ldc = ldm) or C = A^T X
 // (trans = 1; C: n x ell panel, ldc = ldn). A: m x n row-major of type ta
@@ -18,9 +22,10 @@ int64_t tc_partial_elems(int64_t m, int64_t n, int64_t ellp, int64_t ldm, int64_
 // lda (lda * elem_size a multiple of 16 bytes). X: panel of the same element
 // type with ellp columns (padding columns zero), ld ldx. FP32 accumulation;
 // C is written with element type tcout (FP64 or FP32). `part` holds split
-// partials.
+// partials, `tile_cnt` the per-tile counters (tc_counter_elems).
 cudaError_t launch_sketch_tc(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, int trans,
-                             const void* x, int64_t ldx, int64_t ell, int64_t ellp, void* part, void* c,
+                             const void* x, int64_t ldx, int64_t ell, int64_t ellp, void* part, int* tile_cnt,
+                             void* c,
                              ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel,
                              cudaStream_t st);
 
@@ -44,7 +49,8 @@ cudaError_t launch_copy_f32_padded(const float* a, int64_t m, int64_t n, int64_t
 // accumulate in FP32, so W = sum of the nine part products carries the
 // rounding of an FP32 dot product. W: panel (ell columns, type tw, ld ldw).
 cudaError_t launch_project_split_tc(const void* a3, int64_t m, int64_t n, int64_t seg, const void* q3, int64_t ldq,
-                                    int64_t ell, int64_t ellp, void* part, void* w, ElemType tw, int64_t ldw,
+                                    int64_t ell, int64_t ellp, void* part, int* tile_cnt, void* w, ElemType tw,
+                                    int64_t ldw,
                                     int num_sms, int* flags, const int* cancel, cudaStream_t st);
 // Writes a3 (rows of [A_h | A_m | A_l]) from FP32 A.
 cudaError_t launch_cast_bf16_split(const float* a, int64_t m, int64_t n, int64_t lda, void* a3, int64_t seg,
