@@ -177,6 +177,7 @@ struct FactorPlan {
 struct FactorBufs {
     void *x, *c1, *q1, *c2, *q2, *w, *tmp;   // panels of type FactorPlan::tp
     double *gpart, *g, *r, *d, *qt, *rt, *upanel, *zpanel;
+    double* refl;     // reflectors of the QRCP of D (V, tau, signs)
     void *xc, *q1c, *q2c, *part;
     void* abf;        // bf16 copy of A for CORUTV_P_BF16
     int *perm, *skip;
@@ -242,6 +243,7 @@ void carve_factor(C& cv, const FactorPlan& pl, FactorBufs& b) {
     b.d = cv.template take<double>(ll);
     b.qt = cv.template take<double>(ll);
     b.rt = cv.template take<double>(ll);
+    b.refl = cv.template take<double>(pl.ellp * (pl.ellp + 2));
     b.xc = cv.template take<char>(pn * es_c);
     b.q1c = cv.template take<char>(pm * es_c);
     b.q2c = cv.template take<char>(pl.split ? 3 * pn * 2 : pn * es_d);
@@ -405,7 +407,7 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     // eq. 8: D P = Qt Rt
     {
         ProfScope ps(ex.prof, CORUTV_STAGE_QRCP, ex.st);
-        CK(launch_qrcp(b.d, ell, b.qt, b.rt, b.perm, ex.cancel, ex.st));
+        CK(launch_qrcp(b.d, ell, b.qt, b.rt, b.perm, b.refl, ex.cancel, ex.st));
     }
     return CORUTV_OK;
 }
@@ -931,7 +933,9 @@ corutv_status corutv_qrcp(corutv_ctx* ctx, const double* D, int64_t ell, double*
     if (ell < 1 || ell > 128) return fail(CORUTV_EINVAL, "ell must be in [1, 128]");
     std::lock_guard<std::mutex> lk(ctx->call_mu);
     DeviceGuard guard(ctx->device);
-    CK(launch_qrcp(D, ell, Qt, Rt, perm, nullptr, ctx->stream));
+    const size_t work_bytes = sizeof(double) * (size_t)(ell * (ell + 2));
+    CKS(ensure_ws(ctx, ctx->ws, work_bytes, ctx->stream));
+    CK(launch_qrcp(D, ell, Qt, Rt, perm, static_cast<double*>(ctx->ws.ptr), nullptr, ctx->stream));
     return CORUTV_OK;
 }
 

@@ -114,8 +114,10 @@ cudaError_t launch_cholesky(const double* g, int64_t ell, int64_t rows, double* 
 cudaError_t launch_trsm_rows(const void* c, ElemType tp, int64_t ldc, int64_t rows, int64_t ell,
                              const double* r, ElemType tc, void* q, int64_t ldq, void* qc,
                              ElemType tqc, int64_t ldqc, const int* cancel, cudaStream_t st);
-// Column-pivoted QR of the small ell x ell FP64 matrix d (eq. 8), one block.
-cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, int* perm,
+// Column-pivoted QR of the small ell x ell FP64 matrix d (eq. 8): the
+// factorisation in one block, then Qt formed from its reflectors by several
+// blocks. work: ell * (ell + 2) doubles of device scratch.
+cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, int* perm, double* work,
                         const int* cancel, cudaStream_t st);
 // V[i][j] = Q2[perm[j]] (Q2 a panel of type tq2; row-major output of type tv).
 cudaError_t launch_gather_v(const void* q2, ElemType tq2, int64_t ldq2, int64_t n, int64_t ell, const int* perm,

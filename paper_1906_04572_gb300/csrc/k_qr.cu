@@ -17,29 +17,32 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // FP64 reciprocal and reciprocal square root without the FP64 divide / sqrt
-// sequences (each several hundred cycles on this part): an FP32 estimate on
-// the operand scaled into FP32 range by a power of two, then two
-// Newton-Raphson steps in FP64, each squaring the relative error
-// (about 2^-23 -> 2^-46 -> 2^-92, so the result is within a few ulp).
-//   1/sqrt(x): y <- y (3/2 - (x/2) y^2)
-//   1/x      : y <- y + y (1 - x y)
-// For normal, finite, nonzero operands (1/sqrt: positive); others fall back
-// to the library operations.
+// sequences (each several hundred cycles on this part, where every dependent
+// FP64 operation costs about 65 cycles): an FP32 estimate y of the operand
+// scaled into FP32 range by a power of two (relative error |e| below about
+// 2^-22), then ONE third-order Householder step, i.e. the Taylor series of
+// the exact correction factor to second order:
+//   1/sqrt(x): e = 1 - x y^2,  y (1 - e)^-1/2 = y (1 + e/2 + 3e^2/8 + O(e^3))
+//   1/x      : e = 1 - x y,    y (1 - e)^-1   = y (1 + e + e^2 + O(e^3))
+// The truncation error is O(e^3) (about 2^-64), so the result is within a few
+// ulp; the dependent chain is 4 (resp. 3) FP64 operations instead of 6 (4)
+// for two Newton steps. For normal, finite, nonzero operands (1/sqrt:
+// positive); others fall back to the library operations.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double scale_pow2(double x, int k) {  // x * 2^k, k within the exponent range
     return __hiloint2double(__double2hiint(x) + (k << 20), __double2loint(x));
 }
 
 __device__ __forceinline__ double rsqrt_nr(double x) {
-    const int ef = (__double2hiint(x) >> 20) & 0x7ff;
-    if (ef == 0 || ef == 0x7ff || x < 0.0) return 1.0 / sqrt(x);
+    const int hi = __double2hiint(x);
+    const int ef = (hi >> 20) & 0x7ff;
+    if (ef == 0 || ef == 0x7ff || hi < 0) return 1.0 / sqrt(x);  // integer tests: an FP64 compare costs ~2 FMAs of latency
     const int k = (ef - 1023) >> 1;            // x = xs 2^(2k), xs in [1, 4)
     const double xs = scale_pow2(x, -2 * k);
-    double y = (double)rsqrtf((float)xs);
-    const double hx = 0.5 * xs;
-    y = y * fma(-hx, y * y, 1.5);
-    y = y * fma(-hx, y * y, 1.5);
-    return scale_pow2(y, -k);
+    const double y = (double)rsqrtf((float)xs);
+    const double e = fma(-xs, y * y, 1.0);
+    const double c = fma(0.375, e, 0.5);       // 1/2 + 3e/8
+    return scale_pow2(fma(y * e, c, y), -k);
 }
 
 __device__ __forceinline__ double rcp_nr(double x) {
@@ -47,24 +50,51 @@ __device__ __forceinline__ double rcp_nr(double x) {
     if (ef == 0 || ef == 0x7ff) return 1.0 / x;
     const int k = ef - 1023;                   // x = xs 2^k, |xs| in [1, 2)
     const double xs = scale_pow2(x, -k);
-    double y = (double)__frcp_rn((float)xs);
-    y = fma(y, fma(-xs, y, 1.0), y);
-    y = fma(y, fma(-xs, y, 1.0), y);
-    return scale_pow2(y, -k);
+    const double y = (double)__frcp_rn((float)xs);
+    const double e = fma(-xs, y, 1.0);
+    return scale_pow2(fma(y, fma(e, e, e), y), -k);
 }
 
-constexpr int kCholThreads = 128;  // one warp per SM sub-partition (each has its own FP64 unit)
-
-// Right-looking Cholesky, upper factor, R^T R = G (+ shift I), one column at
-// a time, with a one-step lookahead. The upper triangle is enumerated row by
-// row from the bottom row up, columns right to left (table `tri`), so the
-// trailing triangle of step j (rows > j) is a contiguous prefix of length
-// (ell-j-1)(ell-j)/2 whose last entry is the next pivot (j+1, j+1). Step j:
-// all threads scale row j by 1/r_jj (computed one step earlier); then warp 0
-// forms the next pivot d = G'(j+1,j+1) - r(j,j+1)^2, checks it and computes
-// 1/sqrt(d), while warps 1-3 apply the rank-1 update to the rest of the
-// prefix with every lane busy.
+// Right-looking Cholesky, upper factor, R^T R = G (+ shift I), one row of R
+// per step with a one-row lookahead and a single barrier per step. The upper
+// triangle is enumerated row by row from the bottom row up, columns right to
+// left (table `tri`), so the rows > j+1 of the trailing triangle form a
+// contiguous prefix of length (ell-j-2)(ell-j-1)/2. At step j row j of R is
+// final and rows > j carry the updates of steps < j. On this GPU every FP64
+// warp instruction holds its sub-partition's FP64 pipe for about 64 cycles
+// whatever the number of active lanes, so the pivot chain is kept to as few
+// FP64 instructions as possible. At the same time:
+//  * warp 0 forms the pivot d = G'(j+1, j+1) - R(j, j+1)^2, checks it,
+//    computes y = 1/sqrt(d) and R(j+1, j+1) = d y -- the chain that sets the
+//    pace;
+//  * warp 4 (same sub-partition, idle while warp 0 waits on its chain)
+//    applies step j's update to the rest of row j+1 in registers, takes y
+//    from warp 0 at a named barrier and stores the scaled row;
+//  * warps 1-3 and 5-7 apply step j's rank-1 update to rows > j+1, four
+//    independent entries per thread at a time.
 // rows = number of rows of the matrix whose Gram is factorised (for the shift).
+constexpr int kCholThreads = 256;
+constexpr int kCholUpdThreads = 192;
+
+// d > 0 and finite, by integer tests on the bit pattern
+__device__ __forceinline__ bool pos_finite(double d) {
+    const long long b = __double_as_longlong(d);
+    return b > 0 && ((b >> 52) & 0x7ff) != 0x7ff;
+}
+
+// Warp 0: row a of S holds G' with the updates of steps < a; make it row a of R.
+// Returns false (on every lane) when the pivot is not positive and finite.
+__device__ __forceinline__ bool chol_finish_row(double* S, int ld, int ell, int a, int lane) {
+    const double d = S[a * ld + a];
+    const bool ok = pos_finite(d);
+    if (ok) {
+        const double y = rsqrt_nr(d);
+        for (int c = a + 1 + lane; c < ell; c += 32) S[a * ld + c] *= y;
+        if (lane == 0) S[a * ld + a] = d * y;  // d / sqrt(d)
+    }
+    return ok;
+}
+
 __global__ void __launch_bounds__(kCholThreads)
 cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, int* skip_out,
                 const int* cancel) {
@@ -76,7 +106,7 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
     extern __shared__ double S[];  // ell x (ell + 1) doubles, then the uint16 table
     const int ld = ell + 1;
     unsigned short* tri = reinterpret_cast<unsigned short*>(S + (size_t)ell * ld);
-    __shared__ double trace, ynext;
+    __shared__ double trace, ysh;
     __shared__ int fail_s;
     // table: bottom-up rows; row a holds columns ell-1 .. a
     for (int a = ell - 1 - tid; a >= 0; a -= kCholThreads) {
@@ -84,6 +114,8 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
         int e = rb * (rb + 1) / 2;
         for (int c = ell - 1; c >= a; --c) tri[e++] = (unsigned short)((a << 8) | c);
     }
+    const bool upd = warp != 0 && warp != 4;
+    const int ut = upd ? (warp - (warp > 4 ? 2 : 1)) * 32 + lane : 0;  // 0 .. 191
     int attempt = 0;
     bool fail = false;
     for (; attempt < 3; ++attempt) {
@@ -104,35 +136,64 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
             const int a = e / ell, b = e % ell;
             S[a * ld + b] = g[a * ell + b] + (a == b ? shift : 0.0);
         }
-        if (tid == 0) {
-            const double d0 = g[0] + shift;
-            fail_s = !(d0 > 0.0) || !isfinite(d0);
-            ynext = fail_s ? 0.0 : rsqrt_nr(d0);
-        }
+        if (tid == 0) fail_s = 0;
+        __syncthreads();
+        if (warp == 0 && !chol_finish_row(S, ld, ell, 0, lane) && lane == 0) fail_s = 1;
         __syncthreads();
         fail = fail_s != 0;
-        for (int j = 0; j < ell && !fail; ++j) {
-            const double y = ynext;  // 1 / r_jj
-            for (int c = j + 1 + tid; c < ell; c += kCholThreads) S[j * ld + c] *= y;
-            if (tid == 0) S[j * ld + j] *= y;  // d_jj / sqrt(d_jj) = r_jj
-            __syncthreads();
-            if (j + 1 < ell) {
-                if (warp == 0) {
-                    if (lane == 0) {
-                        const double s = S[j * ld + j + 1];
-                        const double d = fma(-s, s, S[(j + 1) * ld + j + 1]);
-                        S[(j + 1) * ld + j + 1] = d;
-                        const bool bad = !(d > 0.0) || !isfinite(d);
-                        if (bad) fail_s = 1;
-                        else ynext = rsqrt_nr(d);
+        for (int j = 0; j + 1 < ell && !fail; ++j) {
+            const double* rj = S + j * ld;  // row j of R
+            if (warp == 0) {
+                // pivot chain: d, 1/sqrt(d), diagonal of R (lanes redundant; one instruction each)
+                const double rjn = rj[j + 1];
+                const double d = fma(-rjn, rjn, S[(j + 1) * ld + j + 1]);
+                const bool ok = pos_finite(d);
+                const double y = ok ? rsqrt_nr(d) : 0.0;
+                if (lane == 0) {
+                    ysh = y;
+                    if (ok) S[(j + 1) * ld + j + 1] = d * y;  // d / sqrt(d)
+                    else fail_s = 1;
+                }
+                asm volatile("bar.sync 2, 64;" ::: "memory");
+            } else if (warp == 4) {
+                // rest of row j+1: step j's update now, the scaling once y is known
+                const double rjn = rj[j + 1];
+                double* rn = S + (j + 1) * ld;
+                const int n_strips = (ell - j - 2 + 31) >> 5;  // columns j+2 .. ell-1
+                double v[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int c = j + 2 + lane + 32 * t;
+                    if (t < n_strips && c < ell) v[t] = fma(-rjn, rj[c], rn[c]);
+                }
+                asm volatile("bar.sync 2, 64;" ::: "memory");
+                const double y = ysh;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int c = j + 2 + lane + 32 * t;
+                    if (t < n_strips && c < ell) rn[c] = v[t] * y;
+                }
+            } else if (upd) {
+                const int len = (ell - j - 2) * (ell - j - 1) / 2;  // rows > j+1
+                for (int e0 = ut; e0 < len; e0 += 4 * kCholUpdThreads) {
+                    int ac[4];
+                    double ra[4], rc[4], sv[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int e = e0 + k * kCholUpdThreads;
+                        ac[k] = e < len ? (int)tri[e] : -1;
                     }
-                } else {
-                    const int len = (ell - j - 1) * (ell - j) / 2 - 1;  // prefix without (j+1, j+1)
-                    for (int e = tid - 32; e < len; e += kCholThreads - 32) {
-                        const int ac = tri[e];
-                        const int a = ac >> 8, c = ac & 0xff;
-                        S[a * ld + c] = fma(-S[j * ld + a], S[j * ld + c], S[a * ld + c]);
-                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (ac[k] >= 0) {
+                            const int a = ac[k] >> 8, c = ac[k] & 0xff;
+                            ra[k] = rj[a];
+                            rc[k] = rj[c];
+                            sv[k] = S[a * ld + c];
+                        }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (ac[k] >= 0) S[(ac[k] >> 8) * ld + (ac[k] & 0xff)] = fma(-ra[k], rc[k], sv[k]);
                 }
             }
             __syncthreads();
@@ -252,165 +313,206 @@ cudaError_t trsm_dispatch(const void* c, int64_t ldc, int64_t rows, int ell, con
 }
 
 // ---------------------------------------------------------------------------
-// QRCP of the small D (eq. 8), one block of four warps (one per SM
-// sub-partition, each sub-partition with its own FP64 unit). W is column-major in shared
-// memory (column c at W + c * ldw, ldw odd so that lanes owning consecutive
-// columns hit distinct banks). Column-wise work (squared norms, reflector
-// dot products and updates) is split as lanes = columns, warps = quarters of
-// the active rows; partial sums meet in shared memory in warp order.
-// Pivot choice compares the non-negative squared norms through their bit
-// patterns (same order as the values), lowest index on ties.
+// QRCP of the small D (eq. 8): one block, FP64, Householder reflections with
+// Businger-Golub pivoting on column norms recomputed exactly at every step.
+//
+// Every step is bound by the FP64 pipe (one warp instruction per sub-partition
+// about every 65 cycles on this GPU) and by its dependent chain, so:
+//  * the active columns are spread over 8 warps with a power-of-two group of
+//    lanes per column (rows split inside the group, sums by xor shuffles), so
+//    the lanes stay full as the active block shrinks;
+//  * the next step's squared norms are recomputed exactly in the same pass
+//    that applies the reflector (no separate norm pass). They are not
+//    downdated: the pivot's norm also builds the next reflector, whose
+//    orthogonality would inherit a downdated norm's error (up to ~1e-8);
+//  * the dot products over the rows below the diagonal, t_c = x_j[j+1:]^T
+//    x_c[j+1:], start before the reflector is known: with v = [1; x_{j+1:} /
+//    (alpha - beta)], v^T x_c = x_c[j] + t_c / (alpha - beta). They run on
+//    warps 1-3 and 5-7 (after the other warps swap the pivot column in),
+//    while warp 0 swaps row j itself and computes beta, tau and 1 / (alpha -
+//    beta) as soon as the pivot is known: its sub-partition's FP64 pipe then
+//    serves that dependent chain alone; warps 4 and 8 stage column j;
+//  * the pivot (argmax of the squared norms, compared through their bit
+//    patterns, lowest index on ties) is taken by every warp redundantly, so it
+//    needs no broadcast.
+// W is column-major in shared memory (column c at W + c * ldw, ldw odd).
 // ---------------------------------------------------------------------------
-constexpr int kQrcpThreads = 128;  // one warp per sub-partition (a second one per sub-partition measured slower)
-constexpr int kQrcpWarps = kQrcpThreads / 32;
+constexpr int kQrcpMapThreads = 256;                  // warps 0-7: column groups
+constexpr int kQrcpThreads = kQrcpMapThreads + 32;    // warp 8: staging
+constexpr int kQrcpDotThreads = 192;                  // warps 1-3, 5-7 during the reflector dots
 
-// rows [lo, hi) of the active range [j, ell) owned by warp w (one of kQrcpWarps shares)
-__device__ __forceinline__ void row_share(int j, int ell, int w, int& lo, int& hi) {
-    const int n = ell - j;
-    const int qn = (n + kQrcpWarps - 1) / kQrcpWarps;
-    lo = j + w * qn;
-    hi = min(ell, lo + qn);
-    if (lo > ell) lo = ell;
+// lanes per column for `ncols` active columns of `nrows` rows over `nthr`
+// threads: a power of two <= 32, and at most a quarter of the rows (fewer
+// shuffle levels once the block is small)
+__device__ __forceinline__ int qr_group(int ncols, int nrows, int nthr = kQrcpMapThreads) {
+    int g = 1;
+    while (g < 32 && 2 * g * ncols <= nthr && 4 * g <= nrows) g <<= 1;
+    return g;
 }
 
-// Apply H_j = I - tau v v^T (v = [1; W[j][j+1:]]) to columns c0..ell-1, rows j..ell-1.
-__device__ void apply_reflector(double* W, int ldw, double* part, int j, int c0, int ell, double tau, int lane,
-                                int warp) {
-    const double* v = W + j * ldw;
-    int lo, hi;
-    row_share(j, ell, warp, lo, hi);
-    for (int cb = c0; cb < ell; cb += 32) {
-        const int c = cb + lane;
-        if (c < ell) {
-            const double* x = W + c * ldw;
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            int i = lo;
-            if (i == j && i < hi) { s0 = x[j]; ++i; }  // v[j] = 1
-            for (; i + 3 < hi; i += 4) {
-                s0 += v[i] * x[i];
-                s1 += v[i + 1] * x[i + 1];
-                s2 += v[i + 2] * x[i + 2];
-                s3 += v[i + 3] * x[i + 3];
-            }
-            for (; i < hi; ++i) s0 += v[i] * x[i];
-            part[warp * 128 + (c - cb)] = (s0 + s1) + (s2 + s3);
-        }
-        __syncthreads();
-        if (c < ell) {
-            double dot = part[c - cb];
-            for (int w = 1; w < kQrcpWarps; ++w) dot += part[w * 128 + (c - cb)];
-            const double f = tau * dot;
-            double* x = W + c * ldw;
-            int i = lo;
-            if (i == j && i < hi) { x[j] -= f; ++i; }
-            for (; i < hi; ++i) x[i] -= f * v[i];
-        }
-        __syncthreads();
+__device__ __forceinline__ double group_sum(double v, int g) {
+    for (int o = g >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// argmax of nrm[j..ell) (non-negative doubles, so their bit patterns order
+// like their values) with one 64-bit max: the key is the bit pattern with its
+// 7 lowest mantissa bits replaced by 127 - c, so equal norms go to the lowest
+// index; norms within 2^-45 relative of each other count as equal.
+__device__ __forceinline__ int qr_pivot(const double* nrm, int j, int ell, int lane) {
+    long long best = -1;
+    for (int c = j + lane; c < ell; c += 32) {
+        const long long key = (__double_as_longlong(nrm[c]) & ~0x7fLL) | (127 - c);
+        best = key > best ? key : best;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        best = ob > best ? ob : best;
+    }
+    return 127 - (int)(best & 0x7f);
 }
 
 __global__ void __launch_bounds__(kQrcpThreads)
-qrcp_kernel(const double* d, int ell, double* qt, double* rt, int* perm, const int* cancel) {
+qrcp_kernel(const double* d, int ell, double* refl, double* rt, int* perm, const int* cancel) {
     if (cancel && *cancel) return;
-    extern __shared__ double W[];  // ell columns of ldw doubles, then part, nrm, tau, sgn, perm
+    extern __shared__ double W[];  // ell columns of ldw doubles, then nrm, xbuf, tau, sgn, tdot, perm
     const int ldw = ell | 1;
-    double* part = W + ell * ldw;           // kQrcpWarps x 128
-    double* nrm = part + kQrcpWarps * 128;  // ell
-    double* tau = nrm + ell;
+    double* nrm = W + ell * ldw;
+    double* xbuf = nrm + ell;
+    double* tau = xbuf + ell;
     double* sgn = tau + ell;
-    int* pv = reinterpret_cast<int*>(sgn + ell);
-    __shared__ int piv_s;
+    double* tdot = sgn + ell;
+    int* pv = reinterpret_cast<int*>(tdot + ell);
+    __shared__ double sc_beta, sc_tau, sc_scale, sc_ts;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool mapped = tid < kQrcpMapThreads;
     for (int e = tid; e < ell * ell; e += kQrcpThreads) {
         const int a = e / ell, b = e % ell;  // d row-major: entry (a, b) -> column b, row a
         W[b * ldw + a] = d[e];
     }
     for (int c = tid; c < ell; c += kQrcpThreads) pv[c] = c;
     __syncthreads();
+    {   // squared norms of all columns
+        const int g = qr_group(ell, ell);
+        const int c = tid / g, ph = tid % g;
+        double s = 0.0;
+        if (mapped && c < ell)
+            for (int i = ph; i < ell; i += g) s = fma(W[c * ldw + i], W[c * ldw + i], s);
+        if (mapped) {
+            s = group_sum(s, g);
+            if (c < ell && ph == 0) nrm[c] = s;
+        }
+    }
+    __syncthreads();
     for (int j = 0; j < ell; ++j) {
-        int lo, hi;
-        row_share(j, ell, warp, lo, hi);
-        // 1. recomputed squared residual norms of columns j..ell-1
-        for (int cb = j; cb < ell; cb += 32) {
-            const int c = cb + lane;
-            if (c < ell) {
-                const double* x = W + c * ldw;
-                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-                int i = lo;
-                for (; i + 3 < hi; i += 4) {
-                    s0 += x[i] * x[i];
-                    s1 += x[i + 1] * x[i + 1];
-                    s2 += x[i + 2] * x[i + 2];
-                    s3 += x[i + 3] * x[i + 3];
-                }
-                for (; i < hi; ++i) s0 += x[i] * x[i];
-                part[warp * 128 + (c - j)] = (s0 + s1) + (s2 + s3);
-            }
-        }
-        __syncthreads();
-        // 2. pivot: warp 0 adds the shares (warp order) and takes the argmax
+        // S1: pivot (every warp)
+        const int p = qr_pivot(nrm, j, ell, lane);
+        const int nc = ell - j - 1;
         if (warp == 0) {
-            long long best = -1;
-            int bi = ell;
-            for (int c = j + lane; c < ell; c += 32) {
-                double s = part[c - j];
-                for (int w = 1; w < kQrcpWarps; ++w) s += part[w * 128 + (c - j)];
-                nrm[c] = s;
-                const long long key = __double_as_longlong(s);
-                if (key > best) { best = key; bi = c; }
+            // row j of columns j and p, then the reflector of the pivot column
+            if (lane == 0) {
+                const double sj = nrm[p];  // squared norm of the pivot column, rows j..ell-1
+                const double alpha = W[p * ldw + j];
+                if (p != j) {
+                    W[p * ldw + j] = W[j * ldw + j];
+                    W[j * ldw + j] = alpha;
+                    const int t = pv[j];
+                    pv[j] = pv[p];
+                    pv[p] = t;
+                }
+                // beta = -sign(alpha) |x| (sign(+-0) = +), tau = (beta - alpha) / beta,
+                // scale = 1 / (alpha - beta); the sign taken by integer bit tests and the
+                // zero-column test kept off the dependent chain
+                const long long ab = __double_as_longlong(alpha);
+                const bool neg = ab < 0 && (ab & 0x7fffffffffffffffLL) != 0;
+                const double y = rsqrt_nr(sj);  // 1 / |column| (unused when the column is zero)
+                const double nr = sj * y;
+                const double beta_c = neg ? nr : -nr;
+                const double inv_beta = neg ? y : -y;
+                const double t_c = fma(-alpha, inv_beta, 1.0);
+                const double scale_c = rcp_nr(alpha - beta_c);
+                // H = I when the part below the diagonal is exactly zero
+                const bool reflect = sj != alpha * alpha;
+                const double beta = reflect ? beta_c : alpha;
+                const double t = reflect ? t_c : 0.0;
+                const double scale = reflect ? scale_c : 0.0;
+                sc_beta = beta;
+                sc_tau = t;
+                sc_scale = scale;
+                sc_ts = t * scale;
+                tau[j] = t;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        } else {
+            // warps 1-8: the other rows of columns j and p
+            if (p != j)
+                for (int i = tid - 32; i < ell; i += kQrcpThreads - 32)
+                    if (i != j) {
+                        const double t = W[j * ldw + i];
+                        W[j * ldw + i] = W[p * ldw + i];
+                        W[p * ldw + i] = t;
+                    }
+            asm volatile("bar.sync 1, %0;" ::"n"(kQrcpThreads - 32) : "memory");
+            // S2: t_c = x_j[j+1:]^T x_c[j+1:] (warps 1-3, 5-7) || staging of column j (warps 4, 8)
+            if (warp != 4 && warp != 8) {
+                const int t2 = (warp - (warp > 4 ? 2 : 1)) * 32 + lane;  // 0 .. 191
+                const int g2 = qr_group(nc > 0 ? nc : 1, ell - j - 1 > 0 ? ell - j - 1 : 1, kQrcpDotThreads);
+                const int c2 = j + 1 + t2 / g2, ph2 = t2 % g2;
+                double tc = 0.0;
+                if (c2 < ell) {
+                    const double* x = W + j * ldw;
+                    const double* y = W + c2 * ldw;
+                    double s0 = 0.0, s1 = 0.0;
+                    int i = j + 1 + ph2;
+                    for (; i + g2 < ell; i += 2 * g2) {
+                        s0 = fma(x[i], y[i], s0);
+                        s1 = fma(x[i + g2], y[i + g2], s1);
+                    }
+                    if (i < ell) s0 = fma(x[i], y[i], s0);
+                    tc = s0 + s1;
+                }
+                tc = group_sum(tc, g2);
+                if (c2 < ell && ph2 == 0) tdot[c2] = tc;
+            } else {
+                for (int i = j + 1 + lane + (warp == 8 ? 32 : 0); i < ell; i += 64) xbuf[i] = W[j * ldw + i];
             }
-            if (lane == 0) piv_s = bi;
         }
         __syncthreads();
-        const int p = piv_s;
-        // 3. swap columns j and p (whole columns)
-        if (p != j) {
-            for (int i = tid; i < ell; i += kQrcpThreads) {
-                const double t = W[j * ldw + i];
-                W[j * ldw + i] = W[p * ldw + i];
-                W[p * ldw + i] = t;
+        const int g = qr_group(nc > 0 ? nc : 1, ell - j);
+        const int c = j + 1 + tid / g, ph = tid % g;
+        const bool act = mapped && c < ell;
+        // S3: apply H_j to columns c > j, accumulating their squared norms over rows > j
+        //     (warps 0-7) || finish column j: v below the diagonal, beta on it (warp 8)
+        if (mapped) {
+            double acc = 0.0, xjc = 0.0, f = 0.0, fs = 0.0;
+            double* y = W + (act ? c : j) * ldw;
+            if (act) {
+                xjc = y[j];
+                const double w = fma(sc_scale, tdot[c], xjc);  // v^T x_c
+                f = sc_tau * w;
+                fs = sc_ts * w;
             }
-            if (tid == 0) {
-                const int t = pv[j];
-                pv[j] = pv[p];
-                pv[p] = t;
-                const double tn = nrm[j];
-                nrm[j] = nrm[p];
-                nrm[p] = tn;
+            __syncwarp();  // every lane of the group has read x_c[j] before lane 0 rewrites it
+            if (act) {
+                int i = j + ph;
+                if (i == j) {
+                    y[j] = xjc - f;
+                    i += g;
+                }
+                for (; i < ell; i += g) {
+                    const double nv = fma(-xbuf[i], fs, y[i]);
+                    y[i] = nv;
+                    acc = fma(nv, nv, acc);
+                }
             }
-            __syncthreads();
+            acc = group_sum(acc, g);
+            if (act && ph == 0) nrm[c] = acc;
+        } else if (sc_tau != 0.0) {
+            const double scale = sc_scale;
+            for (int i = j + 1 + lane; i < ell; i += 32) W[j * ldw + i] = xbuf[i] * scale;
+            if (lane == 0) W[j * ldw + j] = sc_beta;
         }
-        // 4. reflector of column j from its squared norm s = alpha^2 + |x|^2:
-        //    beta = -sign(alpha) sqrt(s), tau = 1 - alpha / beta,
-        //    v[i] = x[i] / (alpha - beta); H = I when x is exactly zero.
-        {
-            double* x = W + j * ldw;
-            const double alpha = x[j];
-            const double s = nrm[j];
-            double t = 0.0;
-            if (s != alpha * alpha) {
-                const double y = rsqrt_nr(s);            // 1 / |column|
-                const double nr = s * y;
-                const double beta = alpha >= 0.0 ? -nr : nr;
-                const double inv_beta = alpha >= 0.0 ? -y : y;
-                t = fma(-alpha, inv_beta, 1.0);
-                const double scale = rcp_nr(alpha - beta);
-                for (int i = j + 1 + tid; i < ell; i += kQrcpThreads) x[i] *= scale;
-                __syncthreads();
-                if (tid == 0) x[j] = beta;
-            }
-            if (tid == 0) tau[j] = t;
-            __syncthreads();
-        }
-        // 5. apply it to the trailing columns
-        const double tj = tau[j];
-        if (tj != 0.0 && j + 1 < ell) apply_reflector(W, ldw, part, j, j + 1, ell, tj, lane, warp);
+        __syncthreads();
     }
     // Rt = upper(W) with diag(Rt) >= 0
     for (int a = tid; a < ell; a += kQrcpThreads) sgn[a] = W[a * ldw + a] < 0.0 ? -1.0 : 1.0;
@@ -421,21 +523,63 @@ qrcp_kernel(const double* d, int ell, double* qt, double* rt, int* perm, const i
     }
     for (int c = tid; c < ell; c += kQrcpThreads) perm[c] = pv[c];
     __syncthreads();
-    // Qt = H_0 H_1 ... H_{ell-1}, accumulated backwards in place
-    for (int j = ell - 1; j >= 0; --j) {
-        const double tj = tau[j];
-        if (j < ell - 1 && tj != 0.0) apply_reflector(W, ldw, part, j, j + 1, ell, tj, lane, warp);
-        double* x = W + j * ldw;
-        for (int i = tid; i < ell; i += kQrcpThreads) {
-            if (i > j) x[i] *= -tj;
-            else if (i == j) x[j] = 1.0 - tj;
-            else x[i] = 0.0;
-        }
-        __syncthreads();
-    }
+    // reflectors for the Q formation: V column-major (v_j below the diagonal of
+    // column j, zero elsewhere), then tau, then the column signs of Qt
     for (int e = tid; e < ell * ell; e += kQrcpThreads) {
-        const int a = e / ell, b = e % ell;
-        qt[e] = W[b * ldw + a] * sgn[b];
+        const int jj = e / ell, i = e % ell;
+        refl[e] = i > jj ? W[jj * ldw + i] : 0.0;
+    }
+    for (int c = tid; c < ell; c += kQrcpThreads) {
+        refl[ell * ell + c] = tau[c];
+        refl[ell * ell + ell + c] = sgn[c];
+    }
+}
+
+// Qt = H_0 H_1 ... H_{ell-1} diag(sgn). Column c of the product is
+// H_0 H_1 ... H_c e_c (H_k leaves e_c alone for k > c), so the columns are
+// independent: one warp per column (lanes own rows lane + 32 t, t < 4),
+// applying H_c, H_{c-1}, ..., H_0 in turn with a warp-wide dot product each,
+// spread over ceil(ell / 8) blocks so that the FP64 pipes of several SMs
+// share the work. V, tau and the signs are staged in shared memory.
+constexpr int kQformWarps = 8;
+
+__global__ void __launch_bounds__(kQformWarps * 32)
+qform_kernel(const double* refl, int ell, double* qt, const int* cancel) {
+    if (cancel && *cancel) return;
+    extern __shared__ double Vs[];  // ell * ell + 2 * ell
+    const int n = ell * ell + 2 * ell;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) Vs[e] = refl[e];
+    __syncthreads();
+    const double* tau = Vs + ell * ell;
+    const double* sgn = tau + ell;
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kQformWarps + (threadIdx.x >> 5);
+    if (c >= ell) return;
+    double q[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) q[t] = (lane + 32 * t == c) ? 1.0 : 0.0;
+    for (int k = c; k >= 0; --k) {
+        const double* v = Vs + k * ell;  // v[k] = 1 implied, v[i] = 0 for i < k
+        double part = 0.0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int i = lane + 32 * t;
+            if (i < ell) part = fma(i == k ? 1.0 : v[i], q[t], part);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        const double f = tau[k] * part;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int i = lane + 32 * t;
+            if (i >= k && i < ell) q[t] = fma(-f, i == k ? 1.0 : v[i], q[t]);
+        }
+    }
+    const double sc = sgn[c];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int i = lane + 32 * t;
+        if (i < ell) qt[(size_t)i * ell + c] = q[t] * sc;
     }
 }
 
@@ -489,13 +633,22 @@ cudaError_t launch_trsm_rows(const void* c, ElemType tp, int64_t ldc, int64_t ro
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, int* perm,
+cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, int* perm, double* work,
                         const int* cancel, cudaStream_t st) {
-    const size_t smem = sizeof(double) * ((size_t)ell * (ell | 1) + kQrcpWarps * 128 + 3 * (size_t)ell) + sizeof(int) * ell;
+    if (ell < 1 || ell > 128 || !work) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(double) * ((size_t)ell * (ell | 1) + 5 * (size_t)ell) + sizeof(int) * ell;
     cudaError_t e = cudaFuncSetAttribute(qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launch();
-    qrcp_kernel<<<1, kQrcpThreads, smem, st>>>(d, (int)ell, qt, rt, perm, cancel);
+    qrcp_kernel<<<1, kQrcpThreads, smem, st>>>(d, (int)ell, work, rt, perm, cancel);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem_q = sizeof(double) * (size_t)(ell * ell + 2 * ell);
+    e = cudaFuncSetAttribute(qform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_q);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    qform_kernel<<<(unsigned)((ell + kQformWarps - 1) / kQformWarps), kQformWarps * 32, smem_q, st>>>(work, (int)ell,
+                                                                                                   qt, cancel);
     return cudaGetLastError();
 }
 
