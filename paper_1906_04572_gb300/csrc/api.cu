@@ -181,7 +181,8 @@ struct FactorBufs {
     void *xc, *q1c, *q2c, *part;
     void* abf;        // bf16 copy of A for CORUTV_P_BF16
     int *perm, *skip;
-    int* tcnt;        // per-tile counters of the tensor-core products
+    int* tcnt;        // per-tile counters of the tensor-core products, then gcnt
+    int* gcnt;        // counters of the FP32 Gram kernel
 };
 
 corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64_t lda, int64_t k,
@@ -224,7 +225,11 @@ corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64
     return CORUTV_OK;
 }
 
-template <typename C>
+int64_t factor_counters(const FactorPlan& pl) {
+    return tc_counter_elems(pl.m, pl.n) + gram_f32_counters(std::max(pl.m, pl.n), (int)pl.ell, pl.num_sms);
+}
+
+template <class C>
 void carve_factor(C& cv, const FactorPlan& pl, FactorBufs& b) {
     const int64_t pm = pl.ellp * pl.ldm, pn = pl.ellp * pl.ldn, ll = pl.ellp * pl.ellp;
     const int es_c = elem_size(pl.tcomp), es_d = elem_size(pl.tdproj), es_p = elem_size(pl.tp);
@@ -237,7 +242,9 @@ void carve_factor(C& cv, const FactorPlan& pl, FactorBufs& b) {
     b.tmp = cv.template take<char>(std::max(pm, pn) * es_p);
     b.upanel = cv.template take<double>(pm);
     b.zpanel = cv.template take<double>(pn);
-    b.gpart = cv.template take<double>((int64_t)std::max(pl.gs_m, pl.gs_n) * ll);
+    b.gpart = cv.template take<double>(std::max((int64_t)std::max(pl.gs_m, pl.gs_n) * ll,
+                                                (gram_f32_work_floats(std::max(pl.m, pl.n), (int)pl.ell,
+                                                                      pl.num_sms) + 1) / 2));
     b.g = cv.template take<double>(ll);
     b.r = cv.template take<double>(ll);
     b.d = cv.template take<double>(ll);
@@ -251,7 +258,8 @@ void carve_factor(C& cv, const FactorPlan& pl, FactorBufs& b) {
     b.abf = pl.prec == CORUTV_P_BF16 ? cv.template take<char>(pl.m * (pl.split ? 3 : 1) * pl.seg * 2) : nullptr;
     b.perm = cv.template take<int>(pl.ellp);
     b.skip = cv.template take<int>(8);
-    b.tcnt = pl.tensor ? cv.template take<int>(tc_counter_elems(pl.m, pl.n)) : nullptr;
+    b.tcnt = cv.template take<int>(factor_counters(pl));
+    b.gcnt = b.tcnt + tc_counter_elems(pl.m, pl.n);
 }
 
 size_t factor_bytes(const FactorPlan& pl) {
@@ -294,6 +302,12 @@ corutv_status sketch_simt(const Exec& ex, const FactorPlan& pl, const FactorBufs
 corutv_status gram(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, const void* x,
                    int64_t ldx, const void* y, int64_t ldy, int64_t len, double* out,
                    const int* cancel, ElemType tg) {
+    if (tg == T_F32 && pl.tp == T_F32 && b.gcnt) {
+        // one launch, split sums reduced in the kernel
+        CK(launch_gram_f32(static_cast<const float*>(x), ldx, static_cast<const float*>(y), ldy, len, (int)pl.ell,
+                           out, reinterpret_cast<float*>(b.gpart), b.gcnt, ex.num_sms, cancel, ex.st));
+        return CORUTV_OK;
+    }
     const int gs = gemm_simt_splits(pl.ell, len, ex.num_sms);
     const int64_t ll = pl.ell * pl.ell;
     GemmArgs g{A_PANEL_T, B_PANEL, O_ROWMAJ, pl.tp, tg, x, ldx, y, ldy, b.gpart, pl.ell, ll,
@@ -344,11 +358,11 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     // Step 1: X = Psi (panel n x ellp, padding columns zero)
     if (psi_dev) CK(launch_rowmajor_to_panel(psi_dev, ell, n, ell, pl.ellp, b.x, pl.tp, pl.ldn, ex.st));
     else CK(launch_gaussian_panel(seed, sid, n, ell, pl.ellp, b.x, pl.tp, pl.ldn, ex.cancel, ex.st));
+    // the workspace is shared with other entry points: start the kernels' counters at zero
+    CK(cudaMemsetAsync(b.tcnt, 0, sizeof(int) * (size_t)factor_counters(pl), ex.st));
     if (pl.tensor) {
         // padding columns of the bf16 / fp32 operand panels must read as zero
         CK(cudaMemsetAsync(b.q1c, 0, (size_t)pl.ellp * pl.ldm * elem_size(pl.tcomp), ex.st));
-        // the workspace is shared with other entry points: start the tile counters at zero
-        CK(cudaMemsetAsync(b.tcnt, 0, sizeof(int) * (size_t)tc_counter_elems(m, n), ex.st));
         CK(launch_panel_convert(b.x, pl.tp, pl.ldn, n, pl.ellp, b.xc, pl.tcomp, pl.ldn, ex.cancel, ex.st));
         if (pl.split)
             CK(launch_cast_bf16_split(static_cast<const float*>(a), m, n, pl.lda, b.abf, pl.seg, ex.cancel, ex.st));

@@ -114,6 +114,14 @@ cudaError_t launch_cholesky(const double* g, int64_t ell, int64_t rows, double* 
 cudaError_t launch_trsm_rows(const void* c, ElemType tp, int64_t ldc, int64_t rows, int64_t ell,
                              const double* r, ElemType tc, void* q, int64_t ldq, void* qc,
                              ElemType tqc, int64_t ldqc, const int* cancel, cudaStream_t st);
+// FP32 Gram G = X^T Y (row-major ell x ell FP64 output) of two FP32 panels
+// in one launch; split sums reduced in the kernel in a fixed order. work:
+// gram_f32_work_floats floats; cnt: gram_f32_counters ints, zero before the
+// first call (every call leaves them zero).
+int64_t gram_f32_work_floats(int64_t len, int ell, int num_sms);
+int64_t gram_f32_counters(int64_t len, int ell, int num_sms);
+cudaError_t launch_gram_f32(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_t len, int ell,
+                            double* out, float* work, int* cnt, int num_sms, const int* cancel, cudaStream_t st);
 // Column-pivoted QR of the small ell x ell FP64 matrix d (eq. 8): the
 // factorisation in one block, then Qt formed from its reflectors by several
 // blocks. work: ell * (ell + 2) doubles of device scratch.

@@ -1,0 +1,205 @@
+// FP32 Gram products G = X^T Y (the Gram matrices of CholeskyQR, Sec. 3.1,
+// and D = Q1^T (A Q2), eq. 7) in a single launch, with the split sums reduced
+// inside the kernel in a fixed order.
+//
+// X, Y: FP32 panels (column j at X + j * ldx, `len` rows), ell <= 128
+// columns. G: ell x ell FP64, row-major. The output is cut into 64 x 64
+// tiles; each tile's rows of X / Y are split into S contiguous ranges, one
+// CTA per (range, tile). A CTA accumulates its 64 x 64 partial in FP32
+// (4 x 4 outputs per thread, operands staged in shared memory 32 rows at a
+// time). The ranges run as thread-block clusters of 8 CTAs: each CTA leaves
+// its partial in its shared memory, and rank r of the cluster adds slice r
+// (512 outputs) of the 8 partials in rank order over distributed shared
+// memory and stores that slice of the cluster sum. A counter per (tile,
+// slice) then tells which CTA stored the last cluster sum of its slice; that
+// CTA adds the clusters' slices in cluster order and writes G. Nobody waits
+// on another CTA outside its cluster, the counters return to zero, and the
+// sums never depend on arrival order.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace corutv {
+
+namespace {
+
+constexpr int kGT = 64;      // output tile
+constexpr int kGChunk = 32;  // rows staged per step
+constexpr int kGThreads = 256;
+constexpr int kGCluster = 8; // CTAs per cluster = output slices
+constexpr int kGLd = kGT + 1;
+constexpr int kGSlice = kGT * kGT / kGCluster;
+
+struct GramPlan {
+    int ntile, tiles, nc;  // clusters per tile; ranges per tile = 8 nc
+};
+
+GramPlan gram_plan(int64_t len, int ell, int num_sms) {
+    GramPlan p;
+    p.ntile = (ell + kGT - 1) / kGT;
+    p.tiles = p.ntile * p.ntile;
+    int64_t nc = 2 * num_sms / (kGCluster * p.tiles);               // about two CTAs per SM
+    nc = std::min<int64_t>(nc, (len + 64 * kGCluster - 1) / (64 * kGCluster));  // >= 64 rows per range
+    p.nc = (int)std::max<int64_t>(1, nc);
+    return p;
+}
+
+// exact float -> double by integer operations (normal and zero inputs); the
+// FP64 conversion instruction would cost a slot of the FP64 pipe
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;  // zero, subnormal, inf, nan
+    const unsigned long long s = (unsigned long long)(u >> 31) << 63;
+    const unsigned long long bits = s | ((unsigned long long)(e + 896u) << 52) |
+                                    ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+__global__ void __launch_bounds__(kGThreads)
+gram_f32_kernel(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_t len, int ell, double* out,
+                float* cpart, int* cnt, GramPlan pl, const int* cancel) {
+    namespace cg = cooperative_groups;
+    if (cancel && *cancel) return;  // uniform over the grid: no cluster barrier is left waiting
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ __align__(16) float sbuf[2 * kGChunk * kGLd];  // staging, then the 64 x 64 partial
+    __shared__ int last_s;
+    float* Xs = sbuf;
+    float* Ys = sbuf + kGChunk * kGLd;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int S = pl.nc * kGCluster;
+    const int s = blockIdx.x, tile = blockIdx.y;
+    const int rank = (int)cluster.block_rank(), cid = s / kGCluster;
+    const int ti = tile / pl.ntile, tj = tile % pl.ntile;
+    const int64_t r_beg = (int64_t)s * len / S, r_end = (int64_t)(s + 1) * len / S;
+    const bool same = x == y && ti == tj;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
+    // staging: each thread moves 8 elements per operand per chunk; the next
+    // chunk's loads are all issued (into registers) before the current chunk
+    // is multiplied, so their latency overlaps the arithmetic
+    constexpr int kPer = kGChunk * kGT / kGThreads;  // 8
+    float px[kPer], py[kPer];
+    auto load_chunk = [&](int64_t r0) {
+        const int nr = (int)(r_end - r0 < kGChunk ? r_end - r0 : kGChunk);
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int idx = tid + k * kGThreads;
+            const int c = idx / kGChunk, r = idx % kGChunk;  // consecutive threads: consecutive rows
+            const int cx = ti * kGT + c, cy = tj * kGT + c;
+            px[k] = (r < nr && cx < ell) ? x[(int64_t)cx * ldx + r0 + r] : 0.f;
+            if (!same) py[k] = (r < nr && cy < ell) ? y[(int64_t)cy * ldy + r0 + r] : 0.f;
+        }
+    };
+    if (r_beg < r_end) load_chunk(r_beg);
+    for (int64_t r0 = r_beg; r0 < r_end; r0 += kGChunk) {
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int idx = tid + k * kGThreads;
+            const int c = idx / kGChunk, r = idx % kGChunk;
+            Xs[r * kGLd + c] = px[k];
+            if (!same) Ys[r * kGLd + c] = py[k];
+        }
+        __syncthreads();
+        if (r0 + kGChunk < r_end) load_chunk(r0 + kGChunk);
+        const float* Yb = same ? Xs : Ys;
+#pragma unroll 4
+        for (int r = 0; r < kGChunk; ++r) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = Xs[r * kGLd + ty + 16 * i];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) b[k] = Yb[r * kGLd + tx + 16 * k];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(a[i], b[k], acc[i][k]);
+        }
+        __syncthreads();
+    }
+    // the partial of this range stays in shared memory (row-major 64 x 64)
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sbuf[(ty + 16 * i) * kGT + tx + 16 * k] = acc[i][k];
+    cluster.sync();
+    // slice `rank` of the cluster sum: the 8 partials in rank order
+    float* cp = cpart + ((size_t)tile * pl.nc + cid) * (kGT * kGT) + (size_t)rank * kGSlice;
+    for (int e = tid; e < kGSlice; e += kGThreads) {
+        float v[kGCluster];
+#pragma unroll
+        for (int q = 0; q < kGCluster; ++q) v[q] = cluster.map_shared_rank(sbuf, q)[rank * kGSlice + e];
+        float sum = 0.f;
+#pragma unroll
+        for (int q = 0; q < kGCluster; ++q) sum += v[q];
+        cp[e] = sum;
+    }
+    cluster.sync();  // no CTA leaves while others still read its shared memory
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        int* c = cnt + tile * kGCluster + rank;
+        const int done = atomicAdd(c, 1) + 1;
+        last_s = done == pl.nc;
+        if (done == pl.nc) *c = 0;
+    }
+    __syncthreads();
+    if (!last_s) return;
+    // slice `rank` of G: the clusters' sums in cluster order
+    __threadfence();
+    const float* c0 = cpart + (size_t)tile * pl.nc * (kGT * kGT) + (size_t)rank * kGSlice;
+    for (int e = tid; e < kGSlice; e += kGThreads) {
+        float sum = 0.f;
+        int q = 0;
+        for (; q + 7 < pl.nc; q += 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcg(c0 + (size_t)(q + u) * (kGT * kGT) + e);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sum += v[u];
+        }
+        for (; q < pl.nc; ++q) sum += __ldcg(c0 + (size_t)q * (kGT * kGT) + e);
+        const int eg = rank * kGSlice + e;
+        const int a = ti * kGT + eg / kGT, b = tj * kGT + eg % kGT;
+        if (a < ell && b < ell) out[(int64_t)a * ell + b] = f2d_exact(sum);
+    }
+}
+
+}  // namespace
+
+int64_t gram_f32_work_floats(int64_t len, int ell, int num_sms) {
+    const GramPlan p = gram_plan(len, ell, num_sms);
+    return (int64_t)p.tiles * p.nc * (kGT * kGT);
+}
+
+int64_t gram_f32_counters(int64_t len, int ell, int num_sms) {
+    const GramPlan p = gram_plan(len, ell, num_sms);
+    return (int64_t)p.tiles * kGCluster;
+}
+
+cudaError_t launch_gram_f32(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_t len, int ell,
+                            double* out, float* work, int* cnt, int num_sms, const int* cancel, cudaStream_t st) {
+    if (ell < 1 || ell > 128 || len < 1 || !work || !cnt) return cudaErrorInvalidValue;
+    const GramPlan p = gram_plan(len, ell, num_sms);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(p.nc * kGCluster), (unsigned)p.tiles, 1);
+    cfg.blockDim = dim3(kGThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kGCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    count_launch();
+    return cudaLaunchKernelEx(&cfg, gram_f32_kernel, x, ldx, y, ldy, len, ell, out, work, cnt, p, cancel);
+}
+
+}  // namespace corutv

@@ -232,11 +232,33 @@ __global__ void trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell
     TC* Ts = Rs + ell * ell;                      // [ell][nthr]
     TC* Rd = Ts + (size_t)ell * nthr;             // 1 / R[j][j]
     const int tid = threadIdx.x;
-    for (int e = tid; e < ell * ell; e += nthr) Rs[e] = (TC)r[e];
+    // loads in batches of 16 per thread, all in flight before their stores
+    // (one at a time, each would wait out a full memory latency)
+    constexpr int kB = 16;
+    for (int e0 = 0; e0 < ell * ell; e0 += kB * nthr) {
+        double v[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int e = e0 + u * nthr + tid;
+            v[u] = e < ell * ell ? r[e] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int e = e0 + u * nthr + tid;
+            if (e < ell * ell) Rs[e] = (TC)v[u];
+        }
+    }
     for (int j = tid; j < ell; j += nthr) Rd[j] = (TC)1 / (TC)r[j * ell + j];
     const int64_t i = (int64_t)blockIdx.x * nthr + tid;
     if (i < rows)
-        for (int j = 0; j < ell; ++j) Ts[j * nthr + tid] = (TC)c[j * ldc + i];
+        for (int j0 = 0; j0 < ell; j0 += kB) {
+            TI v[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u) v[u] = j0 + u < ell ? c[(j0 + u) * ldc + i] : (TI)0;
+#pragma unroll
+            for (int u = 0; u < kB; ++u)
+                if (j0 + u < ell) Ts[(j0 + u) * nthr + tid] = (TC)v[u];
+        }
     __syncthreads();
     if (i >= rows) return;
     for (int j0 = 0; j0 < ell; j0 += kTrsmB) {
@@ -270,15 +292,15 @@ __global__ void trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell
     }
 }
 
-// Threads (= rows) per block: up to 256, bounded by shared memory. A row's
-// solve is a dependent chain, so larger blocks mainly serve to load R once
-// per 256 rows.
+// Threads (= rows) per block: up to 128, bounded by shared memory. A row's
+// solve is a dependent chain; more, smaller blocks spread a panel over more
+// SMs at the price of loading R once per 128 rows.
 template <typename TC>
 int trsm_threads(int ell, int64_t rows) {
     const long budget = 200 * 1024;
     long per = (budget - (long)ell * (ell + 1) * (long)sizeof(TC)) / ((long)ell * (long)sizeof(TC));
     per = per / 32 * 32;
-    if (per > 256) per = 256;
+    if (per > 128) per = 128;  // more blocks: an 8000-row panel spreads over ~60 SMs instead of ~30
     if (per < 32) per = 32;
     (void)rows;
     return (int)per;
