@@ -262,6 +262,125 @@ def time_factor(ctx, A, k, p, q, prec, steps, warmup, world, profile=False):
     return ms, {"U": U, "T": T, "V": V, "perm": perm}, prof
 
 
+def latency_single(ctx, A, k, p, q, prec, reps):
+    """Wall-clock latency of single synchronous factorisations through the C
+    ABI (device-resident input, preallocated outputs): what a caller waits for
+    one result with the GPU otherwise idle."""
+    import torch
+    from paper_1906_04572_gb300 import corutv
+    m, n = A.shape
+    ell = k + p
+    U = torch.empty((m, ell), device=A.device, dtype=A.dtype)
+    V = torch.empty((n, ell), device=A.device, dtype=A.dtype)
+    T = torch.empty((ell, ell), device=A.device, dtype=A.dtype)
+    perm = torch.empty(ell, device=A.device, dtype=torch.int32)
+    lat = []
+    for r in range(reps + 3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        corutv.corutv_factor(ctx.handle, A, k, p, q, prec, U, T, V, perm, seed=0, stream=r)
+        assert ctx.sync() == 0
+        lat.append(time.perf_counter() - t0)
+    lat = np.array(lat[3:]) * 1e3
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)), "reps": reps,
+            "kind": "one factorisation at a time, synchronous, input resident on the device"}
+
+
+def serving_c5(device_index, nreq, rate, prec, slots):
+    """The serving stream (independent requests with Poisson arrivals, m, n ~
+    U[256, 4096], k ~ U[5, 64], ell = k + 10, q ~ U{0, 1, 2}, FP32 inputs with
+    sigma_i = i^-1.5 on the first 256 directions) through corutv_submit /
+    corutv_poll: per-request latency from submission to completion."""
+    import torch
+    import synth
+    from paper_1906_04572_gb300 import Context, corutv
+    reqs = synth.serving_requests(count=nreq, rate_per_s=rate, seed=0)
+    dev = torch.device("cuda", device_index)
+    mats, outs = [], []
+    for r in reqs:
+        u, sig, v = synth.serving_factors(r)
+        a = (torch.from_numpy(u * sig).to(dev) @ torch.from_numpy(v).to(dev).T).float().contiguous()
+        ell = r.k + r.p
+        outs.append(tuple(torch.empty(sh, device=dev, dtype=torch.float32)
+                          for sh in ((r.m, ell), (ell, ell), (r.n, ell))))
+        mats.append(a)
+    torch.cuda.synchronize()
+    flops = sum(flops_per_factor(r.m, r.n, r.k + r.p, r.q) for r in reqs)
+    with Context(device_index, max_slots=slots) as sctx:
+        # warm-up: the first few requests once, outside the measurement
+        warm = [corutv.corutv_submit(sctx.handle, corutv.make_request(mats[i], reqs[i].k, reqs[i].p, reqs[i].q,
+                                                                      prec, *outs[i], seed=reqs[i].seed))
+                for i in range(min(slots, nreq))]
+        for tk in warm:
+            corutv.corutv_poll(sctx.handle, tk, timeout_us=120_000_000)
+        tickets = []
+        t0 = time.perf_counter()
+        for r, a, o in zip(reqs, mats, outs):
+            wait = r.arrival_s - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            tickets.append(corutv.corutv_submit(sctx.handle, corutv.make_request(a, r.k, r.p, r.q, prec, *o,
+                                                                                 seed=r.seed)))
+        lats = []
+        for tk in tickets:
+            st, lat = corutv.corutv_poll(sctx.handle, tk, timeout_us=120_000_000)
+            if st != corutv.OK:
+                raise RuntimeError(f"serving request failed with status {st}")
+            lats.append(lat)
+        wall = time.perf_counter() - t0
+    lats = np.array(lats) * 1e3
+    return {"requests": nreq, "rate_per_s": rate, "slots": slots, "prec": prec,
+            "p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99)),
+            "solves_per_s": nreq / wall, "tflops": flops / wall / 1e12, "wall_s": wall,
+            "inputs": "m, n ~ U[256, 4096], k ~ U[5, 64], ell = k + 10, q ~ U{0,1,2}, sigma_i = i^-1.5 (256 "
+                      "directions), FP32, seed 0; product formed on the device from the seeded factors"}
+
+
+def rpca_c4(ctx, device, prec="f32"):
+    """ALM-CoRUTV on the RPCA workload (4800 x 1200, rank 5, 10 % uniform
+    +-50 outliers, FP32), 50 iterations."""
+    import torch
+    import synth
+    pr = synth.rpca_c4(0)
+    M = torch.from_numpy(pr.m_obs).to(device=device, dtype=torch.float32)
+    ctx.rpca(M, 5, tol=1e-30, max_iter=3, prec=prec, allow_notconv=True)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = ctx.rpca(M, 5, tol=1e-30, max_iter=50, prec=prec, allow_notconv=True)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    L = out["L"].double().cpu().numpy()
+    err = float(np.linalg.norm(L - pr.l_true) / np.linalg.norm(pr.l_true))
+    return {"workload": "rpca_4800x1200_rank5_10pct_50iter", "ms": sec * 1e3, "iters": out["iters"],
+            "ms_per_iter": sec * 1e3 / max(out["iters"], 1), "zeta": out["zeta"], "rank": out["rank"],
+            "rel_err_L": err, "prec": prec}
+
+
+def c3_line(ctx, device, precs, steps):
+    """The 20000 x 20000 mixed-precision workload (sigma_i = exp(-i/20),
+    k = 100, ell = 110, q = 2), FP32 input formed on the device from the
+    seeded Haar factors; a few timed factorisations per sketch precision."""
+    import torch
+    import synth
+    m = n = 20000
+    sig = synth.c3_sigma(n)
+    u, s_, v = synth.spectrum_factors(m, n, sig, seed=0)
+    A = (torch.from_numpy(u * s_).to(device) @ torch.from_numpy(v).to(device).T).float().contiguous()
+    del u, v
+    flops = flops_per_factor(m, n, 110, 2)
+    res = {}
+    for prec in precs:
+        ms, out, _ = time_factor(ctx, A, 100, 10, 2, prec, steps, 1, 1)
+        appr = (out["U"].double() @ out["T"].double()) @ out["V"].double().T
+        err = float(torch.linalg.norm(A.double() - appr) / torch.linalg.norm(A.double()))
+        del appr
+        res[prec] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, "e_rel": err}
+    torch.cuda.synchronize()
+    del A
+    torch.cuda.empty_cache()
+    return {"workload": "c3_20000x20000_k100_l110_q2", "steps": steps, **res}
+
+
 def run_ours(args):
     import torch
     from paper_1906_04572_gb300 import Context, corutv
@@ -361,6 +480,15 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline_sample(args, f, ell)
 
+    latency = latency_single(ctx, A, k, p, q, prec, 30)
+    extra = {}
+    if not args.no_extra:
+        extra["serving"] = serving_c5(local, args.serve_requests, args.serve_rate, prec if prec != "f64" else "f32",
+                                      8)
+        extra["rpca"] = rpca_c4(ctx, device)
+        if args.c3:
+            extra["c3"] = c3_line(ctx, device, ("bf16", "f32"), 3)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -375,12 +503,14 @@ def run_ours(args):
             "fp64_path": fp64,
             "equal_error": (None if fp64 is None else bool(err <= 1.01 * fp64["e_rel"])),
             "roofline": roof,
+            "latency": latency,
             "stages": stages,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": sampler.summary(),
             "gpu_launches": int(prof["launches"]),
             "peaks": {"source": peaks_kind, "hbm_gbs": peaks["hbm_gbs"], "bf16_tflops": peaks.get("bf16_tflops")},
+            **extra,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -401,6 +531,10 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the serving, RPCA and 20000^2 lines")
+    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--c3", type=int, default=1, help="1: also time the 20000 x 20000 workload")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

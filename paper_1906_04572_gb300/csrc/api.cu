@@ -178,6 +178,7 @@ struct FactorBufs {
     void *x, *c1, *q1, *c2, *q2, *w, *tmp;   // panels of type FactorPlan::tp
     double *gpart, *g, *r, *d, *qt, *rt, *upanel, *zpanel;
     double* refl;     // reflectors of the QRCP of D (V, tau, signs)
+    int* defic;       // columns found numerically dependent in the extra CholeskyQR pass
     void *xc, *q1c, *q2c, *part;
     void* abf;        // bf16 copy of A for CORUTV_P_BF16
     int *perm, *skip;
@@ -251,6 +252,7 @@ void carve_factor(C& cv, const FactorPlan& pl, FactorBufs& b) {
     b.qt = cv.template take<double>(ll);
     b.rt = cv.template take<double>(ll);
     b.refl = cv.template take<double>(pl.ellp * (pl.ellp + 2));
+    b.defic = cv.template take<int>(pl.ellp);
     b.xc = cv.template take<char>(pn * es_c);
     b.q1c = cv.template take<char>(pm * es_c);
     b.q2c = cv.template take<char>(pl.split ? 3 * pn * 2 : pn * es_d);
@@ -335,16 +337,21 @@ corutv_status orth(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, co
     void* p1c = passes == 1 ? qc : nullptr;
     // pass 1
     CKS(gram(ex, pl, b, c, ld, c, ld, len, b.g, ex.cancel, tw));
-    CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, b.skip, ex.cancel, ex.st));
+    const double u = tw == T_F64 ? 0x1p-53 : 0x1p-24;  // unit roundoff of the Gram arithmetic
+    CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, b.skip, ex.cancel, ex.st, u));
     CK(launch_trsm_rows(c, tp, ld, len, ell, b.r, tw, p1, ld, p1c, tqc, ld, ex.cancel, ex.st));
-    // extra pass, only after a shifted pass 1
+    // extra pass, only after a shifted pass 1. Directions the shifted pass left
+    // at rounding level (a numerically rank-deficient C) cannot be restored
+    // from C: their columns get a seeded random completion, orthonormalised by
+    // the following pass (and well conditioned as they stand for a
+    // one-pass intermediate basis).
     CKS(gram(ex, pl, b, p1, ld, p1, ld, len, b.g, b.skip, tw));
-    CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, nullptr, b.skip, ex.st));
-    CK(launch_trsm_rows(p1, tp, ld, len, ell, b.r, tw, p1, ld, p1c, tqc, ld, b.skip, ex.st));
+    CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, nullptr, b.skip, ex.st, u, b.defic, 10.0 * (double)ell * u));
+    CK(launch_trsm_rows(p1, tp, ld, len, ell, b.r, tw, p1, ld, p1c, tqc, ld, b.skip, ex.st, b.defic));
     if (passes == 1) return CORUTV_OK;
     // pass 2
     CKS(gram(ex, pl, b, b.tmp, ld, b.tmp, ld, len, b.g, ex.cancel, tw));
-    CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, nullptr, ex.cancel, ex.st));
+    CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, nullptr, ex.cancel, ex.st, u));
     CK(launch_trsm_rows(b.tmp, tp, ld, len, ell, b.r, tw, q, ld, qc, tqc, ld, ex.cancel, ex.st));
     return CORUTV_OK;
 }

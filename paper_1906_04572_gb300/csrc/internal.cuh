@@ -106,14 +106,22 @@ cudaError_t launch_panel_to_rowmajor(const double* src, int64_t lds, int64_t row
 // R = chol(G) (upper, R^T R = G + shift I), FP64, one block; flags as above.
 // *skip_out (optional) is set to 0 when a shift was needed (so a third
 // CholeskyQR pass must run) and to 1 otherwise or when cancelled.
+// unit_roundoff: of the arithmetic G was formed in (2^-53 FP64, 2^-24 FP32);
+// it scales the shift. With `defic` (ell ints, written), a pivot at most
+// tau_rel times the largest diagonal entry marks its column numerically
+// dependent (defic[j] = 1, R row j = e_j) instead of failing.
 cudaError_t launch_cholesky(const double* g, int64_t ell, int64_t rows, double* r, int* flags,
-                            int* skip_out, const int* cancel, cudaStream_t st);
+                            int* skip_out, const int* cancel, cudaStream_t st,
+                            double unit_roundoff = 0x1p-53, int* defic = nullptr, double tau_rel = 0.0);
 // Q = C R^{-1} row by row (forward substitution with R^T), compute type tc;
 // c and q are panels of type tp; if qc != nullptr a copy of type tqc is
 // written too.
+// defic (optional, from launch_cholesky): dependent columns of Q are filled
+// with a seeded random completion.
 cudaError_t launch_trsm_rows(const void* c, ElemType tp, int64_t ldc, int64_t rows, int64_t ell,
                              const double* r, ElemType tc, void* q, int64_t ldq, void* qc,
-                             ElemType tqc, int64_t ldqc, const int* cancel, cudaStream_t st);
+                             ElemType tqc, int64_t ldqc, const int* cancel, cudaStream_t st,
+                             const int* defic = nullptr);
 // FP32 Gram G = X^T Y (row-major ell x ell FP64 output) of two FP32 panels
 // in one launch; split sums reduced in the kernel in a fixed order. work:
 // gram_f32_work_floats floats; cnt: gram_f32_counters ints, zero before the

@@ -84,8 +84,19 @@ __device__ __forceinline__ bool pos_finite(double d) {
 
 // Warp 0: row a of S holds G' with the updates of steps < a; make it row a of R.
 // Returns false (on every lane) when the pivot is not positive and finite.
-__device__ __forceinline__ bool chol_finish_row(double* S, int ld, int ell, int a, int lane) {
+// With `defic`, a pivot <= dmin marks column a numerically dependent instead:
+// R row a becomes e_a (so no later column uses it) and defic[a] = 1.
+__device__ __forceinline__ bool chol_finish_row(double* S, int ld, int ell, int a, int lane, int* defic,
+                                                double dmin) {
     const double d = S[a * ld + a];
+    if (defic && !(d > dmin)) {
+        for (int c = a + 1 + lane; c < ell; c += 32) S[a * ld + c] = 0.0;
+        if (lane == 0) {
+            S[a * ld + a] = 1.0;
+            defic[a] = 1;
+        }
+        return true;
+    }
     const bool ok = pos_finite(d);
     if (ok) {
         const double y = rsqrt_nr(d);
@@ -97,7 +108,7 @@ __device__ __forceinline__ bool chol_finish_row(double* S, int ld, int ell, int 
 
 __global__ void __launch_bounds__(kCholThreads)
 cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, int* skip_out,
-                const int* cancel) {
+                const int* cancel, double unit_roundoff, int* defic, double tau_rel) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (cancel && *cancel) {
         if (skip_out && tid == 0) *skip_out = 1;
@@ -106,13 +117,22 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
     extern __shared__ double S[];  // ell x (ell + 1) doubles, then the uint16 table
     const int ld = ell + 1;
     unsigned short* tri = reinterpret_cast<unsigned short*>(S + (size_t)ell * ld);
-    __shared__ double trace, ysh;
+    __shared__ double trace, ysh, dmin_s;
     __shared__ int fail_s;
     // table: bottom-up rows; row a holds columns ell-1 .. a
     for (int a = ell - 1 - tid; a >= 0; a -= kCholThreads) {
         const int rb = ell - 1 - a;            // rows below the top of the enumeration
         int e = rb * (rb + 1) / 2;
         for (int c = ell - 1; c >= a; --c) tri[e++] = (unsigned short)((a << 8) | c);
+    }
+    if (defic) {
+        // dependence threshold: tau_rel times the largest diagonal entry
+        for (int a = tid; a < ell; a += kCholThreads) defic[a] = 0;
+        if (tid == 0) {
+            double mx = 0.0;
+            for (int a = 0; a < ell; ++a) mx = fmax(mx, g[a * ell + a]);
+            dmin_s = tau_rel * mx;
+        }
     }
     const bool upd = warp != 0 && warp != 4;
     const int ut = upd ? (warp - (warp > 4 ? 2 : 1)) * 32 + lane : 0;  // 0 .. 191
@@ -121,7 +141,8 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
     for (; attempt < 3; ++attempt) {
         double shift = 0.0;
         if (attempt > 0) {
-            // shift s = 11 (rows ell + ell (ell + 1)) u ||C||_F^2 (u = 2^-53), then x100;
+            // shift s = 11 (rows ell + ell (ell + 1)) u ||C||_F^2, u the unit roundoff of the
+            // arithmetic that formed G (Fukaya et al.), then x100;
             // ||C||_F^2 = trace(G), summed only when a shift is needed
             if (tid == 0) {
                 double t = 0.0;
@@ -129,7 +150,7 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
                 trace = t;
             }
             __syncthreads();
-            const double u = 1.1102230246251565e-16;
+            const double u = unit_roundoff;
             shift = 11.0 * ((double)rows * ell + (double)ell * (ell + 1)) * u * trace * (attempt == 1 ? 1.0 : 100.0);
         }
         for (int e = tid; e < ell * ell; e += kCholThreads) {
@@ -138,7 +159,7 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
         }
         if (tid == 0) fail_s = 0;
         __syncthreads();
-        if (warp == 0 && !chol_finish_row(S, ld, ell, 0, lane) && lane == 0) fail_s = 1;
+        if (warp == 0 && !chol_finish_row(S, ld, ell, 0, lane, defic, dmin_s) && lane == 0) fail_s = 1;
         __syncthreads();
         fail = fail_s != 0;
         for (int j = 0; j + 1 < ell && !fail; ++j) {
@@ -147,12 +168,19 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
                 // pivot chain: d, 1/sqrt(d), diagonal of R (lanes redundant; one instruction each)
                 const double rjn = rj[j + 1];
                 const double d = fma(-rjn, rjn, S[(j + 1) * ld + j + 1]);
-                const bool ok = pos_finite(d);
-                const double y = ok ? rsqrt_nr(d) : 0.0;
+                const bool dep = defic && !(d > dmin_s);  // numerically dependent column j+1
+                const bool ok = dep || pos_finite(d);
+                const double y = (ok && !dep) ? rsqrt_nr(d) : 0.0;  // y = 0 zeroes the rest of row j+1
                 if (lane == 0) {
                     ysh = y;
-                    if (ok) S[(j + 1) * ld + j + 1] = d * y;  // d / sqrt(d)
-                    else fail_s = 1;
+                    if (dep) {
+                        S[(j + 1) * ld + j + 1] = 1.0;
+                        defic[j + 1] = 1;
+                    } else if (ok) {
+                        S[(j + 1) * ld + j + 1] = d * y;  // d / sqrt(d)
+                    } else {
+                        fail_s = 1;
+                    }
                 }
                 asm volatile("bar.sync 2, 64;" ::: "memory");
             } else if (warp == 4) {
@@ -216,6 +244,26 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
     }
 }
 
+// Entry (i, j) of a random completion column: N(0, 1) / sqrt(rows) from
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) of the counter (i, j), two
+// 53-bit uniforms and the cosine branch of Box-Muller. Only columns the
+// Cholesky found numerically dependent use it; any orthonormal completion is
+// a valid thin QR there, and the next CholeskyQR pass orthonormalises it.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__device__ __forceinline__ float completion_entry(int64_t i, int j, int64_t rows) {
+    const unsigned long long key = ((unsigned long long)i << 8) | (unsigned long long)(j & 0xff);
+    const unsigned long long h1 = splitmix64(2 * key), h2 = splitmix64(2 * key + 1);
+    const float u1 = (float)((double)((h1 >> 11) + 1) * 0x1p-53);  // (0, 1]
+    const float u2 = (float)((double)(h2 >> 11) * 0x1p-53);        // [0, 1)
+    return sqrtf(-2.f * logf(u1)) * cosf(6.2831853f * u2) * rsqrtf((float)rows);
+}
+
 // Row i of Q solves q_i R = c_i (R upper): q_i[j] = (c_i[j] - sum_{t<j} q_i[t] R[t][j]) / R[j][j].
 // Columns are solved in blocks of kTrsmB: the contributions of the columns
 // already solved go into kTrsmB independent accumulators (one shared load of
@@ -224,7 +272,8 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
 constexpr int kTrsmB = 8;
 template <typename TI, typename TC, typename TQC>
 __global__ void trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* r,
-                                 TI* q, int64_t ldq, TQC* qc, int64_t ldqc, const int* cancel) {
+                                 TI* q, int64_t ldq, TQC* qc, int64_t ldqc, const int* cancel,
+                                 const int* defic) {
     if (cancel && *cancel) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC* Rs = reinterpret_cast<TC*>(smem_raw);   // ell x ell row-major
@@ -286,7 +335,8 @@ __global__ void trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell
             if (k < nb) Ts[(j0 + k) * nthr + tid] = acc[k];
     }
     for (int j = 0; j < ell; ++j) {
-        const TC v = Ts[j * nthr + tid];
+        TC v = Ts[j * nthr + tid];
+        if (defic && defic[j]) v = (TC)completion_entry(i, j, rows);  // R row j is e_j: nothing else used q_j
         q[j * ldq + i] = (TI)v;
         if (qc) qc[j * ldqc + i] = (TQC)v;
     }
@@ -308,7 +358,7 @@ int trsm_threads(int ell, int64_t rows) {
 
 template <typename TI, typename TC, typename TQC>
 cudaError_t trsm_launch(const void* c, int64_t ldc, int64_t rows, int ell, const double* r, void* q, int64_t ldq,
-                        void* qc, int64_t ldqc, const int* cancel, cudaStream_t st) {
+                        void* qc, int64_t ldqc, const int* cancel, cudaStream_t st, const int* defic) {
     const int nthr = trsm_threads<TC>(ell, rows);
     const size_t smem = sizeof(TC) * ((size_t)ell * ell + (size_t)ell * nthr + (size_t)ell);
     cudaError_t e = cudaFuncSetAttribute(trsm_rows_kernel<TI, TC, TQC>,
@@ -318,18 +368,19 @@ cudaError_t trsm_launch(const void* c, int64_t ldc, int64_t rows, int ell, const
     count_launch();
     trsm_rows_kernel<TI, TC, TQC><<<blocks, nthr, smem, st>>>(static_cast<const TI*>(c), ldc, rows, ell, r,
                                                               static_cast<TI*>(q), ldq, static_cast<TQC*>(qc),
-                                                              ldqc, cancel);
+                                                              ldqc, cancel, defic);
     return cudaGetLastError();
 }
 
 template <typename TI, typename TC>
 cudaError_t trsm_dispatch(const void* c, int64_t ldc, int64_t rows, int ell, const double* r, void* q,
-                          int64_t ldq, void* qc, ElemType tqc, int64_t ldqc, const int* cancel, cudaStream_t st) {
-    if (!qc) return trsm_launch<TI, TC, TI>(c, ldc, rows, ell, r, q, ldq, nullptr, 0, cancel, st);
+                          int64_t ldq, void* qc, ElemType tqc, int64_t ldqc, const int* cancel, cudaStream_t st,
+                          const int* defic) {
+    if (!qc) return trsm_launch<TI, TC, TI>(c, ldc, rows, ell, r, q, ldq, nullptr, 0, cancel, st, defic);
     switch (tqc) {
-        case T_F64: return trsm_launch<TI, TC, double>(c, ldc, rows, ell, r, q, ldq, qc, ldqc, cancel, st);
-        case T_F32: return trsm_launch<TI, TC, float>(c, ldc, rows, ell, r, q, ldq, qc, ldqc, cancel, st);
-        case T_BF16: return trsm_launch<TI, TC, __nv_bfloat16>(c, ldc, rows, ell, r, q, ldq, qc, ldqc, cancel, st);
+        case T_F64: return trsm_launch<TI, TC, double>(c, ldc, rows, ell, r, q, ldq, qc, ldqc, cancel, st, defic);
+        case T_F32: return trsm_launch<TI, TC, float>(c, ldc, rows, ell, r, q, ldq, qc, ldqc, cancel, st, defic);
+        case T_BF16: return trsm_launch<TI, TC, __nv_bfloat16>(c, ldc, rows, ell, r, q, ldq, qc, ldqc, cancel, st, defic);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -635,23 +686,26 @@ __global__ void copy_small_kernel(const double* src, int n, TD* dst, const int* 
 }  // namespace
 
 cudaError_t launch_cholesky(const double* g, int64_t ell, int64_t rows, double* r, int* flags,
-                               int* skip_out, const int* cancel, cudaStream_t st) {
+                               int* skip_out, const int* cancel, cudaStream_t st, double unit_roundoff,
+                               int* defic, double tau_rel) {
     const size_t smem = sizeof(double) * (size_t)ell * (ell + 1) + sizeof(unsigned short) * (size_t)ell * (ell + 1) / 2;
     cudaError_t e = cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     count_launch();
-    cholesky_kernel<<<1, kCholThreads, smem, st>>>(g, (int)ell, rows, r, flags, skip_out, cancel);
+    cholesky_kernel<<<1, kCholThreads, smem, st>>>(g, (int)ell, rows, r, flags, skip_out, cancel, unit_roundoff,
+                                                   defic, tau_rel);
     return cudaGetLastError();
 }
 
 cudaError_t launch_trsm_rows(const void* c, ElemType tp, int64_t ldc, int64_t rows, int64_t ell,
                              const double* r, ElemType tc, void* q, int64_t ldq, void* qc,
-                             ElemType tqc, int64_t ldqc, const int* cancel, cudaStream_t st) {
+                             ElemType tqc, int64_t ldqc, const int* cancel, cudaStream_t st,
+                             const int* defic) {
     const int l = (int)ell;
-    if (tp == T_F64 && tc == T_F64) return trsm_dispatch<double, double>(c, ldc, rows, l, r, q, ldq, qc, tqc, ldqc, cancel, st);
-    if (tp == T_F64 && tc == T_F32) return trsm_dispatch<double, float>(c, ldc, rows, l, r, q, ldq, qc, tqc, ldqc, cancel, st);
-    if (tp == T_F32 && tc == T_F32) return trsm_dispatch<float, float>(c, ldc, rows, l, r, q, ldq, qc, tqc, ldqc, cancel, st);
+    if (tp == T_F64 && tc == T_F64) return trsm_dispatch<double, double>(c, ldc, rows, l, r, q, ldq, qc, tqc, ldqc, cancel, st, defic);
+    if (tp == T_F64 && tc == T_F32) return trsm_dispatch<double, float>(c, ldc, rows, l, r, q, ldq, qc, tqc, ldqc, cancel, st, defic);
+    if (tp == T_F32 && tc == T_F32) return trsm_dispatch<float, float>(c, ldc, rows, l, r, q, ldq, qc, tqc, ldqc, cancel, st, defic);
     return cudaErrorInvalidValue;
 }
 

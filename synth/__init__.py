@@ -65,6 +65,18 @@ def spectrum_matrix(m: int, n: int, sigma: np.ndarray, noise: float = 0.0,
     return np.ascontiguousarray(a)
 
 
+def spectrum_factors(m: int, n: int, sigma: np.ndarray, seed: int = 0) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """(U, sigma, V) of spectrum_matrix(m, n, sigma, 0.0, seed): the same Haar
+    factors (same generator, same draw order), so that a caller can form the
+    product U diag(sigma) V^T on a device for large sizes."""
+    rng = np.random.default_rng(seed)
+    sigma = np.asarray(sigma, dtype=np.float64)
+    r = sigma.shape[0]
+    u = haar(rng, m, r)
+    v = haar(rng, n, r)
+    return u, sigma, v
+
+
 def gaussian_psi(n: int, ell: int, seed: int = 0) -> np.ndarray:
     """Psi: n x ell with i.i.d. standard Gaussian entries (Sec. 3.1, Alg. 1
     step 1). Drawn here so that it can be injected into both implementations."""
@@ -219,6 +231,18 @@ def serving_matrix(req: Request, max_rank: int = 256) -> np.ndarray:
     r = min(req.m, req.n, max_rank)
     i = np.arange(1, r + 1, dtype=np.float64)
     return spectrum_matrix(req.m, req.n, i ** -1.5, 0.0, req.seed)
+
+
+def serving_factors(req: Request, max_rank: int = 256) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """(U, sigma, V) of serving_matrix(req, max_rank): the same Haar factors
+    (same generator, same draw order), so U diag(sigma) V^T is that matrix.
+    Lets a caller form the product on a device."""
+    r = min(req.m, req.n, max_rank)
+    sigma = np.arange(1, r + 1, dtype=np.float64) ** -1.5
+    rng = np.random.default_rng(req.seed)
+    u = haar(rng, req.m, r)
+    v = haar(rng, req.n, r)
+    return u, sigma, v
 
 
 def frob(x: np.ndarray) -> float:

@@ -284,6 +284,18 @@ def test_rpca_fixed_iterations_report_notconv(ctx):
     assert res["status"] == corutv.ENOTCONV and res["iters"] == 7
 
 
+def test_rpca_f32_past_convergence_keeps_shifting(ctx):
+    """Once L is exactly rank 5 the sketches (ell = 10) are rank-deficient and
+    their FP32 Gram matrices singular to FP32 rounding: the shift must be sized
+    by the FP32 unit roundoff, so the run continues instead of breaking down."""
+    pr = synth.rpca_problem(1200, 300, 5, 0.10, "uniform", seed=2, amplitude=50.0)
+    m = dev(pr.m_obs, torch.float32)
+    res = ctx.rpca(m, 5, tol=1e-30, max_iter=50, prec="f32", allow_notconv=True)
+    assert res["status"] == corutv.ENOTCONV and res["iters"] == 50
+    assert res["rank"] == 5
+    assert rel(host(res["L"]), pr.l_true) < 1e-4
+
+
 # ---------------------------------------------------------------- serving
 def test_serving_results_equal_alone_and_in_the_mix(ctx):
     rng = np.random.default_rng(0)
