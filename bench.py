@@ -47,6 +47,13 @@ WORKLOADS = {
 }
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one sketch-kernel
+# launch, measured with ncu on the 8000 x 6000 workload with bf16 sketches (mean of
+# the A X and A^T Y launches: 101.39 and 100.66 MB) against 97.68 MB of algorithmic
+# bytes. Only that workload and precision, as the kernel stands, have a figure.
+SKETCH_TRAFFIC_BYTES = {("c2", "bf16"): 101.02e6}
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -435,7 +442,8 @@ def run_ours(args):
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": gbs / peaks["hbm_gbs"], "peak_source": peaks_kind}
-    roof.update({"kernel": "sketch products A X / A^T Y (eqs. 4, 5)", "traffic": None,
+    roof.update({"kernel": "sketch products A X / A^T Y (eqs. 4, 5)",
+                 "traffic": SKETCH_TRAFFIC_BYTES.get((args.workload, prec)),
                  "bytes_per_launch": bytes_per_launch, "launch_ms": per_launch_ms,
                  "launches_timed": sk_n})
 
