@@ -265,58 +265,67 @@ __device__ __forceinline__ float completion_entry(int64_t i, int j, int64_t rows
 }
 
 // Row i of Q solves q_i R = c_i (R upper): q_i[j] = (c_i[j] - sum_{t<j} q_i[t] R[t][j]) / R[j][j].
-// Columns are solved in blocks of kTrsmB: the contributions of the columns
-// already solved go into kTrsmB independent accumulators (one shared load of
-// q_i[t] feeds all of them), then the small triangle inside the block is
-// finished in order. Row i is held in shared memory (one thread per row).
+// Four adjacent lanes share a row. Columns are solved in blocks of kTrsmB:
+// lane s adds the contributions of the solved columns t = s mod 4 into
+// kTrsmB independent accumulators, two xor shuffles combine the four partial
+// sums, and all four lanes finish the small triangle of the block in order
+// (redundantly), each storing its quarter of the new values. A block of 128
+// threads covers 32 rows, so a panel spreads over four times as many threads
+// as with one thread per row, each with about a third of the instructions.
 constexpr int kTrsmB = 8;
+constexpr int kTrsmL = 4;                        // lanes per row
+constexpr int kTrsmRows = 32;                    // rows per block
+constexpr int kTrsmThreads = kTrsmL * kTrsmRows;
 template <typename TI, typename TC, typename TQC>
-__global__ void trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* r,
-                                 TI* q, int64_t ldq, TQC* qc, int64_t ldqc, const int* cancel,
-                                 const int* defic) {
+__global__ void __launch_bounds__(kTrsmThreads)
+trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* r, TI* q, int64_t ldq,
+                 TQC* qc, int64_t ldqc, const int* cancel, const int* defic) {
     if (cancel && *cancel) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC* Rs = reinterpret_cast<TC*>(smem_raw);   // ell x ell row-major
-    const int nthr = blockDim.x;
-    TC* Ts = Rs + ell * ell;                      // [ell][nthr]
-    TC* Rd = Ts + (size_t)ell * nthr;             // 1 / R[j][j]
+    TC* Ts = Rs + ell * ell;                    // [ell][kTrsmRows]: a row's c values, then its q values
+    TC* Rd = Ts + (size_t)ell * kTrsmRows;      // 1 / R[j][j]
     const int tid = threadIdx.x;
+    const int ln = tid & (kTrsmL - 1), rr = tid / kTrsmL;
     // loads in batches of 16 per thread, all in flight before their stores
-    // (one at a time, each would wait out a full memory latency)
     constexpr int kB = 16;
-    for (int e0 = 0; e0 < ell * ell; e0 += kB * nthr) {
+    for (int e0 = 0; e0 < ell * ell; e0 += kB * kTrsmThreads) {
         double v[kB];
 #pragma unroll
         for (int u = 0; u < kB; ++u) {
-            const int e = e0 + u * nthr + tid;
+            const int e = e0 + u * kTrsmThreads + tid;
             v[u] = e < ell * ell ? r[e] : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < kB; ++u) {
-            const int e = e0 + u * nthr + tid;
+            const int e = e0 + u * kTrsmThreads + tid;
             if (e < ell * ell) Rs[e] = (TC)v[u];
         }
     }
-    for (int j = tid; j < ell; j += nthr) Rd[j] = (TC)1 / (TC)r[j * ell + j];
-    const int64_t i = (int64_t)blockIdx.x * nthr + tid;
-    if (i < rows)
-        for (int j0 = 0; j0 < ell; j0 += kB) {
-            TI v[kB];
+    for (int j = tid; j < ell; j += kTrsmThreads) Rd[j] = (TC)1 / (TC)r[j * ell + j];
+    const int64_t i = (int64_t)blockIdx.x * kTrsmRows + rr;
+    const bool live = i < rows;
+    for (int j0 = ln; j0 < ell; j0 += kTrsmL * kB) {  // lane ln loads columns ln, ln + 4, ...
+        TI v[kB];
 #pragma unroll
-            for (int u = 0; u < kB; ++u) v[u] = j0 + u < ell ? c[(j0 + u) * ldc + i] : (TI)0;
-#pragma unroll
-            for (int u = 0; u < kB; ++u)
-                if (j0 + u < ell) Ts[(j0 + u) * nthr + tid] = (TC)v[u];
+        for (int u = 0; u < kB; ++u) {
+            const int j = j0 + kTrsmL * u;
+            v[u] = (live && j < ell) ? c[(int64_t)j * ldc + i] : (TI)0;
         }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int j = j0 + kTrsmL * u;
+            if (j < ell) Ts[j * kTrsmRows + rr] = (TC)v[u];
+        }
+    }
     __syncthreads();
-    if (i >= rows) return;
     for (int j0 = 0; j0 < ell; j0 += kTrsmB) {
         const int nb = min(kTrsmB, ell - j0);
         TC acc[kTrsmB];
 #pragma unroll
-        for (int k = 0; k < kTrsmB; ++k) acc[k] = (k < nb) ? Ts[(j0 + k) * nthr + tid] : (TC)0;
-        for (int t = 0; t < j0; ++t) {
-            const TC qt = Ts[t * nthr + tid];
+        for (int k = 0; k < kTrsmB; ++k) acc[k] = (ln == 0 && k < nb) ? Ts[(j0 + k) * kTrsmRows + rr] : (TC)0;
+        for (int t = ln; t < j0; t += kTrsmL) {
+            const TC qt = Ts[t * kTrsmRows + rr];
             const TC* rrow = Rs + t * ell + j0;
 #pragma unroll
             for (int k = 0; k < kTrsmB; ++k)
@@ -324,51 +333,44 @@ __global__ void trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell
         }
 #pragma unroll
         for (int k = 0; k < kTrsmB; ++k) {
-            if (k >= nb) break;
-            TC s = acc[k];
-#pragma unroll
-            for (int kk = 0; kk < k; ++kk) s -= acc[kk] * Rs[(j0 + kk) * ell + j0 + k];
-            acc[k] = s * Rd[j0 + k];
+            acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 1);
+            acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 2);
         }
 #pragma unroll
+        for (int k = 0; k < kTrsmB; ++k) {
+            if (k >= nb) break;
+            TC sum = acc[k];
+#pragma unroll
+            for (int kk = 0; kk < k; ++kk) sum -= acc[kk] * Rs[(j0 + kk) * ell + j0 + k];
+            acc[k] = sum * Rd[j0 + k];
+        }
+        __syncwarp();  // the row's lanes have read their c values before any is overwritten
+#pragma unroll
         for (int k = 0; k < kTrsmB; ++k)
-            if (k < nb) Ts[(j0 + k) * nthr + tid] = acc[k];
+            if (k < nb && (k & (kTrsmL - 1)) == ln) Ts[(j0 + k) * kTrsmRows + rr] = acc[k];
+        __syncwarp();
     }
-    for (int j = 0; j < ell; ++j) {
-        TC v = Ts[j * nthr + tid];
+    if (!live) return;
+    for (int j = ln; j < ell; j += kTrsmL) {
+        TC v = Ts[j * kTrsmRows + rr];
         if (defic && defic[j]) v = (TC)completion_entry(i, j, rows);  // R row j is e_j: nothing else used q_j
-        q[j * ldq + i] = (TI)v;
-        if (qc) qc[j * ldqc + i] = (TQC)v;
+        q[(int64_t)j * ldq + i] = (TI)v;
+        if (qc) qc[(int64_t)j * ldqc + i] = (TQC)v;
     }
-}
-
-// Threads (= rows) per block: up to 128, bounded by shared memory. A row's
-// solve is a dependent chain; more, smaller blocks spread a panel over more
-// SMs at the price of loading R once per 128 rows.
-template <typename TC>
-int trsm_threads(int ell, int64_t rows) {
-    const long budget = 200 * 1024;
-    long per = (budget - (long)ell * (ell + 1) * (long)sizeof(TC)) / ((long)ell * (long)sizeof(TC));
-    per = per / 32 * 32;
-    if (per > 128) per = 128;  // more blocks: an 8000-row panel spreads over ~60 SMs instead of ~30
-    if (per < 32) per = 32;
-    (void)rows;
-    return (int)per;
 }
 
 template <typename TI, typename TC, typename TQC>
 cudaError_t trsm_launch(const void* c, int64_t ldc, int64_t rows, int ell, const double* r, void* q, int64_t ldq,
                         void* qc, int64_t ldqc, const int* cancel, cudaStream_t st, const int* defic) {
-    const int nthr = trsm_threads<TC>(ell, rows);
-    const size_t smem = sizeof(TC) * ((size_t)ell * ell + (size_t)ell * nthr + (size_t)ell);
+    const size_t smem = sizeof(TC) * ((size_t)ell * ell + (size_t)ell * kTrsmRows + (size_t)ell);
     cudaError_t e = cudaFuncSetAttribute(trsm_rows_kernel<TI, TC, TQC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const unsigned blocks = (unsigned)((rows + nthr - 1) / nthr);
+    const unsigned blocks = (unsigned)((rows + kTrsmRows - 1) / kTrsmRows);
     count_launch();
-    trsm_rows_kernel<TI, TC, TQC><<<blocks, nthr, smem, st>>>(static_cast<const TI*>(c), ldc, rows, ell, r,
-                                                              static_cast<TI*>(q), ldq, static_cast<TQC*>(qc),
-                                                              ldqc, cancel, defic);
+    trsm_rows_kernel<TI, TC, TQC><<<blocks, kTrsmThreads, smem, st>>>(static_cast<const TI*>(c), ldc, rows, ell, r,
+                                                                      static_cast<TI*>(q), ldq,
+                                                                      static_cast<TQC*>(qc), ldqc, cancel, defic);
     return cudaGetLastError();
 }
 
