@@ -74,6 +74,32 @@ int device_sms();
 // Counts every kernel launch issued by this library (instrumentation).
 void count_launch();
 
+// Programmatic dependent launch. Every kernel of the library is launched with
+// programmatic stream serialisation, so the next kernel in a stream can be
+// scheduled while the previous one finishes instead of after it. Each kernel
+// calls pdl_trigger() first (its successor may then launch once all of its
+// blocks are running) and pdl_wait() before it reads anything an earlier
+// kernel wrote (the wait returns when the predecessor has completed and its
+// writes are visible; it is a no-op for a launch without the attribute).
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
 // Sets the calling thread's message returned by corutv_last_error().
 void record_error(const char* msg);
 

@@ -61,6 +61,7 @@ __device__ __forceinline__ double f2d_exact(float f) {
 __global__ void __launch_bounds__(kGThreads)
 gram_f32_kernel(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_t len, int ell, double* out,
                 float* cpart, int* cnt, GramPlan pl, const int* cancel) {
+    pdl_wait();
     namespace cg = cooperative_groups;
     if (cancel && *cancel) return;  // uniform over the grid: no cluster barrier is left waiting
     cg::cluster_group cluster = cg::this_cluster();
@@ -122,6 +123,7 @@ gram_f32_kernel(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_
         }
         __syncthreads();
     }
+    pdl_trigger();  // the successor may launch during the reductions
     // the partial of this range stays in shared memory (row-major 64 x 64)
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -191,13 +193,15 @@ cudaError_t launch_gram_f32(const float* x, int64_t ldx, const float* y, int64_t
     cfg.blockDim = dim3(kGThreads, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = kGCluster;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     count_launch();
     return cudaLaunchKernelEx(&cfg, gram_f32_kernel, x, ldx, y, ldy, len, ell, out, work, cnt, p, cancel);
 }

@@ -109,6 +109,7 @@ __device__ __forceinline__ bool chol_finish_row(double* S, int ld, int ell, int 
 __global__ void __launch_bounds__(kCholThreads)
 cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, int* skip_out,
                 const int* cancel, double unit_roundoff, int* defic, double tau_rel) {
+    pdl_wait();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (cancel && *cancel) {
         if (skip_out && tid == 0) *skip_out = 1;
@@ -230,6 +231,7 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
         if (!fail) break;
         __syncthreads();
     }
+    pdl_trigger();  // the successor may launch while R is written
     const bool broke = attempt == 3;
     for (int e = tid; e < ell * ell; e += kCholThreads) {
         const int a = e / ell, b = e % ell;
@@ -280,6 +282,7 @@ template <typename TI, typename TC, typename TQC>
 __global__ void __launch_bounds__(kTrsmThreads)
 trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* r, TI* q, int64_t ldq,
                  TQC* qc, int64_t ldqc, const int* cancel, const int* defic) {
+    pdl_wait();
     if (cancel && *cancel) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC* Rs = reinterpret_cast<TC*>(smem_raw);   // ell x ell row-major
@@ -350,6 +353,7 @@ trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* 
             if (k < nb && (k & (kTrsmL - 1)) == ln) Ts[(j0 + k) * kTrsmRows + rr] = acc[k];
         __syncwarp();
     }
+    pdl_trigger();  // the successor may launch while Q is written
     if (!live) return;
     for (int j = ln; j < ell; j += kTrsmL) {
         TC v = Ts[j * kTrsmRows + rr];
@@ -368,9 +372,12 @@ cudaError_t trsm_launch(const void* c, int64_t ldc, int64_t rows, int ell, const
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((rows + kTrsmRows - 1) / kTrsmRows);
     count_launch();
-    trsm_rows_kernel<TI, TC, TQC><<<blocks, kTrsmThreads, smem, st>>>(static_cast<const TI*>(c), ldc, rows, ell, r,
+    {
+        cudaError_t pe_ = launch_pdl(trsm_rows_kernel<TI, TC, TQC>, dim3(blocks), dim3(kTrsmThreads), (size_t)(smem), st, static_cast<const TI*>(c), ldc, rows, ell, r,
                                                                       static_cast<TI*>(q), ldq,
                                                                       static_cast<TQC*>(qc), ldqc, cancel, defic);
+        if (pe_ != cudaSuccess) return pe_;
+    }
     return cudaGetLastError();
 }
 
@@ -450,6 +457,7 @@ __device__ __forceinline__ int qr_pivot(const double* nrm, int j, int ell, int l
 
 __global__ void __launch_bounds__(kQrcpThreads)
 qrcp_kernel(const double* d, int ell, double* refl, double* rt, int* perm, const int* cancel) {
+    pdl_wait();
     if (cancel && *cancel) return;
     extern __shared__ double W[];  // ell columns of ldw doubles, then nrm, xbuf, tau, sgn, tdot, perm
     const int ldw = ell | 1;
@@ -598,6 +606,7 @@ qrcp_kernel(const double* d, int ell, double* refl, double* rt, int* perm, const
     }
     for (int c = tid; c < ell; c += kQrcpThreads) perm[c] = pv[c];
     __syncthreads();
+    pdl_trigger();  // the Q formation may launch while the reflectors are written
     // reflectors for the Q formation: V column-major (v_j below the diagonal of
     // column j, zero elsewhere), then tau, then the column signs of Qt
     for (int e = tid; e < ell * ell; e += kQrcpThreads) {
@@ -620,6 +629,7 @@ constexpr int kQformWarps = 8;
 
 __global__ void __launch_bounds__(kQformWarps * 32)
 qform_kernel(const double* refl, int ell, double* qt, const int* cancel) {
+    pdl_wait();
     if (cancel && *cancel) return;
     extern __shared__ double Vs[];  // ell * ell + 2 * ell
     const int n = ell * ell + 2 * ell;
@@ -650,6 +660,7 @@ qform_kernel(const double* refl, int ell, double* qt, const int* cancel) {
             if (i >= k && i < ell) q[t] = fma(-f, i == k ? 1.0 : v[i], q[t]);
         }
     }
+    pdl_trigger();
     const double sc = sgn[c];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -661,6 +672,8 @@ qform_kernel(const double* refl, int ell, double* qt, const int* cancel) {
 template <typename TQ, typename TV>
 __global__ void gather_v_kernel(const TQ* q2, int64_t ldq2, int64_t n, int ell, const int* perm,
                                 TV* v, int64_t ldv, const int* cancel) {
+    pdl_trigger();
+    pdl_wait();
     if (cancel && *cancel) return;
     __shared__ double tile[128][33];
     const int64_t i0 = (int64_t)blockIdx.x * 32;
@@ -680,6 +693,8 @@ __global__ void gather_v_kernel(const TQ* q2, int64_t ldq2, int64_t n, int ell, 
 
 template <typename TD>
 __global__ void copy_small_kernel(const double* src, int n, TD* dst, const int* cancel) {
+    pdl_trigger();
+    pdl_wait();
     if (cancel && *cancel) return;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
         dst[e] = (TD)src[e];
@@ -695,8 +710,11 @@ cudaError_t launch_cholesky(const double* g, int64_t ell, int64_t rows, double* 
                                          (int)smem);
     if (e != cudaSuccess) return e;
     count_launch();
-    cholesky_kernel<<<1, kCholThreads, smem, st>>>(g, (int)ell, rows, r, flags, skip_out, cancel, unit_roundoff,
+    {
+        cudaError_t pe_ = launch_pdl(cholesky_kernel, dim3(1), dim3(kCholThreads), (size_t)(smem), st, g, (int)ell, rows, r, flags, skip_out, cancel, unit_roundoff,
                                                    defic, tau_rel);
+        if (pe_ != cudaSuccess) return pe_;
+    }
     return cudaGetLastError();
 }
 
@@ -718,15 +736,21 @@ cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, in
     cudaError_t e = cudaFuncSetAttribute(qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launch();
-    qrcp_kernel<<<1, kQrcpThreads, smem, st>>>(d, (int)ell, work, rt, perm, cancel);
+    {
+        cudaError_t pe_ = launch_pdl(qrcp_kernel, dim3(1), dim3(kQrcpThreads), (size_t)(smem), st, d, (int)ell, work, rt, perm, cancel);
+        if (pe_ != cudaSuccess) return pe_;
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem_q = sizeof(double) * (size_t)(ell * ell + 2 * ell);
     e = cudaFuncSetAttribute(qform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_q);
     if (e != cudaSuccess) return e;
     count_launch();
-    qform_kernel<<<(unsigned)((ell + kQformWarps - 1) / kQformWarps), kQformWarps * 32, smem_q, st>>>(work, (int)ell,
+    {
+        cudaError_t pe_ = launch_pdl(qform_kernel, dim3((unsigned)((ell + kQformWarps - 1) / kQformWarps)), dim3(kQformWarps * 32), (size_t)(smem_q), st, work, (int)ell,
                                                                                                    qt, cancel);
+        if (pe_ != cudaSuccess) return pe_;
+    }
     return cudaGetLastError();
 }
 
@@ -735,17 +759,29 @@ cudaError_t launch_gather_v(const void* q2, ElemType tq2, int64_t ldq2, int64_t 
     const unsigned blocks = (unsigned)((n + 31) / 32);
     count_launch();
     if (tq2 == T_F64 && tv == T_F64)
-        gather_v_kernel<double, double><<<blocks, 256, 0, st>>>(static_cast<const double*>(q2), ldq2, n, (int)ell,
+        {
+            cudaError_t pe_ = launch_pdl(gather_v_kernel<double, double>, dim3(blocks), dim3(256), (size_t)(0), st, static_cast<const double*>(q2), ldq2, n, (int)ell,
                                                                 perm, static_cast<double*>(v), ldv, cancel);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     else if (tq2 == T_F64)
-        gather_v_kernel<double, float><<<blocks, 256, 0, st>>>(static_cast<const double*>(q2), ldq2, n, (int)ell,
+        {
+            cudaError_t pe_ = launch_pdl(gather_v_kernel<double, float>, dim3(blocks), dim3(256), (size_t)(0), st, static_cast<const double*>(q2), ldq2, n, (int)ell,
                                                                perm, static_cast<float*>(v), ldv, cancel);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     else if (tv == T_F64)
-        gather_v_kernel<float, double><<<blocks, 256, 0, st>>>(static_cast<const float*>(q2), ldq2, n, (int)ell,
+        {
+            cudaError_t pe_ = launch_pdl(gather_v_kernel<float, double>, dim3(blocks), dim3(256), (size_t)(0), st, static_cast<const float*>(q2), ldq2, n, (int)ell,
                                                                perm, static_cast<double*>(v), ldv, cancel);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     else
-        gather_v_kernel<float, float><<<blocks, 256, 0, st>>>(static_cast<const float*>(q2), ldq2, n, (int)ell,
+        {
+            cudaError_t pe_ = launch_pdl(gather_v_kernel<float, float>, dim3(blocks), dim3(256), (size_t)(0), st, static_cast<const float*>(q2), ldq2, n, (int)ell,
                                                               perm, static_cast<float*>(v), ldv, cancel);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     return cudaGetLastError();
 }
 
@@ -754,10 +790,16 @@ cudaError_t launch_copy_small(const double* src, int64_t ell, void* dst, ElemTyp
     const int n = (int)(ell * ell);
     if (tdst == T_F64) {
         count_launch();
-        copy_small_kernel<double><<<(n + 255) / 256, 256, 0, st>>>(src, n, static_cast<double*>(dst), cancel);
+        {
+            cudaError_t pe_ = launch_pdl(copy_small_kernel<double>, dim3((n + 255) / 256), dim3(256), (size_t)(0), st, src, n, static_cast<double*>(dst), cancel);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     } else {
         count_launch();
-        copy_small_kernel<float><<<(n + 255) / 256, 256, 0, st>>>(src, n, static_cast<float*>(dst), cancel);
+        {
+            cudaError_t pe_ = launch_pdl(copy_small_kernel<float>, dim3((n + 255) / 256), dim3(256), (size_t)(0), st, src, n, static_cast<float*>(dst), cancel);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     }
     return cudaGetLastError();
 }

@@ -44,6 +44,8 @@ __device__ __forceinline__ double ld_m(const void* m, int64_t off) {
 template <typename TM, typename TS>
 __global__ void rpca_init_kernel(const TM* m, int64_t ldm, int64_t rows, int64_t cols, TS* s, TS* y,
                                  TS* b, double* fro_part) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ double red[32];
     double acc = 0.0;
     const int64_t total = rows * cols;
@@ -65,6 +67,8 @@ template <typename TQ>
 __global__ void rank_z_kernel(const double* rt, const TQ* q2, int64_t ldq2, const int* perm,
                               int64_t cols, int ell, double inv_mu, int* rank, double* z, int64_t ldz,
                               const int* cancel) {
+    pdl_trigger();
+    pdl_wait();
     if (cancel && *cancel) return;
     __shared__ double Rs[kMaxEll * kMaxEll];
     __shared__ int ps[kMaxEll];
@@ -99,6 +103,8 @@ __global__ void __launch_bounds__(kUpdCols)
 rpca_update_kernel(const TM* m, int64_t ldm, int64_t rows, int64_t cols, TS* s, TS* y, TS* b,
                    const double* u, int64_t ldu, const double* z, int64_t ldz, int ell, const int* rank,
                    double mu, double mu_next, double lambda, double* res_part, const int* cancel) {
+    pdl_trigger();
+    pdl_wait();
     if (cancel && *cancel) return;
     __shared__ double red[32];
     __shared__ double Us[kUpdRows][kMaxEll];
@@ -145,6 +151,8 @@ rpca_update_kernel(const TM* m, int64_t ldm, int64_t rows, int64_t cols, TS* s, 
 // zeta_j and the convergence flag; one block, fixed summation order.
 __global__ void finish_iter_kernel(const double* res_part, int nparts, const double* fro_part, int nfro,
                                    double tol, int iter, double* zeta_hist, int* flags, const int* rank) {
+    pdl_trigger();
+    pdl_wait();
     if (flags[FLAG_RPCA_DONE]) return;
     __shared__ double red[32];
     double a = 0.0, f = 0.0;
@@ -165,6 +173,8 @@ template <typename TL>
 __global__ void __launch_bounds__(kUpdCols)
 reconstruct_kernel(const double* u, int64_t ldu, const double* z, int64_t ldz, const int* rank, int ell,
                    int64_t rows, int64_t cols, TL* lout, int64_t ldl) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ double Us[kUpdRows][kMaxEll];
     const int r = *rank;
     const int64_t i0 = (int64_t)blockIdx.y * kUpdRows;
@@ -196,11 +206,15 @@ int init_blocks(int64_t total) {
 }
 
 __global__ void vec_fill_kernel(double* v, int64_t n, double value) {
+    pdl_trigger();
+    pdl_wait();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         v[i] = value;
 }
 
 __global__ void vec_normalize_kernel(const double* w, double* v, int64_t n, double* lam) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ double red[32];
     __shared__ double nrm;
     double a = 0.0;
@@ -219,13 +233,19 @@ __global__ void vec_normalize_kernel(const double* w, double* v, int64_t n, doub
 
 cudaError_t launch_vec_fill(double* v, int64_t n, double value, cudaStream_t st) {
     count_launch();
-    vec_fill_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(v, n, value);
+    {
+        cudaError_t pe_ = launch_pdl(vec_fill_kernel, dim3((unsigned)std::min<int64_t>((n + 255) / 256, 1024)), dim3(256), (size_t)(0), st, v, n, value);
+        if (pe_ != cudaSuccess) return pe_;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_vec_normalize(const double* w, double* v, int64_t n, double* lam, cudaStream_t st) {
     count_launch();
-    vec_normalize_kernel<<<1, 1024, 0, st>>>(w, v, n, lam);
+    {
+        cudaError_t pe_ = launch_pdl(vec_normalize_kernel, dim3(1), dim3(1024), (size_t)(0), st, w, v, n, lam);
+        if (pe_ != cudaSuccess) return pe_;
+    }
     return cudaGetLastError();
 }
 
@@ -240,12 +260,18 @@ cudaError_t launch_rpca_init(const void* m, ElemType tm, int64_t ldm, int64_t ro
     *nparts = blocks;
     if (tm == T_F32) {
         count_launch();
-        rpca_init_kernel<float, float><<<blocks, 256, 0, st>>>(static_cast<const float*>(m), ldm, rows, cols,
+        {
+            cudaError_t pe_ = launch_pdl(rpca_init_kernel<float, float>, dim3(blocks), dim3(256), (size_t)(0), st, static_cast<const float*>(m), ldm, rows, cols,
                                                                s, y, b, fro_part);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     } else {
         count_launch();
-        rpca_init_kernel<double, double><<<blocks, 256, 0, st>>>(static_cast<const double*>(m), ldm, rows,
+        {
+            cudaError_t pe_ = launch_pdl(rpca_init_kernel<double, double>, dim3(blocks), dim3(256), (size_t)(0), st, static_cast<const double*>(m), ldm, rows,
                                                                  cols, s64, y64, b64, fro_part);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     }
     return cudaGetLastError();
 }
@@ -257,11 +283,17 @@ cudaError_t launch_rpca_rank_z(const double* rt, const void* vq2, ElemType tq2, 
     const unsigned blocks = (unsigned)((cols + 127) / 128);
     count_launch();
     if (tq2 == T_F64)
-        rank_z_kernel<double><<<blocks, 128, 0, st>>>(rt, static_cast<const double*>(vq2), ldv, perm, cols, (int)ell,
+        {
+            cudaError_t pe_ = launch_pdl(rank_z_kernel<double>, dim3(blocks), dim3(128), (size_t)(0), st, rt, static_cast<const double*>(vq2), ldv, perm, cols, (int)ell,
                                                       inv_mu, rank, z, ldz, cancel);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     else
-        rank_z_kernel<float><<<blocks, 128, 0, st>>>(rt, static_cast<const float*>(vq2), ldv, perm, cols, (int)ell,
+        {
+            cudaError_t pe_ = launch_pdl(rank_z_kernel<float>, dim3(blocks), dim3(128), (size_t)(0), st, rt, static_cast<const float*>(vq2), ldv, perm, cols, (int)ell,
                                                      inv_mu, rank, z, ldz, cancel);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     return cudaGetLastError();
 }
 
@@ -271,14 +303,20 @@ cudaError_t launch_rpca_update(const RpcaIterArgs& a, int* nparts, cudaStream_t 
     *nparts = (int)(grid.x * grid.y);
     if (a.tm == T_F32) {
         count_launch();
-        rpca_update_kernel<float, float><<<grid, kUpdCols, 0, st>>>(
+        {
+            cudaError_t pe_ = launch_pdl(rpca_update_kernel<float, float>, dim3(grid), dim3(kUpdCols), (size_t)(0), st, 
             static_cast<const float*>(a.m), a.ldm, a.rows, a.cols, a.s, a.y, a.b, a.u, a.ldu, a.z, a.ldz,
             (int)a.ell, a.rank, a.mu, a.mu_next, a.lambda, a.res_part, a.cancel);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     } else {
         count_launch();
-        rpca_update_kernel<double, double><<<grid, kUpdCols, 0, st>>>(
+        {
+            cudaError_t pe_ = launch_pdl(rpca_update_kernel<double, double>, dim3(grid), dim3(kUpdCols), (size_t)(0), st, 
             static_cast<const double*>(a.m), a.ldm, a.rows, a.cols, a.s64, a.y64, a.b64, a.u, a.ldu, a.z,
             a.ldz, (int)a.ell, a.rank, a.mu, a.mu_next, a.lambda, a.res_part, a.cancel);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     }
     return cudaGetLastError();
 }
@@ -287,8 +325,11 @@ cudaError_t launch_rpca_finish_iter(const double* res_part, int nparts, const do
                                     int nfro, double tol, int iter, double* zeta_hist,
                                     int* flags, const int* rank, cudaStream_t st) {
     count_launch();
-    finish_iter_kernel<<<1, kFinalThreads, 0, st>>>(res_part, nparts, fro_part, nfro, tol, iter, zeta_hist,
+    {
+        cudaError_t pe_ = launch_pdl(finish_iter_kernel, dim3(1), dim3(kFinalThreads), (size_t)(0), st, res_part, nparts, fro_part, nfro, tol, iter, zeta_hist,
                                                     flags, rank);
+        if (pe_ != cudaSuccess) return pe_;
+    }
     return cudaGetLastError();
 }
 
@@ -299,12 +340,18 @@ cudaError_t launch_rpca_reconstruct(const double* u, int64_t ldu, const double* 
     dim3 grid((unsigned)((cols + kUpdCols - 1) / kUpdCols), (unsigned)((rows + kUpdRows - 1) / kUpdRows));
     if (tl == T_F32) {
         count_launch();
-        reconstruct_kernel<float><<<grid, kUpdCols, 0, st>>>(u, ldu, z, ldz, rank, (int)ell, rows, cols,
+        {
+            cudaError_t pe_ = launch_pdl(reconstruct_kernel<float>, dim3(grid), dim3(kUpdCols), (size_t)(0), st, u, ldu, z, ldz, rank, (int)ell, rows, cols,
                                                              static_cast<float*>(lout), ldl);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     } else {
         count_launch();
-        reconstruct_kernel<double><<<grid, kUpdCols, 0, st>>>(u, ldu, z, ldz, rank, (int)ell, rows, cols,
+        {
+            cudaError_t pe_ = launch_pdl(reconstruct_kernel<double>, dim3(grid), dim3(kUpdCols), (size_t)(0), st, u, ldu, z, ldz, rank, (int)ell, rows, cols,
                                                               static_cast<double*>(lout), ldl);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     }
     return cudaGetLastError();
 }

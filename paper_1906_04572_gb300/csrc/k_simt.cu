@@ -48,6 +48,8 @@ __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, float>(float v) { re
 // conflicts on the B tile).
 template <typename TA, typename TB, typename TC, int TN>
 __global__ void __launch_bounds__(kThreads) gemm_simt_kernel(GemmArgs g) {
+    pdl_trigger();
+    pdl_wait();
     if (g.cancel && *g.cancel) return;
     constexpr int LP = 16 * TN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -131,7 +133,10 @@ cudaError_t launch_tn(const GemmArgs& g, cudaStream_t st) {
     }
     dim3 grid((unsigned)((g.R + kBM - 1) / kBM), (unsigned)g.splits);
     count_launch();
-    gemm_simt_kernel<TA, TB, TC, TN><<<grid, kThreads, smem, st>>>(g);
+    {
+        cudaError_t pe_ = launch_pdl(gemm_simt_kernel<TA, TB, TC, TN>, dim3(grid), dim3(kThreads), (size_t)(smem), st, g);
+        if (pe_ != cudaSuccess) return pe_;
+    }
     return cudaGetLastError();
 }
 
@@ -192,6 +197,8 @@ template <typename TP, typename TO>
 __global__ void __launch_bounds__(32 * kRedGroups)
 reduce_splits_kernel(const TP* part, int splits, int64_t stride, TO* out, int64_t ld, int64_t rows,
                      int64_t cols, int64_t ld_out, const int* cancel) {
+    pdl_trigger();
+    pdl_wait();
     if (cancel && *cancel) return;
     __shared__ double red[kRedGroups][33];
     const int tx = threadIdx.x & 31, g = threadIdx.x >> 5;
@@ -227,9 +234,12 @@ cudaError_t reduce_launch(const void* part, int splits, int64_t stride, void* ou
                           int64_t cols, int64_t ld_out, const int* cancel, cudaStream_t st) {
     const unsigned blocks = (unsigned)((rows * cols + 31) / 32);
     count_launch();
-    reduce_splits_kernel<TP, TO><<<blocks, 32 * kRedGroups, 0, st>>>(static_cast<const TP*>(part), splits, stride,
+    {
+        cudaError_t pe_ = launch_pdl(reduce_splits_kernel<TP, TO>, dim3(blocks), dim3(32 * kRedGroups), (size_t)(0), st, static_cast<const TP*>(part), splits, stride,
                                                                      static_cast<TO*>(out), ld, rows, cols, ld_out,
                                                                      cancel);
+        if (pe_ != cudaSuccess) return pe_;
+    }
     return cudaGetLastError();
 }
 }  // namespace
@@ -282,6 +292,8 @@ __device__ __forceinline__ double gauss_at(uint64_t seed, uint32_t sid, uint32_t
 template <typename TX>
 __global__ void gaussian_panel_kernel(uint64_t seed, uint32_t sid, int64_t n, int64_t ell,
                                       int64_t ellp, TX* x, int64_t ldx, const int* cancel) {
+    pdl_trigger();
+    pdl_wait();
     if (cancel && *cancel) return;
     const int64_t total = n * ellp;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -293,6 +305,8 @@ __global__ void gaussian_panel_kernel(uint64_t seed, uint32_t sid, int64_t n, in
 
 __global__ void gaussian_rowmajor_kernel(uint64_t seed, uint32_t sid, int64_t n, int64_t ell,
                                          double* psi, int64_t ld) {
+    pdl_trigger();
+    pdl_wait();
     const int64_t total = n * ell;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -314,18 +328,27 @@ cudaError_t launch_gaussian_panel(uint64_t seed, uint32_t stream_id, int64_t n, 
                                   cudaStream_t st) {
     count_launch();
     if (tx == T_F64)
-        gaussian_panel_kernel<double><<<grid_for(n * ellp), 256, 0, st>>>(seed, stream_id, n, ell, ellp,
+        {
+            cudaError_t pe_ = launch_pdl(gaussian_panel_kernel<double>, dim3(grid_for(n * ellp)), dim3(256), (size_t)(0), st, seed, stream_id, n, ell, ellp,
                                                                           static_cast<double*>(x), ldx, cancel);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     else
-        gaussian_panel_kernel<float><<<grid_for(n * ellp), 256, 0, st>>>(seed, stream_id, n, ell, ellp,
+        {
+            cudaError_t pe_ = launch_pdl(gaussian_panel_kernel<float>, dim3(grid_for(n * ellp)), dim3(256), (size_t)(0), st, seed, stream_id, n, ell, ellp,
                                                                          static_cast<float*>(x), ldx, cancel);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     return cudaGetLastError();
 }
 
 cudaError_t launch_gaussian_rowmajor(uint64_t seed, uint32_t stream_id, int64_t n, int64_t ell,
                                      double* psi, int64_t ld, cudaStream_t st) {
     count_launch();
-    gaussian_rowmajor_kernel<<<grid_for(n * ell), 256, 0, st>>>(seed, stream_id, n, ell, psi, ld);
+    {
+        cudaError_t pe_ = launch_pdl(gaussian_rowmajor_kernel, dim3(grid_for(n * ell)), dim3(256), (size_t)(0), st, seed, stream_id, n, ell, psi, ld);
+        if (pe_ != cudaSuccess) return pe_;
+    }
     return cudaGetLastError();
 }
 
@@ -341,6 +364,8 @@ template <typename TD>
 __global__ void transpose_kernel(const double* src, int64_t lds, int64_t rows, int64_t cols,
                                  int64_t colsp, TD* dst, int64_t ldd, bool to_panel,
                                  const int* cancel) {
+    pdl_trigger();
+    pdl_wait();
     if (cancel && *cancel) return;
     __shared__ double tile[32][33];
     const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
@@ -371,6 +396,8 @@ __global__ void transpose_kernel(const double* src, int64_t lds, int64_t rows, i
 template <typename TS, typename TD>
 __global__ void panel_convert_kernel(const TS* src, int64_t lds, int64_t rows, int64_t cols,
                                      TD* dst, int64_t ldd, const int* cancel) {
+    pdl_trigger();
+    pdl_wait();
     if (cancel && *cancel) return;
     const int64_t total = rows * cols;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -386,11 +413,17 @@ cudaError_t launch_rowmajor_to_panel(const double* src, int64_t lds, int64_t row
     dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((colsp + 31) / 32));
     count_launch();
     if (tdst == T_F64)
-        transpose_kernel<double><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, cols, colsp, static_cast<double*>(dst),
+        {
+            cudaError_t pe_ = launch_pdl(transpose_kernel<double>, dim3(grid), dim3(dim3(32, 8)), (size_t)(0), st, src, lds, rows, cols, colsp, static_cast<double*>(dst),
                                                                ldd, true, nullptr);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     else
-        transpose_kernel<float><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, cols, colsp, static_cast<float*>(dst),
+        {
+            cudaError_t pe_ = launch_pdl(transpose_kernel<float>, dim3(grid), dim3(dim3(32, 8)), (size_t)(0), st, src, lds, rows, cols, colsp, static_cast<float*>(dst),
                                                               ldd, true, nullptr);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     return cudaGetLastError();
 }
 
@@ -400,14 +433,20 @@ cudaError_t launch_panel_to_rowmajor(const double* src, int64_t lds, int64_t row
     dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
     if (tdst == T_F64) {
         count_launch();
-        transpose_kernel<double><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, cols, cols,
+        {
+            cudaError_t pe_ = launch_pdl(transpose_kernel<double>, dim3(grid), dim3(dim3(32, 8)), (size_t)(0), st, src, lds, rows, cols, cols,
                                                                static_cast<double*>(dst), ldd, false,
                                                                cancel);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     } else {
         count_launch();
-        transpose_kernel<float><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, cols, cols,
+        {
+            cudaError_t pe_ = launch_pdl(transpose_kernel<float>, dim3(grid), dim3(dim3(32, 8)), (size_t)(0), st, src, lds, rows, cols, cols,
                                                               static_cast<float*>(dst), ldd, false,
                                                               cancel);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     }
     return cudaGetLastError();
 }
@@ -419,16 +458,25 @@ cudaError_t panel_convert_from(const TS* src, int64_t lds, int64_t rows, int64_t
     count_launch();
     switch (tdst) {
         case T_F64:
-            panel_convert_kernel<TS, double><<<blocks, 256, 0, st>>>(src, lds, rows, cols, static_cast<double*>(dst),
+            {
+                cudaError_t pe_ = launch_pdl(panel_convert_kernel<TS, double>, dim3(blocks), dim3(256), (size_t)(0), st, src, lds, rows, cols, static_cast<double*>(dst),
                                                                      ldd, cancel);
+                if (pe_ != cudaSuccess) return pe_;
+            }
             break;
         case T_F32:
-            panel_convert_kernel<TS, float><<<blocks, 256, 0, st>>>(src, lds, rows, cols, static_cast<float*>(dst),
+            {
+                cudaError_t pe_ = launch_pdl(panel_convert_kernel<TS, float>, dim3(blocks), dim3(256), (size_t)(0), st, src, lds, rows, cols, static_cast<float*>(dst),
                                                                     ldd, cancel);
+                if (pe_ != cudaSuccess) return pe_;
+            }
             break;
         case T_BF16:
-            panel_convert_kernel<TS, __nv_bfloat16><<<blocks, 256, 0, st>>>(
+            {
+                cudaError_t pe_ = launch_pdl(panel_convert_kernel<TS, __nv_bfloat16>, dim3(blocks), dim3(256), (size_t)(0), st, 
                 src, lds, rows, cols, static_cast<__nv_bfloat16*>(dst), ldd, cancel);
+                if (pe_ != cudaSuccess) return pe_;
+            }
             break;
         default:
             return cudaErrorInvalidValue;

@@ -278,7 +278,6 @@ template <bool kTf32>
 __global__ void __launch_bounds__(kThreads, 1)
 sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                  const TcParams p) {
-    if (p.cancel && *p.cancel) return;
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kMaxStages];
     __shared__ __align__(8) uint64_t empty_bar[kMaxStages];
@@ -323,6 +322,9 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
         prefetch_tmap(&map_a);
         prefetch_tmap(&map_b);
     }
+    // setup above overlaps the previous kernel's tail; operands and flags are read below
+    pdl_wait();
+    if (p.cancel && *p.cancel) return;  // uniform over the grid, before any tensor memory is held
     if (warp == 5) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_holder)),
@@ -364,6 +366,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                 if (++kk == p.kc_seg) { kk = 0; ++seg; }
                 if (++kc == KC) { kc = 0; ++t; seg = 0; kk = 0; }
             }
+            pdl_trigger();  // all loads issued: the successor may launch during the last MMAs and the fix-up
             if (abort_s) {
                 // drain: wait (bounded) for every copy that was issued but not consumed
                 const int issued = li;
@@ -573,6 +576,8 @@ __device__ __forceinline__ __nv_bfloat16 to_bf16(double v) {
 template <typename TI>
 __global__ void cast_bf16_kernel(const TI* a, long long m, long long n, long long lda, __nv_bfloat16* out,
                                  long long ldb, const int* cancel) {
+    pdl_trigger();
+    pdl_wait();
     if (cancel && *cancel) return;
     for (long long i = blockIdx.x; i < m; i += gridDim.x) {
         const TI* src = a + i * lda;
@@ -601,6 +606,8 @@ __global__ void cast_bf16_kernel(const TI* a, long long m, long long n, long lon
 
 __global__ void copy_f32_padded_kernel(const float* a, long long m, long long n, long long lda, float* out,
                                        long long ldb) {
+    pdl_trigger();
+    pdl_wait();
     const long long total = m * ldb;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
@@ -625,6 +632,8 @@ __device__ __forceinline__ void split3(float a, __nv_bfloat16& h, __nv_bfloat16&
 // beyond column n. One block per row at a time, 4 columns per thread.
 __global__ void cast_bf16_split_kernel(const float* a, long long m, long long n, long long lda, __nv_bfloat16* out,
                                        long long seg, const int* cancel) {
+    pdl_trigger();
+    pdl_wait();
     if (cancel && *cancel) return;
     for (long long i = blockIdx.x; i < m; i += gridDim.x) {
         const float* src = a + i * lda;
@@ -650,6 +659,8 @@ __global__ void cast_bf16_split_kernel(const float* a, long long m, long long n,
 // q3 column x * ellp + j = part x of panel column j (zero for ell <= j < ellp).
 __global__ void split_panel_kernel(const float* q, long long ldq, long long rows, int ell, int ellp,
                                    __nv_bfloat16* q3, long long ldq3, const int* cancel) {
+    pdl_trigger();
+    pdl_wait();
     if (cancel && *cancel) return;
     const long long total = rows * ellp;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -797,7 +808,10 @@ cudaError_t tc_launch(const void* a, bool tf32, long long mtot, long long ktot_s
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launch();
-    kern<<<pl.grid, kThreads, smem, st>>>(map_a, map_b, p);
+    {
+        cudaError_t pe_ = launch_pdl(kern, dim3(pl.grid), dim3(kThreads), (size_t)(smem), st, map_a, map_b, p);
+        if (pe_ != cudaSuccess) return pe_;
+    }
     return cudaGetLastError();
 }
 
@@ -868,7 +882,10 @@ cudaError_t launch_copy_f32_padded(const float* a, int64_t m, int64_t n, int64_t
     const long long total = m * ldb;
     const int blocks = (int)std::min<long long>((total + 255) / 256, 8192);
     count_launch();
-    copy_f32_padded_kernel<<<blocks, 256, 0, st>>>(a, m, n, lda, out, ldb);
+    {
+        cudaError_t pe_ = launch_pdl(copy_f32_padded_kernel, dim3(blocks), dim3(256), (size_t)(0), st, a, m, n, lda, out, ldb);
+        if (pe_ != cudaSuccess) return pe_;
+    }
     return cudaGetLastError();
 }
 
@@ -877,7 +894,10 @@ cudaError_t launch_cast_bf16_split(const float* a, int64_t m, int64_t n, int64_t
     if (seg % 64 != 0 || seg < n) return cudaErrorInvalidValue;
     const int blocks = (int)std::min<long long>(m, 16LL * 152);
     count_launch();
-    cast_bf16_split_kernel<<<blocks, 256, 0, st>>>(a, m, n, lda, static_cast<__nv_bfloat16*>(a3), seg, cancel);
+    {
+        cudaError_t pe_ = launch_pdl(cast_bf16_split_kernel, dim3(blocks), dim3(256), (size_t)(0), st, a, m, n, lda, static_cast<__nv_bfloat16*>(a3), seg, cancel);
+        if (pe_ != cudaSuccess) return pe_;
+    }
     return cudaGetLastError();
 }
 
@@ -886,8 +906,11 @@ cudaError_t launch_split_panel(const float* q, int64_t ldq, int64_t rows, int64_
     const long long total = rows * ellp;
     const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
     count_launch();
-    split_panel_kernel<<<blocks, 256, 0, st>>>(q, ldq, rows, (int)ell, (int)ellp, static_cast<__nv_bfloat16*>(q3),
+    {
+        cudaError_t pe_ = launch_pdl(split_panel_kernel, dim3(blocks), dim3(256), (size_t)(0), st, q, ldq, rows, (int)ell, (int)ellp, static_cast<__nv_bfloat16*>(q3),
                                                ldq3, cancel);
+        if (pe_ != cudaSuccess) return pe_;
+    }
     return cudaGetLastError();
 }
 
@@ -896,11 +919,17 @@ cudaError_t launch_cast_bf16(const void* a, ElemType ta, int64_t m, int64_t n, i
     const int blocks = (int)std::min<long long>(m, 16LL * 152);
     count_launch();
     if (ta == T_F32)
-        cast_bf16_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(a), m, n, lda,
+        {
+            cudaError_t pe_ = launch_pdl(cast_bf16_kernel<float>, dim3(blocks), dim3(256), (size_t)(0), st, static_cast<const float*>(a), m, n, lda,
                                                         static_cast<__nv_bfloat16*>(abf), ldb, cancel);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     else
-        cast_bf16_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double*>(a), m, n, lda,
+        {
+            cudaError_t pe_ = launch_pdl(cast_bf16_kernel<double>, dim3(blocks), dim3(256), (size_t)(0), st, static_cast<const double*>(a), m, n, lda,
                                                          static_cast<__nv_bfloat16*>(abf), ldb, cancel);
+            if (pe_ != cudaSuccess) return pe_;
+        }
     return cudaGetLastError();
 }
 
