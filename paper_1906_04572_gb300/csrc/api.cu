@@ -428,7 +428,7 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     // eq. 8: D P = Qt Rt
     {
         ProfScope ps(ex.prof, CORUTV_STAGE_QRCP, ex.st);
-        CK(launch_qrcp(b.d, ell, b.qt, b.rt, b.perm, b.refl, ex.cancel, ex.st));
+        CK(launch_qrcp(b.d, ell, b.qt, b.rt, b.perm, b.refl, ex.cancel, ex.st, /*form_q=*/false));
     }
     return CORUTV_OK;
 }
@@ -437,18 +437,8 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
 corutv_status emit_user(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, ElemType tout, void* u,
                         int64_t ldu, void* t, void* v, int64_t ldv, int32_t* perm) {
     const int64_t ell = pl.ell;
-    if (u) {
-        GemmArgs g{A_PANEL, B_SMALL, O_ROWMAJ, pl.tp, tout, b.q1, pl.ldm, nullptr, ell, u, ldu, 0,
-                   pl.m, ell, ell, 1, ex.cancel};
-        // the B operand must have the compute type: Qt in FP64, or converted for FP32
-        if (tout == T_F64) {
-            g.b = b.qt;
-        } else {
-            CK(launch_copy_small(b.qt, ell, b.g, T_F32, ex.cancel, ex.st));  // b.g reused as FP32 scratch
-            g.b = b.g;
-        }
-        CK(launch_gemm_simt(g, ex.st));
-    }
+    // U = Q1 Qt, applied as the QRCP's reflectors to the rows of Q1
+    if (u) CK(launch_apply_reflectors(b.q1, pl.tp, pl.ldm, pl.m, ell, b.refl, u, tout, ldu, false, ex.cancel, ex.st));
     CK(launch_copy_small(b.rt, ell, t, tout, ex.cancel, ex.st));
     if (v) CK(launch_gather_v(b.q2, pl.tp, pl.ldn, pl.n, ell, b.perm, v, tout, ldv, ex.cancel, ex.st));
     if (perm) CK(cudaMemcpyAsync(perm, b.perm, sizeof(int32_t) * ell, cudaMemcpyDeviceToDevice, ex.st));
@@ -1081,9 +1071,9 @@ extern "C" corutv_status corutv_rpca(corutv_ctx* ctx, corutv_dtype dtype, const 
     for (int j = 0; j < max_iter; ++j) {
         // L_{j+1} = C_{1/mu_j}(B_j): CoR-UTV of B_j with ell = 2k, q = 1, fresh Psi
         CKS(run_factor(ex, pl, b, bmat, nullptr, opts->seed, opts->stream + (uint32_t)j + 1u));
-        GemmArgs gu{A_PANEL, B_SMALL, O_PANEL, pl.tp, T_F64, b.q1, pl.ldm, b.qt, pl.ell, b.upanel, pl.ldm, 0,
-                    m, pl.ell, pl.ell, 1, done};
-        CK(launch_gemm_simt(gu, ctx->stream));
+        // U = Q1 Qt (FP64 panel) from the QRCP's reflectors
+        CK(launch_apply_reflectors(b.q1, pl.tp, pl.ldm, m, pl.ell, b.refl, b.upanel, T_F64, pl.ldm, true, done,
+                                   ctx->stream));
         CK(launch_rpca_rank_z(b.rt, b.q2, pl.tp, pl.ldn, b.perm, n, pl.ell, 1.0 / mus[j], rank_dev, b.zpanel,
                               pl.ldn, done, ctx->stream));
         RpcaIterArgs ua{m_dev, tm, ldm_dev, m, n,

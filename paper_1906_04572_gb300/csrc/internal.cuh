@@ -160,7 +160,13 @@ cudaError_t launch_gram_f32(const float* x, int64_t ldx, const float* y, int64_t
 // factorisation in one block, then Qt formed from its reflectors by several
 // blocks. work: ell * (ell + 2) doubles of device scratch.
 cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, int* perm, double* work,
-                        const int* cancel, cudaStream_t st);
+                        const int* cancel, cudaStream_t st, bool form_q = true);
+// U = Q1 Qt from the reflectors the QRCP left in `refl` (its work array),
+// without Qt: q1 a panel of type tp (ld ldq, `rows` rows); out row-major
+// (ld ldo) or, with out_panel, a panel; element type tout.
+cudaError_t launch_apply_reflectors(const void* q1, ElemType tp, int64_t ldq, int64_t rows, int64_t ell,
+                                    const double* refl, void* out, ElemType tout, int64_t ldo, bool out_panel,
+                                    const int* cancel, cudaStream_t st);
 // V[i][j] = Q2[perm[j]] (Q2 a panel of type tq2; row-major output of type tv).
 cudaError_t launch_gather_v(const void* q2, ElemType tq2, int64_t ldq2, int64_t n, int64_t ell, const int* perm,
                             void* v, ElemType tv, int64_t ldv, const int* cancel, cudaStream_t st);

@@ -278,6 +278,10 @@ constexpr int kTrsmB = 8;
 constexpr int kTrsmL = 4;                        // lanes per row
 constexpr int kTrsmRows = 32;                    // rows per block
 constexpr int kTrsmThreads = kTrsmL * kTrsmRows;
+// Row-major per row in shared memory with a stride = 4 (mod 32) elements:
+// the 32 lanes of a warp (8 rows x 4 consecutive columns) hit 32 distinct
+// banks (a stride of 32 rows put a row's four lanes on one bank).
+__host__ __device__ __forceinline__ int trsm_ld(int ell) { return ((ell + 31) & ~31) + 4; }
 template <typename TI, typename TC, typename TQC>
 __global__ void __launch_bounds__(kTrsmThreads)
 trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* r, TI* q, int64_t ldq,
@@ -286,8 +290,9 @@ trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* 
     if (cancel && *cancel) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC* Rs = reinterpret_cast<TC*>(smem_raw);   // ell x ell row-major
-    TC* Ts = Rs + ell * ell;                    // [ell][kTrsmRows]: a row's c values, then its q values
-    TC* Rd = Ts + (size_t)ell * kTrsmRows;      // 1 / R[j][j]
+    TC* Ts = Rs + ell * ell;                    // [kTrsmRows][ld]: a row's c values, then its q values
+    const int ld = trsm_ld(ell);
+    TC* Rd = Ts + (size_t)kTrsmRows * trsm_ld(ell);  // 1 / R[j][j]
     const int tid = threadIdx.x;
     const int ln = tid & (kTrsmL - 1), rr = tid / kTrsmL;
     // loads in batches of 16 per thread, all in flight before their stores
@@ -318,7 +323,7 @@ trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* 
 #pragma unroll
         for (int u = 0; u < kB; ++u) {
             const int j = j0 + kTrsmL * u;
-            if (j < ell) Ts[j * kTrsmRows + rr] = (TC)v[u];
+            if (j < ell) Ts[rr * ld + j] = (TC)v[u];
         }
     }
     __syncthreads();
@@ -326,9 +331,9 @@ trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* 
         const int nb = min(kTrsmB, ell - j0);
         TC acc[kTrsmB];
 #pragma unroll
-        for (int k = 0; k < kTrsmB; ++k) acc[k] = (ln == 0 && k < nb) ? Ts[(j0 + k) * kTrsmRows + rr] : (TC)0;
+        for (int k = 0; k < kTrsmB; ++k) acc[k] = (ln == 0 && k < nb) ? Ts[rr * ld + j0 + k] : (TC)0;
         for (int t = ln; t < j0; t += kTrsmL) {
-            const TC qt = Ts[t * kTrsmRows + rr];
+            const TC qt = Ts[rr * ld + t];
             const TC* rrow = Rs + t * ell + j0;
 #pragma unroll
             for (int k = 0; k < kTrsmB; ++k)
@@ -350,13 +355,13 @@ trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* 
         __syncwarp();  // the row's lanes have read their c values before any is overwritten
 #pragma unroll
         for (int k = 0; k < kTrsmB; ++k)
-            if (k < nb && (k & (kTrsmL - 1)) == ln) Ts[(j0 + k) * kTrsmRows + rr] = acc[k];
+            if (k < nb && (k & (kTrsmL - 1)) == ln) Ts[rr * ld + j0 + k] = acc[k];
         __syncwarp();
     }
     pdl_trigger();  // the successor may launch while Q is written
     if (!live) return;
     for (int j = ln; j < ell; j += kTrsmL) {
-        TC v = Ts[j * kTrsmRows + rr];
+        TC v = Ts[rr * ld + j];
         if (defic && defic[j]) v = (TC)completion_entry(i, j, rows);  // R row j is e_j: nothing else used q_j
         q[(int64_t)j * ldq + i] = (TI)v;
         if (qc) qc[(int64_t)j * ldqc + i] = (TQC)v;
@@ -366,7 +371,7 @@ trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* 
 template <typename TI, typename TC, typename TQC>
 cudaError_t trsm_launch(const void* c, int64_t ldc, int64_t rows, int ell, const double* r, void* q, int64_t ldq,
                         void* qc, int64_t ldqc, const int* cancel, cudaStream_t st, const int* defic) {
-    const size_t smem = sizeof(TC) * ((size_t)ell * ell + (size_t)ell * kTrsmRows + (size_t)ell);
+    const size_t smem = sizeof(TC) * ((size_t)ell * ell + (size_t)kTrsmRows * trsm_ld(ell) + (size_t)ell);
     cudaError_t e = cudaFuncSetAttribute(trsm_rows_kernel<TI, TC, TQC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -669,6 +674,91 @@ qform_kernel(const double* refl, int ell, double* qt, const int* cancel) {
     }
 }
 
+// U = Q1 Qt without forming Qt: each row x of Q1 is multiplied from the right
+// by H_0, H_1, ..., H_{ell-1} (H_j = I - tau_j v_j v_j^T, v_j[j] = 1) and by
+// diag(sgn), the reflectors and column signs the QRCP kernel wrote. Four
+// adjacent lanes share a row (lane s owns the entries i = s mod 4); per
+// reflector each lane forms its part of v_j^T x, two xor shuffles add the
+// parts, and each lane updates its own entries. 32 rows per block.
+template <typename TI, typename TC, typename TO>
+__global__ void __launch_bounds__(kTrsmThreads)
+apply_refl_kernel(const TI* x, int64_t ldx, int64_t rows, int ell, const double* refl, TO* out, int64_t ldo,
+                  int out_panel, const int* cancel) {
+    pdl_wait();
+    if (cancel && *cancel) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TC* Vs = reinterpret_cast<TC*>(smem_raw);   // ell x ell: column j = v_j (below the diagonal)
+    TC* tau = Vs + ell * ell;
+    TC* sgn = tau + ell;
+    TC* Ts = sgn + ell;                         // [kTrsmRows][ld]
+    const int ld = trsm_ld(ell);
+    const int tid = threadIdx.x;
+    const int ln = tid & (kTrsmL - 1), rr = tid / kTrsmL;
+    constexpr int kB = 16;
+    const int nv = ell * ell + 2 * ell;
+    for (int e0 = 0; e0 < nv; e0 += kB * kTrsmThreads) {
+        double v[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int e = e0 + u * kTrsmThreads + tid;
+            v[u] = e < nv ? refl[e] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int e = e0 + u * kTrsmThreads + tid;
+            if (e < nv) Vs[e] = (TC)v[u];  // Vs, tau, sgn are contiguous like refl
+        }
+    }
+    const int64_t i0 = (int64_t)blockIdx.x * kTrsmRows + rr;
+    const bool live = i0 < rows;
+    for (int j0 = ln; j0 < ell; j0 += kTrsmL * kB) {
+        TI v[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int j = j0 + kTrsmL * u;
+            v[u] = (live && j < ell) ? x[(int64_t)j * ldx + i0] : (TI)0;
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int j = j0 + kTrsmL * u;
+            if (j < ell) Ts[rr * ld + j] = (TC)v[u];
+        }
+    }
+    __syncthreads();
+    pdl_trigger();
+    for (int j = 0; j < ell; ++j) {
+        const TC* vj = Vs + j * ell;
+        // first entry of this lane at or after j
+        const int i_beg = j + ((ln - j) & (kTrsmL - 1));
+        // four independent partial sums: the loads and FMAs of a lane overlap
+        TC p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+        int i = i_beg;
+        if (i == j) {
+            p0 = Ts[rr * ld + i];  // v_j[j] = 1
+            i += kTrsmL;
+        }
+        for (; i + 3 * kTrsmL < ell; i += 4 * kTrsmL) {
+            p0 += vj[i] * Ts[rr * ld + i];
+            p1 += vj[i + kTrsmL] * Ts[rr * ld + i + kTrsmL];
+            p2 += vj[i + 2 * kTrsmL] * Ts[rr * ld + i + 2 * kTrsmL];
+            p3 += vj[i + 3 * kTrsmL] * Ts[rr * ld + i + 3 * kTrsmL];
+        }
+        for (; i < ell; i += kTrsmL) p0 += vj[i] * Ts[rr * ld + i];
+        TC part = (p0 + p1) + (p2 + p3);
+        part += __shfl_xor_sync(0xffffffffu, part, 1);
+        part += __shfl_xor_sync(0xffffffffu, part, 2);
+        const TC f = tau[j] * part;
+#pragma unroll 4
+        for (int i2 = i_beg; i2 < ell; i2 += kTrsmL) Ts[rr * ld + i2] -= f * (i2 == j ? (TC)1 : vj[i2]);
+    }
+    if (!live) return;
+    for (int i = ln; i < ell; i += kTrsmL) {
+        const TC val = Ts[rr * ld + i] * sgn[i];
+        if (out_panel) out[(int64_t)i * ldo + i0] = (TO)val;
+        else out[i0 * ldo + i] = (TO)val;
+    }
+}
+
 template <typename TQ, typename TV>
 __global__ void gather_v_kernel(const TQ* q2, int64_t ldq2, int64_t n, int ell, const int* perm,
                                 TV* v, int64_t ldv, const int* cancel) {
@@ -730,28 +820,53 @@ cudaError_t launch_trsm_rows(const void* c, ElemType tp, int64_t ldc, int64_t ro
 }
 
 cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, int* perm, double* work,
-                        const int* cancel, cudaStream_t st) {
+                        const int* cancel, cudaStream_t st, bool form_q) {
     if (ell < 1 || ell > 128 || !work) return cudaErrorInvalidValue;
     const size_t smem = sizeof(double) * ((size_t)ell * (ell | 1) + 5 * (size_t)ell) + sizeof(int) * ell;
     cudaError_t e = cudaFuncSetAttribute(qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launch();
     {
-        cudaError_t pe_ = launch_pdl(qrcp_kernel, dim3(1), dim3(kQrcpThreads), (size_t)(smem), st, d, (int)ell, work, rt, perm, cancel);
+        cudaError_t pe_ = launch_pdl(qrcp_kernel, dim3(1), dim3(kQrcpThreads), (size_t)(smem), st, d, (int)ell, work,
+                                     rt, perm, cancel);
         if (pe_ != cudaSuccess) return pe_;
     }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (!form_q) return cudaSuccess;
     const size_t smem_q = sizeof(double) * (size_t)(ell * ell + 2 * ell);
     e = cudaFuncSetAttribute(qform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_q);
     if (e != cudaSuccess) return e;
     count_launch();
-    {
-        cudaError_t pe_ = launch_pdl(qform_kernel, dim3((unsigned)((ell + kQformWarps - 1) / kQformWarps)), dim3(kQformWarps * 32), (size_t)(smem_q), st, work, (int)ell,
-                                                                                                   qt, cancel);
-        if (pe_ != cudaSuccess) return pe_;
-    }
-    return cudaGetLastError();
+    return launch_pdl(qform_kernel, dim3((unsigned)((ell + kQformWarps - 1) / kQformWarps)), dim3(kQformWarps * 32),
+                      smem_q, st, static_cast<const double*>(work), (int)ell, qt, cancel);
+}
+
+cudaError_t launch_apply_reflectors(const void* q1, ElemType tp, int64_t ldq, int64_t rows, int64_t ell,
+                                    const double* refl, void* out, ElemType tout, int64_t ldo, bool out_panel,
+                                    const int* cancel, cudaStream_t st) {
+    if (ell < 1 || ell > 128) return cudaErrorInvalidValue;
+    const unsigned blocks = (unsigned)((rows + kTrsmRows - 1) / kTrsmRows);
+    const int l = (int)ell;
+    auto go = [&](auto kern, size_t tc_bytes, auto xin, auto outp) -> cudaError_t {
+        const size_t smem = tc_bytes * ((size_t)ell * ell + 2 * (size_t)ell + (size_t)kTrsmRows * trsm_ld(l));
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        count_launch();
+        return launch_pdl(kern, dim3(blocks), dim3(kTrsmThreads), smem, st, xin, ldq, rows, l, refl, outp, ldo,
+                          out_panel ? 1 : 0, cancel);
+    };
+    if (tp == T_F32 && tout == T_F32)
+        return go(apply_refl_kernel<float, float, float>, sizeof(float), static_cast<const float*>(q1),
+                  static_cast<float*>(out));
+    if (tp == T_F32 && tout == T_F64)
+        return go(apply_refl_kernel<float, double, double>, sizeof(double), static_cast<const float*>(q1),
+                  static_cast<double*>(out));
+    if (tp == T_F64 && tout == T_F64)
+        return go(apply_refl_kernel<double, double, double>, sizeof(double), static_cast<const double*>(q1),
+                  static_cast<double*>(out));
+    if (tp == T_F64 && tout == T_F32)
+        return go(apply_refl_kernel<double, double, float>, sizeof(double), static_cast<const double*>(q1),
+                  static_cast<float*>(out));
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_gather_v(const void* q2, ElemType tq2, int64_t ldq2, int64_t n, int64_t ell, const int* perm,
