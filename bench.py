@@ -495,7 +495,7 @@ def run_ours(args):
                                       8)
         extra["rpca"] = rpca_c4(ctx, device)
         if args.c3:
-            extra["c3"] = c3_line(ctx, device, ("bf16", "f32"), 3)
+            extra["c3"] = c3_line(ctx, device, ("bf16", "tf32", "f32"), 3)
 
     if rank == 0:
         line = {

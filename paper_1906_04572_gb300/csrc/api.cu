@@ -167,7 +167,9 @@ struct FactorPlan {
     ElemType torth;   // arithmetic of the Gram products and triangular solves of the thin QRs
     ElemType tp;      // element type of the tall-skinny panels (X, C1, Q1, C2, Q2, W)
     bool tensor;      // sketch products on tcgen05
-    bool split;       // projection by exact bf16 splits on tcgen05 (BF16 sketches, FP32 input)
+    bool split;       // projection by exact bf16 splits on tcgen05 (BF16 / TF32 sketches, FP32 input)
+    bool copy_a;      // TF32: A is not a TMA source as is (base or row stride not 16-byte aligned)
+    int64_t ldc32;    // row stride of that padded FP32 copy of A
     int64_t seg;      // columns per segment of the bf16 copy of A ([A_h | A_m | A_l] when split)
     int sp_ax, sp_aty, sp_w, gs_m, gs_n;
     int64_t part_elems;
@@ -180,14 +182,18 @@ struct FactorBufs {
     double* refl;     // reflectors of the QRCP of D (V, tau, signs)
     int* defic;       // columns found numerically dependent in the extra CholeskyQR pass
     void *xc, *q1c, *q2c, *part;
-    void* abf;        // bf16 copy of A for CORUTV_P_BF16
+    void* abf;        // bf16 copy of A for CORUTV_P_BF16, or its bf16 splits for the projection
+    float* at;        // TF32: A^T (n rows, row stride ldm), so that A^T Y has K-major operands
+    float* a32;       // TF32: padded copy of A when A itself is not TMA-aligned
     int *perm, *skip;
     int* tcnt;        // per-tile counters of the tensor-core products, then gcnt
     int* gcnt;        // counters of the FP32 Gram kernel
 };
 
+// a_aligned: the device copy of A that the factorisation reads starts on a
+// 16-byte boundary (only TF32 sketches read A itself through TMA).
 corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64_t lda, int64_t k,
-                        int64_t p, int64_t q, corutv_prec prec, int num_sms) {
+                        int64_t p, int64_t q, corutv_prec prec, int num_sms, bool a_aligned = true) {
     pl.m = m; pl.n = n; pl.lda = lda; pl.k = k; pl.p = p; pl.q = q;
     pl.ell = k + p;
     pl.ta = ta;
@@ -203,11 +209,11 @@ corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64
     if (lda < n) return fail(CORUTV_EINVAL, "lda = %lld < n = %lld", (long long)lda, (long long)n);
     if (prec < CORUTV_P_F64 || prec > CORUTV_P_BF16) return fail(CORUTV_EINVAL, "unknown sketch precision %d", (int)prec);
     pl.tensor = (prec == CORUTV_P_TF32 || prec == CORUTV_P_BF16);
-    pl.split = prec == CORUTV_P_BF16 && ta == T_F32;
+    if (prec == CORUTV_P_TF32 && ta != T_F32) return fail(CORUTV_EINVAL, "TF32 sketches need FP32 input");
+    pl.split = pl.tensor && ta == T_F32;
     pl.seg = pl.split ? round_up(n, 64) : round_up(n, 8);
-    if (prec == CORUTV_P_TF32)
-        return fail(CORUTV_EINVAL, "TF32 sketches are not available for the full factorisation: the A^T Y "
-                                   "product has no TF32 kernel (use CORUTV_P_BF16 or CORUTV_P_F32)");
+    pl.copy_a = prec == CORUTV_P_TF32 && (!a_aligned || lda % 4 != 0);
+    pl.ldc32 = round_up(n, 4);
     pl.ellp = pl.tensor ? round_up(pl.ell, 16) : pl.ell;
     pl.ldm = round_up(m, 64);
     pl.ldn = round_up(n, 64);
@@ -257,7 +263,10 @@ void carve_factor(C& cv, const FactorPlan& pl, FactorBufs& b) {
     b.q1c = cv.template take<char>(pm * es_c);
     b.q2c = cv.template take<char>(pl.split ? 3 * pn * 2 : pn * es_d);
     b.part = cv.template take<char>(pl.part_elems * std::max(8, std::max(es_c, es_d)));
-    b.abf = pl.prec == CORUTV_P_BF16 ? cv.template take<char>(pl.m * (pl.split ? 3 : 1) * pl.seg * 2) : nullptr;
+    b.abf = (pl.prec == CORUTV_P_BF16 || pl.split) ? cv.template take<char>(pl.m * (pl.split ? 3 : 1) * pl.seg * 2)
+                                                   : nullptr;
+    b.at = pl.prec == CORUTV_P_TF32 ? cv.template take<float>(pl.n * pl.ldm) : nullptr;
+    b.a32 = pl.copy_a ? cv.template take<float>(pl.m * pl.ldc32) : nullptr;
     b.perm = cv.template take<int>(pl.ellp);
     b.skip = cv.template take<int>(8);
     b.tcnt = cv.template take<int>(factor_counters(pl));
@@ -371,7 +380,11 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
         // padding columns of the bf16 / fp32 operand panels must read as zero
         CK(cudaMemsetAsync(b.q1c, 0, (size_t)pl.ellp * pl.ldm * elem_size(pl.tcomp), ex.st));
         CK(launch_panel_convert(b.x, pl.tp, pl.ldn, n, pl.ellp, b.xc, pl.tcomp, pl.ldn, ex.cancel, ex.st));
-        if (pl.split)
+        if (pl.prec == CORUTV_P_TF32)
+            // one pass over A: A^T for the K-major A^T Y, the bf16 splits for eq. 7
+            CK(launch_prep_f32(static_cast<const float*>(a), m, n, pl.lda, b.at, pl.ldm, b.abf, pl.seg, b.a32,
+                               pl.ldc32, ex.cancel, ex.st));
+        else if (pl.split)
             CK(launch_cast_bf16_split(static_cast<const float*>(a), m, n, pl.lda, b.abf, pl.seg, ex.cancel, ex.st));
         else if (pl.prec == CORUTV_P_BF16)
             CK(launch_cast_bf16(a, pl.ta, m, n, pl.lda, b.abf, pl.seg, ex.cancel, ex.st));
@@ -382,8 +395,9 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     for (int64_t it = 0; it <= pl.q; ++it) {
         // eq. 4: C1 = A X
         if (pl.tensor) {
-            const void* aop = pl.prec == CORUTV_P_BF16 ? b.abf : a;
-            const int64_t lda_op = pl.prec == CORUTV_P_BF16 ? ldabf : pl.lda;
+            const bool bf = pl.prec == CORUTV_P_BF16;
+            const void* aop = bf ? b.abf : (pl.copy_a ? static_cast<const void*>(b.a32) : a);
+            const int64_t lda_op = bf ? ldabf : (pl.copy_a ? pl.ldc32 : pl.lda);
             ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
             CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, /*trans=*/0, b.xc, pl.ldn, ell, pl.ellp, b.part,
                                 b.tcnt, b.c1, pl.tp, pl.ldm, ex.num_sms, ex.flags, ex.cancel, ex.st));
@@ -394,11 +408,13 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
         CKS(orth(ex, pl, b, b.c1, pl.ldm, m, b.q1, b.q1c, pl.tcomp, it < pl.q ? inner : 2));
         // eq. 5 (with C1 -> Q1): C2 = A^T Q1
         if (pl.tensor) {
-            const void* aop = pl.prec == CORUTV_P_BF16 ? b.abf : a;
-            const int64_t lda_op = pl.prec == CORUTV_P_BF16 ? ldabf : pl.lda;
             ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
-            CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, /*trans=*/1, b.q1c, pl.ldm, ell, pl.ellp, b.part,
-                                b.tcnt, b.c2, pl.tp, pl.ldn, ex.num_sms, ex.flags, ex.cancel, ex.st));
+            if (pl.prec == CORUTV_P_BF16)
+                CK(launch_sketch_tc(b.abf, pl.tcomp, m, n, ldabf, /*trans=*/1, b.q1c, pl.ldm, ell, pl.ellp, b.part,
+                                    b.tcnt, b.c2, pl.tp, pl.ldn, ex.num_sms, ex.flags, ex.cancel, ex.st));
+            else  // TF32: (A^T) Y with the transposed copy, both operands K-major
+                CK(launch_sketch_tc(b.at, pl.tcomp, n, m, pl.ldm, /*trans=*/0, b.q1c, pl.ldm, ell, pl.ellp, b.part,
+                                    b.tcnt, b.c2, pl.tp, pl.ldn, ex.num_sms, ex.flags, ex.cancel, ex.st));
         } else {
             CKS(sketch_simt(ex, pl, b, A_COLS, a, pl.ta, b.q1c, pl.tcomp, b.c2, pl.ldn));
         }
@@ -699,12 +715,15 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
     DeviceGuard guard(ctx->device);
     const ElemType ta = dtype == CORUTV_F64 ? T_F64 : T_F32;
     const int es = elem_size(ta);
+    const bool dev = is_device_ptr(A);
+    if (lda < n) return fail(CORUTV_EINVAL, "lda = %lld < n = %lld", (long long)lda, (long long)n);
     FactorPlan pl;
-    CKS(make_plan(pl, ta, m, n, lda, opts->k, opts->p, opts->q, (corutv_prec)opts->sketch_prec, ctx->num_sms));
+    // host input is staged with row stride n into the (256-byte aligned) workspace
+    CKS(make_plan(pl, ta, m, n, dev ? lda : n, opts->k, opts->p, opts->q, (corutv_prec)opts->sketch_prec,
+                  ctx->num_sms, !dev || reinterpret_cast<uintptr_t>(A) % 16 == 0));
     const int64_t ell = pl.ell;
     if (U && ldu < ell) return fail(CORUTV_EINVAL, "ldu < ell");
     if (V && ldv < ell) return fail(CORUTV_EINVAL, "ldv < ell");
-    const bool dev = is_device_ptr(A);
     if ((U && is_device_ptr(U) != dev) || is_device_ptr(T) != dev || (V && is_device_ptr(V) != dev) ||
         (perm && is_device_ptr(perm) != dev))
         return fail(CORUTV_EINVAL, "A and the outputs must all be host or all be device memory");
@@ -852,8 +871,11 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
     measure.take<double>(pl.ellp * ldcp);
     measure.take<char>(pl.part_elems * 8);
     if (prec == CORUTV_P_BF16) measure.take<char>(m * round_up(n, 8) * 2);
-    const bool tf32_copy = prec == CORUTV_P_TF32 && !tma_rows_aligned(A, lda, 4);
+    // TF32 A^T X runs as (A^T) X on a transposed copy: both operands K-major
+    const bool tf32_t = prec == CORUTV_P_TF32 && trans;
+    const bool tf32_copy = prec == CORUTV_P_TF32 && !trans && !tma_rows_aligned(A, lda, 4);
     if (tf32_copy) measure.take<float>(m * round_up(n, 4));
+    if (tf32_t) measure.take<float>(n * pl.ldm);
     if (pl.tensor) measure.take<int>(tc_counter_elems(m, n));
     CKS(ensure_ws(ctx, ctx->ws, measure.off, ctx->stream));
     Carver cv(ctx->ws.ptr);
@@ -864,6 +886,7 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
     b.part = cv.take<char>(pl.part_elems * 8);
     b.abf = prec == CORUTV_P_BF16 ? cv.take<char>(m * round_up(n, 8) * 2) : nullptr;
     float* a32 = tf32_copy ? cv.take<float>(m * round_up(n, 4)) : nullptr;
+    float* at = tf32_t ? cv.take<float>(n * pl.ldm) : nullptr;
     b.tcnt = pl.tensor ? cv.take<int>(tc_counter_elems(m, n)) : nullptr;
     if (pl.tensor) CK(cudaMemsetAsync(b.tcnt, 0, sizeof(int) * (size_t)tc_counter_elems(m, n), ctx->stream));
     CK(launch_rowmajor_to_panel(X, ldx, xrows, ell, pl.ellp, xp, T_F64, ldxp, ctx->stream));
@@ -881,8 +904,15 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
             aop = a32;
             lda_op = round_up(n, 4);
         }
-        CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, trans, xc, ldxp, ell, pl.ellp, b.part, b.tcnt, cp, T_F64, ldcp,
-                            ctx->num_sms, ctx->flags, nullptr, ctx->stream));
+        if (tf32_t) {
+            CK(launch_prep_f32(static_cast<const float*>(A), m, n, lda, at, pl.ldm, nullptr, 0, nullptr, 0, nullptr,
+                               ctx->stream));
+            CK(launch_sketch_tc(at, T_F32, n, m, pl.ldm, 0, xc, ldxp, ell, pl.ellp, b.part, b.tcnt, cp, T_F64, ldcp,
+                                ctx->num_sms, ctx->flags, nullptr, ctx->stream));
+        } else {
+            CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, trans, xc, ldxp, ell, pl.ellp, b.part, b.tcnt, cp, T_F64,
+                                ldcp, ctx->num_sms, ctx->flags, nullptr, ctx->stream));
+        }
     } else {
         CKS(sketch_simt(ex, pl, b, trans ? A_COLS : A_ROWS, A, ta, xc, pl.tcomp, cp, ldcp));
     }
@@ -1119,7 +1149,7 @@ size_t request_bytes(const corutv_request& r, bool host, int num_sms, FactorPlan
     FactorPlan pl;
     const ElemType ta = r.dtype == CORUTV_F64 ? T_F64 : T_F32;
     *st = make_plan(pl, ta, r.m, r.n, host ? r.n : r.lda, r.opts.k, r.opts.p, r.opts.q,
-                    (corutv_prec)r.opts.sketch_prec, num_sms);
+                    (corutv_prec)r.opts.sketch_prec, num_sms, host || reinterpret_cast<uintptr_t>(r.A) % 16 == 0);
     if (*st != CORUTV_OK) return 0;
     size_t bytes = factor_bytes(pl);
     const int es = elem_size(ta);
@@ -1289,6 +1319,7 @@ extern "C" corutv_status corutv_submit(corutv_ctx* ctx, const corutv_request* re
     CKS(check_ctx(ctx));
     if (!req || !ticket || !req->A || !req->T) return fail(CORUTV_EINVAL, "req, ticket, A and T must not be NULL");
     if (req->opts.d_mode != 0) return fail(CORUTV_EINVAL, "d_mode must be 0");
+    if (req->lda < req->n) return fail(CORUTV_EINVAL, "lda = %lld < n = %lld", (long long)req->lda, (long long)req->n);
     DeviceGuard guard(ctx->device);
     const bool host = !is_device_ptr(req->A);
     corutv_status st;

@@ -656,6 +656,72 @@ __global__ void cast_bf16_split_kernel(const float* a, long long m, long long n,
     }
 }
 
+// One read of FP32 A (m x n, row stride lda) in 64 x 64 tiles, writing any
+// of: at = A^T (n rows, row stride ldt >= round_up(m, 64); columns
+// [m, round_up(m, 64)) zero, any further ones untouched), the rows of
+// [A_h | A_m | A_l] (a3, segment `seg`, zero beyond n) and a row-major copy
+// with row stride ldc <= round_up(n, 64) (zero for n <= j < ldc). The transposed
+// copy makes A^T Y a product with K-major operands (TF32 has no MN-major form
+// here). 256 threads, a tile staged in shared memory for the transpose.
+constexpr int kPrepT = 64;
+__global__ void __launch_bounds__(256)
+prep_f32_kernel(const float* a, long long m, long long n, long long lda, float* at, long long ldt,
+                __nv_bfloat16* a3, long long seg, float* acopy, long long ldc, const int* cancel) {
+    pdl_trigger();
+    pdl_wait();
+    if (cancel && *cancel) return;
+    __shared__ float tile[kPrepT][kPrepT + 1];
+    const long long i0 = (long long)blockIdx.y * kPrepT, j0 = (long long)blockIdx.x * kPrepT;
+    const int tid = threadIdx.x;
+    const bool vec = (reinterpret_cast<uintptr_t>(a) & 15) == 0 && (lda & 3) == 0;
+    float v[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int idx = tid + 256 * k;
+        const int r = idx >> 4, c4 = (idx & 15) * 4;
+        const long long i = i0 + r, j = j0 + c4;
+        const float* src = a + i * lda + j;
+        if (i < m && vec && j + 3 < n) {
+            const float4 f = *reinterpret_cast<const float4*>(src);
+            v[k][0] = f.x; v[k][1] = f.y; v[k][2] = f.z; v[k][3] = f.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[k][q] = (i < m && j + q < n) ? src[q] : 0.f;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int idx = tid + 256 * k;
+        const int r = idx >> 4, c4 = (idx & 15) * 4;
+        const long long i = i0 + r, j = j0 + c4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tile[r][c4 + q] = v[k][q];
+        if (i >= m) continue;
+        if (a3 && j < seg) {
+            __nv_bfloat16 h[4], md[4], lo[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) split3(v[k][q], h[q], md[q], lo[q]);
+            __nv_bfloat16* dst = a3 + i * 3 * seg + j;
+            *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(h);
+            *reinterpret_cast<uint2*>(dst + seg) = *reinterpret_cast<const uint2*>(md);
+            *reinterpret_cast<uint2*>(dst + 2 * seg) = *reinterpret_cast<const uint2*>(lo);
+        }
+        if (acopy && j < ldc)
+            *reinterpret_cast<float4*>(acopy + i * ldc + j) = make_float4(v[k][0], v[k][1], v[k][2], v[k][3]);
+    }
+    if (!at) return;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int idx = tid + 256 * k;
+        const int jr = idx >> 4, i4 = (idx & 15) * 4;
+        const long long j = j0 + jr, i = i0 + i4;
+        if (j < n && i < ldt)
+            *reinterpret_cast<float4*>(at + j * ldt + i) =
+                make_float4(tile[i4][jr], tile[i4 + 1][jr], tile[i4 + 2][jr], tile[i4 + 3][jr]);
+    }
+}
+
 // q3 column x * ellp + j = part x of panel column j (zero for ell <= j < ellp).
 __global__ void split_panel_kernel(const float* q, long long ldq, long long rows, int ell, int ellp,
                                    __nv_bfloat16* q3, long long ldq3, const int* cancel) {
@@ -896,6 +962,28 @@ cudaError_t launch_cast_bf16_split(const float* a, int64_t m, int64_t n, int64_t
     count_launch();
     {
         cudaError_t pe_ = launch_pdl(cast_bf16_split_kernel, dim3(blocks), dim3(256), (size_t)(0), st, a, m, n, lda, static_cast<__nv_bfloat16*>(a3), seg, cancel);
+        if (pe_ != cudaSuccess) return pe_;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_f32(const float* a, int64_t m, int64_t n, int64_t lda, float* at, int64_t ldt, void* a3,
+                            int64_t seg, float* acopy, int64_t ldc, const int* cancel, cudaStream_t st) {
+    if (m < 1 || n < 1 || lda < n) return cudaErrorInvalidValue;
+    // every vector store stays inside its row: the tiles cover columns up to
+    // round_up(., 64) and the strides are multiples of 64 / 4
+    if (at && (ldt % 64 != 0 || ldt < m || reinterpret_cast<uintptr_t>(at) % 16 != 0)) return cudaErrorInvalidValue;
+    if (a3 && (seg % 64 != 0 || seg < n || reinterpret_cast<uintptr_t>(a3) % 8 != 0)) return cudaErrorInvalidValue;
+    if (acopy && (ldc % 4 != 0 || ldc < n || ldc > (n + kPrepT - 1) / kPrepT * kPrepT ||
+                  reinterpret_cast<uintptr_t>(acopy) % 16 != 0))
+        return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((n + kPrepT - 1) / kPrepT), (unsigned)((m + kPrepT - 1) / kPrepT), 1);
+    if (grid.y > 65535u) return cudaErrorInvalidValue;
+    count_launch();
+    {
+        cudaError_t pe_ = launch_pdl(prep_f32_kernel, grid, dim3(256), (size_t)0, st, a, (long long)m, (long long)n,
+                                     (long long)lda, at, (long long)ldt, static_cast<__nv_bfloat16*>(a3),
+                                     (long long)seg, acopy, (long long)ldc, cancel);
         if (pe_ != cudaSuccess) return pe_;
     }
     return cudaGetLastError();

@@ -55,6 +55,13 @@ cudaError_t launch_project_split_tc(const void* a3, int64_t m, int64_t n, int64_
 // Writes a3 (rows of [A_h | A_m | A_l]) from FP32 A.
 cudaError_t launch_cast_bf16_split(const float* a, int64_t m, int64_t n, int64_t lda, void* a3, int64_t seg,
                                    const int* cancel, cudaStream_t st);
+// One pass over FP32 A (m x n, row stride lda) writing any non-null of: at =
+// A^T (n rows of stride ldt, ldt a multiple of 64 and >= m; columns
+// [m, round_up(m, 64)) zero), a3 (as launch_cast_bf16_split) and a row-major
+// copy acopy (row stride ldc, a multiple of 4 in [n, round_up(n, 64)], zero
+// beyond n).
+cudaError_t launch_prep_f32(const float* a, int64_t m, int64_t n, int64_t lda, float* at, int64_t ldt, void* a3,
+                            int64_t seg, float* acopy, int64_t ldc, const int* cancel, cudaStream_t st);
 // Writes q3 = [Q_h | Q_m | Q_l] from an FP32 panel (ell valid columns of ellp).
 cudaError_t launch_split_panel(const float* q, int64_t ldq, int64_t rows, int64_t ell, int64_t ellp, void* q3,
                                int64_t ldq3, const int* cancel, cudaStream_t st);

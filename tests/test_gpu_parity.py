@@ -296,6 +296,24 @@ def test_rpca_f32_past_convergence_keeps_shifting(ctx):
     assert rel(host(res["L"]), pr.l_true) < 1e-4
 
 
+def test_rpca_tf32_sketches_track_f32(ctx):
+    """Algorithm 2 with TF32 sketch products (FP32 data, FP32-accurate
+    projection) converges to the same tolerance as the FP32 run, with L within
+    the TF32 span error (about 2^-10 relative) of it. It may take more
+    iterations: the span error of each low-rank step enters the residual."""
+    pr = synth.rpca_problem(480, 120, 5, 0.10, "uniform", seed=0, amplitude=50.0)
+    m32 = dev(pr.m_obs.astype(np.float32), torch.float32)
+    d = oracle.rpca_defaults(pr.m_obs.astype(np.float32).astype(np.float64))
+    kw = dict(lam=d["lam"], mu0=d["mu0"], mu_bar=d["mu_bar"], rho=d["rho"], tol=1e-5, max_iter=50)
+    r32 = ctx.rpca(m32, 5, prec="f32", **kw)
+    rtf = ctx.rpca(m32, 5, prec="tf32", **kw)
+    print("iters", r32["iters"], rtf["iters"], "zeta", r32["zeta"], rtf["zeta"],
+          "dL", rel(host(rtf["L"]), host(r32["L"])))
+    assert rtf["rank"] == 5
+    assert r32["status"] == rtf["status"] == corutv.OK and rtf["zeta"] < 1e-5
+    assert rel(host(rtf["L"]), host(r32["L"])) < 4 * 2.0 ** -10
+
+
 # ---------------------------------------------------------------- serving
 def test_serving_results_equal_alone_and_in_the_mix(ctx):
     rng = np.random.default_rng(0)

@@ -5,7 +5,7 @@ Bounds: the tensor cores multiply bf16 operands exactly and accumulate in
 FP32, so against the oracle's product of the same bf16-rounded operands
 |C - C_ref| <= 2 K 2^-24 (|A_r| |X_r|) elementwise. TF32 operands keep 10
 mantissa bits (the low 13 bits of the FP32 input are dropped), which adds
-2^-10 (|A| |X|)."""
+2^-10 (|A| |X|). A^T Y in TF32 runs on a transposed FP32 copy of A."""
 
 import numpy as np
 import pytest
@@ -110,11 +110,21 @@ def test_sketch_bf16x3_has_fp32_accuracy(ctx, m, n, ell):
     assert np.all(err <= bound), float((err / bound).max())
 
 
-def test_sketch_tf32_transposed_is_refused(ctx):
-    a = dev(np.ones((64, 48), np.float32), torch.float32)
-    c = torch.empty((48, 16), dtype=torch.float64, device="cuda")
-    with pytest.raises(corutv.CorutvError):
-        corutv.corutv_sketch(ctx.handle, a, dev(np.ones((64, 16))), c, 1, "tf32")
+@pytest.mark.parametrize("m,n,ell", [(700, 1000, 16), (1021, 333, 60), (130, 4100, 110)])
+def test_sketch_tf32_transposed_within_bound(ctx, m, n, ell):
+    """A^T Y in TF32 runs as (A^T) Y on a transposed FP32 copy of A (K-major
+    operands): the same TF32 bound as A X, with K = m."""
+    rng = np.random.default_rng(3 * m + n)
+    a32 = rng.standard_normal((m, n)).astype(np.float32)
+    y = rng.standard_normal((m, ell))
+    c = torch.empty((n, ell), dtype=torch.float64, device="cuda")
+    corutv.corutv_sketch(ctx.handle, dev(a32, torch.float32), dev(y), c, 1, "tf32")
+    assert ctx.sync() == 0
+    a64 = a32.astype(np.float64)
+    y32 = y.astype(np.float32).astype(np.float64)
+    ref = oracle.gemm_aty(a64, y32)
+    bound = (2 * 2.0 ** -10 + 2 * m * U32) * (np.abs(a64).T @ np.abs(y32))
+    assert np.all(np.abs(host(c) - ref) <= bound)
 
 
 def test_sketch_bf16_stream_k_many_pieces(ctx):
@@ -129,6 +139,35 @@ def test_sketch_bf16_stream_k_many_pieces(ctx):
     ref = oracle.gemm_ax(ar, xr)
     bound = 2 * n * U32 * (np.abs(ar) @ np.abs(xr))
     assert np.all(np.abs(host(c) - ref) <= bound)
+
+
+@pytest.mark.parametrize("m,n,k,p,q,pad", [(2000, 1500, 50, 10, 2, 0), (1500, 2000, 30, 10, 1, 1),
+                                           (777, 513, 10, 5, 0, 3)])
+def test_factor_tf32_error_budget(ctx, m, n, k, p, q, pad):
+    """TF32 sketches (A X on A, A^T Y on its transposed copy) + CholeskyQR2 +
+    the FP32-accurate split projection: within the TF32 budget of the FP64
+    oracle's error. pad > 0 gives A a row stride that is not a multiple of
+    16 bytes (the padded-copy path)."""
+    sigma = np.arange(1, min(m, n) + 1) ** -1.5
+    a = synth.spectrum_matrix(m, n, sigma, 0.0, m + n + 1)
+    a32 = a.astype(np.float32)
+    a64 = a32.astype(np.float64)
+    psi = synth.gaussian_psi(n, k + p, seed=9)
+    ref = oracle.corutv(a64, k, p, q, psi)
+    big = torch.zeros((m, n + pad), dtype=torch.float32, device="cuda")
+    big[:, :n] = dev(a32, torch.float32)
+    out = ctx.factor(big[:, :n], k, p, q, "tf32", psi=dev(psi))
+    assert ctx.sync() == 0
+    u, t, v = (host(out[x]) for x in ("U", "T", "V"))
+    na = np.linalg.norm(a64)
+    e_gpu = np.linalg.norm(a64 - u @ t @ v.T) / na
+    e_or = np.linalg.norm(a64 - ref["U"] @ ref["T"] @ ref["V"].T) / na
+    ell = k + p
+    budget = 4 * 2.0 ** -10 * np.sqrt(ell) * np.linalg.norm(a64, 2) / na
+    assert e_gpu <= e_or + budget, (e_gpu, e_or, budget)
+    assert np.linalg.norm(u.T @ u - np.eye(ell)) < 1e-5
+    assert np.linalg.norm(v.T @ v - np.eye(ell)) < 1e-5
+    assert np.all(np.tril(t, -1) == 0)
 
 
 @pytest.mark.parametrize("m,n,k,p,q", [(2000, 1500, 50, 10, 2), (1500, 2000, 30, 10, 1), (777, 513, 10, 5, 0)])
