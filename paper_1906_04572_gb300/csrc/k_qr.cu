@@ -17,42 +17,41 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // FP64 reciprocal and reciprocal square root without the FP64 divide / sqrt
-// sequences (each several hundred cycles on this part, where every dependent
-// FP64 operation costs about 65 cycles): an FP32 estimate y of the operand
-// scaled into FP32 range by a power of two (relative error |e| below about
-// 2^-22), then ONE third-order Householder step, i.e. the Taylor series of
-// the exact correction factor to second order:
+// sequences (each several hundred cycles on this part, where every FP64
+// warp instruction holds its sub-partition's FP64 pipe for about 64 cycles):
+// the hardware's FP64 estimate (PTX rcp.approx.ftz.f64 / rsqrt.approx.ftz.f64,
+// relative error below 2^-19.9 measured over 2^26 inputs spread across the
+// exponent range, about 40 cycles) followed by ONE third-order Householder
+// step, i.e. the Taylor series of the exact correction factor to second order:
 //   1/sqrt(x): e = 1 - x y^2,  y (1 - e)^-1/2 = y (1 + e/2 + 3e^2/8 + O(e^3))
 //   1/x      : e = 1 - x y,    y (1 - e)^-1   = y (1 + e + e^2 + O(e^3))
-// The truncation error is O(e^3) (about 2^-64), so the result is within a few
-// ulp; the dependent chain is 4 (resp. 3) FP64 operations instead of 6 (4)
-// for two Newton steps. For normal, finite, nonzero operands (1/sqrt:
-// positive); others fall back to the library operations.
+// The truncation error is O(e^3) (about 2^-60), so the result is within a
+// few ulp (1 ulp of the library operation over the same 2^26 inputs); the
+// dependent chain is 4 (resp. 3) FP64 operations after the estimate. For
+// operands of magnitude in [2^-999, 2^1001) (1/sqrt: positive), tested on the
+// bit pattern with integer operations; others fall back to the library
+// operations.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double scale_pow2(double x, int k) {  // x * 2^k, k within the exponent range
-    return __hiloint2double(__double2hiint(x) + (k << 20), __double2loint(x));
-}
-
 __device__ __forceinline__ double rsqrt_nr(double x) {
     const int hi = __double2hiint(x);
     const int ef = (hi >> 20) & 0x7ff;
-    if (ef == 0 || ef == 0x7ff || hi < 0) return 1.0 / sqrt(x);  // integer tests: an FP64 compare costs ~2 FMAs of latency
-    const int k = (ef - 1023) >> 1;            // x = xs 2^(2k), xs in [1, 4)
-    const double xs = scale_pow2(x, -2 * k);
-    const double y = (double)rsqrtf((float)xs);
-    const double e = fma(-xs, y * y, 1.0);
+    // integer tests (an FP64 compare costs ~2 FMAs of latency): positive and
+    // 2^-999 <= x < 2^1001, so that y^2 and the estimate stay normal
+    if (hi < 0 || (unsigned)(ef - 24) >= 2000u) return 1.0 / sqrt(x);
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double e = fma(-x, y * y, 1.0);
     const double c = fma(0.375, e, 0.5);       // 1/2 + 3e/8
-    return scale_pow2(fma(y * e, c, y), -k);
+    return fma(y * e, c, y);
 }
 
 __device__ __forceinline__ double rcp_nr(double x) {
     const int ef = (__double2hiint(x) >> 20) & 0x7ff;
-    if (ef == 0 || ef == 0x7ff) return 1.0 / x;
-    const int k = ef - 1023;                   // x = xs 2^k, |xs| in [1, 2)
-    const double xs = scale_pow2(x, -k);
-    const double y = (double)__frcp_rn((float)xs);
-    const double e = fma(-xs, y, 1.0);
-    return scale_pow2(fma(y, fma(e, e, e), y), -k);
+    if ((unsigned)(ef - 24) >= 2000u) return 1.0 / x;  // 2^-999 <= |x| < 2^1001: 1/x stays normal
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double e = fma(-x, y, 1.0);
+    return fma(y, fma(e, e, e), y);
 }
 
 // Right-looking Cholesky, upper factor, R^T R = G (+ shift I), one row of R
@@ -129,10 +128,12 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
     if (defic) {
         // dependence threshold: tau_rel times the largest diagonal entry
         for (int a = tid; a < ell; a += kCholThreads) defic[a] = 0;
-        if (tid == 0) {
+        if (warp == 0) {
             double mx = 0.0;
-            for (int a = 0; a < ell; ++a) mx = fmax(mx, g[a * ell + a]);
-            dmin_s = tau_rel * mx;
+            for (int a = lane; a < ell; a += 32) mx = fmax(mx, g[a * ell + a]);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) dmin_s = tau_rel * mx;
         }
     }
     const bool upd = warp != 0 && warp != 4;
@@ -145,18 +146,33 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
             // shift s = 11 (rows ell + ell (ell + 1)) u ||C||_F^2, u the unit roundoff of the
             // arithmetic that formed G (Fukaya et al.), then x100;
             // ||C||_F^2 = trace(G), summed only when a shift is needed
-            if (tid == 0) {
+            if (warp == 0) {
                 double t = 0.0;
-                for (int a = 0; a < ell; ++a) t += g[a * ell + a];
-                trace = t;
+                for (int a = lane; a < ell; a += 32) t += g[a * ell + a];
+#pragma unroll
+                for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                if (lane == 0) trace = t;
             }
             __syncthreads();
             const double u = unit_roundoff;
             shift = 11.0 * ((double)rows * ell + (double)ell * (ell + 1)) * u * trace * (attempt == 1 ? 1.0 : 100.0);
         }
-        for (int e = tid; e < ell * ell; e += kCholThreads) {
-            const int a = e / ell, b = e % ell;
-            S[a * ld + b] = g[a * ell + b] + (a == b ? shift : 0.0);
+        // eight loads in flight per thread before their stores
+        for (int e0 = 0; e0 < ell * ell; e0 += 8 * kCholThreads) {
+            double v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int e = e0 + tid + k * kCholThreads;
+                v[k] = e < ell * ell ? g[e] : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int e = e0 + tid + k * kCholThreads;
+                if (e < ell * ell) {
+                    const int a = e / ell, b = e % ell;
+                    S[a * ld + b] = v[k] + (a == b ? shift : 0.0);
+                }
+            }
         }
         if (tid == 0) fail_s = 0;
         __syncthreads();
@@ -172,8 +188,10 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
                 const bool dep = defic && !(d > dmin_s);  // numerically dependent column j+1
                 const bool ok = dep || pos_finite(d);
                 const double y = (ok && !dep) ? rsqrt_nr(d) : 0.0;  // y = 0 zeroes the rest of row j+1
+                if (lane == 0) ysh = y;
+                asm volatile("bar.sync 2, 64;" ::: "memory");
+                // the diagonal is not read before the end of the step: off the chain
                 if (lane == 0) {
-                    ysh = y;
                     if (dep) {
                         S[(j + 1) * ld + j + 1] = 1.0;
                         defic[j + 1] = 1;
@@ -183,7 +201,6 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
                         fail_s = 1;
                     }
                 }
-                asm volatile("bar.sync 2, 64;" ::: "memory");
             } else if (warp == 4) {
                 // rest of row j+1: step j's update now, the scaling once y is known
                 const double rjn = rj[j + 1];

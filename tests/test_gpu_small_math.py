@@ -1,11 +1,12 @@
 """Ulp-level checks of the FP64 reciprocal square root and reciprocal used by
 the small factorisations (they replace the FP64 divide / sqrt sequences with
-an FP32 estimate and one third-order refinement step).
+the hardware's FP64 estimate and one third-order refinement step, and fall
+back to the library operations outside 2^-999 .. 2^1001).
 
 Through the C ABI: the thin QR of C = [diag(s); 0] has the Gram diag(s^2),
 whose Cholesky factor is R = diag(|s|), computed on the device as
-d * rsqrt(d) with d = s^2. For s spread over many binades that product must
-match |s| to a few ulp (the second CholeskyQR pass factors an identity Gram
+d * rsqrt(d) with d = s^2. For s spread over many binades (both paths) that
+product must match |s| to a few ulp (the second CholeskyQR pass factors an identity Gram
 and leaves R unchanged). The reciprocal is exercised by the QRCP of a
 2 x 2 matrix, whose factors have closed forms.
 """
@@ -25,8 +26,9 @@ def test_cholesky_diagonal_rsqrt_within_few_ulp():
     with Context(0) as ctx:
         worst = 0.0
         for trial in range(8):
-            # magnitudes 2^-460 .. 2^460 so that s^2 stays normal; random signs
-            e = rng.uniform(-460, 460, ell)
+            # magnitudes 2^-510 .. 2^510 so that s^2 stays normal (the fast path
+            # takes 2^-999 <= d < 2^1001, the ends the library fallback); random signs
+            e = rng.uniform(-510, 510, ell)
             s = np.ldexp(rng.uniform(1.0, 2.0, ell), e.astype(int)) * rng.choice([-1.0, 1.0], ell)
             c = np.zeros((rows, ell))
             c[np.arange(ell), np.arange(ell)] = s
@@ -40,7 +42,7 @@ def test_cholesky_diagonal_rsqrt_within_few_ulp():
             ulps = np.abs(diag - np.abs(s)) / np.spacing(np.abs(s))
             worst = max(worst, float(ulps.max()))
             assert np.count_nonzero(np.triu(r, 1)) == 0
-        assert worst <= 8.0, worst  # one-step refinement from FP32 would show ~2^-44, i.e. hundreds of ulp
+        assert worst <= 8.0, worst  # a second-order step from a 2^-20 estimate would show ~2^-40, i.e. thousands of ulp
 
 
 def test_qrcp_2x2_closed_form():
