@@ -54,26 +54,37 @@ __device__ __forceinline__ double rcp_nr(double x) {
     return fma(y, fma(e, e, e), y);
 }
 
-// Right-looking Cholesky, upper factor, R^T R = G (+ shift I), one row of R
-// per step with a one-row lookahead and a single barrier per step. The upper
-// triangle is enumerated row by row from the bottom row up, columns right to
-// left (table `tri`), so the rows > j+1 of the trailing triangle form a
-// contiguous prefix of length (ell-j-2)(ell-j-1)/2. At step j row j of R is
-// final and rows > j carry the updates of steps < j. On this GPU every FP64
-// warp instruction holds its sub-partition's FP64 pipe for about 64 cycles
-// whatever the number of active lanes, so the pivot chain is kept to as few
-// FP64 instructions as possible. At the same time:
-//  * warp 0 forms the pivot d = G'(j+1, j+1) - R(j, j+1)^2, checks it,
-//    computes y = 1/sqrt(d) and R(j+1, j+1) = d y -- the chain that sets the
-//    pace;
-//  * warp 4 (same sub-partition, idle while warp 0 waits on its chain)
-//    applies step j's update to the rest of row j+1 in registers, takes y
-//    from warp 0 at a named barrier and stores the scaled row;
-//  * warps 1-3 and 5-7 apply step j's rank-1 update to rows > j+1, four
-//    independent entries per thread at a time.
+// Right-looking Cholesky, upper factor, R^T R = G (+ shift I), in the
+// square-root-free form: S holds the Schur complement rows, p_t = S_tt is the
+// t-th pivot and the step-t update is S_ac -= (S_ta / p_t) S_tc (a, c > t);
+// R_tc = S_tc / sqrt(p_t) once all the rows are final, for all rows at once.
+// The pivots form the only sequential chain: p_{t+1} = S'_{t+1,t+1} -
+// (S_{t,t+1} / p_t) S_{t,t+1}, one reciprocal (estimate + 3 FP64 operations)
+// and two FP64 operations per column. On this GPU every FP64 warp instruction
+// holds its sub-partition's FP64 pipe for about 64 cycles whatever the number
+// of active lanes (a predicated-off one too), so the chain runs alone on one
+// sub-partition and every FP64 instruction sits in a loop whose trip count is
+// the same on all lanes of its warp:
+//  * warp 0 (the chain): at step t it takes row t (final), forms r_t = 1/p_t
+//    and the scaled row L_t = r_t S_t, hands both to the update warps, then
+//    applies step t to row t+1 itself (lanes = columns) once the update warps
+//    have applied steps < t to that row -- which gives p_{t+1};
+//  * warps 1-3 and 5-7 (on the other three sub-partitions) apply step s to
+//    rows >= s+2: row s+2 first, then a signal to warp 0, then the rest of
+//    the trailing triangle (bottom-up enumeration `tri`), 32 entries per warp
+//    instruction;
+//  * warp 4 (sub-partition 0, shared with the chain) stays out of the loop.
+// The two hand-offs are producer/consumer named barriers (update warps
+// arrive, warp 0 waits: ids 1, 2 by the parity of the step; warp 0 arrives,
+// update warps wait: ids 3, 4), so no step waits for the whole trailing update
+// of the step before it. Each side runs at most one step ahead of the other
+// on a hand-off, so two ids per direction keep consecutive steps' arrivals
+// apart; the update warps' waits on the second hand-off also keep them in
+// step with each other.
 // rows = number of rows of the matrix whose Gram is factorised (for the shift).
 constexpr int kCholThreads = 256;
 constexpr int kCholUpdThreads = 192;
+constexpr int kCholMaxEll = 128;
 
 // d > 0 and finite, by integer tests on the bit pattern
 __device__ __forceinline__ bool pos_finite(double d) {
@@ -81,53 +92,48 @@ __device__ __forceinline__ bool pos_finite(double d) {
     return b > 0 && ((b >> 52) & 0x7ff) != 0x7ff;
 }
 
-// Warp 0: row a of S holds G' with the updates of steps < a; make it row a of R.
-// Returns false (on every lane) when the pivot is not positive and finite.
-// With `defic`, a pivot <= dmin marks column a numerically dependent instead:
-// R row a becomes e_a (so no later column uses it) and defic[a] = 1.
-__device__ __forceinline__ bool chol_finish_row(double* S, int ld, int ell, int a, int lane, int* defic,
-                                                double dmin) {
-    const double d = S[a * ld + a];
-    if (defic && !(d > dmin)) {
-        for (int c = a + 1 + lane; c < ell; c += 32) S[a * ld + c] = 0.0;
-        if (lane == 0) {
-            S[a * ld + a] = 1.0;
-            defic[a] = 1;
-        }
-        return true;
-    }
-    const bool ok = pos_finite(d);
-    if (ok) {
-        const double y = rsqrt_nr(d);
-        for (int c = a + 1 + lane; c < ell; c += 32) S[a * ld + c] *= y;
-        if (lane == 0) S[a * ld + a] = d * y;  // d / sqrt(d)
-    }
-    return ok;
+// d > m for m >= 0 finite, with the IEEE result (false for NaN), by integer tests
+__device__ __forceinline__ bool gt_nonneg(double d, double m) {
+    const long long b = __double_as_longlong(d);
+    return b > __double_as_longlong(m) && (b & 0x7fffffffffffffffLL) <= 0x7ff0000000000000LL;
 }
 
+__device__ __forceinline__ void bar_arrive(int id, int count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+template <bool kDefic>
 __global__ void __launch_bounds__(kCholThreads)
 cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, int* skip_out,
                 const int* cancel, double unit_roundoff, int* defic, double tau_rel) {
-    pdl_wait();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (cancel && *cancel) {
-        if (skip_out && tid == 0) *skip_out = 1;
-        return;
-    }
     extern __shared__ double S[];  // ell x (ell + 1) doubles, then the uint16 table
     const int ld = ell + 1;
     unsigned short* tri = reinterpret_cast<unsigned short*>(S + (size_t)ell * ld);
-    __shared__ double trace, ysh, dmin_s;
-    __shared__ int fail_s;
-    // table: bottom-up rows; row a holds columns ell-1 .. a
+    __shared__ double Lr[3][kCholMaxEll];  // L_t in slot t % 3 (read by step t of the update warps)
+    __shared__ double ys[kCholMaxEll];
+    __shared__ int rowdep[kCholMaxEll];
+    __shared__ double trace, dmin_s;
+    __shared__ int fail_at;  // step whose pivot failed (kNoFail: none)
+    constexpr int kNoFail = 1 << 30;
+    constexpr int kSync = 32 + kCholUpdThreads;  // warp 0 + update warps
+    // table (independent of the predecessor's output, built before waiting on
+    // it): bottom-up rows; row a holds columns ell-1 .. a
     for (int a = ell - 1 - tid; a >= 0; a -= kCholThreads) {
         const int rb = ell - 1 - a;            // rows below the top of the enumeration
         int e = rb * (rb + 1) / 2;
         for (int c = ell - 1; c >= a; --c) tri[e++] = (unsigned short)((a << 8) | c);
     }
-    if (defic) {
+    pdl_wait();
+    if (cancel && *cancel) {
+        if (skip_out && tid == 0) *skip_out = 1;
+        return;
+    }
+    if (kDefic) {
         // dependence threshold: tau_rel times the largest diagonal entry
-        for (int a = tid; a < ell; a += kCholThreads) defic[a] = 0;
         if (warp == 0) {
             double mx = 0.0;
             for (int a = lane; a < ell; a += 32) mx = fmax(mx, g[a * ell + a]);
@@ -136,8 +142,7 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
             if (lane == 0) dmin_s = tau_rel * mx;
         }
     }
-    const bool upd = warp != 0 && warp != 4;
-    const int ut = upd ? (warp - (warp > 4 ? 2 : 1)) * 32 + lane : 0;  // 0 .. 191
+    const int wu = warp - (warp > 4 ? 2 : 1);  // update warp 0 .. 5 (warps 1-3, 5-7)
     int attempt = 0;
     bool fail = false;
     for (; attempt < 3; ++attempt) {
@@ -174,87 +179,121 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
                 }
             }
         }
-        if (tid == 0) fail_s = 0;
+        for (int a = tid; a < ell; a += kCholThreads) {
+            rowdep[a] = 0;
+            if (kDefic) defic[a] = 0;
+        }
+        if (tid == 0) fail_at = kNoFail;
         __syncthreads();
-        if (warp == 0 && !chol_finish_row(S, ld, ell, 0, lane, defic, dmin_s) && lane == 0) fail_s = 1;
-        __syncthreads();
-        fail = fail_s != 0;
-        for (int j = 0; j + 1 < ell && !fail; ++j) {
-            const double* rj = S + j * ld;  // row j of R
-            if (warp == 0) {
-                // pivot chain: d, 1/sqrt(d), diagonal of R (lanes redundant; one instruction each)
-                const double rjn = rj[j + 1];
-                const double d = fma(-rjn, rjn, S[(j + 1) * ld + j + 1]);
-                const bool dep = defic && !(d > dmin_s);  // numerically dependent column j+1
-                const bool ok = dep || pos_finite(d);
-                const double y = (ok && !dep) ? rsqrt_nr(d) : 0.0;  // y = 0 zeroes the rest of row j+1
-                if (lane == 0) ysh = y;
-                asm volatile("bar.sync 2, 64;" ::: "memory");
-                // the diagonal is not read before the end of the step: off the chain
-                if (lane == 0) {
-                    if (dep) {
-                        S[(j + 1) * ld + j + 1] = 1.0;
-                        defic[j + 1] = 1;
-                    } else if (ok) {
-                        S[(j + 1) * ld + j + 1] = d * y;  // d / sqrt(d)
-                    } else {
-                        fail_s = 1;
+        // FP64 operations of the update warps sit in loops whose trip counts are
+        // the same on all lanes of a warp (a branch, not a predicate): a
+        // predicated-off FP64 instruction would still hold the pipe.
+        if (warp == 0) {
+            double p = S[0];
+            const double dmin = kDefic ? dmin_s : 0.0;
+            for (int t = 0;; ++t) {
+                // kDefic: a pivot <= dmin marks column t numerically dependent (r_t = 0: row t updates nothing)
+                const bool dep = kDefic && !gt_nonneg(p, dmin);
+                const bool ok = dep || pos_finite(p);
+                double rt = rcp_nr(p);
+                if (kDefic) rt = dep ? 0.0 : rt;
+                // L_t = r_t S_t (row t is final in S)
+                double* Lt = Lr[t % 3];
+                const double* St = S + t * ld;
+                double l0 = 0.0;
+#pragma unroll 1
+                for (int c0 = t; c0 < ell; c0 += 32) {
+                    const int c = c0 + lane;
+                    const double x = St[c < ell ? c : ell - 1] * rt;
+                    if (c < ell) Lt[c] = x;
+                    if (c0 == t) l0 = x;
+                }
+                if (!ok) {
+                    if (lane == 0) fail_at = t;
+                } else if (kDefic && dep) {
+                    if (lane == 0) {
+                        rowdep[t] = 1;
+                        defic[t] = 1;
                     }
                 }
-            } else if (warp == 4) {
-                // rest of row j+1: step j's update now, the scaling once y is known
-                const double rjn = rj[j + 1];
-                double* rn = S + (j + 1) * ld;
-                const int n_strips = (ell - j - 2 + 31) >> 5;  // columns j+2 .. ell-1
-                double v[4];
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int c = j + 2 + lane + 32 * t;
-                    if (t < n_strips && c < ell) v[t] = fma(-rjn, rj[c], rn[c]);
+                if (t <= ell - 3) bar_arrive(3 + (t & 1), kSync);  // L_t, fail_at -> update step t
+                if (!ok) {
+                    // update step t-1 still signals (it saw fail_at = t > t-1): take it so the barrier stays balanced
+                    if (t >= 1 && t - 1 <= ell - 3) bar_sync(1 + ((t - 1) & 1), kSync);
+                    break;
                 }
-                asm volatile("bar.sync 2, 64;" ::: "memory");
-                const double y = ysh;
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int c = j + 2 + lane + 32 * t;
-                    if (t < n_strips && c < ell) rn[c] = v[t] * y;
+                if (t == ell - 1) break;
+                const double w = __shfl_sync(0xffffffffu, l0, 1);  // L_{t,t+1}
+                if (t >= 1) bar_sync(1 + ((t - 1) & 1), kSync);    // update step t-1 has finished row t+1
+                // step t on row t+1 (columns t+1 ..): S_{t+1,c} -= L_{t,t+1} S_{t,c}
+                double* Sn = S + (t + 1) * ld;
+                double p_next = 0.0;
+#pragma unroll 1
+                for (int c0 = t + 1; c0 < ell; c0 += 32) {
+                    const int c = c0 + lane;
+                    const int cc = c < ell ? c : ell - 1;
+                    const double x = fma(-w, St[cc], Sn[cc]);
+                    if (c < ell) Sn[c] = x;
+                    if (c0 == t + 1) p_next = x;
                 }
-            } else if (upd) {
-                const int len = (ell - j - 2) * (ell - j - 1) / 2;  // rows > j+1
-                for (int e0 = ut; e0 < len; e0 += 4 * kCholUpdThreads) {
-                    int ac[4];
-                    double ra[4], rc[4], sv[4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int e = e0 + k * kCholUpdThreads;
-                        ac[k] = e < len ? (int)tri[e] : -1;
+                p = __shfl_sync(0xffffffffu, p_next, 0);
+                __syncwarp();
+            }
+        } else if (warp != 4) {
+            for (int s = 0; s <= ell - 3; ++s) {
+                bar_sync(3 + (s & 1), kSync);  // row s and L_s are final
+                if (fail_at <= s) break;       // a later step's failure does not stop this one
+                const double* rs = S + s * ld;
+                const double* Ls = Lr[s % 3];
+                // row s+2 first (columns s+2 .. ell-1), then the signal
+                const int n1 = ell - s - 2;
+                {
+                    const double l = Ls[s + 2];
+                    double* Sa = S + (s + 2) * ld;
+                    for (int i0 = 32 * wu; i0 < n1; i0 += kCholUpdThreads) {
+                        const int c = s + 2 + i0 + lane;
+                        const int cc = c < ell ? c : ell - 1;
+                        const double x = fma(-l, rs[cc], Sa[cc]);
+                        if (c < ell) Sa[c] = x;
                     }
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (ac[k] >= 0) {
-                            const int a = ac[k] >> 8, c = ac[k] & 0xff;
-                            ra[k] = rj[a];
-                            rc[k] = rj[c];
-                            sv[k] = S[a * ld + c];
-                        }
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (ac[k] >= 0) S[(ac[k] >> 8) * ld + (ac[k] & 0xff)] = fma(-ra[k], rc[k], sv[k]);
+                }
+                bar_arrive(1 + (s & 1), kSync);
+                // rows >= s+3: the prefix tri[0 .. len3) of the bottom-up enumeration
+                const int len3 = (n1 - 1) * n1 / 2;
+#pragma unroll 2
+                for (int e0 = 32 * wu; e0 < len3; e0 += kCholUpdThreads) {
+                    const int e = e0 + lane;
+                    const int ac = tri[e < len3 ? e : len3 - 1];
+                    const int a = ac >> 8, c = ac & 0xff;
+                    const double x = fma(-Ls[a], rs[c], S[a * ld + c]);
+                    if (e < len3) S[a * ld + c] = x;
                 }
             }
-            __syncthreads();
-            fail = fail_s != 0;
         }
-        if (!fail) break;
         __syncthreads();
+        fail = fail_at != kNoFail;
+        if (!fail) break;
     }
     pdl_trigger();  // the successor may launch while R is written
     const bool broke = attempt == 3;
-    for (int e = tid; e < ell * ell; e += kCholThreads) {
-        const int a = e / ell, b = e % ell;
-        double v = (b >= a) ? S[a * ld + b] : 0.0;
-        if (broke) v = (a == b) ? 1.0 : 0.0;
-        r[e] = v;
+    // R_tc = S_tc / sqrt(p_t) for c >= t (the diagonal p_t / sqrt(p_t)); dependent rows -> e_t
+    for (int t = tid; t < ell; t += kCholThreads) ys[t] = (broke || rowdep[t]) ? 0.0 : rsqrt_nr(S[t * ld + t]);
+    __syncthreads();
+    for (int a = warp; a < ell; a += kCholThreads / 32) {
+        double* ra = r + (size_t)a * ell;
+        if (broke || rowdep[a]) {
+            for (int b = lane; b < ell; b += 32) ra[b] = (a == b) ? 1.0 : 0.0;
+            continue;
+        }
+        const double ya = ys[a];
+        const double* Sa = S + a * ld;
+        int b0 = 0;
+        for (; b0 + 31 < a; b0 += 32) ra[b0 + lane] = 0.0;  // strips left of the diagonal
+        for (; b0 < ell; b0 += 32) {
+            const int b = b0 + lane;
+            const double x = Sa[b < ell ? b : ell - 1] * ya;
+            if (b < ell) ra[b] = b >= a ? x : 0.0;
+        }
     }
     if (tid == 0) {
         if (broke) atomicExch(&flags[FLAG_BREAKDOWN], 1);
@@ -812,14 +851,15 @@ __global__ void copy_small_kernel(const double* src, int n, TD* dst, const int* 
 cudaError_t launch_cholesky(const double* g, int64_t ell, int64_t rows, double* r, int* flags,
                                int* skip_out, const int* cancel, cudaStream_t st, double unit_roundoff,
                                int* defic, double tau_rel) {
+    if (ell < 1 || ell > kCholMaxEll) return cudaErrorInvalidValue;
     const size_t smem = sizeof(double) * (size_t)ell * (ell + 1) + sizeof(unsigned short) * (size_t)ell * (ell + 1) / 2;
-    cudaError_t e = cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    auto kern = defic ? cholesky_kernel<true> : cholesky_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launch();
     {
-        cudaError_t pe_ = launch_pdl(cholesky_kernel, dim3(1), dim3(kCholThreads), (size_t)(smem), st, g, (int)ell, rows, r, flags, skip_out, cancel, unit_roundoff,
-                                                   defic, tau_rel);
+        cudaError_t pe_ = launch_pdl(kern, dim3(1), dim3(kCholThreads), smem, st, g, (int)ell, rows, r, flags,
+                                     skip_out, cancel, unit_roundoff, defic, tau_rel);
         if (pe_ != cudaSuccess) return pe_;
     }
     return cudaGetLastError();
