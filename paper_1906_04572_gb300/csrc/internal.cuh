@@ -14,6 +14,8 @@
 #include <stdint.h>
 
 #include <cstddef>
+#include <mutex>
+#include <unordered_set>
 
 namespace corutv {
 
@@ -84,9 +86,24 @@ void count_launch();
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Every kernel asks for the largest shared-memory carve-out once, so that the
+// switches between the tensor-core products (about 200 KB of shared memory
+// per block) and the small kernels around them do not reconfigure the SMs'
+// L1 / shared split.
+inline void prefer_max_shared(const void* fn) {
+    static std::mutex mu;
+    static std::unordered_set<const void*> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.insert(fn).second)
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+            cudaGetLastError();  // a preference only: ignore a refusal
+}
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                               Args&&... args) {
+    prefer_max_shared(reinterpret_cast<const void*>(kernel));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;

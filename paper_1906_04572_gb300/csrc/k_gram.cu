@@ -203,6 +203,7 @@ cudaError_t launch_gram_f32(const float* x, int64_t ldx, const float* y, int64_t
     cfg.attrs = attr;
     cfg.numAttrs = 2;
     count_launch();
+    prefer_max_shared(reinterpret_cast<const void*>(gram_f32_kernel));
     return cudaLaunchKernelEx(&cfg, gram_f32_kernel, x, ldx, y, ldy, len, ell, out, work, cnt, p, cancel);
 }
 
