@@ -997,16 +997,13 @@ corutv_status normest(corutv_ctx* ctx, const FactorPlan& pl, const FactorBufs& b
     double* w = static_cast<double*>(b.c2);   // n
     double* lam = b.g;                        // scalar
     CK(launch_vec_fill(v, n, 1.0 / std::sqrt((double)n), ctx->stream));
-    const int spm = gemm_simt_splits(m, n, ctx->num_sms), spn = gemm_simt_splits(n, m, ctx->num_sms);
+    // M^T u as row-chunk partials (added in chunk order) that fit the partial buffer
+    const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)32, pl.part_elems / pl.ldn, m}));
     for (int it = 0; it < 50; ++it) {
-        GemmArgs g1{A_ROWS, B_PANEL, O_PANEL, tm, T_F64, mat, ldm_user, v, pl.ldn, b.part, pl.ldm, pl.ldm,
-                    m, n, 1, spm, nullptr};
-        CK(launch_gemm_simt(g1, ctx->stream));
-        CK(launch_reduce_splits(b.part, T_F64, spm, pl.ldm, u, T_F64, pl.ldm, m, 1, pl.ldm, nullptr, ctx->stream));
-        GemmArgs g2{A_COLS, B_PANEL, O_PANEL, tm, T_F64, mat, ldm_user, u, pl.ldm, b.part, pl.ldn, pl.ldn,
-                    n, m, 1, spn, nullptr};
-        CK(launch_gemm_simt(g2, ctx->stream));
-        CK(launch_reduce_splits(b.part, T_F64, spn, pl.ldn, w, T_F64, pl.ldn, n, 1, pl.ldn, nullptr, ctx->stream));
+        CK(launch_gemv_rows(mat, tm, ldm_user, m, n, v, u, ctx->stream));
+        CK(launch_gemv_cols_partial(mat, tm, ldm_user, m, n, u, static_cast<double*>(b.part), pl.ldn, chunks,
+                                    ctx->stream));
+        CK(launch_reduce_splits(b.part, T_F64, chunks, pl.ldn, w, T_F64, pl.ldn, n, 1, pl.ldn, nullptr, ctx->stream));
         CK(launch_vec_normalize(w, v, n, lam, ctx->stream));
     }
     double h = 0.0;

@@ -86,6 +86,22 @@ void count_launch();
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+#ifdef __CUDACC__
+// Exact float -> double by integer operations (normal and zero inputs; the
+// rest through the conversion instruction). The FP64 conversion instruction
+// would take a slot of the FP64 pipe, which this GPU has little of.
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;  // zero, subnormal, inf, nan
+    const unsigned long long s = (unsigned long long)(u >> 31) << 63;
+    const unsigned long long bits = s | ((unsigned long long)(e + 896u) << 52) |
+                                    ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double f2d_exact(double d) { return d; }
+#endif
+
 // Every kernel asks for the largest shared-memory carve-out once, so that the
 // switches between the tensor-core products (about 200 KB of shared memory
 // per block) and the small kernels around them do not reconfigure the SMs'
@@ -224,5 +240,13 @@ int rpca_update_blocks(int64_t rows, int64_t cols);
 // with ||w|| stored in *lam (one block).
 cudaError_t launch_vec_fill(double* v, int64_t n, double value, cudaStream_t st);
 cudaError_t launch_vec_normalize(const double* w, double* v, int64_t n, double* lam, cudaStream_t st);
+// y = M x for a row-major m x n matrix M (FP32 or FP64, row stride ldm) and an
+// FP64 vector x; FP64 accumulation, one warp per row.
+cudaError_t launch_gemv_rows(const void* mat, ElemType tm, int64_t ldm, int64_t m, int64_t n, const double* x,
+                             double* y, cudaStream_t st);
+// part[q * ldp + c] = sum over rows i of chunk q (chunk_rows rows each) of
+// M[i][c] u[i]; FP64 accumulation. The chunks are then added in order.
+cudaError_t launch_gemv_cols_partial(const void* mat, ElemType tm, int64_t ldm, int64_t m, int64_t n,
+                                     const double* u, double* part, int64_t ldp, int chunks, cudaStream_t st);
 
 }  // namespace corutv

@@ -46,18 +46,6 @@ GramPlan gram_plan(int64_t len, int ell, int num_sms) {
     return p;
 }
 
-// exact float -> double by integer operations (normal and zero inputs); the
-// FP64 conversion instruction would cost a slot of the FP64 pipe
-__device__ __forceinline__ double f2d_exact(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)f;  // zero, subnormal, inf, nan
-    const unsigned long long s = (unsigned long long)(u >> 31) << 63;
-    const unsigned long long bits = s | ((unsigned long long)(e + 896u) << 52) |
-                                    ((unsigned long long)(u & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)bits);
-}
-
 __global__ void __launch_bounds__(kGThreads)
 gram_f32_kernel(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_t len, int ell, double* out,
                 float* cpart, int* cnt, GramPlan pl, const int* cancel) {

@@ -97,7 +97,10 @@ __global__ void rank_z_kernel(const double* rt, const TQ* q2, int64_t ldq2, cons
     }
 }
 
-// Fused S / Y / B update over a tile of kUpdRows x kUpdCols elements.
+// Fused S / Y / B update over a tile of kUpdRows x kUpdCols elements, in the
+// arithmetic of the state (TS): FP32 for FP32 data (on this GPU the FP64
+// pipe runs at a sixtieth of the FP32 rate), FP64 for FP64 data. The squared
+// residual is summed per thread in TS and across the block in FP64.
 template <typename TM, typename TS>
 __global__ void __launch_bounds__(kUpdCols)
 rpca_update_kernel(const TM* m, int64_t ldm, int64_t rows, int64_t cols, TS* s, TS* y, TS* b,
@@ -107,45 +110,80 @@ rpca_update_kernel(const TM* m, int64_t ldm, int64_t rows, int64_t cols, TS* s, 
     pdl_wait();
     if (cancel && *cancel) return;
     __shared__ double red[32];
-    __shared__ double Us[kUpdRows][kMaxEll];
+    __shared__ TS Us[kUpdRows][kMaxEll];
     const int r = *rank;
     const int64_t i0 = (int64_t)blockIdx.y * kUpdRows;
     const int64_t c = (int64_t)blockIdx.x * kUpdCols + threadIdx.x;
     for (int e = threadIdx.x; e < kUpdRows * kMaxEll; e += blockDim.x) {
         const int ii = e / kMaxEll, sidx = e % kMaxEll;
         const int64_t i = i0 + ii;
-        Us[ii][sidx] = (i < rows && sidx < r) ? u[(int64_t)sidx * ldu + i] : 0.0;
+        Us[ii][sidx] = (i < rows && sidx < r) ? (TS)u[(int64_t)sidx * ldu + i] : (TS)0;
     }
-    double zc[kMaxEll];
+    TS zc[kMaxEll];
     if (c < cols) {
 #pragma unroll 4
-        for (int sidx = 0; sidx < ell; ++sidx) zc[sidx] = (sidx < r) ? z[(int64_t)sidx * ldz + c] : 0.0;
+        for (int sidx = 0; sidx < ell; ++sidx) zc[sidx] = (sidx < r) ? (TS)z[(int64_t)sidx * ldz + c] : (TS)0;
     }
     __syncthreads();
-    const double inv_mu = 1.0 / mu, inv_mu_next = 1.0 / mu_next, delta = lambda / mu;
-    double acc = 0.0;
+    const TS inv_mu = (TS)(1.0 / mu), inv_mu_next = (TS)(1.0 / mu_next), delta = (TS)(lambda / mu), muc = (TS)mu;
+    TS acc = 0;
     if (c < cols) {
         for (int ii = 0; ii < kUpdRows; ++ii) {
             const int64_t i = i0 + ii;
             if (i >= rows) break;
-            double l = 0.0;
-            for (int sidx = 0; sidx < r; ++sidx) l += Us[ii][sidx] * zc[sidx];
+            TS l = 0;
+            for (int sidx = 0; sidx < r; ++sidx) l = fma(Us[ii][sidx], zc[sidx], l);
             const int64_t e = i * cols + c;
-            const double mv = (double)m[i * ldm + c];
-            const double yv = (double)y[e];
-            const double x = mv - l + yv * inv_mu;
-            const double mag = fabs(x) - delta;
-            const double sv = mag > 0.0 ? copysign(mag, x) : 0.0;
-            const double res = mv - l - sv;
-            const double yn = yv + mu * res;
-            s[e] = (TS)sv;
-            y[e] = (TS)yn;
-            b[e] = (TS)(mv - sv + yn * inv_mu_next);
-            acc += res * res;
+            const TS mv = (TS)m[i * ldm + c];
+            const TS yv = y[e];
+            const TS x = mv - l + yv * inv_mu;
+            const TS mag = fabs(x) - delta;
+            const TS sv = mag > (TS)0 ? copysign(mag, x) : (TS)0;
+            const TS res = mv - l - sv;
+            const TS yn = yv + muc * res;
+            s[e] = sv;
+            y[e] = yn;
+            b[e] = mv - sv + yn * inv_mu_next;
+            acc = fma(res, res, acc);
         }
     }
-    const double t = block_sum(acc, red);
+    const double t = block_sum(f2d_exact(acc), red);
     if (threadIdx.x == 0) res_part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+// Power-iteration products for the default mu0 (||M||_2). y = M x: one warp
+// per row, lanes along the row (coalesced), FP64 accumulation.
+template <typename TM>
+__global__ void gemv_rows_kernel(const TM* mat, int64_t ldm, int64_t m, int64_t n, const double* x, double* y) {
+    pdl_trigger();
+    pdl_wait();
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < m; i += nw) {
+        const TM* row = mat + i * ldm;
+        double a = 0.0;
+        for (int64_t c = lane; c < n; c += 32) a = fma(f2d_exact(row[c]), x[c], a);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) y[i] = a;
+    }
+}
+
+// Column partials of M^T u over row chunks: thread = column (coalesced), block
+// row = chunk; FP64 accumulation in row order.
+template <typename TM>
+__global__ void gemv_cols_kernel(const TM* mat, int64_t ldm, int64_t m, int64_t n, const double* u, double* part,
+                                 int64_t ldp, int64_t chunk_rows) {
+    pdl_trigger();
+    pdl_wait();
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.y * chunk_rows;
+    const int64_t r1 = r0 + chunk_rows < m ? r0 + chunk_rows : m;
+    if (c >= n) return;
+    double a = 0.0;
+    for (int64_t i = r0; i < r1; ++i) a = fma(f2d_exact(mat[i * ldm + c]), u[i], a);
+    part[(int64_t)blockIdx.y * ldp + c] = a;
 }
 
 // zeta_j and the convergence flag; one block, fixed summation order.
@@ -175,26 +213,26 @@ reconstruct_kernel(const double* u, int64_t ldu, const double* z, int64_t ldz, c
                    int64_t rows, int64_t cols, TL* lout, int64_t ldl) {
     pdl_trigger();
     pdl_wait();
-    __shared__ double Us[kUpdRows][kMaxEll];
+    __shared__ TL Us[kUpdRows][kMaxEll];
     const int r = *rank;
     const int64_t i0 = (int64_t)blockIdx.y * kUpdRows;
     const int64_t c = (int64_t)blockIdx.x * kUpdCols + threadIdx.x;
     for (int e = threadIdx.x; e < kUpdRows * kMaxEll; e += blockDim.x) {
         const int ii = e / kMaxEll, sidx = e % kMaxEll;
         const int64_t i = i0 + ii;
-        Us[ii][sidx] = (i < rows && sidx < r) ? u[(int64_t)sidx * ldu + i] : 0.0;
+        Us[ii][sidx] = (i < rows && sidx < r) ? (TL)u[(int64_t)sidx * ldu + i] : (TL)0;
     }
-    double zc[kMaxEll];
+    TL zc[kMaxEll];
     if (c < cols)
-        for (int sidx = 0; sidx < ell; ++sidx) zc[sidx] = (sidx < r) ? z[(int64_t)sidx * ldz + c] : 0.0;
+        for (int sidx = 0; sidx < ell; ++sidx) zc[sidx] = (sidx < r) ? (TL)z[(int64_t)sidx * ldz + c] : (TL)0;
     __syncthreads();
     if (c >= cols) return;
     for (int ii = 0; ii < kUpdRows; ++ii) {
         const int64_t i = i0 + ii;
         if (i >= rows) break;
-        double l = 0.0;
-        for (int sidx = 0; sidx < r; ++sidx) l += Us[ii][sidx] * zc[sidx];
-        lout[i * ldl + c] = (TL)l;
+        TL l = 0;
+        for (int sidx = 0; sidx < r; ++sidx) l = fma(Us[ii][sidx], zc[sidx], l);
+        lout[i * ldl + c] = l;
     }
 }
 
@@ -247,6 +285,32 @@ cudaError_t launch_vec_normalize(const double* w, double* v, int64_t n, double* 
         if (pe_ != cudaSuccess) return pe_;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_gemv_rows(const void* mat, ElemType tm, int64_t ldm, int64_t m, int64_t n, const double* x,
+                             double* y, cudaStream_t st) {
+    const unsigned blocks = (unsigned)std::min<int64_t>((m + 7) / 8, 1216);  // 8 rows (warps) per block
+    count_launch();
+    cudaError_t e = tm == T_F32
+        ? launch_pdl(gemv_rows_kernel<float>, dim3(blocks), dim3(256), (size_t)0, st, static_cast<const float*>(mat),
+                     ldm, m, n, x, y)
+        : launch_pdl(gemv_rows_kernel<double>, dim3(blocks), dim3(256), (size_t)0, st,
+                     static_cast<const double*>(mat), ldm, m, n, x, y);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_gemv_cols_partial(const void* mat, ElemType tm, int64_t ldm, int64_t m, int64_t n,
+                                     const double* u, double* part, int64_t ldp, int chunks, cudaStream_t st) {
+    if (chunks < 1 || ldp < n) return cudaErrorInvalidValue;
+    const int64_t chunk_rows = (m + chunks - 1) / chunks;
+    const dim3 grid((unsigned)((n + 255) / 256), (unsigned)chunks);
+    count_launch();
+    cudaError_t e = tm == T_F32
+        ? launch_pdl(gemv_cols_kernel<float>, grid, dim3(256), (size_t)0, st, static_cast<const float*>(mat), ldm, m,
+                     n, u, part, ldp, chunk_rows)
+        : launch_pdl(gemv_cols_kernel<double>, grid, dim3(256), (size_t)0, st, static_cast<const double*>(mat), ldm,
+                     m, n, u, part, ldp, chunk_rows);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 int rpca_update_blocks(int64_t rows, int64_t cols) {
