@@ -197,16 +197,20 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
                 const bool ok = dep || pos_finite(p);
                 double rt = rcp_nr(p);
                 if (kDefic) rt = dep ? 0.0 : rt;
-                // L_t = r_t S_t (row t is final in S)
+                // L_t = r_t S_t (row t is final in S): strip 0 inline, the rest in a loop
                 double* Lt = Lr[t % 3];
                 const double* St = S + t * ld;
-                double l0 = 0.0;
+                double l0;
+                {
+                    const int c = t + lane;
+                    l0 = St[c < ell ? c : ell - 1] * rt;
+                    if (c < ell) Lt[c] = l0;
+                }
 #pragma unroll 1
-                for (int c0 = t; c0 < ell; c0 += 32) {
+                for (int c0 = t + 32; c0 < ell; c0 += 32) {
                     const int c = c0 + lane;
                     const double x = St[c < ell ? c : ell - 1] * rt;
                     if (c < ell) Lt[c] = x;
-                    if (c0 == t) l0 = x;
                 }
                 if (!ok) {
                     if (lane == 0) fail_at = t;
@@ -227,16 +231,21 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
                 if (t >= 1) bar_sync(1 + ((t - 1) & 1), kSync);    // update step t-1 has finished row t+1
                 // step t on row t+1 (columns t+1 ..): S_{t+1,c} -= L_{t,t+1} S_{t,c}
                 double* Sn = S + (t + 1) * ld;
-                double p_next = 0.0;
+                double p_next;
+                {
+                    const int c = t + 1 + lane;
+                    const int cc = c < ell ? c : ell - 1;
+                    p_next = fma(-w, St[cc], Sn[cc]);
+                    if (c < ell) Sn[c] = p_next;
+                }
+                p = __shfl_sync(0xffffffffu, p_next, 0);
 #pragma unroll 1
-                for (int c0 = t + 1; c0 < ell; c0 += 32) {
+                for (int c0 = t + 33; c0 < ell; c0 += 32) {
                     const int c = c0 + lane;
                     const int cc = c < ell ? c : ell - 1;
                     const double x = fma(-w, St[cc], Sn[cc]);
                     if (c < ell) Sn[c] = x;
-                    if (c0 == t + 1) p_next = x;
                 }
-                p = __shfl_sync(0xffffffffu, p_next, 0);
                 __syncwarp();
             }
         } else if (warp != 4) {
