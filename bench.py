@@ -141,13 +141,18 @@ class ClockSampler:
 
 
 def dist_setup():
+    """Rank, world size and local rank from the launcher's environment; joins
+    the process group once (NCCL, or gloo with BENCH_BACKEND=gloo)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import datetime
         import torch.distributed as dist
-        backend = "nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo"
-        dist.init_process_group(backend=backend)
+        if not dist.is_initialized():
+            backend = "nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+            timeout = datetime.timedelta(seconds=int(os.environ.get("BENCH_PG_TIMEOUT", "1800")))
+            dist.init_process_group(backend=backend, timeout=timeout)
     return world, rank, local
 
 
@@ -451,6 +456,14 @@ def run_ours(args):
                  "traffic": SKETCH_TRAFFIC_BYTES.get((args.workload, prec)),
                  "bytes_per_launch": bytes_per_launch, "launch_ms": per_launch_ms,
                  "launches_timed": sk_n})
+    if prec in ("bf16", "tf32"):
+        # the raw fraction of the tensor-core peak for this operand type, beside the
+        # attainable (HBM) roofline above: the products' arithmetic intensity is only
+        # 2 ell / s flop per byte of A
+        tpk = peaks["bf16_tflops"] * (1.0 if prec == "bf16" else TF32_OF_BF16)
+        roof["tensor"] = {"achieved_tflops": tfs, "peak_tflops": tpk, "frac_raw": tfs / tpk,
+                          "arithmetic_intensity": 2.0 * m * n * ell / bytes_per_launch,
+                          "peak_source": peaks_kind + (" (tf32 = bf16 x 0.5, nominal ratio)" if prec == "tf32" else "")}
 
     stages = {name: {"ms_per_step": prof[i][0] / psteps, "intervals": prof[i][1]}
               for i, name in enumerate(["sketch", "project", "orth", "qrcp", "factor"])}
