@@ -348,6 +348,61 @@ def serving_c5(device_index, nreq, rate, prec, slots):
                       "directions), FP32, seed 0; product formed on the device from the seeded factors"}
 
 
+def serving_capacity(device_index, nreq, slots, nerr=64):
+    """The first nreq requests of the serving stream submitted at once, in the
+    mixed-precision form (FP32 data, bf16 sketches) and on the plain FP64 path
+    (FP64 data and arithmetic): completed requests per second, and the
+    reconstruction error ||A - U T V^T|| / ||A|| of the first nerr requests in
+    both forms ("equal error": the mixed error within 1 % of the FP64 one)."""
+    import torch
+    import synth
+    from paper_1906_04572_gb300 import Context, corutv
+    reqs = synth.serving_requests(count=nreq, rate_per_s=1.0, seed=0)
+    dev = torch.device("cuda", device_index)
+    res = {}
+    errs = {}
+    for form, dt, prec in (("mixed_bf16", torch.float32, "bf16"), ("fp64", torch.float64, "f64")):
+        mats, outs = [], []
+        for r in reqs:
+            u, sig, v = synth.serving_factors(r)
+            a = (torch.from_numpy(u * sig).to(dev) @ torch.from_numpy(v).to(dev).T).to(dt).contiguous()
+            ell = r.k + r.p
+            outs.append(tuple(torch.empty(sh, device=dev, dtype=dt) for sh in ((r.m, ell), (ell, ell), (r.n, ell))))
+            mats.append(a)
+        torch.cuda.synchronize()
+        with Context(device_index, max_slots=slots) as sctx:
+            warm = [corutv.corutv_submit(sctx.handle, corutv.make_request(mats[i], reqs[i].k, reqs[i].p, reqs[i].q,
+                                                                          prec, *outs[i], seed=reqs[i].seed))
+                    for i in range(min(slots, nreq))]
+            for tk in warm:
+                corutv.corutv_poll(sctx.handle, tk, timeout_us=600_000_000)
+            t0 = time.perf_counter()
+            tickets = [corutv.corutv_submit(sctx.handle, corutv.make_request(a, r.k, r.p, r.q, prec, *o, seed=r.seed))
+                       for r, a, o in zip(reqs, mats, outs)]
+            for tk in tickets:
+                st, _ = corutv.corutv_poll(sctx.handle, tk, timeout_us=600_000_000)
+                if st != corutv.OK:
+                    raise RuntimeError(f"serving request failed with status {st}")
+            wall = time.perf_counter() - t0
+        e = []
+        for a, (U, T, V) in list(zip(mats, outs))[:nerr]:
+            a64 = a.double()
+            e.append(float(torch.linalg.norm(a64 - (U.double() @ T.double()) @ V.double().T) / torch.linalg.norm(a64)))
+        errs[form] = np.array(e)
+        res[form] = {"solves_per_s": nreq / wall, "wall_s": wall,
+                     "tflops": sum(flops_per_factor(r.m, r.n, r.k + r.p, r.q) for r in reqs) / wall / 1e12,
+                     "e_rel_median": float(np.median(errs[form]))}
+        del mats, outs
+        torch.cuda.empty_cache()
+    ratio = errs["mixed_bf16"] / errs["fp64"]
+    res.update({"requests": nreq, "slots": slots, "errors_compared": int(len(ratio)),
+                "error_ratio_max": float(ratio.max()), "error_ratio_median": float(np.median(ratio)),
+                "equal_error": bool(ratio.max() <= 1.01),
+                "speedup": res["mixed_bf16"]["solves_per_s"] / res["fp64"]["solves_per_s"],
+                "kind": "all requests submitted at once (capacity); same seeded requests and Psi in both forms"})
+    return res
+
+
 def rpca_c4(ctx, device, prec="f32"):
     """ALM-CoRUTV on the RPCA workload (4800 x 1200, rank 5, 10 % uniform
     +-50 outliers, FP32), 50 iterations."""
@@ -512,6 +567,7 @@ def run_ours(args):
     if not args.no_extra:
         extra["serving"] = serving_c5(local, args.serve_requests, args.serve_rate, prec if prec != "f64" else "f32",
                                       8)
+        extra["serving"]["capacity_vs_fp64"] = serving_capacity(local, args.serve_capacity, 8)
         extra["rpca"] = rpca_c4(ctx, device)
         if args.c3:
             extra["c3"] = c3_line(ctx, device, ("bf16", "tf32", "f32"), 3)
@@ -562,6 +618,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--c3", type=int, default=1, help="1: also time the 20000 x 20000 workload")
+    ap.add_argument("--serve-capacity", type=int, default=128,
+                    help="requests of the serving stream timed at once in the mixed and the FP64 form")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":
