@@ -218,6 +218,32 @@ def corutv(a: np.ndarray, k: int, p: int, q: int, psi: np.ndarray | None = None,
     return out
 
 
+def corutv_dapprox(a: np.ndarray, k: int, p: int, q: int, psi: np.ndarray) -> dict:
+    """CoR-UTV with the single-pass core (Sec. 3.1, the paragraph after eq. 9;
+    Algorithm 1, its "D_approx" alternative): D = Q1^T A Q2 (eq. 7) is replaced
+    by D_approx = Q1^T C1 (Q2^T X)^+, where C1 = A X is the last product with A
+    and X the matrix it was formed from -- Psi when q = 0, else the
+    re-orthonormalised C2 of the round before (the text writes Psi, Algorithm 1
+    the current C2; the text's reading, applied to the power method, is the
+    matrix C1 was formed from). The loop is the oracle's own (the same steps as
+    `corutv`); the pseudo-inverse of the ell x ell matrix Q2^T X is numpy's
+    (SVD-based) pinv. Returns dict with U, T, V, perm, Q1, Q2, D."""
+    a = _f64(a)
+    x = _f64(psi).copy()
+    n, l = x.shape
+    assert l == k + p and a.shape[1] == n
+    for it in range(q + 1):
+        c1 = gemm_ax(a, x)                 # eq. 4
+        q1, _ = qr(c1)
+        c2 = gemm_aty(a, q1)               # eq. 5 with C1 -> Q1
+        if it < q:
+            x, _ = qr(c2)
+    q2, _ = qr(c2)
+    d = (q1.T @ c1) @ np.linalg.pinv(q2.T @ x)
+    qt, rt, perm = qrcp(d)                 # eq. 8
+    return {"U": q1 @ qt, "T": rt, "V": q2[:, perm], "perm": perm, "Q1": q1, "Q2": q2, "D": d}
+
+
 def shrink(x: np.ndarray, delta: float) -> np.ndarray:
     x = _f64(x)
     out = np.empty_like(x)

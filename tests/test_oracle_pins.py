@@ -216,6 +216,42 @@ def test_d_equals_r2_transpose(oracle_lib):
     assert _rel(o["D"], r2.T) < 1e-12
 
 
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_dapprox_equals_exact_d(oracle_lib, q):
+    """The single-pass core D_approx = Q1^T C1 (Q2^T X)^+ (Sec. 3.1): C1 = A X and
+    C2 = A^T Q1 = Q2 R2 give Q1^T C1 = R2^T (Q2^T X), so D_approx = R2^T = D of
+    eq. 7 whenever Q2^T X is invertible -- for any A, not only an exactly
+    low-rank one. A mistake in the operand (Psi in place of X when q > 0, a
+    transposed or missing pseudo-inverse) breaks the equality."""
+    a, _ = _moderate_case(seed=11 + q)
+    k, p = 8, 4
+    psi = synth.gaussian_psi(a.shape[1], k + p, seed=5)
+    ex = oracle_lib.corutv(a, k, p, q, psi)
+    ap = oracle_lib.corutv_dapprox(a, k, p, q, psi)
+    assert np.linalg.norm(ap["Q1"] - ex["Q1"]) < 1e-13 and np.linalg.norm(ap["Q2"] - ex["Q2"]) < 1e-13
+    assert _rel(ap["D"], ex["D"]) < 1e-12
+    assert list(ap["perm"]) == list(ex["perm"])
+    assert _rel(_approx(ap), _approx(ex)) < 1e-12
+    # the factors reproduce Q1 D_approx Q2^T (eqs. 8, 9)
+    assert _rel(_approx(ap), ap["Q1"] @ ap["D"] @ ap["Q2"].T) < 1e-13
+    # plausible mistakes move D_approx away from D
+    x = _last_operand(oracle_lib, a, k, p, q, psi)
+    c1 = oracle_lib.gemm_ax(a, x)
+    assert _rel(ap["Q1"].T @ c1 @ np.linalg.pinv((ap["Q2"].T @ x).T), ex["D"]) > 1e-6  # transposed operand
+    assert _rel(ap["Q1"].T @ c1, ex["D"]) > 1e-6                                       # pseudo-inverse dropped
+    if q > 0:
+        assert _rel(ap["Q1"].T @ c1 @ np.linalg.pinv(ap["Q2"].T @ psi), ex["D"]) > 1e-6  # Psi in place of X
+
+
+def _last_operand(oracle_lib, a, k, p, q, psi):
+    """X of the last round: Psi, or the re-orthonormalised C2 of the round before."""
+    x = psi
+    for it in range(q):
+        q1, _ = oracle_lib.qr(oracle_lib.gemm_ax(a, x))
+        x, _ = oracle_lib.qr(oracle_lib.gemm_aty(a, q1))
+    return x
+
+
 def test_factor_structure(oracle_lib):
     """U, V orthonormal; T upper with non-negative, non-increasing diagonal;
     sigma(T) = sigma(D); V = Q2 P; U = Q1 Qt."""
