@@ -240,7 +240,7 @@ def rel_error(A, out):
     return float(torch.linalg.norm(A.double() - approx) / torch.linalg.norm(A.double()))
 
 
-def time_factor(ctx, A, k, p, q, prec, steps, warmup, world, profile=False):
+def time_factor(ctx, A, k, p, q, prec, steps, warmup, world, profile=False, d_mode=0):
     """Device-timed steps of corutv_factor with outputs preallocated."""
     import torch
     from paper_1906_04572_gb300 import corutv
@@ -251,7 +251,7 @@ def time_factor(ctx, A, k, p, q, prec, steps, warmup, world, profile=False):
     T = torch.empty((ell, ell), device=A.device, dtype=A.dtype)
     perm = torch.empty(ell, device=A.device, dtype=torch.int32)
     for w in range(warmup):
-        corutv.corutv_factor(ctx.handle, A, k, p, q, prec, U, T, V, perm, seed=0, stream=w)
+        corutv.corutv_factor(ctx.handle, A, k, p, q, prec, U, T, V, perm, seed=0, stream=w, d_mode=d_mode)
     ctx.sync()
     if profile:
         corutv.corutv_profile_enable(ctx.handle, True)
@@ -260,7 +260,7 @@ def time_factor(ctx, A, k, p, q, prec, steps, warmup, world, profile=False):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for s in range(steps):
-        corutv.corutv_factor(ctx.handle, A, k, p, q, prec, U, T, V, perm, seed=0, stream=s)
+        corutv.corutv_factor(ctx.handle, A, k, p, q, prec, U, T, V, perm, seed=0, stream=s, d_mode=d_mode)
     e1.record()
     torch.cuda.synchronize()
     barrier(world)
@@ -569,6 +569,15 @@ def run_ours(args):
                                       8)
         extra["serving"]["capacity_vs_fp64"] = serving_capacity(local, args.serve_capacity, 8)
         extra["rpca"] = rpca_c4(ctx, device)
+        # the single-pass core (Sec. 3.1, d_mode 1): 2q+2 passes over A instead of 2q+3
+        sp = {}
+        for sp_prec in (("bf16", "tf32") if prec in ("bf16", "tf32") else (prec,)):
+            ms1, out1, _ = time_factor(ctx, A, k, p, q, sp_prec, max(3, args.steps // 2), 2, world, d_mode=1)
+            sp[sp_prec] = {"ms": ms1, "solves_per_s": 1e3 / ms1,
+                           "tflops_2q2_passes": (2 * q + 2) * 2.0 * m * n * ell / (ms1 / 1e3) / 1e12,
+                           "e_rel": rel_error(A, out1)}
+        sp["e_rel_exact_d"] = err
+        extra["single_pass"] = sp
         if args.c3:
             extra["c3"] = c3_line(ctx, device, ("bf16", "tf32", "f32"), 3)
 

@@ -67,7 +67,13 @@ typedef struct {
     int64_t p;            /* oversampling; ell = k + p */
     int64_t q;            /* power iterations (Algorithm 1 runs its loop q+1 times) */
     int32_t sketch_prec;  /* corutv_prec */
-    int32_t d_mode;       /* 0: exact D = Q1^T A Q2 (eq. 7); other values rejected */
+    int32_t d_mode;       /* 0: D = Q1^T A Q2 (eq. 7), a third pass over A (FP32-accurate on
+                             the mixed paths); 1: the single-pass core of Sec. 3.1,
+                             D_approx = Q1^T C1 (Q2^T X)^+ with X the matrix the last C1 was
+                             formed from, which with C2 = A^T Q1 = Q2 R2 equals R2^T: formed
+                             from the factors of the final thin QR, no third pass (on the
+                             mixed paths D then carries the sketch products' rounding);
+                             other values -> CORUTV_EINVAL */
     uint64_t seed;        /* Philox-4x32-10 key for Psi when psi == NULL */
     uint32_t stream;      /* Philox counter word 2 (independent draws per call) */
     uint32_t reserved;

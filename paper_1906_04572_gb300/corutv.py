@@ -152,11 +152,11 @@ def _check(ctx, status: int, allow=(OK,)):
     return status
 
 
-def _opts(k, p, q, prec, seed=0, stream=0, psi=None) -> Opts:
+def _opts(k, p, q, prec, seed=0, stream=0, psi=None, d_mode=0) -> Opts:
     o = Opts()
     o.k, o.p, o.q = int(k), int(p), int(q)
     o.sketch_prec = PREC_NAMES[prec] if isinstance(prec, str) else int(prec)
-    o.d_mode = 0
+    o.d_mode = int(d_mode)
     o.seed = int(seed)
     o.stream = int(stream)
     o.psi = _ptr(psi).value if psi is not None else None
@@ -199,11 +199,11 @@ def corutv_sync(ctx) -> int:
 
 
 def corutv_factor(ctx, A, k: int, p: int, q: int, prec="f64", U=None, T=None, V=None, perm=None,
-                  psi=None, seed: int = 0, stream: int = 0) -> int:
+                  psi=None, seed: int = 0, stream: int = 0, d_mode: int = 0) -> int:
     """Algorithm 1 into caller-provided U (m x ell), T (ell x ell), V (n x ell),
     perm (ell int32). Buffers must share A's device and dtype."""
     m, n = A.shape
-    o = _opts(k, p, q, prec, seed, stream, psi)
+    o = _opts(k, p, q, prec, seed, stream, psi, d_mode)
     _use_torch_stream(ctx, A)
     st = load().corutv_factor(ctx, _dtype_code(A), _ptr(A), m, n, _rowmajor_ld(A), ctypes.byref(o),
                               _ptr(U), _rowmajor_ld(U) if U is not None else 0, _ptr(T), _ptr(V),
@@ -227,13 +227,13 @@ def corutv_rpca(ctx, M, k: int, L, S, lam=0.0, mu0=0.0, mu_bar=0.0, rho=0.0, tol
     return {"status": st, "iters": it.value, "zeta": z.value, "rank": r.value}
 
 
-def make_request(A, k, p, q, prec, U, T, V=None, perm=None, psi=None, seed=0, stream=0) -> Request:
+def make_request(A, k, p, q, prec, U, T, V=None, perm=None, psi=None, seed=0, stream=0, d_mode=0) -> Request:
     m, n = A.shape
     rq = Request()
     rq.dtype = _dtype_code(A)
     rq.A = _ptr(A).value
     rq.m, rq.n, rq.lda = m, n, _rowmajor_ld(A)
-    rq.opts = _opts(k, p, q, prec, seed, stream, psi)
+    rq.opts = _opts(k, p, q, prec, seed, stream, psi, d_mode)
     rq.U = _ptr(U).value if U is not None else None
     rq.T = _ptr(T).value
     rq.V = _ptr(V).value if V is not None else None
@@ -341,7 +341,7 @@ class Context:
         except Exception:
             pass
 
-    def factor(self, A, k, p, q, prec="f64", psi=None, seed=0, stream=0, want_uv=True):
+    def factor(self, A, k, p, q, prec="f64", psi=None, seed=0, stream=0, want_uv=True, d_mode=0):
         import torch
         m, n = A.shape
         ell = k + p
@@ -350,7 +350,7 @@ class Context:
         V = torch.empty((n, ell), **kw) if want_uv else None
         T = torch.empty((ell, ell), **kw)
         perm = torch.empty(ell, dtype=torch.int32, device=A.device)
-        corutv_factor(self.handle, A, k, p, q, prec, U, T, V, perm, psi, seed, stream)
+        corutv_factor(self.handle, A, k, p, q, prec, U, T, V, perm, psi, seed, stream, d_mode)
         return {"U": U, "T": T, "V": V, "perm": perm}
 
     def rpca(self, M, k, **kw):

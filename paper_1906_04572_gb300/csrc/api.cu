@@ -169,6 +169,7 @@ struct FactorPlan {
     bool tensor;      // sketch products on tcgen05
     bool split;       // projection by exact bf16 splits on tcgen05 (BF16 / TF32 sketches, FP32 input)
     bool copy_a;      // TF32: A is not a TMA source as is (base or row stride not 16-byte aligned)
+    int dmode;        // 0: D = Q1^T A Q2 (eq. 7, a third pass); 1: the single-pass core (= R2^T)
     int64_t ldc32;    // row stride of that padded FP32 copy of A
     int64_t seg;      // columns per segment of the bf16 copy of A ([A_h | A_m | A_l] when split)
     int sp_ax, sp_aty, sp_w, gs_m, gs_n;
@@ -180,6 +181,7 @@ struct FactorBufs {
     void *x, *c1, *q1, *c2, *q2, *w, *tmp;   // panels of type FactorPlan::tp
     double *gpart, *g, *r, *d, *qt, *rt, *upanel, *zpanel;
     double* refl;     // reflectors of the QRCP of D (V, tau, signs)
+    double *racc, *racc2;  // products of CholeskyQR pass factors (single-pass core)
     int* defic;       // columns found numerically dependent in the extra CholeskyQR pass
     void *xc, *q1c, *q2c, *part;
     void* abf;        // bf16 copy of A for CORUTV_P_BF16, or its bf16 splits for the projection
@@ -193,7 +195,8 @@ struct FactorBufs {
 // a_aligned: the device copy of A that the factorisation reads starts on a
 // 16-byte boundary (only TF32 sketches read A itself through TMA).
 corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64_t lda, int64_t k,
-                        int64_t p, int64_t q, corutv_prec prec, int num_sms, bool a_aligned = true) {
+                        int64_t p, int64_t q, corutv_prec prec, int num_sms, bool a_aligned = true,
+                        int d_mode = 0) {
     pl.m = m; pl.n = n; pl.lda = lda; pl.k = k; pl.p = p; pl.q = q;
     pl.ell = k + p;
     pl.ta = ta;
@@ -210,7 +213,9 @@ corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64
     if (prec < CORUTV_P_F64 || prec > CORUTV_P_BF16) return fail(CORUTV_EINVAL, "unknown sketch precision %d", (int)prec);
     pl.tensor = (prec == CORUTV_P_TF32 || prec == CORUTV_P_BF16);
     if (prec == CORUTV_P_TF32 && ta != T_F32) return fail(CORUTV_EINVAL, "TF32 sketches need FP32 input");
-    pl.split = pl.tensor && ta == T_F32;
+    if (d_mode != 0 && d_mode != 1) return fail(CORUTV_EINVAL, "d_mode %d is not supported (0 exact D, 1 single-pass core)", d_mode);
+    pl.dmode = d_mode;
+    pl.split = pl.tensor && ta == T_F32 && d_mode == 0;  // the bf16 splits serve the projection only
     pl.seg = pl.split ? round_up(n, 64) : round_up(n, 8);
     pl.copy_a = prec == CORUTV_P_TF32 && (!a_aligned || lda % 4 != 0);
     pl.ldc32 = round_up(n, 4);
@@ -258,6 +263,8 @@ void carve_factor(C& cv, const FactorPlan& pl, FactorBufs& b) {
     b.qt = cv.template take<double>(ll);
     b.rt = cv.template take<double>(ll);
     b.refl = cv.template take<double>(pl.ellp * (pl.ellp + 2));
+    b.racc = pl.dmode == 1 ? cv.template take<double>(ll) : nullptr;
+    b.racc2 = pl.dmode == 1 ? cv.template take<double>(ll) : nullptr;
     b.defic = cv.template take<int>(pl.ellp);
     b.xc = cv.template take<char>(pn * es_c);
     b.q1c = cv.template take<char>(pm * es_c);
@@ -338,7 +345,8 @@ corutv_status gram(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, co
 // pl.torth; every Cholesky factorisation runs in FP64. Writes the panel q
 // (type pl.tp) and, if qc != nullptr, a copy of type tqc.
 corutv_status orth(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, const void* c,
-                   int64_t ld, int64_t len, void* q, void* qc, ElemType tqc, int passes = 2) {
+                   int64_t ld, int64_t len, void* q, void* qc, ElemType tqc, int passes = 2,
+                   double* rt_out = nullptr) {
     const int64_t ell = pl.ell;
     const ElemType tw = pl.torth, tp = pl.tp;
     ProfScope ps(ex.prof, CORUTV_STAGE_ORTH, ex.st);
@@ -348,6 +356,7 @@ corutv_status orth(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, co
     CKS(gram(ex, pl, b, c, ld, c, ld, len, b.g, ex.cancel, tw));
     const double u = tw == T_F64 ? 0x1p-53 : 0x1p-24;  // unit roundoff of the Gram arithmetic
     CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, b.skip, ex.cancel, ex.st, u));
+    if (rt_out) CK(launch_trimul(b.r, nullptr, b.racc, ell, false, nullptr, ex.cancel, ex.st));
     CK(launch_trsm_rows(c, tp, ld, len, ell, b.r, tw, p1, ld, p1c, tqc, ld, ex.cancel, ex.st));
     // extra pass, only after a shifted pass 1. Directions the shifted pass left
     // at rounding level (a numerically rank-deficient C) cannot be restored
@@ -356,11 +365,15 @@ corutv_status orth(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, co
     // one-pass intermediate basis).
     CKS(gram(ex, pl, b, p1, ld, p1, ld, len, b.g, b.skip, tw));
     CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, nullptr, b.skip, ex.st, u, b.defic, 10.0 * (double)ell * u));
+    // the extra pass's factor joins the product only if that pass ran
+    if (rt_out) CK(launch_trimul(b.r, b.racc, b.racc2, ell, false, b.skip, ex.cancel, ex.st));
     CK(launch_trsm_rows(p1, tp, ld, len, ell, b.r, tw, p1, ld, p1c, tqc, ld, b.skip, ex.st, b.defic));
-    if (passes == 1) return CORUTV_OK;
+    if (passes == 1) return rt_out ? fail(CORUTV_EINVAL, "the R factor needs two passes") : CORUTV_OK;
     // pass 2
     CKS(gram(ex, pl, b, b.tmp, ld, b.tmp, ld, len, b.g, ex.cancel, tw));
     CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, nullptr, ex.cancel, ex.st, u));
+    // C = Q (R_2 R_extra R_1): rt_out receives that product transposed
+    if (rt_out) CK(launch_trimul(b.r, b.racc2, rt_out, ell, true, nullptr, ex.cancel, ex.st));
     CK(launch_trsm_rows(b.tmp, tp, ld, len, ell, b.r, tw, q, ld, qc, tqc, ld, ex.cancel, ex.st));
     return CORUTV_OK;
 }
@@ -421,6 +434,15 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
         if (it < pl.q) CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.x, b.xc, pl.tcomp, inner));
     }
     // Q2 = qr(C2), with a copy in the projection's arithmetic
+    // single-pass core (Sec. 3.1): D_approx = Q1^T C1 (Q2^T X)^+, and with
+    // C2 = A^T Q1 = Q2 R2 that is R2^T (Q2^T X)(Q2^T X)^+ = R2^T: the transposed
+    // product of this thin QR's pass factors, with no third pass over A
+    if (pl.dmode == 1) {
+        CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.q2, nullptr, pl.tdproj, 2, b.d));
+        ProfScope ps(ex.prof, CORUTV_STAGE_QRCP, ex.st);
+        CK(launch_qrcp(b.d, ell, b.qt, b.rt, b.perm, b.refl, ex.cancel, ex.st, /*form_q=*/false));
+        return CORUTV_OK;
+    }
     CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.q2, pl.split ? nullptr : b.q2c, pl.tdproj, 2));
     // eq. 7: W = A Q2 (FP64, or FP32-accurate from the original A), D = Q1^T W
     if (pl.split) {
@@ -710,7 +732,6 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
     CKS(check_ctx(ctx));
     if (!A || !opts || !T) return fail(CORUTV_EINVAL, "A, opts and T must not be NULL");
     if (dtype != CORUTV_F64 && dtype != CORUTV_F32) return fail(CORUTV_EINVAL, "unknown dtype %d", (int)dtype);
-    if (opts->d_mode != 0) return fail(CORUTV_EINVAL, "d_mode %d is not supported (0 = exact D)", opts->d_mode);
     std::lock_guard<std::mutex> lk(ctx->call_mu);
     DeviceGuard guard(ctx->device);
     const ElemType ta = dtype == CORUTV_F64 ? T_F64 : T_F32;
@@ -720,7 +741,7 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
     FactorPlan pl;
     // host input is staged with row stride n into the (256-byte aligned) workspace
     CKS(make_plan(pl, ta, m, n, dev ? lda : n, opts->k, opts->p, opts->q, (corutv_prec)opts->sketch_prec,
-                  ctx->num_sms, !dev || reinterpret_cast<uintptr_t>(A) % 16 == 0));
+                  ctx->num_sms, !dev || reinterpret_cast<uintptr_t>(A) % 16 == 0, opts->d_mode));
     const int64_t ell = pl.ell;
     if (U && ldu < ell) return fail(CORUTV_EINVAL, "ldu < ell");
     if (V && ldv < ell) return fail(CORUTV_EINVAL, "ldv < ell");
@@ -1146,7 +1167,8 @@ size_t request_bytes(const corutv_request& r, bool host, int num_sms, FactorPlan
     FactorPlan pl;
     const ElemType ta = r.dtype == CORUTV_F64 ? T_F64 : T_F32;
     *st = make_plan(pl, ta, r.m, r.n, host ? r.n : r.lda, r.opts.k, r.opts.p, r.opts.q,
-                    (corutv_prec)r.opts.sketch_prec, num_sms, host || reinterpret_cast<uintptr_t>(r.A) % 16 == 0);
+                    (corutv_prec)r.opts.sketch_prec, num_sms, host || reinterpret_cast<uintptr_t>(r.A) % 16 == 0,
+                    r.opts.d_mode);
     if (*st != CORUTV_OK) return 0;
     size_t bytes = factor_bytes(pl);
     const int es = elem_size(ta);
@@ -1315,7 +1337,7 @@ corutv_status start_worker(corutv_ctx* ctx) {
 extern "C" corutv_status corutv_submit(corutv_ctx* ctx, const corutv_request* req, uint64_t* ticket) {
     CKS(check_ctx(ctx));
     if (!req || !ticket || !req->A || !req->T) return fail(CORUTV_EINVAL, "req, ticket, A and T must not be NULL");
-    if (req->opts.d_mode != 0) return fail(CORUTV_EINVAL, "d_mode must be 0");
+    if (req->opts.d_mode != 0 && req->opts.d_mode != 1) return fail(CORUTV_EINVAL, "d_mode must be 0 or 1");
     if (req->lda < req->n) return fail(CORUTV_EINVAL, "lda = %lld < n = %lld", (long long)req->lda, (long long)req->n);
     DeviceGuard guard(ctx->device);
     const bool host = !is_device_ptr(req->A);

@@ -172,6 +172,11 @@ cudaError_t launch_panel_to_rowmajor(const double* src, int64_t lds, int64_t row
 cudaError_t launch_cholesky(const double* g, int64_t ell, int64_t rows, double* r, int* flags,
                             int* skip_out, const int* cancel, cudaStream_t st,
                             double unit_roundoff = 0x1p-53, int* defic = nullptr, double tau_rel = 0.0);
+// out = Rn Ra for upper triangular ell x ell FP64 factors (row-major); Ra null:
+// out = Rn; *skip set: out = Ra (copy-through for a pass that did not run);
+// transpose: out receives the transpose. out must not alias Rn or Ra.
+cudaError_t launch_trimul(const double* rn, const double* ra, double* out, int64_t ell, bool transpose,
+                          const int* skip, const int* cancel, cudaStream_t st);
 // Q = C R^{-1} row by row (forward substitution with R^T), compute type tc;
 // c and q are panels of type tp; if qc != nullptr a copy of type tqc is
 // written too.

@@ -311,6 +311,31 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
     }
 }
 
+// Product of the upper triangular factors of successive CholeskyQR passes:
+// out = Rn Ra (the thin QR C = Q R of the passes together has R = R_last ...
+// R_first), or out = Rn when Ra is null, or out = Ra when *skip is set (a pass
+// that did not run); with `transpose` out receives the transpose. One block
+// per row a, thread c forms sum_{a <= t <= c} Rn[a][t] Ra[t][c] in FP64.
+__global__ void trimul_kernel(const double* rn, const double* ra, double* out, int ell, int transpose,
+                              const int* skip, const int* cancel) {
+    pdl_trigger();
+    pdl_wait();
+    if (cancel && *cancel) return;
+    const int a = blockIdx.x, c = threadIdx.x;
+    if (c >= ell) return;
+    double v;
+    if (skip && *skip) {
+        v = ra[a * ell + c];
+    } else if (!ra) {
+        v = c >= a ? rn[a * ell + c] : 0.0;
+    } else {
+        v = 0.0;
+        for (int t = a; t <= c; ++t) v = fma(rn[a * ell + t], ra[t * ell + c], v);
+    }
+    if (transpose) out[c * ell + a] = v;
+    else out[a * ell + c] = v;
+}
+
 // Entry (i, j) of a random completion column: N(0, 1) / sqrt(rows) from
 // SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) of the counter (i, j), two
 // 53-bit uniforms and the cosine branch of Box-Muller. Only columns the
@@ -856,6 +881,15 @@ __global__ void copy_small_kernel(const double* src, int n, TD* dst, const int* 
 }
 
 }  // namespace
+
+cudaError_t launch_trimul(const double* rn, const double* ra, double* out, int64_t ell, bool transpose,
+                          const int* skip, const int* cancel, cudaStream_t st) {
+    if (ell < 1 || ell > 128 || out == rn || out == ra) return cudaErrorInvalidValue;
+    count_launch();
+    cudaError_t e = launch_pdl(trimul_kernel, dim3((unsigned)ell), dim3(128), (size_t)0, st, rn, ra, out, (int)ell,
+                               transpose ? 1 : 0, skip, cancel);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
 
 cudaError_t launch_cholesky(const double* g, int64_t ell, int64_t rows, double* r, int* flags,
                                int* skip_out, const int* cancel, cudaStream_t st, double unit_roundoff,

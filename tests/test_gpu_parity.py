@@ -239,6 +239,54 @@ def test_factor_f32_error_budget(ctx):
     assert np.linalg.norm(got["U"].T @ got["U"] - np.eye(ell)) < 1e-5
 
 
+@pytest.mark.parametrize("m,n,k,p,q", [(500, 400, 10, 5, 0), (600, 450, 12, 6, 1), (450, 600, 8, 8, 2)])
+def test_factor_single_pass_core_f64_matches_oracle(ctx, m, n, k, p, q):
+    """d_mode 1 (Sec. 3.1's D_approx, formed on the device as R2^T from the
+    CholeskyQR factors of the final thin QR, no third pass over A) against the
+    oracle's literal D_approx = Q1^T C1 (Q2^T X)^+."""
+    a = _case_matrix(m, n, m + q)
+    psi = synth.gaussian_psi(n, k + p, seed=q + 20)
+    ref = oracle.corutv_dapprox(a, k, p, q, psi)
+    got = ctx.factor(dev(a), k, p, q, "f64", psi=dev(psi), d_mode=1)
+    assert ctx.sync() == 0
+    got = {x: host(got[x]) for x in ("U", "T", "V")}
+    na = np.linalg.norm(a)
+    assert np.linalg.norm(approx_of(got) - approx_of(ref)) / na <= 1e-12
+    assert np.linalg.norm(got["U"].T @ got["U"] - np.eye(k + p)) < 1e-12
+    assert np.all(np.tril(got["T"], -1) == 0)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_factor_single_pass_core_mixed_budget(ctx, prec):
+    """d_mode 1 on the mixed paths: D comes from the sketch products'
+    precision (no FP32 refinement pass), so the reconstruction error stays
+    within that precision's budget of the oracle's."""
+    m, n, k, p, q = 2000, 1500, 40, 10, 1
+    sigma = np.arange(1, min(m, n) + 1) ** -1.5
+    a = synth.spectrum_matrix(m, n, sigma, 0.0, 77)
+    a32 = a.astype(np.float32)
+    a64 = a32.astype(np.float64)
+    psi = synth.gaussian_psi(n, k + p, seed=21)
+    ref = oracle.corutv_dapprox(a64, k, p, q, psi)
+    out = ctx.factor(dev(a32, torch.float32), k, p, q, prec, psi=dev(psi), d_mode=1)
+    assert ctx.sync() == 0
+    u, t, v = (host(out[x]) for x in ("U", "T", "V"))
+    na = np.linalg.norm(a64)
+    e_gpu = np.linalg.norm(a64 - u @ t @ v.T) / na
+    e_or = np.linalg.norm(a64 - ref["U"] @ ref["T"] @ ref["V"].T) / na
+    unit = 2.0 ** -8 if prec == "bf16" else 2.0 ** -10
+    budget = 4 * unit * np.sqrt(k + p) * np.linalg.norm(a64, 2) / na
+    assert e_gpu <= e_or + budget, (e_gpu, e_or, budget)
+    assert np.linalg.norm(u.T @ u - np.eye(k + p)) < 1e-5
+
+
+def test_factor_rejects_unknown_d_mode(ctx):
+    a = dev(_case_matrix(60, 50, 3))
+    with pytest.raises(corutv.CorutvError) as ei:
+        ctx.factor(a, 5, 3, 0, "f64", d_mode=2)
+    assert ei.value.status == corutv.EINVAL
+
+
 @pytest.mark.parametrize("bad", ["ell_too_big", "mixed_memory", "null_t"])
 def test_factor_rejects_bad_arguments(ctx, bad):
     a = dev(_case_matrix(50, 40, 1))
