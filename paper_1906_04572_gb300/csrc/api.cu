@@ -1044,7 +1044,7 @@ extern "C" corutv_status corutv_rpca(corutv_ctx* ctx, corutv_dtype dtype, const 
     if (!M || !opts || !L || !S) return fail(CORUTV_EINVAL, "M, opts, L and S must not be NULL");
     if (dtype != CORUTV_F64 && dtype != CORUTV_F32) return fail(CORUTV_EINVAL, "unknown dtype");
     const int64_t k = opts->k;
-    if (k < 1 || 2 * k > 64) return fail(CORUTV_EINVAL, "rank guess k must be in [1, 32] (ell = 2k <= 64)");
+    if (k < 1 || 2 * k > 128) return fail(CORUTV_EINVAL, "rank guess k must be in [1, 64] (ell = 2k <= 128)");
     if (ldm < n) return fail(CORUTV_EINVAL, "ldm < n");
     const bool dev = is_device_ptr(M);
     if (is_device_ptr(L) != dev || is_device_ptr(S) != dev)

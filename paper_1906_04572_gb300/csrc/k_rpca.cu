@@ -20,7 +20,7 @@ namespace {
 
 constexpr int kUpdCols = 128;   // threads per block = columns per tile
 constexpr int kUpdRows = 16;    // rows per tile
-constexpr int kMaxEll = 64;
+constexpr int kMaxEll = 128;  // ell = 2k; kernels are instantiated for ell <= 64 and <= 128
 constexpr int kFinalThreads = 256;
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -63,15 +63,15 @@ __global__ void rpca_init_kernel(const TM* m, int64_t ldm, int64_t rows, int64_t
 }
 
 // r = #{i : Rt_ii > inv_mu}; Z[i][s] = sum_h Q2[i][perm[h]] Rt[s][h] for s < r.
-template <typename TQ>
+template <typename TQ, int kE>
 __global__ void rank_z_kernel(const double* rt, const TQ* q2, int64_t ldq2, const int* perm,
                               int64_t cols, int ell, double inv_mu, int* rank, double* z, int64_t ldz,
                               const int* cancel) {
     pdl_trigger();
     pdl_wait();
     if (cancel && *cancel) return;
-    __shared__ double Rs[kMaxEll * kMaxEll];
-    __shared__ int ps[kMaxEll];
+    extern __shared__ double Rs[];  // ell x ell
+    __shared__ int ps[kE];
     __shared__ int r_s;
     for (int e = threadIdx.x; e < ell * ell; e += blockDim.x) Rs[e] = rt[e];
     for (int e = threadIdx.x; e < ell; e += blockDim.x) ps[e] = perm[e];
@@ -86,7 +86,7 @@ __global__ void rank_z_kernel(const double* rt, const TQ* q2, int64_t ldq2, cons
     const int r = r_s;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cols) return;
-    double v[kMaxEll];
+    double v[kE];
 #pragma unroll 4
     for (int h = 0; h < ell; ++h) v[h] = (double)q2[(int64_t)ps[h] * ldq2 + i];
     for (int s = 0; s < ell; ++s) {
@@ -101,7 +101,7 @@ __global__ void rank_z_kernel(const double* rt, const TQ* q2, int64_t ldq2, cons
 // arithmetic of the state (TS): FP32 for FP32 data (on this GPU the FP64
 // pipe runs at a sixtieth of the FP32 rate), FP64 for FP64 data. The squared
 // residual is summed per thread in TS and across the block in FP64.
-template <typename TM, typename TS>
+template <typename TM, typename TS, int kE>
 __global__ void __launch_bounds__(kUpdCols)
 rpca_update_kernel(const TM* m, int64_t ldm, int64_t rows, int64_t cols, TS* s, TS* y, TS* b,
                    const double* u, int64_t ldu, const double* z, int64_t ldz, int ell, const int* rank,
@@ -110,16 +110,16 @@ rpca_update_kernel(const TM* m, int64_t ldm, int64_t rows, int64_t cols, TS* s, 
     pdl_wait();
     if (cancel && *cancel) return;
     __shared__ double red[32];
-    __shared__ TS Us[kUpdRows][kMaxEll];
+    __shared__ TS Us[kUpdRows][kE];
     const int r = *rank;
     const int64_t i0 = (int64_t)blockIdx.y * kUpdRows;
     const int64_t c = (int64_t)blockIdx.x * kUpdCols + threadIdx.x;
-    for (int e = threadIdx.x; e < kUpdRows * kMaxEll; e += blockDim.x) {
-        const int ii = e / kMaxEll, sidx = e % kMaxEll;
+    for (int e = threadIdx.x; e < kUpdRows * kE; e += blockDim.x) {
+        const int ii = e / kE, sidx = e % kE;
         const int64_t i = i0 + ii;
         Us[ii][sidx] = (i < rows && sidx < r) ? (TS)u[(int64_t)sidx * ldu + i] : (TS)0;
     }
-    TS zc[kMaxEll];
+    TS zc[kE];
     if (c < cols) {
 #pragma unroll 4
         for (int sidx = 0; sidx < ell; ++sidx) zc[sidx] = (sidx < r) ? (TS)z[(int64_t)sidx * ldz + c] : (TS)0;
@@ -207,22 +207,22 @@ __global__ void finish_iter_kernel(const double* res_part, int nparts, const dou
     }
 }
 
-template <typename TL>
+template <typename TL, int kE>
 __global__ void __launch_bounds__(kUpdCols)
 reconstruct_kernel(const double* u, int64_t ldu, const double* z, int64_t ldz, const int* rank, int ell,
                    int64_t rows, int64_t cols, TL* lout, int64_t ldl) {
     pdl_trigger();
     pdl_wait();
-    __shared__ TL Us[kUpdRows][kMaxEll];
+    __shared__ TL Us[kUpdRows][kE];
     const int r = *rank;
     const int64_t i0 = (int64_t)blockIdx.y * kUpdRows;
     const int64_t c = (int64_t)blockIdx.x * kUpdCols + threadIdx.x;
-    for (int e = threadIdx.x; e < kUpdRows * kMaxEll; e += blockDim.x) {
-        const int ii = e / kMaxEll, sidx = e % kMaxEll;
+    for (int e = threadIdx.x; e < kUpdRows * kE; e += blockDim.x) {
+        const int ii = e / kE, sidx = e % kE;
         const int64_t i = i0 + ii;
         Us[ii][sidx] = (i < rows && sidx < r) ? (TL)u[(int64_t)sidx * ldu + i] : (TL)0;
     }
-    TL zc[kMaxEll];
+    TL zc[kE];
     if (c < cols)
         for (int sidx = 0; sidx < ell; ++sidx) zc[sidx] = (sidx < r) ? (TL)z[(int64_t)sidx * ldz + c] : (TL)0;
     __syncthreads();
@@ -340,25 +340,36 @@ cudaError_t launch_rpca_init(const void* m, ElemType tm, int64_t ldm, int64_t ro
     return cudaGetLastError();
 }
 
+template <typename TQ, int kE>
+cudaError_t rank_z_launch(const double* rt, const void* vq2, int64_t ldv, const int* perm, int64_t cols, int64_t ell,
+                          double inv_mu, int* rank, double* z, int64_t ldz, const int* cancel, cudaStream_t st) {
+    const size_t smem = sizeof(double) * (size_t)ell * ell;
+    cudaError_t e = cudaFuncSetAttribute(rank_z_kernel<TQ, kE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    e = launch_pdl(rank_z_kernel<TQ, kE>, dim3((unsigned)((cols + 127) / 128)), dim3(128), smem, st, rt,
+                   static_cast<const TQ*>(vq2), ldv, perm, cols, (int)ell, inv_mu, rank, z, ldz, cancel);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 cudaError_t launch_rpca_rank_z(const double* rt, const void* vq2, ElemType tq2, int64_t ldv, const int* perm,
                                int64_t cols, int64_t ell, double inv_mu, int* rank, double* z,
                                int64_t ldz, const int* cancel, cudaStream_t st) {
     if (ell > kMaxEll) return cudaErrorInvalidValue;
-    const unsigned blocks = (unsigned)((cols + 127) / 128);
-    count_launch();
     if (tq2 == T_F64)
-        {
-            cudaError_t pe_ = launch_pdl(rank_z_kernel<double>, dim3(blocks), dim3(128), (size_t)(0), st, rt, static_cast<const double*>(vq2), ldv, perm, cols, (int)ell,
-                                                      inv_mu, rank, z, ldz, cancel);
-            if (pe_ != cudaSuccess) return pe_;
-        }
-    else
-        {
-            cudaError_t pe_ = launch_pdl(rank_z_kernel<float>, dim3(blocks), dim3(128), (size_t)(0), st, rt, static_cast<const float*>(vq2), ldv, perm, cols, (int)ell,
-                                                     inv_mu, rank, z, ldz, cancel);
-            if (pe_ != cudaSuccess) return pe_;
-        }
-    return cudaGetLastError();
+        return ell <= 64 ? rank_z_launch<double, 64>(rt, vq2, ldv, perm, cols, ell, inv_mu, rank, z, ldz, cancel, st)
+                         : rank_z_launch<double, 128>(rt, vq2, ldv, perm, cols, ell, inv_mu, rank, z, ldz, cancel, st);
+    return ell <= 64 ? rank_z_launch<float, 64>(rt, vq2, ldv, perm, cols, ell, inv_mu, rank, z, ldz, cancel, st)
+                     : rank_z_launch<float, 128>(rt, vq2, ldv, perm, cols, ell, inv_mu, rank, z, ldz, cancel, st);
+}
+
+template <typename TM, typename TS, int kE>
+cudaError_t update_launch(const RpcaIterArgs& a, const TM* m, TS* s, TS* y, TS* b, dim3 grid, cudaStream_t st) {
+    count_launch();
+    cudaError_t e = launch_pdl(rpca_update_kernel<TM, TS, kE>, grid, dim3(kUpdCols), (size_t)0, st, m, a.ldm, a.rows,
+                               a.cols, s, y, b, a.u, a.ldu, a.z, a.ldz, (int)a.ell, a.rank, a.mu, a.mu_next,
+                               a.lambda, a.res_part, a.cancel);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_rpca_update(const RpcaIterArgs& a, int* nparts, cudaStream_t st) {
@@ -366,23 +377,13 @@ cudaError_t launch_rpca_update(const RpcaIterArgs& a, int* nparts, cudaStream_t 
     dim3 grid((unsigned)((a.cols + kUpdCols - 1) / kUpdCols), (unsigned)((a.rows + kUpdRows - 1) / kUpdRows));
     *nparts = (int)(grid.x * grid.y);
     if (a.tm == T_F32) {
-        count_launch();
-        {
-            cudaError_t pe_ = launch_pdl(rpca_update_kernel<float, float>, dim3(grid), dim3(kUpdCols), (size_t)(0), st, 
-            static_cast<const float*>(a.m), a.ldm, a.rows, a.cols, a.s, a.y, a.b, a.u, a.ldu, a.z, a.ldz,
-            (int)a.ell, a.rank, a.mu, a.mu_next, a.lambda, a.res_part, a.cancel);
-            if (pe_ != cudaSuccess) return pe_;
-        }
-    } else {
-        count_launch();
-        {
-            cudaError_t pe_ = launch_pdl(rpca_update_kernel<double, double>, dim3(grid), dim3(kUpdCols), (size_t)(0), st, 
-            static_cast<const double*>(a.m), a.ldm, a.rows, a.cols, a.s64, a.y64, a.b64, a.u, a.ldu, a.z,
-            a.ldz, (int)a.ell, a.rank, a.mu, a.mu_next, a.lambda, a.res_part, a.cancel);
-            if (pe_ != cudaSuccess) return pe_;
-        }
+        const float* m = static_cast<const float*>(a.m);
+        return a.ell <= 64 ? update_launch<float, float, 64>(a, m, a.s, a.y, a.b, grid, st)
+                           : update_launch<float, float, 128>(a, m, a.s, a.y, a.b, grid, st);
     }
-    return cudaGetLastError();
+    const double* m = static_cast<const double*>(a.m);
+    return a.ell <= 64 ? update_launch<double, double, 64>(a, m, a.s64, a.y64, a.b64, grid, st)
+                       : update_launch<double, double, 128>(a, m, a.s64, a.y64, a.b64, grid, st);
 }
 
 cudaError_t launch_rpca_finish_iter(const double* res_part, int nparts, const double* fro_part,
@@ -397,27 +398,25 @@ cudaError_t launch_rpca_finish_iter(const double* res_part, int nparts, const do
     return cudaGetLastError();
 }
 
+template <typename TL, int kE>
+cudaError_t reconstruct_launch(const double* u, int64_t ldu, const double* z, int64_t ldz, const int* rank,
+                               int64_t ell, int64_t rows, int64_t cols, void* lout, int64_t ldl, cudaStream_t st) {
+    dim3 grid((unsigned)((cols + kUpdCols - 1) / kUpdCols), (unsigned)((rows + kUpdRows - 1) / kUpdRows));
+    count_launch();
+    cudaError_t e = launch_pdl(reconstruct_kernel<TL, kE>, grid, dim3(kUpdCols), (size_t)0, st, u, ldu, z, ldz, rank,
+                               (int)ell, rows, cols, static_cast<TL*>(lout), ldl);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 cudaError_t launch_rpca_reconstruct(const double* u, int64_t ldu, const double* z, int64_t ldz,
                                     const int* rank, int64_t ell, int64_t rows, int64_t cols,
                                     void* lout, ElemType tl, int64_t ldl, cudaStream_t st) {
     if (ell > kMaxEll) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)((cols + kUpdCols - 1) / kUpdCols), (unsigned)((rows + kUpdRows - 1) / kUpdRows));
-    if (tl == T_F32) {
-        count_launch();
-        {
-            cudaError_t pe_ = launch_pdl(reconstruct_kernel<float>, dim3(grid), dim3(kUpdCols), (size_t)(0), st, u, ldu, z, ldz, rank, (int)ell, rows, cols,
-                                                             static_cast<float*>(lout), ldl);
-            if (pe_ != cudaSuccess) return pe_;
-        }
-    } else {
-        count_launch();
-        {
-            cudaError_t pe_ = launch_pdl(reconstruct_kernel<double>, dim3(grid), dim3(kUpdCols), (size_t)(0), st, u, ldu, z, ldz, rank, (int)ell, rows, cols,
-                                                              static_cast<double*>(lout), ldl);
-            if (pe_ != cudaSuccess) return pe_;
-        }
-    }
-    return cudaGetLastError();
+    if (tl == T_F32)
+        return ell <= 64 ? reconstruct_launch<float, 64>(u, ldu, z, ldz, rank, ell, rows, cols, lout, ldl, st)
+                         : reconstruct_launch<float, 128>(u, ldu, z, ldz, rank, ell, rows, cols, lout, ldl, st);
+    return ell <= 64 ? reconstruct_launch<double, 64>(u, ldu, z, ldz, rank, ell, rows, cols, lout, ldl, st)
+                     : reconstruct_launch<double, 128>(u, ldu, z, ldz, rank, ell, rows, cols, lout, ldl, st);
 }
 
 }  // namespace corutv
