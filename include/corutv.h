@@ -121,8 +121,9 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
  * Lagrange multipliers with the CoR-UTV thresholding operator
  * C_delta(B) = U(:,1:r) T(1:r,:) V^T, r = #{i : T_ii > delta}, and the
  * shrinkage S_delta(x) = sgn(x) max(|x| - delta, 0) (Sec. 4). opts->k is the
- * rank guess; the low-rank step uses ell = 2k and q = 1 (Sec. 5.3) and a
- * fresh Psi per iteration (Philox stream opts->stream + j + 1).
+ * rank guess, 1 <= k <= 64 (CORUTV_EINVAL otherwise); the low-rank step uses
+ * ell = 2k and q = 1 (Sec. 5.3) and a fresh Psi per iteration (Philox stream
+ * opts->stream + j + 1).
  * Y_0 = S_0 = 0; mu_{j+1} = min(rho mu_j, mu_bar); stop after the first
  * iteration with zeta = ||M - L - S||_F / ||M||_F < tol or after max_iter.
  * Parameters <= 0 select: lambda = 1/sqrt(max(m, n)), mu0 = 1.25/||M||_2
