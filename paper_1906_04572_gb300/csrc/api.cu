@@ -317,15 +317,20 @@ corutv_status sketch_simt(const Exec& ex, const FactorPlan& pl, const FactorBufs
 
 // G = X^T Y (ell x ell, written as FP64) for two panels of type pl.tp and
 // `len` rows; products and split sums in arithmetic tg.
+// px / py: pieces of a tensor-core product still to be added to X / Y (the
+// Gram is their first reader; writeback completes the panel for later ones).
 corutv_status gram(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, const void* x,
                    int64_t ldx, const void* y, int64_t ldy, int64_t len, double* out,
-                   const int* cancel, ElemType tg) {
+                   const int* cancel, ElemType tg, const TcPieces* px = nullptr, const TcPieces* py = nullptr,
+                   bool writeback = false) {
     if (tg == T_F32 && pl.tp == T_F32 && b.gcnt) {
         // one launch, split sums reduced in the kernel
         CK(launch_gram_f32(static_cast<const float*>(x), ldx, static_cast<const float*>(y), ldy, len, (int)pl.ell,
-                           out, reinterpret_cast<float*>(b.gpart), b.gcnt, ex.num_sms, cancel, ex.st));
+                           out, reinterpret_cast<float*>(b.gpart), b.gcnt, ex.num_sms, cancel, ex.st,
+                           px ? *px : TcPieces(), py ? *py : TcPieces(), writeback));
         return CORUTV_OK;
     }
+    if ((px && px->part) || (py && py->part)) return fail(CORUTV_ECUDA, "pending product pieces need the FP32 Gram");
     const int gs = gemm_simt_splits(pl.ell, len, ex.num_sms);
     const int64_t ll = pl.ell * pl.ell;
     GemmArgs g{A_PANEL_T, B_PANEL, O_ROWMAJ, pl.tp, tg, x, ldx, y, ldy, b.gpart, pl.ell, ll,
@@ -346,14 +351,14 @@ corutv_status gram(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, co
 // (type pl.tp) and, if qc != nullptr, a copy of type tqc.
 corutv_status orth(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, const void* c,
                    int64_t ld, int64_t len, void* q, void* qc, ElemType tqc, int passes = 2,
-                   double* rt_out = nullptr) {
+                   double* rt_out = nullptr, const TcPieces* pieces = nullptr) {
     const int64_t ell = pl.ell;
     const ElemType tw = pl.torth, tp = pl.tp;
     ProfScope ps(ex.prof, CORUTV_STAGE_ORTH, ex.st);
     void* p1 = passes == 1 ? q : b.tmp;
     void* p1c = passes == 1 ? qc : nullptr;
-    // pass 1
-    CKS(gram(ex, pl, b, c, ld, c, ld, len, b.g, ex.cancel, tw));
+    // pass 1 (the first reader of c: it adds any pieces the product left and completes c)
+    CKS(gram(ex, pl, b, c, ld, c, ld, len, b.g, ex.cancel, tw, pieces, pieces, true));
     const double u = tw == T_F64 ? 0x1p-53 : 0x1p-24;  // unit roundoff of the Gram arithmetic
     CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, b.skip, ex.cancel, ex.st, u));
     if (rt_out) CK(launch_trimul(b.r, nullptr, b.racc, ell, false, nullptr, ex.cancel, ex.st));
@@ -405,6 +410,10 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
         CK(launch_panel_convert(b.x, pl.tp, pl.ldn, n, ell, b.xc, pl.tcomp, pl.ldn, ex.cancel, ex.st));
     }
     const int64_t ldabf = (pl.split ? 3 : 1) * pl.seg;  // the sketches read the A_h segment
+    // split tiles of a tensor-core product stay pieces until the Gram that
+    // first reads the panel adds them (no fix-up tail in the product)
+    TcPieces pieces;
+    TcPieces* defer = (pl.tp == T_F32 && pl.torth == T_F32 && pl.tdproj == T_F32) ? &pieces : nullptr;
     for (int64_t it = 0; it <= pl.q; ++it) {
         // eq. 4: C1 = A X
         if (pl.tensor) {
@@ -413,37 +422,42 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
             const int64_t lda_op = bf ? ldabf : (pl.copy_a ? pl.ldc32 : pl.lda);
             ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
             CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, /*trans=*/0, b.xc, pl.ldn, ell, pl.ellp, b.part,
-                                b.tcnt, b.c1, pl.tp, pl.ldm, ex.num_sms, ex.flags, ex.cancel, ex.st));
+                                b.tcnt, b.c1, pl.tp, pl.ldm, ex.num_sms, ex.flags, ex.cancel, ex.st, defer));
         } else {
             CKS(sketch_simt(ex, pl, b, A_ROWS, a, pl.ta, b.xc, pl.tcomp, b.c1, pl.ldm));
         }
         const int inner = (pl.prec == CORUTV_P_F64) ? 2 : 1;  // passes for the intermediate bases
-        CKS(orth(ex, pl, b, b.c1, pl.ldm, m, b.q1, b.q1c, pl.tcomp, it < pl.q ? inner : 2));
+        CKS(orth(ex, pl, b, b.c1, pl.ldm, m, b.q1, b.q1c, pl.tcomp, it < pl.q ? inner : 2, nullptr, &pieces));
+        pieces = TcPieces();
         // eq. 5 (with C1 -> Q1): C2 = A^T Q1
         if (pl.tensor) {
             ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
             if (pl.prec == CORUTV_P_BF16)
                 CK(launch_sketch_tc(b.abf, pl.tcomp, m, n, ldabf, /*trans=*/1, b.q1c, pl.ldm, ell, pl.ellp, b.part,
-                                    b.tcnt, b.c2, pl.tp, pl.ldn, ex.num_sms, ex.flags, ex.cancel, ex.st));
+                                    b.tcnt, b.c2, pl.tp, pl.ldn, ex.num_sms, ex.flags, ex.cancel, ex.st, defer));
             else  // TF32: (A^T) Y with the transposed copy, both operands K-major
                 CK(launch_sketch_tc(b.at, pl.tcomp, n, m, pl.ldm, /*trans=*/0, b.q1c, pl.ldm, ell, pl.ellp, b.part,
-                                    b.tcnt, b.c2, pl.tp, pl.ldn, ex.num_sms, ex.flags, ex.cancel, ex.st));
+                                    b.tcnt, b.c2, pl.tp, pl.ldn, ex.num_sms, ex.flags, ex.cancel, ex.st, defer));
         } else {
             CKS(sketch_simt(ex, pl, b, A_COLS, a, pl.ta, b.q1c, pl.tcomp, b.c2, pl.ldn));
         }
-        if (it < pl.q) CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.x, b.xc, pl.tcomp, inner));
+        if (it < pl.q) {
+            CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.x, b.xc, pl.tcomp, inner, nullptr, &pieces));
+            pieces = TcPieces();
+        }
     }
     // Q2 = qr(C2), with a copy in the projection's arithmetic
     // single-pass core (Sec. 3.1): D_approx = Q1^T C1 (Q2^T X)^+, and with
     // C2 = A^T Q1 = Q2 R2 that is R2^T (Q2^T X)(Q2^T X)^+ = R2^T: the transposed
     // product of this thin QR's pass factors, with no third pass over A
     if (pl.dmode == 1) {
-        CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.q2, nullptr, pl.tdproj, 2, b.d));
+        CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.q2, nullptr, pl.tdproj, 2, b.d, &pieces));
         ProfScope ps(ex.prof, CORUTV_STAGE_QRCP, ex.st);
         CK(launch_qrcp(b.d, ell, b.qt, b.rt, b.perm, b.refl, ex.cancel, ex.st, /*form_q=*/false));
         return CORUTV_OK;
     }
-    CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.q2, pl.split ? nullptr : b.q2c, pl.tdproj, 2));
+    CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.q2, pl.split ? nullptr : b.q2c, pl.tdproj, 2, nullptr, &pieces));
+    pieces = TcPieces();
     // eq. 7: W = A Q2 (FP64, or FP32-accurate from the original A), D = Q1^T W
     if (pl.split) {
         CK(launch_split_panel(static_cast<const float*>(b.q2), pl.ldn, n, ell, pl.ellp, b.q2c, pl.ldn, ex.cancel,
@@ -451,7 +465,7 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
         ProfScope ps(ex.prof, CORUTV_STAGE_PROJECT, ex.st);
         CK(launch_project_split_tc(b.abf, m, n, pl.seg, b.q2c, pl.ldn, ell, pl.ellp, b.part, b.tcnt, b.w, pl.tp,
                                    pl.ldm,
-                                   ex.num_sms, ex.flags, ex.cancel, ex.st));
+                                   ex.num_sms, ex.flags, ex.cancel, ex.st, defer));
     } else {
         GemmArgs g{A_ROWS, B_PANEL, O_PANEL, pl.ta, pl.tdproj, a, pl.lda, b.q2c, pl.ldn, b.part, pl.ldm,
                    pl.ellp * pl.ldm, m, n, ell, pl.sp_w, ex.cancel};
@@ -462,7 +476,7 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
         CK(launch_reduce_splits(b.part, pl.tdproj, pl.sp_w, pl.ellp * pl.ldm, b.w, pl.tp, pl.ldm, m, ell, pl.ldm,
                                 ex.cancel, ex.st));
     }
-    CKS(gram(ex, pl, b, b.q1, pl.ldm, b.w, pl.ldm, m, b.d, ex.cancel, pl.tdproj));
+    CKS(gram(ex, pl, b, b.q1, pl.ldm, b.w, pl.ldm, m, b.d, ex.cancel, pl.tdproj, nullptr, &pieces));
     // eq. 8: D P = Qt Rt
     {
         ProfScope ps(ex.prof, CORUTV_STAGE_QRCP, ex.st);

@@ -102,6 +102,24 @@ __device__ __forceinline__ double f2d_exact(float f) {
 __device__ __forceinline__ double f2d_exact(double d) { return d; }
 #endif
 
+// Stream-K tile ownership of the tensor-core products: unit u (tile t = u / kc,
+// K chunk u % kc) belongs to CTA c with c units / grid <= u < (c + 1) units / grid.
+__host__ __device__ __forceinline__ long long unit_owner(long long u, long long units, long long grid) {
+    return ((u + 1) * grid + units - 1) / units - 1;
+}
+
+// Output of a tensor-core product whose split tiles were left as pieces for
+// the consumer (the first kernel to read the panel adds them): tile t of 128
+// rows covered by np(t) > 1 CTAs has its FP32 partials at part[((t * maxp +
+// pc) * ellp + j) * 128 + (row % 128)], pc = 0 .. np-1, added in that order;
+// tiles covered by one CTA are in the panel itself. part == nullptr: the
+// panel is complete.
+struct TcPieces {
+    const float* part = nullptr;
+    long long units = 0, kc = 1;
+    int grid = 1, maxp = 1, ellp = 0;
+};
+
 // Every kernel asks for the largest shared-memory carve-out once, so that the
 // switches between the tensor-core products (about 200 KB of shared memory
 // per block) and the small kernels around them do not reconfigure the SMs'
@@ -192,8 +210,12 @@ cudaError_t launch_trsm_rows(const void* c, ElemType tp, int64_t ldc, int64_t ro
 // first call (every call leaves them zero).
 int64_t gram_f32_work_floats(int64_t len, int ell, int num_sms);
 int64_t gram_f32_counters(int64_t len, int ell, int num_sms);
+// px / py: pieces of X / Y still to be added (TcPieces); with writeback the
+// added rows are stored into that panel as well, completing it for later
+// kernels.
 cudaError_t launch_gram_f32(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_t len, int ell,
-                            double* out, float* work, int* cnt, int num_sms, const int* cancel, cudaStream_t st);
+                            double* out, float* work, int* cnt, int num_sms, const int* cancel, cudaStream_t st,
+                            const TcPieces& px = TcPieces(), const TcPieces& py = TcPieces(), bool writeback = false);
 // Column-pivoted QR of the small ell x ell FP64 matrix d (eq. 8): the
 // factorisation in one block, then Qt formed from its reflectors by several
 // blocks. work: ell * (ell + 2) doubles of device scratch.

@@ -46,9 +46,68 @@ GramPlan gram_plan(int64_t len, int ell, int num_sms) {
     return p;
 }
 
+constexpr int kPer = kGChunk * kGT / kGThreads;  // elements per thread and operand per chunk (8)
+
+// Row `row`, columns col0 + 8 k (k < kPer), of an FP32 panel whose split
+// product tiles may still be pieces (zero for rows outside the chunk and
+// columns >= ell). A row of a tile covered by np > 1 CTAs is the sum of its
+// np FP32 partials in piece order, the order the product's own fix-up adds
+// them in, so the value is the one the product would have stored; with
+// writeback it is stored into the panel. The loads of four pieces of all
+// eight columns are issued before any add (one L2 round trip per four
+// pieces).
+__device__ __forceinline__ void load_row(const float* panel, int64_t ld, const TcPieces& pc, bool writeback,
+                                         int64_t row, bool row_ok, int col0, int ell, float (&v)[kPer]) {
+    int np = 1;
+    const float* src = nullptr;
+    if (pc.part && row_ok) {
+        const long long t = row >> 7;
+        const long long first = unit_owner(t * pc.kc, pc.units, pc.grid);
+        np = (int)(unit_owner((t + 1) * pc.kc - 1, pc.units, pc.grid) - first) + 1;
+        src = pc.part + (t * pc.maxp * pc.ellp) * 128 + (row & 127);
+    }
+    if (np == 1) {
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int col = col0 + 8 * k;
+            v[k] = (row_ok && col < ell) ? panel[(int64_t)col * ld + row] : 0.f;
+        }
+        return;
+    }
+    const long long ps = (long long)pc.ellp * 128;  // piece stride
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) v[k] = 0.f;
+    for (int q0 = 0; q0 < np; q0 += 4) {
+        float w[4][kPer];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const float* sp = src + (long long)min(q0 + g, np - 1) * ps;  // clamped: loads stay unconditional
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) {
+                const int col = col0 + 8 * k;
+                w[g][k] = col < ell ? __ldcg(sp + (long long)col * 128) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+            if (q0 + g < np) {
+#pragma unroll
+                for (int k = 0; k < kPer; ++k) v[k] += w[g][k];
+            }
+    }
+    if (writeback) {
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int col = col0 + 8 * k;
+            if (col < ell) const_cast<float*>(panel)[(int64_t)col * ld + row] = v[k];
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kGThreads)
 gram_f32_kernel(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_t len, int ell, double* out,
-                float* cpart, int* cnt, GramPlan pl, const int* cancel) {
+                float* cpart, int* cnt, GramPlan pl, const int* cancel, TcPieces pieces_x, TcPieces pieces_y,
+                int writeback) {
     pdl_wait();
     namespace cg = cooperative_groups;
     if (cancel && *cancel) return;  // uniform over the grid: no cluster barrier is left waiting
@@ -64,26 +123,26 @@ gram_f32_kernel(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_
     const int ti = tile / pl.ntile, tj = tile % pl.ntile;
     const int64_t r_beg = (int64_t)s * len / S, r_end = (int64_t)(s + 1) * len / S;
     const bool same = x == y && ti == tj;
+    const TcPieces& pcx = pieces_x;
+    const TcPieces& pcy = pieces_y;
+    const bool wb = writeback != 0;
+    const bool wb_y = wb && x != y;  // with X = Y the X loads complete the panel
     float acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
-    // staging: each thread moves 8 elements per operand per chunk; the next
-    // chunk's loads are all issued (into registers) before the current chunk
-    // is multiplied, so their latency overlaps the arithmetic
-    constexpr int kPer = kGChunk * kGT / kGThreads;  // 8
+    // staging: each thread moves 8 elements per operand per chunk (one row,
+    // eight columns); the next chunk's loads are all issued (into registers)
+    // before the current chunk is multiplied, so their latency overlaps the
+    // arithmetic
+    static_assert(kGThreads % kGChunk == 0, "a thread keeps one row of each chunk");
     float px[kPer], py[kPer];
     auto load_chunk = [&](int64_t r0) {
         const int nr = (int)(r_end - r0 < kGChunk ? r_end - r0 : kGChunk);
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int idx = tid + k * kGThreads;
-            const int c = idx / kGChunk, r = idx % kGChunk;  // consecutive threads: consecutive rows
-            const int cx = ti * kGT + c, cy = tj * kGT + c;
-            px[k] = (r < nr && cx < ell) ? x[(int64_t)cx * ldx + r0 + r] : 0.f;
-            if (!same) py[k] = (r < nr && cy < ell) ? y[(int64_t)cy * ldy + r0 + r] : 0.f;
-        }
+        const int r = tid % kGChunk, c = tid / kGChunk;  // consecutive threads: consecutive rows
+        load_row(x, ldx, pcx, wb, r0 + r, r < nr, ti * kGT + c, ell, px);
+        if (!same) load_row(y, ldy, pcy, wb_y, r0 + r, r < nr, tj * kGT + c, ell, py);
     };
     if (r_beg < r_end) load_chunk(r_beg);
     for (int64_t r0 = r_beg; r0 < r_end; r0 += kGChunk) {
@@ -173,7 +232,8 @@ int64_t gram_f32_counters(int64_t len, int ell, int num_sms) {
 }
 
 cudaError_t launch_gram_f32(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_t len, int ell,
-                            double* out, float* work, int* cnt, int num_sms, const int* cancel, cudaStream_t st) {
+                            double* out, float* work, int* cnt, int num_sms, const int* cancel, cudaStream_t st,
+                            const TcPieces& px, const TcPieces& py, bool writeback) {
     if (ell < 1 || ell > 128 || len < 1 || !work || !cnt) return cudaErrorInvalidValue;
     const GramPlan p = gram_plan(len, ell, num_sms);
     cudaLaunchConfig_t cfg = {};
@@ -192,7 +252,8 @@ cudaError_t launch_gram_f32(const float* x, int64_t ldx, const float* y, int64_t
     cfg.numAttrs = 2;
     count_launch();
     prefer_max_shared(reinterpret_cast<const void*>(gram_f32_kernel));
-    return cudaLaunchKernelEx(&cfg, gram_f32_kernel, x, ldx, y, ldy, len, ell, out, work, cnt, p, cancel);
+    return cudaLaunchKernelEx(&cfg, gram_f32_kernel, x, ldx, y, ldy, len, ell, out, work, cnt, p, cancel, px, py,
+                              writeback ? 1 : 0);
 }
 
 }  // namespace corutv

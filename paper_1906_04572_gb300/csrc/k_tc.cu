@@ -82,6 +82,7 @@ struct TcParams {
     long long mtot;       // valid output rows
     int* flags;
     const int* cancel;
+    int defer;            // split tiles: leave the pieces for the consumer (no count, no reduction)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -210,9 +211,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 
 // Owner CTA of stream-K unit u when `units` units are split over `grid` CTAs
 // as [floor(c U / G), floor((c+1) U / G)).
-__host__ __device__ __forceinline__ long long unit_owner(long long u, long long units, long long grid) {
-    return ((u + 1) * grid + units - 1) / units - 1;
-}
 
 // Output row rg of a tile split over np pieces: out[j * ldc + rg] = the
 // pieces' FP32 partials added in piece order in FP32, for j < ell, then
@@ -522,7 +520,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce_bar[a]);
-            if (np > 1) {
+            if (np > 1 && !p.defer) {
                 // publish this piece, then count it; the CTA completing the count reduces the tile
                 __threadfence();
                 __syncwarp();
@@ -848,7 +846,7 @@ cudaError_t tc_launch(const void* a, bool tf32, long long mtot, long long ktot_s
                       long long brows_k, int nparts, int trans, int64_t ell, int64_t ellp, void* part,
                       int* tile_cnt, void* c,
                       ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel, cudaStream_t st,
-                      int kgroup) {
+                      int kgroup, TcPieces* pieces) {
     const Plan pl = make_plan(mtot, ktot_seg, kseg, tf32, num_sms, kgroup);
     const int ke = tf32 ? 32 : 64;  // K elements per 128-byte row
     const int nb = nparts * (int)ellp;
@@ -874,6 +872,15 @@ cudaError_t tc_launch(const void* a, bool tf32, long long mtot, long long ktot_s
     p.mtot = mtot;
     p.flags = flags;
     p.cancel = cancel;
+    p.defer = pieces ? 1 : 0;
+    if (pieces) {
+        pieces->part = static_cast<const float*>(part);
+        pieces->units = pl.units;
+        pieces->kc = pl.kc;
+        pieces->grid = pl.grid;
+        pieces->maxp = pl.maxp;
+        pieces->ellp = (int)ellp;
+    }
     p.a_boxes = a_boxes;
     p.a_box_cols = a_box_cols;
     p.b_boxes = nb > 256 ? 2 : 1;
@@ -938,7 +945,7 @@ int sketch_kgroup(int64_t ellp) { return ellp <= 64 ? 2 : 1; }
 cudaError_t launch_sketch_tc(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, int trans,
                              const void* x, int64_t ldx, int64_t ell, int64_t ellp, void* part, int* tile_cnt,
                              void* c, ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel,
-                             cudaStream_t st) {
+                             cudaStream_t st, TcPieces* pieces) {
     if (ta != T_BF16 && ta != T_F32) return cudaErrorInvalidValue;
     if (ellp % 16 != 0 || ellp < 16 || ellp > 128 || ell > ellp) return cudaErrorInvalidValue;
     // The MN-major tf32 operand form (A^T Y in TF32) is not enabled.
@@ -961,12 +968,13 @@ cudaError_t launch_sketch_tc(const void* a, ElemType ta, int64_t m, int64_t n, i
     if (e != cudaSuccess) return e;
     return tc_launch(a, tf32, trans ? n : m, trans ? m : n, 1, 0, map_a, a_boxes, a_box_cols, x, ldx, trans ? m : n,
                      1, trans, ell, ellp, part, tile_cnt, c, tcout, ldc, num_sms, flags, cancel, st,
-                     sketch_kgroup(ellp));
+                     sketch_kgroup(ellp), pieces);
 }
 
 cudaError_t launch_project_split_tc(const void* a3, int64_t m, int64_t n, int64_t seg, const void* q3, int64_t ldq,
                                     int64_t ell, int64_t ellp, void* part, int* tile_cnt, void* w, ElemType tw,
-                                    int64_t ldw, int num_sms, int* flags, const int* cancel, cudaStream_t st) {
+                                    int64_t ldw, int num_sms, int* flags, const int* cancel, cudaStream_t st,
+                                    TcPieces* pieces) {
     if (ellp % 16 != 0 || ellp < 16 || ellp > 128 || ell > ellp || seg % 64 != 0) return cudaErrorInvalidValue;
     cudaError_t e = get_encoder();
     if (e != cudaSuccess) return e;
@@ -975,7 +983,7 @@ cudaError_t launch_project_split_tc(const void* a3, int64_t m, int64_t n, int64_
     if (e != cudaSuccess) return e;
     // one box per stage: a K chunk must not run from one split segment into the next
     return tc_launch(a3, false, m, n, 3, seg, map_a, 1, 0, q3, ldq, n, 3, 0, ell, ellp, part, tile_cnt, w, tw, ldw,
-                     num_sms, flags, cancel, st, 1);
+                     num_sms, flags, cancel, st, 1, pieces);
 }
 
 bool tma_rows_aligned(const void* a, int64_t lda, int elem_bytes) {

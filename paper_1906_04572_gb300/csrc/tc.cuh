@@ -22,12 +22,14 @@ int64_t tc_counter_elems(int64_t m, int64_t n);
 // lda (lda * elem_size a multiple of 16 bytes). X: panel of the same element
 // type with ellp columns (padding columns zero), ld ldx. FP32 accumulation;
 // C is written with element type tcout (FP64 or FP32). `part` holds split
-// partials, `tile_cnt` the per-tile counters (tc_counter_elems).
+// partials, `tile_cnt` the per-tile counters (tc_counter_elems). With
+// `pieces` non-null the split tiles are left as pieces in `part` (described in
+// *pieces) for the consumer to add; the counters are not used.
 cudaError_t launch_sketch_tc(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, int trans,
                              const void* x, int64_t ldx, int64_t ell, int64_t ellp, void* part, int* tile_cnt,
                              void* c,
                              ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel,
-                             cudaStream_t st);
+                             cudaStream_t st, TcPieces* pieces = nullptr);
 
 // abf[i * ldb + j] = bf16(A[i * lda + j]) (round to nearest even); columns
 // [n, ldb) are zero.
@@ -51,7 +53,8 @@ cudaError_t launch_copy_f32_padded(const float* a, int64_t m, int64_t n, int64_t
 cudaError_t launch_project_split_tc(const void* a3, int64_t m, int64_t n, int64_t seg, const void* q3, int64_t ldq,
                                     int64_t ell, int64_t ellp, void* part, int* tile_cnt, void* w, ElemType tw,
                                     int64_t ldw,
-                                    int num_sms, int* flags, const int* cancel, cudaStream_t st);
+                                    int num_sms, int* flags, const int* cancel, cudaStream_t st,
+                                    TcPieces* pieces = nullptr);
 // Writes a3 (rows of [A_h | A_m | A_l]) from FP32 A.
 cudaError_t launch_cast_bf16_split(const float* a, int64_t m, int64_t n, int64_t lda, void* a3, int64_t seg,
                                    const int* cancel, cudaStream_t st);
