@@ -162,7 +162,11 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
             const double u = unit_roundoff;
             shift = 11.0 * ((double)rows * ell + (double)ell * (ell + 1)) * u * trace * (attempt == 1 ? 1.0 : 100.0);
         }
-        // eight loads in flight per thread before their stores
+        // eight loads in flight per thread before their stores; the row index
+        // from an FP32 product ((e + 1/2) / ell is at least 1/(2 ell) away from an
+        // integer, far above the product's rounding for e < 2^14), and no FP64
+        // operation on the way (the shift is added to the diagonal afterwards)
+        const float inv_ell = 1.0f / (float)ell;
         for (int e0 = 0; e0 < ell * ell; e0 += 8 * kCholThreads) {
             double v[8];
 #pragma unroll
@@ -174,10 +178,14 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
             for (int k = 0; k < 8; ++k) {
                 const int e = e0 + tid + k * kCholThreads;
                 if (e < ell * ell) {
-                    const int a = e / ell, b = e % ell;
-                    S[a * ld + b] = v[k] + (a == b ? shift : 0.0);
+                    const int a = __float2int_rz(((float)e + 0.5f) * inv_ell), b = e - a * ell;
+                    S[a * ld + b] = v[k];
                 }
             }
+        }
+        if (attempt > 0) {
+            __syncthreads();
+            for (int a = tid; a < ell; a += kCholThreads) S[a * ld + a] += shift;
         }
         for (int a = tid; a < ell; a += kCholThreads) {
             rowdep[a] = 0;
@@ -269,7 +277,7 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
                 bar_arrive(1 + (s & 1), kSync);
                 // rows >= s+3: the prefix tri[0 .. len3) of the bottom-up enumeration
                 const int len3 = (n1 - 1) * n1 / 2;
-#pragma unroll 2
+#pragma unroll 4
                 for (int e0 = 32 * wu; e0 < len3; e0 += kCholUpdThreads) {
                     const int e = e0 + lane;
                     const int ac = tri[e < len3 ? e : len3 - 1];
@@ -288,21 +296,21 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
     // R_tc = S_tc / sqrt(p_t) for c >= t (the diagonal p_t / sqrt(p_t)); dependent rows -> e_t
     for (int t = tid; t < ell; t += kCholThreads) ys[t] = (broke || rowdep[t]) ? 0.0 : rsqrt_nr(S[t * ld + t]);
     __syncthreads();
-    for (int a = warp; a < ell; a += kCholThreads / 32) {
-        double* ra = r + (size_t)a * ell;
-        if (broke || rowdep[a]) {
-            for (int b = lane; b < ell; b += 32) ra[b] = (a == b) ? 1.0 : 0.0;
-            continue;
-        }
-        const double ya = ys[a];
-        const double* Sa = S + a * ld;
-        int b0 = 0;
-        for (; b0 + 31 < a; b0 += 32) ra[b0 + lane] = 0.0;  // strips left of the diagonal
-        for (; b0 < ell; b0 += 32) {
-            const int b = b0 + lane;
-            const double x = Sa[b < ell ? b : ell - 1] * ya;
-            if (b < ell) ra[b] = b >= a ? x : 0.0;
-        }
+    // the upper triangle through the packed enumeration `tri` (every lane of an
+    // FP64 multiply busy), the lower one as zeros; dependent rows (and all rows
+    // after a breakdown) are e_a
+    const int ntri = ell * (ell + 1) / 2;
+    for (int e = tid; e < ntri; e += kCholThreads) {
+        const int ac = tri[e];
+        const int a = ac >> 8, c = ac & 0xff;
+        const bool unit = broke || rowdep[a];
+        const double x = S[a * ld + c] * ys[a];
+        r[(size_t)a * ell + c] = unit ? (a == c ? 1.0 : 0.0) : x;
+    }
+    const float inv_ell = 1.0f / (float)ell;
+    for (int e = tid; e < ell * ell; e += kCholThreads) {
+        const int a = __float2int_rz(((float)e + 0.5f) * inv_ell), c = e - a * ell;
+        if (c < a) r[e] = 0.0;
     }
     if (tid == 0) {
         if (broke) atomicExch(&flags[FLAG_BREAKDOWN], 1);
