@@ -218,6 +218,21 @@ def corutv(a: np.ndarray, k: int, p: int, q: int, psi: np.ndarray | None = None,
     return out
 
 
+def corutv_lower(a: np.ndarray, k: int, p: int, q: int, psi: np.ndarray | None = None,
+                 seed: int = 0, stream: int = 0) -> dict:
+    """CoR-UTV with a lower triangular middle factor, the variant Sec. 3 sets
+    beside the m >= n form for m < n and calls a direct modification of it.
+    Reading: Algorithm 1 applied to A^T. Its factorisation A^T ~ U' T' V'^T
+    gives A ~ V' T'^T U'^T, so U = V' = Q2' P (m x ell), T = T'^T (lower
+    triangular), V = U' = Q1' Qt (n x ell); perm is the column permutation of
+    U. psi is the m x ell test matrix of A^T. Q1, Q2 and D are those of the
+    run on A^T (Q1: n x ell, Q2: m x ell). Any shape is accepted."""
+    a = _f64(a)
+    o = corutv(np.ascontiguousarray(a.T), k, p, q, psi=psi, seed=seed, stream=stream)
+    return {"U": o["V"], "T": np.ascontiguousarray(o["T"].T), "V": o["U"], "perm": o["perm"],
+            "Q1": o["Q1"], "Q2": o["Q2"], "D": o["D"]}
+
+
 def corutv_dapprox(a: np.ndarray, k: int, p: int, q: int, psi: np.ndarray) -> dict:
     """CoR-UTV with the single-pass core (Sec. 3.1, the paragraph after eq. 9;
     Algorithm 1, its "D_approx" alternative): D = Q1^T A Q2 (eq. 7) is replaced

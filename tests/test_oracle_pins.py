@@ -307,6 +307,46 @@ def test_error_versus_truncated_svd(oracle_lib, q):
     assert ek >= np.sqrt(np.sum(sv[k:] ** 2)) * (1 - 1e-12)
 
 
+# ------------------------------------------------------------ m < n, lower T
+
+@pytest.mark.parametrize("m,n,rank,k,p,q", [(200, 300, 8, 8, 4, 1), (120, 400, 5, 10, 10, 2)])
+def test_lower_variant_reproduces_exact_rank(oracle_lib, m, n, rank, k, p, q):
+    """The m < n variant (lower triangular T, Sec. 3) reproduces an A of exact
+    rank <= ell to rounding, with T exactly lower triangular, U (m x ell) and
+    V (n x ell) orthonormal and |diag T| non-increasing (rank revealing)."""
+    f = synth.exact_rank_case(m, n, rank, k, p, q, seed=m + 2 * n)
+    ell = k + p
+    o = oracle_lib.corutv_lower(f.a, k, p, q, synth.gaussian_psi(m, ell, seed=3))
+    u, t, v = o["U"], o["T"], o["V"]
+    assert u.shape == (m, ell) and t.shape == (ell, ell) and v.shape == (n, ell)
+    assert np.all(np.triu(t, 1) == 0)
+    assert np.linalg.norm(u.T @ u - np.eye(ell)) < 50 * ell * 2.2e-16
+    assert np.linalg.norm(v.T @ v - np.eye(ell)) < 50 * ell * 2.2e-16
+    assert _rel(u @ t @ v.T, f.a) < 1e-13
+    dg = np.abs(np.diag(t))
+    assert np.all(np.diff(dg[:rank]) <= 1e-12 * dg[0])
+
+
+@pytest.mark.parametrize("q", [0, 2])
+def test_lower_variant_error_versus_truncated_svd(oracle_lib, q):
+    """For a wide A (m < n) the lower-T factorisation meets the same bounds as
+    the upper one: ||A - U T V^T||_F at least the ell-term optimum, within a few
+    per cent of it with q = 2; the leading k x k block of T keeps the rank-k
+    truncation above the rank-k optimum."""
+    m, n = 250, 300
+    sigma = 1.0 / np.arange(1, 251) ** 1.0
+    a = synth.spectrum_matrix(m, n, sigma, 0.0, 12)
+    k, p = 20, 5
+    o = oracle_lib.corutv_lower(a, k, p, q, synth.gaussian_psi(m, k + p, seed=6))
+    err = np.linalg.norm(a - o["U"] @ o["T"] @ o["V"].T)
+    sv = np.linalg.svd(a, compute_uv=False)
+    opt = np.sqrt(np.sum(sv[k + p:] ** 2))
+    assert err >= opt * (1 - 1e-12)
+    assert err <= (1.05 if q == 2 else 3.0) * opt
+    ek = np.linalg.norm(a - o["U"][:, :k] @ o["T"][:k, :k] @ o["V"][:, :k].T)
+    assert ek >= np.sqrt(np.sum(sv[k:] ** 2)) * (1 - 1e-12)
+
+
 def test_literal_and_reorthonormalised_forms_agree(oracle_lib):
     """Algorithm 1 as printed and the re-orthonormalised loop give the same
     factorisation in exact arithmetic; on a well-conditioned case they agree
