@@ -76,8 +76,13 @@ typedef struct {
                              other values -> CORUTV_EINVAL */
     uint64_t seed;        /* Philox-4x32-10 key for Psi when psi == NULL */
     uint32_t stream;      /* Philox counter word 2 (independent draws per call) */
-    uint32_t reserved;
-    const double* psi;    /* optional n x ell row-major FP64 Gaussian test matrix */
+    uint32_t t_lower;     /* 0: T upper triangular (Algorithm 1 on A, any shape); 1: T lower
+                             triangular, the variant Sec. 3 gives for m < n: Algorithm 1 on
+                             A^T, whose A^T ~ U' T' V'^T is returned as U = V' (its Q2 P: perm
+                             permutes the columns of U), T = T'^T, V = U' (any shape);
+                             other values -> CORUTV_EINVAL */
+    const double* psi;    /* optional row-major FP64 Gaussian test matrix: n x ell, or
+                             m x ell when t_lower = 1 */
 } corutv_opts;
 
 typedef struct corutv_ctx corutv_ctx;
@@ -107,6 +112,8 @@ corutv_status corutv_sync(corutv_ctx* ctx);
  *   Psi (n x ell, Gaussian) -> for i = 0..q: C1 = A X, Q1 = qr(C1),
  *   C2 = A^T Q1, X = qr(C2) (i < q) -> Q2 = qr(C2) -> D = Q1^T A Q2 ->
  *   D P = Qt Rt (column-pivoted QR) -> U = Q1 Qt, T = Rt, V = Q2 P.
+ *   With opts->t_lower = 1 the same steps run on A^T (the lower-T variant of
+ *   Sec. 3 for m < n): U = Q2 P, T = Rt^T, V = Q1 Qt of that run.
  * Each sketch is re-orthonormalised before its next use (CholeskyQR2); in
  * exact arithmetic this gives the same Q1, Q2 as the printed loop.
  * A: m x n (lda). U: m x ell (ldu), T: ell x ell upper triangular (row

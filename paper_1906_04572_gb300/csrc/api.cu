@@ -159,7 +159,12 @@ struct DeviceBuffer {
 // Plan and buffers of one factorisation.
 // ---------------------------------------------------------------------------
 struct FactorPlan {
+    // m, n (and the panel strides ldm, ldn) are those of the matrix Algorithm 1
+    // runs on: A, or A^T for the lower-T variant (tr); ma, na are A's own
+    // rows and columns and ldma, ldna the strides of panels with ma / na rows
     int64_t m, n, lda, k, p, q, ell, ellp, ldm, ldn;
+    bool tr;
+    int64_t ma, na, ldma, ldna;
     ElemType ta;
     corutv_prec prec;
     ElemType tcomp;   // element type of the B operand of the sketch products
@@ -194,10 +199,14 @@ struct FactorBufs {
 
 // a_aligned: the device copy of A that the factorisation reads starts on a
 // 16-byte boundary (only TF32 sketches read A itself through TMA).
+// t_lower: the variant with a lower triangular T (Algorithm 1 on A^T).
 corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64_t lda, int64_t k,
                         int64_t p, int64_t q, corutv_prec prec, int num_sms, bool a_aligned = true,
-                        int d_mode = 0) {
-    pl.m = m; pl.n = n; pl.lda = lda; pl.k = k; pl.p = p; pl.q = q;
+                        int d_mode = 0, bool t_lower = false) {
+    pl.tr = t_lower;
+    pl.ma = m; pl.na = n;
+    pl.m = t_lower ? n : m; pl.n = t_lower ? m : n;
+    pl.lda = lda; pl.k = k; pl.p = p; pl.q = q;
     pl.ell = k + p;
     pl.ta = ta;
     pl.prec = prec;
@@ -220,14 +229,16 @@ corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64
     pl.copy_a = prec == CORUTV_P_TF32 && (!a_aligned || lda % 4 != 0);
     pl.ldc32 = round_up(n, 4);
     pl.ellp = pl.tensor ? round_up(pl.ell, 16) : pl.ell;
-    pl.ldm = round_up(m, 64);
-    pl.ldn = round_up(n, 64);
+    pl.ldm = round_up(pl.m, 64);
+    pl.ldn = round_up(pl.n, 64);
+    pl.ldma = t_lower ? pl.ldn : pl.ldm;
+    pl.ldna = t_lower ? pl.ldm : pl.ldn;
     pl.tcomp = pl.tensor ? (prec == CORUTV_P_BF16 ? T_BF16 : T_F32) : (prec == CORUTV_P_F64 ? T_F64 : T_F32);
     pl.tdproj = (ta == T_F64) ? T_F64 : T_F32;
     pl.torth = (prec == CORUTV_P_F64) ? T_F64 : T_F32;
     pl.tp = (ta == T_F32 && prec != CORUTV_P_F64) ? T_F32 : T_F64;
-    pl.sp_ax = gemm_simt_splits(m, n, num_sms);
-    pl.sp_aty = gemm_simt_splits(n, m, num_sms);
+    pl.sp_ax = gemm_simt_splits(pl.m, pl.n, num_sms);
+    pl.sp_aty = gemm_simt_splits(pl.n, pl.m, num_sms);
     pl.sp_w = pl.sp_ax;
     pl.gs_m = gemm_simt_splits(pl.ell, m, num_sms);
     pl.gs_n = gemm_simt_splits(pl.ell, n, num_sms);
@@ -250,7 +261,7 @@ void carve_factor(C& cv, const FactorPlan& pl, FactorBufs& b) {
     b.q1 = cv.template take<char>(pm * es_p);
     b.c2 = cv.template take<char>(pn * es_p);
     b.q2 = cv.template take<char>(pn * es_p);
-    b.w = cv.template take<char>(pm * es_p);
+    b.w = cv.template take<char>(std::max(pm, pn) * es_p);  // A Q2, or A Q1 for the lower-T variant
     b.tmp = cv.template take<char>(std::max(pm, pn) * es_p);
     b.upanel = cv.template take<double>(pm);
     b.zpanel = cv.template take<double>(pn);
@@ -268,12 +279,12 @@ void carve_factor(C& cv, const FactorPlan& pl, FactorBufs& b) {
     b.defic = cv.template take<int>(pl.ellp);
     b.xc = cv.template take<char>(pn * es_c);
     b.q1c = cv.template take<char>(pm * es_c);
-    b.q2c = cv.template take<char>(pl.split ? 3 * pn * 2 : pn * es_d);
+    b.q2c = cv.template take<char>(pl.split ? 3 * std::max(pm, pn) * 2 : std::max(pm, pn) * es_d);
     b.part = cv.template take<char>(pl.part_elems * std::max(8, std::max(es_c, es_d)));
-    b.abf = (pl.prec == CORUTV_P_BF16 || pl.split) ? cv.template take<char>(pl.m * (pl.split ? 3 : 1) * pl.seg * 2)
+    b.abf = (pl.prec == CORUTV_P_BF16 || pl.split) ? cv.template take<char>(pl.ma * (pl.split ? 3 : 1) * pl.seg * 2)
                                                    : nullptr;
-    b.at = pl.prec == CORUTV_P_TF32 ? cv.template take<float>(pl.n * pl.ldm) : nullptr;
-    b.a32 = pl.copy_a ? cv.template take<float>(pl.m * pl.ldc32) : nullptr;
+    b.at = pl.prec == CORUTV_P_TF32 ? cv.template take<float>(pl.na * pl.ldma) : nullptr;
+    b.a32 = pl.copy_a ? cv.template take<float>(pl.ma * pl.ldc32) : nullptr;
     b.perm = cv.template take<int>(pl.ellp);
     b.skip = cv.template take<int>(8);
     b.tcnt = cv.template take<int>(factor_counters(pl));
@@ -296,14 +307,14 @@ struct Exec {
 };
 
 // C = A X (am = A_ROWS, R = m, K = n) or A^T Y (am = A_COLS, R = n, K = m) on
-// SIMT cores, written to the panel `out` (type pl.tp).
+// SIMT cores for A's own m x n, written to the panel `out` (type pl.tp).
 corutv_status sketch_simt(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, AMode am,
                           const void* a, ElemType ta, const void* bop, ElemType tc, void* out,
                           int64_t ldout) {
-    const int64_t R = am == A_ROWS ? pl.m : pl.n;
-    const int64_t K = am == A_ROWS ? pl.n : pl.m;
-    const int splits = am == A_ROWS ? pl.sp_ax : pl.sp_aty;
-    const int64_t ldb = am == A_ROWS ? pl.ldn : pl.ldm;
+    const int64_t R = am == A_ROWS ? pl.ma : pl.na;
+    const int64_t K = am == A_ROWS ? pl.na : pl.ma;
+    const int splits = gemm_simt_splits(R, K, ex.num_sms);
+    const int64_t ldb = am == A_ROWS ? pl.ldna : pl.ldma;
     GemmArgs g{am, B_PANEL, O_PANEL, ta, tc, a, pl.lda, bop, ldb, b.part, ldout, pl.ellp * ldout,
                R, K, pl.ell, splits, ex.cancel};
     {
@@ -400,12 +411,13 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
         CK(launch_panel_convert(b.x, pl.tp, pl.ldn, n, pl.ellp, b.xc, pl.tcomp, pl.ldn, ex.cancel, ex.st));
         if (pl.prec == CORUTV_P_TF32)
             // one pass over A: A^T for the K-major A^T Y, the bf16 splits for eq. 7
-            CK(launch_prep_f32(static_cast<const float*>(a), m, n, pl.lda, b.at, pl.ldm, b.abf, pl.seg, b.a32,
-                               pl.ldc32, ex.cancel, ex.st));
+            CK(launch_prep_f32(static_cast<const float*>(a), pl.ma, pl.na, pl.lda, b.at, pl.ldma, b.abf, pl.seg,
+                               b.a32, pl.ldc32, ex.cancel, ex.st));
         else if (pl.split)
-            CK(launch_cast_bf16_split(static_cast<const float*>(a), m, n, pl.lda, b.abf, pl.seg, ex.cancel, ex.st));
+            CK(launch_cast_bf16_split(static_cast<const float*>(a), pl.ma, pl.na, pl.lda, b.abf, pl.seg, ex.cancel,
+                                      ex.st));
         else if (pl.prec == CORUTV_P_BF16)
-            CK(launch_cast_bf16(a, pl.ta, m, n, pl.lda, b.abf, pl.seg, ex.cancel, ex.st));
+            CK(launch_cast_bf16(a, pl.ta, pl.ma, pl.na, pl.lda, b.abf, pl.seg, ex.cancel, ex.st));
     } else {
         CK(launch_panel_convert(b.x, pl.tp, pl.ldn, n, ell, b.xc, pl.tcomp, pl.ldn, ex.cancel, ex.st));
     }
@@ -414,33 +426,36 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     // first reads the panel adds them (no fix-up tail in the product)
     TcPieces pieces;
     TcPieces* defer = (pl.tp == T_F32 && pl.torth == T_F32 && pl.tdproj == T_F32) ? &pieces : nullptr;
-    for (int64_t it = 0; it <= pl.q; ++it) {
-        // eq. 4: C1 = A X
-        if (pl.tensor) {
+    // A X (a_rows: the output has A's rows, the operand is a panel with A's
+    // columns) or A^T Y (the other way round). Algorithm 1's C1 = A X is the
+    // first, C2 = A^T Q1 the second; on A^T (the lower-T variant) the two swap.
+    auto product = [&](bool a_rows, const void* opnd, void* out, TcPieces* pc) -> corutv_status {
+        const int64_t ldo = a_rows ? pl.ldna : pl.ldma, ldout = a_rows ? pl.ldma : pl.ldna;
+        if (!pl.tensor) return sketch_simt(ex, pl, b, a_rows ? A_ROWS : A_COLS, a, pl.ta, opnd, pl.tcomp, out, ldout);
+        ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
+        if (a_rows) {
             const bool bf = pl.prec == CORUTV_P_BF16;
             const void* aop = bf ? b.abf : (pl.copy_a ? static_cast<const void*>(b.a32) : a);
             const int64_t lda_op = bf ? ldabf : (pl.copy_a ? pl.ldc32 : pl.lda);
-            ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
-            CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, /*trans=*/0, b.xc, pl.ldn, ell, pl.ellp, b.part,
-                                b.tcnt, b.c1, pl.tp, pl.ldm, ex.num_sms, ex.flags, ex.cancel, ex.st, defer));
-        } else {
-            CKS(sketch_simt(ex, pl, b, A_ROWS, a, pl.ta, b.xc, pl.tcomp, b.c1, pl.ldm));
+            CK(launch_sketch_tc(aop, pl.tcomp, pl.ma, pl.na, lda_op, /*trans=*/0, opnd, ldo, ell, pl.ellp, b.part,
+                                b.tcnt, out, pl.tp, ldout, ex.num_sms, ex.flags, ex.cancel, ex.st, pc));
+        } else if (pl.prec == CORUTV_P_BF16) {
+            CK(launch_sketch_tc(b.abf, pl.tcomp, pl.ma, pl.na, ldabf, /*trans=*/1, opnd, ldo, ell, pl.ellp, b.part,
+                                b.tcnt, out, pl.tp, ldout, ex.num_sms, ex.flags, ex.cancel, ex.st, pc));
+        } else {  // TF32: (A^T) Y with the transposed copy, both operands K-major
+            CK(launch_sketch_tc(b.at, pl.tcomp, pl.na, pl.ma, pl.ldma, /*trans=*/0, opnd, ldo, ell, pl.ellp, b.part,
+                                b.tcnt, out, pl.tp, ldout, ex.num_sms, ex.flags, ex.cancel, ex.st, pc));
         }
+        return CORUTV_OK;
+    };
+    for (int64_t it = 0; it <= pl.q; ++it) {
+        // eq. 4: C1 = A X
+        CKS(product(!pl.tr, b.xc, b.c1, defer));
         const int inner = (pl.prec == CORUTV_P_F64) ? 2 : 1;  // passes for the intermediate bases
         CKS(orth(ex, pl, b, b.c1, pl.ldm, m, b.q1, b.q1c, pl.tcomp, it < pl.q ? inner : 2, nullptr, &pieces));
         pieces = TcPieces();
         // eq. 5 (with C1 -> Q1): C2 = A^T Q1
-        if (pl.tensor) {
-            ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
-            if (pl.prec == CORUTV_P_BF16)
-                CK(launch_sketch_tc(b.abf, pl.tcomp, m, n, ldabf, /*trans=*/1, b.q1c, pl.ldm, ell, pl.ellp, b.part,
-                                    b.tcnt, b.c2, pl.tp, pl.ldn, ex.num_sms, ex.flags, ex.cancel, ex.st, defer));
-            else  // TF32: (A^T) Y with the transposed copy, both operands K-major
-                CK(launch_sketch_tc(b.at, pl.tcomp, n, m, pl.ldm, /*trans=*/0, b.q1c, pl.ldm, ell, pl.ellp, b.part,
-                                    b.tcnt, b.c2, pl.tp, pl.ldn, ex.num_sms, ex.flags, ex.cancel, ex.st, defer));
-        } else {
-            CKS(sketch_simt(ex, pl, b, A_COLS, a, pl.ta, b.q1c, pl.tcomp, b.c2, pl.ldn));
-        }
+        CKS(product(pl.tr, b.q1c, b.c2, defer));
         if (it < pl.q) {
             CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.x, b.xc, pl.tcomp, inner, nullptr, &pieces));
             pieces = TcPieces();
@@ -456,27 +471,39 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
         CK(launch_qrcp(b.d, ell, b.qt, b.rt, b.perm, b.refl, ex.cancel, ex.st, /*form_q=*/false));
         return CORUTV_OK;
     }
-    CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.q2, pl.split ? nullptr : b.q2c, pl.tdproj, 2, nullptr, &pieces));
+    // the non-split projection multiplies A by Q2 in its own arithmetic (a copy
+    // made here), or by Q1 for the lower-T variant (converted below)
+    CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.q2, (pl.split || pl.tr) ? nullptr : b.q2c, pl.tdproj, 2, nullptr,
+             &pieces));
     pieces = TcPieces();
-    // eq. 7: W = A Q2 (FP64, or FP32-accurate from the original A), D = Q1^T W
+    // eq. 7: W = A Q2 (FP64, or FP32-accurate from the original A), D = Q1^T W.
+    // Lower-T variant (Algorithm 1 on A^T): D = Q1^T A^T Q2 = (A Q1)^T Q2, so W = A Q1
+    // and D = W^T Q2 -- the same product with A, Q1 in the place of Q2.
+    const void* pan = pl.tr ? b.q1 : b.q2;  // the operand panel (A's columns)
     if (pl.split) {
-        CK(launch_split_panel(static_cast<const float*>(b.q2), pl.ldn, n, ell, pl.ellp, b.q2c, pl.ldn, ex.cancel,
-                              ex.st));
+        CK(launch_split_panel(static_cast<const float*>(pan), pl.ldna, pl.na, ell, pl.ellp, b.q2c, pl.ldna,
+                              ex.cancel, ex.st));
         ProfScope ps(ex.prof, CORUTV_STAGE_PROJECT, ex.st);
-        CK(launch_project_split_tc(b.abf, m, n, pl.seg, b.q2c, pl.ldn, ell, pl.ellp, b.part, b.tcnt, b.w, pl.tp,
-                                   pl.ldm,
-                                   ex.num_sms, ex.flags, ex.cancel, ex.st, defer));
+        CK(launch_project_split_tc(b.abf, pl.ma, pl.na, pl.seg, b.q2c, pl.ldna, ell, pl.ellp, b.part, b.tcnt, b.w,
+                                   pl.tp, pl.ldma, ex.num_sms, ex.flags, ex.cancel, ex.st, defer));
     } else {
-        GemmArgs g{A_ROWS, B_PANEL, O_PANEL, pl.ta, pl.tdproj, a, pl.lda, b.q2c, pl.ldn, b.part, pl.ldm,
-                   pl.ellp * pl.ldm, m, n, ell, pl.sp_w, ex.cancel};
+        const void* opnd = b.q2c;
+        if (pl.tr) {
+            if (pl.tp == pl.tdproj) opnd = b.q1;
+            else CK(launch_panel_convert(b.q1, pl.tp, pl.ldna, pl.na, ell, b.q2c, pl.tdproj, pl.ldna, ex.cancel, ex.st));
+        }
+        const int sp = gemm_simt_splits(pl.ma, pl.na, ex.num_sms);
+        GemmArgs g{A_ROWS, B_PANEL, O_PANEL, pl.ta, pl.tdproj, a, pl.lda, opnd, pl.ldna, b.part, pl.ldma,
+                   pl.ellp * pl.ldma, pl.ma, pl.na, ell, sp, ex.cancel};
         {
             ProfScope ps(ex.prof, CORUTV_STAGE_PROJECT, ex.st);
             CK(launch_gemm_simt(g, ex.st));
         }
-        CK(launch_reduce_splits(b.part, pl.tdproj, pl.sp_w, pl.ellp * pl.ldm, b.w, pl.tp, pl.ldm, m, ell, pl.ldm,
+        CK(launch_reduce_splits(b.part, pl.tdproj, sp, pl.ellp * pl.ldma, b.w, pl.tp, pl.ldma, pl.ma, ell, pl.ldma,
                                 ex.cancel, ex.st));
     }
-    CKS(gram(ex, pl, b, b.q1, pl.ldm, b.w, pl.ldm, m, b.d, ex.cancel, pl.tdproj, nullptr, &pieces));
+    if (pl.tr) CKS(gram(ex, pl, b, b.w, pl.ldn, b.q2, pl.ldn, n, b.d, ex.cancel, pl.tdproj, &pieces, nullptr));
+    else CKS(gram(ex, pl, b, b.q1, pl.ldm, b.w, pl.ldm, m, b.d, ex.cancel, pl.tdproj, nullptr, &pieces));
     // eq. 8: D P = Qt Rt
     {
         ProfScope ps(ex.prof, CORUTV_STAGE_QRCP, ex.st);
@@ -485,14 +512,19 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     return CORUTV_OK;
 }
 
-// Eq. 9 into caller buffers (device): U = Q1 Qt, T = Rt, V = Q2 P, perm.
+// Eq. 9 into caller buffers (device): U = Q1 Qt, T = Rt, V = Q2 P, perm. For
+// the lower-T variant the run was on A^T: A's U is that run's Q2 P (the
+// permutation acts on U's columns), V its Q1 Qt and T = Rt^T.
 corutv_status emit_user(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, ElemType tout, void* u,
                         int64_t ldu, void* t, void* v, int64_t ldv, int32_t* perm) {
     const int64_t ell = pl.ell;
-    // U = Q1 Qt, applied as the QRCP's reflectors to the rows of Q1
-    if (u) CK(launch_apply_reflectors(b.q1, pl.tp, pl.ldm, pl.m, ell, b.refl, u, tout, ldu, false, ex.cancel, ex.st));
-    CK(launch_copy_small(b.rt, ell, t, tout, ex.cancel, ex.st));
-    if (v) CK(launch_gather_v(b.q2, pl.tp, pl.ldn, pl.n, ell, b.perm, v, tout, ldv, ex.cancel, ex.st));
+    void* uq = pl.tr ? v : u;  // receives Q1 Qt
+    void* vq = pl.tr ? u : v;  // receives Q2 P
+    const int64_t lduq = pl.tr ? ldv : ldu, ldvq = pl.tr ? ldu : ldv;
+    // Q1 Qt, applied as the QRCP's reflectors to the rows of Q1
+    if (uq) CK(launch_apply_reflectors(b.q1, pl.tp, pl.ldm, pl.m, ell, b.refl, uq, tout, lduq, false, ex.cancel, ex.st));
+    CK(launch_copy_small(b.rt, ell, t, tout, ex.cancel, ex.st, pl.tr));
+    if (vq) CK(launch_gather_v(b.q2, pl.tp, pl.ldn, pl.n, ell, b.perm, vq, tout, ldvq, ex.cancel, ex.st));
     if (perm) CK(cudaMemcpyAsync(perm, b.perm, sizeof(int32_t) * ell, cudaMemcpyDeviceToDevice, ex.st));
     return CORUTV_OK;
 }
@@ -753,9 +785,10 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
     const bool dev = is_device_ptr(A);
     if (lda < n) return fail(CORUTV_EINVAL, "lda = %lld < n = %lld", (long long)lda, (long long)n);
     FactorPlan pl;
+    if (opts->t_lower > 1) return fail(CORUTV_EINVAL, "t_lower %u is not supported (0 upper T, 1 lower T)", opts->t_lower);
     // host input is staged with row stride n into the (256-byte aligned) workspace
     CKS(make_plan(pl, ta, m, n, dev ? lda : n, opts->k, opts->p, opts->q, (corutv_prec)opts->sketch_prec,
-                  ctx->num_sms, !dev || reinterpret_cast<uintptr_t>(A) % 16 == 0, opts->d_mode));
+                  ctx->num_sms, !dev || reinterpret_cast<uintptr_t>(A) % 16 == 0, opts->d_mode, opts->t_lower == 1));
     const int64_t ell = pl.ell;
     if (U && ldu < ell) return fail(CORUTV_EINVAL, "ldu < ell");
     if (V && ldv < ell) return fail(CORUTV_EINVAL, "ldv < ell");
@@ -773,7 +806,7 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
         extra_measure.take<char>(ell * ell * es);
         extra_measure.take<int>(ell);
     }
-    if (opts->psi && !psi_dev) extra_measure.take<double>(n * ell);
+    if (opts->psi && !psi_dev) extra_measure.take<double>(pl.n * ell);  // Psi has the rows of pl.n
     CKS(ensure_ws(ctx, ctx->ws, bytes + extra_measure.off, ctx->stream));
     Carver cv(ctx->ws.ptr);
     FactorBufs b;
@@ -802,8 +835,8 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
         if (psi_dev) {
             psi = opts->psi;
         } else {
-            double* ps = cv.take<double>(n * ell);
-            CK(cudaMemcpyAsync(ps, opts->psi, sizeof(double) * n * ell, cudaMemcpyHostToDevice, ctx->stream));
+            double* ps = cv.take<double>(pl.n * ell);
+            CK(cudaMemcpyAsync(ps, opts->psi, sizeof(double) * pl.n * ell, cudaMemcpyHostToDevice, ctx->stream));
             psi = ps;
         }
     }
@@ -890,6 +923,8 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
     pl.ellp = pl.tensor ? round_up(ell, 16) : ell;
     pl.ldm = round_up(m, 64);
     pl.ldn = round_up(n, 64);
+    pl.tr = false;
+    pl.ma = m; pl.na = n; pl.ldma = pl.ldm; pl.ldna = pl.ldn;
     pl.tcomp = pl.tensor ? (prec == CORUTV_P_BF16 ? T_BF16 : T_F32) : (prec == CORUTV_P_F64 ? T_F64 : T_F32);
     pl.tdproj = pl.tcomp;
     pl.tp = T_F64;
@@ -1180,9 +1215,13 @@ namespace {
 size_t request_bytes(const corutv_request& r, bool host, int num_sms, FactorPlan* plan_out, corutv_status* st) {
     FactorPlan pl;
     const ElemType ta = r.dtype == CORUTV_F64 ? T_F64 : T_F32;
+    if (r.opts.t_lower > 1) {
+        *st = fail(CORUTV_EINVAL, "t_lower %u is not supported (0 upper T, 1 lower T)", r.opts.t_lower);
+        return 0;
+    }
     *st = make_plan(pl, ta, r.m, r.n, host ? r.n : r.lda, r.opts.k, r.opts.p, r.opts.q,
                     (corutv_prec)r.opts.sketch_prec, num_sms, host || reinterpret_cast<uintptr_t>(r.A) % 16 == 0,
-                    r.opts.d_mode);
+                    r.opts.d_mode, r.opts.t_lower == 1);
     if (*st != CORUTV_OK) return 0;
     size_t bytes = factor_bytes(pl);
     const int es = elem_size(ta);
@@ -1196,7 +1235,7 @@ size_t request_bytes(const corutv_request& r, bool host, int num_sms, FactorPlan
         c.take<int>(ell);
         bytes += c.off;
     }
-    if (r.opts.psi) bytes += (size_t)round_up(r.n * ell * 8, 256);
+    if (r.opts.psi) bytes += (size_t)round_up(pl.n * ell * 8, 256);
     if (plan_out) *plan_out = pl;
     return bytes;
 }
@@ -1230,8 +1269,8 @@ corutv_status launch_request(corutv_ctx* ctx, ServingSlot& s, const PendingReq& 
     }
     const double* psi = nullptr;
     if (r.opts.psi) {
-        double* ps = cv.take<double>(n * ell);
-        CK(cudaMemcpyAsync(ps, r.opts.psi, sizeof(double) * n * ell, cudaMemcpyDefault, s.st));
+        double* ps = cv.take<double>(pl.n * ell);
+        CK(cudaMemcpyAsync(ps, r.opts.psi, sizeof(double) * pl.n * ell, cudaMemcpyDefault, s.st));
         psi = ps;
     }
     CK(cudaMemsetAsync(s.flags, 0, sizeof(int) * FLAG_COUNT, s.st));

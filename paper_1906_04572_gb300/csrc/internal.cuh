@@ -231,7 +231,7 @@ cudaError_t launch_apply_reflectors(const void* q1, ElemType tp, int64_t ldq, in
 cudaError_t launch_gather_v(const void* q2, ElemType tq2, int64_t ldq2, int64_t n, int64_t ell, const int* perm,
                             void* v, ElemType tv, int64_t ldv, const int* cancel, cudaStream_t st);
 cudaError_t launch_copy_small(const double* src, int64_t ell, void* dst, ElemType tdst,
-                              const int* cancel, cudaStream_t st);
+                              const int* cancel, cudaStream_t st, bool transpose = false);
 
 // RPCA pieces (k_rpca.cu).
 struct RpcaIterArgs {

@@ -879,13 +879,17 @@ __global__ void gather_v_kernel(const TQ* q2, int64_t ldq2, int64_t n, int ell, 
     }
 }
 
+// dst = src (ell x ell, row-major), or its transpose
 template <typename TD>
-__global__ void copy_small_kernel(const double* src, int n, TD* dst, const int* cancel) {
+__global__ void copy_small_kernel(const double* src, int ell, TD* dst, int transpose, const int* cancel) {
     pdl_trigger();
     pdl_wait();
     if (cancel && *cancel) return;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
-        dst[e] = (TD)src[e];
+    const int n = ell * ell;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int a = e / ell, c = e - a * ell;
+        dst[e] = (TD)src[transpose ? c * ell + a : e];
+    }
 }
 
 }  // namespace
@@ -1009,22 +1013,15 @@ cudaError_t launch_gather_v(const void* q2, ElemType tq2, int64_t ldq2, int64_t 
 }
 
 cudaError_t launch_copy_small(const double* src, int64_t ell, void* dst, ElemType tdst,
-                              const int* cancel, cudaStream_t st) {
-    const int n = (int)(ell * ell);
-    if (tdst == T_F64) {
-        count_launch();
-        {
-            cudaError_t pe_ = launch_pdl(copy_small_kernel<double>, dim3((n + 255) / 256), dim3(256), (size_t)(0), st, src, n, static_cast<double*>(dst), cancel);
-            if (pe_ != cudaSuccess) return pe_;
-        }
-    } else {
-        count_launch();
-        {
-            cudaError_t pe_ = launch_pdl(copy_small_kernel<float>, dim3((n + 255) / 256), dim3(256), (size_t)(0), st, src, n, static_cast<float*>(dst), cancel);
-            if (pe_ != cudaSuccess) return pe_;
-        }
-    }
-    return cudaGetLastError();
+                              const int* cancel, cudaStream_t st, bool transpose) {
+    const int l = (int)ell, n = l * l;
+    count_launch();
+    cudaError_t e = tdst == T_F64
+                        ? launch_pdl(copy_small_kernel<double>, dim3((n + 255) / 256), dim3(256), (size_t)0, st, src, l,
+                                     static_cast<double*>(dst), transpose ? 1 : 0, cancel)
+                        : launch_pdl(copy_small_kernel<float>, dim3((n + 255) / 256), dim3(256), (size_t)0, st, src, l,
+                                     static_cast<float*>(dst), transpose ? 1 : 0, cancel);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace corutv
