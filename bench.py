@@ -240,7 +240,7 @@ def rel_error(A, out):
     return float(torch.linalg.norm(A.double() - approx) / torch.linalg.norm(A.double()))
 
 
-def time_factor(ctx, A, k, p, q, prec, steps, warmup, world, profile=False, d_mode=0):
+def time_factor(ctx, A, k, p, q, prec, steps, warmup, world, profile=False, d_mode=0, t_lower=0):
     """Device-timed steps of corutv_factor with outputs preallocated."""
     import torch
     from paper_1906_04572_gb300 import corutv
@@ -251,7 +251,8 @@ def time_factor(ctx, A, k, p, q, prec, steps, warmup, world, profile=False, d_mo
     T = torch.empty((ell, ell), device=A.device, dtype=A.dtype)
     perm = torch.empty(ell, device=A.device, dtype=torch.int32)
     for w in range(warmup):
-        corutv.corutv_factor(ctx.handle, A, k, p, q, prec, U, T, V, perm, seed=0, stream=w, d_mode=d_mode)
+        corutv.corutv_factor(ctx.handle, A, k, p, q, prec, U, T, V, perm, seed=0, stream=w, d_mode=d_mode,
+                             t_lower=t_lower)
     ctx.sync()
     if profile:
         corutv.corutv_profile_enable(ctx.handle, True)
@@ -260,7 +261,8 @@ def time_factor(ctx, A, k, p, q, prec, steps, warmup, world, profile=False, d_mo
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for s in range(steps):
-        corutv.corutv_factor(ctx.handle, A, k, p, q, prec, U, T, V, perm, seed=0, stream=s, d_mode=d_mode)
+        corutv.corutv_factor(ctx.handle, A, k, p, q, prec, U, T, V, perm, seed=0, stream=s, d_mode=d_mode,
+                             t_lower=t_lower)
     e1.record()
     torch.cuda.synchronize()
     barrier(world)
@@ -578,6 +580,14 @@ def run_ours(args):
                            "e_rel": rel_error(A, out1)}
         sp["e_rel_exact_d"] = err
         extra["single_pass"] = sp
+        # the m < n variant with a lower triangular T (Sec. 3): the same matrix
+        # transposed (n x m, wide), Algorithm 1 on its transpose
+        At = A.t().contiguous()
+        ms_l, out_l, _ = time_factor(ctx, At, k, p, q, prec, max(3, args.steps // 2), 2, world, t_lower=1)
+        extra["lower_t"] = {"workload": f"{n}x{m} (the same matrix transposed)", "ms": ms_l,
+                            "tflops": flops / (ms_l / 1e3) / 1e12, "e_rel": rel_error(At, out_l),
+                            "t_lower_triangular": bool(torch.all(torch.triu(out_l["T"], 1) == 0).item())}
+        del At
         if args.c3:
             extra["c3"] = c3_line(ctx, device, ("bf16", "tf32", "f32"), 3)
 
