@@ -952,6 +952,96 @@ cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, in
                       smem_q, st, static_cast<const double*>(work), (int)ell, qt, cancel);
 }
 
+// The same product for FP32 arithmetic and ell <= 64 with one thread per row
+// of Q1, the row held in registers: each reflector is a dot product and an
+// update of register values against v_j broadcast from shared memory (four
+// v entries per 128-bit load), with no shuffle and no shared-memory round
+// trip on the row's chain. The 64 columns are taken in four blocks of 16 so
+// that reflector j touches only the blocks at or after j's own.
+constexpr int kRrThreads = 128;   // rows per block
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(kRrThreads)
+apply_refl_rows_kernel(const TI* x, int64_t ldx, int64_t rows, int ell, const double* refl, TO* out, int64_t ldo,
+                       int out_panel, const int* cancel) {
+    constexpr int kE = 64, kLdv = 64;  // v_j at Vs + j * kLdv (16-byte aligned columns)
+    pdl_wait();
+    if (cancel && *cancel) return;
+    __shared__ __align__(16) float Vs[kE * kLdv];
+    __shared__ float tau[kE], sgn[kE];
+    __shared__ float Os[kRrThreads * 33];        // 32 columns of the rows, for coalesced row-major stores
+    const int tid = threadIdx.x;
+    // v_j below the diagonal, zero elsewhere (including the padding), as FP32
+    for (int e = tid; e < kE * kLdv; e += kRrThreads) {
+        const int j = e / kLdv, i = e - j * kLdv;
+        Vs[e] = (j < ell && i > j && i < ell) ? (float)refl[(size_t)j * ell + i] : 0.f;
+    }
+    for (int j = tid; j < kE; j += kRrThreads) {
+        tau[j] = j < ell ? (float)refl[(size_t)ell * ell + j] : 0.f;
+        sgn[j] = j < ell ? (float)refl[(size_t)ell * ell + ell + j] : 0.f;
+    }
+    const int64_t i0 = (int64_t)blockIdx.x * kRrThreads + tid;
+    const bool live = i0 < rows;
+    float u[kE];
+#pragma unroll
+    for (int i = 0; i < kE; ++i) u[i] = (live && i < ell) ? (float)x[(int64_t)i * ldx + i0] : 0.f;
+    __syncthreads();
+    pdl_trigger();
+#pragma unroll
+    for (int jb = 0; jb < kE / 16; ++jb) {
+        const int jend = min(ell, 16 * (jb + 1));
+        for (int j = 16 * jb; j < jend; ++j) {
+            const float4* v4 = reinterpret_cast<const float4*>(Vs + j * kLdv);
+            // v_j^T u with v_j[j] = 1: u[j] plus the entries below (zero in Vs above j)
+            float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+#pragma unroll
+            for (int c = 4 * jb; c < kE / 4; ++c) {
+                const float4 v = v4[c];
+                d0 = fmaf(v.x, u[4 * c + 0], d0);
+                d1 = fmaf(v.y, u[4 * c + 1], d1);
+                d2 = fmaf(v.z, u[4 * c + 2], d2);
+                d3 = fmaf(v.w, u[4 * c + 3], d3);
+            }
+            float uj = 0.f;  // u[j] (a register of this block of 16, picked by value)
+#pragma unroll
+            for (int i = 16 * jb; i < 16 * (jb + 1); ++i) uj = (i == j) ? u[i] : uj;
+            const float f = tau[j] * (uj + ((d0 + d1) + (d2 + d3)));
+#pragma unroll
+            for (int i = 16 * jb; i < 16 * (jb + 1); ++i)
+                if (i == j) u[i] -= f;
+#pragma unroll
+            for (int c = 4 * jb; c < kE / 4; ++c) {
+                const float4 v = v4[c];
+                u[4 * c + 0] = fmaf(-f, v.x, u[4 * c + 0]);
+                u[4 * c + 1] = fmaf(-f, v.y, u[4 * c + 1]);
+                u[4 * c + 2] = fmaf(-f, v.z, u[4 * c + 2]);
+                u[4 * c + 3] = fmaf(-f, v.w, u[4 * c + 3]);
+            }
+        }
+    }
+    if (out_panel) {
+        if (live)
+#pragma unroll
+            for (int i = 0; i < kE; ++i)
+                if (i < ell) out[(int64_t)i * ldo + i0] = (TO)(u[i] * sgn[i]);
+        return;
+    }
+    // row-major, 32 columns at a time: consecutive threads store consecutive
+    // entries of one row
+    const int64_t r0 = (int64_t)blockIdx.x * kRrThreads;
+#pragma unroll
+    for (int cb = 0; cb < kE; cb += 32) {
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) Os[tid * 33 + i] = u[cb + i] * sgn[cb + i];
+        __syncthreads();
+        const int nc = min(32, ell - cb);
+        for (int e = tid; e < kRrThreads * nc; e += kRrThreads) {
+            const int r = e / nc, i = e - r * nc;
+            if (r0 + r < rows) out[(r0 + r) * ldo + cb + i] = (TO)Os[r * 33 + i];
+        }
+    }
+}
+
 cudaError_t launch_apply_reflectors(const void* q1, ElemType tp, int64_t ldq, int64_t rows, int64_t ell,
                                     const double* refl, void* out, ElemType tout, int64_t ldo, bool out_panel,
                                     const int* cancel, cudaStream_t st) {
@@ -966,6 +1056,12 @@ cudaError_t launch_apply_reflectors(const void* q1, ElemType tp, int64_t ldq, in
         return launch_pdl(kern, dim3(blocks), dim3(kTrsmThreads), smem, st, xin, ldq, rows, l, refl, outp, ldo,
                           out_panel ? 1 : 0, cancel);
     };
+    if (tp == T_F32 && tout == T_F32 && ell <= 64) {  // the register-row form
+        count_launch();
+        return launch_pdl(apply_refl_rows_kernel<float, float>, dim3((unsigned)((rows + kRrThreads - 1) / kRrThreads)),
+                          dim3(kRrThreads), (size_t)0, st, static_cast<const float*>(q1), ldq, rows, l, refl,
+                          static_cast<float*>(out), ldo, out_panel ? 1 : 0, cancel);
+    }
     if (tp == T_F32 && tout == T_F32)
         return go(apply_refl_kernel<float, float, float>, sizeof(float), static_cast<const float*>(q1),
                   static_cast<float*>(out));
