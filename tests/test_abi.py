@@ -52,3 +52,36 @@ def test_create_fails_loudly_without_gpu(lib):
 def test_library_is_sm103a_only():
     from paper_1906_04572_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """corutv_opts and corutv_request as the C compiler lays them out (size and
+    every field's offset, from a program built against include/corutv.h)
+    equal the ctypes structures the binding passes across the boundary."""
+    import shutil
+    import subprocess
+    from paper_1906_04572_gb300 import corutv
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"corutv_opts": corutv.Opts, "corutv_request": corutv.Request}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "corutv.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        cname, field, val = line.split()
+        got[(cname, field)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
