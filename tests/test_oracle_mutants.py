@@ -89,3 +89,50 @@ def test_planted_mistake_is_caught(oracle_lib, tmp_path, name, orig, mut):
                 break
     assert caught, f"no pin detects the planted mistake {name}"
     os.remove(path)
+
+
+# Planted mistakes in the lower-triangular-T variant (a Python composition of
+# the C oracle): each returns what a plausible slip in corutv_lower would, and
+# the lower-variant pins must reject it.
+def _lower_mutants(orc):
+    import numpy as np
+
+    def base(a, k, p, q, psi=None, seed=0, stream=0):
+        return orc.corutv(np.ascontiguousarray(a.T), k, p, q, psi=psi, seed=seed, stream=stream)
+
+    def t_not_transposed(*args, **kw):
+        o = base(*args, **kw)
+        return {"U": o["V"], "T": o["T"], "V": o["U"], "perm": o["perm"]}
+
+    def factors_not_swapped(*args, **kw):
+        o = base(*args, **kw)
+        return {"U": o["U"], "T": np.ascontiguousarray(o["T"].T), "V": o["V"], "perm": o["perm"]}
+
+    def u_without_permutation(*args, **kw):
+        o = base(*args, **kw)
+        return {"U": o["Q2"], "T": np.ascontiguousarray(o["T"].T), "V": o["U"], "perm": o["perm"]}
+
+    def run_on_a_not_at(a, k, p, q, psi=None, seed=0, stream=0):
+        o = orc.corutv(a, k, p, q, psi=None, seed=seed, stream=stream)
+        return {"U": o["U"], "T": np.ascontiguousarray(o["T"].T), "V": o["V"], "perm": o["perm"]}
+
+    return {"t_not_transposed": t_not_transposed, "factors_not_swapped": factors_not_swapped,
+            "u_without_permutation": u_without_permutation, "run_on_a_not_at": run_on_a_not_at}
+
+
+@pytest.mark.parametrize("name", ["t_not_transposed", "factors_not_swapped", "u_without_permutation",
+                                  "run_on_a_not_at"])
+def test_planted_mistake_in_lower_variant_is_caught(oracle_lib, name):
+    import types
+    fake = types.SimpleNamespace(**{k: getattr(oracle_lib, k) for k in dir(oracle_lib) if not k.startswith("__")})
+    fake.corutv_lower = _lower_mutants(oracle_lib)[name]
+    failed = 0
+    checks = [lambda: pins.test_lower_variant_reproduces_exact_rank(fake, 200, 300, 8, 8, 4, 1),
+              lambda: pins.test_lower_variant_reproduces_exact_rank(fake, 120, 400, 5, 10, 10, 2),
+              lambda: pins.test_lower_variant_error_versus_truncated_svd(fake, 2)]
+    for check in checks:
+        try:
+            check()
+        except (AssertionError, ValueError):
+            failed += 1
+    assert failed > 0, name
