@@ -177,7 +177,7 @@ struct FactorPlan {
     int dmode;        // 0: D = Q1^T A Q2 (eq. 7, a third pass); 1: the single-pass core (= R2^T)
     int64_t ldc32;    // row stride of that padded FP32 copy of A
     int64_t seg;      // columns per segment of the bf16 copy of A ([A_h | A_m | A_l] when split)
-    int sp_ax, sp_aty, sp_w, gs_m, gs_n;
+    int sp_ax, sp_aty, gs_m, gs_n;  // SIMT split counts (sizing the partial buffers)
     int64_t part_elems;
     int num_sms;
 };
@@ -239,7 +239,6 @@ corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64
     pl.tp = (ta == T_F32 && prec != CORUTV_P_F64) ? T_F32 : T_F64;
     pl.sp_ax = gemm_simt_splits(pl.m, pl.n, num_sms);
     pl.sp_aty = gemm_simt_splits(pl.n, pl.m, num_sms);
-    pl.sp_w = pl.sp_ax;
     pl.gs_m = gemm_simt_splits(pl.ell, m, num_sms);
     pl.gs_n = gemm_simt_splits(pl.ell, n, num_sms);
     int64_t part = std::max((int64_t)pl.sp_ax * pl.ellp * pl.ldm, (int64_t)pl.sp_aty * pl.ellp * pl.ldn);
@@ -930,7 +929,6 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
     pl.tp = T_F64;
     pl.sp_ax = gemm_simt_splits(m, n, ctx->num_sms);
     pl.sp_aty = gemm_simt_splits(n, m, ctx->num_sms);
-    pl.sp_w = pl.sp_ax;
     pl.gs_m = pl.gs_n = 1;
     pl.part_elems = std::max((int64_t)pl.sp_ax * pl.ellp * pl.ldm, (int64_t)pl.sp_aty * pl.ellp * pl.ldn);
     if (pl.tensor) pl.part_elems = std::max(pl.part_elems, tc_partial_elems(m, n, pl.ellp, pl.ldm, pl.ldn, ctx->num_sms));
