@@ -610,7 +610,10 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": sampler.summary(),
-            "gpu_launches": int(prof["launches"]),
+            # kernels of this library launched in the timed region: the profiled pass
+            # counts them (a fixed number per factorisation) over its psteps steps
+            "gpu_launches": int(round(prof["launches"] / psteps)) * args.steps,
+            "gpu_launches_per_step": int(round(prof["launches"] / psteps)),
             "peaks": {"source": peaks_kind, "hbm_gbs": peaks["hbm_gbs"], "bf16_tflops": peaks.get("bf16_tflops")},
             **extra,
         }
