@@ -14,7 +14,9 @@
 // slice) then tells which CTA stored the last cluster sum of its slice; that
 // CTA adds the clusters' slices in cluster order and writes G. Nobody waits
 // on another CTA outside its cluster, the counters return to zero, and the
-// sums never depend on arrival order.
+// sums never depend on arrival order. A panel whose tensor-core product left
+// its split tiles as pieces is completed here: the pieces of each row are
+// added as it is staged (and, on request, written back into the panel).
 #include <cooperative_groups.h>
 
 #include <algorithm>

@@ -18,6 +18,9 @@
 // in `part`; each finished piece bumps the tile's counter, and the CTA that
 // finishes last adds the tile's pieces in piece order (in FP32) and writes
 // the output, so the sum never depends on which CTA happened to finish last.
+// When the caller asks for the pieces (TcPieces), the counting and adding
+// are left out: the next kernel that reads the panel adds the same pieces in
+// the same order.
 //
 // Warp roles (192 threads): warps 0-3 read the accumulator out of tensor
 // memory (warp w owns TMEM lanes 32w..32w+31 = rows of the tile), warp 4 is
