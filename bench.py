@@ -2,12 +2,19 @@
 
 One step = one complete factorisation (Gaussian test matrix, 2q+2 sketch /
 power products with their thin QRs, the projection D = Q1^T A Q2, the pivoted
-QR of D and the assembly of U, T, V) of the 8000 x 6000 power-method workload
-(k = 50, ell = 60, q = 2, sigma_i = i^-2 for i <= 200 plus N(0, 1e-4^2) noise,
-Haar factors), synthetic, inputs resident in HBM.
+QR of D and the assembly of U, T, V). The default workload is the largest
+dense one: 20000 x 20000, sigma_i = exp(-i/20), k = 100, ell = 110, q = 2,
+with the mixed-precision arithmetic it is stated with -- bf16 sketch / power
+products on the tensor cores with FP32 accumulation, the projection D
+FP32-accurate, the Gram Cholesky factorisations and the pivoted QR of D in
+FP64 -- synthetic (seeded Haar factors, the product formed on the device),
+inputs resident in HBM. Secondary lines: the same matrix on the plain FP64
+path (equal error) and with TF32 / FP32 sketches; the 8000 x 6000 workload
+at FP32 and FP64 (q = 1, 2); single-call latency of the 1000 x 1000 FP64
+workload; the 1024-request serving stream; ALM-CoRUTV on 4800 x 1200.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c2|c1|c3] [--prec f32|tf32|bf16|f64]
+                  [--workload c3|c2|c1] [--prec bf16|tf32|f32|f64]
 
 Prints one JSON line (rank 0). Under torchrun each rank factorises its own
 matrix (independent replicas, weak scaling); value = all ranks' flops / the
@@ -175,6 +182,20 @@ def max_over_ranks(x: float, world: int, device) -> float:
 # ---------------------------------------------------------------------------
 # reference arm: the FP64 CPU oracle on the host cores
 # ---------------------------------------------------------------------------
+def host_rows_of(workload: str, rows: int, seed: int = 0):
+    """The first `rows` rows of the workload's matrix, formed on the host
+    from the same seeded factors as the device copy (FP64)."""
+    import synth
+    if workload == "c3":
+        u, s_, v = synth.spectrum_factors(20000, 20000, synth.c3_sigma(20000), seed=seed)
+        return np.ascontiguousarray((u[:rows] * s_) @ v.T)
+    return np.ascontiguousarray(make_matrix(workload, seed).a[:rows])
+
+
+REF_ROWS = {"c1": 1000, "c2": 1000, "c3": 200}   # per step of the reference arm (a few seconds each)
+CPU_ROWS = {"c1": 1000, "c2": 2000, "c3": 400}   # the cpu_baseline sample of our arm (10-30 s)
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
@@ -183,12 +204,12 @@ def run_reference(args):
     import synth
     oracle.build()
     wl = WORKLOADS[args.workload]
-    rows = min(wl["m"], 2000)
-    f = make_matrix(args.workload, seed=0)
-    a = np.ascontiguousarray(f.a[:rows])
+    rows = REF_ROWS[args.workload]
+    a = host_rows_of(args.workload, rows)
+    n = a.shape[1]
     ell = wl["k"] + wl["p"]
-    psi = synth.gaussian_psi(f.n, ell, seed=0)
-    flops = flops_per_factor(rows, f.n, ell, wl["q"])
+    psi = synth.gaussian_psi(n, ell, seed=0)
+    flops = flops_per_factor(rows, n, ell, wl["q"])
     for _ in range(args.warmup):
         oracle.corutv(a, wl["k"], wl["p"], wl["q"], psi)
     times = []
@@ -214,21 +235,24 @@ def run_reference(args):
     return 0
 
 
-def cpu_baseline_sample(args, f, ell):
-    """The oracle as it stands, on a bounded sample of the workload."""
+def cpu_baseline_sample(args, host_rows, A, ell):
+    """The oracle as it stands, on a bounded sample of the workload: its
+    first rows, one full factorisation."""
     import oracle
     import synth
     oracle.build()
     wl = WORKLOADS[args.workload]
-    rows = min(f.m, 2000)
-    a = np.ascontiguousarray(f.a[:rows])
-    psi = synth.gaussian_psi(f.n, ell, seed=0)
+    rows = CPU_ROWS[args.workload]
+    a = (np.ascontiguousarray(host_rows[:rows]) if host_rows is not None
+         else host_rows_of(args.workload, rows))
+    n = a.shape[1]
+    psi = synth.gaussian_psi(n, ell, seed=0)
     t0 = time.perf_counter()
     oracle.corutv(a, wl["k"], wl["p"], wl["q"], psi)
     sec = time.perf_counter() - t0
-    return {"value": flops_per_factor(rows, f.n, ell, wl["q"]) / sec / 1e12, "unit": "TFLOP/s",
+    return {"value": flops_per_factor(rows, n, ell, wl["q"]) / sec / 1e12, "unit": "TFLOP/s",
             "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"one FP64 oracle factorisation of the first {rows} of {f.m} rows ({sec:.2f} s)"}
+            "sample": f"one FP64 oracle factorisation of the first {rows} of {wl['m']} rows ({sec:.2f} s)"}
 
 
 # ---------------------------------------------------------------------------
@@ -425,29 +449,103 @@ def rpca_c4(ctx, device, prec="f32"):
             "rel_err_L": err, "prec": prec}
 
 
-def c3_line(ctx, device, precs, steps):
-    """The 20000 x 20000 mixed-precision workload (sigma_i = exp(-i/20),
-    k = 100, ell = 110, q = 2), FP32 input formed on the device from the
-    seeded Haar factors; a few timed factorisations per sketch precision."""
+def c3_matrix(device, seed=0):
+    """The 20000 x 20000 mixed-precision workload's matrix (sigma_i =
+    exp(-i/20), seeded Haar factors), FP32, formed on the device."""
     import torch
     import synth
     m = n = 20000
-    sig = synth.c3_sigma(n)
-    u, s_, v = synth.spectrum_factors(m, n, sig, seed=0)
+    u, s_, v = synth.spectrum_factors(m, n, synth.c3_sigma(n), seed=seed)
     A = (torch.from_numpy(u * s_).to(device) @ torch.from_numpy(v).to(device).T).float().contiguous()
-    del u, v
-    flops = flops_per_factor(m, n, 110, 2)
+    return A
+
+
+def c2_lines(ctx, device, steps):
+    """The 8000 x 6000 power-method workload at its stated arithmetic (FP32
+    and FP64 sketches, q = 1 and q = 2; k = 50, ell = 60) and, for context,
+    with tensor-core sketches: device time per factorisation, TFLOP/s and
+    the reconstruction error."""
+    import torch
+    import synth
     res = {}
-    for prec in precs:
-        ms, out, _ = time_factor(ctx, A, 100, 10, 2, prec, steps, 1, 1)
-        appr = (out["U"].double() @ out["T"].double()) @ out["V"].double().T
-        err = float(torch.linalg.norm(A.double() - appr) / torch.linalg.norm(A.double()))
-        del appr
-        res[prec] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, "e_rel": err}
-    torch.cuda.synchronize()
-    del A
-    torch.cuda.empty_cache()
-    return {"workload": "c3_20000x20000_k100_l110_q2", "steps": steps, **res}
+    for q in (1, 2):
+        f = synth.factor_c2(q=q, seed=0)
+        m, n = f.m, f.n
+        flops = flops_per_factor(m, n, 60, q)
+        for prec in ("f64", "f32", "bf16", "tf32"):
+            dt = torch.float64 if prec == "f64" else torch.float32
+            A = torch.from_numpy(f.a).to(device=device, dtype=dt)
+            st = max(2, steps // (8 if prec == "f64" else 2))
+            ms, out, _ = time_factor(ctx, A, 50, 10, q, prec, st, 3, 1)
+            res[f"q{q}_{prec}"] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, "solves_per_s": 1e3 / ms,
+                                   "e_rel": rel_error(A, out), "steps": st}
+            del A, out
+    res["workload"] = "c2_8000x6000_k50_l60 (sigma_i = i^-2, i <= 200, + N(0, 1e-4^2))"
+    return res
+
+
+def c1_latency(ctx, device, reps):
+    """The 1000 x 1000 exact-rank-10 workload (FP64, ell = 15, q = 0):
+    latency of single synchronous factorisations (launch- and latency-bound)."""
+    import torch
+    import synth
+    f = synth.factor_c1(seed=0)
+    A = torch.from_numpy(f.a).to(device=device, dtype=torch.float64)
+    lat = latency_single(ctx, A, f.k, f.p, f.q, "f64", reps)
+    ms, out, _ = time_factor(ctx, A, f.k, f.p, f.q, "f64", 50, 5, 1)
+    lat.update({"workload": "c1_1000x1000_k10_l15_q0", "prec": "f64", "device_ms_back_to_back": ms,
+                "e_rel": rel_error(A, out)})
+    return lat
+
+
+def sketch_roofline(prof, psteps, m, n, ell, prec, peaks, peaks_kind, workload):
+    """Roofline line of the dominant kernel, the sketch / power products
+    (eqs. 4, 5): algorithmic bytes per launch (the A copy read once, s bytes
+    per element, plus the two panels) over the mean launch time that CUDA
+    events around every launch measured in the profiled pass."""
+    from paper_1906_04572_gb300 import corutv
+    sk_ms, sk_n = prof[corutv.STAGE_SKETCH]
+    per_launch_ms = sk_ms / max(sk_n, 1)
+    s_a = {"f64": 8, "f32": 4, "tf32": 4, "bf16": 2}[prec]
+    bytes_per_launch = m * n * s_a + (m + n) * ell * s_a
+    flops_per_launch = 2.0 * m * n * ell
+    gbs = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+    tfs = flops_per_launch / (per_launch_ms / 1e3) / 1e12
+    if prec in ("f32", "f64") and ALU_PEAK_TFLOPS[prec] < peaks["hbm_gbs"] * 1e9 * (flops_per_launch / bytes_per_launch) / 1e12:
+        alu = ALU_PEAK_TFLOPS[prec]
+        roof = {"bound": "alu", "achieved": tfs, "peak": alu, "unit": "TFLOP/s", "frac": tfs / alu,
+                "peak_source": "derived: 152 SMs x FMA/clk x 2 x 2.07 GHz"}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / peaks["hbm_gbs"], "peak_source": peaks_kind + " (burst copy)"}
+    roof.update({"kernel": "sketch_tc_kernel: A X / A^T Y (eqs. 4, 5)" if prec in ("bf16", "tf32")
+                 else "gemm_simt_kernel: A X / A^T Y (eqs. 4, 5)",
+                 "traffic": SKETCH_TRAFFIC_BYTES.get((workload, prec)),
+                 "bytes_per_launch": bytes_per_launch, "launch_ms": per_launch_ms, "launches_timed": sk_n})
+    if prec in ("bf16", "tf32"):
+        tpk = peaks["bf16_tflops"] * (1.0 if prec == "bf16" else TF32_OF_BF16)
+        roof["tensor"] = {"achieved_tflops": tfs, "peak_tflops": tpk, "frac_raw": tfs / tpk,
+                          "arithmetic_intensity": flops_per_launch / bytes_per_launch,
+                          "peak_source": peaks_kind + (" (tf32 = bf16 x 0.5, nominal ratio)" if prec == "tf32" else "")}
+    return roof
+
+
+def step_bytes(m, n, q, prec, input_es):
+    """HBM bytes of one factorisation: the algorithmic budget (the passes over
+    A at the sketch precision, the projection at the input precision, one
+    cast for bf16) and what this implementation moves (its bf16 cast writes
+    the three exact splits of A, which the projection reads)."""
+    passes = 2 * q + 2
+    if prec == "bf16" and input_es == 4:
+        alg = 4 * m * n + 2 * m * n + passes * 2 * m * n + 4 * m * n
+        impl = 4 * m * n + 6 * m * n + passes * 2 * m * n + 6 * m * n
+    elif prec == "tf32":
+        alg = (passes + 1) * 4 * m * n
+        impl = 4 * m * n + (4 + 6) * m * n + passes * 4 * m * n + 6 * m * n
+    else:
+        es = 8 if prec == "f64" else 4
+        alg = impl = (passes + 1) * es * m * n
+    return alg, impl
 
 
 def run_ours(args):
@@ -463,11 +561,16 @@ def run_ours(args):
     k, p, q = wl["k"], wl["p"], wl["q"]
     ell = k + p
     peaks, peaks_kind = load_peaks()
-    f = make_matrix(args.workload, seed=rank)
-    m, n = f.m, f.n
     prec = args.prec
     dt = torch.float64 if prec == "f64" else torch.float32
-    A = torch.from_numpy(f.a).to(device=device, dtype=dt)
+    if args.workload == "c3":
+        A = c3_matrix(device, seed=rank).to(dt)
+        host_rows = None
+    else:
+        f = make_matrix(args.workload, seed=rank)
+        A = torch.from_numpy(f.a).to(device=device, dtype=dt)
+        host_rows = f.a
+    m, n = A.shape
     flops = flops_per_factor(m, n, ell, q)
     ctx = Context(local)
     corutv.corutv_set_stream(ctx.handle, torch.cuda.current_stream(device).cuda_stream)
@@ -484,70 +587,59 @@ def run_ours(args):
     ms_max = max_over_ranks(ms, world, device)
     value = world * flops / (ms_max / 1e3) / 1e12
     err = rel_error(A, out)
+    del out
     # a second, profiled pass: CUDA events around every stage (the sketch
     # launches among them) for the stage split and the roofline figure
-    psteps = max(3, args.steps // 2)
+    psteps = max(3, min(args.steps // 2, 10))
     ms_prof, _, prof = time_factor(ctx, A, k, p, q, prec, psteps, 1, world, profile=True)
-
-    # dominant kernel: the sketch / power products (eqs. 4, 5)
-    sk_ms, sk_n = prof[corutv.STAGE_SKETCH]
-    per_launch_ms = sk_ms / max(sk_n, 1)
-    s_a = {"f64": 8, "f32": 4, "tf32": 4, "bf16": 2}[prec]
-    bytes_per_launch = m * n * s_a + (m + n) * ell * s_a
-    flops_per_launch = 2.0 * m * n * ell
-    gbs = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
-    tfs = flops_per_launch / (per_launch_ms / 1e3) / 1e12
-    if prec in ("f32", "f64"):
-        ai = flops_per_launch / bytes_per_launch
-        alu = ALU_PEAK_TFLOPS[prec]
-        if alu < peaks["hbm_gbs"] * 1e9 * ai / 1e12:
-            roof = {"bound": "alu", "achieved": tfs, "peak": alu, "unit": "TFLOP/s", "frac": tfs / alu,
-                    "peak_source": "derived: 152 SMs x FMA/clk x 2 x 2.07 GHz"}
-        else:
-            roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": gbs / peaks["hbm_gbs"], "peak_source": peaks_kind}
-    else:
-        roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": gbs / peaks["hbm_gbs"], "peak_source": peaks_kind}
-    roof.update({"kernel": "sketch products A X / A^T Y (eqs. 4, 5)",
-                 "traffic": SKETCH_TRAFFIC_BYTES.get((args.workload, prec)),
-                 "bytes_per_launch": bytes_per_launch, "launch_ms": per_launch_ms,
-                 "launches_timed": sk_n})
-    if prec in ("bf16", "tf32"):
-        # the raw fraction of the tensor-core peak for this operand type, beside the
-        # attainable (HBM) roofline above: the products' arithmetic intensity is only
-        # 2 ell / s flop per byte of A
-        tpk = peaks["bf16_tflops"] * (1.0 if prec == "bf16" else TF32_OF_BF16)
-        roof["tensor"] = {"achieved_tflops": tfs, "peak_tflops": tpk, "frac_raw": tfs / tpk,
-                          "arithmetic_intensity": 2.0 * m * n * ell / bytes_per_launch,
-                          "peak_source": peaks_kind + (" (tf32 = bf16 x 0.5, nominal ratio)" if prec == "tf32" else "")}
-
+    roof = sketch_roofline(prof, psteps, m, n, ell, prec, peaks, peaks_kind, args.workload)
+    alg_b, impl_b = step_bytes(m, n, q, prec, A.element_size())
+    whole = {"algorithmic_bytes": alg_b, "implementation_bytes": impl_b,
+             "achieved_gbs": alg_b / (ms_max / 1e3) / 1e9,
+             "frac": alg_b / (ms_max / 1e3) / 1e9 / peaks["hbm_gbs"],
+             "frac_of_moved_bytes": impl_b / (ms_max / 1e3) / 1e9 / peaks["hbm_gbs"],
+             "tensor_frac_raw": (value / peaks["bf16_tflops"] if prec == "bf16" else None),
+             "what": "whole factorisation: algorithmic HBM bytes / device time per step, of the measured copy "
+                     "bandwidth (" + peaks_kind + ")"}
+    roof["whole_step"] = whole
     stages = {name: {"ms_per_step": prof[i][0] / psteps, "intervals": prof[i][1]}
               for i, name in enumerate(["sketch", "project", "orth", "qrcp", "factor"])}
     stages["profiled_ms_per_step"] = ms_prof
+    stages["share_of_profiled"] = {name: stages[name]["ms_per_step"] / ms_prof
+                                   for name in ("sketch", "project", "orth", "qrcp")}
 
-    # FP64 path at the same workload (the comparison the metric names)
+    # the FP64 path on the same matrix: the comparison the metric names
     fp64 = None
     if not args.skip_fp64 and prec != "f64":
-        A64 = torch.from_numpy(f.a).to(device=device, dtype=torch.float64)
-        ms64, out64, _ = time_factor(ctx, A64, k, p, q, "f64", max(2, args.steps // 10), 1, world)
+        A64 = A.double()
+        st64 = 2 if args.workload == "c3" else max(2, args.steps // 10)
+        ms64, out64, _ = time_factor(ctx, A64, k, p, q, "f64", st64, 1, world)
         err64 = rel_error(A64, out64)
         fp64 = {"tflops": flops / (ms64 / 1e3) / 1e12, "solves_per_s": 1e3 / ms64, "ms_per_step": ms64,
-                "e_rel": err64}
-        del A64
+                "e_rel": err64, "steps": st64}
+        del A64, out64
+        torch.cuda.empty_cache()
+    others = {}
+    if not args.no_extra and prec in ("bf16", "tf32"):
+        for op in ("tf32", "f32") if prec == "bf16" else ("bf16", "f32"):
+            st = 3 if op == "f32" else max(3, args.steps // 4)
+            ms_o, out_o, _ = time_factor(ctx, A, k, p, q, op, st, 1, world)
+            others[op] = {"ms": ms_o, "tflops": flops / (ms_o / 1e3) / 1e12, "e_rel": rel_error(A, out_o),
+                          "steps": st}
+            del out_o
 
     # end to end through the C ABI with host (pinned) buffers
     e2e = None
     if not args.no_e2e:
-        hA = torch.from_numpy(f.a).to(dtype=dt).pin_memory()
+        hA = A.cpu().pin_memory()
         hU = torch.empty((m, ell), dtype=dt).pin_memory()
         hV = torch.empty((n, ell), dtype=dt).pin_memory()
         hT = torch.empty((ell, ell), dtype=dt).pin_memory()
         hP = torch.empty(ell, dtype=torch.int32).pin_memory()
         npA, npU, npV, npT, npP = (x.numpy() for x in (hA, hU, hV, hT, hP))
-        for w in range(args.warmup):
+        for w in range(2):
             corutv.corutv_factor(ctx.handle, npA, k, p, q, prec, npU, npT, npV, npP, stream=w)
-        e2e_steps = max(3, min(args.steps, 20))
+        e2e_steps = max(3, min(args.steps, 10))
         barrier(world)
         t0 = time.perf_counter()
         for s in range(e2e_steps):
@@ -559,37 +651,37 @@ def run_ours(args):
                "h2d_bytes_per_step": m * n * es,
                "d2h_bytes_per_step": (m * ell + n * ell + ell * ell) * es + ell * 4,
                "ms_per_step": sec * 1e3, "steps": e2e_steps}
+        del hA, npA
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline_sample(args, f, ell)
+        cpu = cpu_baseline_sample(args, host_rows, A, ell)
 
-    latency = latency_single(ctx, A, k, p, q, prec, 30)
+    latency = latency_single(ctx, A, k, p, q, prec, 10 if args.workload == "c3" else 30)
     extra = {}
     if not args.no_extra:
-        extra["serving"] = serving_c5(local, args.serve_requests, args.serve_rate, prec if prec != "f64" else "f32",
-                                      8)
+        extra["c1_latency"] = c1_latency(ctx, device, 50)
+        extra["c2"] = c2_lines(ctx, device, args.steps)
+        extra["serving"] = serving_c5(local, args.serve_requests, args.serve_rate, "bf16", 8)
         extra["serving"]["capacity_vs_fp64"] = serving_capacity(local, args.serve_capacity, 8)
         extra["rpca"] = rpca_c4(ctx, device)
         # the single-pass core (Sec. 3.1, d_mode 1): 2q+2 passes over A instead of 2q+3
         sp = {}
         for sp_prec in (("bf16", "tf32") if prec in ("bf16", "tf32") else (prec,)):
-            ms1, out1, _ = time_factor(ctx, A, k, p, q, sp_prec, max(3, args.steps // 2), 2, world, d_mode=1)
+            ms1, out1, _ = time_factor(ctx, A, k, p, q, sp_prec, max(3, args.steps // 4), 2, world, d_mode=1)
             sp[sp_prec] = {"ms": ms1, "solves_per_s": 1e3 / ms1,
                            "tflops_2q2_passes": (2 * q + 2) * 2.0 * m * n * ell / (ms1 / 1e3) / 1e12,
                            "e_rel": rel_error(A, out1)}
+            del out1
         sp["e_rel_exact_d"] = err
         extra["single_pass"] = sp
-        # the m < n variant with a lower triangular T (Sec. 3): the same matrix
-        # transposed (n x m, wide), Algorithm 1 on its transpose
+        # the lower-T variant (Sec. 3, m < n): the matrix transposed, Algorithm 1 on its transpose
         At = A.t().contiguous()
-        ms_l, out_l, _ = time_factor(ctx, At, k, p, q, prec, max(3, args.steps // 2), 2, world, t_lower=1)
+        ms_l, out_l, _ = time_factor(ctx, At, k, p, q, prec, max(3, args.steps // 4), 2, world, t_lower=1)
         extra["lower_t"] = {"workload": f"{n}x{m} (the same matrix transposed)", "ms": ms_l,
                             "tflops": flops / (ms_l / 1e3) / 1e12, "e_rel": rel_error(At, out_l),
                             "t_lower_triangular": bool(torch.all(torch.triu(out_l["T"], 1) == 0).item())}
-        del At
-        if args.c3:
-            extra["c3"] = c3_line(ctx, device, ("bf16", "tf32", "f32"), 3)
+        del At, out_l
 
     if rank == 0:
         line = {
@@ -598,12 +690,17 @@ def run_ours(args):
             "vs_baseline": None, "dtype": prec, "data": "synthetic",
             "config": {"workload": wl["name"], "m": m, "n": n, "k": k, "ell": ell, "q": q,
                        "sketch_prec": prec, "input_dtype": str(dt).replace("torch.", ""),
+                       "projection": ("FP32-accurate (exact bf16 splits on the tensor cores)"
+                                      if prec in ("bf16", "tf32") else prec),
+                       "small_factorisations": "FP64 (Cholesky of the Gram matrices, pivoted QR of D)",
                        "l2": f"A is {m * n * A.element_size() / 1e6:.0f} MB, larger than the 129 MB L2",
                        "parallelism": f"replicas x{world}"},
             "solves_per_s": world * 1e3 / ms_max,
             "e_rel": err,
             "fp64_path": fp64,
             "equal_error": (None if fp64 is None else bool(err <= 1.01 * fp64["e_rel"])),
+            "speedup_vs_fp64_path": (None if fp64 is None else fp64["ms_per_step"] / ms_max),
+            "other_sketch_precisions": others or None,
             "roofline": roof,
             "latency": latency,
             "stages": stages,
@@ -631,15 +728,15 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="bf16", choices=["f32", "tf32", "bf16", "f64"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the serving, RPCA and 20000^2 lines")
-    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the secondary lines (C1 latency, C2, serving, RPCA, variants)")
+    ap.add_argument("--serve-requests", type=int, default=1024)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--c3", type=int, default=1, help="1: also time the 20000 x 20000 workload")
     ap.add_argument("--serve-capacity", type=int, default=128,
                     help="requests of the serving stream timed at once in the mixed and the FP64 form")
     args = ap.parse_args()

@@ -100,7 +100,10 @@ corutv_status corutv_destroy(corutv_ctx* ctx);
 const char* corutv_last_error(const corutv_ctx* ctx);
 
 /* Use `cuda_stream` (a cudaStream_t, may be NULL for the legacy stream) for
- * subsequent stream-ordered calls. The caller keeps the stream alive. */
+ * subsequent stream-ordered calls. The caller keeps the stream alive. Work
+ * enqueued afterwards waits (on the device, through an event) for the work
+ * already queued on the previous stream, since every call of the context
+ * shares its workspace: alternating streams never lets two calls overlap. */
 corutv_status corutv_set_stream(corutv_ctx* ctx, void* cuda_stream);
 
 /* Wait for all work enqueued on the context's stream; returns the first
@@ -159,7 +162,11 @@ typedef struct {
  * are borrowed until corutv_poll returns something other than
  * CORUTV_EPENDING. Requests are admitted in arrival order as slots and
  * workspace memory free up, and run concurrently on the device. Returns
- * CORUTV_ENOMEM only if the request could never fit the budget. */
+ * CORUTV_ENOMEM only if the request could never fit the budget.
+ * Device inputs: submit records an event on the context's stream
+ * (corutv_set_stream) and the request's work waits for it, so A and psi may
+ * still be in production on that stream when the caller submits (no host
+ * synchronisation needed). Host inputs must be complete at submit. */
 corutv_status corutv_submit(corutv_ctx* ctx, const corutv_request* req, uint64_t* ticket);
 
 /* Wait up to timeout_us (0 = do not wait, < 0 = forever) for a ticket.
@@ -208,6 +215,14 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
  * R: ell x ell upper (optional), diag(R) > 0. */
 corutv_status corutv_orth(corutv_ctx* ctx, const double* C, int64_t rows, int64_t ell, int64_t ldc,
                           double* Q, int64_t ldq, double* R);
+
+/* Failure detection of the device waits (not part of the method): enqueue on
+ * the context's stream a kernel that holds tensor memory while it waits on an
+ * mbarrier nothing arrives on, gives up after about limit_ns (0 .. 1e10),
+ * raises the device timeout status, frees the tensor memory and returns --
+ * the bounded-wait path every tcgen05 kernel of the library takes. The next
+ * corutv_sync returns CORUTV_ETIMEDOUT; the context stays usable. */
+corutv_status corutv_selftest_wait(corutv_ctx* ctx, int64_t limit_ns);
 
 /* Eq. 8: D P = Qt Rt for the ell x ell FP64 matrix D (row stride ell), one
  * thread block, FP64, Businger-Golub pivoting on recomputed column norms

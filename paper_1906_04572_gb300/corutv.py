@@ -77,6 +77,7 @@ _SIGS = {
                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
     "corutv_qrcp": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                      ctypes.c_void_p], ctypes.c_int),
+    "corutv_selftest_wait": ([ctypes.c_void_p, ctypes.c_int64], ctypes.c_int),
     "corutv_orth_noalloc": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
                              ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
 }
@@ -231,8 +232,14 @@ def corutv_rpca(ctx, M, k: int, L, S, lam=0.0, mu0=0.0, mu_bar=0.0, rho=0.0, tol
 
 def make_request(A, k, p, q, prec, U, T, V=None, perm=None, psi=None, seed=0, stream=0, d_mode=0,
                  t_lower=0) -> Request:
+    """Request descriptor; for a CUDA tensor A it remembers the torch stream
+    current now, which corutv_submit makes the context's stream so that the
+    request waits for A's producer on it."""
     m, n = A.shape
     rq = Request()
+    if _is_torch(A) and A.is_cuda:
+        import torch
+        rq._torch_stream = torch.cuda.current_stream(A.device).cuda_stream
     rq.dtype = _dtype_code(A)
     rq.A = _ptr(A).value
     rq.m, rq.n, rq.lda = m, n, _rowmajor_ld(A)
@@ -248,6 +255,9 @@ def make_request(A, k, p, q, prec, U, T, V=None, perm=None, psi=None, seed=0, st
 
 def corutv_submit(ctx, req: Request) -> int:
     t = ctypes.c_uint64(0)
+    s = getattr(req, "_torch_stream", None)
+    if s is not None:
+        _check(ctx, load().corutv_set_stream(ctx, ctypes.c_void_p(s)))
     _check(ctx, load().corutv_submit(ctx, ctypes.byref(req), ctypes.byref(t)))
     return t.value
 
@@ -294,6 +304,12 @@ def corutv_orth(ctx, C, Q, R=None) -> None:
     rows, ell = C.shape
     _use_torch_stream(ctx, C)
     _check(ctx, load().corutv_orth(ctx, _ptr(C), rows, ell, _rowmajor_ld(C), _ptr(Q), _rowmajor_ld(Q), _ptr(R)))
+
+
+def corutv_selftest_wait(ctx, limit_ns: int) -> None:
+    """Enqueue the bounded-wait probe (see the header); corutv_sync then
+    returns ETIMEDOUT."""
+    _check(ctx, load().corutv_selftest_wait(ctx, int(limit_ns)))
 
 
 def corutv_qrcp(ctx, D, Qt, Rt, perm) -> None:

@@ -573,6 +573,7 @@ struct PendingReq {
     std::chrono::steady_clock::time_point t0;
     size_t bytes;
     bool host;
+    cudaEvent_t ready = nullptr;  // device inputs: recorded on the caller's stream at submit
 };
 
 struct ReqResult {
@@ -588,6 +589,7 @@ struct corutv_ctx {
     size_t budget = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaEvent_t switch_ev = nullptr;  // orders a newly set stream after the previous one
     std::mutex call_mu;
     DeviceBuffer ws;
     int* flags = nullptr;
@@ -604,6 +606,7 @@ struct corutv_ctx {
     bool worker_started = false;
     uint64_t next_ticket = 1;
     size_t serving_bytes = 0;
+    std::vector<cudaEvent_t> ev_pool;  // events for submit-time ordering (under smu)
 };
 
 namespace {
@@ -677,8 +680,14 @@ corutv_status corutv_create(corutv_ctx** out, int device, size_t mem_budget_byte
         return fail(CORUTV_ECUDA, "cudaStreamCreate failed");
     }
     ctx->own_stream = true;
+    if (cudaEventCreateWithFlags(&ctx->switch_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return fail(CORUTV_ECUDA, "cudaEventCreate failed");
+    }
     if (cudaMalloc(&ctx->flags, sizeof(int) * FLAG_COUNT) != cudaSuccess ||
         cudaMemset(ctx->flags, 0, sizeof(int) * FLAG_COUNT) != cudaSuccess) {
+        cudaEventDestroy(ctx->switch_ev);
         cudaStreamDestroy(ctx->stream);
         delete ctx;
         return fail(CORUTV_ENOMEM, "cannot allocate the status words");
@@ -698,6 +707,8 @@ corutv_status corutv_destroy(corutv_ctx* ctx) {
         ctx->scv.notify_all();
         ctx->worker.join();
     }
+    for (auto& pr : ctx->queue)
+        if (pr.ready) cudaEventDestroy(pr.ready);
     for (auto& s : ctx->slots) {
         if (s.st) cudaStreamSynchronize(s.st);
         if (s.ws.ptr) cudaFree(s.ws.ptr);
@@ -706,9 +717,11 @@ corutv_status corutv_destroy(corutv_ctx* ctx) {
         if (s.done) cudaEventDestroy(s.done);
         if (s.st) cudaStreamDestroy(s.st);
     }
+    for (auto ev : ctx->ev_pool) cudaEventDestroy(ev);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->ws.ptr) cudaFree(ctx->ws.ptr);
     if (ctx->flags) cudaFree(ctx->flags);
+    if (ctx->switch_ev) cudaEventDestroy(ctx->switch_ev);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return CORUTV_OK;
@@ -723,12 +736,19 @@ corutv_status corutv_set_stream(corutv_ctx* ctx, void* cuda_stream) {
     CKS(check_ctx(ctx));
     std::lock_guard<std::mutex> lk(ctx->call_mu);
     DeviceGuard guard(ctx->device);
+    cudaStream_t next = static_cast<cudaStream_t>(cuda_stream);
+    if (next == ctx->stream) return CORUTV_OK;
+    // every call of the context shares its workspace and status words: work
+    // enqueued from now on, on the new stream, must not start before the work
+    // already queued on the previous stream has finished with them
+    CK(cudaEventRecord(ctx->switch_ev, ctx->stream));
+    CK(cudaStreamWaitEvent(next, ctx->switch_ev, 0));
     if (ctx->own_stream) {
-        CK(cudaStreamSynchronize(ctx->stream));
+        // released by the runtime once its queued work has completed
         CK(cudaStreamDestroy(ctx->stream));
         ctx->own_stream = false;
     }
-    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    ctx->stream = next;
     return CORUTV_OK;
 }
 
@@ -1034,6 +1054,15 @@ corutv_status corutv_orth(corutv_ctx* ctx, const double* C, int64_t rows, int64_
     return CORUTV_OK;
 }
 
+corutv_status corutv_selftest_wait(corutv_ctx* ctx, int64_t limit_ns) {
+    CKS(check_ctx(ctx));
+    if (limit_ns < 0 || limit_ns > 10000000000LL) return fail(CORUTV_EINVAL, "limit_ns must be in [0, 1e10]");
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    DeviceGuard guard(ctx->device);
+    CK(launch_wait_probe(ctx->flags, (unsigned long long)limit_ns, ctx->stream));
+    return CORUTV_OK;
+}
+
 corutv_status corutv_qrcp(corutv_ctx* ctx, const double* D, int64_t ell, double* Qt, double* Rt, int32_t* perm) {
     CKS(check_ctx(ctx));
     if (!D || !Qt || !Rt || !perm) return fail(CORUTV_EINVAL, "null pointer");
@@ -1247,6 +1276,9 @@ corutv_status launch_request(corutv_ctx* ctx, ServingSlot& s, const PendingReq& 
     const ElemType ta = r.dtype == CORUTV_F64 ? T_F64 : T_F32;
     const int es = elem_size(ta);
     const int64_t m = r.m, n = r.n, ell = pl.ell;
+    // device inputs: nothing of this request starts before the work the caller
+    // had queued on its stream when it submitted (the producer of A, psi)
+    if (pr.ready) CK(cudaStreamWaitEvent(s.st, pr.ready, 0));
     Carver cv(s.ws.ptr);
     FactorBufs b;
     carve_factor(cv, pl, b);
@@ -1356,6 +1388,8 @@ void worker_main(corutv_ctx* ctx) {
             lk.unlock();
             corutv_status st = launch_request(ctx, *pick, pr);
             lk.lock();
+            // the slot stream's wait is enqueued: the event may be recorded again
+            if (pr.ready) ctx->ev_pool.push_back(pr.ready);
             if (st != CORUTV_OK) finish_slot(ctx, *pick, st);
             progressed = true;
         }
@@ -1399,7 +1433,27 @@ extern "C" corutv_status corutv_submit(corutv_ctx* ctx, const corutv_request* re
         return fail(CORUTV_ENOMEM, "request needs %zu bytes of workspace, budget is %zu", bytes, ctx->budget);
     std::lock_guard<std::mutex> lk(ctx->smu);
     CKS(start_worker(ctx));
-    PendingReq pr{ctx->next_ticket++, *req, std::chrono::steady_clock::now(), bytes, host};
+    cudaEvent_t ready = nullptr;
+    if (!host) {
+        // mark the caller's stream (the context's stream, corutv_set_stream) at
+        // submission: the request's kernels wait for everything queued before it
+        if (!ctx->ev_pool.empty()) {
+            ready = ctx->ev_pool.back();
+            ctx->ev_pool.pop_back();
+        } else {
+            CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+        }
+        cudaError_t e;
+        {
+            std::lock_guard<std::mutex> lk2(ctx->call_mu);
+            e = cudaEventRecord(ready, ctx->stream);
+        }
+        if (e != cudaSuccess) {
+            ctx->ev_pool.push_back(ready);
+            return fail(CORUTV_ECUDA, "cudaEventRecord at submit failed: %s", cudaGetErrorString(e));
+        }
+    }
+    PendingReq pr{ctx->next_ticket++, *req, std::chrono::steady_clock::now(), bytes, host, ready};
     ReqResult rr;
     rr.t0 = pr.t0;
     ctx->results[pr.ticket] = rr;

@@ -591,6 +591,33 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
     }
 }
 
+// The bounded-wait path of the tensor-core kernels, exercised on purpose:
+// one warp allocates 32 columns of tensor memory, waits on an mbarrier that
+// nothing ever arrives on, gives up after about limit_ns, raises
+// FLAG_TIMEOUT, frees the tensor memory and returns. The context stays usable
+// and the next kernel can allocate tensor memory again.
+__global__ void __launch_bounds__(32) wait_probe_kernel(int* flags, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_holder;
+    pdl_trigger();
+    pdl_wait();
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                 "r"(32u));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    tc_fence_before();
+    __syncwarp();
+    tc_fence_after();
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0u, nullptr, limit_ns)) atomicExch(&flags[FLAG_TIMEOUT], 1);
+    tc_fence_before();
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_holder), "r"(32u));
+}
+
 __device__ __forceinline__ __nv_bfloat16 to_bf16(float v) { return __float2bfloat16_rn(v); }
 // double -> bf16 without double rounding (round to odd through float).
 __device__ __forceinline__ __nv_bfloat16 to_bf16(double v) {
@@ -989,6 +1016,13 @@ cudaError_t launch_project_split_tc(const void* a3, int64_t m, int64_t n, int64_
                      num_sms, flags, cancel, st, 1, pieces);
 }
 
+cudaError_t launch_wait_probe(int* flags, unsigned long long limit_ns, cudaStream_t st) {
+    if (!flags) return cudaErrorInvalidValue;
+    count_launch();
+    cudaError_t e = launch_pdl(wait_probe_kernel, dim3(1), dim3(32), (size_t)0, st, flags, limit_ns);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 bool tma_rows_aligned(const void* a, int64_t lda, int elem_bytes) {
     return reinterpret_cast<uintptr_t>(a) % 16 == 0 && (lda * elem_bytes) % 16 == 0;
 }
@@ -1008,7 +1042,7 @@ cudaError_t launch_copy_f32_padded(const float* a, int64_t m, int64_t n, int64_t
 cudaError_t launch_cast_bf16_split(const float* a, int64_t m, int64_t n, int64_t lda, void* a3, int64_t seg,
                                    const int* cancel, cudaStream_t st) {
     if (seg % 64 != 0 || seg < n) return cudaErrorInvalidValue;
-    const int blocks = (int)std::min<long long>(m, 16LL * 152);
+    const int blocks = (int)std::min<long long>(m, 16LL * device_sms());  // 16 row blocks per SM
     count_launch();
     {
         cudaError_t pe_ = launch_pdl(cast_bf16_split_kernel, dim3(blocks), dim3(256), (size_t)(0), st, a, m, n, lda, static_cast<__nv_bfloat16*>(a3), seg, cancel);
@@ -1054,7 +1088,7 @@ cudaError_t launch_split_panel(const float* q, int64_t ldq, int64_t rows, int64_
 
 cudaError_t launch_cast_bf16(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, void* abf,
                              int64_t ldb, const int* cancel, cudaStream_t st) {
-    const int blocks = (int)std::min<long long>(m, 16LL * 152);
+    const int blocks = (int)std::min<long long>(m, 16LL * device_sms());  // 16 row blocks per SM
     count_launch();
     if (ta == T_F32)
         {

@@ -52,6 +52,17 @@ corutv_status noalloc_fail(corutv_status st, const char* msg, cudaError_t e = cu
 
 int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+// Device (or managed) memory, asked of the runtime (no allocation). A host
+// pointer passed by mistake would otherwise reach the kernels as a raw address.
+bool on_device(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
@@ -60,6 +71,8 @@ extern "C" corutv_status corutv_orth_noalloc(const double* C, int64_t rows, int6
                                             int64_t ldq, double* R, int* info, void* cuda_stream) {
     using namespace corutv;
     if (!C || !Q) return noalloc_fail(CORUTV_EINVAL, "C and Q must not be NULL");
+    if (!on_device(C) || !on_device(Q) || (R && !on_device(R)) || (info && !on_device(info)))
+        return noalloc_fail(CORUTV_EINVAL, "C, Q, R and info must be device memory");
     if (ell < 1 || ell > 128 || rows < ell || ldc < ell || ldq < ell)
         return noalloc_fail(CORUTV_EINVAL, "need 1 <= ell <= 128, rows >= ell, ldc >= ell, ldq >= ell");
     const int64_t ld = rup(rows, 64);

@@ -36,6 +36,11 @@ cudaError_t launch_sketch_tc(const void* a, ElemType ta, int64_t m, int64_t n, i
 cudaError_t launch_cast_bf16(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, void* abf,
                              int64_t ldb, const int* cancel, cudaStream_t st);
 
+// One warp holds tensor memory while it waits on an mbarrier nothing arrives
+// on; after about limit_ns it sets flags[FLAG_TIMEOUT], frees the tensor
+// memory and returns (a test of the bounded-wait path).
+cudaError_t launch_wait_probe(int* flags, unsigned long long limit_ns, cudaStream_t st);
+
 // True when a row-major matrix can be a TMA source as is: 16-byte aligned
 // base and row stride.
 bool tma_rows_aligned(const void* a, int64_t lda, int elem_bytes);

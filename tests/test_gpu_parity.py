@@ -388,3 +388,26 @@ def test_serving_results_equal_alone_and_in_the_mix(ctx):
         u, t, v = (host(x) for x in bufs[i])
         a_alone = alone[i]
         assert rel(u @ t @ v.T, approx_of(a_alone)) < 1e-13
+
+
+def test_rpca_c4_workload_matches_oracle(ctx):
+    """Algorithm 2 on the full RPCA workload (4800 x 1200, rank 5, 10 % of the
+    entries replaced by uniform [-50, 50] outliers), FP32 data, against the
+    FP64 oracle run on the same FP32-rounded M with the same parameters:
+    the same number of iterations, rank 5, zeta < tol, the exact support of
+    S, and L within 1e-5 relative."""
+    pr = synth.rpca_c4(0)
+    m32 = pr.m_obs.astype(np.float32)
+    mm = m32.astype(np.float64)
+    d = oracle.rpca_defaults(mm)
+    ref = oracle.rpca(mm, 5, d["lam"], d["mu0"], d["mu_bar"], d["rho"], 1e-5, 50)
+    res = ctx.rpca(dev(m32, torch.float32), 5, lam=d["lam"], mu0=d["mu0"], mu_bar=d["mu_bar"], rho=d["rho"],
+                   tol=1e-5, max_iter=50, prec="f32")
+    lg, sg = host(res["L"]), host(res["S"])
+    print("C4 iters", res["iters"], ref["iters"], "zeta", res["zeta"], ref["zeta"], "dL", rel(lg, ref["L"]))
+    assert res["iters"] == ref["iters"]
+    assert res["rank"] == ref["rank"] == 5
+    assert res["zeta"] < 1e-5
+    assert np.array_equal(sg != 0, ref["S"] != 0)
+    assert rel(lg, ref["L"]) < 1e-5
+    assert rel(lg, pr.l_true) < 1e-4

@@ -192,3 +192,68 @@ def test_factor_bf16_error_budget(ctx, m, n, k, p, q):
     assert np.linalg.norm(u.T @ u - np.eye(ell)) < 1e-5
     assert np.linalg.norm(v.T @ v - np.eye(ell)) < 1e-5
     assert np.all(np.tril(t, -1) == 0)
+
+
+@pytest.mark.parametrize("prec,u_p", [("bf16", 2.0 ** -8), ("tf32", 2.0 ** -10)])
+@pytest.mark.parametrize("k,p", [(100, 10), (118, 10)])
+def test_factor_mixed_wide_sketch_matches_oracle(ctx, prec, u_p, k, p):
+    """The mixed paths at the sketch widths of the 20000 x 20000 workload
+    (ell = 110) and at the largest supported one (ell = 128), on a 3000 x 2500
+    matrix with its spectrum sigma_i = exp(-i/20), q = 2. At these widths the
+    FP32 Gram runs on 2 x 2 output tiles and adds the products' split tiles
+    (pieces) with write-back for the off-diagonal tiles too. Against the FP64
+    oracle: the reconstruction error within the per-precision budget, the
+    rank-ell approximation itself within that budget of the oracle's, and
+    orthonormal factors."""
+    m, n, q = 3000, 2500, 2
+    a = synth.spectrum_matrix(m, n, synth.c3_sigma(min(m, n)), 0.0, 11)
+    a32 = a.astype(np.float32)
+    a64 = a32.astype(np.float64)
+    ell = k + p
+    psi = synth.gaussian_psi(n, ell, seed=3)
+    ref = oracle.corutv(a64, k, p, q, psi)
+    out = ctx.factor(dev(a32, torch.float32), k, p, q, prec, psi=dev(psi))
+    assert ctx.sync() == 0
+    u, t, v = (host(out[x]) for x in ("U", "T", "V"))
+    na = np.linalg.norm(a64)
+    approx = u @ t @ v.T
+    ref_approx = ref["U"] @ ref["T"] @ ref["V"].T
+    e_gpu = np.linalg.norm(a64 - approx) / na
+    e_or = np.linalg.norm(a64 - ref_approx) / na
+    budget = 4 * u_p * np.sqrt(ell) * np.linalg.norm(a64, 2) / na
+    assert e_gpu <= e_or + budget, (e_gpu, e_or, budget)
+    assert np.linalg.norm(approx - ref_approx) / na <= e_or + budget
+    assert np.linalg.norm(u.T @ u - np.eye(ell)) < 1e-5
+    assert np.linalg.norm(v.T @ v - np.eye(ell)) < 1e-5
+    assert np.all(np.tril(t, -1) == 0) and np.all(np.diag(t) >= 0)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_serving_mixed_results_equal_alone_and_in_the_mix(ctx, prec):
+    """Requests of different m, n, k, q with FP32 data and tensor-core
+    sketches, submitted together so that they overlap on the device: each
+    result is bitwise the result of the same request run alone (every kernel's
+    summation order depends only on the request's own sizes)."""
+    shapes = [(300, 200, 10, 5, 0), (512, 700, 20, 10, 1), (257, 263, 5, 10, 2), (1000, 333, 30, 10, 1),
+              (640, 640, 64, 10, 2), (260, 1200, 12, 10, 0), (2048, 1024, 40, 10, 2), (900, 1500, 50, 14, 1)]
+    mats, alone = [], []
+    for i, (m, n, k, p, q) in enumerate(shapes):
+        a = dev(synth.spectrum_matrix(m, n, np.arange(1, min(m, n) + 1) ** -1.5, 0.0, 40 + i), torch.float32)
+        mats.append(a)
+        o = ctx.factor(a, k, p, q, prec, seed=i)
+        alone.append({x: host(o[x]) for x in ("U", "T", "V", "perm")})
+    bufs, tickets = [], []
+    for i, (m, n, k, p, q) in enumerate(shapes):
+        ell = k + p
+        u = torch.empty((m, ell), dtype=torch.float32, device="cuda")
+        t = torch.empty((ell, ell), dtype=torch.float32, device="cuda")
+        v = torch.empty((n, ell), dtype=torch.float32, device="cuda")
+        perm = torch.empty(ell, dtype=torch.int32, device="cuda")
+        bufs.append((u, t, v, perm))
+        tickets.append(corutv.corutv_submit(ctx.handle, corutv.make_request(mats[i], k, p, q, prec, u, t, v, perm,
+                                                                            seed=i)))
+    for i, tk in enumerate(tickets):
+        st, lat = corutv.corutv_poll(ctx.handle, tk, timeout_us=60_000_000)
+        assert st == corutv.OK and lat > 0
+        for name, x in zip(("U", "T", "V", "perm"), bufs[i]):
+            assert np.array_equal(host(x), alone[i][name]), f"request {i}: {name} differs from the lone run"
