@@ -264,7 +264,8 @@ def rel_error(A, out):
     return float(torch.linalg.norm(A.double() - approx) / torch.linalg.norm(A.double()))
 
 
-def time_factor(ctx, A, k, p, q, prec, steps, warmup, world, profile=False, d_mode=0, t_lower=0):
+def time_factor(ctx, A, k, p, q, prec, steps, warmup, world, profile=False, d_mode=0, t_lower=0, power_form=0,
+                bf16_last_round=0):
     """Device-timed steps of corutv_factor with outputs preallocated."""
     import torch
     from paper_1906_04572_gb300 import corutv
@@ -276,7 +277,7 @@ def time_factor(ctx, A, k, p, q, prec, steps, warmup, world, profile=False, d_mo
     perm = torch.empty(ell, device=A.device, dtype=torch.int32)
     for w in range(warmup):
         corutv.corutv_factor(ctx.handle, A, k, p, q, prec, U, T, V, perm, seed=0, stream=w, d_mode=d_mode,
-                             t_lower=t_lower)
+                             t_lower=t_lower, power_form=power_form, bf16_last_round=bf16_last_round)
     ctx.sync()
     if profile:
         corutv.corutv_profile_enable(ctx.handle, True)
@@ -286,7 +287,7 @@ def time_factor(ctx, A, k, p, q, prec, steps, warmup, world, profile=False, d_mo
     e0.record()
     for s in range(steps):
         corutv.corutv_factor(ctx.handle, A, k, p, q, prec, U, T, V, perm, seed=0, stream=s, d_mode=d_mode,
-                             t_lower=t_lower)
+                             t_lower=t_lower, power_form=power_form, bf16_last_round=bf16_last_round)
     e1.record()
     torch.cuda.synchronize()
     barrier(world)
@@ -484,6 +485,22 @@ def c2_lines(ctx, device, steps):
     return res
 
 
+def power_forms(ctx, A, k, p, q, steps, e_fp64):
+    """One thin QR per power round (power_form 1: C1 = A X used as it is,
+    X = qr(A^T C1)) against re-orthonormalising every sketch (power_form 0),
+    per sketch precision: device time and reconstruction error, the error
+    also as a ratio to the FP64 path's on the same matrix."""
+    res = {}
+    for prec in ("f32", "tf32", "bf16"):
+        for pf in (0, 1):
+            st = 2 if prec == "f32" else steps
+            ms, out, _ = time_factor(ctx, A, k, p, q, prec, st, 1, 1, power_form=pf)
+            e = rel_error(A, out)
+            res[f"{prec}_pf{pf}"] = {"ms": ms, "e_rel": e, "e_ratio_to_fp64": (e / e_fp64) if e_fp64 else None}
+            del out
+    return res
+
+
 def c1_latency(ctx, device, reps):
     """The 1000 x 1000 exact-rank-10 workload (FP64, ell = 15, q = 0):
     latency of single synchronous factorisations (launch- and latency-bound)."""
@@ -627,6 +644,17 @@ def run_ours(args):
             others[op] = {"ms": ms_o, "tflops": flops / (ms_o / 1e3) / 1e12, "e_rel": rel_error(A, out_o),
                           "steps": st}
             del out_o
+        # bf16 with the last power round on A_h alone like the others
+        ms_o, out_o, _ = time_factor(ctx, A, k, p, q, "bf16", max(3, args.steps // 4), 1, world, bf16_last_round=1)
+        others["bf16_plain_last_round"] = {"ms": ms_o, "tflops": flops / (ms_o / 1e3) / 1e12,
+                                           "e_rel": rel_error(A, out_o)}
+        del out_o
+        if fp64 is not None:
+            for v in others.values():
+                v["e_ratio_to_fp64"] = v["e_rel"] / fp64["e_rel"]
+                v["equal_error"] = bool(v["e_rel"] <= 1.01 * fp64["e_rel"])
+        others["power_forms"] = power_forms(ctx, A, k, p, q, max(3, args.steps // 4),
+                                            fp64["e_rel"] if fp64 else None)
 
     # end to end through the C ABI with host (pinned) buffers
     e2e = None

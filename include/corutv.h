@@ -83,6 +83,18 @@ typedef struct {
                              other values -> CORUTV_EINVAL */
     const double* psi;    /* optional row-major FP64 Gaussian test matrix: n x ell, or
                              m x ell when t_lower = 1 */
+    uint32_t power_form;  /* 0: every sketch is re-orthonormalised before its next use (C1 -> Q1,
+                             C2 -> X); 1: one thin QR per power round, X = qr(A^T (A X)) -- the
+                             power step of Algorithm 1 with C1 used as it is, the form the
+                             paper's loop has between A and A^T (Sec. 3.2); in exact arithmetic
+                             the same Q1, Q2. Loses the weak directions of C1 to rounding when
+                             C1 is an operand of reduced precision (BF16 sketches). Other values
+                             -> CORUTV_EINVAL */
+    uint32_t bf16_last_round; /* BF16 sketches of FP32 input with d_mode 0: 0 (default) the two
+                             products of the last power round multiply by A_h + A_m, the first two
+                             exact bf16 parts of A (16 significant bits), the earlier rounds by
+                             A_h; 1: every round by A_h. Ignored otherwise; other values ->
+                             CORUTV_EINVAL */
 } corutv_opts;
 
 typedef struct corutv_ctx corutv_ctx;

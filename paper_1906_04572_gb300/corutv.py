@@ -35,7 +35,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int64), ("p", ctypes.c_int64), ("q", ctypes.c_int64),
                 ("sketch_prec", ctypes.c_int32), ("d_mode", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_uint32), ("t_lower", ctypes.c_uint32),
-                ("psi", ctypes.c_void_p)]
+                ("psi", ctypes.c_void_p), ("power_form", ctypes.c_uint32), ("bf16_last_round", ctypes.c_uint32)]
 
 
 class Request(ctypes.Structure):
@@ -153,8 +153,11 @@ def _check(ctx, status: int, allow=(OK,)):
     return status
 
 
-def _opts(k, p, q, prec, seed=0, stream=0, psi=None, d_mode=0, t_lower=0) -> Opts:
+def _opts(k, p, q, prec, seed=0, stream=0, psi=None, d_mode=0, t_lower=0, power_form=0,
+          bf16_last_round=0) -> Opts:
     o = Opts()
+    o.power_form = int(power_form)
+    o.bf16_last_round = int(bf16_last_round)
     o.k, o.p, o.q = int(k), int(p), int(q)
     o.sketch_prec = PREC_NAMES[prec] if isinstance(prec, str) else int(prec)
     o.d_mode = int(d_mode)
@@ -201,12 +204,13 @@ def corutv_sync(ctx) -> int:
 
 
 def corutv_factor(ctx, A, k: int, p: int, q: int, prec="f64", U=None, T=None, V=None, perm=None,
-                  psi=None, seed: int = 0, stream: int = 0, d_mode: int = 0, t_lower: int = 0) -> int:
+                  psi=None, seed: int = 0, stream: int = 0, d_mode: int = 0, t_lower: int = 0,
+                  power_form: int = 0, bf16_last_round: int = 0) -> int:
     """Algorithm 1 into caller-provided U (m x ell), T (ell x ell), V (n x ell),
     perm (ell int32). Buffers must share A's device and dtype. t_lower = 1:
     the lower-triangular-T variant (Algorithm 1 on A^T; psi is then m x ell)."""
     m, n = A.shape
-    o = _opts(k, p, q, prec, seed, stream, psi, d_mode, t_lower)
+    o = _opts(k, p, q, prec, seed, stream, psi, d_mode, t_lower, power_form, bf16_last_round)
     _use_torch_stream(ctx, A)
     st = load().corutv_factor(ctx, _dtype_code(A), _ptr(A), m, n, _rowmajor_ld(A), ctypes.byref(o),
                               _ptr(U), _rowmajor_ld(U) if U is not None else 0, _ptr(T), _ptr(V),
@@ -231,7 +235,7 @@ def corutv_rpca(ctx, M, k: int, L, S, lam=0.0, mu0=0.0, mu_bar=0.0, rho=0.0, tol
 
 
 def make_request(A, k, p, q, prec, U, T, V=None, perm=None, psi=None, seed=0, stream=0, d_mode=0,
-                 t_lower=0) -> Request:
+                 t_lower=0, power_form=0, bf16_last_round=0) -> Request:
     """Request descriptor; for a CUDA tensor A it remembers the torch stream
     current now, which corutv_submit makes the context's stream so that the
     request waits for A's producer on it."""
@@ -243,7 +247,7 @@ def make_request(A, k, p, q, prec, U, T, V=None, perm=None, psi=None, seed=0, st
     rq.dtype = _dtype_code(A)
     rq.A = _ptr(A).value
     rq.m, rq.n, rq.lda = m, n, _rowmajor_ld(A)
-    rq.opts = _opts(k, p, q, prec, seed, stream, psi, d_mode, t_lower)
+    rq.opts = _opts(k, p, q, prec, seed, stream, psi, d_mode, t_lower, power_form, bf16_last_round)
     rq.U = _ptr(U).value if U is not None else None
     rq.T = _ptr(T).value
     rq.V = _ptr(V).value if V is not None else None
@@ -360,7 +364,8 @@ class Context:
         except Exception:
             pass
 
-    def factor(self, A, k, p, q, prec="f64", psi=None, seed=0, stream=0, want_uv=True, d_mode=0, t_lower=0):
+    def factor(self, A, k, p, q, prec="f64", psi=None, seed=0, stream=0, want_uv=True, d_mode=0, t_lower=0,
+               power_form=0, bf16_last_round=0):
         import torch
         m, n = A.shape
         ell = k + p
@@ -369,7 +374,8 @@ class Context:
         V = torch.empty((n, ell), **kw) if want_uv else None
         T = torch.empty((ell, ell), **kw)
         perm = torch.empty(ell, dtype=torch.int32, device=A.device)
-        corutv_factor(self.handle, A, k, p, q, prec, U, T, V, perm, psi, seed, stream, d_mode, t_lower)
+        corutv_factor(self.handle, A, k, p, q, prec, U, T, V, perm, psi, seed, stream, d_mode, t_lower,
+                      power_form, bf16_last_round)
         return {"U": U, "T": T, "V": V, "perm": perm}
 
     def rpca(self, M, k, **kw):

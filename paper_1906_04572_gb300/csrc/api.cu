@@ -175,8 +175,9 @@ struct FactorPlan {
     bool split;       // projection by exact bf16 splits on tcgen05 (BF16 / TF32 sketches, FP32 input)
     bool copy_a;      // TF32: A is not a TMA source as is (base or row stride not 16-byte aligned)
     int dmode;        // 0: D = Q1^T A Q2 (eq. 7, a third pass); 1: the single-pass core (= R2^T)
+    int power_form;   // 0: every sketch re-orthonormalised; 1: one thin QR per power round (C1 used as is)
+    bool x2_last;     // the last power round's products multiply by A_h + A_m (bf16 split copy)
     int64_t ldc32;    // row stride of that padded FP32 copy of A
-    int64_t seg;      // columns per segment of the bf16 copy of A ([A_h | A_m | A_l] when split)
     int sp_ax, sp_aty, gs_m, gs_n;  // SIMT split counts (sizing the partial buffers)
     int64_t part_elems;
     int num_sms;
@@ -202,7 +203,8 @@ struct FactorBufs {
 // t_lower: the variant with a lower triangular T (Algorithm 1 on A^T).
 corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64_t lda, int64_t k,
                         int64_t p, int64_t q, corutv_prec prec, int num_sms, bool a_aligned = true,
-                        int d_mode = 0, bool t_lower = false) {
+                        int d_mode = 0, bool t_lower = false, uint32_t power_form = 0,
+                        uint32_t bf16_last_round = 0) {
     pl.tr = t_lower;
     pl.ma = m; pl.na = n;
     pl.m = t_lower ? n : m; pl.n = t_lower ? m : n;
@@ -225,7 +227,10 @@ corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64
     if (d_mode != 0 && d_mode != 1) return fail(CORUTV_EINVAL, "d_mode %d is not supported (0 exact D, 1 single-pass core)", d_mode);
     pl.dmode = d_mode;
     pl.split = pl.tensor && ta == T_F32 && d_mode == 0;  // the bf16 splits serve the projection only
-    pl.seg = pl.split ? round_up(n, 64) : round_up(n, 8);
+    if (power_form > 1) return fail(CORUTV_EINVAL, "power_form %u is not supported (0 or 1)", power_form);
+    if (bf16_last_round > 1) return fail(CORUTV_EINVAL, "bf16_last_round %u is not supported (0 or 1)", bf16_last_round);
+    pl.power_form = (int)power_form;
+    pl.x2_last = pl.split && prec == CORUTV_P_BF16 && bf16_last_round == 0;
     pl.copy_a = prec == CORUTV_P_TF32 && (!a_aligned || lda % 4 != 0);
     pl.ldc32 = round_up(n, 4);
     pl.ellp = pl.tensor ? round_up(pl.ell, 16) : pl.ell;
@@ -280,7 +285,8 @@ void carve_factor(C& cv, const FactorPlan& pl, FactorBufs& b) {
     b.q1c = cv.template take<char>(pm * es_c);
     b.q2c = cv.template take<char>(pl.split ? 3 * std::max(pm, pn) * 2 : std::max(pm, pn) * es_d);
     b.part = cv.template take<char>(pl.part_elems * std::max(8, std::max(es_c, es_d)));
-    b.abf = (pl.prec == CORUTV_P_BF16 || pl.split) ? cv.template take<char>(pl.ma * (pl.split ? 3 : 1) * pl.seg * 2)
+    b.abf = (pl.prec == CORUTV_P_BF16 || pl.split) ? cv.template take<char>((pl.split ? 3 : 1) *
+                                                                            tiled_part_bytes(pl.ma, pl.na))
                                                    : nullptr;
     b.at = pl.prec == CORUTV_P_TF32 ? cv.template take<float>(pl.na * pl.ldma) : nullptr;
     b.a32 = pl.copy_a ? cv.template take<float>(pl.ma * pl.ldc32) : nullptr;
@@ -409,18 +415,15 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
         CK(cudaMemsetAsync(b.q1c, 0, (size_t)pl.ellp * pl.ldm * elem_size(pl.tcomp), ex.st));
         CK(launch_panel_convert(b.x, pl.tp, pl.ldn, n, pl.ellp, b.xc, pl.tcomp, pl.ldn, ex.cancel, ex.st));
         if (pl.prec == CORUTV_P_TF32)
-            // one pass over A: A^T for the K-major A^T Y, the bf16 splits for eq. 7
-            CK(launch_prep_f32(static_cast<const float*>(a), pl.ma, pl.na, pl.lda, b.at, pl.ldma, b.abf, pl.seg,
-                               b.a32, pl.ldc32, ex.cancel, ex.st));
-        else if (pl.split)
-            CK(launch_cast_bf16_split(static_cast<const float*>(a), pl.ma, pl.na, pl.lda, b.abf, pl.seg, ex.cancel,
-                                      ex.st));
+            // one pass over A: A^T for the K-major A^T Y, the tiled bf16 splits for eq. 7
+            CK(launch_prep_f32(static_cast<const float*>(a), pl.ma, pl.na, pl.lda, b.at, pl.ldma, b.abf, b.a32,
+                               pl.ldc32, ex.cancel, ex.st));
         else if (pl.prec == CORUTV_P_BF16)
-            CK(launch_cast_bf16(a, pl.ta, pl.ma, pl.na, pl.lda, b.abf, pl.seg, ex.cancel, ex.st));
+            // the tiled bf16 copy the products read (A_h), with A_m, A_l for eq. 7 when split
+            CK(launch_cast_tiled(a, pl.ta, pl.ma, pl.na, pl.lda, b.abf, pl.split ? 3 : 1, ex.cancel, ex.st));
     } else {
         CK(launch_panel_convert(b.x, pl.tp, pl.ldn, n, ell, b.xc, pl.tcomp, pl.ldn, ex.cancel, ex.st));
     }
-    const int64_t ldabf = (pl.split ? 3 : 1) * pl.seg;  // the sketches read the A_h segment
     // split tiles of a tensor-core product stay pieces until the Gram that
     // first reads the panel adds them (no fix-up tail in the product)
     TcPieces pieces;
@@ -428,18 +431,18 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     // A X (a_rows: the output has A's rows, the operand is a panel with A's
     // columns) or A^T Y (the other way round). Algorithm 1's C1 = A X is the
     // first, C2 = A^T Q1 the second; on A^T (the lower-T variant) the two swap.
-    auto product = [&](bool a_rows, const void* opnd, void* out, TcPieces* pc) -> corutv_status {
+    auto product = [&](bool a_rows, const void* opnd, void* out, TcPieces* pc, int nsegs = 1) -> corutv_status {
         const int64_t ldo = a_rows ? pl.ldna : pl.ldma, ldout = a_rows ? pl.ldma : pl.ldna;
         if (!pl.tensor) return sketch_simt(ex, pl, b, a_rows ? A_ROWS : A_COLS, a, pl.ta, opnd, pl.tcomp, out, ldout);
         ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
-        if (a_rows) {
-            const bool bf = pl.prec == CORUTV_P_BF16;
-            const void* aop = bf ? b.abf : (pl.copy_a ? static_cast<const void*>(b.a32) : a);
-            const int64_t lda_op = bf ? ldabf : (pl.copy_a ? pl.ldc32 : pl.lda);
+        if (pl.prec == CORUTV_P_BF16) {
+            // the tiled bf16 copy (its first part, A_h) serves both directions
+            CK(launch_sketch_tc_tiled(b.abf, pl.ma, pl.na, a_rows ? 0 : 1, opnd, ldo, ell, pl.ellp, b.part, b.tcnt,
+                                      out, pl.tp, ldout, ex.num_sms, ex.flags, ex.cancel, ex.st, pc, nsegs));
+        } else if (a_rows) {
+            const void* aop = pl.copy_a ? static_cast<const void*>(b.a32) : a;
+            const int64_t lda_op = pl.copy_a ? pl.ldc32 : pl.lda;
             CK(launch_sketch_tc(aop, pl.tcomp, pl.ma, pl.na, lda_op, /*trans=*/0, opnd, ldo, ell, pl.ellp, b.part,
-                                b.tcnt, out, pl.tp, ldout, ex.num_sms, ex.flags, ex.cancel, ex.st, pc));
-        } else if (pl.prec == CORUTV_P_BF16) {
-            CK(launch_sketch_tc(b.abf, pl.tcomp, pl.ma, pl.na, ldabf, /*trans=*/1, opnd, ldo, ell, pl.ellp, b.part,
                                 b.tcnt, out, pl.tp, ldout, ex.num_sms, ex.flags, ex.cancel, ex.st, pc));
         } else {  // TF32: (A^T) Y with the transposed copy, both operands K-major
             CK(launch_sketch_tc(b.at, pl.tcomp, pl.na, pl.ma, pl.ldma, /*trans=*/0, opnd, ldo, ell, pl.ellp, b.part,
@@ -448,13 +451,22 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
         return CORUTV_OK;
     };
     for (int64_t it = 0; it <= pl.q; ++it) {
+        // the last round's products read A_h + A_m when asked (the rounding of A's
+        // bf16 copy there is what limits the captured subspace)
+        const int nsegs = (pl.x2_last && it == pl.q) ? 2 : 1;
+        // one thin QR per power round: C1 = A X is the operand of A^T as it is
+        const bool raw_c1 = pl.power_form == 1 && it < pl.q;
         // eq. 4: C1 = A X
-        CKS(product(!pl.tr, b.xc, b.c1, defer));
+        CKS(product(!pl.tr, b.xc, b.c1, raw_c1 ? nullptr : defer, nsegs));
         const int inner = (pl.prec == CORUTV_P_F64) ? 2 : 1;  // passes for the intermediate bases
-        CKS(orth(ex, pl, b, b.c1, pl.ldm, m, b.q1, b.q1c, pl.tcomp, it < pl.q ? inner : 2, nullptr, &pieces));
+        if (raw_c1) {
+            CK(launch_panel_convert(b.c1, pl.tp, pl.ldm, m, ell, b.q1c, pl.tcomp, pl.ldm, ex.cancel, ex.st));
+        } else {
+            CKS(orth(ex, pl, b, b.c1, pl.ldm, m, b.q1, b.q1c, pl.tcomp, it < pl.q ? inner : 2, nullptr, &pieces));
+        }
         pieces = TcPieces();
         // eq. 5 (with C1 -> Q1): C2 = A^T Q1
-        CKS(product(pl.tr, b.q1c, b.c2, defer));
+        CKS(product(pl.tr, b.q1c, b.c2, defer, nsegs));
         if (it < pl.q) {
             CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.x, b.xc, pl.tcomp, inner, nullptr, &pieces));
             pieces = TcPieces();
@@ -483,8 +495,8 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
         CK(launch_split_panel(static_cast<const float*>(pan), pl.ldna, pl.na, ell, pl.ellp, b.q2c, pl.ldna,
                               ex.cancel, ex.st));
         ProfScope ps(ex.prof, CORUTV_STAGE_PROJECT, ex.st);
-        CK(launch_project_split_tc(b.abf, pl.ma, pl.na, pl.seg, b.q2c, pl.ldna, ell, pl.ellp, b.part, b.tcnt, b.w,
-                                   pl.tp, pl.ldma, ex.num_sms, ex.flags, ex.cancel, ex.st, defer));
+        CK(launch_project_split_tc_tiled(b.abf, pl.ma, pl.na, b.q2c, pl.ldna, ell, pl.ellp, b.part, b.tcnt, b.w,
+                                         pl.tp, pl.ldma, ex.num_sms, ex.flags, ex.cancel, ex.st, defer));
     } else {
         const void* opnd = b.q2c;
         if (pl.tr) {
@@ -807,7 +819,8 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
     if (opts->t_lower > 1) return fail(CORUTV_EINVAL, "t_lower %u is not supported (0 upper T, 1 lower T)", opts->t_lower);
     // host input is staged with row stride n into the (256-byte aligned) workspace
     CKS(make_plan(pl, ta, m, n, dev ? lda : n, opts->k, opts->p, opts->q, (corutv_prec)opts->sketch_prec,
-                  ctx->num_sms, !dev || reinterpret_cast<uintptr_t>(A) % 16 == 0, opts->d_mode, opts->t_lower == 1));
+                  ctx->num_sms, !dev || reinterpret_cast<uintptr_t>(A) % 16 == 0, opts->d_mode, opts->t_lower == 1,
+                  opts->power_form, opts->bf16_last_round));
     const int64_t ell = pl.ell;
     if (U && ldu < ell) return fail(CORUTV_EINVAL, "ldu < ell");
     if (V && ldv < ell) return fail(CORUTV_EINVAL, "ldv < ell");
@@ -907,14 +920,14 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
     if ((int)prec == CORUTV_P_BF16X3) {
         // FP32-accurate A X from exact bf16 splits (tensor cores)
         if (ta != T_F32 || trans) return fail(CORUTV_EINVAL, "BF16X3 needs FP32 A and trans = 0");
-        const int64_t ellp = round_up(ell, 16), ldn = round_up(n, 64), ldm = round_up(m, 64), seg = round_up(n, 64);
+        const int64_t ellp = round_up(ell, 16), ldn = round_up(n, 64), ldm = round_up(m, 64);
         const int64_t part_elems = tc_partial_elems(m, n, ellp, ldm, ldn, ctx->num_sms);
         Carver measure(nullptr);
         measure.take<float>(ellp * ldn);
         measure.take<char>(3 * ellp * ldn * 2);
         measure.take<double>(ellp * ldm);
         measure.take<float>(part_elems);
-        measure.take<char>(m * 3 * seg * 2);
+        measure.take<char>(3 * tiled_part_bytes(m, n));
         measure.take<int>(tc_counter_elems(m, n));
         CKS(ensure_ws(ctx, ctx->ws, measure.off, ctx->stream));
         Carver cv(ctx->ws.ptr);
@@ -922,14 +935,14 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
         void* x3 = cv.take<char>(3 * ellp * ldn * 2);
         double* cp = cv.take<double>(ellp * ldm);
         void* part = cv.take<float>(part_elems);
-        void* a3 = cv.take<char>(m * 3 * seg * 2);
+        void* a3 = cv.take<char>(3 * tiled_part_bytes(m, n));
         int* tcnt = cv.take<int>(tc_counter_elems(m, n));
         CK(cudaMemsetAsync(tcnt, 0, sizeof(int) * (size_t)tc_counter_elems(m, n), ctx->stream));
         CK(launch_rowmajor_to_panel(X, ldx, n, ell, ellp, xp, T_F32, ldn, ctx->stream));
         CK(launch_split_panel(xp, ldn, n, ell, ellp, x3, ldn, nullptr, ctx->stream));
-        CK(launch_cast_bf16_split(static_cast<const float*>(A), m, n, lda, a3, seg, nullptr, ctx->stream));
-        CK(launch_project_split_tc(a3, m, n, seg, x3, ldn, ell, ellp, part, tcnt, cp, T_F64, ldm, ctx->num_sms,
-                                   ctx->flags, nullptr, ctx->stream));
+        CK(launch_cast_tiled(A, T_F32, m, n, lda, a3, 3, nullptr, ctx->stream));
+        CK(launch_project_split_tc_tiled(a3, m, n, x3, ldn, ell, ellp, part, tcnt, cp, T_F64, ldm, ctx->num_sms,
+                                         ctx->flags, nullptr, ctx->stream));
         CK(launch_panel_to_rowmajor(cp, ldm, m, ell, C, T_F64, ldc, nullptr, ctx->stream));
         return CORUTV_OK;
     }
@@ -958,7 +971,7 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
     measure.take<char>(pl.ellp * ldxp * 8);
     measure.take<double>(pl.ellp * ldcp);
     measure.take<char>(pl.part_elems * 8);
-    if (prec == CORUTV_P_BF16) measure.take<char>(m * round_up(n, 8) * 2);
+    if (prec == CORUTV_P_BF16) measure.take<char>(tiled_part_bytes(m, n));
     // TF32 A^T X runs as (A^T) X on a transposed copy: both operands K-major
     const bool tf32_t = prec == CORUTV_P_TF32 && trans;
     const bool tf32_copy = prec == CORUTV_P_TF32 && !trans && !tma_rows_aligned(A, lda, 4);
@@ -972,7 +985,7 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
     double* cp = cv.take<double>(pl.ellp * ldcp);
     FactorBufs b{};
     b.part = cv.take<char>(pl.part_elems * 8);
-    b.abf = prec == CORUTV_P_BF16 ? cv.take<char>(m * round_up(n, 8) * 2) : nullptr;
+    b.abf = prec == CORUTV_P_BF16 ? cv.take<char>(tiled_part_bytes(m, n)) : nullptr;
     float* a32 = tf32_copy ? cv.take<float>(m * round_up(n, 4)) : nullptr;
     float* at = tf32_t ? cv.take<float>(n * pl.ldm) : nullptr;
     b.tcnt = pl.tensor ? cv.take<int>(tc_counter_elems(m, n)) : nullptr;
@@ -984,19 +997,21 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
         const void* aop = A;
         int64_t lda_op = lda;
         if (prec == CORUTV_P_BF16) {
-            CK(launch_cast_bf16(A, ta, m, n, lda, b.abf, round_up(n, 8), nullptr, ctx->stream));
+            CK(launch_cast_tiled(A, ta, m, n, lda, b.abf, 1, nullptr, ctx->stream));
             aop = b.abf;
-            lda_op = round_up(n, 8);
         } else if (tf32_copy) {
             CK(launch_copy_f32_padded(static_cast<const float*>(A), m, n, lda, a32, round_up(n, 4), ctx->stream));
             aop = a32;
             lda_op = round_up(n, 4);
         }
         if (tf32_t) {
-            CK(launch_prep_f32(static_cast<const float*>(A), m, n, lda, at, pl.ldm, nullptr, 0, nullptr, 0, nullptr,
+            CK(launch_prep_f32(static_cast<const float*>(A), m, n, lda, at, pl.ldm, nullptr, nullptr, 0, nullptr,
                                ctx->stream));
             CK(launch_sketch_tc(at, T_F32, n, m, pl.ldm, 0, xc, ldxp, ell, pl.ellp, b.part, b.tcnt, cp, T_F64, ldcp,
                                 ctx->num_sms, ctx->flags, nullptr, ctx->stream));
+        } else if (prec == CORUTV_P_BF16) {
+            CK(launch_sketch_tc_tiled(aop, m, n, trans, xc, ldxp, ell, pl.ellp, b.part, b.tcnt, cp, T_F64, ldcp,
+                                      ctx->num_sms, ctx->flags, nullptr, ctx->stream));
         } else {
             CK(launch_sketch_tc(aop, pl.tcomp, m, n, lda_op, trans, xc, ldxp, ell, pl.ellp, b.part, b.tcnt, cp, T_F64,
                                 ldcp, ctx->num_sms, ctx->flags, nullptr, ctx->stream));
@@ -1137,7 +1152,8 @@ extern "C" corutv_status corutv_rpca(corutv_ctx* ctx, corutv_dtype dtype, const 
     if (rho <= 0) rho = 1.6;
     if (lambda <= 0) lambda = 1.0 / std::sqrt((double)std::max(m, n));
     FactorPlan pl;
-    CKS(make_plan(pl, tm, m, n, n, k, k, 1, prec, ctx->num_sms));
+    CKS(make_plan(pl, tm, m, n, n, k, k, 1, prec, ctx->num_sms, true, 0, false, opts->power_form,
+                  opts->bf16_last_round));
     const int64_t mn = m * n;
     const int nup = rpca_update_blocks(m, n);
     size_t bytes = factor_bytes(pl);
@@ -1248,7 +1264,7 @@ size_t request_bytes(const corutv_request& r, bool host, int num_sms, FactorPlan
     }
     *st = make_plan(pl, ta, r.m, r.n, host ? r.n : r.lda, r.opts.k, r.opts.p, r.opts.q,
                     (corutv_prec)r.opts.sketch_prec, num_sms, host || reinterpret_cast<uintptr_t>(r.A) % 16 == 0,
-                    r.opts.d_mode, r.opts.t_lower == 1);
+                    r.opts.d_mode, r.opts.t_lower == 1, r.opts.power_form, r.opts.bf16_last_round);
     if (*st != CORUTV_OK) return 0;
     size_t bytes = factor_bytes(pl);
     const int es = elem_size(ta);

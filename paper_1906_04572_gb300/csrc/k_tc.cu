@@ -65,6 +65,9 @@ struct TcParams {
     int stages;
     int a_boxes;          // TMA boxes per A tile (MN-major needs several)
     int a_box_cols;       // columns (MN elements) per A box
+    const uint8_t* a_tiles;  // non-null: A is a tiled bf16 copy (see launch_cast_tiled), read by bulk copies
+    long long a_ntp;      // tiles per 128-row block of that copy (even)
+    long long a_seg_bytes;   // bytes between its K segments (split parts)
     int b_boxes;          // TMA boxes per B tile
     int b_box_rows;       // rows per B box
     uint32_t a_bytes;     // A tile bytes per stage
@@ -336,7 +339,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 4 && lane == 0) {
-        prefetch_tmap(&map_a);
+        if (!p.a_tiles) prefetch_tmap(&map_a);
         prefetch_tmap(&map_b);
     }
     // setup above overlaps the previous kernel's tail; operands and flags are read below
@@ -372,10 +375,31 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                 uint8_t* sb = sa + (size_t)p.kgroup * p.a_bytes;
                 mbar_expect_tx(&full_bar[s], p.stage_bytes);
                 // kgroup boxes along K: A at sa + g a_bytes, B at sb + g b_bytes
+                if (p.a_tiles) {
+                    // tiled copy: tile (I, J) = rows 128 I.., columns 64 J.. at (I ntp + J) 16 KB,
+                    // each the image of a 128-byte-swizzled box; A X takes kgroup tiles of
+                    // one row block (adjacent), A^T Y the two tiles of a 128-column block
+                    // (adjacent) over kgroup 64-row halves
+                    if (!p.trans) {
+                        const uint8_t* src = p.a_tiles + seg * p.a_seg_bytes +
+                                             (((long long)t * p.a_ntp + (long long)kk * p.kgroup) << 14);
+                        bulk_load(sa, src, (uint32_t)p.kgroup << 14, &full_bar[s]);
+                    } else if (p.kgroup == 2) {
+                        bulk_load(sa, p.a_tiles + seg * p.a_seg_bytes + (((long long)kk * p.a_ntp + 2LL * t) << 14),
+                                  32768u, &full_bar[s]);
+                    } else {
+                        const uint8_t* src = p.a_tiles + seg * p.a_seg_bytes +
+                                             (((long long)(kk >> 1) * p.a_ntp + 2LL * t) << 14) + (size_t)(kk & 1) * 8192;
+                        bulk_load(sa, src, 8192u, &full_bar[s]);
+                        bulk_load(sa + 8192, src + 16384, 8192u, &full_bar[s]);
+                    }
+                }
                 for (int g = 0; g < p.kgroup; ++g) {
                     const int kx = kk * p.kchunk_elems + g * ke;
                     uint8_t* sag = sa + (size_t)g * p.a_bytes;
-                    if (!p.trans) {
+                    if (p.a_tiles) {
+                        // A already requested above
+                    } else if (!p.trans) {
                         tma_load_2d(sag, &map_a, &full_bar[s], seg * p.seg_stride + kx, (int)(t * kTileM));
                     } else {
                         for (int bx = 0; bx < p.a_boxes; ++bx)
@@ -414,9 +438,10 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                 a_desc0 = smem_desc(sbase, 16, 1024, 2);
                 a_kstep = 32u >> 4;
             } else if (!kTf32) {
-                // MN-major A: 64-element MN atoms (a_bytes / a_boxes apart), 8-row K groups 1024 B
-                // apart; a K step of 16 consumes two K groups
-                a_desc0 = smem_desc(sbase, p.a_bytes / p.a_boxes, 1024, 2);
+                // MN-major A: 64-element MN atoms (a_bytes / a_boxes apart; in a tiled copy the
+                // two atoms are whole 64 kgroup-row tiles), 8-row K groups 1024 B apart; a K step
+                // of 16 consumes two K groups
+                a_desc0 = smem_desc(sbase, p.a_tiles ? (uint32_t)p.kgroup * 8192u : p.a_bytes / p.a_boxes, 1024, 2);
                 a_kstep = 2048u >> 4;
             } else {
                 // MN-major tf32: 32-element MN atoms, a K step of 8 is one K group
@@ -424,7 +449,9 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                 a_kstep = 1024u >> 4;
             }
             const uint64_t b_desc0 = smem_desc(sbase + (uint32_t)p.kgroup * p.a_bytes, 16, 1024, 2);
-            const uint32_t a_g16 = p.a_bytes >> 4;                                       // next K box of A
+            // next K box of A: the next kgroup box (A X), or 64 rows further down both MN atoms
+            // of a tiled A^T Y operand
+            const uint32_t a_g16 = (p.a_tiles && p.trans) ? (8192u >> 4) : (p.a_bytes >> 4);
             const uint32_t b_g16 = ((uint32_t)(p.b_boxes * p.b_box_rows) * 128u) >> 4;  // next K box of B
             const int kg = p.kgroup;
             const uint32_t b_kstep = 32u >> 4;  // 16 bf16 or 8 tf32 elements of K
@@ -626,40 +653,6 @@ __device__ __forceinline__ __nv_bfloat16 to_bf16(double v) {
     return __float2bfloat16_rn(f);
 }
 
-// One block row-segment per iteration: block b handles rows b, b + G, ...;
-// threads cover the row 4 elements at a time (float4 loads when the row start
-// is 16-byte aligned, 8-byte bf16x4 stores; ldb is a multiple of 8).
-template <typename TI>
-__global__ void cast_bf16_kernel(const TI* a, long long m, long long n, long long lda, __nv_bfloat16* out,
-                                 long long ldb, const int* cancel) {
-    pdl_trigger();
-    pdl_wait();
-    if (cancel && *cancel) return;
-    for (long long i = blockIdx.x; i < m; i += gridDim.x) {
-        const TI* src = a + i * lda;
-        __nv_bfloat16* dst = out + i * ldb;
-        const bool vec = sizeof(TI) == 4 && (reinterpret_cast<uintptr_t>(src) & 15) == 0;
-        for (long long j = 4LL * threadIdx.x; j < ldb; j += 4LL * blockDim.x) {
-            float v[4];
-            if (vec && j + 3 < n) {
-                const float4 f = *reinterpret_cast<const float4*>(src + j);
-                v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
-                __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
-                __nv_bfloat162 hi = __floats2bfloat162_rn(v[2], v[3]);
-                uint2 pk;
-                pk.x = *reinterpret_cast<uint32_t*>(&lo);
-                pk.y = *reinterpret_cast<uint32_t*>(&hi);
-                *reinterpret_cast<uint2*>(dst + j) = pk;
-            } else {
-                for (int q = 0; q < 4; ++q) {
-                    const long long jj = j + q;
-                    if (jj < ldb) dst[jj] = (jj < n) ? to_bf16(src[jj]) : __float2bfloat16_rn(0.f);
-                }
-            }
-        }
-    }
-}
-
 __global__ void copy_f32_padded_kernel(const float* a, long long m, long long n, long long lda, float* out,
                                        long long ldb) {
     pdl_trigger();
@@ -684,45 +677,18 @@ __device__ __forceinline__ void split3(float a, __nv_bfloat16& h, __nv_bfloat16&
     l = __float2bfloat16_rn(r2);
 }
 
-// Rows of [A_h | A_m | A_l], each segment `seg` (multiple of 64) wide, zero
-// beyond column n. One block per row at a time, 4 columns per thread.
-__global__ void cast_bf16_split_kernel(const float* a, long long m, long long n, long long lda, __nv_bfloat16* out,
-                                       long long seg, const int* cancel) {
-    pdl_trigger();
-    pdl_wait();
-    if (cancel && *cancel) return;
-    for (long long i = blockIdx.x; i < m; i += gridDim.x) {
-        const float* src = a + i * lda;
-        __nv_bfloat16* dst = out + i * 3 * seg;
-        const bool vec = (reinterpret_cast<uintptr_t>(src) & 15) == 0;
-        for (long long j = 4LL * threadIdx.x; j < seg; j += 4LL * blockDim.x) {
-            float v[4];
-            if (vec && j + 3 < n) {
-                const float4 f = *reinterpret_cast<const float4*>(src + j);
-                v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
-            } else {
-                for (int q = 0; q < 4; ++q) v[q] = (j + q < n) ? src[j + q] : 0.f;
-            }
-            __nv_bfloat16 h[4], md[4], lo[4];
-            for (int q = 0; q < 4; ++q) split3(v[q], h[q], md[q], lo[q]);
-            *reinterpret_cast<uint2*>(dst + j) = *reinterpret_cast<const uint2*>(h);
-            *reinterpret_cast<uint2*>(dst + seg + j) = *reinterpret_cast<const uint2*>(md);
-            *reinterpret_cast<uint2*>(dst + 2 * seg + j) = *reinterpret_cast<const uint2*>(lo);
-        }
-    }
-}
-
 // One read of FP32 A (m x n, row stride lda) in 64 x 64 tiles, writing any
 // of: at = A^T (n rows, row stride ldt >= round_up(m, 64); columns
-// [m, round_up(m, 64)) zero, any further ones untouched), the rows of
-// [A_h | A_m | A_l] (a3, segment `seg`, zero beyond n) and a row-major copy
-// with row stride ldc <= round_up(n, 64) (zero for n <= j < ldc). The transposed
+// [m, round_up(m, 64)) zero, any further ones untouched), the exact splits
+// A_h, A_m, A_l as the three parts of a tiled bf16 copy (a3, the layout of
+// launch_cast_tiled, padding zero) and a row-major copy with row stride
+// ldc <= round_up(n, 64) (zero for n <= j < ldc). The transposed
 // copy makes A^T Y a product with K-major operands (TF32 has no MN-major form
 // here). 256 threads, a tile staged in shared memory for the transpose.
 constexpr int kPrepT = 64;
 __global__ void __launch_bounds__(256)
 prep_f32_kernel(const float* a, long long m, long long n, long long lda, float* at, long long ldt,
-                __nv_bfloat16* a3, long long seg, float* acopy, long long ldc, const int* cancel) {
+                uint8_t* a3, long long ntp, long long part_bytes, float* acopy, long long ldc, const int* cancel) {
     pdl_trigger();
     pdl_wait();
     if (cancel && *cancel) return;
@@ -752,16 +718,18 @@ prep_f32_kernel(const float* a, long long m, long long n, long long lda, float* 
         const long long i = i0 + r, j = j0 + c4;
 #pragma unroll
         for (int q = 0; q < 4; ++q) tile[r][c4 + q] = v[k][q];
-        if (i >= m) continue;
-        if (a3 && j < seg) {
+        if (a3 && (j >> 6) < ntp) {  // the grid covers every tile of the copy; padding is written as zero
             __nv_bfloat16 h[4], md[4], lo[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) split3(v[k][q], h[q], md[q], lo[q]);
-            __nv_bfloat16* dst = a3 + i * 3 * seg + j;
-            *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(h);
-            *reinterpret_cast<uint2*>(dst + seg) = *reinterpret_cast<const uint2*>(md);
-            *reinterpret_cast<uint2*>(dst + 2 * seg) = *reinterpret_cast<const uint2*>(lo);
+            const int rt = (int)(i & (kTileM - 1)), cc = (int)(j & 63);
+            const size_t off = ((size_t)((i >> 7) * ntp + (j >> 6)) << 14) + (size_t)rt * 128 +
+                               ((size_t)((cc >> 3) ^ (rt & 7)) << 4) + (size_t)(cc & 7) * 2;
+            *reinterpret_cast<uint2*>(a3 + off) = *reinterpret_cast<const uint2*>(h);
+            *reinterpret_cast<uint2*>(a3 + part_bytes + off) = *reinterpret_cast<const uint2*>(md);
+            *reinterpret_cast<uint2*>(a3 + 2 * part_bytes + off) = *reinterpret_cast<const uint2*>(lo);
         }
+        if (i >= m) continue;
         if (acopy && j < ldc)
             *reinterpret_cast<float4*>(acopy + i * ldc + j) = make_float4(v[k][0], v[k][1], v[k][2], v[k][3]);
     }
@@ -793,6 +761,68 @@ __global__ void split_panel_kernel(const float* q, long long ldq, long long rows
         q3[j * ldq3 + i] = h;
         q3[(ellp + j) * ldq3 + i] = md;
         q3[(2 * ellp + j) * ldq3 + i] = lo;
+    }
+}
+
+// Tiled bf16 copy of A for the sketch products (and, with three parts, the
+// exact splits A = A_h + A_m + A_l of the projection): tile (I, J) holds rows
+// 128 I .. 128 I + 127 and columns 64 J .. 64 J + 63 (zero beyond m, n) in 16 KB
+// at byte ((I ntp + J) << 14) of each part, laid out as a 128-byte-swizzled TMA
+// box would land in shared memory: row r at 128 r, its 16-byte chunk c at
+// chunk position c ^ (r mod 8). A product then moves each stage of A with one
+// contiguous bulk copy, and the same tiles serve as the K-major operand of A X
+// (128 rows x 64 K) and as the MN-major operand of A^T Y (64-column atoms of
+// 128 K rows). ntp (tiles per row block) is even, so 128-column blocks are
+// whole pairs. A block converts 128 rows x 512 columns: 128 threads per row,
+// four columns each (2 KB of FP32 read per row, 128-byte lines written).
+template <typename TI, int NP>
+__global__ void __launch_bounds__(256)
+cast_tiled_kernel(const TI* a, long long m, long long n, long long lda, uint8_t* out, long long ntp,
+                  long long part_bytes, const int* cancel) {
+    pdl_trigger();
+    pdl_wait();
+    if (cancel && *cancel) return;
+    const long long I = blockIdx.y;
+    const int half = threadIdx.x >> 7, t = threadIdx.x & 127;
+    const long long c = (long long)blockIdx.x * 512 + 4 * t;  // first of this thread's four columns
+    const long long J = c >> 6;
+    if (J >= ntp) return;
+    const int cc = (int)(c & 63);
+    const bool vec = sizeof(TI) == 4 && (reinterpret_cast<uintptr_t>(a) & 15) == 0 && (lda & 3) == 0;
+    uint8_t* tile = out + ((I * ntp + J) << 14);
+    for (int r = half; r < kTileM; r += 2) {
+        const long long row = I * kTileM + r;
+        float v[4];
+        if (row < m && vec && c + 3 < n) {
+            const float4 f = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(a) + row * lda + c);
+            v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = 0.f;
+        }
+        const size_t off = (size_t)r * 128 + ((size_t)(((cc >> 3) ^ (r & 7))) << 4) + (size_t)(cc & 7) * 2;
+        if (NP == 1) {
+            __nv_bfloat16 h[4];
+            if (row < m && vec && c + 3 < n) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) h[q] = to_bf16(v[q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) h[q] = (row < m && c + q < n) ? to_bf16(a[row * lda + c + q]) : to_bf16(0.f);
+            }
+            *reinterpret_cast<uint2*>(tile + off) = *reinterpret_cast<const uint2*>(h);
+        } else {
+            if (!(row < m && vec && c + 3 < n)) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = (row < m && c + q < n) ? (float)a[row * lda + c + q] : 0.f;
+            }
+            __nv_bfloat16 h[4], md[4], lo[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) split3(v[q], h[q], md[q], lo[q]);
+            *reinterpret_cast<uint2*>(tile + off) = *reinterpret_cast<const uint2*>(h);
+            *reinterpret_cast<uint2*>(tile + part_bytes + off) = *reinterpret_cast<const uint2*>(md);
+            *reinterpret_cast<uint2*>(tile + 2 * part_bytes + off) = *reinterpret_cast<const uint2*>(lo);
+        }
     }
 }
 
@@ -876,7 +906,8 @@ cudaError_t tc_launch(const void* a, bool tf32, long long mtot, long long ktot_s
                       long long brows_k, int nparts, int trans, int64_t ell, int64_t ellp, void* part,
                       int* tile_cnt, void* c,
                       ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel, cudaStream_t st,
-                      int kgroup, TcPieces* pieces) {
+                      int kgroup, TcPieces* pieces, const uint8_t* a_tiles = nullptr, long long a_ntp = 0,
+                      long long a_seg_bytes = 0) {
     const Plan pl = make_plan(mtot, ktot_seg, kseg, tf32, num_sms, kgroup);
     const int ke = tf32 ? 32 : 64;  // K elements per 128-byte row
     const int nb = nparts * (int)ellp;
@@ -913,6 +944,11 @@ cudaError_t tc_launch(const void* a, bool tf32, long long mtot, long long ktot_s
     }
     p.a_boxes = a_boxes;
     p.a_box_cols = a_box_cols;
+    p.a_tiles = a_tiles;
+    p.a_ntp = a_ntp;
+    p.a_seg_bytes = a_seg_bytes;
+    if (a_tiles && (tf32 || (reinterpret_cast<uintptr_t>(a_tiles) & 15) != 0))
+        return cudaErrorInvalidValue;
     p.b_boxes = nb > 256 ? 2 : 1;
     p.b_box_rows = nb / p.b_boxes;
     CUtensorMap map_b;
@@ -960,10 +996,11 @@ int64_t tc_partial_elems(int64_t m, int64_t n, int64_t ellp, int64_t ldm, int64_
     int64_t best = 0;
     for (int trans = 0; trans < 2; ++trans)
         for (int tf = 0; tf < 2; ++tf)
-            for (int kseg : {1, 3}) {
-                const Plan pl = make_plan(trans ? n : m, trans ? m : n, kseg, tf != 0, num_sms, 1);
-                best = std::max<int64_t>(best, pl.mtiles * pl.maxp * ellp * kTileM);
-            }
+            for (int kseg : {1, 2, 3})
+                for (int kgroup : {1, 2}) {
+                    const Plan pl = make_plan(trans ? n : m, trans ? m : n, kseg, tf != 0, num_sms, kgroup);
+                    best = std::max<int64_t>(best, pl.mtiles * pl.maxp * ellp * kTileM);
+                }
     return best;
 }
 
@@ -1001,19 +1038,61 @@ cudaError_t launch_sketch_tc(const void* a, ElemType ta, int64_t m, int64_t n, i
                      sketch_kgroup(ellp), pieces);
 }
 
-cudaError_t launch_project_split_tc(const void* a3, int64_t m, int64_t n, int64_t seg, const void* q3, int64_t ldq,
-                                    int64_t ell, int64_t ellp, void* part, int* tile_cnt, void* w, ElemType tw,
-                                    int64_t ldw, int num_sms, int* flags, const int* cancel, cudaStream_t st,
-                                    TcPieces* pieces) {
-    if (ellp % 16 != 0 || ellp < 16 || ellp > 128 || ell > ellp || seg % 64 != 0) return cudaErrorInvalidValue;
+int64_t tiled_ntp(int64_t n) { return ((n + 63) / 64 + 1) / 2 * 2; }
+
+int64_t tiled_part_bytes(int64_t m, int64_t n) { return ((m + kTileM - 1) / kTileM) * tiled_ntp(n) * 16384; }
+
+cudaError_t launch_cast_tiled(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, void* out, int nparts,
+                              const int* cancel, cudaStream_t st) {
+    if (m < 1 || n < 1 || lda < n || !out || (reinterpret_cast<uintptr_t>(out) & 15) != 0) return cudaErrorInvalidValue;
+    if (nparts != 1 && !(nparts == 3 && ta == T_F32)) return cudaErrorInvalidValue;
+    const int64_t ntp = tiled_ntp(n), mt = (m + kTileM - 1) / kTileM;
+    if (mt > 65535) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((ntp + 7) / 8), (unsigned)mt);
+    const long long pb = tiled_part_bytes(m, n);
+    uint8_t* o = static_cast<uint8_t*>(out);
+    count_launch();
+    cudaError_t e;
+    if (ta == T_F64)
+        e = launch_pdl(cast_tiled_kernel<double, 1>, grid, dim3(256), (size_t)0, st, static_cast<const double*>(a),
+                       (long long)m, (long long)n, (long long)lda, o, (long long)ntp, pb, cancel);
+    else if (nparts == 1)
+        e = launch_pdl(cast_tiled_kernel<float, 1>, grid, dim3(256), (size_t)0, st, static_cast<const float*>(a),
+                       (long long)m, (long long)n, (long long)lda, o, (long long)ntp, pb, cancel);
+    else
+        e = launch_pdl(cast_tiled_kernel<float, 3>, grid, dim3(256), (size_t)0, st, static_cast<const float*>(a),
+                       (long long)m, (long long)n, (long long)lda, o, (long long)ntp, pb, cancel);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_sketch_tc_tiled(const void* a_tiles, int64_t m, int64_t n, int trans, const void* x, int64_t ldx,
+                                   int64_t ell, int64_t ellp, void* part, int* tile_cnt, void* c, ElemType tcout,
+                                   int64_t ldc, int num_sms, int* flags, const int* cancel, cudaStream_t st,
+                                   TcPieces* pieces, int nsegs) {
+    if (ellp % 16 != 0 || ellp < 16 || ellp > 128 || ell > ellp || nsegs < 1 || nsegs > 3) return cudaErrorInvalidValue;
     cudaError_t e = get_encoder();
     if (e != cudaSuccess) return e;
-    CUtensorMap map_a;
-    e = encode_2d(&map_a, a3, false, 3 * seg, m, 3 * seg, 64u, kTileM, CU_TENSOR_MAP_SWIZZLE_128B);
+    CUtensorMap unused{};
+    const uint8_t* at = static_cast<const uint8_t*>(a_tiles);
+    return tc_launch(a_tiles, false, trans ? n : m, trans ? m : n, nsegs, 0, unused, 1, 0, x, ldx, trans ? m : n, 1, trans,
+                     ell, ellp, part, tile_cnt, c, tcout, ldc, num_sms, flags, cancel, st, sketch_kgroup(ellp), pieces,
+                     at, tiled_ntp(n), tiled_part_bytes(m, n));
+}
+
+cudaError_t launch_project_split_tc_tiled(const void* a3, int64_t m, int64_t n, const void* q3, int64_t ldq,
+                                          int64_t ell, int64_t ellp, void* part, int* tile_cnt, void* w, ElemType tw,
+                                          int64_t ldw, int num_sms, int* flags, const int* cancel, cudaStream_t st,
+                                          TcPieces* pieces) {
+    if (ellp % 16 != 0 || ellp < 16 || ellp > 128 || ell > ellp) return cudaErrorInvalidValue;
+    cudaError_t e = get_encoder();
     if (e != cudaSuccess) return e;
-    // one box per stage: a K chunk must not run from one split segment into the next
-    return tc_launch(a3, false, m, n, 3, seg, map_a, 1, 0, q3, ldq, n, 3, 0, ell, ellp, part, tile_cnt, w, tw, ldw,
-                     num_sms, flags, cancel, st, 1, pieces);
+    CUtensorMap unused{};
+    // the K chunks of each split segment stay inside it: the segment's tiles are
+    // kgroup-aligned (ntp is even)
+    const int kgroup = sketch_kgroup(3 * ellp);
+    return tc_launch(a3, false, m, n, 3, 0, unused, 1, 0, q3, ldq, n, 3, 0, ell, ellp, part, tile_cnt, w, tw, ldw,
+                     num_sms, flags, cancel, st, kgroup, pieces, static_cast<const uint8_t*>(a3), tiled_ntp(n),
+                     tiled_part_bytes(m, n));
 }
 
 cudaError_t launch_wait_probe(int* flags, unsigned long long limit_ns, cudaStream_t st) {
@@ -1039,35 +1118,27 @@ cudaError_t launch_copy_f32_padded(const float* a, int64_t m, int64_t n, int64_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_cast_bf16_split(const float* a, int64_t m, int64_t n, int64_t lda, void* a3, int64_t seg,
-                                   const int* cancel, cudaStream_t st) {
-    if (seg % 64 != 0 || seg < n) return cudaErrorInvalidValue;
-    const int blocks = (int)std::min<long long>(m, 16LL * device_sms());  // 16 row blocks per SM
-    count_launch();
-    {
-        cudaError_t pe_ = launch_pdl(cast_bf16_split_kernel, dim3(blocks), dim3(256), (size_t)(0), st, a, m, n, lda, static_cast<__nv_bfloat16*>(a3), seg, cancel);
-        if (pe_ != cudaSuccess) return pe_;
-    }
-    return cudaGetLastError();
-}
-
 cudaError_t launch_prep_f32(const float* a, int64_t m, int64_t n, int64_t lda, float* at, int64_t ldt, void* a3,
-                            int64_t seg, float* acopy, int64_t ldc, const int* cancel, cudaStream_t st) {
+                            float* acopy, int64_t ldc, const int* cancel, cudaStream_t st) {
     if (m < 1 || n < 1 || lda < n) return cudaErrorInvalidValue;
     // every vector store stays inside its row: the tiles cover columns up to
     // round_up(., 64) and the strides are multiples of 64 / 4
     if (at && (ldt % 64 != 0 || ldt < m || reinterpret_cast<uintptr_t>(at) % 16 != 0)) return cudaErrorInvalidValue;
-    if (a3 && (seg % 64 != 0 || seg < n || reinterpret_cast<uintptr_t>(a3) % 8 != 0)) return cudaErrorInvalidValue;
+    if (a3 && reinterpret_cast<uintptr_t>(a3) % 16 != 0) return cudaErrorInvalidValue;
     if (acopy && (ldc % 4 != 0 || ldc < n || ldc > (n + kPrepT - 1) / kPrepT * kPrepT ||
                   reinterpret_cast<uintptr_t>(acopy) % 16 != 0))
         return cudaErrorInvalidValue;
-    const dim3 grid((unsigned)((n + kPrepT - 1) / kPrepT), (unsigned)((m + kPrepT - 1) / kPrepT), 1);
+    // with a3, every tile of the tiled copy (128-row blocks, ntp column tiles) is written
+    const int64_t ntp = tiled_ntp(n);
+    const int64_t gx = a3 ? ntp : (n + kPrepT - 1) / kPrepT;
+    const int64_t gy = a3 ? (m + kTileM - 1) / kTileM * (kTileM / kPrepT) : (m + kPrepT - 1) / kPrepT;
+    const dim3 grid((unsigned)gx, (unsigned)gy, 1);
     if (grid.y > 65535u) return cudaErrorInvalidValue;
     count_launch();
     {
         cudaError_t pe_ = launch_pdl(prep_f32_kernel, grid, dim3(256), (size_t)0, st, a, (long long)m, (long long)n,
-                                     (long long)lda, at, (long long)ldt, static_cast<__nv_bfloat16*>(a3),
-                                     (long long)seg, acopy, (long long)ldc, cancel);
+                                     (long long)lda, at, (long long)ldt, static_cast<uint8_t*>(a3), (long long)ntp,
+                                     (long long)tiled_part_bytes(m, n), acopy, (long long)ldc, cancel);
         if (pe_ != cudaSuccess) return pe_;
     }
     return cudaGetLastError();
@@ -1083,25 +1154,6 @@ cudaError_t launch_split_panel(const float* q, int64_t ldq, int64_t rows, int64_
                                                ldq3, cancel);
         if (pe_ != cudaSuccess) return pe_;
     }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_cast_bf16(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, void* abf,
-                             int64_t ldb, const int* cancel, cudaStream_t st) {
-    const int blocks = (int)std::min<long long>(m, 16LL * device_sms());  // 16 row blocks per SM
-    count_launch();
-    if (ta == T_F32)
-        {
-            cudaError_t pe_ = launch_pdl(cast_bf16_kernel<float>, dim3(blocks), dim3(256), (size_t)(0), st, static_cast<const float*>(a), m, n, lda,
-                                                        static_cast<__nv_bfloat16*>(abf), ldb, cancel);
-            if (pe_ != cudaSuccess) return pe_;
-        }
-    else
-        {
-            cudaError_t pe_ = launch_pdl(cast_bf16_kernel<double>, dim3(blocks), dim3(256), (size_t)(0), st, static_cast<const double*>(a), m, n, lda,
-                                                         static_cast<__nv_bfloat16*>(abf), ldb, cancel);
-            if (pe_ != cudaSuccess) return pe_;
-        }
     return cudaGetLastError();
 }
 

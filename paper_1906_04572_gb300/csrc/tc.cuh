@@ -31,10 +31,34 @@ cudaError_t launch_sketch_tc(const void* a, ElemType ta, int64_t m, int64_t n, i
                              ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel,
                              cudaStream_t st, TcPieces* pieces = nullptr);
 
-// abf[i * ldb + j] = bf16(A[i * lda + j]) (round to nearest even); columns
-// [n, ldb) are zero.
-cudaError_t launch_cast_bf16(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, void* abf,
-                             int64_t ldb, const int* cancel, cudaStream_t st);
+// Tiled bf16 copy of A (m x n, row stride lda, FP32 or FP64): tile (I, J) =
+// rows 128 I.., columns 64 J.. (zero beyond m, n), 16 KB at byte
+// ((I * tiled_ntp(n) + J) << 14) of each part, in the layout a 128-byte-swizzled
+// TMA box of it takes in shared memory. nparts = 1: bf16(A) (round to nearest
+// even); nparts = 3 (FP32 A): the exact splits A_h, A_m, A_l, one part each,
+// tiled_part_bytes(m, n) apart. `out` 16-byte aligned.
+int64_t tiled_ntp(int64_t n);
+int64_t tiled_part_bytes(int64_t m, int64_t n);
+cudaError_t launch_cast_tiled(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, void* out, int nparts,
+                              const int* cancel, cudaStream_t st);
+// launch_sketch_tc with A given as its tiled bf16 copy (launch_cast_tiled):
+// every stage of A is one contiguous bulk copy. nsegs > 1 multiplies by the
+// sum of the copy's first nsegs parts (A_h + A_m: A to about 16 significant
+// bits instead of 8), each part a K segment of the same accumulation.
+cudaError_t launch_sketch_tc_tiled(const void* a_tiles, int64_t m, int64_t n, int trans, const void* x, int64_t ldx,
+                                   int64_t ell, int64_t ellp, void* part, int* tile_cnt, void* c, ElemType tcout,
+                                   int64_t ldc, int num_sms, int* flags, const int* cancel, cudaStream_t st,
+                                   TcPieces* pieces = nullptr, int nsegs = 1);
+// FP32-accurate W = A Q on the tensor cores by exact three-way bf16 splits:
+// a3 is the tiled copy of A with its three parts A_h, A_m, A_l
+// (launch_cast_tiled with nparts = 3), q3 a bf16 panel of 3 * ellp columns
+// [Q_h | Q_m | Q_l] (ld ldq). Products of bf16 parts are exact and accumulate
+// in FP32, so W = the sum of the nine part products carries the rounding of an
+// FP32 dot product. W: panel (ell columns, type tw, ld ldw).
+cudaError_t launch_project_split_tc_tiled(const void* a3, int64_t m, int64_t n, const void* q3, int64_t ldq,
+                                          int64_t ell, int64_t ellp, void* part, int* tile_cnt, void* w, ElemType tw,
+                                          int64_t ldw, int num_sms, int* flags, const int* cancel, cudaStream_t st,
+                                          TcPieces* pieces = nullptr);
 
 // One warp holds tensor memory while it waits on an mbarrier nothing arrives
 // on; after about limit_ns it sets flags[FLAG_TIMEOUT], frees the tensor
@@ -49,27 +73,13 @@ bool tma_rows_aligned(const void* a, int64_t lda, int elem_bytes);
 cudaError_t launch_copy_f32_padded(const float* a, int64_t m, int64_t n, int64_t lda, float* out, int64_t ldb,
                                    cudaStream_t st);
 
-// FP32-accurate W = A Q on the tensor cores by exact three-way bf16 splits:
-// a3 holds rows [A_h | A_m | A_l] (each segment `seg` elements, seg a multiple
-// of 64, zero beyond n), q3 is a bf16 panel of 3 * ellp columns
-// [Q_h | Q_m | Q_l] (ld ldq). Products of bf16 parts are exact and
-// accumulate in FP32, so W = sum of the nine part products carries the
-// rounding of an FP32 dot product. W: panel (ell columns, type tw, ld ldw).
-cudaError_t launch_project_split_tc(const void* a3, int64_t m, int64_t n, int64_t seg, const void* q3, int64_t ldq,
-                                    int64_t ell, int64_t ellp, void* part, int* tile_cnt, void* w, ElemType tw,
-                                    int64_t ldw,
-                                    int num_sms, int* flags, const int* cancel, cudaStream_t st,
-                                    TcPieces* pieces = nullptr);
-// Writes a3 (rows of [A_h | A_m | A_l]) from FP32 A.
-cudaError_t launch_cast_bf16_split(const float* a, int64_t m, int64_t n, int64_t lda, void* a3, int64_t seg,
-                                   const int* cancel, cudaStream_t st);
 // One pass over FP32 A (m x n, row stride lda) writing any non-null of: at =
 // A^T (n rows of stride ldt, ldt a multiple of 64 and >= m; columns
-// [m, round_up(m, 64)) zero), a3 (as launch_cast_bf16_split) and a row-major
-// copy acopy (row stride ldc, a multiple of 4 in [n, round_up(n, 64)], zero
-// beyond n).
+// [m, round_up(m, 64)) zero), a3 (as launch_cast_tiled with three parts) and a
+// row-major copy acopy (row stride ldc, a multiple of 4 in [n, round_up(n, 64)],
+// zero beyond n).
 cudaError_t launch_prep_f32(const float* a, int64_t m, int64_t n, int64_t lda, float* at, int64_t ldt, void* a3,
-                            int64_t seg, float* acopy, int64_t ldc, const int* cancel, cudaStream_t st);
+                            float* acopy, int64_t ldc, const int* cancel, cudaStream_t st);
 // Writes q3 = [Q_h | Q_m | Q_l] from an FP32 panel (ell valid columns of ellp).
 cudaError_t launch_split_panel(const float* q, int64_t ldq, int64_t rows, int64_t ell, int64_t ellp, void* q3,
                                int64_t ldq3, const int* cancel, cudaStream_t st);

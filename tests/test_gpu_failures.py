@@ -132,6 +132,9 @@ def test_device_wait_runs_out_and_the_context_stays_usable():
         out = c.factor(a, 20, 10, 1, "bf16")
         assert c.sync() == 0
         torch.cuda.synchronize()
-        u, t, vv = (out[x].double() for x in ("U", "T", "V"))
-        e = float(torch.linalg.norm(a.double() - u @ t @ vv.T) / torch.linalg.norm(a.double()))
-        assert e < 1e-2
+    # bitwise the result of the same call on a context that never timed out
+    with Context(0) as fresh:
+        ref = fresh.factor(a, 20, 10, 1, "bf16")
+        torch.cuda.synchronize()
+    for x in ("U", "T", "V", "perm"):
+        assert torch.equal(out[x], ref[x]), x

@@ -257,3 +257,61 @@ def test_serving_mixed_results_equal_alone_and_in_the_mix(ctx, prec):
         assert st == corutv.OK and lat > 0
         for name, x in zip(("U", "T", "V", "perm"), bufs[i]):
             assert np.array_equal(host(x), alone[i][name]), f"request {i}: {name} differs from the lone run"
+
+
+@pytest.mark.parametrize("spectrum", ["c2", "c3"])
+@pytest.mark.parametrize("prec,u_p", [("f32", 2.0 ** -24), ("tf32", 2.0 ** -10)])
+def test_power_form_one_qr_per_round(ctx, spectrum, prec, u_p):
+    """power_form 1 (X = qr(A^T (A X)), C1 used as it is) on the spectra of
+    the 8000 x 6000 (sigma_i = i^-2, i <= 200) and 20000 x 20000 (sigma_i =
+    exp(-i/20)) workloads, 2000 x 1500, q = 2: the error within the precision's
+    budget of the FP64 oracle's, both its re-orthonormalised form and the
+    printed loop without re-orthonormalisation (equal in exact arithmetic)."""
+    m, n, k, p, q = 2000, 1500, 50, 10, 2
+    sigma = np.arange(1, 201) ** -2.0 if spectrum == "c2" else synth.c3_sigma(n)
+    a = synth.spectrum_matrix(m, n, sigma, 0.0, 17)
+    a32 = a.astype(np.float32)
+    a64 = a32.astype(np.float64)
+    psi = synth.gaussian_psi(n, k + p, seed=18)
+    na = np.linalg.norm(a64)
+    budget = 4 * u_p * np.sqrt(k + p) * np.linalg.norm(a64, 2) / na
+    e_or = {}
+    for lit in (False, True):
+        r = oracle.corutv(a64, k, p, q, psi, literal=lit)
+        e_or[lit] = np.linalg.norm(a64 - r["U"] @ r["T"] @ r["V"].T) / na
+    e = {}
+    for pf in (0, 1):
+        out = ctx.factor(dev(a32, torch.float32), k, p, q, prec, psi=dev(psi), power_form=pf)
+        assert ctx.sync() == 0
+        u, t, v = (host(out[x]) for x in ("U", "T", "V"))
+        e[pf] = np.linalg.norm(a64 - u @ t @ v.T) / na
+        assert np.linalg.norm(u.T @ u - np.eye(k + p)) < 1e-5
+    print(spectrum, prec, "pf0", e[0], "pf1", e[1], "oracle", e_or[False], "literal", e_or[True])
+    for lit in (False, True):
+        assert e[1] <= e_or[lit] + budget
+    assert e[0] <= e_or[False] + budget
+
+
+def test_bf16_last_round_refinement_reaches_fp64_error(ctx):
+    """BF16 sketches on the spectrum of the 20000 x 20000 workload: with the
+    last power round on A_h + A_m (the default) the reconstruction error is
+    within 1 % of the FP64 oracle's (equal error); with every round on A_h it
+    is worse, and both stay within the bf16 budget."""
+    m, n, k, p, q = 3000, 2500, 100, 10, 2
+    a = synth.spectrum_matrix(m, n, synth.c3_sigma(min(m, n)), 0.0, 11)
+    a32 = a.astype(np.float32)
+    a64 = a32.astype(np.float64)
+    psi = synth.gaussian_psi(n, k + p, seed=3)
+    ref = oracle.corutv(a64, k, p, q, psi)
+    na = np.linalg.norm(a64)
+    e_or = np.linalg.norm(a64 - ref["U"] @ ref["T"] @ ref["V"].T) / na
+    e = {}
+    for last in (0, 1):
+        out = ctx.factor(dev(a32, torch.float32), k, p, q, "bf16", psi=dev(psi), bf16_last_round=last)
+        assert ctx.sync() == 0
+        u, t, v = (host(out[x]) for x in ("U", "T", "V"))
+        e[last] = np.linalg.norm(a64 - u @ t @ v.T) / na
+    print("bf16 last round x2", e[0] / e_or, "plain", e[1] / e_or)
+    budget = 4 * 2.0 ** -8 * np.sqrt(k + p) * np.linalg.norm(a64, 2) / na
+    assert e[1] <= e_or + budget
+    assert e[0] <= 1.01 * e_or
