@@ -264,6 +264,24 @@ def rel_error(A, out):
     return float(torch.linalg.norm(A.double() - approx) / torch.linalg.norm(A.double()))
 
 
+def error_same_psi(ctx, A, k, p, q, prec, **kw):
+    """||A - U T V^T||_F / ||A||_F of one factorisation with the test matrix
+    of (seed 0, stream 0): every variant's error is taken on the same A and
+    Psi (the spread between Psi draws is larger than the precision effects)."""
+    import torch
+    from paper_1906_04572_gb300 import corutv
+    m, n = A.shape
+    ell = k + p
+    out = {"U": torch.empty((m, ell), device=A.device, dtype=A.dtype),
+           "T": torch.empty((ell, ell), device=A.device, dtype=A.dtype),
+           "V": torch.empty((n, ell), device=A.device, dtype=A.dtype)}
+    corutv.corutv_factor(ctx.handle, A, k, p, q, prec, out["U"], out["T"], out["V"], None, seed=0, stream=0, **kw)
+    assert ctx.sync() == 0
+    e = rel_error(A, out)
+    del out
+    return e
+
+
 def time_factor(ctx, A, k, p, q, prec, steps, warmup, world, profile=False, d_mode=0, t_lower=0, power_form=0,
                 bf16_last_round=0):
     """Device-timed steps of corutv_factor with outputs preallocated."""
@@ -478,9 +496,10 @@ def c2_lines(ctx, device, steps):
             A = torch.from_numpy(f.a).to(device=device, dtype=dt)
             st = max(2, steps // (8 if prec == "f64" else 2))
             ms, out, _ = time_factor(ctx, A, 50, 10, q, prec, st, 3, 1)
+            del out
             res[f"q{q}_{prec}"] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, "solves_per_s": 1e3 / ms,
-                                   "e_rel": rel_error(A, out), "steps": st}
-            del A, out
+                                   "e_rel": error_same_psi(ctx, A, 50, 10, q, prec), "steps": st}
+            del A
     res["workload"] = "c2_8000x6000_k50_l60 (sigma_i = i^-2, i <= 200, + N(0, 1e-4^2))"
     return res
 
@@ -495,9 +514,9 @@ def power_forms(ctx, A, k, p, q, steps, e_fp64):
         for pf in (0, 1):
             st = 2 if prec == "f32" else steps
             ms, out, _ = time_factor(ctx, A, k, p, q, prec, st, 1, 1, power_form=pf)
-            e = rel_error(A, out)
-            res[f"{prec}_pf{pf}"] = {"ms": ms, "e_rel": e, "e_ratio_to_fp64": (e / e_fp64) if e_fp64 else None}
             del out
+            e = error_same_psi(ctx, A, k, p, q, prec, power_form=pf)
+            res[f"{prec}_pf{pf}"] = {"ms": ms, "e_rel": e, "e_ratio_to_fp64": (e / e_fp64) if e_fp64 else None}
     return res
 
 
@@ -603,8 +622,8 @@ def run_ours(args):
     sampler.stop()
     ms_max = max_over_ranks(ms, world, device)
     value = world * flops / (ms_max / 1e3) / 1e12
-    err = rel_error(A, out)
     del out
+    err = error_same_psi(ctx, A, k, p, q, prec)
     # a second, profiled pass: CUDA events around every stage (the sketch
     # launches among them) for the stage split and the roofline figure
     psteps = max(3, min(args.steps // 2, 10))
@@ -631,24 +650,25 @@ def run_ours(args):
         A64 = A.double()
         st64 = 2 if args.workload == "c3" else max(2, args.steps // 10)
         ms64, out64, _ = time_factor(ctx, A64, k, p, q, "f64", st64, 1, world)
-        err64 = rel_error(A64, out64)
+        del out64
+        err64 = error_same_psi(ctx, A64, k, p, q, "f64")
         fp64 = {"tflops": flops / (ms64 / 1e3) / 1e12, "solves_per_s": 1e3 / ms64, "ms_per_step": ms64,
                 "e_rel": err64, "steps": st64}
-        del A64, out64
+        del A64
         torch.cuda.empty_cache()
     others = {}
     if not args.no_extra and prec in ("bf16", "tf32"):
         for op in ("tf32", "f32") if prec == "bf16" else ("bf16", "f32"):
             st = 3 if op == "f32" else max(3, args.steps // 4)
             ms_o, out_o, _ = time_factor(ctx, A, k, p, q, op, st, 1, world)
-            others[op] = {"ms": ms_o, "tflops": flops / (ms_o / 1e3) / 1e12, "e_rel": rel_error(A, out_o),
-                          "steps": st}
             del out_o
-        # bf16 with the last power round on A_h alone like the others
+            others[op] = {"ms": ms_o, "tflops": flops / (ms_o / 1e3) / 1e12,
+                          "e_rel": error_same_psi(ctx, A, k, p, q, op), "steps": st}
+        # bf16 with the last power round on A_h + A_m (the first two exact bf16 parts of A)
         ms_o, out_o, _ = time_factor(ctx, A, k, p, q, "bf16", max(3, args.steps // 4), 1, world, bf16_last_round=1)
-        others["bf16_plain_last_round"] = {"ms": ms_o, "tflops": flops / (ms_o / 1e3) / 1e12,
-                                           "e_rel": rel_error(A, out_o)}
         del out_o
+        others["bf16_last_round_x2"] = {"ms": ms_o, "tflops": flops / (ms_o / 1e3) / 1e12,
+                                        "e_rel": error_same_psi(ctx, A, k, p, q, "bf16", bf16_last_round=1)}
         if fp64 is not None:
             for v in others.values():
                 v["e_ratio_to_fp64"] = v["e_rel"] / fp64["e_rel"]
@@ -699,7 +719,7 @@ def run_ours(args):
             ms1, out1, _ = time_factor(ctx, A, k, p, q, sp_prec, max(3, args.steps // 4), 2, world, d_mode=1)
             sp[sp_prec] = {"ms": ms1, "solves_per_s": 1e3 / ms1,
                            "tflops_2q2_passes": (2 * q + 2) * 2.0 * m * n * ell / (ms1 / 1e3) / 1e12,
-                           "e_rel": rel_error(A, out1)}
+                           "e_rel": error_same_psi(ctx, A, k, p, q, sp_prec, d_mode=1)}
             del out1
         sp["e_rel_exact_d"] = err
         extra["single_pass"] = sp
@@ -707,7 +727,8 @@ def run_ours(args):
         At = A.t().contiguous()
         ms_l, out_l, _ = time_factor(ctx, At, k, p, q, prec, max(3, args.steps // 4), 2, world, t_lower=1)
         extra["lower_t"] = {"workload": f"{n}x{m} (the same matrix transposed)", "ms": ms_l,
-                            "tflops": flops / (ms_l / 1e3) / 1e12, "e_rel": rel_error(At, out_l),
+                            "tflops": flops / (ms_l / 1e3) / 1e12,
+                            "e_rel": error_same_psi(ctx, At, k, p, q, prec, t_lower=1),
                             "t_lower_triangular": bool(torch.all(torch.triu(out_l["T"], 1) == 0).item())}
         del At, out_l
 

@@ -90,11 +90,11 @@ typedef struct {
                              the same Q1, Q2. Loses the weak directions of C1 to rounding when
                              C1 is an operand of reduced precision (BF16 sketches). Other values
                              -> CORUTV_EINVAL */
-    uint32_t bf16_last_round; /* BF16 sketches of FP32 input with d_mode 0: 0 (default) the two
-                             products of the last power round multiply by A_h + A_m, the first two
-                             exact bf16 parts of A (16 significant bits), the earlier rounds by
-                             A_h; 1: every round by A_h. Ignored otherwise; other values ->
-                             CORUTV_EINVAL */
+    uint32_t bf16_last_round; /* BF16 sketches of FP32 input with d_mode 0: 0 (default) every
+                             round multiplies by A_h = bf16(A); 1: the two products of the last
+                             power round multiply by A_h + A_m, the first two exact bf16 parts of
+                             A (16 significant bits; two more bf16 reads of A). Ignored otherwise;
+                             other values -> CORUTV_EINVAL */
 } corutv_opts;
 
 typedef struct corutv_ctx corutv_ctx;
@@ -138,6 +138,35 @@ corutv_status corutv_sync(corutv_ctx* ctx);
 corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, int64_t m, int64_t n,
                             int64_t lda, const corutv_opts* opts, void* U, int64_t ldu, void* T,
                             void* V, int64_t ldv, int32_t* perm);
+
+/* Row-partitioned CoR-UTV: the form of Algorithm 1 for a matrix whose rows are
+ * spread over several processes (GPUs), A = [A_1; A_2; ...], each rank holding
+ * A_i (m_local x n, lda) on its own device. Every pass over A is local; the
+ * only exchanges are the sums that reduce over A's rows, which the library
+ * hands to the caller's `allreduce`:
+ *   - the ell x ell Gram matrix of each thin QR of C1 = A X (eq. 4; C1 stays
+ *     row-distributed, Q1_i = C1_i R^-1), FP64;
+ *   - C2 = sum_i A_i^T Q1_i (eq. 5; n x ell, then replicated), in the panel
+ *     arithmetic (FP32 with FP32 data and F32/TF32/BF16 sketches, else FP64);
+ *   - D = sum_i Q1_i^T (A_i Q2) (eq. 7; ell x ell), FP64.
+ * Everything else (Psi, the thin QRs of C2, the pivoted QR of D, T, V) is
+ * computed identically on every rank. Per factorisation the exchanged volume
+ * is (q+1) n ell + (2q+3) ell^2 values (one Gram per CholeskyQR pass), against
+ * (2q+3) m_local n elements of A read locally.
+ * allreduce(buf, count, dtype, user) must replace the `count` values of
+ * `dtype` at `buf` (pinned host memory owned by the library) by their sum over
+ * all ranks, in the same order on every rank, and return CORUTV_OK; the
+ * library calls it synchronously (the device work producing buf has finished)
+ * and the same number of times on every rank.
+ * m_total = sum of the ranks' m_local; each rank needs m_local > ell. U:
+ * this rank's rows of U (m_local x ell, ldu); T, V, perm as in corutv_factor,
+ * identical on all ranks. opts->seed / stream must agree across ranks (Psi is
+ * drawn, not passed); d_mode, t_lower and power_form must be 0.
+ * Device pointers only; returns once enqueued (corutv_sync waits). */
+typedef corutv_status (*corutv_allreduce_fn)(void* buf, int64_t count, corutv_dtype dtype, void* user);
+corutv_status corutv_factor_rows(corutv_ctx* ctx, corutv_dtype dtype, const void* A, int64_t m_local, int64_t n,
+                                 int64_t lda, int64_t m_total, const corutv_opts* opts, corutv_allreduce_fn allreduce,
+                                 void* user, void* U, int64_t ldu, void* T, void* V, int64_t ldv, int32_t* perm);
 
 /* ALM-CoRUTV (Algorithm 2; eq. 13): M = L + S by inexact augmented
  * Lagrange multipliers with the CoR-UTV thresholding operator

@@ -45,6 +45,9 @@ class Request(ctypes.Structure):
                 ("ldu", ctypes.c_int64), ("ldv", ctypes.c_int64), ("perm", ctypes.c_void_p)]
 
 
+# corutv_allreduce_fn: (buf, count, dtype, user) -> status
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p)
+
 _lib = None
 _lock = threading.Lock()
 
@@ -62,6 +65,10 @@ _SIGS = {
                      ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                      ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "corutv_factor_rows": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                            ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(Opts), ALLREDUCE_FN, ctypes.c_void_p,
+                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                            ctypes.c_void_p], ctypes.c_int),
     "corutv_submit": ([ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "corutv_poll": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)],
                     ctypes.c_int),
@@ -215,6 +222,46 @@ def corutv_factor(ctx, A, k: int, p: int, q: int, prec="f64", U=None, T=None, V=
     st = load().corutv_factor(ctx, _dtype_code(A), _ptr(A), m, n, _rowmajor_ld(A), ctypes.byref(o),
                               _ptr(U), _rowmajor_ld(U) if U is not None else 0, _ptr(T), _ptr(V),
                               _rowmajor_ld(V) if V is not None else 0, _ptr(perm))
+    return _check(ctx, st)
+
+
+def allreduce_callback(sum_fn):
+    """A corutv_allreduce_fn from a Python function sum_fn(array) that
+    replaces a 1-D numpy array (float64 or float32, a view of the library's
+    host buffer) by its sum over the ranks. Keep the returned object alive
+    for as long as the library may call it."""
+    def cb(buf, count, dtype, user):
+        try:
+            ct = ctypes.c_double if dtype == F64 else ctypes.c_float
+            arr = np.ctypeslib.as_array(ctypes.cast(buf, ctypes.POINTER(ct)), shape=(int(count),))
+            sum_fn(arr)
+            return OK
+        except Exception:  # reported to the library as a failed exchange
+            return ECUDA
+    return ALLREDUCE_FN(cb)
+
+
+def torch_distributed_sum(arr) -> None:
+    """sum_fn for allreduce_callback over the default torch.distributed group
+    (for example gloo): the array is summed in place."""
+    import torch
+    import torch.distributed as dist
+    t = torch.from_numpy(arr)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+
+
+def corutv_factor_rows(ctx, A_local, m_total: int, k: int, p: int, q: int, prec, allreduce, U=None, T=None,
+                       V=None, perm=None, seed: int = 0, stream: int = 0) -> int:
+    """The row-partitioned form: this rank's rows A_local (device), the rows of
+    all ranks m_total; allreduce from allreduce_callback (the same on every
+    rank). U: this rank's rows of U; T, V, perm replicated."""
+    m, n = A_local.shape
+    o = _opts(k, p, q, prec, seed, stream)
+    _use_torch_stream(ctx, A_local)
+    st = load().corutv_factor_rows(ctx, _dtype_code(A_local), _ptr(A_local), m, n, _rowmajor_ld(A_local),
+                                   int(m_total), ctypes.byref(o), allreduce, None, _ptr(U),
+                                   _rowmajor_ld(U) if U is not None else 0, _ptr(T), _ptr(V),
+                                   _rowmajor_ld(V) if V is not None else 0, _ptr(perm))
     return _check(ctx, st)
 
 

@@ -230,7 +230,7 @@ corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64
     if (power_form > 1) return fail(CORUTV_EINVAL, "power_form %u is not supported (0 or 1)", power_form);
     if (bf16_last_round > 1) return fail(CORUTV_EINVAL, "bf16_last_round %u is not supported (0 or 1)", bf16_last_round);
     pl.power_form = (int)power_form;
-    pl.x2_last = pl.split && prec == CORUTV_P_BF16 && bf16_last_round == 0;
+    pl.x2_last = pl.split && prec == CORUTV_P_BF16 && bf16_last_round == 1;
     pl.copy_a = prec == CORUTV_P_TF32 && (!a_aligned || lda % 4 != 0);
     pl.ldc32 = round_up(n, 4);
     pl.ellp = pl.tensor ? round_up(pl.ell, 16) : pl.ell;
@@ -303,13 +303,36 @@ size_t factor_bytes(const FactorPlan& pl) {
     return cv.off;
 }
 
+// The exchange of a row-partitioned factorisation (corutv_factor_rows): sums
+// over the ranks through the caller's callback, on pinned host buffers.
+struct Exchange {
+    corutv_allreduce_fn fn = nullptr;
+    void* user = nullptr;
+    void* host = nullptr;      // pinned staging buffer
+    int64_t total_rows = 0;    // rows of the whole matrix (sizes the Cholesky shift)
+};
+
 struct Exec {
     cudaStream_t st;
     int* flags;
     const int* cancel;
     int num_sms;
     Profiler* prof = nullptr;
+    const Exchange* xch = nullptr;  // set for the rows of a row-partitioned matrix
 };
+
+// buf (device, count elements of type t) <- its sum over the ranks: copied to
+// the pinned staging buffer once the stream has produced it, summed in place by
+// the caller's callback, copied back in stream order.
+corutv_status exchange_sum(const Exec& ex, void* buf, int64_t count, ElemType t) {
+    const size_t bytes = (size_t)count * elem_size(t);
+    CK(cudaMemcpyAsync(ex.xch->host, buf, bytes, cudaMemcpyDeviceToHost, ex.st));
+    CK(cudaStreamSynchronize(ex.st));
+    const corutv_status st = ex.xch->fn(ex.xch->host, count, t == T_F64 ? CORUTV_F64 : CORUTV_F32, ex.xch->user);
+    if (st != CORUTV_OK) return fail(st, "the all-reduce callback returned status %d", (int)st);
+    CK(cudaMemcpyAsync(buf, ex.xch->host, bytes, cudaMemcpyHostToDevice, ex.st));
+    return CORUTV_OK;
+}
 
 // C = A X (am = A_ROWS, R = m, K = n) or A^T Y (am = A_COLS, R = n, K = m) on
 // SIMT cores for A's own m x n, written to the panel `out` (type pl.tp).
@@ -367,16 +390,21 @@ corutv_status gram(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, co
 // (type pl.tp) and, if qc != nullptr, a copy of type tqc.
 corutv_status orth(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, const void* c,
                    int64_t ld, int64_t len, void* q, void* qc, ElemType tqc, int passes = 2,
-                   double* rt_out = nullptr, const TcPieces* pieces = nullptr) {
+                   double* rt_out = nullptr, const TcPieces* pieces = nullptr, bool dist = false) {
     const int64_t ell = pl.ell;
     const ElemType tw = pl.torth, tp = pl.tp;
     ProfScope ps(ex.prof, CORUTV_STAGE_ORTH, ex.st);
+    // a panel whose rows are spread over ranks: each Gram is the sum of the
+    // ranks' Gram matrices, and the shift counts all rows
+    const bool sum = dist && ex.xch;
+    const int64_t rows_all = sum ? ex.xch->total_rows : len;
     void* p1 = passes == 1 ? q : b.tmp;
     void* p1c = passes == 1 ? qc : nullptr;
     // pass 1 (the first reader of c: it adds any pieces the product left and completes c)
     CKS(gram(ex, pl, b, c, ld, c, ld, len, b.g, ex.cancel, tw, pieces, pieces, true));
+    if (sum) CKS(exchange_sum(ex, b.g, ell * ell, T_F64));
     const double u = tw == T_F64 ? 0x1p-53 : 0x1p-24;  // unit roundoff of the Gram arithmetic
-    CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, b.skip, ex.cancel, ex.st, u));
+    CK(launch_cholesky(b.g, ell, rows_all, b.r, ex.flags, b.skip, ex.cancel, ex.st, u));
     if (rt_out) CK(launch_trimul(b.r, nullptr, b.racc, ell, false, nullptr, ex.cancel, ex.st));
     CK(launch_trsm_rows(c, tp, ld, len, ell, b.r, tw, p1, ld, p1c, tqc, ld, ex.cancel, ex.st));
     // extra pass, only after a shifted pass 1. Directions the shifted pass left
@@ -385,19 +413,25 @@ corutv_status orth(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, co
     // the following pass (and well conditioned as they stand for a
     // one-pass intermediate basis).
     CKS(gram(ex, pl, b, p1, ld, p1, ld, len, b.g, b.skip, tw));
-    CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, nullptr, b.skip, ex.st, u, b.defic, 10.0 * (double)ell * u));
+    if (sum) CKS(exchange_sum(ex, b.g, ell * ell, T_F64));  // (summed but unused when the pass is skipped)
+    CK(launch_cholesky(b.g, ell, rows_all, b.r, ex.flags, nullptr, b.skip, ex.st, u, b.defic, 10.0 * (double)ell * u));
     // the extra pass's factor joins the product only if that pass ran
     if (rt_out) CK(launch_trimul(b.r, b.racc, b.racc2, ell, false, b.skip, ex.cancel, ex.st));
     CK(launch_trsm_rows(p1, tp, ld, len, ell, b.r, tw, p1, ld, p1c, tqc, ld, b.skip, ex.st, b.defic));
     if (passes == 1) return rt_out ? fail(CORUTV_EINVAL, "the R factor needs two passes") : CORUTV_OK;
     // pass 2
     CKS(gram(ex, pl, b, b.tmp, ld, b.tmp, ld, len, b.g, ex.cancel, tw));
-    CK(launch_cholesky(b.g, ell, len, b.r, ex.flags, nullptr, ex.cancel, ex.st, u));
+    if (sum) CKS(exchange_sum(ex, b.g, ell * ell, T_F64));
+    CK(launch_cholesky(b.g, ell, rows_all, b.r, ex.flags, nullptr, ex.cancel, ex.st, u));
     // C = Q (R_2 R_extra R_1): rt_out receives that product transposed
     if (rt_out) CK(launch_trimul(b.r, b.racc2, rt_out, ell, true, nullptr, ex.cancel, ex.st));
     CK(launch_trsm_rows(b.tmp, tp, ld, len, ell, b.r, tw, q, ld, qc, tqc, ld, ex.cancel, ex.st));
     return CORUTV_OK;
 }
+
+// U = Q1 Qt is formed from the explicit Qt (qform) for FP32 panels wider than 64
+// columns; otherwise from the reflectors.
+bool explicit_qt(const FactorPlan& pl, ElemType tout) { return pl.tp == T_F32 && tout == T_F32 && pl.ell > 64; }
 
 // Algorithm 1 on device data; leaves Q1, Q2, D, Qt, Rt, perm in the buffers.
 // psi_dev: optional n x ell row-major FP64 test matrix.
@@ -427,7 +461,8 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     // split tiles of a tensor-core product stay pieces until the Gram that
     // first reads the panel adds them (no fix-up tail in the product)
     TcPieces pieces;
-    TcPieces* defer = (pl.tp == T_F32 && pl.torth == T_F32 && pl.tdproj == T_F32) ? &pieces : nullptr;
+    // (a row-partitioned run sums its panels over ranks: no pieces left for a consumer)
+    TcPieces* defer = (pl.tp == T_F32 && pl.torth == T_F32 && pl.tdproj == T_F32 && !ex.xch) ? &pieces : nullptr;
     // A X (a_rows: the output has A's rows, the operand is a panel with A's
     // columns) or A^T Y (the other way round). Algorithm 1's C1 = A X is the
     // first, C2 = A^T Q1 the second; on A^T (the lower-T variant) the two swap.
@@ -462,11 +497,14 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
         if (raw_c1) {
             CK(launch_panel_convert(b.c1, pl.tp, pl.ldm, m, ell, b.q1c, pl.tcomp, pl.ldm, ex.cancel, ex.st));
         } else {
-            CKS(orth(ex, pl, b, b.c1, pl.ldm, m, b.q1, b.q1c, pl.tcomp, it < pl.q ? inner : 2, nullptr, &pieces));
+            CKS(orth(ex, pl, b, b.c1, pl.ldm, m, b.q1, b.q1c, pl.tcomp, it < pl.q ? inner : 2, nullptr, &pieces,
+                     /*dist=*/true));
         }
         pieces = TcPieces();
         // eq. 5 (with C1 -> Q1): C2 = A^T Q1
         CKS(product(pl.tr, b.q1c, b.c2, defer, nsegs));
+        // row-partitioned: C2 = sum over the ranks of A_i^T Q1_i (eq. 5), then replicated
+        if (ex.xch) CKS(exchange_sum(ex, b.c2, ell * pl.ldn, pl.tp));
         if (it < pl.q) {
             CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.x, b.xc, pl.tcomp, inner, nullptr, &pieces));
             pieces = TcPieces();
@@ -479,7 +517,7 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     if (pl.dmode == 1) {
         CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.q2, nullptr, pl.tdproj, 2, b.d, &pieces));
         ProfScope ps(ex.prof, CORUTV_STAGE_QRCP, ex.st);
-        CK(launch_qrcp(b.d, ell, b.qt, b.rt, b.perm, b.refl, ex.cancel, ex.st, /*form_q=*/false));
+        CK(launch_qrcp(b.d, ell, b.qt, b.rt, b.perm, b.refl, ex.cancel, ex.st, explicit_qt(pl, pl.tp)));
         return CORUTV_OK;
     }
     // the non-split projection multiplies A by Q2 in its own arithmetic (a copy
@@ -515,10 +553,12 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     }
     if (pl.tr) CKS(gram(ex, pl, b, b.w, pl.ldn, b.q2, pl.ldn, n, b.d, ex.cancel, pl.tdproj, &pieces, nullptr));
     else CKS(gram(ex, pl, b, b.q1, pl.ldm, b.w, pl.ldm, m, b.d, ex.cancel, pl.tdproj, nullptr, &pieces));
+    // row-partitioned: D = sum over the ranks of Q1_i^T (A_i Q2) (eq. 7)
+    if (ex.xch) CKS(exchange_sum(ex, b.d, ell * ell, T_F64));
     // eq. 8: D P = Qt Rt
     {
         ProfScope ps(ex.prof, CORUTV_STAGE_QRCP, ex.st);
-        CK(launch_qrcp(b.d, ell, b.qt, b.rt, b.perm, b.refl, ex.cancel, ex.st, /*form_q=*/false));
+        CK(launch_qrcp(b.d, ell, b.qt, b.rt, b.perm, b.refl, ex.cancel, ex.st, explicit_qt(pl, pl.tp)));
     }
     return CORUTV_OK;
 }
@@ -532,8 +572,18 @@ corutv_status emit_user(const Exec& ex, const FactorPlan& pl, const FactorBufs& 
     void* uq = pl.tr ? v : u;  // receives Q1 Qt
     void* vq = pl.tr ? u : v;  // receives Q2 P
     const int64_t lduq = pl.tr ? ldv : ldu, ldvq = pl.tr ? ldu : ldv;
-    // Q1 Qt, applied as the QRCP's reflectors to the rows of Q1
-    if (uq) CK(launch_apply_reflectors(b.q1, pl.tp, pl.ldm, pl.m, ell, b.refl, uq, tout, lduq, false, ex.cancel, ex.st));
+    if (uq && explicit_qt(pl, tout)) {
+        // Q1 Qt as a product with the explicit Qt (FP32): for wide Qt the reflector
+        // form below is a long per-row chain (ell reflectors of ell entries each)
+        float* qt32 = static_cast<float*>(b.tmp);
+        CK(launch_copy_small(b.qt, ell, qt32, T_F32, ex.cancel, ex.st));
+        GemmArgs g{A_PANEL, B_SMALL, O_ROWMAJ, T_F32, T_F32, b.q1, pl.ldm, qt32, ell, uq, lduq, 0,
+                   pl.m, ell, ell, 1, ex.cancel};
+        CK(launch_gemm_simt(g, ex.st));
+    } else if (uq) {
+        // Q1 Qt, applied as the QRCP's reflectors to the rows of Q1
+        CK(launch_apply_reflectors(b.q1, pl.tp, pl.ldm, pl.m, ell, b.refl, uq, tout, lduq, false, ex.cancel, ex.st));
+    }
     CK(launch_copy_small(b.rt, ell, t, tout, ex.cancel, ex.st, pl.tr));
     if (vq) CK(launch_gather_v(b.q2, pl.tp, pl.ldn, pl.n, ell, b.perm, vq, tout, ldvq, ex.cancel, ex.st));
     if (perm) CK(cudaMemcpyAsync(perm, b.perm, sizeof(int32_t) * ell, cudaMemcpyDeviceToDevice, ex.st));
@@ -619,6 +669,8 @@ struct corutv_ctx {
     uint64_t next_ticket = 1;
     size_t serving_bytes = 0;
     std::vector<cudaEvent_t> ev_pool;  // events for submit-time ordering (under smu)
+    void* xhost = nullptr;             // pinned staging of the row-partitioned exchanges
+    size_t xcap = 0;
 };
 
 namespace {
@@ -734,6 +786,7 @@ corutv_status corutv_destroy(corutv_ctx* ctx) {
     if (ctx->ws.ptr) cudaFree(ctx->ws.ptr);
     if (ctx->flags) cudaFree(ctx->flags);
     if (ctx->switch_ev) cudaEventDestroy(ctx->switch_ev);
+    if (ctx->xhost) cudaFreeHost(ctx->xhost);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return CORUTV_OK;
@@ -886,6 +939,50 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
         CK(cudaStreamSynchronize(ctx->stream));
         return flags_status(hf);
     }
+    CK(cudaGetLastError());
+    return CORUTV_OK;
+}
+
+corutv_status corutv_factor_rows(corutv_ctx* ctx, corutv_dtype dtype, const void* A, int64_t m_local, int64_t n,
+                                 int64_t lda, int64_t m_total, const corutv_opts* opts, corutv_allreduce_fn allreduce,
+                                 void* user, void* U, int64_t ldu, void* T, void* V, int64_t ldv, int32_t* perm) {
+    CKS(check_ctx(ctx));
+    if (!A || !opts || !T || !allreduce) return fail(CORUTV_EINVAL, "A, opts, T and allreduce must not be NULL");
+    if (dtype != CORUTV_F64 && dtype != CORUTV_F32) return fail(CORUTV_EINVAL, "unknown dtype %d", (int)dtype);
+    if (opts->d_mode != 0 || opts->t_lower != 0 || opts->power_form != 0 || opts->psi)
+        return fail(CORUTV_EINVAL, "the row-partitioned form takes d_mode 0, t_lower 0, power_form 0 and a seeded Psi");
+    if (m_total < m_local || m_local < 1) return fail(CORUTV_EINVAL, "need 1 <= m_local <= m_total");
+    if (opts->k + opts->p >= std::min(m_total, n))
+        return fail(CORUTV_EINVAL, "ell = k + p must be < min(m_total, n)");
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    DeviceGuard guard(ctx->device);
+    if (!is_device_ptr(A) || !is_device_ptr(T) || (U && !is_device_ptr(U)) || (V && !is_device_ptr(V)) ||
+        (perm && !is_device_ptr(perm)))
+        return fail(CORUTV_EINVAL, "corutv_factor_rows takes device pointers only");
+    const ElemType ta = dtype == CORUTV_F64 ? T_F64 : T_F32;
+    FactorPlan pl;
+    // the local block must itself be taller than ell (its thin QR panels hold m_local rows)
+    CKS(make_plan(pl, ta, m_local, n, lda, opts->k, opts->p, opts->q, (corutv_prec)opts->sketch_prec, ctx->num_sms,
+                  reinterpret_cast<uintptr_t>(A) % 16 == 0, 0, false, 0, opts->bf16_last_round));
+    const int64_t ell = pl.ell;
+    if ((U && ldu < ell) || (V && ldv < ell)) return fail(CORUTV_EINVAL, "ldu, ldv must be >= ell");
+    CKS(ensure_ws(ctx, ctx->ws, factor_bytes(pl), ctx->stream));
+    const size_t xbytes = sizeof(double) * (size_t)std::max(ell * ell, ell * pl.ldn);
+    if (ctx->xcap < xbytes) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (ctx->xhost) CK(cudaFreeHost(ctx->xhost));
+        ctx->xhost = nullptr;
+        ctx->xcap = 0;
+        CK(cudaMallocHost(&ctx->xhost, xbytes));
+        ctx->xcap = xbytes;
+    }
+    Carver cv(ctx->ws.ptr);
+    FactorBufs b;
+    carve_factor(cv, pl, b);
+    Exchange xch{allreduce, user, ctx->xhost, m_total};
+    Exec ex{ctx->stream, ctx->flags, nullptr, ctx->num_sms, &ctx->prof, &xch};
+    CKS(run_factor(ex, pl, b, A, nullptr, opts->seed, opts->stream));
+    CKS(emit_user(ex, pl, b, ta, U, ldu, T, V, ldv, perm));
     CK(cudaGetLastError());
     return CORUTV_OK;
 }

@@ -9,6 +9,8 @@
 //  * the gathers of eq. 9 (V = Q2 P, T = Rt).
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace corutv {
@@ -380,10 +382,11 @@ constexpr int kTrsmThreads = kTrsmL * kTrsmRows;
 // the 32 lanes of a warp (8 rows x 4 consecutive columns) hit 32 distinct
 // banks (a stride of 32 rows put a row's four lanes on one bank).
 __host__ __device__ __forceinline__ int trsm_ld(int ell) { return ((ell + 31) & ~31) + 4; }
-template <typename TI, typename TC, typename TQC>
-__global__ void __launch_bounds__(kTrsmThreads)
+template <typename TI, typename TC, typename TQC, int kRows>
+__global__ void __launch_bounds__(kTrsmL * kRows)
 trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* r, TI* q, int64_t ldq,
                  TQC* qc, int64_t ldqc, const int* cancel, const int* defic) {
+    constexpr int kTrsmRows = kRows, kTrsmThreads = kTrsmL * kRows;
     pdl_wait();
     if (cancel && *cancel) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -466,22 +469,48 @@ trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* 
     }
 }
 
-template <typename TI, typename TC, typename TQC>
-cudaError_t trsm_launch(const void* c, int64_t ldc, int64_t rows, int ell, const double* r, void* q, int64_t ldq,
-                        void* qc, int64_t ldqc, const int* cancel, cudaStream_t st, const int* defic) {
-    const size_t smem = sizeof(TC) * ((size_t)ell * ell + (size_t)kTrsmRows * trsm_ld(ell) + (size_t)ell);
-    cudaError_t e = cudaFuncSetAttribute(trsm_rows_kernel<TI, TC, TQC>,
+template <typename TI, typename TC, typename TQC, int kRows>
+cudaError_t trsm_launch_rows(const void* c, int64_t ldc, int64_t rows, int ell, const double* r, void* q,
+                             int64_t ldq, void* qc, int64_t ldqc, const int* cancel, cudaStream_t st,
+                             const int* defic) {
+    const size_t smem = sizeof(TC) * ((size_t)ell * ell + (size_t)kRows * trsm_ld(ell) + (size_t)ell);
+    cudaError_t e = cudaFuncSetAttribute(trsm_rows_kernel<TI, TC, TQC, kRows>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const unsigned blocks = (unsigned)((rows + kTrsmRows - 1) / kTrsmRows);
+    const unsigned blocks = (unsigned)((rows + kRows - 1) / kRows);
     count_launch();
     {
-        cudaError_t pe_ = launch_pdl(trsm_rows_kernel<TI, TC, TQC>, dim3(blocks), dim3(kTrsmThreads), (size_t)(smem), st, static_cast<const TI*>(c), ldc, rows, ell, r,
-                                                                      static_cast<TI*>(q), ldq,
-                                                                      static_cast<TQC*>(qc), ldqc, cancel, defic);
+        cudaError_t pe_ = launch_pdl(trsm_rows_kernel<TI, TC, TQC, kRows>, dim3(blocks), dim3(kTrsmL * kRows), (size_t)(smem), st,
+                                     static_cast<const TI*>(c), ldc, rows, ell, r, static_cast<TI*>(q), ldq,
+                                     static_cast<TQC*>(qc), ldqc, cancel, defic);
         if (pe_ != cudaSuccess) return pe_;
     }
     return cudaGetLastError();
+}
+
+// Rows per block: every block stages R and runs the same substitution chain,
+// so the kernel takes about one block's time per wave of blocks. 32 rows per
+// block while all blocks fit in one wave; for longer panels 96 rows (three
+// times the threads on the same staged R) when that takes fewer waves.
+template <typename TC>
+int trsm_rows_per_block(int64_t rows, int ell) {
+    auto waves = [&](int per) {
+        const size_t smem = sizeof(TC) * ((size_t)ell * ell + (size_t)per * trsm_ld(ell) + (size_t)ell);
+        if (smem > 227 * 1024) return (int64_t)1 << 40;  // does not fit one SM's shared memory
+        int res = (int)std::min<size_t>(227 * 1024 / smem, 2048 / (size_t)(kTrsmL * per));
+        if (res < 1) res = 1;
+        const int64_t blocks = (rows + per - 1) / per;
+        return (blocks + (int64_t)res * device_sms() - 1) / ((int64_t)res * device_sms());
+    };
+    return waves(96) < waves(32) ? 96 : 32;
+}
+
+template <typename TI, typename TC, typename TQC>
+cudaError_t trsm_launch(const void* c, int64_t ldc, int64_t rows, int ell, const double* r, void* q, int64_t ldq,
+                        void* qc, int64_t ldqc, const int* cancel, cudaStream_t st, const int* defic) {
+    if (trsm_rows_per_block<TC>(rows, ell) == 96)
+        return trsm_launch_rows<TI, TC, TQC, 96>(c, ldc, rows, ell, r, q, ldq, qc, ldqc, cancel, st, defic);
+    return trsm_launch_rows<TI, TC, TQC, 32>(c, ldc, rows, ell, r, q, ldq, qc, ldqc, cancel, st, defic);
 }
 
 template <typename TI, typename TC>

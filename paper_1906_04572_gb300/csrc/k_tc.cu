@@ -1004,10 +1004,12 @@ int64_t tc_partial_elems(int64_t m, int64_t n, int64_t ellp, int64_t ldm, int64_
     return best;
 }
 
-// Two 128-byte K boxes per stage (256 contiguous bytes of each row of A per
-// load; measured about 8 % faster on the 8000 x 6000 products) while the ring
-// keeps at least four stages, i.e. for B tiles of up to 64 columns.
-int sketch_kgroup(int64_t ellp) { return ellp <= 64 ? 2 : 1; }
+// Two 128-byte K boxes per stage (twice the bytes per copy; measured about 8 %
+// faster on the 8000 x 6000 products at ell = 60 and 12 % at 12000 x 12000,
+// ell = 110, where the ring then holds three stages instead of six) whenever
+// three such stages fit the 200 KB ring; nb = B columns per stage (nparts x
+// ellp), so the split projection's three-times-wider B keeps one box.
+int sketch_kgroup(int64_t nb) { return 3 * 2 * (16384 + nb * 128) <= 200 * 1024 ? 2 : 1; }
 
 cudaError_t launch_sketch_tc(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, int trans,
                              const void* x, int64_t ldx, int64_t ell, int64_t ellp, void* part, int* tile_cnt,

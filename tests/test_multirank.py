@@ -63,3 +63,52 @@ def test_two_ranks_replicas_and_max_time():
     assert s0 == s1 == 15.0          # every rank reports the slowest rank's time
     assert d0 != d1                  # the ranks factorise different (seeded) matrices
     assert rc1 == 0                  # the reference arm: rank 1 returns at once
+
+
+def _sum_worker(rank, world, port, queue):
+    """The exchange of the row-partitioned factorisation as the library drives
+    it: a corutv_allreduce_fn built by the binding is called on a host buffer
+    (the way the library calls it) on each of two gloo ranks."""
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import ctypes
+
+    import torch.distributed as dist
+
+    from paper_1906_04572_gb300 import corutv
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    cb = corutv.allreduce_callback(corutv.torch_distributed_sum)
+    out = []
+    for dtype, code in ((np.float64, corutv.F64), (np.float32, corutv.F32)):
+        buf = (np.arange(37, dtype=dtype) + 1000 * rank).copy()
+        st = cb(ctypes.c_void_p(buf.ctypes.data), buf.size, code, None)
+        out.append((st, buf.copy()))
+    # a failing sum is reported as a status, not raised through the C caller
+    bad = corutv.allreduce_callback(lambda a: (_ for _ in ()).throw(RuntimeError("lost rank")))
+    st_bad = bad(ctypes.c_void_p(np.zeros(4).ctypes.data), 4, corutv.F64, None)
+    dist.destroy_process_group()
+    queue.put((rank, out, st_bad))
+
+
+def test_row_partition_exchange_sums_over_two_ranks():
+    import multiprocessing as mp
+    from paper_1906_04572_gb300 import corutv
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_sum_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict((r, (o, b)) for r, o, b in (q.get(timeout=120) for _ in procs))
+    for p in procs:
+        p.join(timeout=60)
+        if p.is_alive():
+            p.kill()
+        assert p.exitcode == 0
+    for r in range(2):
+        out, st_bad = res[r]
+        for (st, buf), dtype in zip(out, (np.float64, np.float32)):
+            assert st == corutv.OK
+            want = 2 * np.arange(37, dtype=dtype) + 1000
+            assert np.array_equal(buf, want)
+        assert st_bad != corutv.OK
