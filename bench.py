@@ -51,6 +51,9 @@ WORKLOADS = {
     "c1": dict(m=1000, n=1000, k=10, p=5, q=0, name="c1_1000x1000_k10_l15_q0"),
     "c2": dict(m=8000, n=6000, k=50, p=10, q=2, name="c2_8000x6000_k50_l60_q2"),
     "c3": dict(m=20000, n=20000, k=100, p=10, q=2, name="c3_20000x20000_k100_l110_q2"),
+    # the same spectrum and sketch width at 8000 x 8000: a case small enough for
+    # ncu captures with many passes (about 0.7 GB on the device)
+    "c3s": dict(m=8000, n=8000, k=100, p=10, q=2, name="c3s_8000x8000_k100_l110_q2"),
 }
 
 
@@ -186,14 +189,15 @@ def host_rows_of(workload: str, rows: int, seed: int = 0):
     """The first `rows` rows of the workload's matrix, formed on the host
     from the same seeded factors as the device copy (FP64)."""
     import synth
-    if workload == "c3":
-        u, s_, v = synth.spectrum_factors(20000, 20000, synth.c3_sigma(20000), seed=seed)
+    if workload in ("c3", "c3s"):
+        wl = WORKLOADS[workload]
+        u, s_, v = synth.spectrum_factors(wl["m"], wl["n"], synth.c3_sigma(wl["n"]), seed=seed)
         return np.ascontiguousarray((u[:rows] * s_) @ v.T)
     return np.ascontiguousarray(make_matrix(workload, seed).a[:rows])
 
 
-REF_ROWS = {"c1": 1000, "c2": 1000, "c3": 200}   # per step of the reference arm (a few seconds each)
-CPU_ROWS = {"c1": 1000, "c2": 2000, "c3": 400}   # the cpu_baseline sample of our arm (10-30 s)
+REF_ROWS = {"c1": 1000, "c2": 1000, "c3": 200, "c3s": 200}   # per step of the reference arm (a few seconds each)
+CPU_ROWS = {"c1": 1000, "c2": 2000, "c3": 400, "c3s": 400}   # the cpu_baseline sample of our arm (10-30 s)
 
 
 def run_reference(args):
@@ -468,12 +472,11 @@ def rpca_c4(ctx, device, prec="f32"):
             "rel_err_L": err, "prec": prec}
 
 
-def c3_matrix(device, seed=0):
+def c3_matrix(device, seed=0, m=20000, n=20000):
     """The 20000 x 20000 mixed-precision workload's matrix (sigma_i =
     exp(-i/20), seeded Haar factors), FP32, formed on the device."""
     import torch
     import synth
-    m = n = 20000
     u, s_, v = synth.spectrum_factors(m, n, synth.c3_sigma(n), seed=seed)
     A = (torch.from_numpy(u * s_).to(device) @ torch.from_numpy(v).to(device).T).float().contiguous()
     return A
@@ -599,8 +602,8 @@ def run_ours(args):
     peaks, peaks_kind = load_peaks()
     prec = args.prec
     dt = torch.float64 if prec == "f64" else torch.float32
-    if args.workload == "c3":
-        A = c3_matrix(device, seed=rank).to(dt)
+    if args.workload in ("c3", "c3s"):
+        A = c3_matrix(device, seed=rank, m=wl["m"], n=wl["n"]).to(dt)
         host_rows = None
     else:
         f = make_matrix(args.workload, seed=rank)

@@ -134,6 +134,32 @@ inline void prefer_max_shared(const void* fn) {
             cudaGetLastError();  // a preference only: ignore a refusal
 }
 
+// Raises the largest dynamic shared memory a launch of `fn` may ask for to
+// what the device allows, once per function and device. It is a limit, not a
+// reservation: each launch still gets (and is scheduled with) the size it
+// asks for. Setting it per launch to that launch's size instead would race
+// between host threads that launch the same kernel with different sizes (the
+// serving slots), one thread's smaller setting failing the other's launch.
+inline cudaError_t allow_max_dynamic_smem(const void* fn) {
+    static std::mutex mu;
+    static std::unordered_set<unsigned long long> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long key = (reinterpret_cast<unsigned long long>(fn) << 6) ^ (unsigned long long)dev;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(key)) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) done.insert(key);
+    return e;
+}
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                               Args&&... args) {

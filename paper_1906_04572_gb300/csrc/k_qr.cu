@@ -474,8 +474,7 @@ cudaError_t trsm_launch_rows(const void* c, int64_t ldc, int64_t rows, int ell, 
                              int64_t ldq, void* qc, int64_t ldqc, const int* cancel, cudaStream_t st,
                              const int* defic) {
     const size_t smem = sizeof(TC) * ((size_t)ell * ell + (size_t)kRows * trsm_ld(ell) + (size_t)ell);
-    cudaError_t e = cudaFuncSetAttribute(trsm_rows_kernel<TI, TC, TQC, kRows>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(trsm_rows_kernel<TI, TC, TQC, kRows>));
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((rows + kRows - 1) / kRows);
     count_launch();
@@ -938,7 +937,7 @@ cudaError_t launch_cholesky(const double* g, int64_t ell, int64_t rows, double* 
     if (ell < 1 || ell > kCholMaxEll) return cudaErrorInvalidValue;
     const size_t smem = sizeof(double) * (size_t)ell * (ell + 1) + sizeof(unsigned short) * (size_t)ell * (ell + 1) / 2;
     auto kern = defic ? cholesky_kernel<true> : cholesky_kernel<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(kern));
     if (e != cudaSuccess) return e;
     count_launch();
     {
@@ -964,7 +963,7 @@ cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, in
                         const int* cancel, cudaStream_t st, bool form_q) {
     if (ell < 1 || ell > 128 || !work) return cudaErrorInvalidValue;
     const size_t smem = sizeof(double) * ((size_t)ell * (ell | 1) + 5 * (size_t)ell) + sizeof(int) * ell;
-    cudaError_t e = cudaFuncSetAttribute(qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(qrcp_kernel));
     if (e != cudaSuccess) return e;
     count_launch();
     {
@@ -974,7 +973,7 @@ cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, in
     }
     if (!form_q) return cudaSuccess;
     const size_t smem_q = sizeof(double) * (size_t)(ell * ell + 2 * ell);
-    e = cudaFuncSetAttribute(qform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_q);
+    e = allow_max_dynamic_smem(reinterpret_cast<const void*>(qform_kernel));
     if (e != cudaSuccess) return e;
     count_launch();
     return launch_pdl(qform_kernel, dim3((unsigned)((ell + kQformWarps - 1) / kQformWarps)), dim3(kQformWarps * 32),
@@ -1079,7 +1078,7 @@ cudaError_t launch_apply_reflectors(const void* q1, ElemType tp, int64_t ldq, in
     const int l = (int)ell;
     auto go = [&](auto kern, size_t tc_bytes, auto xin, auto outp) -> cudaError_t {
         const size_t smem = tc_bytes * ((size_t)ell * ell + 2 * (size_t)ell + (size_t)kTrsmRows * trsm_ld(l));
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(kern));
         if (e != cudaSuccess) return e;
         count_launch();
         return launch_pdl(kern, dim3(blocks), dim3(kTrsmThreads), smem, st, xin, ldq, rows, l, refl, outp, ldo,

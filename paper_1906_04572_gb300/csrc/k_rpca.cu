@@ -344,7 +344,7 @@ template <typename TQ, int kE>
 cudaError_t rank_z_launch(const double* rt, const void* vq2, int64_t ldv, const int* perm, int64_t cols, int64_t ell,
                           double inv_mu, int* rank, double* z, int64_t ldz, const int* cancel, cudaStream_t st) {
     const size_t smem = sizeof(double) * (size_t)ell * ell;
-    cudaError_t e = cudaFuncSetAttribute(rank_z_kernel<TQ, kE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(rank_z_kernel<TQ, kE>));
     if (e != cudaSuccess) return e;
     count_launch();
     e = launch_pdl(rank_z_kernel<TQ, kE>, dim3((unsigned)((cols + 127) / 128)), dim3(128), smem, st, rt,

@@ -7,6 +7,8 @@
 //  * layout / precision conversions of the tall-skinny panels.
 #include <cuda_bf16.h>
 
+#include <atomic>
+
 #include "internal.cuh"
 
 namespace corutv {
@@ -124,13 +126,8 @@ __global__ void __launch_bounds__(kThreads) gemm_simt_kernel(GemmArgs g) {
 template <typename TA, typename TB, typename TC, int TN>
 cudaError_t launch_tn(const GemmArgs& g, cudaStream_t st) {
     const size_t smem = sizeof(TC) * (size_t)(kBK * (kBM + 1) + kBK * (16 * TN + 1));
-    static bool attr_set = false;  // per instantiation; benign race (idempotent)
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_simt_kernel<TA, TB, TC, TN>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(gemm_simt_kernel<TA, TB, TC, TN>));
+    if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((g.R + kBM - 1) / kBM), (unsigned)g.splits);
     count_launch();
     {
@@ -172,7 +169,7 @@ cudaError_t launch_gemm_simt(const GemmArgs& g, cudaStream_t st) {
 }
 
 int device_sms() {
-    static int cached[64] = {0};
+    static std::atomic<int> cached[64];  // zero until first asked
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
     if (!cached[dev]) {

@@ -976,7 +976,7 @@ cudaError_t tc_launch(const void* a, bool tf32, long long mtot, long long ktot_s
     p.tmem_cols = p.nacc * cols;
     const size_t smem = (size_t)p.stages * p.stage_bytes + 1024;
     auto kern = tf32 ? sketch_tc_kernel<true> : sketch_tc_kernel<false>;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = allow_max_dynamic_smem(reinterpret_cast<const void*>(kern));
     if (e != cudaSuccess) return e;
     count_launch();
     {
