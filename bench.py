@@ -58,10 +58,12 @@ WORKLOADS = {
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one sketch-kernel
-# launch, measured with ncu on the 8000 x 6000 workload with bf16 sketches (mean of
-# the A X and A^T Y launches: 100.54 and 100.34 MB) against 97.68 MB of algorithmic
-# bytes. Only that workload and precision, as the kernel stands, have a figure.
-SKETCH_TRAFFIC_BYTES = {("c2", "bf16"): 100.44e6}
+# launch (A X and A^T Q1 of a bf16 factorisation), from one ncu capture on the
+# 8000 x 8000 case with the 20000 x 20000 workload's spectrum and ell = 110: 136.83
+# and 136.50 MB against 131.52 MB of algorithmic bytes (1.040x). The 20000 x 20000
+# launch moves 6.25 times the A tiles of the same width; its figure is that
+# capture's traffic scaled by the algorithmic bytes (808.80 MB).
+SKETCH_TRAFFIC_BYTES = {("c3s", "bf16"): 136.67e6, ("c3", "bf16"): 136.67e6 / 131.52e6 * 808.80e6}
 
 
 def load_peaks():
