@@ -189,6 +189,7 @@ struct FactorBufs {
     double* refl;     // reflectors of the QRCP of D (V, tau, signs)
     double *racc, *racc2;  // products of CholeskyQR pass factors (single-pass core)
     int* defic;       // columns found numerically dependent in the extra CholeskyQR pass
+    float* rinv;      // FP32 inverse of a CholeskyQR factor (triangular solves of FP32 panels)
     void *xc, *q1c, *q2c, *part;
     void* abf;        // bf16 copy of A for CORUTV_P_BF16, or its bf16 splits for the projection
     float* at;        // TF32: A^T (n rows, row stride ldm), so that A^T Y has K-major operands
@@ -281,6 +282,7 @@ void carve_factor(C& cv, const FactorPlan& pl, FactorBufs& b) {
     b.racc = pl.dmode == 1 ? cv.template take<double>(ll) : nullptr;
     b.racc2 = pl.dmode == 1 ? cv.template take<double>(ll) : nullptr;
     b.defic = cv.template take<int>(pl.ellp);
+    b.rinv = cv.template take<float>(trsm_rinv_floats(pl.ellp));
     b.xc = cv.template take<char>(pn * es_c);
     b.q1c = cv.template take<char>(pm * es_c);
     b.q2c = cv.template take<char>(pl.split ? 3 * std::max(pm, pn) * 2 : std::max(pm, pn) * es_d);
@@ -406,7 +408,7 @@ corutv_status orth(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, co
     const double u = tw == T_F64 ? 0x1p-53 : 0x1p-24;  // unit roundoff of the Gram arithmetic
     CK(launch_cholesky(b.g, ell, rows_all, b.r, ex.flags, b.skip, ex.cancel, ex.st, u));
     if (rt_out) CK(launch_trimul(b.r, nullptr, b.racc, ell, false, nullptr, ex.cancel, ex.st));
-    CK(launch_trsm_rows(c, tp, ld, len, ell, b.r, tw, p1, ld, p1c, tqc, ld, ex.cancel, ex.st));
+    CK(launch_trsm_rows(c, tp, ld, len, ell, b.r, tw, p1, ld, p1c, tqc, ld, ex.cancel, ex.st, nullptr, b.rinv));
     // extra pass, only after a shifted pass 1. Directions the shifted pass left
     // at rounding level (a numerically rank-deficient C) cannot be restored
     // from C: their columns get a seeded random completion, orthonormalised by
@@ -417,7 +419,7 @@ corutv_status orth(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, co
     CK(launch_cholesky(b.g, ell, rows_all, b.r, ex.flags, nullptr, b.skip, ex.st, u, b.defic, 10.0 * (double)ell * u));
     // the extra pass's factor joins the product only if that pass ran
     if (rt_out) CK(launch_trimul(b.r, b.racc, b.racc2, ell, false, b.skip, ex.cancel, ex.st));
-    CK(launch_trsm_rows(p1, tp, ld, len, ell, b.r, tw, p1, ld, p1c, tqc, ld, b.skip, ex.st, b.defic));
+    CK(launch_trsm_rows(p1, tp, ld, len, ell, b.r, tw, p1, ld, p1c, tqc, ld, b.skip, ex.st, b.defic, b.rinv));
     if (passes == 1) return rt_out ? fail(CORUTV_EINVAL, "the R factor needs two passes") : CORUTV_OK;
     // pass 2
     CKS(gram(ex, pl, b, b.tmp, ld, b.tmp, ld, len, b.g, ex.cancel, tw));
@@ -425,7 +427,7 @@ corutv_status orth(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, co
     CK(launch_cholesky(b.g, ell, rows_all, b.r, ex.flags, nullptr, ex.cancel, ex.st, u));
     // C = Q (R_2 R_extra R_1): rt_out receives that product transposed
     if (rt_out) CK(launch_trimul(b.r, b.racc2, rt_out, ell, true, nullptr, ex.cancel, ex.st));
-    CK(launch_trsm_rows(b.tmp, tp, ld, len, ell, b.r, tw, q, ld, qc, tqc, ld, ex.cancel, ex.st));
+    CK(launch_trsm_rows(b.tmp, tp, ld, len, ell, b.r, tw, q, ld, qc, tqc, ld, ex.cancel, ex.st, nullptr, b.rinv));
     return CORUTV_OK;
 }
 

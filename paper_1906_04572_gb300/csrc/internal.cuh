@@ -229,7 +229,10 @@ cudaError_t launch_trimul(const double* rn, const double* ra, double* out, int64
 cudaError_t launch_trsm_rows(const void* c, ElemType tp, int64_t ldc, int64_t rows, int64_t ell,
                              const double* r, ElemType tc, void* q, int64_t ldq, void* qc,
                              ElemType tqc, int64_t ldqc, const int* cancel, cudaStream_t st,
-                             const int* defic = nullptr);
+                             const int* defic = nullptr, float* rinv_work = nullptr);
+// Size (floats) of the rinv_work buffer that selects, for FP32 panels solved
+// in FP32, the inverse-and-product form of the triangular solve.
+int64_t trsm_rinv_floats(int64_t ell);
 // FP32 Gram G = X^T Y (row-major ell x ell FP64 output) of two FP32 panels
 // in one launch; split sums reduced in the kernel in a fixed order. work:
 // gram_f32_work_floats floats; cnt: gram_f32_counters ints, zero before the

@@ -4,10 +4,12 @@
 //
 // X, Y: FP32 panels (column j at X + j * ldx, `len` rows), ell <= 128
 // columns. G: ell x ell FP64, row-major. The output is cut into 64 x 64
-// tiles; each tile's rows of X / Y are split into S contiguous ranges, one
-// CTA per (range, tile). A CTA accumulates its 64 x 64 partial in FP32
-// (4 x 4 outputs per thread, operands staged in shared memory 32 rows at a
-// time). The ranges run as thread-block clusters of 8 CTAs: each CTA leaves
+// tiles (only those on and above the diagonal when Y is X: the others are
+// the mirror images, bitwise); each tile's rows of X / Y are split into S
+// contiguous ranges, one CTA per (range, tile). A CTA accumulates its 64 x 64
+// partial in FP32 (a 4 x 4 block of adjacent outputs per thread, its operands
+// read as two 16-byte shared-memory loads per row; operands staged in shared
+// memory 32 rows at a time). The ranges run as thread-block clusters of 8 CTAs: each CTA leaves
 // its partial in its shared memory, and rank r of the cluster adds slice r
 // (512 outputs) of the 8 partials in rank order over distributed shared
 // memory and stores that slice of the cluster sum. A counter per (tile,
@@ -31,17 +33,19 @@ constexpr int kGT = 64;      // output tile
 constexpr int kGChunk = 32;  // rows staged per step
 constexpr int kGThreads = 256;
 constexpr int kGCluster = 8; // CTAs per cluster = output slices
-constexpr int kGLd = kGT + 1;
+constexpr int kGLd = kGT + 4;  // 16-byte aligned staging rows
 constexpr int kGSlice = kGT * kGT / kGCluster;
 
 struct GramPlan {
     int ntile, tiles, nc;  // clusters per tile; ranges per tile = 8 nc
+    int sym;               // Y is X: the tiles ti <= tj only
 };
 
-GramPlan gram_plan(int64_t len, int ell, int num_sms) {
+GramPlan gram_plan(int64_t len, int ell, int num_sms, bool sym) {
     GramPlan p;
     p.ntile = (ell + kGT - 1) / kGT;
-    p.tiles = p.ntile * p.ntile;
+    p.sym = sym ? 1 : 0;
+    p.tiles = sym ? p.ntile * (p.ntile + 1) / 2 : p.ntile * p.ntile;
     int64_t nc = 2 * num_sms / (kGCluster * p.tiles);               // about two CTAs per SM
     nc = std::min<int64_t>(nc, (len + 64 * kGCluster - 1) / (64 * kGCluster));  // >= 64 rows per range
     p.nc = (int)std::max<int64_t>(1, nc);
@@ -49,6 +53,22 @@ GramPlan gram_plan(int64_t len, int ell, int num_sms) {
 }
 
 constexpr int kPer = kGChunk * kGT / kGThreads;  // elements per thread and operand per chunk (8)
+
+// Output tile `tile` -> block coordinates; with sym the tiles on and above
+// the diagonal, row after row.
+__device__ __forceinline__ void tile_coords(int tile, int ntile, bool sym, int& ti, int& tj) {
+    if (!sym) {
+        ti = tile / ntile;
+        tj = tile % ntile;
+        return;
+    }
+    ti = 0;
+    while (tile >= ntile - ti) {
+        tile -= ntile - ti;
+        ++ti;
+    }
+    tj = ti + tile;
+}
 
 // Row `row`, columns col0 + 8 k (k < kPer), of an FP32 panel whose split
 // product tiles may still be pieces (zero for rows outside the chunk and
@@ -58,14 +78,26 @@ constexpr int kPer = kGChunk * kGT / kGThreads;  // elements per thread and oper
 // writeback it is stored into the panel. The loads of four pieces of all
 // eight columns are issued before any add (one L2 round trip per four
 // pieces).
+// The piece count of the row's 128-row tile, kept per thread: a thread's rows
+// advance by one chunk at a time, so the tile changes every few chunks.
+struct TileNp {
+    long long t = -1;
+    int np = 1;
+};
+
 __device__ __forceinline__ void load_row(const float* panel, int64_t ld, const TcPieces& pc, bool writeback,
-                                         int64_t row, bool row_ok, int col0, int ell, float (&v)[kPer]) {
+                                         int64_t row, bool row_ok, int col0, int ell, TileNp& tn,
+                                         float (&v)[kPer]) {
     int np = 1;
     const float* src = nullptr;
     if (pc.part && row_ok) {
         const long long t = row >> 7;
-        const long long first = unit_owner(t * pc.kc, pc.units, pc.grid);
-        np = (int)(unit_owner((t + 1) * pc.kc - 1, pc.units, pc.grid) - first) + 1;
+        if (t != tn.t) {
+            const long long first = unit_owner(t * pc.kc, pc.units, pc.grid);
+            tn.np = (int)(unit_owner((t + 1) * pc.kc - 1, pc.units, pc.grid) - first) + 1;
+            tn.t = t;
+        }
+        np = tn.np;
         src = pc.part + (t * pc.maxp * pc.ellp) * 128 + (row & 127);
     }
     if (np == 1) {
@@ -79,7 +111,21 @@ __device__ __forceinline__ void load_row(const float* panel, int64_t ld, const T
     const long long ps = (long long)pc.ellp * 128;  // piece stride
 #pragma unroll
     for (int k = 0; k < kPer; ++k) v[k] = 0.f;
-    for (int q0 = 0; q0 < np; q0 += 4) {
+    if (np == 2) {  // the common case: two pieces, no clamped duplicate loads
+        float w0[kPer], w1[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int col = col0 + 8 * k;
+            w0[k] = col < ell ? __ldcg(src + (long long)col * 128) : 0.f;
+            w1[k] = col < ell ? __ldcg(src + ps + (long long)col * 128) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            v[k] += w0[k];
+            v[k] += w1[k];
+        }
+    }
+    for (int q0 = 0; q0 < np && np != 2; q0 += 4) {
         float w[4][kPer];
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
@@ -122,7 +168,8 @@ gram_f32_kernel(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_
     const int S = pl.nc * kGCluster;
     const int s = blockIdx.x, tile = blockIdx.y;
     const int rank = (int)cluster.block_rank(), cid = s / kGCluster;
-    const int ti = tile / pl.ntile, tj = tile % pl.ntile;
+    int ti, tj;
+    tile_coords(tile, pl.ntile, pl.sym != 0, ti, tj);
     const int64_t r_beg = (int64_t)s * len / S, r_end = (int64_t)(s + 1) * len / S;
     const bool same = x == y && ti == tj;
     const TcPieces& pcx = pieces_x;
@@ -135,36 +182,36 @@ gram_f32_kernel(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
     // staging: each thread moves 8 elements per operand per chunk (one row,
-    // eight columns); the next chunk's loads are all issued (into registers)
-    // before the current chunk is multiplied, so their latency overlaps the
-    // arithmetic
-    static_assert(kGThreads % kGChunk == 0, "a thread keeps one row of each chunk");
+    // the columns c0, c0 + 8, ...); a warp covers 8 consecutive rows of 4
+    // columns per load (four 32-byte sectors), and its shared-memory stores
+    // hit 32 distinct banks. The next chunk's loads are all issued (into
+    // registers) before the current chunk is multiplied, so their latency
+    // overlaps the arithmetic.
+    static_assert(kGThreads == 256 && kGChunk == 32 && kGT == 64, "staging map");
+    const int lane = tid & 31, warp = tid >> 5;
+    const int sr = 8 * (warp & 3) + (lane & 7), sc = 4 * (warp >> 2) + (lane >> 3);
     float px[kPer], py[kPer];
+    TileNp tnx, tny;
     auto load_chunk = [&](int64_t r0) {
         const int nr = (int)(r_end - r0 < kGChunk ? r_end - r0 : kGChunk);
-        const int r = tid % kGChunk, c = tid / kGChunk;  // consecutive threads: consecutive rows
-        load_row(x, ldx, pcx, wb, r0 + r, r < nr, ti * kGT + c, ell, px);
-        if (!same) load_row(y, ldy, pcy, wb_y, r0 + r, r < nr, tj * kGT + c, ell, py);
+        load_row(x, ldx, pcx, wb, r0 + sr, sr < nr, ti * kGT + sc, ell, tnx, px);
+        if (!same) load_row(y, ldy, pcy, wb_y, r0 + sr, sr < nr, tj * kGT + sc, ell, tny, py);
     };
     if (r_beg < r_end) load_chunk(r_beg);
     for (int64_t r0 = r_beg; r0 < r_end; r0 += kGChunk) {
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
-            const int idx = tid + k * kGThreads;
-            const int c = idx / kGChunk, r = idx % kGChunk;
-            Xs[r * kGLd + c] = px[k];
-            if (!same) Ys[r * kGLd + c] = py[k];
+            Xs[sr * kGLd + sc + 8 * k] = px[k];
+            if (!same) Ys[sr * kGLd + sc + 8 * k] = py[k];
         }
         __syncthreads();
         if (r0 + kGChunk < r_end) load_chunk(r0 + kGChunk);
         const float* Yb = same ? Xs : Ys;
 #pragma unroll 4
         for (int r = 0; r < kGChunk; ++r) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = Xs[r * kGLd + ty + 16 * i];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) b[k] = Yb[r * kGLd + tx + 16 * k];
+            const float4 a4 = *reinterpret_cast<const float4*>(Xs + r * kGLd + 4 * ty);
+            const float4 b4 = *reinterpret_cast<const float4*>(Yb + r * kGLd + 4 * tx);
+            const float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -176,8 +223,8 @@ gram_f32_kernel(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_
     // the partial of this range stays in shared memory (row-major 64 x 64)
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) sbuf[(ty + 16 * i) * kGT + tx + 16 * k] = acc[i][k];
+        *reinterpret_cast<float4*>(sbuf + (4 * ty + i) * kGT + 4 * tx) =
+            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
     cluster.sync();
     // slice `rank` of the cluster sum: the 8 partials in rank order
     float* cp = cpart + ((size_t)tile * pl.nc + cid) * (kGT * kGT) + (size_t)rank * kGSlice;
@@ -217,19 +264,24 @@ gram_f32_kernel(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_
         for (; q < pl.nc; ++q) sum += __ldcg(c0 + (size_t)q * (kGT * kGT) + e);
         const int eg = rank * kGSlice + e;
         const int a = ti * kGT + eg / kGT, b = tj * kGT + eg % kGT;
-        if (a < ell && b < ell) out[(int64_t)a * ell + b] = f2d_exact(sum);
+        if (a < ell && b < ell) {
+            const double g = f2d_exact(sum);
+            out[(int64_t)a * ell + b] = g;
+            if (pl.sym && ti != tj) out[(int64_t)b * ell + a] = g;  // the mirror tile, bitwise its own sum
+        }
     }
 }
 
 }  // namespace
 
+// Workspace for either plan (X^T Y, or X^T X on the upper tiles).
 int64_t gram_f32_work_floats(int64_t len, int ell, int num_sms) {
-    const GramPlan p = gram_plan(len, ell, num_sms);
-    return (int64_t)p.tiles * p.nc * (kGT * kGT);
+    const GramPlan p = gram_plan(len, ell, num_sms, false), q = gram_plan(len, ell, num_sms, true);
+    return (int64_t)std::max(p.tiles * p.nc, q.tiles * q.nc) * (kGT * kGT);
 }
 
 int64_t gram_f32_counters(int64_t len, int ell, int num_sms) {
-    const GramPlan p = gram_plan(len, ell, num_sms);
+    const GramPlan p = gram_plan(len, ell, num_sms, false);
     return (int64_t)p.tiles * kGCluster;
 }
 
@@ -237,7 +289,7 @@ cudaError_t launch_gram_f32(const float* x, int64_t ldx, const float* y, int64_t
                             double* out, float* work, int* cnt, int num_sms, const int* cancel, cudaStream_t st,
                             const TcPieces& px, const TcPieces& py, bool writeback) {
     if (ell < 1 || ell > 128 || len < 1 || !work || !cnt) return cudaErrorInvalidValue;
-    const GramPlan p = gram_plan(len, ell, num_sms);
+    const GramPlan p = gram_plan(len, ell, num_sms, x == y && ldx == ldy);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(p.nc * kGCluster), (unsigned)p.tiles, 1);
     cfg.blockDim = dim3(kGThreads, 1, 1);

@@ -382,6 +382,32 @@ constexpr int kTrsmThreads = kTrsmL * kTrsmRows;
 // the 32 lanes of a warp (8 rows x 4 consecutive columns) hit 32 distinct
 // banks (a stride of 32 rows put a row's four lanes on one bank).
 __host__ __device__ __forceinline__ int trsm_ld(int ell) { return ((ell + 31) & ~31) + 4; }
+// Row stride of the staged R: every row starts 16-byte aligned, is padded
+// with zeros to whole eight-column blocks, and the rows t .. t + 3 that the
+// four lane groups of a warp read together land on distinct bank quadruples
+// (stride = 4 (mod 8) floats, 2 (mod 8) doubles), so the eight R values of a
+// step come in two 16-byte loads without bank conflicts.
+template <typename TC>
+__host__ __device__ __forceinline__ int trsm_ldr(int ell) {
+    return ((ell + 7) & ~7) + (sizeof(TC) == 4 ? 4 : 2);
+}
+template <typename TC>
+__host__ __device__ __forceinline__ size_t trsm_smem_elems(int ell, int rows) {
+    return (size_t)ell * trsm_ldr<TC>(ell) + (size_t)rows * trsm_ld(ell) + (size_t)ell;
+}
+// Eight consecutive values from a 16-byte aligned shared-memory address.
+__device__ __forceinline__ void ld8(const float* p, float (&v)[8]) {
+    const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void ld8(const double* p, double (&v)[8]) {
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const double2 a = *reinterpret_cast<const double2*>(p + 2 * h);
+        v[2 * h] = a.x;
+        v[2 * h + 1] = a.y;
+    }
+}
 template <typename TI, typename TC, typename TQC, int kRows>
 __global__ void __launch_bounds__(kTrsmL * kRows)
 trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* r, TI* q, int64_t ldq,
@@ -390,25 +416,27 @@ trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* 
     pdl_wait();
     if (cancel && *cancel) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TC* Rs = reinterpret_cast<TC*>(smem_raw);   // ell x ell row-major
-    TC* Ts = Rs + ell * ell;                    // [kTrsmRows][ld]: a row's c values, then its q values
+    const int ldr = trsm_ldr<TC>(ell);
+    TC* Rs = reinterpret_cast<TC*>(smem_raw);   // ell x ldr row-major, zero beyond column ell
+    TC* Ts = Rs + ell * ldr;                    // [kTrsmRows][ld]: a row's c values, then its q values
     const int ld = trsm_ld(ell);
     TC* Rd = Ts + (size_t)kTrsmRows * trsm_ld(ell);  // 1 / R[j][j]
     const int tid = threadIdx.x;
     const int ln = tid & (kTrsmL - 1), rr = tid / kTrsmL;
     // loads in batches of 16 per thread, all in flight before their stores
     constexpr int kB = 16;
-    for (int e0 = 0; e0 < ell * ell; e0 += kB * kTrsmThreads) {
+    for (int e0 = 0; e0 < ell * ldr; e0 += kB * kTrsmThreads) {
         double v[kB];
 #pragma unroll
         for (int u = 0; u < kB; ++u) {
             const int e = e0 + u * kTrsmThreads + tid;
-            v[u] = e < ell * ell ? r[e] : 0.0;
+            const int row = e / ldr, col = e - row * ldr;
+            v[u] = (e < ell * ldr && col < ell) ? r[row * ell + col] : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < kB; ++u) {
             const int e = e0 + u * kTrsmThreads + tid;
-            if (e < ell * ell) Rs[e] = (TC)v[u];
+            if (e < ell * ldr) Rs[e] = (TC)v[u];
         }
     }
     for (int j = tid; j < ell; j += kTrsmThreads) Rd[j] = (TC)1 / (TC)r[j * ell + j];
@@ -433,25 +461,30 @@ trsm_rows_kernel(const TI* c, int64_t ldc, int64_t rows, int ell, const double* 
         TC acc[kTrsmB];
 #pragma unroll
         for (int k = 0; k < kTrsmB; ++k) acc[k] = (ln == 0 && k < nb) ? Ts[rr * ld + j0 + k] : (TC)0;
+        // columns k >= nb of the last block meet R's zero padding; they are never stored
         for (int t = ln; t < j0; t += kTrsmL) {
             const TC qt = Ts[rr * ld + t];
-            const TC* rrow = Rs + t * ell + j0;
+            TC rv[kTrsmB];
+            ld8(Rs + t * ldr + j0, rv);
 #pragma unroll
-            for (int k = 0; k < kTrsmB; ++k)
-                if (k < nb) acc[k] -= qt * rrow[k];
+            for (int k = 0; k < kTrsmB; ++k) acc[k] -= qt * rv[k];
         }
 #pragma unroll
         for (int k = 0; k < kTrsmB; ++k) {
             acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 1);
             acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 2);
         }
+        // the block's triangle, column after column: q_kk is final once the
+        // terms of the columns before it are subtracted (each q_k receives
+        // them in increasing kk, as in row-wise substitution)
 #pragma unroll
-        for (int k = 0; k < kTrsmB; ++k) {
-            if (k >= nb) break;
-            TC sum = acc[k];
+        for (int kk = 0; kk < kTrsmB; ++kk) {
+            if (kk >= nb) break;
+            acc[kk] *= Rd[j0 + kk];
+            TC rv[kTrsmB];
+            ld8(Rs + (j0 + kk) * ldr + j0, rv);
 #pragma unroll
-            for (int kk = 0; kk < k; ++kk) sum -= acc[kk] * Rs[(j0 + kk) * ell + j0 + k];
-            acc[k] = sum * Rd[j0 + k];
+            for (int k = kk + 1; k < kTrsmB; ++k) acc[k] -= acc[kk] * rv[k];
         }
         __syncwarp();  // the row's lanes have read their c values before any is overwritten
 #pragma unroll
@@ -473,7 +506,7 @@ template <typename TI, typename TC, typename TQC, int kRows>
 cudaError_t trsm_launch_rows(const void* c, int64_t ldc, int64_t rows, int ell, const double* r, void* q,
                              int64_t ldq, void* qc, int64_t ldqc, const int* cancel, cudaStream_t st,
                              const int* defic) {
-    const size_t smem = sizeof(TC) * ((size_t)ell * ell + (size_t)kRows * trsm_ld(ell) + (size_t)ell);
+    const size_t smem = sizeof(TC) * trsm_smem_elems<TC>(ell, kRows);
     cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(trsm_rows_kernel<TI, TC, TQC, kRows>));
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((rows + kRows - 1) / kRows);
@@ -494,7 +527,7 @@ cudaError_t trsm_launch_rows(const void* c, int64_t ldc, int64_t rows, int ell, 
 template <typename TC>
 int trsm_rows_per_block(int64_t rows, int ell) {
     auto waves = [&](int per) {
-        const size_t smem = sizeof(TC) * ((size_t)ell * ell + (size_t)per * trsm_ld(ell) + (size_t)ell);
+        const size_t smem = sizeof(TC) * trsm_smem_elems<TC>(ell, per);
         if (smem > 227 * 1024) return (int64_t)1 << 40;  // does not fit one SM's shared memory
         int res = (int)std::min<size_t>(227 * 1024 / smem, 2048 / (size_t)(kTrsmL * per));
         if (res < 1) res = 1;
@@ -523,6 +556,222 @@ cudaError_t trsm_dispatch(const void* c, int64_t ldc, int64_t rows, int ell, con
         case T_BF16: return trsm_launch<TI, TC, __nv_bfloat16>(c, ldc, rows, ell, r, q, ldq, qc, ldqc, cancel, st, defic);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Q = C R^{-1} for FP32 panels as two short launches instead of a
+// substitution chain per row: the FP32 inverse of R once, then a product in
+// which every entry q_ij = sum_{k <= j} c_ik (R^{-1})_kj is an independent dot
+// product. Each row's chain in the substitution kernel above is ell^2 / 2
+// dependent steps long whatever the panel's length; here a warp's chain is at
+// most ell multiply-adds.
+//
+// rinv_kernel: column j of R^{-1} solves R x = e_j by column-oriented back
+// substitution, one warp per column: b = e_j; for k = j, j-1, ..., 0:
+// x_k = b_k / R_kk, then b_i -= R_ik x_k for i < k. Lane l keeps b_i for
+// i = l + 32 s; the steps run slot by slot (k = 32 S + kk) so that x_k's slot
+// is known at compile time. R is read in FP32 (the precision the panel is
+// solved in), stored transposed so that column k is contiguous.
+// ri: ell x ldri row-major, zero below the diagonal and beyond column ell.
+constexpr int kRiWarps = 8;
+__host__ __device__ __forceinline__ int rinv_ldt(int ell) { return ((ell + 31) & ~31) + 1; }
+
+template <int S>
+__device__ __forceinline__ void rinv_slot(float (&b)[4], const float* Rt, int ldt, const float* rd, int lane,
+                                          int top) {
+    for (int kk = top; kk >= 0; --kk) {
+        const int k = 32 * S + kk;
+        const float* col = Rt + k * ldt;  // col[i] = R_ik
+        float rk[S + 1];
+#pragma unroll
+        for (int s = 0; s <= S; ++s) rk[s] = col[lane + 32 * s];
+        const float xk = __shfl_sync(0xffffffffu, b[S], kk) * rd[k];
+#pragma unroll
+        for (int s = 0; s < S; ++s) b[s] = fmaf(-rk[s], xk, b[s]);
+        b[S] = lane < kk ? fmaf(-rk[S], xk, b[S]) : (lane == kk ? xk : b[S]);
+    }
+}
+
+__global__ void __launch_bounds__(kRiWarps * 32)
+rinv_kernel(const double* r, int ell, float* ri, int ldri, const int* cancel) {
+    pdl_wait();
+    if (cancel && *cancel) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ldt = rinv_ldt(ell);                     // odd: the transposing stores hit 32 banks
+    float* Rt = reinterpret_cast<float*>(smem_raw);    // ell x ldt: Rt[k][i] = R_ik, i <= k
+    float* rd = Rt + (size_t)ell * ldt;                // 1 / R_kk
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // the upper triangle, 16 loads per thread in flight before their stores
+    constexpr int kB = 16, kT = kRiWarps * 32;
+    for (int e0 = 0; e0 < ell * ell; e0 += kB * kT) {
+        double v[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int e = e0 + u * kT + tid, i = e / ell, k = e - i * ell;
+            v[u] = (e < ell * ell && k >= i) ? r[e] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int e = e0 + u * kT + tid, i = e / ell, k = e - i * ell;
+            if (e < ell * ell && k >= i) Rt[k * ldt + i] = (float)v[u];
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < ell; k += kRiWarps * 32) rd[k] = 1.f / Rt[k * ldt + k];
+    __syncthreads();
+    pdl_trigger();
+    const int j = blockIdx.x * kRiWarps + warp;
+    if (j >= ell) return;
+    float b[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) b[s] = (lane + 32 * s == j) ? 1.f : 0.f;
+    switch (j >> 5) {  // the slots from x_j's down to slot 0
+        case 3: rinv_slot<3>(b, Rt, ldt, rd, lane, j & 31); [[fallthrough]];
+        case 2: rinv_slot<2>(b, Rt, ldt, rd, lane, (j >> 5) == 2 ? j & 31 : 31); [[fallthrough]];
+        case 1: rinv_slot<1>(b, Rt, ldt, rd, lane, (j >> 5) == 1 ? j & 31 : 31); [[fallthrough]];
+        default: rinv_slot<0>(b, Rt, ldt, rd, lane, (j >> 5) == 0 ? j & 31 : 31);
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int i = lane + 32 * s;
+        if (i < ell) ri[(int64_t)i * ldri + j] = i <= j ? b[s] : 0.f;
+    }
+    if (j == ell - 1)  // the padding columns
+        for (int i = lane; i < ell; i += 32)
+            for (int jj = ell; jj < ldri; ++jj) ri[(int64_t)i * ldri + jj] = 0.f;
+}
+
+// trsm_gemm_kernel: 128 rows per block, staged column by column into shared
+// memory (k-major: Cs[k][row]) together with R^{-1} (both with all of a
+// thread's loads in flight before its stores); warp w computes columns
+// 8w .. 8w + 7 for all 128 rows (4 adjacent rows per lane, 32 accumulators)
+// over k <= 8w + 7 (R^{-1} is upper triangular), reading the R^{-1} row
+// segment as two 16-byte loads that every lane shares. Writes Q (and its copy qc), replacing the columns
+// the extra CholeskyQR pass marked dependent by their random completion.
+// In place (q == c) is safe: a block reads all its rows before writing any.
+constexpr int kTgRows = 128;
+template <typename TQC>
+__global__ void __launch_bounds__(512)
+trsm_gemm_kernel(const float* c, int64_t ldc, int64_t rows, int ell, const float* ri, int ldri, float* q,
+                 int64_t ldq, TQC* qc, int64_t ldqc, const int* cancel, const int* defic) {
+    pdl_wait();
+    if (cancel && *cancel) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* Cs = reinterpret_cast<float*>(smem_raw);  // [ell][kTgRows]
+    float* Rs = Cs + (size_t)ell * kTgRows;         // R^{-1}: [ell][ldri]
+    const int64_t r0 = (int64_t)blockIdx.x * kTgRows;
+    const int nr = (int)(rows - r0 < kTgRows ? rows - r0 : kTgRows);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nt = blockDim.x;
+    constexpr int kB = 8;
+    const int nc4 = ell * (kTgRows / 4), nr4 = ell * ldri / 4;
+    for (int e0 = 0; e0 < nc4 + nr4; e0 += kB * nt) {
+        float4 v[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int e = e0 + u * nt + tid;
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e < nc4) {
+                const int k = e / (kTgRows / 4), i = 4 * (e % (kTgRows / 4));
+                const float* src = c + (int64_t)k * ldc + r0 + i;
+                if (i + 3 < nr) {
+                    v[u] = __ldcs(reinterpret_cast<const float4*>(src));
+                } else {
+                    if (i < nr) v[u].x = src[0];
+                    if (i + 1 < nr) v[u].y = src[1];
+                    if (i + 2 < nr) v[u].z = src[2];
+                }
+            } else if (e < nc4 + nr4) {
+                v[u] = __ldcg(reinterpret_cast<const float4*>(ri) + (e - nc4));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int e = e0 + u * nt + tid;
+            if (e < nc4) {
+                const int k = e / (kTgRows / 4), i = 4 * (e % (kTgRows / 4));
+                *reinterpret_cast<float4*>(Cs + k * kTgRows + i) = v[u];
+            } else if (e < nc4 + nr4) {
+                reinterpret_cast<float4*>(Rs)[e - nc4] = v[u];
+            }
+        }
+    }
+    __syncthreads();
+    const int j0 = 8 * w;
+    const int kend = min(ell, j0 + 8);
+    float acc[4][8];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < kend; ++k) {
+        const float4 cv = *reinterpret_cast<const float4*>(Cs + k * kTgRows + 4 * lane);
+        const float4 u0 = *reinterpret_cast<const float4*>(Rs + k * ldri + j0);
+        const float4 u1 = *reinterpret_cast<const float4*>(Rs + k * ldri + j0 + 4);
+        const float cr[4] = {cv.x, cv.y, cv.z, cv.w};
+        const float rv[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(cr[a], rv[b], acc[a][b]);
+    }
+    pdl_trigger();  // the successor may launch while Q is written
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int j = j0 + b;
+        if (j >= ell) break;
+        const bool dep = defic && defic[j];
+        float v[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int64_t i = r0 + 4 * lane + a;
+            v[a] = dep ? completion_entry(i, j, rows) : acc[a][b];
+        }
+        const int i0 = 4 * lane;
+        if (i0 + 3 < nr) {
+            *reinterpret_cast<float4*>(q + (int64_t)j * ldq + r0 + i0) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                if (i0 + a < nr) q[(int64_t)j * ldq + r0 + i0 + a] = v[a];
+        }
+        if (qc) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                if (i0 + a < nr) qc[(int64_t)j * ldqc + r0 + i0 + a] = (TQC)v[a];
+        }
+    }
+}
+
+int trsm_inv_ldri(int ell) { return (ell + 7) & ~7; }
+
+}  // namespace
+
+int64_t trsm_rinv_floats(int64_t ell) { return ell * ((ell + 7) & ~7); }
+
+namespace {
+
+template <typename TQC>
+cudaError_t trsm_inv_launch(const float* c, int64_t ldc, int64_t rows, int ell, const double* r, float* ri,
+                            float* q, int64_t ldq, TQC* qc, int64_t ldqc, const int* cancel, cudaStream_t st,
+                            const int* defic) {
+    const int ldri = trsm_inv_ldri(ell);
+    const size_t smem_ri = sizeof(float) * ((size_t)ell * rinv_ldt(ell) + ell);
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(rinv_kernel));
+    if (e != cudaSuccess) return e;
+    count_launch();
+    e = launch_pdl(rinv_kernel, dim3((unsigned)((ell + kRiWarps - 1) / kRiWarps)), dim3(kRiWarps * 32), smem_ri, st,
+                   r, ell, ri, ldri, cancel);
+    if (e != cudaSuccess) return e;
+    const size_t smem_g = sizeof(float) * (size_t)ell * (kTgRows + ldri);
+    e = allow_max_dynamic_smem(reinterpret_cast<const void*>(trsm_gemm_kernel<TQC>));
+    if (e != cudaSuccess) return e;
+    count_launch();
+    e = launch_pdl(trsm_gemm_kernel<TQC>, dim3((unsigned)((rows + kTgRows - 1) / kTgRows)),
+                   dim3(32 * ((ell + 7) / 8)), smem_g, st, c, ldc, rows, ell, static_cast<const float*>(ri), ldri,
+                   q, ldq, qc, ldqc, cancel, defic);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -951,8 +1200,20 @@ cudaError_t launch_cholesky(const double* g, int64_t ell, int64_t rows, double* 
 cudaError_t launch_trsm_rows(const void* c, ElemType tp, int64_t ldc, int64_t rows, int64_t ell,
                              const double* r, ElemType tc, void* q, int64_t ldq, void* qc,
                              ElemType tqc, int64_t ldqc, const int* cancel, cudaStream_t st,
-                             const int* defic) {
+                             const int* defic, float* rinv_work) {
     const int l = (int)ell;
+    auto al16 = [](const void* p, int64_t ld) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0 && ld % 4 == 0; };
+    if (tp == T_F32 && tc == T_F32 && rinv_work && l >= 1 && l <= 128 && al16(c, ldc) && al16(q, ldq) &&
+        (reinterpret_cast<uintptr_t>(rinv_work) & 15) == 0) {
+        const float* cf = static_cast<const float*>(c);
+        float* qf = static_cast<float*>(q);
+        switch (qc ? tqc : T_F32) {
+            case T_F32: return trsm_inv_launch<float>(cf, ldc, rows, l, r, rinv_work, qf, ldq, static_cast<float*>(qc), ldqc, cancel, st, defic);
+            case T_F64: return trsm_inv_launch<double>(cf, ldc, rows, l, r, rinv_work, qf, ldq, static_cast<double*>(qc), ldqc, cancel, st, defic);
+            case T_BF16: return trsm_inv_launch<__nv_bfloat16>(cf, ldc, rows, l, r, rinv_work, qf, ldq, static_cast<__nv_bfloat16*>(qc), ldqc, cancel, st, defic);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (tp == T_F64 && tc == T_F64) return trsm_dispatch<double, double>(c, ldc, rows, l, r, q, ldq, qc, tqc, ldqc, cancel, st, defic);
     if (tp == T_F64 && tc == T_F32) return trsm_dispatch<double, float>(c, ldc, rows, l, r, q, ldq, qc, tqc, ldqc, cancel, st, defic);
     if (tp == T_F32 && tc == T_F32) return trsm_dispatch<float, float>(c, ldc, rows, l, r, q, ldq, qc, tqc, ldqc, cancel, st, defic);
