@@ -231,6 +231,18 @@ corutv_status corutv_poll(corutv_ctx* ctx, uint64_t ticket, int64_t timeout_us, 
 enum { CORUTV_STAGE_SKETCH = 0, CORUTV_STAGE_PROJECT = 1, CORUTV_STAGE_ORTH = 2, CORUTV_STAGE_QRCP = 3,
        CORUTV_STAGE_FACTOR = 4, CORUTV_STAGE_COUNT = 5, CORUTV_STAGE_ALL = -1 };
 corutv_status corutv_profile_enable(corutv_ctx* ctx, int enable);
+
+/* CUDA-graph replay of repeated factorisations (not part of the method).
+ * With enable = 1, a corutv_factor call on device pointers whose arguments
+ * (dtype, A, m, n, lda, every option, the output pointers and leading
+ * dimensions) equal those of an earlier call on this context is captured,
+ * on its second occurrence, into a CUDA graph of all its launches, and that
+ * graph is replayed for every later occurrence: the same kernels on the same
+ * buffers, one launch call instead of one per kernel. Results are bitwise
+ * those of the direct calls. Up to 16 argument sets are kept; a workspace
+ * growth or enable = 0 drops them. Ignored while profiling is enabled and
+ * for host pointers. Returns CORUTV_EINVAL for a bad context. */
+corutv_status corutv_set_graphs(corutv_ctx* ctx, int enable);
 corutv_status corutv_profile_read(corutv_ctx* ctx, int stage, double* total_ms, int64_t* count);
 
 /* ---- single steps of Algorithm 1, for testing and composition ----------

@@ -73,6 +73,7 @@ _SIGS = {
     "corutv_poll": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)],
                     ctypes.c_int),
     "corutv_profile_enable": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "corutv_set_graphs": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "corutv_profile_read": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "corutv_gaussian": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64,
@@ -322,6 +323,11 @@ def corutv_poll(ctx, ticket: int, timeout_us: int = -1):
 
 
 STAGE_SKETCH, STAGE_PROJECT, STAGE_ORTH, STAGE_QRCP, STAGE_FACTOR, STAGE_ALL = 0, 1, 2, 3, 4, -1
+
+
+def corutv_set_graphs(ctx, enable: bool = True) -> None:
+    """Replay repeated device-pointer factorisations from captured CUDA graphs."""
+    _check(ctx, load().corutv_set_graphs(ctx, int(bool(enable))))
 
 
 def corutv_profile_enable(ctx, enable: bool = True) -> None:

@@ -27,9 +27,15 @@ using namespace corutv;
 
 namespace {
 std::atomic<long long> g_launches{0};
+// while this thread captures a CUDA graph, its launches are counted here (they
+// run when the graph is launched, and are counted then)
+thread_local long long* t_capture_count = nullptr;
 }  // namespace
 
-void corutv::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void corutv::count_launch() {
+    if (t_capture_count) ++*t_capture_count;
+    else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 
 namespace {
 
@@ -673,9 +679,34 @@ struct corutv_ctx {
     std::vector<cudaEvent_t> ev_pool;  // events for submit-time ordering (under smu)
     void* xhost = nullptr;             // pinned staging of the row-partitioned exchanges
     size_t xcap = 0;
+    // CUDA-graph replay of repeated factorisations (corutv_set_graphs)
+    bool graphs = false;
+    struct GraphEntry {
+        int seen = 0;                    // direct runs so far (captured on the second)
+        cudaGraphExec_t exec = nullptr;
+        long long kernels = 0;           // library kernels in the graph
+    };
+    std::map<std::string, GraphEntry> graph_cache;
+    cudaStream_t cap_stream = nullptr;   // captures run here (the caller's stream may be the legacy one)
 };
 
 namespace {
+
+// The arguments of a call as bytes (the key of its captured graph).
+struct KeyBytes {
+    std::string s;
+    template <typename T>
+    KeyBytes& add(const T& v) {
+        s.append(reinterpret_cast<const char*>(&v), sizeof(T));
+        return *this;
+    }
+};
+
+void drop_graphs(corutv_ctx* ctx) {
+    for (auto& kv : ctx->graph_cache)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    ctx->graph_cache.clear();
+}
 
 corutv_status ensure_ws(corutv_ctx* ctx, DeviceBuffer& buf, size_t bytes, cudaStream_t st) {
     if (buf.cap >= bytes) return CORUTV_OK;
@@ -683,6 +714,7 @@ corutv_status ensure_ws(corutv_ctx* ctx, DeviceBuffer& buf, size_t bytes, cudaSt
         return fail(CORUTV_ENOMEM, "workspace of %zu bytes exceeds the context budget %zu", bytes, ctx->budget);
     if (buf.ptr) {
         CK(cudaStreamSynchronize(st));
+        if (&buf == &ctx->ws) drop_graphs(ctx);  // the captured graphs use the old workspace
         CK(cudaFree(buf.ptr));
         buf.ptr = nullptr;
         buf.cap = 0;
@@ -694,6 +726,53 @@ corutv_status ensure_ws(corutv_ctx* ctx, DeviceBuffer& buf, size_t bytes, cudaSt
         return fail(CORUTV_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
     }
     buf.cap = bytes;
+    return CORUTV_OK;
+}
+
+// Runs `enqueue(stream)` (all launches of one call, stream-ordered) directly
+// on ctx->stream at the first occurrence of `key`, captured into a CUDA graph
+// on the second (on a stream of the context's own, as the caller's may be the
+// legacy stream, which cannot be captured) and launched on ctx->stream, and
+// as that graph's replay afterwards. A capture that fails (an unsupported call
+// inside) leaves the key on direct runs.
+template <class F>
+corutv_status graph_run(corutv_ctx* ctx, const std::string& key, F&& enqueue) {
+    auto it = ctx->graph_cache.find(key);
+    if (it == ctx->graph_cache.end()) {
+        if (ctx->graph_cache.size() >= 16) drop_graphs(ctx);
+        it = ctx->graph_cache.emplace(key, corutv_ctx::GraphEntry{}).first;
+    }
+    corutv_ctx::GraphEntry& g = it->second;
+    if (g.exec) {
+        CK(cudaGraphLaunch(g.exec, ctx->stream));
+        g_launches.fetch_add(g.kernels, std::memory_order_relaxed);
+        return CORUTV_OK;
+    }
+    if (g.seen++ != 1) return enqueue(ctx->stream);  // first occurrence, or a capture that failed before
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    long long kernels = 0;
+    CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    t_capture_count = &kernels;
+    const corutv_status st = enqueue(ctx->cap_stream);
+    t_capture_count = nullptr;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ie = cudaErrorUnknown;
+    if (st == CORUTV_OK && ce == cudaSuccess && graph) ie = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (st != CORUTV_OK) {
+        cudaGetLastError();
+        return st;
+    }
+    if (ce != cudaSuccess || ie != cudaSuccess) {
+        cudaGetLastError();  // not capturable here: stay on direct runs
+        return enqueue(ctx->stream);
+    }
+    g.exec = exec;
+    g.kernels = kernels;
+    CK(cudaGraphLaunch(g.exec, ctx->stream));
+    g_launches.fetch_add(kernels, std::memory_order_relaxed);
     return CORUTV_OK;
 }
 
@@ -785,6 +864,8 @@ corutv_status corutv_destroy(corutv_ctx* ctx) {
     }
     for (auto ev : ctx->ev_pool) cudaEventDestroy(ev);
     cudaStreamSynchronize(ctx->stream);
+    drop_graphs(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->ws.ptr) cudaFree(ctx->ws.ptr);
     if (ctx->flags) cudaFree(ctx->flags);
     if (ctx->switch_ev) cudaEventDestroy(ctx->switch_ev);
@@ -828,6 +909,18 @@ corutv_status corutv_sync(corutv_ctx* ctx) {
     CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int) * FLAG_COUNT, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return flags_status(hf);
+}
+
+corutv_status corutv_set_graphs(corutv_ctx* ctx, int enable) {
+    CKS(check_ctx(ctx));
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    DeviceGuard guard(ctx->device);
+    if (!enable) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        drop_graphs(ctx);
+    }
+    ctx->graphs = enable != 0;
+    return CORUTV_OK;
 }
 
 corutv_status corutv_profile_enable(corutv_ctx* ctx, int enable) {
@@ -927,9 +1020,20 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
             psi = ps;
         }
     }
-    Exec ex{ctx->stream, ctx->flags, nullptr, ctx->num_sms, &ctx->prof};
-    CKS(run_factor(ex, pl, b, a_dev, psi, opts->seed, opts->stream));
-    CKS(emit_user(ex, pl, b, ta, u_dev, ldu_dev, t_dev, v_dev, ldv_dev, perm_dev));
+    auto enqueue = [&](cudaStream_t st) -> corutv_status {
+        const Exec ex{st, ctx->flags, nullptr, ctx->num_sms, &ctx->prof};
+        CKS(run_factor(ex, pl, b, a_dev, psi, opts->seed, opts->stream));
+        return emit_user(ex, pl, b, ta, u_dev, ldu_dev, t_dev, v_dev, ldv_dev, perm_dev);
+    };
+    if (dev && ctx->graphs && !ctx->prof.on) {
+        KeyBytes key;
+        key.add(dtype).add(A).add(m).add(n).add(lda).add(opts->k).add(opts->p).add(opts->q);
+        key.add(opts->sketch_prec).add(opts->d_mode).add(opts->seed).add(opts->stream).add(opts->t_lower);
+        key.add(opts->psi).add(opts->power_form).add(opts->bf16_last_round);
+        key.add(U).add(ldu).add(T).add(V).add(ldv).add(perm).add(ctx->ws.ptr).add(ctx->stream);
+        return graph_run(ctx, key.s, enqueue);
+    }
+    CKS(enqueue(ctx->stream));
     if (!dev) {
         if (U) CK(cudaMemcpy2DAsync(U, ldu * es, u_dev, ell * es, ell * es, m, cudaMemcpyDeviceToHost, ctx->stream));
         if (V) CK(cudaMemcpy2DAsync(V, ldv * es, v_dev, ell * es, ell * es, n, cudaMemcpyDeviceToHost, ctx->stream));

@@ -118,3 +118,42 @@ def test_submit_waits_for_the_producer_of_a(ctx):
     for name, g, r in zip(("U", "T", "V", "perm"), (U, T, V, perm), ref):
         assert np.array_equal(g.cpu().numpy(), r), f"{name} differs from the synchronous result"
     del big
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f64"])
+def test_graph_replay_is_bitwise_the_direct_call(ctx, prec):
+    """With graph replay on, the second occurrence of a call is captured and
+    later ones are replayed: every result is bitwise the direct call's, and a
+    replay reads the buffers' current contents (A overwritten in place)."""
+    m, n, k, p, q = 900, 700, 20, 10, 2
+    dtype = torch.float64 if prec == "f64" else torch.float32
+    sig = np.arange(1, min(m, n) + 1) ** -1.2
+    a1 = torch.from_numpy(synth.spectrum_matrix(m, n, sig, 1e-6, 41)).to("cuda", dtype)
+    a2 = torch.from_numpy(synth.spectrum_matrix(m, n, sig, 1e-6, 42)).to("cuda", dtype)
+    ell = k + p
+    A = a1.clone()
+    U = torch.empty((m, ell), device="cuda", dtype=dtype)
+    T = torch.empty((ell, ell), device="cuda", dtype=dtype)
+    V = torch.empty((n, ell), device="cuda", dtype=dtype)
+    perm = torch.empty(ell, device="cuda", dtype=torch.int32)
+
+    def run():
+        corutv.corutv_factor(ctx.handle, A, k, p, q, prec, U, T, V, perm, seed=3, stream=0)
+        torch.cuda.synchronize()
+        return tuple(x.cpu().numpy().copy() for x in (U, T, V, perm))
+
+    refs = []
+    for src in (a1, a2):
+        A.copy_(src)
+        refs.append(run())
+    corutv.corutv_set_graphs(ctx.handle, True)
+    try:
+        for i, src in enumerate((a1, a1, a1, a2, a1, a2)):
+            A.copy_(src)
+            got = run()
+            want = refs[0] if src is a1 else refs[1]
+            for name, g, r in zip(("U", "T", "V", "perm"), got, want):
+                assert np.array_equal(g, r), f"call {i}: {name} differs"
+    finally:
+        corutv.corutv_set_graphs(ctx.handle, False)
+    assert ctx.sync() == 0
