@@ -646,6 +646,15 @@ def run_ours(args):
     del out_g
     graph_replay = {"ms_per_step": ms_g, "tflops": world * flops / (max_over_ranks(ms_g, world, device) / 1e3) / 1e12,
                     "kind": "corutv_set_graphs: every launch of a factorisation replayed from one CUDA graph"}
+    # the stage shape of every product picked by the library's autotuner
+    # (timed candidates on first use) instead of the fixed rule
+    corutv.corutv_set_autotune(True)
+    ms_t, out_t, _ = time_factor(ctx, A, k, p, q, prec, args.steps, max(args.warmup, 3), world)
+    corutv.corutv_set_autotune(False)
+    autotuned = {"ms_per_step": ms_t, "tflops": world * flops / (max_over_ranks(ms_t, world, device) / 1e3) / 1e12,
+                 "choices": corutv.corutv_autotune_entries(),
+                 "rule": "two 128-byte K boxes per stage when three such stages fit 200 KB, else one; deepest ring"}
+    del out_t
     err = error_same_psi(ctx, A, k, p, q, prec)
     # a second, profiled pass: CUDA events around every stage (the sketch
     # launches among them) for the stage split and the roofline figure
@@ -777,6 +786,7 @@ def run_ours(args):
             "latency": latency,
             "stages": stages,
             "graph_replay": graph_replay,
+            "autotuned": autotuned,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": sampler.summary(),

@@ -243,6 +243,23 @@ corutv_status corutv_profile_enable(corutv_ctx* ctx, int enable);
  * growth or enable = 0 drops them. Ignored while profiling is enabled and
  * for host pointers. Returns CORUTV_EINVAL for a bad context. */
 corutv_status corutv_set_graphs(corutv_ctx* ctx, int enable);
+
+/* Autotuning of the tensor-core products' stage shape (process-wide, all
+ * contexts; not part of the method). With enable = 1, the first launch of
+ * each product shape (its M and K extents, K segments, operand kind, panel
+ * width, direction, output handling and grid) times the candidate shapes --
+ * one or two 128-byte K boxes of A per pipeline stage, each with the deepest
+ * ring that fits and with half of it -- with CUDA events on the caller's
+ * stream (three launches each; the call then synchronises that stream) and
+ * keeps the fastest for the process; later launches of that shape use it.
+ * enable = 0 (the default) returns to the fixed rule; choices made are kept.
+ * Results change only in the order of FP32 partial sums. */
+corutv_status corutv_set_autotune(int enable);
+/* Returns the number of tuned shapes; for 0 <= index < that number, also
+ * the shape (M extent, K extent, panel columns, 1 for A^T Y) and its choice
+ * (K boxes per stage, stages, best launch time in microseconds). */
+int corutv_autotune_entry(int index, int64_t* mtot, int64_t* ktot, int* nb, int* trans, int* kgroup, int* stages,
+                          float* us);
 corutv_status corutv_profile_read(corutv_ctx* ctx, int stage, double* total_ms, int64_t* count);
 
 /* ---- single steps of Algorithm 1, for testing and composition ----------

@@ -74,6 +74,11 @@ _SIGS = {
                     ctypes.c_int),
     "corutv_profile_enable": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "corutv_set_graphs": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "corutv_set_autotune": ([ctypes.c_int], ctypes.c_int),
+    "corutv_autotune_entry": ([ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "corutv_profile_read": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "corutv_gaussian": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64,
@@ -323,6 +328,31 @@ def corutv_poll(ctx, ticket: int, timeout_us: int = -1):
 
 
 STAGE_SKETCH, STAGE_PROJECT, STAGE_ORTH, STAGE_QRCP, STAGE_FACTOR, STAGE_ALL = 0, 1, 2, 3, 4, -1
+
+
+def corutv_set_autotune(enable: bool = True) -> None:
+    """Tune the tensor-core products' stage shape on first use (process-wide)."""
+    status = load().corutv_set_autotune(int(bool(enable)))
+    if status != OK:
+        raise CorutvError(status, "corutv_set_autotune failed")
+
+
+def corutv_autotune_entries() -> list:
+    """The tuned product shapes and their choices."""
+    lib = load()
+    out = []
+    i = 0
+    while True:
+        mt, kt = ctypes.c_int64(), ctypes.c_int64()
+        nb, tr, kg, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        us = ctypes.c_float()
+        count = lib.corutv_autotune_entry(i, ctypes.byref(mt), ctypes.byref(kt), ctypes.byref(nb), ctypes.byref(tr),
+                                          ctypes.byref(kg), ctypes.byref(st), ctypes.byref(us))
+        if i >= count:
+            return out
+        out.append({"m": mt.value, "k": kt.value, "panel_cols": nb.value, "trans": tr.value,
+                    "kgroup": kg.value, "stages": st.value, "us": us.value})
+        i += 1
 
 
 def corutv_set_graphs(ctx, enable: bool = True) -> None:

@@ -923,6 +923,29 @@ corutv_status corutv_set_graphs(corutv_ctx* ctx, int enable) {
     return CORUTV_OK;
 }
 
+corutv_status corutv_set_autotune(int enable) {
+    tc_set_autotune(enable != 0);
+    return CORUTV_OK;
+}
+
+int corutv_autotune_entry(int index, int64_t* mtot, int64_t* ktot, int* nb, int* trans, int* kgroup, int* stages,
+                          float* us) {
+    long long mt = 0, kt = 0;
+    int b = 0, tr = 0, kg = 0, st = 0;
+    float t = 0.f;
+    const int count = tc_autotune_entry(index, &mt, &kt, &b, &tr, &kg, &st, &t);
+    if (index >= 0 && index < count) {
+        if (mtot) *mtot = mt;
+        if (ktot) *ktot = kt;
+        if (nb) *nb = b;
+        if (trans) *trans = tr;
+        if (kgroup) *kgroup = kg;
+        if (stages) *stages = st;
+        if (us) *us = t;
+    }
+    return count;
+}
+
 corutv_status corutv_profile_enable(corutv_ctx* ctx, int enable) {
     CKS(check_ctx(ctx));
     std::lock_guard<std::mutex> lk(ctx->call_mu);

@@ -37,7 +37,11 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "tc.cuh"
 
@@ -901,13 +905,15 @@ uint32_t make_idesc(bool tf32, bool a_mn_major, int n) {
 // for trans = 1) with `kseg` K segments `seg_stride` columns apart; B: panel
 // with nparts * ellp rows of the K-major operand (ldb); output: the panel c
 // (ell columns, type tcout) = sum over the nparts column groups.
-cudaError_t tc_launch(const void* a, bool tf32, long long mtot, long long ktot_seg, int kseg, long long seg_stride,
-                      const CUtensorMap& map_a, int a_boxes, int a_box_cols, const void* b, long long ldb,
-                      long long brows_k, int nparts, int trans, int64_t ell, int64_t ellp, void* part,
-                      int* tile_cnt, void* c,
-                      ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel, cudaStream_t st,
-                      int kgroup, TcPieces* pieces, const uint8_t* a_tiles = nullptr, long long a_ntp = 0,
-                      long long a_seg_bytes = 0) {
+// One launch of the product with kgroup K boxes per stage and `stages_req`
+// ring stages (0: as many as fit 200 KB).
+cudaError_t tc_launch_cfg(const void* a, bool tf32, long long mtot, long long ktot_seg, int kseg, long long seg_stride,
+                          const CUtensorMap& map_a, int a_boxes, int a_box_cols, const void* b, long long ldb,
+                          long long brows_k, int nparts, int trans, int64_t ell, int64_t ellp, void* part,
+                          int* tile_cnt, void* c,
+                          ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel, cudaStream_t st,
+                          int kgroup, int stages_req, TcPieces* pieces, const uint8_t* a_tiles, long long a_ntp,
+                          long long a_seg_bytes) {
     const Plan pl = make_plan(mtot, ktot_seg, kseg, tf32, num_sms, kgroup);
     const int ke = tf32 ? 32 : 64;  // K elements per 128-byte row
     const int nb = nparts * (int)ellp;
@@ -968,6 +974,7 @@ cudaError_t tc_launch(const void* a, bool tf32, long long mtot, long long ktot_s
     p.a_bytes = kTileM * 128;
     p.stage_bytes = (uint32_t)kgroup * (p.a_bytes + (uint32_t)nb * 128);
     p.stages = std::min<int>(kMaxStages, (int)((200 * 1024) / p.stage_bytes));
+    if (stages_req > 0) p.stages = std::min(p.stages, stages_req);
     if (p.stages < 2) return cudaErrorInvalidValue;
     uint32_t cols = 32;
     while (cols < (uint32_t)nb) cols <<= 1;
@@ -986,7 +993,108 @@ cudaError_t tc_launch(const void* a, bool tf32, long long mtot, long long ktot_s
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner of the stage shape (corutv_set_autotune): for each product shape
+// (M and K extents, K segments, operand kind, B width, direction, output
+// handling, grid) the first launch times the candidates -- one or two
+// 128-byte K boxes per stage, each with the deepest ring that fits and with
+// half of it -- three launches each with CUDA events on the caller's stream,
+// keeps the fastest (its best launch) for the process, and launches it;
+// later launches of that shape use the kept choice. Off, or while a stream
+// is being captured into a graph, the rule of sketch_kgroup applies.
+struct TuneKey {
+    long long mtot, ktot;
+    int kseg, tf32, trans, tiled, nb, sms, out_f64, defer;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(mtot, ktot, kseg, tf32, trans, tiled, nb, sms, out_f64, defer) <
+               std::tie(o.mtot, o.ktot, o.kseg, o.tf32, o.trans, o.tiled, o.nb, o.sms, o.out_f64, o.defer);
+    }
+};
+struct TuneVal {
+    int kgroup, stages;
+    float us;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+std::vector<TuneKey> g_tune_order;
+std::atomic<int> g_tune_on{0};
+
+cudaError_t tc_launch(const void* a, bool tf32, long long mtot, long long ktot_seg, int kseg, long long seg_stride,
+                      const CUtensorMap& map_a, int a_boxes, int a_box_cols, const void* b, long long ldb,
+                      long long brows_k, int nparts, int trans, int64_t ell, int64_t ellp, void* part,
+                      int* tile_cnt, void* c,
+                      ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel, cudaStream_t st,
+                      int kgroup, TcPieces* pieces, const uint8_t* a_tiles = nullptr, long long a_ntp = 0,
+                      long long a_seg_bytes = 0) {
+    auto go = [&](int kg, int stages) {
+        return tc_launch_cfg(a, tf32, mtot, ktot_seg, kseg, seg_stride, map_a, a_boxes, a_box_cols, b, ldb, brows_k,
+                             nparts, trans, ell, ellp, part, tile_cnt, c, tcout, ldc, num_sms, flags, cancel, st, kg,
+                             stages, pieces, a_tiles, a_ntp, a_seg_bytes);
+    };
+    if (!g_tune_on.load(std::memory_order_relaxed)) return go(kgroup, 0);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return go(kgroup, 0);
+    }
+    const int nb = nparts * (int)ellp;
+    const TuneKey key{mtot, ktot_seg, kseg, tf32 ? 1 : 0, trans, a_tiles ? 1 : 0, nb, num_sms,
+                      tcout == T_F64 ? 1 : 0, pieces ? 1 : 0};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) return go(it->second.kgroup, it->second.stages);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    TuneVal best{kgroup, 0, 1e30f};
+    for (int kg = 1; kg <= 2 && e == cudaSuccess; ++kg) {
+        const int smax = std::min<int>(kMaxStages, (200 * 1024) / (kg * (kTileM * 128 + nb * 128)));
+        for (int stages : {smax, smax / 2}) {
+            if (stages < 2 || (stages == smax / 2 && smax / 2 == smax)) continue;
+            float t_best = 1e30f;
+            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                e = cudaEventRecord(e0, st);
+                if (e == cudaSuccess) e = go(kg, stages);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e == cudaSuccess) t_best = std::min(t_best, 1000.f * ms);
+            }
+            if (e == cudaSuccess && t_best < best.us) best = TuneVal{kg, stages, t_best};
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (g_tune.emplace(key, best).second) g_tune_order.push_back(key);
+    }
+    return go(best.kgroup, best.stages);
+}
+
 }  // namespace
+
+void tc_set_autotune(bool on) { g_tune_on.store(on ? 1 : 0); }
+
+int tc_autotune_entry(int index, long long* mtot, long long* ktot, int* nb, int* trans, int* kgroup, int* stages,
+                      float* us) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (index < 0 || index >= (int)g_tune_order.size()) return (int)g_tune_order.size();
+    const TuneKey& k = g_tune_order[index];
+    const TuneVal& v = g_tune.at(k);
+    *mtot = k.mtot;
+    *ktot = k.ktot;
+    *nb = k.nb;
+    *trans = k.trans;
+    *kgroup = v.kgroup;
+    *stages = v.stages;
+    *us = v.us;
+    return (int)g_tune_order.size();
+}
 
 int64_t tc_counter_elems(int64_t m, int64_t n) { return (std::max(m, n) + kTileM - 1) / kTileM; }
 

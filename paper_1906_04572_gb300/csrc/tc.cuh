@@ -84,4 +84,10 @@ cudaError_t launch_prep_f32(const float* a, int64_t m, int64_t n, int64_t lda, f
 cudaError_t launch_split_panel(const float* q, int64_t ldq, int64_t rows, int64_t ell, int64_t ellp, void* q3,
                                int64_t ldq3, const int* cancel, cudaStream_t st);
 
+// Stage-shape autotuner of the tensor-core products (process-wide).
+void tc_set_autotune(bool on);
+// Number of tuned shapes; for 0 <= index < that number, its extents and choice.
+int tc_autotune_entry(int index, long long* mtot, long long* ktot, int* nb, int* trans, int* kgroup, int* stages,
+                      float* us);
+
 }  // namespace corutv

@@ -319,3 +319,42 @@ def test_bf16_last_round_refinement_reaches_fp64_error(ctx):
     print("bf16 plain", e[0] / e_or, "last round x2", e[1] / e_or)
     assert e[0] <= 1.01 * e_or
     assert e[1] <= 1.01 * e_or and e[1] <= e[0] * (1 + 1e-3)
+
+
+@pytest.mark.parametrize("prec,u_p", [("bf16", 2.0 ** -8), ("tf32", 2.0 ** -10)])
+def test_autotuned_products_meet_the_budget(ctx, prec, u_p):
+    """With the stage-shape autotuner on, the first factorisation tunes each
+    product shape (timed candidates, then the chosen launch), the second
+    reuses the choices: both stay within the per-precision budget of the FP64
+    oracle, the second is bitwise the first (same choices, fixed sums), and
+    every choice is one of the candidate shapes."""
+    m, n, k, p, q = 2600, 2100, 60, 10, 2
+    a = synth.spectrum_matrix(m, n, synth.c3_sigma(min(m, n)), 0.0, 21)
+    a32 = a.astype(np.float32)
+    a64 = a32.astype(np.float64)
+    ell = k + p
+    psi = synth.gaussian_psi(n, ell, seed=5)
+    ref = oracle.corutv(a64, k, p, q, psi)
+    na = np.linalg.norm(a64)
+    e_or = np.linalg.norm(a64 - ref["U"] @ ref["T"] @ ref["V"].T) / na
+    budget = 4 * u_p * np.sqrt(ell) * np.linalg.norm(a64, 2) / na
+    corutv.corutv_set_autotune(True)
+    try:
+        outs = []
+        for _ in range(2):
+            out = ctx.factor(dev(a32, torch.float32), k, p, q, prec, psi=dev(psi))
+            assert ctx.sync() == 0
+            outs.append({x: host(out[x]) for x in ("U", "T", "V")})
+    finally:
+        corutv.corutv_set_autotune(False)
+    for o in outs:
+        e_gpu = np.linalg.norm(a64 - o["U"] @ o["T"] @ o["V"].T) / na
+        assert e_gpu <= e_or + budget, (e_gpu, e_or, budget)
+    for x in ("U", "T", "V"):
+        assert np.array_equal(outs[0][x], outs[1][x]), x
+    entries = corutv.corutv_autotune_entries()
+    assert entries
+    for ent in entries:
+        assert ent["kgroup"] in (1, 2) and 2 <= ent["stages"] <= 8 and ent["us"] > 0
+        stage_bytes = ent["kgroup"] * (128 * 128 + ent["panel_cols"] * 128)
+        assert ent["stages"] * stage_bytes <= 200 * 1024
