@@ -19,8 +19,10 @@
  *    context owns its workspace and streams.
  *  - Errors are reported only through the returned status; nothing aborts or
  *    exits. corutv_last_error gives a one-line message for the calling thread.
- *  - ell = k + p must satisfy 1 <= k <= ell < min(m, n) and ell <= 128
- *    (Sec. 3.1: "an integer k <= ell < min{m, n}"); q >= 0.
+ *  - ell = k + p must satisfy 1 <= k <= ell < min(m, n) (Sec. 3.1: "an
+ *    integer k <= ell < min{m, n}"), and ell <= 128 for the tensor-core
+ *    sketch precisions (BF16, TF32), ell <= 320 for FP64 and FP32 sketches;
+ *    q >= 0.
  *  - Every step of every call runs in this library's CUDA kernels; there is
  *    no CPU fallback. Without a usable GPU, corutv_create returns CORUTV_ECUDA.
  */
@@ -172,7 +174,8 @@ corutv_status corutv_factor_rows(corutv_ctx* ctx, corutv_dtype dtype, const void
  * Lagrange multipliers with the CoR-UTV thresholding operator
  * C_delta(B) = U(:,1:r) T(1:r,:) V^T, r = #{i : T_ii > delta}, and the
  * shrinkage S_delta(x) = sgn(x) max(|x| - delta, 0) (Sec. 4). opts->k is the
- * rank guess, 1 <= k <= 64 (CORUTV_EINVAL otherwise); the low-rank step uses
+ * rank guess, 1 <= k <= 160 and ell = 2k <= 128 for tensor-core sketches
+ * (CORUTV_EINVAL otherwise); the low-rank step uses
  * ell = 2k and q = 1 (Sec. 5.3) and a fresh Psi per iteration (Philox stream
  * opts->stream + j + 1).
  * Y_0 = S_0 = 0; mu_{j+1} = min(rho mu_j, mu_bar); stop after the first
@@ -282,7 +285,9 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
 /* Sec. 3.1 "C = Q R": thin QR of the rows x ell FP64 matrix C (rows >= ell)
  * by CholeskyQR2 (Gram in FP64, Cholesky in FP64, shifted once if the
  * first Gram is not numerically positive definite). Q: rows x ell (ldq),
- * R: ell x ell upper (optional), diag(R) > 0. */
+ * R: ell x ell upper (optional), diag(R) > 0. 1 <= ell <= 320 (beyond 128
+ * the Cholesky runs in global memory and the triangular solve as R^-1 and a
+ * product). */
 corutv_status corutv_orth(corutv_ctx* ctx, const double* C, int64_t rows, int64_t ell, int64_t ldc,
                           double* Q, int64_t ldq, double* R);
 
@@ -296,7 +301,9 @@ corutv_status corutv_selftest_wait(corutv_ctx* ctx, int64_t limit_ns);
 
 /* Eq. 8: D P = Qt Rt for the ell x ell FP64 matrix D (row stride ell), one
  * thread block, FP64, Businger-Golub pivoting on recomputed column norms
- * (lowest index on ties), diag(Rt) >= 0. Qt, Rt: ell x ell. */
+ * (lowest index on ties), diag(Rt) >= 0. Qt, Rt: ell x ell, 1 <= ell <= 320:
+ * up to 128 in shared memory, where norms within 2^-45 relative of each other
+ * count as ties; beyond, in global memory with an exact comparison. */
 corutv_status corutv_qrcp(corutv_ctx* ctx, const double* D, int64_t ell, double* Qt, double* Rt,
                           int32_t* perm);
 

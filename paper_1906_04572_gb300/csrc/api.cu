@@ -226,10 +226,13 @@ corutv_status make_plan(FactorPlan& pl, ElemType ta, int64_t m, int64_t n, int64
     if (pl.ell >= std::min(m, n))
         return fail(CORUTV_EINVAL, "ell = k + p = %lld must be < min(m, n) = %lld", (long long)pl.ell,
                     (long long)std::min(m, n));
-    if (pl.ell > 128) return fail(CORUTV_EINVAL, "ell = %lld exceeds the supported maximum 128", (long long)pl.ell);
     if (lda < n) return fail(CORUTV_EINVAL, "lda = %lld < n = %lld", (long long)lda, (long long)n);
     if (prec < CORUTV_P_F64 || prec > CORUTV_P_BF16) return fail(CORUTV_EINVAL, "unknown sketch precision %d", (int)prec);
     pl.tensor = (prec == CORUTV_P_TF32 || prec == CORUTV_P_BF16);
+    // tensor-core sketches up to 128 columns; FP64 / FP32 sketches up to 320
+    if (pl.ell > (pl.tensor ? 128 : kMaxEllSimt))
+        return fail(CORUTV_EINVAL, "ell = %lld exceeds the supported maximum %d for this sketch precision",
+                    (long long)pl.ell, pl.tensor ? 128 : kMaxEllSimt);
     if (prec == CORUTV_P_TF32 && ta != T_F32) return fail(CORUTV_EINVAL, "TF32 sketches need FP32 input");
     if (d_mode != 0 && d_mode != 1) return fail(CORUTV_EINVAL, "d_mode %d is not supported (0 exact D, 1 single-pass core)", d_mode);
     pl.dmode = d_mode;
@@ -288,7 +291,7 @@ void carve_factor(C& cv, const FactorPlan& pl, FactorBufs& b) {
     b.racc = pl.dmode == 1 ? cv.template take<double>(ll) : nullptr;
     b.racc2 = pl.dmode == 1 ? cv.template take<double>(ll) : nullptr;
     b.defic = cv.template take<int>(pl.ellp);
-    b.rinv = cv.template take<float>(trsm_rinv_floats(pl.ellp));
+    b.rinv = reinterpret_cast<float*>(cv.template take<double>(trsm_rinv_floats(pl.ellp)));  // FP64 for wide FP64 panels
     b.xc = cv.template take<char>(pn * es_c);
     b.q1c = cv.template take<char>(pm * es_c);
     b.q2c = cv.template take<char>(pl.split ? 3 * std::max(pm, pn) * 2 : std::max(pm, pn) * es_d);
@@ -439,7 +442,9 @@ corutv_status orth(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, co
 
 // U = Q1 Qt is formed from the explicit Qt (qform) for FP32 panels wider than 64
 // columns; otherwise from the reflectors.
-bool explicit_qt(const FactorPlan& pl, ElemType tout) { return pl.tp == T_F32 && tout == T_F32 && pl.ell > 64; }
+bool explicit_qt(const FactorPlan& pl, ElemType tout) {
+    return pl.ell > 128 || (pl.tp == T_F32 && tout == T_F32 && pl.ell > 64);
+}
 
 // Algorithm 1 on device data; leaves Q1, Q2, D, Qt, Rt, perm in the buffers.
 // psi_dev: optional n x ell row-major FP64 test matrix.
@@ -580,7 +585,13 @@ corutv_status emit_user(const Exec& ex, const FactorPlan& pl, const FactorBufs& 
     void* uq = pl.tr ? v : u;  // receives Q1 Qt
     void* vq = pl.tr ? u : v;  // receives Q2 P
     const int64_t lduq = pl.tr ? ldv : ldu, ldvq = pl.tr ? ldu : ldv;
-    if (uq && explicit_qt(pl, tout)) {
+    if (uq && explicit_qt(pl, tout) && pl.tp == T_F64) {
+        // Q1 Qt as an FP64 product with the explicit Qt (widths beyond the
+        // reflector kernel's shared memory)
+        GemmArgs g{A_PANEL, B_SMALL, O_ROWMAJ, T_F64, tout, b.q1, pl.ldm, b.qt, ell, uq, lduq, 0,
+                   pl.m, ell, ell, 1, ex.cancel, T_F64};
+        CK(launch_gemm_simt(g, ex.st));
+    } else if (uq && explicit_qt(pl, tout)) {
         // Q1 Qt as a product with the explicit Qt (FP32): for wide Qt the reflector
         // form below is a long per-row chain (ell reflectors of ell entries each)
         float* qt32 = static_cast<float*>(b.tmp);
@@ -1138,7 +1149,8 @@ corutv_status corutv_sketch(corutv_ctx* ctx, corutv_dtype dtype, corutv_prec pre
     if (!is_device_ptr(A) || !is_device_ptr(X) || !is_device_ptr(C))
         return fail(CORUTV_EINVAL, "corutv_sketch takes device pointers only");
     const int64_t xrows = trans ? m : n, crows = trans ? n : m;
-    if (ell < 1 || ell > 128 || ldx < ell || ldc < ell || lda < n || m < 1 || n < 1)
+    const bool tc_prec = prec == CORUTV_P_TF32 || prec == CORUTV_P_BF16 || (int)prec == CORUTV_P_BF16X3;
+    if (ell < 1 || ell > (tc_prec ? 128 : kMaxEllSimt) || ldx < ell || ldc < ell || lda < n || m < 1 || n < 1)
         return fail(CORUTV_EINVAL, "bad sketch sizes");
     std::lock_guard<std::mutex> lk(ctx->call_mu);
     DeviceGuard guard(ctx->device);
@@ -1255,7 +1267,7 @@ corutv_status corutv_orth(corutv_ctx* ctx, const double* C, int64_t rows, int64_
     if (!C || !Q) return fail(CORUTV_EINVAL, "null pointer");
     if (!is_device_ptr(C) || !is_device_ptr(Q) || (R && !is_device_ptr(R)))
         return fail(CORUTV_EINVAL, "corutv_orth takes device pointers only");
-    if (ell < 1 || ell > 128 || rows < ell || ldc < ell || ldq < ell) return fail(CORUTV_EINVAL, "bad orth sizes");
+    if (ell < 1 || ell > kMaxEllSimt || rows < ell || ldc < ell || ldq < ell) return fail(CORUTV_EINVAL, "bad orth sizes");
     std::lock_guard<std::mutex> lk(ctx->call_mu);
     DeviceGuard guard(ctx->device);
     FactorPlan pl{};
@@ -1271,6 +1283,7 @@ corutv_status corutv_orth(corutv_ctx* ctx, const double* C, int64_t rows, int64_
     measure.take<double>(ell * ell);
     measure.take<double>(ell * ell);
     measure.take<int>(8);
+    measure.take<double>(trsm_rinv_floats(ell));
     CKS(ensure_ws(ctx, ctx->ws, measure.off, ctx->stream));
     Carver cv(ctx->ws.ptr);
     double* cp = cv.take<double>(pm);
@@ -1281,6 +1294,7 @@ corutv_status corutv_orth(corutv_ctx* ctx, const double* C, int64_t rows, int64_
     b.g = cv.take<double>(ell * ell);
     b.r = cv.take<double>(ell * ell);
     b.skip = cv.take<int>(8);
+    b.rinv = reinterpret_cast<float*>(cv.take<double>(trsm_rinv_floats(ell)));  // wide panels only
     CK(launch_rowmajor_to_panel(C, ldc, rows, ell, ell, cp, T_F64, pl.ldm, ctx->stream));
     Exec ex{ctx->stream, ctx->flags, nullptr, ctx->num_sms};
     pl.torth = T_F64;
@@ -1309,7 +1323,7 @@ corutv_status corutv_qrcp(corutv_ctx* ctx, const double* D, int64_t ell, double*
     if (!D || !Qt || !Rt || !perm) return fail(CORUTV_EINVAL, "null pointer");
     if (!is_device_ptr(D) || !is_device_ptr(Qt) || !is_device_ptr(Rt) || !is_device_ptr(perm))
         return fail(CORUTV_EINVAL, "corutv_qrcp takes device pointers only");
-    if (ell < 1 || ell > 128) return fail(CORUTV_EINVAL, "ell must be in [1, 128]");
+    if (ell < 1 || ell > kMaxEllSimt) return fail(CORUTV_EINVAL, "ell must be in [1, %d]", kMaxEllSimt);
     std::lock_guard<std::mutex> lk(ctx->call_mu);
     DeviceGuard guard(ctx->device);
     const size_t work_bytes = sizeof(double) * (size_t)(ell * (ell + 2));
@@ -1361,7 +1375,8 @@ extern "C" corutv_status corutv_rpca(corutv_ctx* ctx, corutv_dtype dtype, const 
     if (!M || !opts || !L || !S) return fail(CORUTV_EINVAL, "M, opts, L and S must not be NULL");
     if (dtype != CORUTV_F64 && dtype != CORUTV_F32) return fail(CORUTV_EINVAL, "unknown dtype");
     const int64_t k = opts->k;
-    if (k < 1 || 2 * k > 128) return fail(CORUTV_EINVAL, "rank guess k must be in [1, 64] (ell = 2k <= 128)");
+    if (k < 1 || 2 * k > kMaxEllSimt)
+        return fail(CORUTV_EINVAL, "rank guess k must be in [1, %d] (ell = 2k <= %d)", kMaxEllSimt / 2, kMaxEllSimt);
     if (ldm < n) return fail(CORUTV_EINVAL, "ldm < n");
     const bool dev = is_device_ptr(M);
     if (is_device_ptr(L) != dev || is_device_ptr(S) != dev)
@@ -1438,8 +1453,15 @@ extern "C" corutv_status corutv_rpca(corutv_ctx* ctx, corutv_dtype dtype, const 
         // L_{j+1} = C_{1/mu_j}(B_j): CoR-UTV of B_j with ell = 2k, q = 1, fresh Psi
         CKS(run_factor(ex, pl, b, bmat, nullptr, opts->seed, opts->stream + (uint32_t)j + 1u));
         // U = Q1 Qt (FP64 panel) from the QRCP's reflectors
-        CK(launch_apply_reflectors(b.q1, pl.tp, pl.ldm, m, pl.ell, b.refl, b.upanel, T_F64, pl.ldm, true, done,
-                                   ctx->stream));
+        if (pl.ell > 128) {
+            // wide sketches: U = Q1 Qt as an FP64 product with the explicit Qt
+            GemmArgs g{A_PANEL, B_SMALL, O_PANEL, pl.tp, T_F64, b.q1, pl.ldm, b.qt, pl.ell, b.upanel, pl.ldm, 0,
+                       m, pl.ell, pl.ell, 1, done, T_F64};
+            CK(launch_gemm_simt(g, ctx->stream));
+        } else {
+            CK(launch_apply_reflectors(b.q1, pl.tp, pl.ldm, m, pl.ell, b.refl, b.upanel, T_F64, pl.ldm, true, done,
+                                       ctx->stream));
+        }
         CK(launch_rpca_rank_z(b.rt, b.q2, pl.tp, pl.ldn, b.perm, n, pl.ell, 1.0 / mus[j], rank_dev, b.zpanel,
                               pl.ldn, done, ctx->stream));
         RpcaIterArgs ua{m_dev, tm, ldm_dev, m, n,

@@ -75,6 +75,10 @@ int device_sms();
 
 // Counts every kernel launch issued by this library (instrumentation).
 void count_launch();
+// Largest sketch width ell on the SIMT paths (FP64 / FP32 sketches): the
+// ell x ell steps beyond 128 run in global memory (one block each), the
+// products in column groups of at most 128.
+constexpr int kMaxEllSimt = 320;
 
 // Programmatic dependent launch. Every kernel of the library is launched with
 // programmatic stream serialisation, so the next kernel in a stream can be

@@ -2,7 +2,7 @@
 // and D = Q1^T (A Q2), eq. 7) in a single launch, with the split sums reduced
 // inside the kernel in a fixed order.
 //
-// X, Y: FP32 panels (column j at X + j * ldx, `len` rows), ell <= 128
+// X, Y: FP32 panels (column j at X + j * ldx, `len` rows), ell <= 320
 // columns. G: ell x ell FP64, row-major. The output is cut into 64 x 64
 // tiles (only those on and above the diagonal when Y is X: the others are
 // the mirror images, bitwise); each tile's rows of X / Y are split into S
@@ -288,7 +288,7 @@ int64_t gram_f32_counters(int64_t len, int ell, int num_sms) {
 cudaError_t launch_gram_f32(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_t len, int ell,
                             double* out, float* work, int* cnt, int num_sms, const int* cancel, cudaStream_t st,
                             const TcPieces& px, const TcPieces& py, bool writeback) {
-    if (ell < 1 || ell > 128 || len < 1 || !work || !cnt) return cudaErrorInvalidValue;
+    if (ell < 1 || ell > kMaxEllSimt || len < 1 || !work || !cnt) return cudaErrorInvalidValue;
     const GramPlan p = gram_plan(len, ell, num_sms, x == y && ldx == ldy);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(p.nc * kGCluster), (unsigned)p.tiles, 1);

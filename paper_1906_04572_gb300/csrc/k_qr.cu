@@ -11,6 +11,8 @@
 
 #include <algorithm>
 
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace corutv {
@@ -359,7 +361,9 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
 }
 
 __device__ __forceinline__ float completion_entry(int64_t i, int j, int64_t rows) {
-    const unsigned long long key = ((unsigned long long)i << 8) | (unsigned long long)(j & 0xff);
+    // (i, j) with j < 256 keeps its original key; wider columns add their high bits at the top
+    const unsigned long long key =
+        (((unsigned long long)i << 8) | (unsigned long long)(j & 0xff)) + ((unsigned long long)(j >> 8) << 56);
     const unsigned long long h1 = splitmix64(2 * key), h2 = splitmix64(2 * key + 1);
     const float u1 = (float)((double)((h1 >> 11) + 1) * 0x1p-53);  // (0, 1]
     const float u2 = (float)((double)(h2 >> 11) * 0x1p-53);        // [0, 1)
@@ -1143,16 +1147,20 @@ __global__ void gather_v_kernel(const TQ* q2, int64_t ldq2, int64_t n, int ell, 
     __shared__ double tile[128][33];
     const int64_t i0 = (int64_t)blockIdx.x * 32;
     const int tid = threadIdx.x;  // 256
-    for (int e = tid; e < ell * 32; e += blockDim.x) {
-        const int j = e / 32, ii = e % 32;
-        const int64_t i = i0 + ii;
-        tile[j][ii] = (i < n) ? (double)q2[(int64_t)perm[j] * ldq2 + i] : 0.0;
-    }
-    __syncthreads();
-    for (int e = tid; e < ell * 32; e += blockDim.x) {
-        const int ii = e / ell, j = e % ell;
-        const int64_t i = i0 + ii;
-        if (i < n) v[i * ldv + j] = (TV)tile[j][ii];
+    for (int j0 = 0; j0 < ell; j0 += 128) {  // column blocks of 128 (one for ell <= 128)
+        const int nj = ell - j0 < 128 ? ell - j0 : 128;
+        if (j0 > 0) __syncthreads();
+        for (int e = tid; e < nj * 32; e += blockDim.x) {
+            const int j = e / 32, ii = e % 32;
+            const int64_t i = i0 + ii;
+            tile[j][ii] = (i < n) ? (double)q2[(int64_t)perm[j0 + j] * ldq2 + i] : 0.0;
+        }
+        __syncthreads();
+        for (int e = tid; e < nj * 32; e += blockDim.x) {
+            const int ii = e / nj, j = e % nj;
+            const int64_t i = i0 + ii;
+            if (i < n) v[i * ldv + j0 + j] = (TV)tile[j][ii];
+        }
     }
 }
 
@@ -1169,13 +1177,372 @@ __global__ void copy_small_kernel(const double* src, int ell, TD* dst, int trans
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// The ell x ell steps for sketch widths 128 < ell <= 320 (SIMT paths only):
+// one block each, the matrices in global memory (L2-resident: at most 800 KB)
+// instead of one SM's shared memory. The same arithmetic as the one-SM
+// kernels above, organised for correctness before speed: these widths serve
+// the paper's larger RPCA problems (ell = 2k = 200, 300), not the throughput
+// workloads.
+// ---------------------------------------------------------------------------
+constexpr int kBigThreads = 1024;
+constexpr int kBigSlots = (kMaxEllSimt + 31) / 32;  // rows per lane of a one-warp column
+
+// Cholesky with the contract of cholesky_kernel (shift passes, dependent
+// columns, skip flag, status words), right-looking in the square-root-free
+// form on R itself as the working matrix: p_t = S_tt, L_t = S_t / p_t,
+// S_ac -= L_ta S_tc (t < a <= c), then R_tc = S_tc / sqrt(p_t).
+template <bool kDefic>
+__global__ void __launch_bounds__(kBigThreads)
+cholesky_big_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, int* skip_out,
+                    const int* cancel, double unit_roundoff, int* defic, double tau_rel) {
+    pdl_wait();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (cancel && *cancel) {
+        if (skip_out && tid == 0) *skip_out = 1;
+        return;
+    }
+    __shared__ double L[kMaxEllSimt];
+    __shared__ double ys[kMaxEllSimt];
+    __shared__ int rowdep[kMaxEllSimt];
+    __shared__ double rt_s, trace_s, dmin_s;
+    __shared__ int fail_s;
+    if (warp == 0) {
+        double mx = 0.0, tr = 0.0;
+        for (int a = lane; a < ell; a += 32) {
+            mx = fmax(mx, g[(size_t)a * ell + a]);
+            tr += g[(size_t)a * ell + a];
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            tr += __shfl_xor_sync(0xffffffffu, tr, o);
+        }
+        if (lane == 0) {
+            dmin_s = tau_rel * mx;
+            trace_s = tr;
+        }
+    }
+    __syncthreads();
+    const double dmin = kDefic ? dmin_s : 0.0;
+    int attempt = 0;
+    for (; attempt < 3; ++attempt) {
+        // shift s = 11 (rows ell + ell (ell + 1)) u ||C||_F^2 (Fukaya et al.), then x100
+        const double shift = attempt == 0 ? 0.0
+                                          : 11.0 * ((double)rows * ell + (double)ell * (ell + 1)) * unit_roundoff *
+                                                trace_s * (attempt == 1 ? 1.0 : 100.0);
+        for (int e = tid; e < ell * ell; e += kBigThreads) {
+            const int a = e / ell, c = e - a * ell;
+            r[e] = a == c ? g[e] + shift : g[e];
+        }
+        for (int a = tid; a < ell; a += kBigThreads) {
+            rowdep[a] = 0;
+            if (kDefic) defic[a] = 0;
+        }
+        if (tid == 0) fail_s = 0;
+        __syncthreads();
+        for (int t = 0; t < ell; ++t) {
+            if (tid == 0) {
+                const double p = r[(size_t)t * ell + t];
+                const bool dep = kDefic && !gt_nonneg(p, dmin);
+                if (!(dep || pos_finite(p))) fail_s = 1;
+                if (dep) {
+                    rowdep[t] = 1;
+                    defic[t] = 1;
+                }
+                rt_s = dep ? 0.0 : rcp_nr(p);
+            }
+            __syncthreads();
+            if (fail_s) break;
+            const double rt = rt_s;
+            for (int c = t + tid; c < ell; c += kBigThreads) L[c] = r[(size_t)t * ell + c] * rt;
+            __syncthreads();
+            for (int a = t + 1 + warp; a < ell; a += kBigThreads / 32) {
+                const double la = L[a];
+                double* ra = r + (size_t)a * ell;
+                const double* rtt = r + (size_t)t * ell;
+                for (int c = a + lane; c < ell; c += 32) ra[c] = fma(-la, rtt[c], ra[c]);
+            }
+            __syncthreads();
+        }
+        const bool failed = fail_s != 0;
+        __syncthreads();
+        if (!failed) break;
+    }
+    pdl_trigger();
+    const bool broke = attempt == 3;
+    for (int t = tid; t < ell; t += kBigThreads)
+        ys[t] = (broke || rowdep[t]) ? 0.0 : rsqrt_nr(r[(size_t)t * ell + t]);
+    __syncthreads();
+    for (int e = tid; e < ell * ell; e += kBigThreads) {
+        const int a = e / ell, c = e - a * ell;
+        const bool unit = broke || rowdep[a];
+        const double x = c >= a ? r[e] * ys[a] : 0.0;
+        r[e] = c < a ? 0.0 : (unit ? (a == c ? 1.0 : 0.0) : x);
+    }
+    if (tid == 0) {
+        if (broke) atomicExch(&flags[FLAG_BREAKDOWN], 1);
+        if (attempt > 0) atomicAdd(&flags[FLAG_SHIFTED], 1);
+        if (skip_out) *skip_out = (attempt > 0 && !broke) ? 0 : 1;
+    }
+}
+
+// R^{-1} (type T, ell x ldri row-major, zero below the diagonal and beyond
+// column ell) by column-oriented back substitution, one warp per column
+// (lane l keeps rows l + 32 s), R read from global memory.
+template <typename T>
+__global__ void __launch_bounds__(256) rinv_big_kernel(const double* r, int ell, T* ri, int ldri, const int* cancel) {
+    pdl_wait();
+    if (cancel && *cancel) return;
+    const int lane = threadIdx.x & 31, j = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (j >= ell) return;
+    T b[kBigSlots];
+#pragma unroll
+    for (int s = 0; s < kBigSlots; ++s) b[s] = (lane + 32 * s == j) ? (T)1 : (T)0;
+    for (int k = j; k >= 0; --k) {
+        const int sk = k >> 5;
+        T bk = b[0];
+#pragma unroll
+        for (int s = 1; s < kBigSlots; ++s)
+            if (s == sk) bk = b[s];
+        const T xk = __shfl_sync(0xffffffffu, bk, k & 31) / (T)r[(size_t)k * ell + k];
+#pragma unroll
+        for (int s = 0; s < kBigSlots; ++s) {
+            const int i = lane + 32 * s;
+            if (i < k) b[s] = fma(-(T)r[(size_t)i * ell + k], xk, b[s]);
+            else if (i == k) b[s] = xk;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < kBigSlots; ++s) {
+        const int i = lane + 32 * s;
+        if (i < ell) ri[(size_t)i * ldri + j] = i <= j ? b[s] : (T)0;
+    }
+    if (j == ell - 1)
+        for (int i = lane; i < ell; i += 32)
+            for (int jj = ell; jj < ldri; ++jj) ri[(size_t)i * ldri + jj] = (T)0;
+}
+
+// After Q = C R^{-1} (as a product): columns the extra CholeskyQR pass found
+// dependent get their random completion, and qc receives Q's copy.
+template <typename TI, typename TQC>
+__global__ void trsm_post_kernel(TI* q, int64_t ldq, int64_t rows, int ell, TQC* qc, int64_t ldqc, const int* defic,
+                                 const int* cancel) {
+    pdl_wait();
+    if (cancel && *cancel) return;
+    const int64_t total = rows * ell;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / rows);
+        const int64_t i = e - (int64_t)j * rows;
+        TI v = q[(int64_t)j * ldq + i];
+        if (defic && defic[j]) {
+            v = (TI)completion_entry(i, j, rows);
+            q[(int64_t)j * ldq + i] = v;
+        }
+        if (qc) qc[(int64_t)j * ldqc + i] = (TQC)v;
+    }
+}
+
+// QRCP (eq. 8) with the contract of qrcp_kernel: Businger-Golub pivoting on
+// column norms recomputed at every step, Householder reflections, diag(Rt) >= 0;
+// the pivot is the largest norm, the lowest index among equal ones (exact
+// comparison). W (column-major, column c at W + c * ell) is the reflector
+// buffer itself: V, tau and the signs end there in qrcp_kernel's layout.
+__global__ void __launch_bounds__(kBigThreads)
+qrcp_big_kernel(const double* d, int ell, double* refl, double* rt, int* perm, const int* cancel) {
+    pdl_wait();
+    if (cancel && *cancel) return;
+    __shared__ double nrm[kMaxEllSimt];
+    __shared__ double tau[kMaxEllSimt];
+    __shared__ int pv[kMaxEllSimt];
+    __shared__ double wv[32];
+    __shared__ int wi[32];
+    __shared__ double sc_tau, sc_scale, sc_beta;
+    __shared__ int sc_p, sc_reflect;
+    double* W = refl;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = kBigThreads / 32;
+    for (int e = tid; e < ell * ell; e += kBigThreads) {
+        const int a = e / ell, b = e - a * ell;  // d row-major: (a, b) -> column b, row a
+        W[(size_t)b * ell + a] = d[e];
+    }
+    for (int c = tid; c < ell; c += kBigThreads) pv[c] = c;
+    __syncthreads();
+    for (int c = warp; c < ell; c += nw) {
+        double s = 0.0;
+        for (int i = lane; i < ell; i += 32) s = fma(W[(size_t)c * ell + i], W[(size_t)c * ell + i], s);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) nrm[c] = s;
+    }
+    __syncthreads();
+    for (int j = 0; j < ell; ++j) {
+        // pivot: the largest recomputed norm among columns j.., the lowest index on ties
+        {
+            double bv = -1.0;
+            int bi = ell;
+            for (int c = j + tid; c < ell; c += kBigThreads)
+                if (nrm[c] > bv || (nrm[c] == bv && c < bi)) {
+                    bv = nrm[c];
+                    bi = c;
+                }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) {
+                    bv = ov;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                wv[warp] = bv;
+                wi[warp] = bi;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double v = wv[0];
+                int i = wi[0];
+                for (int w = 1; w < nw; ++w)
+                    if (wv[w] > v || (wv[w] == v && wi[w] < i)) {
+                        v = wv[w];
+                        i = wi[w];
+                    }
+                sc_p = i;
+            }
+            __syncthreads();
+        }
+        const int p = sc_p;
+        if (p != j) {
+            for (int i = tid; i < ell; i += kBigThreads) {
+                const double t = W[(size_t)j * ell + i];
+                W[(size_t)j * ell + i] = W[(size_t)p * ell + i];
+                W[(size_t)p * ell + i] = t;
+            }
+            if (tid == 0) {
+                const int t = pv[j];
+                pv[j] = pv[p];
+                pv[p] = t;
+                const double s = nrm[j];
+                nrm[j] = nrm[p];
+                nrm[p] = s;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            // beta = -sign(alpha) |x| (sign(+-0) = +), tau = (beta - alpha) / beta,
+            // v = x / (alpha - beta) below the diagonal; H = I when that part is exactly zero
+            const double sj = nrm[j];
+            const double alpha = W[(size_t)j * ell + j];
+            const bool neg = alpha < 0.0;
+            const double nr = sqrt(sj);
+            const bool reflect = sj != alpha * alpha;
+            const double beta = neg ? nr : -nr;
+            sc_reflect = reflect ? 1 : 0;
+            sc_beta = reflect ? beta : alpha;
+            sc_tau = reflect ? (beta - alpha) / beta : 0.0;
+            sc_scale = reflect ? 1.0 / (alpha - beta) : 0.0;
+            tau[j] = sc_tau;
+        }
+        __syncthreads();
+        if (sc_reflect)
+            for (int i = j + 1 + tid; i < ell; i += kBigThreads) W[(size_t)j * ell + i] *= sc_scale;
+        __syncthreads();
+        const double tj = sc_tau;
+        const double* v = W + (size_t)j * ell;
+        for (int c = j + 1 + warp; c < ell; c += nw) {
+            double* x = W + (size_t)c * ell;
+            double part = 0.0;
+            for (int i = j + 1 + lane; i < ell; i += 32) part = fma(v[i], x[i], part);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            const double f = tj * (x[j] + part);  // v^T x_c with v_j = 1
+            double acc = 0.0;
+            for (int i = j + 1 + lane; i < ell; i += 32) {
+                const double nv = fma(-f, v[i], x[i]);
+                x[i] = nv;
+                acc = fma(nv, nv, acc);
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) {
+                x[j] -= f;
+                nrm[c] = acc;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) W[(size_t)j * ell + j] = sc_beta;
+        __syncthreads();
+    }
+    // Rt = upper(W) with diag(Rt) >= 0 (row a scaled by the sign of its diagonal)
+    for (int e = tid; e < ell * ell; e += kBigThreads) {
+        const int a = e / ell, b = e - a * ell;
+        const double sa = W[(size_t)a * ell + a] < 0.0 ? -1.0 : 1.0;
+        rt[e] = b >= a ? sa * W[(size_t)b * ell + a] : 0.0;
+    }
+    for (int c = tid; c < ell; c += kBigThreads) perm[c] = pv[c];
+    __syncthreads();
+    pdl_trigger();
+    // tau and the signs after V; then V keeps only the part below the diagonal
+    for (int c = tid; c < ell; c += kBigThreads) {
+        refl[(size_t)ell * ell + c] = tau[c];
+        refl[(size_t)ell * ell + ell + c] = W[(size_t)c * ell + c] < 0.0 ? -1.0 : 1.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < ell * ell; e += kBigThreads) {
+        const int jj = e / ell, i = e - jj * ell;
+        if (i <= jj) W[e] = 0.0;
+    }
+}
+
+// Qt = H_0 ... H_{ell-1} diag(sgn) column by column, one warp per column,
+// the reflectors read from global memory.
+__global__ void __launch_bounds__(256) qform_big_kernel(const double* refl, int ell, double* qt, const int* cancel) {
+    pdl_wait();
+    if (cancel && *cancel) return;
+    const double* tau = refl + (size_t)ell * ell;
+    const double* sgn = tau + ell;
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (c >= ell) return;
+    double q[kBigSlots];
+#pragma unroll
+    for (int t = 0; t < kBigSlots; ++t) q[t] = (lane + 32 * t == c) ? 1.0 : 0.0;
+    for (int k = c; k >= 0; --k) {
+        const double* v = refl + (size_t)k * ell;  // v[k] = 1 implied, v[i] = 0 for i < k
+        double part = 0.0;
+#pragma unroll
+        for (int t = 0; t < kBigSlots; ++t) {
+            const int i = lane + 32 * t;
+            if (i < ell) part = fma(i == k ? 1.0 : v[i], q[t], part);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        const double f = tau[k] * part;
+#pragma unroll
+        for (int t = 0; t < kBigSlots; ++t) {
+            const int i = lane + 32 * t;
+            if (i >= k && i < ell) q[t] = fma(-f, i == k ? 1.0 : v[i], q[t]);
+        }
+    }
+    const double sc = sgn[c];
+#pragma unroll
+    for (int t = 0; t < kBigSlots; ++t) {
+        const int i = lane + 32 * t;
+        if (i < ell) qt[(size_t)i * ell + c] = q[t] * sc;
+    }
+}
+
+
 }  // namespace
 
 cudaError_t launch_trimul(const double* rn, const double* ra, double* out, int64_t ell, bool transpose,
                           const int* skip, const int* cancel, cudaStream_t st) {
-    if (ell < 1 || ell > 128 || out == rn || out == ra) return cudaErrorInvalidValue;
+    if (ell < 1 || ell > kMaxEllSimt || out == rn || out == ra) return cudaErrorInvalidValue;
     count_launch();
-    cudaError_t e = launch_pdl(trimul_kernel, dim3((unsigned)ell), dim3(128), (size_t)0, st, rn, ra, out, (int)ell,
+    cudaError_t e = launch_pdl(trimul_kernel, dim3((unsigned)ell), dim3(ell > 128 ? (unsigned)((ell + 31) / 32 * 32) : 128u),
+                               (size_t)0, st, rn, ra, out, (int)ell,
                                transpose ? 1 : 0, skip, cancel);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -1183,7 +1550,15 @@ cudaError_t launch_trimul(const double* rn, const double* ra, double* out, int64
 cudaError_t launch_cholesky(const double* g, int64_t ell, int64_t rows, double* r, int* flags,
                                int* skip_out, const int* cancel, cudaStream_t st, double unit_roundoff,
                                int* defic, double tau_rel) {
-    if (ell < 1 || ell > kCholMaxEll) return cudaErrorInvalidValue;
+    if (ell < 1 || ell > kMaxEllSimt) return cudaErrorInvalidValue;
+    if (ell > kCholMaxEll) {
+        count_launch();
+        cudaError_t pe = defic ? launch_pdl(cholesky_big_kernel<true>, dim3(1), dim3(kBigThreads), (size_t)0, st, g, (int)ell,
+                                            rows, r, flags, skip_out, cancel, unit_roundoff, defic, tau_rel)
+                               : launch_pdl(cholesky_big_kernel<false>, dim3(1), dim3(kBigThreads), (size_t)0, st, g,
+                                            (int)ell, rows, r, flags, skip_out, cancel, unit_roundoff, defic, tau_rel);
+        return pe != cudaSuccess ? pe : cudaGetLastError();
+    }
     const size_t smem = sizeof(double) * (size_t)ell * (ell + 1) + sizeof(unsigned short) * (size_t)ell * (ell + 1) / 2;
     auto kern = defic ? cholesky_kernel<true> : cholesky_kernel<false>;
     cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(kern));
@@ -1197,11 +1572,60 @@ cudaError_t launch_cholesky(const double* g, int64_t ell, int64_t rows, double* 
     return cudaGetLastError();
 }
 
+// Q = C R^{-1} for 128 < ell <= 320: R^{-1} (rinv_big_kernel, into rinv_work),
+// then the product in column groups of at most 128, the last group first so
+// that an in-place solve (q == c) reads only columns it has not overwritten
+// (group J needs C's columns up to its own last one: R^{-1} is upper
+// triangular), then the dependent columns' completion and the copy qc.
+cudaError_t trsm_big(const void* c, ElemType tp, int64_t ldc, int64_t rows, int ell, const double* r, ElemType tc,
+                     void* q, int64_t ldq, void* qc, ElemType tqc, int64_t ldqc, const int* cancel, cudaStream_t st,
+                     const int* defic, void* rinv_work) {
+    if (!rinv_work || ell > kMaxEllSimt || tp != tc || (tp != T_F64 && tp != T_F32)) return cudaErrorInvalidValue;
+    const int ldri = (ell + 7) & ~7;
+    const unsigned rb = (unsigned)((ell + 7) / 8);
+    count_launch();
+    cudaError_t e = tc == T_F64 ? launch_pdl(rinv_big_kernel<double>, dim3(rb), dim3(256), (size_t)0, st, r, ell,
+                                             static_cast<double*>(rinv_work), ldri, cancel)
+                                : launch_pdl(rinv_big_kernel<float>, dim3(rb), dim3(256), (size_t)0, st, r, ell,
+                                             static_cast<float*>(rinv_work), ldri, cancel);
+    if (e != cudaSuccess) return e;
+    const int64_t es = elem_size(tc);
+    for (int64_t j0 = (int64_t)(ell - 1) / 128 * 128; j0 >= 0; j0 -= 128) {
+        const int64_t L = std::min<int64_t>(128, ell - j0);
+        GemmArgs g{A_PANEL, B_SMALL, O_PANEL, tp, tc, c, ldc,
+                   static_cast<const char*>(rinv_work) + j0 * es, ldri,
+                   static_cast<char*>(q) + j0 * ldq * es, ldq, 0, rows, j0 + L, L, 1, cancel};
+        e = launch_gemm_simt(g, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (!defic && !qc) return cudaSuccess;
+    const int64_t total = rows * ell;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 4096);
+    count_launch();
+    auto post = [&](auto* qp, auto* qcp) {
+        return launch_pdl(trsm_post_kernel<std::remove_pointer_t<decltype(qp)>, std::remove_pointer_t<decltype(qcp)>>,
+                          dim3(blocks), dim3(256), (size_t)0, st, qp, ldq, rows, ell, qcp, ldqc, defic, cancel);
+    };
+    if (tp == T_F64) {
+        double* qp = static_cast<double*>(q);
+        if (!qc || tqc == T_F64) e = post(qp, static_cast<double*>(qc));
+        else if (tqc == T_F32) e = post(qp, static_cast<float*>(qc));
+        else return cudaErrorInvalidValue;
+    } else {
+        float* qp = static_cast<float*>(q);
+        if (!qc || tqc == T_F32) e = post(qp, static_cast<float*>(qc));
+        else if (tqc == T_F64) e = post(qp, static_cast<double*>(qc));
+        else return cudaErrorInvalidValue;
+    }
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 cudaError_t launch_trsm_rows(const void* c, ElemType tp, int64_t ldc, int64_t rows, int64_t ell,
                              const double* r, ElemType tc, void* q, int64_t ldq, void* qc,
                              ElemType tqc, int64_t ldqc, const int* cancel, cudaStream_t st,
                              const int* defic, float* rinv_work) {
     const int l = (int)ell;
+    if (l > 128) return trsm_big(c, tp, ldc, rows, l, r, tc, q, ldq, qc, tqc, ldqc, cancel, st, defic, rinv_work);
     auto al16 = [](const void* p, int64_t ld) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0 && ld % 4 == 0; };
     if (tp == T_F32 && tc == T_F32 && rinv_work && l >= 1 && l <= 128 && al16(c, ldc) && al16(q, ldq) &&
         (reinterpret_cast<uintptr_t>(rinv_work) & 15) == 0) {
@@ -1222,7 +1646,17 @@ cudaError_t launch_trsm_rows(const void* c, ElemType tp, int64_t ldc, int64_t ro
 
 cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, int* perm, double* work,
                         const int* cancel, cudaStream_t st, bool form_q) {
-    if (ell < 1 || ell > 128 || !work) return cudaErrorInvalidValue;
+    if (ell < 1 || ell > kMaxEllSimt || !work) return cudaErrorInvalidValue;
+    if (ell > 128) {
+        count_launch();
+        cudaError_t pe = launch_pdl(qrcp_big_kernel, dim3(1), dim3(kBigThreads), (size_t)0, st, d, (int)ell, work, rt,
+                                    perm, cancel);
+        if (pe != cudaSuccess || !form_q) return pe != cudaSuccess ? pe : cudaGetLastError();
+        count_launch();
+        pe = launch_pdl(qform_big_kernel, dim3((unsigned)((ell + 7) / 8)), dim3(256), (size_t)0, st,
+                        static_cast<const double*>(work), (int)ell, qt, cancel);
+        return pe != cudaSuccess ? pe : cudaGetLastError();
+    }
     const size_t smem = sizeof(double) * ((size_t)ell * (ell | 1) + 5 * (size_t)ell) + sizeof(int) * ell;
     cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(qrcp_kernel));
     if (e != cudaSuccess) return e;

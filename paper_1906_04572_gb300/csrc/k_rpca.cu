@@ -20,7 +20,7 @@ namespace {
 
 constexpr int kUpdCols = 128;   // threads per block = columns per tile
 constexpr int kUpdRows = 16;    // rows per tile
-constexpr int kMaxEll = 128;  // ell = 2k; kernels are instantiated for ell <= 64 and <= 128
+constexpr int kMaxEll = kMaxEllSimt;  // ell = 2k; kernels are instantiated for ell <= 64, <= 128 and <= 320
 constexpr int kFinalThreads = 256;
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -63,6 +63,8 @@ __global__ void rpca_init_kernel(const TM* m, int64_t ldm, int64_t rows, int64_t
 }
 
 // r = #{i : Rt_ii > inv_mu}; Z[i][s] = sum_h Q2[i][perm[h]] Rt[s][h] for s < r.
+// Rt is staged in shared memory up to ell = 128 and read from global memory
+// (the same entries for every thread of a warp) beyond.
 template <typename TQ, int kE>
 __global__ void rank_z_kernel(const double* rt, const TQ* q2, int64_t ldq2, const int* perm,
                               int64_t cols, int ell, double inv_mu, int* rank, double* z, int64_t ldz,
@@ -70,10 +72,12 @@ __global__ void rank_z_kernel(const double* rt, const TQ* q2, int64_t ldq2, cons
     pdl_trigger();
     pdl_wait();
     if (cancel && *cancel) return;
-    extern __shared__ double Rs[];  // ell x ell
+    extern __shared__ double Rsm[];  // ell x ell (kE <= 128)
+    const double* Rs = kE <= 128 ? Rsm : rt;
     __shared__ int ps[kE];
     __shared__ int r_s;
-    for (int e = threadIdx.x; e < ell * ell; e += blockDim.x) Rs[e] = rt[e];
+    if (kE <= 128)
+        for (int e = threadIdx.x; e < ell * ell; e += blockDim.x) Rsm[e] = rt[e];
     for (int e = threadIdx.x; e < ell; e += blockDim.x) ps[e] = perm[e];
     if (threadIdx.x == 0) {
         int r = 0;
@@ -343,7 +347,7 @@ cudaError_t launch_rpca_init(const void* m, ElemType tm, int64_t ldm, int64_t ro
 template <typename TQ, int kE>
 cudaError_t rank_z_launch(const double* rt, const void* vq2, int64_t ldv, const int* perm, int64_t cols, int64_t ell,
                           double inv_mu, int* rank, double* z, int64_t ldz, const int* cancel, cudaStream_t st) {
-    const size_t smem = sizeof(double) * (size_t)ell * ell;
+    const size_t smem = kE <= 128 ? sizeof(double) * (size_t)ell * ell : 0;
     cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(rank_z_kernel<TQ, kE>));
     if (e != cudaSuccess) return e;
     count_launch();
@@ -357,10 +361,12 @@ cudaError_t launch_rpca_rank_z(const double* rt, const void* vq2, ElemType tq2, 
                                int64_t ldz, const int* cancel, cudaStream_t st) {
     if (ell > kMaxEll) return cudaErrorInvalidValue;
     if (tq2 == T_F64)
-        return ell <= 64 ? rank_z_launch<double, 64>(rt, vq2, ldv, perm, cols, ell, inv_mu, rank, z, ldz, cancel, st)
-                         : rank_z_launch<double, 128>(rt, vq2, ldv, perm, cols, ell, inv_mu, rank, z, ldz, cancel, st);
-    return ell <= 64 ? rank_z_launch<float, 64>(rt, vq2, ldv, perm, cols, ell, inv_mu, rank, z, ldz, cancel, st)
-                     : rank_z_launch<float, 128>(rt, vq2, ldv, perm, cols, ell, inv_mu, rank, z, ldz, cancel, st);
+        return ell <= 64    ? rank_z_launch<double, 64>(rt, vq2, ldv, perm, cols, ell, inv_mu, rank, z, ldz, cancel, st)
+               : ell <= 128 ? rank_z_launch<double, 128>(rt, vq2, ldv, perm, cols, ell, inv_mu, rank, z, ldz, cancel, st)
+                            : rank_z_launch<double, kMaxEll>(rt, vq2, ldv, perm, cols, ell, inv_mu, rank, z, ldz, cancel, st);
+    return ell <= 64    ? rank_z_launch<float, 64>(rt, vq2, ldv, perm, cols, ell, inv_mu, rank, z, ldz, cancel, st)
+           : ell <= 128 ? rank_z_launch<float, 128>(rt, vq2, ldv, perm, cols, ell, inv_mu, rank, z, ldz, cancel, st)
+                        : rank_z_launch<float, kMaxEll>(rt, vq2, ldv, perm, cols, ell, inv_mu, rank, z, ldz, cancel, st);
 }
 
 template <typename TM, typename TS, int kE>
@@ -378,12 +384,14 @@ cudaError_t launch_rpca_update(const RpcaIterArgs& a, int* nparts, cudaStream_t 
     *nparts = (int)(grid.x * grid.y);
     if (a.tm == T_F32) {
         const float* m = static_cast<const float*>(a.m);
-        return a.ell <= 64 ? update_launch<float, float, 64>(a, m, a.s, a.y, a.b, grid, st)
-                           : update_launch<float, float, 128>(a, m, a.s, a.y, a.b, grid, st);
+        return a.ell <= 64    ? update_launch<float, float, 64>(a, m, a.s, a.y, a.b, grid, st)
+               : a.ell <= 128 ? update_launch<float, float, 128>(a, m, a.s, a.y, a.b, grid, st)
+                              : update_launch<float, float, kMaxEll>(a, m, a.s, a.y, a.b, grid, st);
     }
     const double* m = static_cast<const double*>(a.m);
-    return a.ell <= 64 ? update_launch<double, double, 64>(a, m, a.s64, a.y64, a.b64, grid, st)
-                       : update_launch<double, double, 128>(a, m, a.s64, a.y64, a.b64, grid, st);
+    return a.ell <= 64    ? update_launch<double, double, 64>(a, m, a.s64, a.y64, a.b64, grid, st)
+           : a.ell <= 128 ? update_launch<double, double, 128>(a, m, a.s64, a.y64, a.b64, grid, st)
+                          : update_launch<double, double, kMaxEll>(a, m, a.s64, a.y64, a.b64, grid, st);
 }
 
 cudaError_t launch_rpca_finish_iter(const double* res_part, int nparts, const double* fro_part,
@@ -413,10 +421,12 @@ cudaError_t launch_rpca_reconstruct(const double* u, int64_t ldu, const double* 
                                     void* lout, ElemType tl, int64_t ldl, cudaStream_t st) {
     if (ell > kMaxEll) return cudaErrorInvalidValue;
     if (tl == T_F32)
-        return ell <= 64 ? reconstruct_launch<float, 64>(u, ldu, z, ldz, rank, ell, rows, cols, lout, ldl, st)
-                         : reconstruct_launch<float, 128>(u, ldu, z, ldz, rank, ell, rows, cols, lout, ldl, st);
-    return ell <= 64 ? reconstruct_launch<double, 64>(u, ldu, z, ldz, rank, ell, rows, cols, lout, ldl, st)
-                     : reconstruct_launch<double, 128>(u, ldu, z, ldz, rank, ell, rows, cols, lout, ldl, st);
+        return ell <= 64    ? reconstruct_launch<float, 64>(u, ldu, z, ldz, rank, ell, rows, cols, lout, ldl, st)
+               : ell <= 128 ? reconstruct_launch<float, 128>(u, ldu, z, ldz, rank, ell, rows, cols, lout, ldl, st)
+                            : reconstruct_launch<float, kMaxEll>(u, ldu, z, ldz, rank, ell, rows, cols, lout, ldl, st);
+    return ell <= 64    ? reconstruct_launch<double, 64>(u, ldu, z, ldz, rank, ell, rows, cols, lout, ldl, st)
+           : ell <= 128 ? reconstruct_launch<double, 128>(u, ldu, z, ldz, rank, ell, rows, cols, lout, ldl, st)
+                        : reconstruct_launch<double, kMaxEll>(u, ldu, z, ldz, rank, ell, rows, cols, lout, ldl, st);
 }
 
 }  // namespace corutv

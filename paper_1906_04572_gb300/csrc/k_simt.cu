@@ -7,6 +7,7 @@
 //  * layout / precision conversions of the tall-skinny panels.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "internal.cuh"
@@ -158,8 +159,21 @@ int gemm_simt_splits(int64_t R, int64_t K, int num_sms) {
 }
 
 cudaError_t launch_gemm_simt(const GemmArgs& g, cudaStream_t st) {
-    if (g.R <= 0 || g.L <= 0 || g.L > 128 || g.splits < 1) return cudaErrorInvalidValue;
+    if (g.R <= 0 || g.L <= 0 || g.L > kMaxEllSimt || g.splits < 1) return cudaErrorInvalidValue;
     const ElemType tb = g.tb == T_SAME ? g.tc : g.tb;
+    if (g.L > 128) {
+        // column groups of at most 128 output columns: the B operand and the
+        // output (each split's partial alike) start j0 columns further on
+        for (int64_t j0 = 0; j0 < g.L; j0 += 128) {
+            GemmArgs h = g;
+            h.L = std::min<int64_t>(128, g.L - j0);
+            h.b = static_cast<const char*>(g.b) + (g.bmode == B_PANEL ? j0 * g.ldb : j0) * elem_size(tb);
+            h.out = static_cast<char*>(g.out) + (g.omode == O_PANEL ? j0 * g.ldo : j0) * elem_size(g.tc);
+            const cudaError_t e = launch_gemm_simt(h, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     if (g.ta == T_F64 && tb == T_F64 && g.tc == T_F64) return launch_types<double, double, double>(g, st);
     if (g.ta == T_F32 && tb == T_F32 && g.tc == T_F32) return launch_types<float, float, float>(g, st);
     if (g.ta == T_F32 && tb == T_F64 && g.tc == T_F64) return launch_types<float, double, double>(g, st);
