@@ -360,6 +360,42 @@ def latency_single(ctx, A, k, p, q, prec, reps, graphs=False):
                     (", replayed from its CUDA graph" if graphs else "")}
 
 
+def concurrent_factorisations(device_index, A, k, p, q, prec, flops, counts=(1, 2, 3, 4), nreq=12):
+    """The same workload as a job of nreq factorisations submitted at once
+    through corutv_submit with 1..4 serving slots (each slot with its own
+    stream and workspace): while one factorisation runs its single-SM FP64
+    steps, another's products use the other SMs. Wall time from the first
+    submission to the last completion, inputs resident on the device."""
+    import torch
+    from paper_1906_04572_gb300 import Context, corutv
+    m, n = A.shape
+    ell = k + p
+    out = {}
+    for slots in counts:
+        with Context(device_index, max_slots=slots) as sctx:
+            bufs = [(torch.empty((m, ell), device=A.device, dtype=A.dtype),
+                     torch.empty((ell, ell), device=A.device, dtype=A.dtype),
+                     torch.empty((n, ell), device=A.device, dtype=A.dtype)) for _ in range(slots)]
+            warm = [corutv.corutv_submit(sctx.handle, corutv.make_request(A, k, p, q, prec, *bufs[i], stream=i))
+                    for i in range(slots)]
+            for tk in warm:
+                assert corutv.corutv_poll(sctx.handle, tk, timeout_us=600_000_000)[0] == corutv.OK
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            # request i writes the buffers of slot i mod slots (only timing is read)
+            tks = [corutv.corutv_submit(sctx.handle, corutv.make_request(A, k, p, q, prec, *bufs[i % slots],
+                                                                          stream=100 + i)) for i in range(nreq)]
+            for tk in tks:
+                assert corutv.corutv_poll(sctx.handle, tk, timeout_us=600_000_000)[0] == corutv.OK
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        out[f"slots_{slots}"] = {"ms_per_factorisation": wall / nreq * 1e3, "solves_per_s": nreq / wall,
+                                 "tflops": nreq * flops / wall / 1e12}
+    out["kind"] = (f"{nreq} factorisations of the same workload submitted at once through corutv_submit, "
+                   "wall clock from the first submission to the last completion")
+    return out
+
+
 def serving_c5(device_index, nreq, rate, prec, slots):
     """The serving stream (independent requests with Poisson arrivals, m, n ~
     U[256, 4096], k ~ U[5, 64], ell = k + 10, q ~ U{0, 1, 2}, FP32 inputs with
@@ -742,6 +778,7 @@ def run_ours(args):
     if not args.no_extra:
         extra["c1_latency"] = c1_latency(ctx, device, 50)
         extra["c2"] = c2_lines(ctx, device, args.steps)
+        extra["concurrent"] = concurrent_factorisations(local, A, k, p, q, prec, flops)
         extra["serving"] = serving_c5(local, args.serve_requests, args.serve_rate, "bf16", 8)
         extra["serving"]["capacity_vs_fp64"] = serving_capacity(local, args.serve_capacity, 8)
         extra["rpca"] = rpca_c4(ctx, device)

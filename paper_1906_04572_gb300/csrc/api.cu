@@ -323,6 +323,42 @@ struct Exchange {
     int64_t total_rows = 0;    // rows of the whole matrix (sizes the Cholesky shift)
 };
 
+// The bf16 splits A_m, A_l of the tiled copy (needed only by the projection,
+// eq. 7) cast on a side stream in row chunks while the main stream runs the
+// thin QRs' single-SM FP64 steps: one chunk is forked at the first Gram of
+// every thin QR and joined before the next product over A, the rest forked
+// and joined before the projection. The critical path casts A_h alone.
+struct CastOverlap {
+    cudaStream_t side = nullptr;
+    cudaEvent_t* ev = nullptr;   // 2 per chunk: fork (main) and done (side)
+    const void* a = nullptr;
+    ElemType ta = T_F32;
+    int64_t m = 0, n = 0, lda = 0;
+    void* out = nullptr;
+    const int* cancel = nullptr;
+    int chunks = 0, issued = 0, joined = 0;
+    corutv_status issue(cudaStream_t main) {
+        if (issued >= chunks) return CORUTV_OK;
+        const int64_t mt = (m + 127) / 128;
+        const int64_t rb0 = mt * issued / chunks, rb1 = mt * (issued + 1) / chunks;
+        CK(cudaEventRecord(ev[2 * issued], main));
+        CK(cudaStreamWaitEvent(side, ev[2 * issued], 0));
+        if (rb1 > rb0) CK(launch_cast_tiled_rows(a, ta, m, n, lda, out, 2, rb0, rb1, cancel, side));
+        CK(cudaEventRecord(ev[2 * issued + 1], side));
+        ++issued;
+        return CORUTV_OK;
+    }
+    corutv_status join(cudaStream_t main) {
+        for (; joined < issued; ++joined) CK(cudaStreamWaitEvent(main, ev[2 * joined + 1], 0));
+        return CORUTV_OK;
+    }
+    corutv_status finish(cudaStream_t main) {
+        while (issued < chunks) CKS(issue(main));
+        return join(main);
+    }
+};
+constexpr int kMaxCastChunks = 8;
+
 struct Exec {
     cudaStream_t st;
     int* flags;
@@ -330,6 +366,7 @@ struct Exec {
     int num_sms;
     Profiler* prof = nullptr;
     const Exchange* xch = nullptr;  // set for the rows of a row-partitioned matrix
+    CastOverlap* ov = nullptr;      // set: A_m, A_l are cast on a side stream (run_factor)
 };
 
 // buf (device, count elements of type t) <- its sum over the ranks: copied to
@@ -413,6 +450,7 @@ corutv_status orth(const Exec& ex, const FactorPlan& pl, const FactorBufs& b, co
     void* p1c = passes == 1 ? qc : nullptr;
     // pass 1 (the first reader of c: it adds any pieces the product left and completes c)
     CKS(gram(ex, pl, b, c, ld, c, ld, len, b.g, ex.cancel, tw, pieces, pieces, true));
+    if (ex.ov) CKS(ex.ov->issue(ex.st));  // a chunk of A_m, A_l beside the Cholesky and the solves
     if (sum) CKS(exchange_sum(ex, b.g, ell * ell, T_F64));
     const double u = tw == T_F64 ? 0x1p-53 : 0x1p-24;  // unit roundoff of the Gram arithmetic
     CK(launch_cholesky(b.g, ell, rows_all, b.r, ex.flags, b.skip, ex.cancel, ex.st, u));
@@ -465,7 +503,20 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
             // one pass over A: A^T for the K-major A^T Y, the tiled bf16 splits for eq. 7
             CK(launch_prep_f32(static_cast<const float*>(a), pl.ma, pl.na, pl.lda, b.at, pl.ldma, b.abf, b.a32,
                                pl.ldc32, ex.cancel, ex.st));
-        else if (pl.prec == CORUTV_P_BF16)
+        else if (pl.prec == CORUTV_P_BF16 && pl.split && ex.ov) {
+            // A_h now; A_m, A_l for eq. 7 in row chunks on the side stream (CastOverlap)
+            CK(launch_cast_tiled(a, pl.ta, pl.ma, pl.na, pl.lda, b.abf, 1, ex.cancel, ex.st));
+            CastOverlap& ov = *ex.ov;
+            ov.a = a;
+            ov.ta = pl.ta;
+            ov.m = pl.ma;
+            ov.n = pl.na;
+            ov.lda = pl.lda;
+            ov.out = b.abf;
+            ov.cancel = ex.cancel;
+            ov.chunks = (int)std::min<int64_t>(kMaxCastChunks, std::max<int64_t>(1, 2 * pl.q + 2));
+            ov.issued = ov.joined = 0;
+        } else if (pl.prec == CORUTV_P_BF16)
             // the tiled bf16 copy the products read (A_h), with A_m, A_l for eq. 7 when split
             CK(launch_cast_tiled(a, pl.ta, pl.ma, pl.na, pl.lda, b.abf, pl.split ? 3 : 1, ex.cancel, ex.st));
     } else {
@@ -482,6 +533,7 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     auto product = [&](bool a_rows, const void* opnd, void* out, TcPieces* pc, int nsegs = 1) -> corutv_status {
         const int64_t ldo = a_rows ? pl.ldna : pl.ldma, ldout = a_rows ? pl.ldma : pl.ldna;
         if (!pl.tensor) return sketch_simt(ex, pl, b, a_rows ? A_ROWS : A_COLS, a, pl.ta, opnd, pl.tcomp, out, ldout);
+        if (ex.ov && ex.ov->chunks) CKS(ex.ov->join(ex.st));  // no cast chunk beside a product
         ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
         if (pl.prec == CORUTV_P_BF16) {
             // the tiled bf16 copy (its first part, A_h) serves both directions
@@ -543,6 +595,7 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     // and D = W^T Q2 -- the same product with A, Q1 in the place of Q2.
     const void* pan = pl.tr ? b.q1 : b.q2;  // the operand panel (A's columns)
     if (pl.split) {
+        if (ex.ov && ex.ov->chunks) CKS(ex.ov->finish(ex.st));  // all of A_m, A_l before eq. 7
         CK(launch_split_panel(static_cast<const float*>(pan), pl.ldna, pl.na, ell, pl.ellp, b.q2c, pl.ldna,
                               ex.cancel, ex.st));
         ProfScope ps(ex.prof, CORUTV_STAGE_PROJECT, ex.st);
@@ -699,6 +752,8 @@ struct corutv_ctx {
     };
     std::map<std::string, GraphEntry> graph_cache;
     cudaStream_t cap_stream = nullptr;   // captures run here (the caller's stream may be the legacy one)
+    cudaStream_t side = nullptr;         // the A_m, A_l cast chunks (CastOverlap)
+    cudaEvent_t ov_ev[2 * kMaxCastChunks] = {};
 };
 
 namespace {
@@ -877,6 +932,10 @@ corutv_status corutv_destroy(corutv_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     drop_graphs(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->side) cudaStreamSynchronize(ctx->side);
+    for (auto ev : ctx->ov_ev)
+        if (ev) cudaEventDestroy(ev);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->ws.ptr) cudaFree(ctx->ws.ptr);
     if (ctx->flags) cudaFree(ctx->flags);
     if (ctx->switch_ev) cudaEventDestroy(ctx->switch_ev);
@@ -1054,8 +1113,21 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
             psi = ps;
         }
     }
+    // A_m, A_l of the projection cast beside the thin QRs (device input, bf16 sketches)
+    CastOverlap ov;
+    const bool overlap = dev && pl.split && pl.prec == CORUTV_P_BF16;
+    if (overlap && !ctx->side) {
+        CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+        for (auto& ev : ctx->ov_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
     auto enqueue = [&](cudaStream_t st) -> corutv_status {
-        const Exec ex{st, ctx->flags, nullptr, ctx->num_sms, &ctx->prof};
+        Exec ex{st, ctx->flags, nullptr, ctx->num_sms, &ctx->prof};
+        if (overlap) {
+            ov = CastOverlap();
+            ov.side = ctx->side;
+            ov.ev = ctx->ov_ev;
+            ex.ov = &ov;
+        }
         CKS(run_factor(ex, pl, b, a_dev, psi, opts->seed, opts->stream));
         return emit_user(ex, pl, b, ta, u_dev, ldu_dev, t_dev, v_dev, ldv_dev, perm_dev);
     };

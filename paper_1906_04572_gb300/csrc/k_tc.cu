@@ -779,14 +779,16 @@ __global__ void split_panel_kernel(const float* q, long long ldq, long long rows
 // 128 K rows). ntp (tiles per row block) is even, so 128-column blocks are
 // whole pairs. A block converts 128 rows x 512 columns: 128 threads per row,
 // four columns each (2 KB of FP32 read per row, 128-byte lines written).
+// NP = 1: A_h only; 3: A_h, A_m, A_l; 2: A_m, A_l only (parts 1 and 2).
+// Row blocks rb0 + blockIdx.y.
 template <typename TI, int NP>
 __global__ void __launch_bounds__(256)
 cast_tiled_kernel(const TI* a, long long m, long long n, long long lda, uint8_t* out, long long ntp,
-                  long long part_bytes, const int* cancel) {
+                  long long part_bytes, long long rb0, const int* cancel) {
     pdl_trigger();
     pdl_wait();
     if (cancel && *cancel) return;
-    const long long I = blockIdx.y;
+    const long long I = rb0 + blockIdx.y;
     const int half = threadIdx.x >> 7, t = threadIdx.x & 127;
     const long long c = (long long)blockIdx.x * 512 + 4 * t;  // first of this thread's four columns
     const long long J = c >> 6;
@@ -823,7 +825,7 @@ cast_tiled_kernel(const TI* a, long long m, long long n, long long lda, uint8_t*
             __nv_bfloat16 h[4], md[4], lo[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) split3(v[q], h[q], md[q], lo[q]);
-            *reinterpret_cast<uint2*>(tile + off) = *reinterpret_cast<const uint2*>(h);
+            if (NP == 3) *reinterpret_cast<uint2*>(tile + off) = *reinterpret_cast<const uint2*>(h);
             *reinterpret_cast<uint2*>(tile + part_bytes + off) = *reinterpret_cast<const uint2*>(md);
             *reinterpret_cast<uint2*>(tile + 2 * part_bytes + off) = *reinterpret_cast<const uint2*>(lo);
         }
@@ -1152,27 +1154,36 @@ int64_t tiled_ntp(int64_t n) { return ((n + 63) / 64 + 1) / 2 * 2; }
 
 int64_t tiled_part_bytes(int64_t m, int64_t n) { return ((m + kTileM - 1) / kTileM) * tiled_ntp(n) * 16384; }
 
-cudaError_t launch_cast_tiled(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, void* out, int nparts,
-                              const int* cancel, cudaStream_t st) {
+cudaError_t launch_cast_tiled_rows(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, void* out,
+                                   int parts, int64_t rb0, int64_t rb1, const int* cancel, cudaStream_t st) {
     if (m < 1 || n < 1 || lda < n || !out || (reinterpret_cast<uintptr_t>(out) & 15) != 0) return cudaErrorInvalidValue;
-    if (nparts != 1 && !(nparts == 3 && ta == T_F32)) return cudaErrorInvalidValue;
+    if (parts != 1 && !((parts == 2 || parts == 3) && ta == T_F32)) return cudaErrorInvalidValue;
     const int64_t ntp = tiled_ntp(n), mt = (m + kTileM - 1) / kTileM;
-    if (mt > 65535) return cudaErrorInvalidValue;
-    const dim3 grid((unsigned)((ntp + 7) / 8), (unsigned)mt);
+    if (rb0 < 0 || rb1 > mt || rb0 >= rb1 || rb1 - rb0 > 65535) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((ntp + 7) / 8), (unsigned)(rb1 - rb0));
     const long long pb = tiled_part_bytes(m, n);
     uint8_t* o = static_cast<uint8_t*>(out);
     count_launch();
     cudaError_t e;
     if (ta == T_F64)
         e = launch_pdl(cast_tiled_kernel<double, 1>, grid, dim3(256), (size_t)0, st, static_cast<const double*>(a),
-                       (long long)m, (long long)n, (long long)lda, o, (long long)ntp, pb, cancel);
-    else if (nparts == 1)
+                       (long long)m, (long long)n, (long long)lda, o, (long long)ntp, pb, (long long)rb0, cancel);
+    else if (parts == 1)
         e = launch_pdl(cast_tiled_kernel<float, 1>, grid, dim3(256), (size_t)0, st, static_cast<const float*>(a),
-                       (long long)m, (long long)n, (long long)lda, o, (long long)ntp, pb, cancel);
+                       (long long)m, (long long)n, (long long)lda, o, (long long)ntp, pb, (long long)rb0, cancel);
+    else if (parts == 2)
+        e = launch_pdl(cast_tiled_kernel<float, 2>, grid, dim3(256), (size_t)0, st, static_cast<const float*>(a),
+                       (long long)m, (long long)n, (long long)lda, o, (long long)ntp, pb, (long long)rb0, cancel);
     else
         e = launch_pdl(cast_tiled_kernel<float, 3>, grid, dim3(256), (size_t)0, st, static_cast<const float*>(a),
-                       (long long)m, (long long)n, (long long)lda, o, (long long)ntp, pb, cancel);
+                       (long long)m, (long long)n, (long long)lda, o, (long long)ntp, pb, (long long)rb0, cancel);
     return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_cast_tiled(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, void* out, int nparts,
+                              const int* cancel, cudaStream_t st) {
+    if (nparts != 1 && nparts != 3) return cudaErrorInvalidValue;
+    return launch_cast_tiled_rows(a, ta, m, n, lda, out, nparts, 0, (m + kTileM - 1) / kTileM, cancel, st);
 }
 
 cudaError_t launch_sketch_tc_tiled(const void* a_tiles, int64_t m, int64_t n, int trans, const void* x, int64_t ldx,

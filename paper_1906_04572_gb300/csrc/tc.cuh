@@ -41,6 +41,10 @@ int64_t tiled_ntp(int64_t n);
 int64_t tiled_part_bytes(int64_t m, int64_t n);
 cudaError_t launch_cast_tiled(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, void* out, int nparts,
                               const int* cancel, cudaStream_t st);
+// The same for the 128-row blocks [rb0, rb1) and a choice of parts: 1 (A_h),
+// 2 (A_m and A_l only, FP32 A), 3 (all three, FP32 A).
+cudaError_t launch_cast_tiled_rows(const void* a, ElemType ta, int64_t m, int64_t n, int64_t lda, void* out,
+                                   int parts, int64_t rb0, int64_t rb1, const int* cancel, cudaStream_t st);
 // launch_sketch_tc with A given as its tiled bf16 copy (launch_cast_tiled):
 // every stage of A is one contiguous bulk copy. nsegs > 1 multiplies by the
 // sum of the copy's first nsegs parts (A_h + A_m: A to about 16 significant
