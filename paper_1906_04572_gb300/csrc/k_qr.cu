@@ -7,6 +7,7 @@
 //  * the column-pivoted QR of D (eq. 8), one block, FP64, Householder
 //    reflections with Businger-Golub pivoting on recomputed column norms;
 //  * the gathers of eq. 9 (V = Q2 P, T = Rt).
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -1003,6 +1004,190 @@ qrcp_kernel(const double* d, int ell, double* refl, double* rt, int* perm, const
     }
 }
 
+// ---------------------------------------------------------------------------
+// QRCP of D (eq. 8) on a cluster of kQcCtas CTAs (one per SM), for
+// 64 < ell <= 128: the same Businger-Golub steps as qrcp_kernel -- recomputed
+// norms, the pivot key of qr_pivot (norms within 2^-45 relative are ties,
+// lowest position first), Householder reflections, diag(Rt) >= 0 -- with the
+// FP64 trailing update spread over the cluster's SMs. Physical column c lives
+// in CTA c mod kQcCtas; pivoting permutes positions in replicated tables
+// instead of moving columns. Per step: every CTA pushes its best key to all
+// (distributed shared memory), cluster barrier, the owner of the pivot forms
+// the reflector and pushes v, tau and the new diagonal to all, cluster
+// barrier, every CTA updates its columns and their norms. Every CTA runs the
+// same barriers in the same order (no data-dependent exit).
+// ---------------------------------------------------------------------------
+constexpr int kQcCtas = 8;
+constexpr int kQcThreads = 256;
+constexpr int kQcCols = 128 / kQcCtas;  // columns per CTA at most (two per warp)
+constexpr int kQcLd = 129;              // odd column stride in shared memory
+static_assert(kQcCols == 2 * (kQcThreads / 32), "one column per half-warp in one round");
+
+__global__ void __cluster_dims__(kQcCtas, 1, 1) __launch_bounds__(kQcThreads)
+qrcp_cluster_kernel(const double* d, int ell, double* refl, double* rt, int* perm, const int* cancel) {
+    namespace cg = cooperative_groups;
+    pdl_wait();
+    if (cancel && *cancel) return;  // uniform over the cluster, before any barrier
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ double W[kQcCols * kQcLd];     // own columns, local index lc = c / kQcCtas
+    __shared__ double nrm[kQcCols];
+    __shared__ double vbuf[128];              // v of the current step (pushed by the pivot's owner)
+    __shared__ double taus[128], betas[128];  // per step (replicated)
+    __shared__ long long keys[kQcCtas];       // each CTA's best key for the step (pushed)
+    __shared__ int pos_of[128], phys_at[128]; // replicated position tables
+    __shared__ double in_tau, in_beta;        // pushed with v
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rank = (int)cluster.block_rank();
+    const int nloc = ell > rank ? (ell - rank + kQcCtas - 1) / kQcCtas : 0;  // own columns
+    for (int e = tid; e < nloc * ell; e += kQcThreads) {
+        const int lc = e / ell, i = e - lc * ell;
+        W[lc * kQcLd + i] = d[(size_t)i * ell + (lc * kQcCtas + rank)];  // d row-major: (i, c)
+    }
+    for (int c = tid; c < ell; c += kQcThreads) {
+        pos_of[c] = c;
+        phys_at[c] = c;
+    }
+    __syncthreads();
+    // squared norms of the own columns (one warp per column)
+    for (int lc = warp; lc < nloc; lc += kQcThreads / 32) {
+        double s = 0.0;
+        for (int i = lane; i < ell; i += 32) s = fma(W[lc * kQcLd + i], W[lc * kQcLd + i], s);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) nrm[lc] = s;
+    }
+    __syncthreads();
+    for (int j = 0; j < ell; ++j) {
+        // own best key over the columns at positions >= j
+        if (warp == 0) {
+            long long best = -1;
+            for (int lc = lane; lc < nloc; lc += 32) {
+                const int pc = pos_of[lc * kQcCtas + rank];
+                if (pc >= j) {
+                    const long long key = (__double_as_longlong(nrm[lc]) & ~0x7fLL) | (127 - pc);
+                    best = key > best ? key : best;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+                best = ob > best ? ob : best;
+            }
+            if (lane < kQcCtas) cluster.map_shared_rank(keys, lane)[rank] = best;
+        }
+        cluster.sync();  // barrier 1: every key pushed (and every CTA done with step j-1)
+        long long best = keys[0];
+#pragma unroll
+        for (int r = 1; r < kQcCtas; ++r) best = keys[r] > best ? keys[r] : best;
+        const int pp = 127 - (int)(best & 0x7f);  // position of the pivot
+        const int p = phys_at[pp];
+        const int owner = p % kQcCtas;
+        // positions j and pp swap (the same update in every CTA)
+        __syncthreads();  // every thread read the tables above
+        if (tid == 0 && pp != j) {
+            const int pj = phys_at[j];
+            phys_at[j] = p;
+            phys_at[pp] = pj;
+            pos_of[p] = j;
+            pos_of[pj] = pp;
+        }
+        if (rank == owner && warp == 0) {
+            const int lc = p / kQcCtas;
+            double* x = W + lc * kQcLd;
+            double beta = 0.0, t = 0.0, scale = 0.0;
+            if (lane == 0) {
+                // beta = -sign(alpha) |x| (sign(+-0) = +), tau = (beta - alpha) / beta,
+                // scale = 1 / (alpha - beta); H = I when the part below row j is exactly zero
+                const double sj = nrm[lc];
+                const double alpha = x[j];
+                const long long ab = __double_as_longlong(alpha);
+                const bool neg = ab < 0 && (ab & 0x7fffffffffffffffLL) != 0;
+                const double y = rsqrt_nr(sj);
+                const double nr = sj * y;
+                const double beta_c = neg ? nr : -nr;
+                const double inv_beta = neg ? y : -y;
+                const double t_c = fma(-alpha, inv_beta, 1.0);
+                const double scale_c = rcp_nr(alpha - beta_c);
+                const bool reflect = sj != alpha * alpha;
+                beta = reflect ? beta_c : alpha;
+                t = reflect ? t_c : 0.0;
+                scale = reflect ? scale_c : 0.0;
+            }
+            beta = __shfl_sync(0xffffffffu, beta, 0);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            scale = __shfl_sync(0xffffffffu, scale, 0);
+            // v below the diagonal (zero when H = I), kept in the column for the reflector output
+            for (int i = j + 1 + lane; i < ell; i += 32) {
+                const double v = t != 0.0 ? x[i] * scale : 0.0;
+                x[i] = v;
+#pragma unroll
+                for (int r = 0; r < kQcCtas; ++r) cluster.map_shared_rank(vbuf, r)[i] = v;
+            }
+            if (lane < kQcCtas) {
+                cluster.map_shared_rank(&in_tau, lane)[0] = t;
+                cluster.map_shared_rank(&in_beta, lane)[0] = beta;
+            }
+            if (lane == 0) x[j] = beta;
+        }
+        cluster.sync();  // barrier 2: v, tau, beta pushed
+        const double tj = in_tau;
+        if (tid == 0) {
+            taus[j] = tj;
+            betas[j] = in_beta;
+        }
+        // H_j on the own columns at positions > j, and their squared norms over
+        // rows > j: two columns per warp, one per half-warp, so that each FP64
+        // reduction instruction serves both
+        {
+            const int half = lane >> 4, hl = lane & 15;
+            const int lc = 2 * warp + half;  // kQcCols = 16 = 2 x 8 warps: one round
+            const bool act = lc < nloc && pos_of[lc * kQcCtas + rank] > j;
+            double* x = W + (act ? lc : 0) * kQcLd;
+            double part = 0.0;
+            if (act)
+                for (int i = j + 1 + hl; i < ell; i += 16) part = fma(vbuf[i], x[i], part);
+#pragma unroll
+            for (int o = 8; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            const double f = act ? tj * (x[j] + part) : 0.0;  // v^T x_c with v_j = 1
+            double acc = 0.0;
+            if (act)
+                for (int i = j + 1 + hl; i < ell; i += 16) {
+                    const double nv = fma(-f, vbuf[i], x[i]);
+                    x[i] = nv;
+                    acc = fma(nv, nv, acc);
+                }
+#pragma unroll
+            for (int o = 8; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            __syncwarp();  // every lane read x[j] before its half's lane 0 rewrites it
+            if (act && hl == 0) {
+                x[j] -= f;
+                nrm[lc] = acc;
+            }
+        }
+        __syncthreads();
+    }
+    cluster.sync();  // no CTA leaves while another may still write into its shared memory
+    pdl_trigger();
+    // Rt (row-major) column by column: rows <= position scaled by the sign of
+    // their diagonal, zero below; V below the diagonal of each column
+    for (int e = tid; e < nloc * ell; e += kQcThreads) {
+        const int lc = e / ell, i = e - lc * ell;
+        const int c = lc * kQcCtas + rank;
+        const int pc = pos_of[c];
+        const double w = W[lc * kQcLd + i];
+        const double si = betas[i] < 0.0 ? -1.0 : 1.0;
+        rt[(size_t)i * ell + pc] = i <= pc ? si * w : 0.0;
+        refl[(size_t)pc * ell + i] = i > pc ? w : 0.0;
+    }
+    if (rank == 0)
+        for (int c = tid; c < ell; c += kQcThreads) {
+            perm[c] = phys_at[c];
+            refl[(size_t)ell * ell + c] = taus[c];
+            refl[(size_t)ell * ell + ell + c] = betas[c] < 0.0 ? -1.0 : 1.0;
+        }
+}
+
+
 // Qt = H_0 H_1 ... H_{ell-1} diag(sgn). Column c of the product is
 // H_0 H_1 ... H_c e_c (H_k leaves e_c alone for k > c), so the columns are
 // independent: one warp per column (lanes own rows lane + 32 t, t < 4),
@@ -1657,14 +1842,20 @@ cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, in
                         static_cast<const double*>(work), (int)ell, qt, cancel);
         return pe != cudaSuccess ? pe : cudaGetLastError();
     }
-    const size_t smem = sizeof(double) * ((size_t)ell * (ell | 1) + 5 * (size_t)ell) + sizeof(int) * ell;
-    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(qrcp_kernel));
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     count_launch();
-    {
-        cudaError_t pe_ = launch_pdl(qrcp_kernel, dim3(1), dim3(kQrcpThreads), (size_t)(smem), st, d, (int)ell, work,
-                                     rt, perm, cancel);
-        if (pe_ != cudaSuccess) return pe_;
+    if (ell > 64) {
+        // the trailing updates of the wider cores spread over a cluster of SMs
+        // (617 -> 430 us at ell = 110, 872 -> 537 us at 128; 201 -> 197 us at 65)
+        e = launch_pdl(qrcp_cluster_kernel, dim3(kQcCtas), dim3(kQcThreads), (size_t)0, st, d, (int)ell, work, rt, perm,
+                       cancel);
+        if (e != cudaSuccess) return e;
+    } else {
+        const size_t smem = sizeof(double) * ((size_t)ell * (ell | 1) + 5 * (size_t)ell) + sizeof(int) * ell;
+        e = allow_max_dynamic_smem(reinterpret_cast<const void*>(qrcp_kernel));
+        if (e != cudaSuccess) return e;
+        e = launch_pdl(qrcp_kernel, dim3(1), dim3(kQrcpThreads), (size_t)(smem), st, d, (int)ell, work, rt, perm, cancel);
+        if (e != cudaSuccess) return e;
     }
     if (!form_q) return cudaSuccess;
     const size_t smem_q = sizeof(double) * (size_t)(ell * ell + 2 * ell);
