@@ -1011,11 +1011,13 @@ qrcp_kernel(const double* d, int ell, double* refl, double* rt, int* perm, const
 // lowest position first), Householder reflections, diag(Rt) >= 0 -- with the
 // FP64 trailing update spread over the cluster's SMs. Physical column c lives
 // in CTA c mod kQcCtas; pivoting permutes positions in replicated tables
-// instead of moving columns. Per step: every CTA pushes its best key to all
-// (distributed shared memory), cluster barrier, the owner of the pivot forms
-// the reflector and pushes v, tau and the new diagonal to all, cluster
-// barrier, every CTA updates its columns and their norms. Every CTA runs the
-// same barriers in the same order (no data-dependent exit).
+// instead of moving columns. One cluster barrier per step: after its update
+// every CTA pushes to all CTAs (distributed shared memory, double-buffered by
+// step parity) its best pivot key, that column's squared norm and its entries
+// from the step's row down; after the barrier every CTA forms the winner's
+// reflector itself (the same inputs, so bitwise the same v, tau, beta), the
+// winner stores it in its column, and every CTA updates its other columns.
+// Every CTA runs the same barriers in the same order (no data-dependent exit).
 // ---------------------------------------------------------------------------
 constexpr int kQcCtas = 8;
 constexpr int kQcThreads = 256;
@@ -1029,13 +1031,16 @@ qrcp_cluster_kernel(const double* d, int ell, double* refl, double* rt, int* per
     pdl_wait();
     if (cancel && *cancel) return;  // uniform over the cluster, before any barrier
     cg::cluster_group cluster = cg::this_cluster();
-    __shared__ double W[kQcCols * kQcLd];     // own columns, local index lc = c / kQcCtas
+    __shared__ double W[kQcCols * kQcLd];       // own columns, local index lc = c / kQcCtas
     __shared__ double nrm[kQcCols];
-    __shared__ double vbuf[128];              // v of the current step (pushed by the pivot's owner)
-    __shared__ double taus[128], betas[128];  // per step (replicated)
-    __shared__ long long keys[kQcCtas];       // each CTA's best key for the step (pushed)
-    __shared__ int pos_of[128], phys_at[128]; // replicated position tables
-    __shared__ double in_tau, in_beta;        // pushed with v
+    __shared__ double cand[2][kQcCtas][128];    // each CTA's candidate column (rows from the step down)
+    __shared__ double cnrm[2][kQcCtas];         // its squared norm
+    __shared__ long long keys[2][kQcCtas];      // its pivot key (-1: no column left)
+    __shared__ double vbuf[128];                // v of the current step
+    __shared__ double taus[128], betas[128];    // per step (replicated)
+    __shared__ int pos_of[128], phys_at[128];   // replicated position tables
+    __shared__ double sc_beta, sc_tau, sc_scale;
+    __shared__ int sc_lc;                       // own local column of the next candidate (-1: none)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rank = (int)cluster.block_rank();
     const int nloc = ell > rank ? (ell - rank + kQcCtas - 1) / kQcCtas : 0;  // own columns
@@ -1048,7 +1053,6 @@ qrcp_cluster_kernel(const double* d, int ell, double* refl, double* rt, int* per
         phys_at[c] = c;
     }
     __syncthreads();
-    // squared norms of the own columns (one warp per column)
     for (int lc = warp; lc < nloc; lc += kQcThreads / 32) {
         double s = 0.0;
         for (int i = lane; i < ell; i += 32) s = fma(W[lc * kQcLd + i], W[lc * kQcLd + i], s);
@@ -1057,83 +1061,97 @@ qrcp_cluster_kernel(const double* d, int ell, double* refl, double* rt, int* per
         if (lane == 0) nrm[lc] = s;
     }
     __syncthreads();
-    for (int j = 0; j < ell; ++j) {
-        // own best key over the columns at positions >= j
+    // own best candidate for step j, pushed into buffer j & 1 of every CTA
+    auto push_candidate = [&](int j) {
+        const int b = j & 1;
         if (warp == 0) {
             long long best = -1;
+            int blc = -1;
             for (int lc = lane; lc < nloc; lc += 32) {
                 const int pc = pos_of[lc * kQcCtas + rank];
                 if (pc >= j) {
                     const long long key = (__double_as_longlong(nrm[lc]) & ~0x7fLL) | (127 - pc);
-                    best = key > best ? key : best;
+                    if (key > best) {
+                        best = key;
+                        blc = lc;
+                    }
                 }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-                best = ob > best ? ob : best;
-            }
-            if (lane < kQcCtas) cluster.map_shared_rank(keys, lane)[rank] = best;
-        }
-        cluster.sync();  // barrier 1: every key pushed (and every CTA done with step j-1)
-        long long best = keys[0];
-#pragma unroll
-        for (int r = 1; r < kQcCtas; ++r) best = keys[r] > best ? keys[r] : best;
-        const int pp = 127 - (int)(best & 0x7f);  // position of the pivot
-        const int p = phys_at[pp];
-        const int owner = p % kQcCtas;
-        // positions j and pp swap (the same update in every CTA)
-        __syncthreads();  // every thread read the tables above
-        if (tid == 0 && pp != j) {
-            const int pj = phys_at[j];
-            phys_at[j] = p;
-            phys_at[pp] = pj;
-            pos_of[p] = j;
-            pos_of[pj] = pp;
-        }
-        if (rank == owner && warp == 0) {
-            const int lc = p / kQcCtas;
-            double* x = W + lc * kQcLd;
-            double beta = 0.0, t = 0.0, scale = 0.0;
-            if (lane == 0) {
-                // beta = -sign(alpha) |x| (sign(+-0) = +), tau = (beta - alpha) / beta,
-                // scale = 1 / (alpha - beta); H = I when the part below row j is exactly zero
-                const double sj = nrm[lc];
-                const double alpha = x[j];
-                const long long ab = __double_as_longlong(alpha);
-                const bool neg = ab < 0 && (ab & 0x7fffffffffffffffLL) != 0;
-                const double y = rsqrt_nr(sj);
-                const double nr = sj * y;
-                const double beta_c = neg ? nr : -nr;
-                const double inv_beta = neg ? y : -y;
-                const double t_c = fma(-alpha, inv_beta, 1.0);
-                const double scale_c = rcp_nr(alpha - beta_c);
-                const bool reflect = sj != alpha * alpha;
-                beta = reflect ? beta_c : alpha;
-                t = reflect ? t_c : 0.0;
-                scale = reflect ? scale_c : 0.0;
-            }
-            beta = __shfl_sync(0xffffffffu, beta, 0);
-            t = __shfl_sync(0xffffffffu, t, 0);
-            scale = __shfl_sync(0xffffffffu, scale, 0);
-            // v below the diagonal (zero when H = I), kept in the column for the reflector output
-            for (int i = j + 1 + lane; i < ell; i += 32) {
-                const double v = t != 0.0 ? x[i] * scale : 0.0;
-                x[i] = v;
-#pragma unroll
-                for (int r = 0; r < kQcCtas; ++r) cluster.map_shared_rank(vbuf, r)[i] = v;
+                const int ol = __shfl_xor_sync(0xffffffffu, blc, o);
+                if (ob > best) {
+                    best = ob;
+                    blc = ol;
+                }
             }
             if (lane < kQcCtas) {
-                cluster.map_shared_rank(&in_tau, lane)[0] = t;
-                cluster.map_shared_rank(&in_beta, lane)[0] = beta;
+                cluster.map_shared_rank(&keys[b][0], lane)[rank] = best;
+                cluster.map_shared_rank(&cnrm[b][0], lane)[rank] = blc >= 0 ? nrm[blc] : 0.0;
             }
-            if (lane == 0) x[j] = beta;
+            if (lane == 0) sc_lc = blc;
         }
-        cluster.sync();  // barrier 2: v, tau, beta pushed
-        const double tj = in_tau;
+        __syncthreads();
+        const int blc = sc_lc;
+        if (blc >= 0)
+            for (int e = tid; e < kQcCtas * (ell - j); e += kQcThreads) {
+                const int r = e / (ell - j), i = j + (e - r * (ell - j));
+                cluster.map_shared_rank(&cand[b][0][0], r)[rank * 128 + i] = W[blc * kQcLd + i];
+            }
+    };
+    push_candidate(0);
+    for (int j = 0; j < ell; ++j) {
+        const int b = j & 1;
+        cluster.sync();  // every candidate of step j pushed (and every CTA done with step j-1)
+        long long best = keys[b][0];
+        int wr = 0;
+#pragma unroll
+        for (int r = 1; r < kQcCtas; ++r)
+            if (keys[b][r] > best) {
+                best = keys[b][r];
+                wr = r;
+            }
+        const int pp = 127 - (int)(best & 0x7f);  // position of the pivot
+        const int p = phys_at[pp];
+        const double* x = &cand[b][wr][0];
+        __syncthreads();  // every thread read the tables before thread 0 swaps
         if (tid == 0) {
-            taus[j] = tj;
-            betas[j] = in_beta;
+            // positions j and pp swap (the same update in every CTA)
+            if (pp != j) {
+                const int pj = phys_at[j];
+                phys_at[j] = p;
+                phys_at[pp] = pj;
+                pos_of[p] = j;
+                pos_of[pj] = pp;
+            }
+            // beta = -sign(alpha) |x| (sign(+-0) = +), tau = (beta - alpha) / beta,
+            // scale = 1 / (alpha - beta); H = I when the part below row j is exactly zero
+            const double sj = cnrm[b][wr];
+            const double alpha = x[j];
+            const long long ab = __double_as_longlong(alpha);
+            const bool neg = ab < 0 && (ab & 0x7fffffffffffffffLL) != 0;
+            const double y = rsqrt_nr(sj);
+            const double nr = sj * y;
+            const double beta_c = neg ? nr : -nr;
+            const double inv_beta = neg ? y : -y;
+            const double t_c = fma(-alpha, inv_beta, 1.0);
+            const double scale_c = rcp_nr(alpha - beta_c);
+            const bool reflect = sj != alpha * alpha;
+            sc_beta = reflect ? beta_c : alpha;
+            sc_tau = reflect ? t_c : 0.0;
+            sc_scale = reflect ? scale_c : 0.0;
+            taus[j] = sc_tau;
+            betas[j] = sc_beta;
+        }
+        __syncthreads();
+        const double tj = sc_tau, scale = sc_scale;
+        for (int i = j + 1 + tid; i < ell; i += kQcThreads) vbuf[i] = tj != 0.0 ? x[i] * scale : 0.0;
+        __syncthreads();
+        if (wr == rank) {  // the pivot column is own: it keeps v below the diagonal and beta on it
+            double* xo = W + (p / kQcCtas) * kQcLd;
+            for (int i = j + 1 + tid; i < ell; i += kQcThreads) xo[i] = vbuf[i];
+            if (tid == 0) xo[j] = sc_beta;
         }
         // H_j on the own columns at positions > j, and their squared norms over
         // rows > j: two columns per warp, one per half-warp, so that each FP64
@@ -1142,29 +1160,30 @@ qrcp_cluster_kernel(const double* d, int ell, double* refl, double* rt, int* per
             const int half = lane >> 4, hl = lane & 15;
             const int lc = 2 * warp + half;  // kQcCols = 16 = 2 x 8 warps: one round
             const bool act = lc < nloc && pos_of[lc * kQcCtas + rank] > j;
-            double* x = W + (act ? lc : 0) * kQcLd;
+            double* xc = W + (act ? lc : 0) * kQcLd;
             double part = 0.0;
             if (act)
-                for (int i = j + 1 + hl; i < ell; i += 16) part = fma(vbuf[i], x[i], part);
+                for (int i = j + 1 + hl; i < ell; i += 16) part = fma(vbuf[i], xc[i], part);
 #pragma unroll
             for (int o = 8; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            const double f = act ? tj * (x[j] + part) : 0.0;  // v^T x_c with v_j = 1
+            const double f = act ? tj * (xc[j] + part) : 0.0;  // v^T x_c with v_j = 1
             double acc = 0.0;
             if (act)
                 for (int i = j + 1 + hl; i < ell; i += 16) {
-                    const double nv = fma(-f, vbuf[i], x[i]);
-                    x[i] = nv;
+                    const double nv = fma(-f, vbuf[i], xc[i]);
+                    xc[i] = nv;
                     acc = fma(nv, nv, acc);
                 }
 #pragma unroll
             for (int o = 8; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            __syncwarp();  // every lane read x[j] before its half's lane 0 rewrites it
+            __syncwarp();  // every lane read x_c[j] before its half's lane 0 rewrites it
             if (act && hl == 0) {
-                x[j] -= f;
+                xc[j] -= f;
                 nrm[lc] = acc;
             }
         }
         __syncthreads();
+        if (j + 1 < ell) push_candidate(j + 1);
     }
     cluster.sync();  // no CTA leaves while another may still write into its shared memory
     pdl_trigger();
@@ -1186,7 +1205,6 @@ qrcp_cluster_kernel(const double* d, int ell, double* refl, double* rt, int* per
             refl[(size_t)ell * ell + ell + c] = betas[c] < 0.0 ? -1.0 : 1.0;
         }
 }
-
 
 // Qt = H_0 H_1 ... H_{ell-1} diag(sgn). Column c of the product is
 // H_0 H_1 ... H_c e_c (H_k leaves e_c alone for k > c), so the columns are
