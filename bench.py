@@ -766,7 +766,8 @@ def run_ours(args):
         e2e = {"value": world * flops / sec / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": m * n * es,
                "d2h_bytes_per_step": (m * ell + n * ell + ell * ell) * es + ell * 4,
-               "ms_per_step": sec * 1e3, "steps": e2e_steps}
+               "ms_per_step": sec * 1e3, "steps": e2e_steps,
+               "kind": "corutv_factor with pinned host buffers, one call at a time"}
         del hA, npA
 
     cpu = None

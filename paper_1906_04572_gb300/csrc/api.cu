@@ -1115,7 +1115,7 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
     }
     // A_m, A_l of the projection cast beside the thin QRs (device input, bf16 sketches)
     CastOverlap ov;
-    const bool overlap = dev && pl.split && pl.prec == CORUTV_P_BF16;
+    const bool overlap = pl.split && pl.prec == CORUTV_P_BF16;  // (host input: on its staged copy)
     if (overlap && !ctx->side) {
         CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
         for (auto& ev : ctx->ov_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
