@@ -1210,17 +1210,36 @@ qrcp_cluster_kernel(const double* d, int ell, double* refl, double* rt, int* per
 // H_0 H_1 ... H_c e_c (H_k leaves e_c alone for k > c), so the columns are
 // independent: one warp per column (lanes own rows lane + 32 t, t < 4),
 // applying H_c, H_{c-1}, ..., H_0 in turn with a warp-wide dot product each,
-// spread over ceil(ell / 8) blocks so that the FP64 pipes of several SMs
-// share the work. V, tau and the signs are staged in shared memory.
-constexpr int kQformWarps = 8;
+// two warps per block (ceil(ell / 2) blocks) so that each warp has a
+// sub-partition's FP64 pipe to itself: a warp's steps are bound by that pipe
+// (about 13 FP64 warp instructions per reflector), not by the other warps.
+// V, tau and the signs are staged in shared memory.
+constexpr int kQformWarps = 2;
 
 __global__ void __launch_bounds__(kQformWarps * 32)
 qform_kernel(const double* refl, int ell, double* qt, const int* cancel) {
     pdl_wait();
     if (cancel && *cancel) return;
     extern __shared__ double Vs[];  // ell * ell + 2 * ell
-    const int n = ell * ell + 2 * ell;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) Vs[e] = refl[e];
+    // the reflectors this block's columns use (k <= its last column), 16 loads
+    // per thread in flight before their stores; then tau and the signs
+    const int cmax = min(ell - 1, (int)blockIdx.x * kQformWarps + kQformWarps - 1);
+    const int nv = (cmax + 1) * ell;
+    constexpr int kB = 16;
+    for (int e0 = 0; e0 < nv; e0 += kB * (int)blockDim.x) {
+        double v[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int e = e0 + u * (int)blockDim.x + (int)threadIdx.x;
+            v[u] = e < nv ? refl[e] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int e = e0 + u * (int)blockDim.x + (int)threadIdx.x;
+            if (e < nv) Vs[e] = v[u];
+        }
+    }
+    for (int e = threadIdx.x; e < 2 * ell; e += blockDim.x) Vs[ell * ell + e] = refl[ell * ell + e];
     __syncthreads();
     const double* tau = Vs + ell * ell;
     const double* sgn = tau + ell;
