@@ -336,6 +336,7 @@ struct CastOverlap {
     int64_t m = 0, n = 0, lda = 0;
     void* out = nullptr;
     const int* cancel = nullptr;
+    int parts = 2;               // 2: A_m, A_l (A_h is on the critical path); 3: all three (TF32 sketches)
     int chunks = 0, issued = 0, joined = 0;
     corutv_status issue(cudaStream_t main) {
         if (issued >= chunks) return CORUTV_OK;
@@ -343,7 +344,7 @@ struct CastOverlap {
         const int64_t rb0 = mt * issued / chunks, rb1 = mt * (issued + 1) / chunks;
         CK(cudaEventRecord(ev[2 * issued], main));
         CK(cudaStreamWaitEvent(side, ev[2 * issued], 0));
-        if (rb1 > rb0) CK(launch_cast_tiled_rows(a, ta, m, n, lda, out, 2, rb0, rb1, cancel, side));
+        if (rb1 > rb0) CK(launch_cast_tiled_rows(a, ta, m, n, lda, out, parts, rb0, rb1, cancel, side));
         CK(cudaEventRecord(ev[2 * issued + 1], side));
         ++issued;
         return CORUTV_OK;
@@ -499,7 +500,22 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
         // padding columns of the bf16 / fp32 operand panels must read as zero
         CK(cudaMemsetAsync(b.q1c, 0, (size_t)pl.ellp * pl.ldm * elem_size(pl.tcomp), ex.st));
         CK(launch_panel_convert(b.x, pl.tp, pl.ldn, n, pl.ellp, b.xc, pl.tcomp, pl.ldn, ex.cancel, ex.st));
-        if (pl.prec == CORUTV_P_TF32)
+        if (pl.prec == CORUTV_P_TF32 && pl.split && ex.ov) {
+            // A^T (and the padded copy) now; the bf16 splits for eq. 7 in row chunks on the side stream
+            CK(launch_prep_f32(static_cast<const float*>(a), pl.ma, pl.na, pl.lda, b.at, pl.ldma, nullptr, b.a32,
+                               pl.ldc32, ex.cancel, ex.st));
+            CastOverlap& ov = *ex.ov;
+            ov.a = a;
+            ov.ta = pl.ta;
+            ov.m = pl.ma;
+            ov.n = pl.na;
+            ov.lda = pl.lda;
+            ov.out = b.abf;
+            ov.cancel = ex.cancel;
+            ov.parts = 3;
+            ov.chunks = (int)std::min<int64_t>(kMaxCastChunks, std::max<int64_t>(1, 2 * pl.q + 2));
+            ov.issued = ov.joined = 0;
+        } else if (pl.prec == CORUTV_P_TF32)
             // one pass over A: A^T for the K-major A^T Y, the tiled bf16 splits for eq. 7
             CK(launch_prep_f32(static_cast<const float*>(a), pl.ma, pl.na, pl.lda, b.at, pl.ldma, b.abf, b.a32,
                                pl.ldc32, ex.cancel, ex.st));
@@ -1115,7 +1131,7 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
     }
     // A_m, A_l of the projection cast beside the thin QRs (device input, bf16 sketches)
     CastOverlap ov;
-    const bool overlap = pl.split && pl.prec == CORUTV_P_BF16;  // (host input: on its staged copy)
+    const bool overlap = pl.split && (pl.prec == CORUTV_P_BF16 || pl.prec == CORUTV_P_TF32);  // (host input: its staged copy)
     if (overlap && !ctx->side) {
         CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
         for (auto& ev : ctx->ov_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
