@@ -338,6 +338,8 @@ struct CastOverlap {
     const int* cancel = nullptr;
     int parts = 2;               // 2: A_m, A_l (A_h is on the critical path); 3: all three (TF32 sketches)
     int chunks = 0, issued = 0, joined = 0;
+    cudaEvent_t psi_fork = nullptr, psi_done = nullptr;  // the test matrix formed on the side stream
+    bool psi_pending = false;
     corutv_status issue(cudaStream_t main) {
         if (issued >= chunks) return CORUTV_OK;
         const int64_t mt = (m + 127) / 128;
@@ -350,6 +352,10 @@ struct CastOverlap {
         return CORUTV_OK;
     }
     corutv_status join(cudaStream_t main) {
+        if (psi_pending) {
+            CK(cudaStreamWaitEvent(main, psi_done, 0));
+            psi_pending = false;
+        }
         for (; joined < issued; ++joined) CK(cudaStreamWaitEvent(main, ev[2 * joined + 1], 0));
         return CORUTV_OK;
     }
@@ -491,15 +497,27 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
                          const double* psi_dev, uint64_t seed, uint32_t sid) {
     const int64_t m = pl.m, n = pl.n, ell = pl.ell;
     ProfScope ps_all(ex.prof, CORUTV_STAGE_FACTOR, ex.st);
-    // Step 1: X = Psi (panel n x ellp, padding columns zero)
-    if (psi_dev) CK(launch_rowmajor_to_panel(psi_dev, ell, n, ell, pl.ellp, b.x, pl.tp, pl.ldn, ex.st));
-    else CK(launch_gaussian_panel(seed, sid, n, ell, pl.ellp, b.x, pl.tp, pl.ldn, ex.cancel, ex.st));
+    // Step 1: X = Psi (panel n x ellp, padding columns zero); with a side stream
+    // it is formed there, beside the cast of A, and joined before the first product
+    const bool side_psi = ex.ov && pl.tensor && pl.split && ex.ov->psi_fork;
+    cudaStream_t pst = ex.st;
+    if (side_psi) {
+        CK(cudaEventRecord(ex.ov->psi_fork, ex.st));
+        CK(cudaStreamWaitEvent(ex.ov->side, ex.ov->psi_fork, 0));
+        pst = ex.ov->side;
+    }
+    if (psi_dev) CK(launch_rowmajor_to_panel(psi_dev, ell, n, ell, pl.ellp, b.x, pl.tp, pl.ldn, pst));
+    else CK(launch_gaussian_panel(seed, sid, n, ell, pl.ellp, b.x, pl.tp, pl.ldn, ex.cancel, pst));
     // the workspace is shared with other entry points: start the kernels' counters at zero
     CK(cudaMemsetAsync(b.tcnt, 0, sizeof(int) * (size_t)factor_counters(pl), ex.st));
     if (pl.tensor) {
         // padding columns of the bf16 / fp32 operand panels must read as zero
         CK(cudaMemsetAsync(b.q1c, 0, (size_t)pl.ellp * pl.ldm * elem_size(pl.tcomp), ex.st));
-        CK(launch_panel_convert(b.x, pl.tp, pl.ldn, n, pl.ellp, b.xc, pl.tcomp, pl.ldn, ex.cancel, ex.st));
+        CK(launch_panel_convert(b.x, pl.tp, pl.ldn, n, pl.ellp, b.xc, pl.tcomp, pl.ldn, ex.cancel, pst));
+        if (side_psi) {
+            CK(cudaEventRecord(ex.ov->psi_done, pst));
+            ex.ov->psi_pending = true;
+        }
         if (pl.prec == CORUTV_P_TF32 && pl.split && ex.ov) {
             // A^T (and the padded copy) now; the bf16 splits for eq. 7 in row chunks on the side stream
             CK(launch_prep_f32(static_cast<const float*>(a), pl.ma, pl.na, pl.lda, b.at, pl.ldma, nullptr, b.a32,
@@ -549,7 +567,7 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     auto product = [&](bool a_rows, const void* opnd, void* out, TcPieces* pc, int nsegs = 1) -> corutv_status {
         const int64_t ldo = a_rows ? pl.ldna : pl.ldma, ldout = a_rows ? pl.ldma : pl.ldna;
         if (!pl.tensor) return sketch_simt(ex, pl, b, a_rows ? A_ROWS : A_COLS, a, pl.ta, opnd, pl.tcomp, out, ldout);
-        if (ex.ov && ex.ov->chunks) CKS(ex.ov->join(ex.st));  // no cast chunk beside a product
+        if (ex.ov && (ex.ov->chunks || ex.ov->psi_pending)) CKS(ex.ov->join(ex.st));  // nothing beside a product
         ProfScope ps(ex.prof, CORUTV_STAGE_SKETCH, ex.st);
         if (pl.prec == CORUTV_P_BF16) {
             // the tiled bf16 copy (its first part, A_h) serves both directions
@@ -769,7 +787,7 @@ struct corutv_ctx {
     std::map<std::string, GraphEntry> graph_cache;
     cudaStream_t cap_stream = nullptr;   // captures run here (the caller's stream may be the legacy one)
     cudaStream_t side = nullptr;         // the A_m, A_l cast chunks (CastOverlap)
-    cudaEvent_t ov_ev[2 * kMaxCastChunks] = {};
+    cudaEvent_t ov_ev[2 * kMaxCastChunks + 2] = {};  // chunk fork / done, then the test matrix's
 };
 
 namespace {
@@ -1142,6 +1160,8 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
             ov = CastOverlap();
             ov.side = ctx->side;
             ov.ev = ctx->ov_ev;
+            ov.psi_fork = ctx->ov_ev[2 * kMaxCastChunks];
+            ov.psi_done = ctx->ov_ev[2 * kMaxCastChunks + 1];
             ex.ov = &ov;
         }
         CKS(run_factor(ex, pl, b, a_dev, psi, opts->seed, opts->stream));
