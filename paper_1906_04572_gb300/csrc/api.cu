@@ -340,6 +340,7 @@ struct CastOverlap {
     int chunks = 0, issued = 0, joined = 0;
     cudaEvent_t psi_fork = nullptr, psi_done = nullptr;  // the test matrix formed on the side stream
     bool psi_pending = false;
+    cudaEvent_t emit_fork = nullptr, emit_done = nullptr;  // T, V, perm written on the side stream
     corutv_status issue(cudaStream_t main) {
         if (issued >= chunks) return CORUTV_OK;
         const int64_t mt = (m + 127) / 128;
@@ -616,7 +617,7 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     if (pl.dmode == 1) {
         CKS(orth(ex, pl, b, b.c2, pl.ldn, n, b.q2, nullptr, pl.tdproj, 2, b.d, &pieces));
         ProfScope ps(ex.prof, CORUTV_STAGE_QRCP, ex.st);
-        CK(launch_qrcp(b.d, ell, b.qt, b.rt, b.perm, b.refl, ex.cancel, ex.st, explicit_qt(pl, pl.tp)));
+        CK(launch_qrcp(b.d, ell, b.qt, b.rt, b.perm, b.refl, ex.cancel, ex.st, explicit_qt(pl, pl.tp) && !ex.ov));
         return CORUTV_OK;
     }
     // the non-split projection multiplies A by Q2 in its own arithmetic (a copy
@@ -658,7 +659,7 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     // eq. 8: D P = Qt Rt
     {
         ProfScope ps(ex.prof, CORUTV_STAGE_QRCP, ex.st);
-        CK(launch_qrcp(b.d, ell, b.qt, b.rt, b.perm, b.refl, ex.cancel, ex.st, explicit_qt(pl, pl.tp)));
+        CK(launch_qrcp(b.d, ell, b.qt, b.rt, b.perm, b.refl, ex.cancel, ex.st, explicit_qt(pl, pl.tp) && !ex.ov));
     }
     return CORUTV_OK;
 }
@@ -672,6 +673,19 @@ corutv_status emit_user(const Exec& ex, const FactorPlan& pl, const FactorBufs& 
     void* uq = pl.tr ? v : u;  // receives Q1 Qt
     void* vq = pl.tr ? u : v;  // receives Q2 P
     const int64_t lduq = pl.tr ? ldv : ldu, ldvq = pl.tr ? ldu : ldv;
+    // with a side stream: T, V = Q2 P and perm there, beside the formation of Qt
+    // (run_factor left it to this step) and U = Q1 Qt on the main stream
+    cudaStream_t sst = ex.st;
+    if (ex.ov && ex.ov->emit_fork) {
+        CK(cudaEventRecord(ex.ov->emit_fork, ex.st));
+        CK(cudaStreamWaitEvent(ex.ov->side, ex.ov->emit_fork, 0));
+        sst = ex.ov->side;
+        CK(launch_copy_small(b.rt, ell, t, tout, ex.cancel, sst, pl.tr));
+        if (vq) CK(launch_gather_v(b.q2, pl.tp, pl.ldn, pl.n, ell, b.perm, vq, tout, ldvq, ex.cancel, sst));
+        if (perm) CK(cudaMemcpyAsync(perm, b.perm, sizeof(int32_t) * ell, cudaMemcpyDeviceToDevice, sst));
+        CK(cudaEventRecord(ex.ov->emit_done, sst));
+    }
+    if (ex.ov && explicit_qt(pl, pl.tp)) CK(launch_qform(b.refl, ell, b.qt, ex.cancel, ex.st));
     if (uq && explicit_qt(pl, tout) && pl.tp == T_F64) {
         // Q1 Qt as an FP64 product with the explicit Qt (widths beyond the
         // reflector kernel's shared memory)
@@ -689,6 +703,10 @@ corutv_status emit_user(const Exec& ex, const FactorPlan& pl, const FactorBufs& 
     } else if (uq) {
         // Q1 Qt, applied as the QRCP's reflectors to the rows of Q1
         CK(launch_apply_reflectors(b.q1, pl.tp, pl.ldm, pl.m, ell, b.refl, uq, tout, lduq, false, ex.cancel, ex.st));
+    }
+    if (sst != ex.st) {
+        CK(cudaStreamWaitEvent(ex.st, ex.ov->emit_done, 0));  // joined: the call ends on the main stream
+        return CORUTV_OK;
     }
     CK(launch_copy_small(b.rt, ell, t, tout, ex.cancel, ex.st, pl.tr));
     if (vq) CK(launch_gather_v(b.q2, pl.tp, pl.ldn, pl.n, ell, b.perm, vq, tout, ldvq, ex.cancel, ex.st));
@@ -787,7 +805,7 @@ struct corutv_ctx {
     std::map<std::string, GraphEntry> graph_cache;
     cudaStream_t cap_stream = nullptr;   // captures run here (the caller's stream may be the legacy one)
     cudaStream_t side = nullptr;         // the A_m, A_l cast chunks (CastOverlap)
-    cudaEvent_t ov_ev[2 * kMaxCastChunks + 2] = {};  // chunk fork / done, then the test matrix's
+    cudaEvent_t ov_ev[2 * kMaxCastChunks + 4] = {};  // chunk fork / done, the test matrix's, the outputs'
 };
 
 namespace {
@@ -1162,6 +1180,8 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
             ov.ev = ctx->ov_ev;
             ov.psi_fork = ctx->ov_ev[2 * kMaxCastChunks];
             ov.psi_done = ctx->ov_ev[2 * kMaxCastChunks + 1];
+            ov.emit_fork = ctx->ov_ev[2 * kMaxCastChunks + 2];
+            ov.emit_done = ctx->ov_ev[2 * kMaxCastChunks + 3];
             ex.ov = &ov;
         }
         CKS(run_factor(ex, pl, b, a_dev, psi, opts->seed, opts->stream));

@@ -254,6 +254,8 @@ cudaError_t launch_gram_f32(const float* x, int64_t ldx, const float* y, int64_t
 // blocks. work: ell * (ell + 2) doubles of device scratch.
 cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, int* perm, double* work,
                         const int* cancel, cudaStream_t st, bool form_q = true);
+// Qt (ell x ell, row-major) from the reflectors launch_qrcp left in refl.
+cudaError_t launch_qform(const double* refl, int64_t ell, double* qt, const int* cancel, cudaStream_t st);
 // U = Q1 Qt from the reflectors the QRCP left in `refl` (its work array),
 // without Qt: q1 a panel of type tp (ld ldq, `rows` rows); out row-major
 // (ld ldo) or, with out_panel, a panel; element type tout.

@@ -1866,6 +1866,23 @@ cudaError_t launch_trsm_rows(const void* c, ElemType tp, int64_t ldc, int64_t ro
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_qform(const double* refl, int64_t ell, double* qt, const int* cancel, cudaStream_t st) {
+    if (ell < 1 || ell > kMaxEllSimt) return cudaErrorInvalidValue;
+    count_launch();
+    cudaError_t e;
+    if (ell > 128) {
+        e = launch_pdl(qform_big_kernel, dim3((unsigned)((ell + 7) / 8)), dim3(256), (size_t)0, st, refl, (int)ell, qt,
+                       cancel);
+    } else {
+        const size_t smem_q = sizeof(double) * (size_t)(ell * ell + 2 * ell);
+        e = allow_max_dynamic_smem(reinterpret_cast<const void*>(qform_kernel));
+        if (e != cudaSuccess) return e;
+        e = launch_pdl(qform_kernel, dim3((unsigned)((ell + kQformWarps - 1) / kQformWarps)), dim3(kQformWarps * 32),
+                       smem_q, st, refl, (int)ell, qt, cancel);
+    }
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, int* perm, double* work,
                         const int* cancel, cudaStream_t st, bool form_q) {
     if (ell < 1 || ell > kMaxEllSimt || !work) return cudaErrorInvalidValue;
@@ -1874,10 +1891,7 @@ cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, in
         cudaError_t pe = launch_pdl(qrcp_big_kernel, dim3(1), dim3(kBigThreads), (size_t)0, st, d, (int)ell, work, rt,
                                     perm, cancel);
         if (pe != cudaSuccess || !form_q) return pe != cudaSuccess ? pe : cudaGetLastError();
-        count_launch();
-        pe = launch_pdl(qform_big_kernel, dim3((unsigned)((ell + 7) / 8)), dim3(256), (size_t)0, st,
-                        static_cast<const double*>(work), (int)ell, qt, cancel);
-        return pe != cudaSuccess ? pe : cudaGetLastError();
+        return launch_qform(work, ell, qt, cancel, st);
     }
     cudaError_t e;
     count_launch();
@@ -1895,12 +1909,7 @@ cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, in
         if (e != cudaSuccess) return e;
     }
     if (!form_q) return cudaSuccess;
-    const size_t smem_q = sizeof(double) * (size_t)(ell * ell + 2 * ell);
-    e = allow_max_dynamic_smem(reinterpret_cast<const void*>(qform_kernel));
-    if (e != cudaSuccess) return e;
-    count_launch();
-    return launch_pdl(qform_kernel, dim3((unsigned)((ell + kQformWarps - 1) / kQformWarps)), dim3(kQformWarps * 32),
-                      smem_q, st, static_cast<const double*>(work), (int)ell, qt, cancel);
+    return launch_qform(work, ell, qt, cancel, st);
 }
 
 // The same product for FP32 arithmetic and ell <= 64 with one thread per row
