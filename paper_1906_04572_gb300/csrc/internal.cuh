@@ -129,9 +129,13 @@ struct TcPieces {
 // per block) and the small kernels around them do not reconfigure the SMs'
 // L1 / shared split.
 inline void prefer_max_shared(const void* fn) {
+    // a per-thread record first: no lock on the launch path once a kernel is known
+    thread_local std::unordered_set<const void*> seen;
+    if (seen.count(fn)) return;
     static std::mutex mu;
     static std::unordered_set<const void*> done;
     std::lock_guard<std::mutex> lk(mu);
+    seen.insert(fn);
     if (done.insert(fn).second)
         if (cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
@@ -151,8 +155,13 @@ inline cudaError_t allow_max_dynamic_smem(const void* fn) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const unsigned long long key = (reinterpret_cast<unsigned long long>(fn) << 6) ^ (unsigned long long)dev;
+    thread_local std::unordered_set<unsigned long long> seen;  // per-thread record: no lock once known
+    if (seen.count(key)) return cudaSuccess;
     std::lock_guard<std::mutex> lk(mu);
-    if (done.count(key)) return cudaSuccess;
+    if (done.count(key)) {
+        seen.insert(key);
+        return cudaSuccess;
+    }
     int optin = 0;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
@@ -160,7 +169,10 @@ inline cudaError_t allow_max_dynamic_smem(const void* fn) {
     e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-    if (e == cudaSuccess) done.insert(key);
+    if (e == cudaSuccess) {
+        done.insert(key);
+        seen.insert(key);
+    }
     return e;
 }
 
