@@ -560,8 +560,15 @@ corutv_status run_factor(const Exec& ex, const FactorPlan& pl, const FactorBufs&
     // split tiles of a tensor-core product stay pieces until the Gram that
     // first reads the panel adds them (no fix-up tail in the product)
     TcPieces pieces;
-    // (a row-partitioned run sums its panels over ranks: no pieces left for a consumer)
-    TcPieces* defer = (pl.tp == T_F32 && pl.torth == T_F32 && pl.tdproj == T_F32 && !ex.xch) ? &pieces : nullptr;
+    // (a row-partitioned run sums its panels over ranks: no pieces left for a consumer).
+    // Measured: the deferral pays up to about 10^4 rows (8000 x 6000, ell = 60:
+    // 1.139 against 1.144 ms; 8000 x 8000, ell = 110: equal); beyond, the Gram's
+    // per-row piece loads cost more than the products' own fix-up (20000 x 20000,
+    // ell = 110: 4.28 against 4.19 ms). Bitwise the same sums either way.
+    TcPieces* defer = (pl.tp == T_F32 && pl.torth == T_F32 && pl.tdproj == T_F32 && !ex.xch &&
+                       std::max(pl.m, pl.n) <= 12000)
+                          ? &pieces
+                          : nullptr;
     // A X (a_rows: the output has A's rows, the operand is a panel with A's
     // columns) or A^T Y (the other way round). Algorithm 1's C1 = A X is the
     // first, C2 = A^T Q1 the second; on A^T (the lower-T variant) the two swap.
