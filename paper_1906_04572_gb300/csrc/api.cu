@@ -731,6 +731,18 @@ bool is_device_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// The device's view of page-locked host memory (UVA), or null for pageable
+// memory and device pointers: kernels may read such memory directly.
+const void* pinned_host_view(const void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -1131,8 +1143,11 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
     // workspace: factor buffers + staging for host calls / host psi
     size_t bytes = factor_bytes(pl);
     Carver extra_measure(nullptr);
+    // pinned host A on the bf16 path: the three-part cast reads it in place
+    // (one pass over the host copy instead of a copy to the device and a cast)
+    const void* a_view = (!dev && pl.split && pl.prec == CORUTV_P_BF16 && !pl.tr) ? pinned_host_view(A) : nullptr;
     if (!dev) {
-        extra_measure.take<char>(m * n * es);
+        if (!a_view) extra_measure.take<char>(m * n * es);
         extra_measure.take<char>(m * ell * es);
         extra_measure.take<char>(n * ell * es);
         extra_measure.take<char>(ell * ell * es);
@@ -1148,7 +1163,7 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
     int32_t* perm_dev = perm;
     int64_t ldu_dev = ldu, ldv_dev = ldv;
     if (!dev) {
-        void* as = cv.take<char>(m * n * es);
+        void* as = a_view ? nullptr : cv.take<char>(m * n * es);
         u_dev = U ? cv.take<char>(m * ell * es) : nullptr;
         v_dev = V ? cv.take<char>(n * ell * es) : nullptr;
         t_dev = cv.take<char>(ell * ell * es);
@@ -1156,11 +1171,16 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
         if (!U) cv.take<char>(m * ell * es);
         if (!V) cv.take<char>(n * ell * es);
         if (!perm) cv.take<int>(ell);
-        CK(cudaMemcpy2DAsync(as, n * es, A, lda * es, n * es, m, cudaMemcpyHostToDevice, ctx->stream));
-        a_dev = as;
+        if (a_view) {
+            a_dev = a_view;
+            pl.lda = lda;  // read in place with the caller's row stride
+        } else {
+            CK(cudaMemcpy2DAsync(as, n * es, A, lda * es, n * es, m, cudaMemcpyHostToDevice, ctx->stream));
+            a_dev = as;
+            pl.lda = n;
+        }
         ldu_dev = ell;
         ldv_dev = ell;
-        pl.lda = n;
     }
     const double* psi = nullptr;
     if (opts->psi) {
@@ -1174,7 +1194,8 @@ corutv_status corutv_factor(corutv_ctx* ctx, corutv_dtype dtype, const void* A, 
     }
     // A_m, A_l of the projection cast beside the thin QRs (device input, bf16 sketches)
     CastOverlap ov;
-    const bool overlap = pl.split && (pl.prec == CORUTV_P_BF16 || pl.prec == CORUTV_P_TF32);  // (host input: its staged copy)
+    // (host input: its staged copy; not for A read in place from host memory, cast whole in one pass)
+    const bool overlap = pl.split && (pl.prec == CORUTV_P_BF16 || pl.prec == CORUTV_P_TF32) && !a_view;
     if (overlap && !ctx->side) {
         CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
         for (auto& ev : ctx->ov_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));

@@ -358,3 +358,31 @@ def test_autotuned_products_meet_the_budget(ctx, prec, u_p):
         assert ent["kgroup"] in (1, 2) and 2 <= ent["stages"] <= 8 and ent["us"] > 0
         stage_bytes = ent["kgroup"] * (128 * 128 + ent["panel_cols"] * 128)
         assert ent["stages"] * stage_bytes <= 200 * 1024
+
+
+@pytest.mark.parametrize("pad", [0, 12])
+def test_factor_bf16_pinned_host_input_equals_device(ctx, pad):
+    """FP32 A in page-locked host memory on the split BF16 path: the tiled
+    three-part cast reads A where it lies (row stride n + pad) instead of a
+    staged device copy; pageable host memory takes the staged copy. Both give
+    bitwise the results of the same call on device data."""
+    m, n, k, p, q = 1300, 1100, 40, 10, 2
+    ell = k + p
+    a = synth.spectrum_matrix(m, n, synth.c3_sigma(min(m, n)), 0.0, 31).astype(np.float32)
+    psi = synth.gaussian_psi(n, ell, seed=8)
+    want = ctx.factor(dev(a, torch.float32), k, p, q, "bf16", psi=dev(psi))
+    assert ctx.sync() == 0
+    want = {x: host(want[x]) for x in ("U", "T", "V", "perm")}
+    hbuf = torch.zeros((m, n + pad), dtype=torch.float32).pin_memory()
+    hbuf[:, :n] = torch.from_numpy(a)
+    pinned = hbuf.numpy()[:, :n]
+    for src in (pinned, np.ascontiguousarray(a)):
+        u = np.empty((m, ell), dtype=np.float32)
+        t = np.empty((ell, ell), dtype=np.float32)
+        v = np.empty((n, ell), dtype=np.float32)
+        perm = np.empty(ell, dtype=np.int32)
+        corutv.corutv_factor(ctx.handle, src, k, p, q, "bf16", u, t, v, perm, psi=psi)
+        assert np.array_equal(u.astype(np.float64), want["U"])
+        assert np.array_equal(t.astype(np.float64), want["T"])
+        assert np.array_equal(v.astype(np.float64), want["V"])
+        assert np.array_equal(perm, want["perm"].astype(np.int32))
