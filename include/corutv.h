@@ -218,6 +218,29 @@ corutv_status corutv_submit(corutv_ctx* ctx, const corutv_request* req, uint64_t
  * request's own status, with latency_s (optional) = completion - submit. */
 corutv_status corutv_poll(corutv_ctx* ctx, uint64_t ticket, int64_t timeout_us, double* latency_s);
 
+/* ---- batched factorisation: grouped launches over uneven shapes ----------
+ * Algorithm 1 (eqs. 4-9) for `count` requests (1 .. 4096) of different m, n,
+ * k, p, q at once, every step of the method one kernel launch over all of
+ * them: the sketch, power and projection products as one grouped tcgen05
+ * launch (each problem its own stream-K tiles, panel width and tensor map),
+ * the Grams, FP64 Choleskys, triangular solves, pivoted QRs of D and the
+ * assembly of U, T, V each as one launch with a block range per problem.
+ * Power rounds are aligned at the end (a problem with q < max q joins the
+ * later rounds), so a round's launches cover the problems still iterating.
+ * Requests: FP32 A and device pointers only (A, T required; U, V, perm
+ * optional, FP32 outputs as in corutv_factor); opts.sketch_prec BF16 with
+ * the FP32-accurate split projection; d_mode, t_lower, power_form and
+ * bf16_last_round 0; psi NULL (Psi from seed and stream); ell = k + p <= 128.
+ * The arithmetic of each step is that of corutv_factor's BF16 path; each
+ * problem's launch shapes (stream-K grid, Gram split) depend on its own sizes
+ * only, so a problem's results are bitwise the same alone and in any batch
+ * (they differ from a corutv_factor call in the order of FP32 partial sums
+ * and in forming U from the QRCP's reflectors). Stream-ordered on the
+ * context's stream; returns once the work is enqueued (corutv_sync gives the
+ * device status). The batch's buffers are held by the context until the next
+ * batch call or corutv_destroy. */
+corutv_status corutv_factor_batch(corutv_ctx* ctx, const corutv_request* reqs, int count);
+
 /* ---- per-stage device timers and launch counter --------------------------
  * Not part of the method: instrumentation for roofline measurements. With
  * profiling enabled, corutv_factor / corutv_rpca record a CUDA event pair on

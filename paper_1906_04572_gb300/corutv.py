@@ -70,6 +70,7 @@ _SIGS = {
                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                             ctypes.c_void_p], ctypes.c_int),
     "corutv_submit": ([ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "corutv_factor_batch": ([ctypes.c_void_p, ctypes.POINTER(Request), ctypes.c_int], ctypes.c_int),
     "corutv_poll": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)],
                     ctypes.c_int),
     "corutv_profile_enable": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
@@ -317,6 +318,16 @@ def corutv_submit(ctx, req: Request) -> int:
         _check(ctx, load().corutv_set_stream(ctx, ctypes.c_void_p(s)))
     _check(ctx, load().corutv_submit(ctx, ctypes.byref(req), ctypes.byref(t)))
     return t.value
+
+
+def corutv_factor_batch(ctx, reqs) -> int:
+    """Grouped launches over the requests (make_request descriptors, device
+    tensors), enqueued on the torch stream current for the first request's A."""
+    arr = (Request * len(reqs))(*reqs)
+    s = getattr(reqs[0], "_torch_stream", None) if reqs else None
+    if s is not None:
+        _check(ctx, load().corutv_set_stream(ctx, ctypes.c_void_p(s)))
+    return _check(ctx, load().corutv_factor_batch(ctx, arr, len(reqs)))
 
 
 def corutv_poll(ctx, ticket: int, timeout_us: int = -1):

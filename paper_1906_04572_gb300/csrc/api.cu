@@ -788,6 +788,16 @@ struct ReqResult {
     std::chrono::steady_clock::time_point t0;
 };
 
+// State of the grouped executor (corutv_factor_batch): the problems'
+// buffers, the launch records and their pinned staging copy.
+struct BatchState {
+    DeviceBuffer ws, desc;
+    char* host = nullptr;         // pinned staging of the records
+    size_t hcap = 0;
+    cudaEvent_t copied = nullptr;  // recorded after the records' copy: `host` may be rewritten
+    std::vector<char> rec;        // records being built
+};
+
 struct corutv_ctx {
     int device = 0;
     int num_sms = 0;
@@ -825,6 +835,7 @@ struct corutv_ctx {
     cudaStream_t cap_stream = nullptr;   // captures run here (the caller's stream may be the legacy one)
     cudaStream_t side = nullptr;         // the A_m, A_l cast chunks (CastOverlap)
     cudaEvent_t ov_ev[2 * kMaxCastChunks + 4] = {};  // chunk fork / done, the test matrix's, the outputs'
+    BatchState batch;                    // corutv_factor_batch
 };
 
 namespace {
@@ -863,6 +874,296 @@ corutv_status ensure_ws(corutv_ctx* ctx, DeviceBuffer& buf, size_t bytes, cudaSt
         return fail(CORUTV_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
     }
     buf.cap = bytes;
+    return CORUTV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Grouped execution of a batch of factorisations (corutv_factor_batch):
+// Algorithm 1 for every problem of the batch with each step one launch over
+// all problems (the grouped kernels), on BF16 sketches of FP32 input as in
+// run_factor's split path. The problems run their power rounds aligned at the
+// end: sorted by q (largest first), problem i joins at round qmax - q_i, so
+// the problems of round r are a prefix of the sorted order and every launch
+// of that round covers the first cnt_r records of its array. The records
+// (arguments and grids of every launch, tensor maps of the products) are
+// built on the host once per batch and copied to the device in one transfer.
+// ---------------------------------------------------------------------------
+
+// One array of launch records in the records buffer.
+struct RecArr {
+    size_t off = 0;
+    int count = 0;
+    unsigned gx = 0, gy = 0;  // largest grid of the records (kAnyGrid records excluded)
+    int max_ell = 0;
+    size_t smem = 0;          // grouped products: largest shared memory
+    int64_t stride_total = 0; // grid-stride kernels: largest element count
+};
+
+struct RecBuilder {
+    std::vector<char>& h;
+    explicit RecBuilder(std::vector<char>& buf) : h(buf) { h.clear(); }
+    size_t reserve(size_t bytes) {
+        const size_t off = (h.size() + 127) & ~size_t(127);
+        h.resize(off + bytes);
+        return off;
+    }
+    template <class A>
+    RecArr add(const std::vector<GroupItem<A>>& items, const std::vector<int>& ells, int64_t stride_total = 0) {
+        RecArr r;
+        r.count = (int)items.size();
+        r.off = reserve(sizeof(GroupItem<A>) * items.size());
+        if (!items.empty()) std::memcpy(h.data() + r.off, items.data(), sizeof(GroupItem<A>) * items.size());
+        for (size_t i = 0; i < items.size(); ++i) {
+            if (items[i].gx != kAnyGrid) r.gx = std::max(r.gx, items[i].gx);
+            r.gy = std::max(r.gy, items[i].gy);
+            if (i < ells.size()) r.max_ell = std::max(r.max_ell, ells[i]);
+        }
+        r.stride_total = stride_total;
+        return r;
+    }
+};
+
+// The arrays of one thin QR (orth: CholeskyQR with one or two passes and the
+// dependence-check pass) over the problems.
+struct OrthRecs {
+    int passes = 1;
+    RecArr gram[3], chol[3], rinv[3], trsm[3];
+    bool qc_bf16[3] = {false, false, false};
+};
+
+struct BatchProblem {
+    FactorPlan pl;
+    FactorBufs b;
+    const corutv_request* req;
+};
+
+enum OrthKind { ORTH_C1_1 = 0, ORTH_C1_2 = 1, ORTH_C2_1 = 2, ORTH_C2_2 = 3 };
+
+void build_orth(RecBuilder& rb, const std::vector<BatchProblem>& P, OrthKind kind, int* flags, int num_sms,
+                OrthRecs& o) {
+    const bool c1 = kind == ORTH_C1_1 || kind == ORTH_C1_2;
+    o.passes = (kind == ORTH_C1_2 || kind == ORTH_C2_2) ? 2 : 1;
+    const double u = 0x1p-24;  // FP32 Grams
+    std::vector<int> ells;
+    for (auto& pb : P) ells.push_back((int)pb.pl.ell);
+    for (int pass = 0; pass < (o.passes == 2 ? 3 : 2); ++pass) {
+        std::vector<GroupItem<GramArgs>> g;
+        std::vector<GroupItem<CholArgs>> ch;
+        std::vector<GroupItem<RinvArgs>> ri;
+        std::vector<GroupItem<TrsmArgs>> tr;
+        for (auto& pb : P) {
+            const FactorPlan& pl = pb.pl;
+            const FactorBufs& b = pb.b;
+            const int ell = (int)pl.ell, ldri = (ell + 7) & ~7;
+            const int64_t ld = c1 ? pl.ldm : pl.ldn, len = c1 ? pl.m : pl.n;
+            float* c = static_cast<float*>(c1 ? b.c1 : b.c2);
+            float* q = static_cast<float*>(c1 ? b.q1 : (kind == ORTH_C2_1 ? b.x : b.q2));
+            void* qc = c1 ? b.q1c : (kind == ORTH_C2_1 ? b.xc : nullptr);
+            float* tmp = static_cast<float*>(b.tmp);
+            float* p1 = o.passes == 1 ? q : tmp;
+            void* p1c = o.passes == 1 ? qc : nullptr;
+            float* in = pass == 0 ? c : (pass == 1 ? p1 : tmp);
+            float* out = pass == 2 ? q : p1;
+            void* outc = pass == 2 ? qc : p1c;
+            const int* cancel = pass == 1 ? b.skip : nullptr;  // the dependence-check pass runs only after a shift
+            g.push_back(gram_group_item(in, ld, in, ld, len, ell, b.g, reinterpret_cast<float*>(b.gpart), b.gcnt,
+                                        cancel, num_sms));
+            CholArgs ca{b.g, ell, len, b.r, flags, pass == 0 ? b.skip : nullptr, cancel, u,
+                        pass == 1 ? b.defic : nullptr, pass == 1 ? 10.0 * (double)ell * u : 0.0};
+            ch.push_back(cholesky_item(ca));
+            ri.push_back(rinv_item(RinvArgs{b.r, ell, b.rinv, ldri, cancel}));
+            tr.push_back(trsm_item(TrsmArgs{in, ld, len, ell, b.rinv, ldri, out, ld, outc, ld, cancel,
+                                            pass == 1 ? b.defic : nullptr}));
+            o.qc_bf16[pass] = outc != nullptr;
+        }
+        o.gram[pass] = rb.add(g, ells);
+        o.chol[pass] = rb.add(ch, ells);
+        o.rinv[pass] = rb.add(ri, ells);
+        o.trsm[pass] = rb.add(tr, ells);
+    }
+}
+
+// The records of the products (one TcGroupItem each) in the records buffer.
+struct ProdRecs {
+    RecArr arr;
+    int max_grid = 0;
+};
+
+corutv_status build_products(RecBuilder& rb, const std::vector<BatchProblem>& P, int which, int* flags,
+                             int num_sms, ProdRecs& out) {
+    const size_t isz = tc_group_item_bytes();
+    out.arr.count = (int)P.size();
+    out.arr.off = rb.reserve(isz * P.size());
+    for (size_t i = 0; i < P.size(); ++i) {
+        const FactorPlan& pl = P[i].pl;
+        const FactorBufs& b = P[i].b;
+        void* item = rb.h.data() + out.arr.off + i * isz;
+        int grid = 0;
+        size_t smem = 0;
+        int64_t pf = 0;
+        cudaError_t e;
+        if (which == 0)  // eq. 4: C1 = A X
+            e = tc_group_sketch_item(item, b.abf, pl.m, pl.n, 0, b.xc, pl.ldn, pl.ell, pl.ellp, b.part, b.tcnt, b.c1,
+                                     T_F32, pl.ldm, num_sms, flags, nullptr, &grid, &smem, &pf);
+        else if (which == 1)  // eq. 5: C2 = A^T Q1
+            e = tc_group_sketch_item(item, b.abf, pl.m, pl.n, 1, b.q1c, pl.ldm, pl.ell, pl.ellp, b.part, b.tcnt,
+                                     b.c2, T_F32, pl.ldn, num_sms, flags, nullptr, &grid, &smem, &pf);
+        else  // eq. 7: W = A Q2 from the exact splits
+            e = tc_group_project_item(item, b.abf, pl.m, pl.n, b.q2c, pl.ldn, pl.ell, pl.ellp, b.part, b.tcnt, b.w,
+                                      T_F32, pl.ldm, num_sms, flags, nullptr, &grid, &smem, &pf);
+        if (e != cudaSuccess) return fail(CORUTV_ECUDA, "grouped product record %zu: %s", i, cudaGetErrorString(e));
+        if (pf > pl.part_elems) return fail(CORUTV_EINVAL, "grouped product %zu needs more partial storage", i);
+        out.max_grid = std::max(out.max_grid, grid);
+        out.arr.smem = std::max(out.arr.smem, smem);
+    }
+    return CORUTV_OK;
+}
+
+// Algorithm 1 for the requests of a batch (validated; device pointers) with
+// grouped launches on `st`.
+corutv_status run_batch(corutv_ctx* ctx, BatchState& bs, const corutv_request* reqs, int count, cudaStream_t st,
+                        int* flags) {
+    const int num_sms = ctx->num_sms;
+    // problems sorted by q, largest first (stable: equal q keep the caller's order)
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return reqs[x].opts.q > reqs[y].opts.q; });
+    std::vector<BatchProblem> P(count);
+    size_t bytes = 0;
+    for (int i = 0; i < count; ++i) {
+        const corutv_request& r = reqs[order[i]];
+        P[i].req = &r;
+        CKS(make_plan(P[i].pl, T_F32, r.m, r.n, r.lda, r.opts.k, r.opts.p, r.opts.q, CORUTV_P_BF16, num_sms,
+                      reinterpret_cast<uintptr_t>(r.A) % 16 == 0));
+        if (!P[i].pl.split) return fail(CORUTV_EINVAL, "batch request %d: the grouped path needs FP32 A", order[i]);
+        bytes += factor_bytes(P[i].pl);
+    }
+    CKS(ensure_ws(ctx, bs.ws, bytes, st));
+    Carver cv(bs.ws.ptr);
+    for (auto& pb : P) carve_factor(cv, pb.pl, pb.b);
+    const int qmax = (int)P[0].pl.q;
+    std::vector<int> ells;
+    for (auto& pb : P) ells.push_back((int)pb.pl.ell);
+
+    RecBuilder rb(bs.rec);
+    // zero: the products' and Grams' counters, the padding columns of Q1's bf16 copy
+    std::vector<GroupItem<ZeroArgs>> zi;
+    int64_t zmax = 0;
+    for (auto& pb : P) {
+        const int64_t cb = (int64_t)sizeof(int) * factor_counters(pb.pl);
+        const int64_t qb = pb.pl.ellp * pb.pl.ldm * 2;
+        zi.push_back(zero_item(pb.b.tcnt, (cb + 3) & ~int64_t(3)));
+        zi.push_back(zero_item(pb.b.q1c, qb));
+        zmax = std::max(zmax, std::max(cb, qb) / 16);
+    }
+    const RecArr rz = rb.add(zi, {}, zmax);
+    std::vector<GroupItem<GaussArgs>> gi;
+    std::vector<GroupItem<CastArgs>> ci;
+    std::vector<GroupItem<SplitArgs>> si;
+    std::vector<GroupItem<GramArgs>> di;
+    std::vector<GroupItem<QrcpArgs>> qi;
+    std::vector<GroupItem<ReflArgs>> ui;
+    std::vector<GroupItem<GatherArgs>> vi;
+    std::vector<GroupItem<EmitArgs>> ei;
+    int64_t gmax = 0, smax = 0;
+    bool want_u = false, want_v = false;
+    for (auto& pb : P) {
+        const FactorPlan& pl = pb.pl;
+        const FactorBufs& b = pb.b;
+        const corutv_request& r = *pb.req;
+        const int ell = (int)pl.ell;
+        gi.push_back(gaussian_item(GaussArgs{r.opts.seed, r.opts.stream, pl.n, pl.ell, pl.ellp, b.xc, pl.ldn, nullptr}));
+        gmax = std::max(gmax, pl.n * pl.ellp);
+        ci.push_back(cast3_item(CastArgs{static_cast<const float*>(r.A), pl.m, pl.n, pl.lda, b.abf, nullptr}));
+        si.push_back(split_item(SplitArgs{static_cast<const float*>(b.q2), pl.ldn, pl.n, ell, (int)pl.ellp, b.q2c,
+                                          pl.ldn, nullptr}));
+        smax = std::max(smax, pl.n * pl.ellp);
+        di.push_back(gram_group_item(static_cast<const float*>(b.q1), pl.ldm, static_cast<const float*>(b.w), pl.ldm,
+                                     pl.m, ell, b.d, reinterpret_cast<float*>(b.gpart), b.gcnt, nullptr, num_sms));
+        qi.push_back(qrcp_item(QrcpArgs{b.d, ell, b.refl, b.rt, b.perm, nullptr}));
+        if (r.U) want_u = true;
+        if (r.V) want_v = true;
+        ui.push_back(refl_item(ReflArgs{static_cast<const float*>(b.q1), pl.ldm, r.U ? pl.m : 0, ell, b.refl,
+                                        static_cast<float*>(r.U), r.ldu, nullptr}));
+        vi.push_back(gather_item(GatherArgs{static_cast<const float*>(b.q2), pl.ldn, r.V ? pl.n : 0, ell, b.perm,
+                                            static_cast<float*>(r.V), r.ldv, nullptr}));
+        ei.push_back(emit_item(EmitArgs{b.rt, ell, static_cast<float*>(r.T), b.perm, r.perm, nullptr}));
+    }
+    const RecArr rg = rb.add(gi, ells, gmax), rc = rb.add(ci, ells), rs = rb.add(si, ells, smax);
+    const RecArr rd = rb.add(di, ells), rq = rb.add(qi, ells), ru = rb.add(ui, ells), rvv = rb.add(vi, ells);
+    const RecArr re = rb.add(ei, ells, (int64_t)128 * 129);
+    ProdRecs pax, paty, pproj;
+    CKS(build_products(rb, P, 0, flags, num_sms, pax));
+    CKS(build_products(rb, P, 1, flags, num_sms, paty));
+    CKS(build_products(rb, P, 2, flags, num_sms, pproj));
+    OrthRecs o_c1_1, o_c1_2, o_c2_1, o_c2_2;
+    if (qmax > 0) {
+        build_orth(rb, P, ORTH_C1_1, flags, num_sms, o_c1_1);
+        build_orth(rb, P, ORTH_C2_1, flags, num_sms, o_c2_1);
+    }
+    build_orth(rb, P, ORTH_C1_2, flags, num_sms, o_c1_2);
+    build_orth(rb, P, ORTH_C2_2, flags, num_sms, o_c2_2);
+
+    // the records to the device: pinned staging (reused once its previous copy has run), one copy
+    const size_t rbytes = bs.rec.size();
+    if (!bs.copied) CK(cudaEventCreateWithFlags(&bs.copied, cudaEventDisableTiming));
+    CK(cudaEventSynchronize(bs.copied));
+    if (bs.hcap < rbytes) {
+        if (bs.host) CK(cudaFreeHost(bs.host));
+        bs.host = nullptr;
+        bs.hcap = 0;
+        CK(cudaMallocHost(reinterpret_cast<void**>(&bs.host), rbytes));
+        bs.hcap = rbytes;
+    }
+    std::memcpy(bs.host, bs.rec.data(), rbytes);
+    CKS(ensure_ws(ctx, bs.desc, rbytes, st));
+    CK(cudaMemcpyAsync(bs.desc.ptr, bs.host, rbytes, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(bs.copied, st));
+    char* dr = static_cast<char*>(bs.desc.ptr);
+    auto at = [&](const RecArr& r) { return dr + r.off; };
+    auto items = [&](const RecArr& r, auto tag) { return reinterpret_cast<const GroupItem<decltype(tag)>*>(at(r)); };
+
+    // round r covers the problems with q >= qmax - r: a prefix of the sorted order
+    auto active = [&](int r) {
+        int c = 0;
+        while (c < count && P[c].pl.q >= qmax - r) ++c;
+        return c;
+    };
+    auto product = [&](const ProdRecs& pr, int cnt) -> corutv_status {
+        CK(launch_sketch_tc_grouped(at(pr.arr), cnt, pr.max_grid, pr.arr.smem, st));
+        return CORUTV_OK;
+    };
+    auto orth = [&](const OrthRecs& o, int cnt) -> corutv_status {
+        for (int pass = 0; pass < (o.passes == 2 ? 3 : 2); ++pass) {
+            CK(launch_gram_grouped(items(o.gram[pass], GramArgs{}), cnt, o.gram[pass].gx, o.gram[pass].gy, st));
+            CK(launch_cholesky_grouped(items(o.chol[pass], CholArgs{}), cnt, o.chol[pass].max_ell, pass == 1, st));
+            CK(launch_rinv_grouped(items(o.rinv[pass], RinvArgs{}), cnt, o.rinv[pass].gx, o.rinv[pass].max_ell, st));
+            CK(launch_trsm_grouped(items(o.trsm[pass], TrsmArgs{}), cnt, o.trsm[pass].gx, o.trsm[pass].max_ell,
+                                   o.qc_bf16[pass], st));
+        }
+        return CORUTV_OK;
+    };
+    CK(launch_zero_grouped(items(rz, ZeroArgs{}), rz.count, stride_grid(rz.stride_total), st));
+    // Step 1 (Psi as the bf16 operand panel) and the tiled bf16 splits of A
+    CK(launch_gaussian_grouped(items(rg, GaussArgs{}), count, stride_grid(rg.stride_total), st));
+    CK(launch_cast3_grouped(items(rc, CastArgs{}), count, rc.gx, rc.gy, st));
+    for (int r = 0; r <= qmax; ++r) {
+        const int cnt = active(r);
+        CKS(product(pax, cnt));                                  // eq. 4
+        CKS(orth(r < qmax ? o_c1_1 : o_c1_2, cnt));              // Q1 = qr(C1)
+        CKS(product(paty, cnt));                                 // eq. 5
+        if (r < qmax) CKS(orth(o_c2_1, cnt));                    // X = qr(C2)
+    }
+    CKS(orth(o_c2_2, count));  // Q2 = qr(C2)
+    // eq. 7: W = A Q2 from the exact splits, D = Q1^T W
+    CK(launch_split_grouped(items(rs, SplitArgs{}), count, stride_grid(rs.stride_total), st));
+    CKS(product(pproj, count));
+    CK(launch_gram_grouped(items(rd, GramArgs{}), count, rd.gx, rd.gy, st));
+    // eq. 8, then eq. 9: U = Q1 Qt, T = Rt, V = Q2 P
+    CK(launch_qrcp_grouped(items(rq, QrcpArgs{}), count, rq.max_ell, st));
+    if (want_u) CK(launch_refl_grouped(items(ru, ReflArgs{}), count, ru.gx, ru.max_ell, st));
+    if (want_v) CK(launch_gather_grouped(items(rvv, GatherArgs{}), count, rvv.gx, st));
+    CK(launch_emit_grouped(items(re, EmitArgs{}), count, stride_grid(re.stride_total), st));
     return CORUTV_OK;
 }
 
@@ -1008,6 +1309,10 @@ corutv_status corutv_destroy(corutv_ctx* ctx) {
         if (ev) cudaEventDestroy(ev);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->ws.ptr) cudaFree(ctx->ws.ptr);
+    if (ctx->batch.ws.ptr) cudaFree(ctx->batch.ws.ptr);
+    if (ctx->batch.desc.ptr) cudaFree(ctx->batch.desc.ptr);
+    if (ctx->batch.host) cudaFreeHost(ctx->batch.host);
+    if (ctx->batch.copied) cudaEventDestroy(ctx->batch.copied);
     if (ctx->flags) cudaFree(ctx->flags);
     if (ctx->switch_ev) cudaEventDestroy(ctx->switch_ev);
     if (ctx->xhost) cudaFreeHost(ctx->xhost);
@@ -1286,6 +1591,35 @@ corutv_status corutv_factor_rows(corutv_ctx* ctx, corutv_dtype dtype, const void
 // ---------------------------------------------------------------------------
 // Single steps.
 // ---------------------------------------------------------------------------
+corutv_status corutv_factor_batch(corutv_ctx* ctx, const corutv_request* reqs, int count) {
+    CKS(check_ctx(ctx));
+    if (!reqs || count < 1 || count > 4096) return fail(CORUTV_EINVAL, "need 1 <= count <= 4096 requests");
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    DeviceGuard guard(ctx->device);
+    for (int i = 0; i < count; ++i) {
+        const corutv_request& r = reqs[i];
+        const corutv_opts& o = r.opts;
+        if (r.dtype != CORUTV_F32 || o.sketch_prec != CORUTV_P_BF16)
+            return fail(CORUTV_EINVAL, "batch request %d: the grouped path takes FP32 A and BF16 sketches", i);
+        if (o.d_mode != 0 || o.t_lower != 0 || o.power_form != 0 || o.bf16_last_round != 0 || o.psi)
+            return fail(CORUTV_EINVAL,
+                        "batch request %d: the grouped path takes d_mode 0, t_lower 0, power_form 0, "
+                        "bf16_last_round 0 and a seeded Psi", i);
+        if (!r.A || !r.T) return fail(CORUTV_EINVAL, "batch request %d: A and T must not be NULL", i);
+        if (!is_device_ptr(r.A) || !is_device_ptr(r.T) || (r.U && !is_device_ptr(r.U)) ||
+            (r.V && !is_device_ptr(r.V)) || (r.perm && !is_device_ptr(r.perm)))
+            return fail(CORUTV_EINVAL, "batch request %d: corutv_factor_batch takes device pointers only", i);
+        if (o.k < 1 || o.p < 0 || o.q < 0 || o.k + o.p > 128 || o.k + o.p >= std::min(r.m, r.n) || r.lda < r.n)
+            return fail(CORUTV_EINVAL, "batch request %d: need 1 <= k, ell = k + p <= 128, ell < min(m, n), lda >= n",
+                        i);
+        if ((r.U && r.ldu < o.k + o.p) || (r.V && r.ldv < o.k + o.p))
+            return fail(CORUTV_EINVAL, "batch request %d: ldu, ldv must be >= ell", i);
+    }
+    CKS(run_batch(ctx, ctx->batch, reqs, count, ctx->stream, ctx->flags));
+    CK(cudaGetLastError());
+    return CORUTV_OK;
+}
+
 corutv_status corutv_gaussian(corutv_ctx* ctx, uint64_t seed, uint32_t stream, int64_t n, int64_t ell,
                               double* psi, int64_t ldpsi) {
     CKS(check_ctx(ctx));

@@ -280,6 +280,101 @@ cudaError_t launch_gather_v(const void* q2, ElemType tq2, int64_t ldq2, int64_t 
 cudaError_t launch_copy_small(const double* src, int64_t ell, void* dst, ElemType tdst,
                               const int* cancel, cudaStream_t st, bool transpose = false);
 
+// ---- grouped launches: one launch over the problems of a batch ----------
+// Problem z of a grouped launch (blockIdx.z) runs the blocks (x, y) < (gx, gy)
+// of its own grid with its own arguments; blocks beyond that grid return at
+// once. The launch's grid is the largest over its problems, by the number of
+// problems. Kernels with grid-stride loops get gx = the launch's gx (no block
+// returns early), so the stride is the launch's own.
+template <class A>
+struct GroupItem {
+    A a;
+    unsigned gx, gy;
+};
+
+#ifdef __CUDACC__
+template <class A, void (*F)(const A&), int kMaxThreads>
+__global__ void __launch_bounds__(kMaxThreads) grouped_kernel(const GroupItem<A>* items) {
+    const GroupItem<A>& it = items[blockIdx.z];
+    if (blockIdx.x >= it.gx || blockIdx.y >= it.gy) return;
+    F(it.a);
+}
+#endif
+
+// Arguments of the grouped kernels (each the argument list of its one-problem
+// launch; panels and small matrices as above).
+struct ZeroArgs { void* p; int64_t bytes; };
+// Gaussian test panel written as bf16 (the FP32 draw of launch_gaussian_panel, rounded)
+struct GaussArgs { uint64_t seed; uint32_t sid; int64_t n, ell, ellp; void* x; int64_t ldx; const int* cancel; };
+// tiled bf16 splits A_h, A_m, A_l of FP32 A (launch_cast_tiled with three parts)
+struct CastArgs { const float* a; int64_t m, n, lda; void* out; const int* cancel; };
+// [Q_h | Q_m | Q_l] of an FP32 panel (launch_split_panel)
+struct SplitArgs { const float* q; int64_t ldq, rows; int ell, ellp; void* q3; int64_t ldq3; const int* cancel; };
+struct CholArgs {
+    const double* g; int ell; int64_t rows; double* r; int* flags; int* skip_out; const int* cancel;
+    double unit_roundoff; int* defic; double tau_rel;
+};
+struct RinvArgs { const double* r; int ell; float* ri; int ldri; const int* cancel; };
+// Q = C R^{-1} from R^{-1} (FP32 panels); qc: copy of element type bf16 or none
+struct TrsmArgs {
+    const float* c; int64_t ldc, rows; int ell; const float* ri; int ldri; float* q; int64_t ldq; void* qc;
+    int64_t ldqc; const int* cancel; const int* defic;
+};
+struct QrcpArgs { const double* d; int ell; double* refl; double* rt; int* perm; const int* cancel; };
+// U = Q1 Qt from the reflectors (FP32 panel in, FP32 row-major out)
+struct ReflArgs { const float* x; int64_t ldx, rows; int ell; const double* refl; float* out; int64_t ldo; const int* cancel; };
+struct GatherArgs { const float* q2; int64_t ldq2, n; int ell; const int* perm; float* v; int64_t ldv; const int* cancel; };
+// T = Rt as FP32 (row-major ell x ell) and perm copied out
+struct EmitArgs { const double* rt; int ell; float* t; const int* perm_src; int* perm_dst; const int* cancel; };
+// FP32 Gram X^T Y of two complete panels (no pieces): its plan fields as
+// chosen by gram_group_item
+struct GramArgs {
+    const float* x; int64_t ldx; const float* y; int64_t ldy; int64_t len; int ell; double* out; float* work;
+    int* cnt; int ntile, tiles, nc, sym; const int* cancel;
+};
+
+// Grid-stride kernels: every block of the launch serves every problem.
+constexpr unsigned kAnyGrid = 0xffffffffu;
+// Blocks of 256 threads for a grid-stride pass over `total` elements.
+inline unsigned stride_grid(int64_t total) {
+    const int64_t b = (total + 255) / 256;
+    return (unsigned)(b < 1 ? 1 : (b > 8192 ? 8192 : b));
+}
+
+// Items with their grids, and the grouped launches (gx, gy: the largest grid
+// of the items launched; count: how many items, from the first).
+GroupItem<ZeroArgs> zero_item(void* p, int64_t bytes);
+GroupItem<GaussArgs> gaussian_item(const GaussArgs& a);
+GroupItem<CastArgs> cast3_item(const CastArgs& a);
+GroupItem<SplitArgs> split_item(const SplitArgs& a);
+GroupItem<CholArgs> cholesky_item(const CholArgs& a);
+GroupItem<RinvArgs> rinv_item(const RinvArgs& a);
+GroupItem<TrsmArgs> trsm_item(const TrsmArgs& a);
+GroupItem<QrcpArgs> qrcp_item(const QrcpArgs& a);
+GroupItem<ReflArgs> refl_item(const ReflArgs& a);
+GroupItem<GatherArgs> gather_item(const GatherArgs& a);
+GroupItem<EmitArgs> emit_item(const EmitArgs& a);
+// The Gram's plan for a problem of a batch: about 256 rows per CTA, from the
+// problem's own sizes only (so a problem's sums do not depend on the batch).
+// Its workspace and counters fit gram_f32_work_floats / gram_f32_counters
+// for the same num_sms.
+GroupItem<GramArgs> gram_group_item(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_t len, int ell,
+                                    double* out, float* work, int* cnt, const int* cancel, int num_sms);
+cudaError_t launch_zero_grouped(const GroupItem<ZeroArgs>* it, int count, unsigned gx, cudaStream_t st);
+cudaError_t launch_gaussian_grouped(const GroupItem<GaussArgs>* it, int count, unsigned gx, cudaStream_t st);
+cudaError_t launch_cast3_grouped(const GroupItem<CastArgs>* it, int count, unsigned gx, unsigned gy, cudaStream_t st);
+cudaError_t launch_split_grouped(const GroupItem<SplitArgs>* it, int count, unsigned gx, cudaStream_t st);
+cudaError_t launch_cholesky_grouped(const GroupItem<CholArgs>* it, int count, int max_ell, bool defic,
+                                    cudaStream_t st);
+cudaError_t launch_rinv_grouped(const GroupItem<RinvArgs>* it, int count, unsigned gx, int max_ell, cudaStream_t st);
+cudaError_t launch_trsm_grouped(const GroupItem<TrsmArgs>* it, int count, unsigned gx, int max_ell, bool qc_bf16,
+                                cudaStream_t st);
+cudaError_t launch_qrcp_grouped(const GroupItem<QrcpArgs>* it, int count, int max_ell, cudaStream_t st);
+cudaError_t launch_refl_grouped(const GroupItem<ReflArgs>* it, int count, unsigned gx, int max_ell, cudaStream_t st);
+cudaError_t launch_gather_grouped(const GroupItem<GatherArgs>* it, int count, unsigned gx, cudaStream_t st);
+cudaError_t launch_emit_grouped(const GroupItem<EmitArgs>* it, int count, unsigned gx, cudaStream_t st);
+cudaError_t launch_gram_grouped(const GroupItem<GramArgs>* it, int count, unsigned gx, unsigned gy, cudaStream_t st);
+
 // RPCA pieces (k_rpca.cu).
 struct RpcaIterArgs {
     const void* m; ElemType tm; int64_t ldm;

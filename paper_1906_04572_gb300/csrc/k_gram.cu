@@ -152,10 +152,10 @@ __device__ __forceinline__ void load_row(const float* panel, int64_t ld, const T
     }
 }
 
-__global__ void __launch_bounds__(kGThreads)
-gram_f32_kernel(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_t len, int ell, double* out,
-                float* cpart, int* cnt, GramPlan pl, const int* cancel, TcPieces pieces_x, TcPieces pieces_y,
-                int writeback) {
+__device__ __forceinline__ void gram_f32_body(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_t len,
+                                              int ell, double* out, float* cpart, int* cnt, const GramPlan& pl,
+                                              const int* cancel, const TcPieces& pieces_x, const TcPieces& pieces_y,
+                                              int writeback) {
     pdl_wait();
     namespace cg = cooperative_groups;
     if (cancel && *cancel) return;  // uniform over the grid: no cluster barrier is left waiting
@@ -272,6 +272,24 @@ gram_f32_kernel(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_
     }
 }
 
+__global__ void __launch_bounds__(kGThreads)
+gram_f32_kernel(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_t len, int ell, double* out,
+                float* cpart, int* cnt, GramPlan pl, const int* cancel, TcPieces pieces_x, TcPieces pieces_y,
+                int writeback) {
+    gram_f32_body(x, ldx, y, ldy, len, ell, out, cpart, cnt, pl, cancel, pieces_x, pieces_y, writeback);
+}
+
+// One problem of a grouped Gram launch (complete panels: no pieces)
+__device__ __forceinline__ void gram_group_body(const GramArgs& a) {
+    GramPlan pl;
+    pl.ntile = a.ntile;
+    pl.tiles = a.tiles;
+    pl.nc = a.nc;
+    pl.sym = a.sym;
+    const TcPieces none;
+    gram_f32_body(a.x, a.ldx, a.y, a.ldy, a.len, a.ell, a.out, a.work, a.cnt, pl, a.cancel, none, none, 0);
+}
+
 }  // namespace
 
 // Workspace for either plan (X^T Y, or X^T X on the upper tiles).
@@ -308,6 +326,45 @@ cudaError_t launch_gram_f32(const float* x, int64_t ldx, const float* y, int64_t
     prefer_max_shared(reinterpret_cast<const void*>(gram_f32_kernel));
     return cudaLaunchKernelEx(&cfg, gram_f32_kernel, x, ldx, y, ldy, len, ell, out, work, cnt, p, cancel, px, py,
                               writeback ? 1 : 0);
+}
+
+
+GroupItem<GramArgs> gram_group_item(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_t len, int ell,
+                                    double* out, float* work, int* cnt, const int* cancel, int num_sms) {
+    const bool sym = x == y && ldx == ldy;
+    const GramPlan full = gram_plan(len, ell, num_sms, sym);
+    GramPlan p = full;
+    const int64_t nc = (len + 256 * kGCluster - 1) / (256 * kGCluster);  // about 256 rows per CTA
+    p.nc = (int)std::max<int64_t>(1, std::min<int64_t>(nc, full.nc));    // within the one-problem workspace
+    GroupItem<GramArgs> it;
+    it.a = GramArgs{x, ldx, y, ldy, len, ell, out, work, cnt, p.ntile, p.tiles, p.nc, p.sym, cancel};
+    it.gx = (unsigned)(p.nc * kGCluster);
+    it.gy = (unsigned)p.tiles;
+    return it;
+}
+
+cudaError_t launch_gram_grouped(const GroupItem<GramArgs>* it, int count, unsigned gx, unsigned gy, cudaStream_t st) {
+    if (count < 1) return cudaSuccess;
+    if (gx % kGCluster != 0) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(gx, gy, (unsigned)count);
+    cfg.blockDim = dim3(kGThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kGCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    count_launch();
+    auto kern = grouped_kernel<GramArgs, gram_group_body, kGThreads>;
+    prefer_max_shared(reinterpret_cast<const void*>(kern));
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, it);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace corutv

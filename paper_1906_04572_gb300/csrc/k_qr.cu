@@ -111,9 +111,9 @@ __device__ __forceinline__ void bar_sync(int id, int count) {
 }
 
 template <bool kDefic>
-__global__ void __launch_bounds__(kCholThreads)
-cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, int* skip_out,
-                const int* cancel, double unit_roundoff, int* defic, double tau_rel) {
+__device__ __forceinline__ void cholesky_body(const double* g, int ell, int64_t rows, double* r, int* flags,
+                                              int* skip_out, const int* cancel, double unit_roundoff, int* defic,
+                                              double tau_rel) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     extern __shared__ double S[];  // ell x (ell + 1) doubles, then the uint16 table
     const int ld = ell + 1;
@@ -322,6 +322,13 @@ cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, i
         if (attempt > 0) atomicAdd(&flags[FLAG_SHIFTED], 1);
         if (skip_out) *skip_out = (attempt > 0 && !broke) ? 0 : 1;
     }
+}
+
+template <bool kDefic>
+__global__ void __launch_bounds__(kCholThreads)
+cholesky_kernel(const double* g, int ell, int64_t rows, double* r, int* flags, int* skip_out,
+                const int* cancel, double unit_roundoff, int* defic, double tau_rel) {
+    cholesky_body<kDefic>(g, ell, rows, r, flags, skip_out, cancel, unit_roundoff, defic, tau_rel);
 }
 
 // Product of the upper triangular factors of successive CholeskyQR passes:
@@ -597,8 +604,7 @@ __device__ __forceinline__ void rinv_slot(float (&b)[4], const float* Rt, int ld
     }
 }
 
-__global__ void __launch_bounds__(kRiWarps * 32)
-rinv_kernel(const double* r, int ell, float* ri, int ldri, const int* cancel) {
+__device__ __forceinline__ void rinv_body(const double* r, int ell, float* ri, int ldri, const int* cancel) {
     pdl_wait();
     if (cancel && *cancel) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -646,6 +652,11 @@ rinv_kernel(const double* r, int ell, float* ri, int ldri, const int* cancel) {
             for (int jj = ell; jj < ldri; ++jj) ri[(int64_t)i * ldri + jj] = 0.f;
 }
 
+__global__ void __launch_bounds__(kRiWarps * 32)
+rinv_kernel(const double* r, int ell, float* ri, int ldri, const int* cancel) {
+    rinv_body(r, ell, ri, ldri, cancel);
+}
+
 // trsm_gemm_kernel: 128 rows per block, staged column by column into shared
 // memory (k-major: Cs[k][row]) together with R^{-1} (both with all of a
 // thread's loads in flight before its stores); warp w computes columns
@@ -656,9 +667,9 @@ rinv_kernel(const double* r, int ell, float* ri, int ldri, const int* cancel) {
 // In place (q == c) is safe: a block reads all its rows before writing any.
 constexpr int kTgRows = 128;
 template <typename TQC>
-__global__ void __launch_bounds__(512)
-trsm_gemm_kernel(const float* c, int64_t ldc, int64_t rows, int ell, const float* ri, int ldri, float* q,
-                 int64_t ldq, TQC* qc, int64_t ldqc, const int* cancel, const int* defic) {
+__device__ __forceinline__ void trsm_gemm_body(const float* c, int64_t ldc, int64_t rows, int ell, const float* ri,
+                                               int ldri, float* q, int64_t ldq, TQC* qc, int64_t ldqc,
+                                               const int* cancel, const int* defic) {
     pdl_wait();
     if (cancel && *cancel) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -702,6 +713,7 @@ trsm_gemm_kernel(const float* c, int64_t ldc, int64_t rows, int ell, const float
     }
     __syncthreads();
     const int j0 = 8 * w;
+    if (j0 >= ell) return;  // warps beyond this problem's columns (a grouped launch sized for a wider one)
     const int kend = min(ell, j0 + 8);
     float acc[4][8];
 #pragma unroll
@@ -746,6 +758,13 @@ trsm_gemm_kernel(const float* c, int64_t ldc, int64_t rows, int ell, const float
                 if (i0 + a < nr) qc[(int64_t)j * ldqc + r0 + i0 + a] = (TQC)v[a];
         }
     }
+}
+
+template <typename TQC>
+__global__ void __launch_bounds__(512)
+trsm_gemm_kernel(const float* c, int64_t ldc, int64_t rows, int ell, const float* ri, int ldri, float* q,
+                 int64_t ldq, TQC* qc, int64_t ldqc, const int* cancel, const int* defic) {
+    trsm_gemm_body<TQC>(c, ldc, rows, ell, ri, ldri, q, ldq, qc, ldqc, cancel, defic);
 }
 
 int trsm_inv_ldri(int ell) { return (ell + 7) & ~7; }
@@ -840,8 +859,8 @@ __device__ __forceinline__ int qr_pivot(const double* nrm, int j, int ell, int l
     return 127 - (int)(best & 0x7f);
 }
 
-__global__ void __launch_bounds__(kQrcpThreads)
-qrcp_kernel(const double* d, int ell, double* refl, double* rt, int* perm, const int* cancel) {
+__device__ __forceinline__ void qrcp_body(const double* d, int ell, double* refl, double* rt, int* perm,
+                                          const int* cancel) {
     pdl_wait();
     if (cancel && *cancel) return;
     extern __shared__ double W[];  // ell columns of ldw doubles, then nrm, xbuf, tau, sgn, tdot, perm
@@ -1002,6 +1021,11 @@ qrcp_kernel(const double* d, int ell, double* refl, double* rt, int* perm, const
         refl[ell * ell + c] = tau[c];
         refl[ell * ell + ell + c] = sgn[c];
     }
+}
+
+__global__ void __launch_bounds__(kQrcpThreads)
+qrcp_kernel(const double* d, int ell, double* refl, double* rt, int* perm, const int* cancel) {
+    qrcp_body(d, ell, refl, rt, perm, cancel);
 }
 
 // ---------------------------------------------------------------------------
@@ -1282,9 +1306,8 @@ qform_kernel(const double* refl, int ell, double* qt, const int* cancel) {
 // reflector each lane forms its part of v_j^T x, two xor shuffles add the
 // parts, and each lane updates its own entries. 32 rows per block.
 template <typename TI, typename TC, typename TO>
-__global__ void __launch_bounds__(kTrsmThreads)
-apply_refl_kernel(const TI* x, int64_t ldx, int64_t rows, int ell, const double* refl, TO* out, int64_t ldo,
-                  int out_panel, const int* cancel) {
+__device__ __forceinline__ void apply_refl_body(const TI* x, int64_t ldx, int64_t rows, int ell, const double* refl,
+                                                TO* out, int64_t ldo, int out_panel, const int* cancel) {
     pdl_wait();
     if (cancel && *cancel) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1360,9 +1383,16 @@ apply_refl_kernel(const TI* x, int64_t ldx, int64_t rows, int ell, const double*
     }
 }
 
+template <typename TI, typename TC, typename TO>
+__global__ void __launch_bounds__(kTrsmThreads)
+apply_refl_kernel(const TI* x, int64_t ldx, int64_t rows, int ell, const double* refl, TO* out, int64_t ldo,
+                  int out_panel, const int* cancel) {
+    apply_refl_body<TI, TC, TO>(x, ldx, rows, ell, refl, out, ldo, out_panel, cancel);
+}
+
 template <typename TQ, typename TV>
-__global__ void gather_v_kernel(const TQ* q2, int64_t ldq2, int64_t n, int ell, const int* perm,
-                                TV* v, int64_t ldv, const int* cancel) {
+__device__ __forceinline__ void gather_v_body(const TQ* q2, int64_t ldq2, int64_t n, int ell, const int* perm,
+                                              TV* v, int64_t ldv, const int* cancel) {
     pdl_trigger();
     pdl_wait();
     if (cancel && *cancel) return;
@@ -1384,6 +1414,12 @@ __global__ void gather_v_kernel(const TQ* q2, int64_t ldq2, int64_t n, int ell, 
             if (i < n) v[i * ldv + j0 + j] = (TV)tile[j][ii];
         }
     }
+}
+
+template <typename TQ, typename TV>
+__global__ void gather_v_kernel(const TQ* q2, int64_t ldq2, int64_t n, int ell, const int* perm,
+                                TV* v, int64_t ldv, const int* cancel) {
+    gather_v_body<TQ, TV>(q2, ldq2, n, ell, perm, v, ldv, cancel);
 }
 
 // dst = src (ell x ell, row-major), or its transpose
@@ -2078,6 +2114,139 @@ cudaError_t launch_copy_small(const double* src, int64_t ell, void* dst, ElemTyp
                         : launch_pdl(copy_small_kernel<float>, dim3((n + 255) / 256), dim3(256), (size_t)0, st, src, l,
                                      static_cast<float*>(dst), transpose ? 1 : 0, cancel);
     return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+}  // namespace corutv
+
+// ---------------------------------------------------------------------------
+// Grouped forms of the small steps (one launch over the problems of a batch):
+// the one-problem kernels' bodies, blockIdx.z selecting the problem.
+// ---------------------------------------------------------------------------
+namespace corutv {
+namespace {
+
+template <bool kDefic>
+__device__ __forceinline__ void chol_g(const CholArgs& a) {
+    cholesky_body<kDefic>(a.g, a.ell, a.rows, a.r, a.flags, a.skip_out, a.cancel, a.unit_roundoff, a.defic,
+                          a.tau_rel);
+}
+__device__ __forceinline__ void rinv_g(const RinvArgs& a) { rinv_body(a.r, a.ell, a.ri, a.ldri, a.cancel); }
+template <typename TQC>
+__device__ __forceinline__ void trsm_g(const TrsmArgs& a) {
+    trsm_gemm_body<TQC>(a.c, a.ldc, a.rows, a.ell, a.ri, a.ldri, a.q, a.ldq, static_cast<TQC*>(a.qc), a.ldqc,
+                        a.cancel, a.defic);
+}
+__device__ __forceinline__ void qrcp_g(const QrcpArgs& a) { qrcp_body(a.d, a.ell, a.refl, a.rt, a.perm, a.cancel); }
+__device__ __forceinline__ void refl_g(const ReflArgs& a) {
+    apply_refl_body<float, float, float>(a.x, a.ldx, a.rows, a.ell, a.refl, a.out, a.ldo, 0, a.cancel);
+}
+__device__ __forceinline__ void gather_g(const GatherArgs& a) {
+    gather_v_body<float, float>(a.q2, a.ldq2, a.n, a.ell, a.perm, a.v, a.ldv, a.cancel);
+}
+// T = Rt in FP32 (row-major) and the pivots copied out
+__device__ __forceinline__ void emit_g(const EmitArgs& a) {
+    pdl_trigger();
+    pdl_wait();
+    if (a.cancel && *a.cancel) return;
+    const int n = a.ell * a.ell;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n + a.ell; e += gridDim.x * blockDim.x) {
+        if (e < n) a.t[e] = (float)a.rt[e];
+        else if (a.perm_dst) a.perm_dst[e - n] = a.perm_src[e - n];
+    }
+}
+
+template <class A>
+GroupItem<A> item_of(const A& a, unsigned gx, unsigned gy = 1) {
+    GroupItem<A> it;
+    it.a = a;
+    it.gx = gx;
+    it.gy = gy;
+    return it;
+}
+
+template <class A, void (*F)(const A&), int kT>
+cudaError_t launch_group(const GroupItem<A>* it, int count, dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
+    if (count < 1) return cudaSuccess;
+    if (count > 65535) return cudaErrorInvalidValue;
+    auto kern = grouped_kernel<A, F, kT>;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(kern));
+        if (e != cudaSuccess) return e;
+    }
+    count_launch();
+    grid.z = (unsigned)count;
+    const cudaError_t e = launch_pdl(kern, grid, block, smem, st, it);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+size_t chol_smem(int ell) {
+    return sizeof(double) * (size_t)ell * (ell + 1) + sizeof(unsigned short) * (size_t)ell * (ell + 1) / 2;
+}
+size_t rinv_smem(int ell) { return sizeof(float) * ((size_t)ell * rinv_ldt(ell) + ell); }
+size_t trsmg_smem(int ell) { return sizeof(float) * (size_t)ell * (kTgRows + trsm_inv_ldri(ell)); }
+size_t qrcp_smem(int ell) {
+    return sizeof(double) * ((size_t)ell * (ell | 1) + 5 * (size_t)ell) + sizeof(int) * ell;
+}
+size_t refl_smem(int ell) {
+    return sizeof(float) * ((size_t)ell * ell + 2 * (size_t)ell + (size_t)kTrsmRows * trsm_ld(ell));
+}
+
+}  // namespace
+
+GroupItem<CholArgs> cholesky_item(const CholArgs& a) { return item_of(a, 1); }
+GroupItem<RinvArgs> rinv_item(const RinvArgs& a) { return item_of(a, (unsigned)((a.ell + kRiWarps - 1) / kRiWarps)); }
+GroupItem<TrsmArgs> trsm_item(const TrsmArgs& a) {
+    return item_of(a, (unsigned)((a.rows + kTgRows - 1) / kTgRows));
+}
+GroupItem<QrcpArgs> qrcp_item(const QrcpArgs& a) { return item_of(a, 1); }
+GroupItem<ReflArgs> refl_item(const ReflArgs& a) {
+    return item_of(a, (unsigned)((a.rows + kTrsmRows - 1) / kTrsmRows));
+}
+GroupItem<GatherArgs> gather_item(const GatherArgs& a) { return item_of(a, (unsigned)((a.n + 31) / 32)); }
+GroupItem<EmitArgs> emit_item(const EmitArgs& a) { return item_of(a, kAnyGrid); }
+
+cudaError_t launch_cholesky_grouped(const GroupItem<CholArgs>* it, int count, int max_ell, bool defic,
+                                    cudaStream_t st) {
+    if (max_ell < 1 || max_ell > kCholMaxEll) return cudaErrorInvalidValue;
+    const size_t smem = chol_smem(max_ell);
+    return defic ? launch_group<CholArgs, chol_g<true>, kCholThreads>(it, count, dim3(1), dim3(kCholThreads), smem, st)
+                 : launch_group<CholArgs, chol_g<false>, kCholThreads>(it, count, dim3(1), dim3(kCholThreads), smem,
+                                                                       st);
+}
+
+cudaError_t launch_rinv_grouped(const GroupItem<RinvArgs>* it, int count, unsigned gx, int max_ell, cudaStream_t st) {
+    if (max_ell < 1 || max_ell > 128) return cudaErrorInvalidValue;
+    return launch_group<RinvArgs, rinv_g, kRiWarps * 32>(it, count, dim3(gx), dim3(kRiWarps * 32), rinv_smem(max_ell),
+                                                         st);
+}
+
+cudaError_t launch_trsm_grouped(const GroupItem<TrsmArgs>* it, int count, unsigned gx, int max_ell, bool qc_bf16,
+                                cudaStream_t st) {
+    if (max_ell < 1 || max_ell > 128) return cudaErrorInvalidValue;
+    const dim3 block(32 * ((max_ell + 7) / 8));
+    const size_t smem = trsmg_smem(max_ell);
+    return qc_bf16 ? launch_group<TrsmArgs, trsm_g<__nv_bfloat16>, 512>(it, count, dim3(gx), block, smem, st)
+                   : launch_group<TrsmArgs, trsm_g<float>, 512>(it, count, dim3(gx), block, smem, st);
+}
+
+cudaError_t launch_qrcp_grouped(const GroupItem<QrcpArgs>* it, int count, int max_ell, cudaStream_t st) {
+    if (max_ell < 1 || max_ell > 128) return cudaErrorInvalidValue;
+    return launch_group<QrcpArgs, qrcp_g, kQrcpThreads>(it, count, dim3(1), dim3(kQrcpThreads), qrcp_smem(max_ell),
+                                                        st);
+}
+
+cudaError_t launch_refl_grouped(const GroupItem<ReflArgs>* it, int count, unsigned gx, int max_ell, cudaStream_t st) {
+    if (max_ell < 1 || max_ell > 128) return cudaErrorInvalidValue;
+    return launch_group<ReflArgs, refl_g, kTrsmThreads>(it, count, dim3(gx), dim3(kTrsmThreads), refl_smem(max_ell),
+                                                        st);
+}
+
+cudaError_t launch_gather_grouped(const GroupItem<GatherArgs>* it, int count, unsigned gx, cudaStream_t st) {
+    return launch_group<GatherArgs, gather_g, 256>(it, count, dim3(gx), dim3(256), 0, st);
+}
+
+cudaError_t launch_emit_grouped(const GroupItem<EmitArgs>* it, int count, unsigned gx, cudaStream_t st) {
+    return launch_group<EmitArgs, emit_g, 256>(it, count, dim3(gx), dim3(256), 0, st);
 }
 
 }  // namespace corutv

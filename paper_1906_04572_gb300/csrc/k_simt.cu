@@ -529,4 +529,72 @@ cudaError_t launch_panel_convert(const void* src, ElemType tsrc, int64_t lds, in
     return cudaErrorInvalidValue;
 }
 
+
+// ---------------------------------------------------------------------------
+// Grouped forms (one launch over the problems of a batch).
+// ---------------------------------------------------------------------------
+namespace {
+// zero fill of a byte range (16-byte aligned start, length a multiple of 4)
+__device__ __forceinline__ void zero_body(const ZeroArgs& a) {
+    pdl_trigger();
+    pdl_wait();
+    const int64_t n4 = a.bytes >> 4;
+    uint4* p = static_cast<uint4*>(a.p);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n4; e += (int64_t)gridDim.x * blockDim.x)
+        p[e] = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t* q = reinterpret_cast<uint32_t*>(static_cast<char*>(a.p) + (n4 << 4));
+    const int64_t r4 = (a.bytes - (n4 << 4)) >> 2;
+    if (blockIdx.x == 0)
+        for (int64_t e = threadIdx.x; e < r4; e += blockDim.x) q[e] = 0u;
+}
+
+// The Gaussian panel of launch_gaussian_panel's FP32 draw, stored as bf16
+// (the rounding panel_convert applies to that FP32 panel)
+__device__ __forceinline__ void gaussian_bf16_body(const GaussArgs& a) {
+    pdl_trigger();
+    pdl_wait();
+    if (a.cancel && *a.cancel) return;
+    const int64_t total = a.n * a.ellp;
+    __nv_bfloat16* x = static_cast<__nv_bfloat16*>(a.x);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / a.n, i = e % a.n;
+        const float v = (j < a.ell) ? gauss_elem<float>(a.seed, a.sid, (uint32_t)i, (uint32_t)j) : 0.f;
+        x[j * a.ldx + i] = cvt<__nv_bfloat16>(v);
+    }
+}
+}  // namespace
+
+GroupItem<ZeroArgs> zero_item(void* p, int64_t bytes) {
+    GroupItem<ZeroArgs> it;
+    it.a = ZeroArgs{p, bytes};
+    it.gx = kAnyGrid;
+    it.gy = 1;
+    return it;
+}
+
+GroupItem<GaussArgs> gaussian_item(const GaussArgs& a) {
+    GroupItem<GaussArgs> it;
+    it.a = a;
+    it.gx = kAnyGrid;
+    it.gy = 1;
+    return it;
+}
+
+cudaError_t launch_zero_grouped(const GroupItem<ZeroArgs>* it, int count, unsigned gx, cudaStream_t st) {
+    if (count < 1) return cudaSuccess;
+    count_launch();
+    cudaError_t e = launch_pdl(grouped_kernel<ZeroArgs, zero_body, 256>, dim3(gx, 1, (unsigned)count), dim3(256),
+                               (size_t)0, st, it);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_gaussian_grouped(const GroupItem<GaussArgs>* it, int count, unsigned gx, cudaStream_t st) {
+    if (count < 1) return cudaSuccess;
+    count_launch();
+    cudaError_t e = launch_pdl(grouped_kernel<GaussArgs, gaussian_bf16_body, 256>, dim3(gx, 1, (unsigned)count),
+                               dim3(256), (size_t)0, st, it);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 }  // namespace corutv

@@ -37,6 +37,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -93,6 +94,13 @@ struct TcParams {
     int* flags;
     const int* cancel;
     int defer;            // split tiles: leave the pieces for the consumer (no count, no reduction)
+};
+
+// One problem of a grouped product launch: the B panel's tensor map and the
+// problem's parameters (the CUtensorMap first: 64-byte aligned in the array).
+struct alignas(128) TcGroupItem {
+    CUtensorMap map_b;
+    TcParams p;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -299,9 +307,8 @@ __device__ __forceinline__ void sum_staged(const float* sp, int np, int ellp, in
 }
 
 template <bool kTf32>
-__global__ void __launch_bounds__(kThreads, 1)
-sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
-                 const TcParams p) {
+__device__ __forceinline__ void sketch_tc_body(const CUtensorMap* map_a, const CUtensorMap* map_b, const TcParams& p,
+                                               bool prefetch_maps) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kMaxStages];
     __shared__ __align__(8) uint64_t empty_bar[kMaxStages];
@@ -342,9 +349,9 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
         consumed_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 4 && lane == 0) {
-        if (!p.a_tiles) prefetch_tmap(&map_a);
-        prefetch_tmap(&map_b);
+    if (warp == 4 && lane == 0 && prefetch_maps) {
+        if (!p.a_tiles) prefetch_tmap(map_a);
+        prefetch_tmap(map_b);
     }
     // setup above overlaps the previous kernel's tail; operands and flags are read below
     pdl_wait();
@@ -404,15 +411,15 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                     if (p.a_tiles) {
                         // A already requested above
                     } else if (!p.trans) {
-                        tma_load_2d(sag, &map_a, &full_bar[s], seg * p.seg_stride + kx, (int)(t * kTileM));
+                        tma_load_2d(sag, map_a, &full_bar[s], seg * p.seg_stride + kx, (int)(t * kTileM));
                     } else {
                         for (int bx = 0; bx < p.a_boxes; ++bx)
-                            tma_load_2d(sag + bx * box_bytes, &map_a, &full_bar[s],
+                            tma_load_2d(sag + bx * box_bytes, map_a, &full_bar[s],
                                         (int)(t * kTileM + bx * p.a_box_cols), kx);
                     }
                     uint8_t* sbg = sb + (size_t)g * b_bytes;
                     for (int bx = 0; bx < p.b_boxes; ++bx)
-                        tma_load_2d(sbg + bx * p.b_box_rows * 128, &map_b, &full_bar[s], kx, bx * p.b_box_rows);
+                        tma_load_2d(sbg + bx * p.b_box_rows * 128, map_b, &full_bar[s], kx, bx * p.b_box_rows);
                 }
                 if (++s == S) { s = 0; ++r; }
                 if (++kk == p.kc_seg) { kk = 0; ++seg; }
@@ -622,6 +629,32 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
     }
 }
 
+template <bool kTf32>
+__global__ void __launch_bounds__(kThreads, 1)
+sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                 const __grid_constant__ TcParams p) {
+    sketch_tc_body<kTf32>(&map_a, &map_b, p, true);
+}
+
+// The products of the problems of a batch in one launch: problem blockIdx.y
+// runs the stream-K schedule of its own TcParams (its grid, operands, output,
+// partials and counters) on the CTAs blockIdx.x < its grid; the B panel's
+// tensor map is read from the item in global memory (written by a copy
+// before the launch: the acquire fence orders the tensor-map proxy's read of
+// it after that write).
+__global__ void __launch_bounds__(kThreads, 1) sketch_tc_grouped_kernel(const TcGroupItem* items) {
+    const TcGroupItem* gi = items + blockIdx.y;
+    __shared__ TcParams ps;
+    if ((int)blockIdx.x >= gi->p.grid) return;
+    if (threadIdx.x == 0) ps = gi->p;
+    if (threadIdx.x == 128)  // the producer thread
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                         reinterpret_cast<uint64_t>(&gi->map_b))
+                     : "memory");
+    __syncthreads();
+    sketch_tc_body<false>(nullptr, &gi->map_b, ps, false);
+}
+
 // The bounded-wait path of the tensor-core kernels, exercised on purpose:
 // one warp allocates 32 columns of tensor memory, waits on an mbarrier that
 // nothing ever arrives on, gives up after about limit_ns, raises
@@ -751,8 +784,8 @@ prep_f32_kernel(const float* a, long long m, long long n, long long lda, float* 
 }
 
 // q3 column x * ellp + j = part x of panel column j (zero for ell <= j < ellp).
-__global__ void split_panel_kernel(const float* q, long long ldq, long long rows, int ell, int ellp,
-                                   __nv_bfloat16* q3, long long ldq3, const int* cancel) {
+__device__ __forceinline__ void split_panel_body(const float* q, long long ldq, long long rows, int ell, int ellp,
+                                                 __nv_bfloat16* q3, long long ldq3, const int* cancel) {
     pdl_trigger();
     pdl_wait();
     if (cancel && *cancel) return;
@@ -766,6 +799,11 @@ __global__ void split_panel_kernel(const float* q, long long ldq, long long rows
         q3[(ellp + j) * ldq3 + i] = md;
         q3[(2 * ellp + j) * ldq3 + i] = lo;
     }
+}
+
+__global__ void split_panel_kernel(const float* q, long long ldq, long long rows, int ell, int ellp,
+                                   __nv_bfloat16* q3, long long ldq3, const int* cancel) {
+    split_panel_body(q, ldq, rows, ell, ellp, q3, ldq3, cancel);
 }
 
 // Tiled bf16 copy of A for the sketch products (and, with three parts, the
@@ -782,9 +820,9 @@ __global__ void split_panel_kernel(const float* q, long long ldq, long long rows
 // NP = 1: A_h only; 3: A_h, A_m, A_l; 2: A_m, A_l only (parts 1 and 2).
 // Row blocks rb0 + blockIdx.y.
 template <typename TI, int NP>
-__global__ void __launch_bounds__(256)
-cast_tiled_kernel(const TI* a, long long m, long long n, long long lda, uint8_t* out, long long ntp,
-                  long long part_bytes, long long rb0, const int* cancel) {
+__device__ __forceinline__ void cast_tiled_body(const TI* a, long long m, long long n, long long lda, uint8_t* out,
+                                                long long ntp, long long part_bytes, long long rb0,
+                                                const int* cancel) {
     pdl_trigger();
     pdl_wait();
     if (cancel && *cancel) return;
@@ -830,6 +868,13 @@ cast_tiled_kernel(const TI* a, long long m, long long n, long long lda, uint8_t*
             *reinterpret_cast<uint2*>(tile + 2 * part_bytes + off) = *reinterpret_cast<const uint2*>(lo);
         }
     }
+}
+
+template <typename TI, int NP>
+__global__ void __launch_bounds__(256)
+cast_tiled_kernel(const TI* a, long long m, long long n, long long lda, uint8_t* out, long long ntp,
+                  long long part_bytes, long long rb0, const int* cancel) {
+    cast_tiled_body<TI, NP>(a, m, n, lda, out, ntp, part_bytes, rb0, cancel);
 }
 
 // ---------------------------------------------------------------------------
@@ -903,23 +948,31 @@ uint32_t make_idesc(bool tf32, bool a_mn_major, int n) {
     return d;
 }
 
-// Shared launcher. A: rows x cols row-major (K-major for trans = 0, MN-major
-// for trans = 1) with `kseg` K segments `seg_stride` columns apart; B: panel
-// with nparts * ellp rows of the K-major operand (ldb); output: the panel c
-// (ell columns, type tcout) = sum over the nparts column groups.
-// One launch of the product with kgroup K boxes per stage and `stages_req`
-// ring stages (0: as many as fit 200 KB).
-cudaError_t tc_launch_cfg(const void* a, bool tf32, long long mtot, long long ktot_seg, int kseg, long long seg_stride,
-                          const CUtensorMap& map_a, int a_boxes, int a_box_cols, const void* b, long long ldb,
-                          long long brows_k, int nparts, int trans, int64_t ell, int64_t ellp, void* part,
-                          int* tile_cnt, void* c,
-                          ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel, cudaStream_t st,
-                          int kgroup, int stages_req, TcPieces* pieces, const uint8_t* a_tiles, long long a_ntp,
-                          long long a_seg_bytes) {
-    const Plan pl = make_plan(mtot, ktot_seg, kseg, tf32, num_sms, kgroup);
+// Parameters and B tensor map of one product. units_per_cta > 0: the grid is
+// the problem's own (about that many units per CTA, at most num_sms CTAs) and
+// the ring and accumulators are sized so that two CTAs share an SM (a
+// problem of a grouped launch); 0: one CTA per SM on min(num_sms, units).
+struct TcBuilt {
+    TcParams p;
+    CUtensorMap map_b;
+    size_t smem;
+};
+
+cudaError_t tc_build(TcBuilt& out, bool tf32, long long mtot, long long ktot_seg, int kseg, long long seg_stride,
+                     int a_boxes, int a_box_cols, const void* b, long long ldb, long long brows_k, int nparts,
+                     int trans, int64_t ell, int64_t ellp, void* part, int* tile_cnt, void* c, ElemType tcout,
+                     int64_t ldc, int num_sms, int* flags, const int* cancel, int kgroup, int stages_req,
+                     TcPieces* pieces, const uint8_t* a_tiles, long long a_ntp, long long a_seg_bytes,
+                     int units_per_cta = 0) {
+    Plan pl = make_plan(mtot, ktot_seg, kseg, tf32, num_sms, kgroup);
+    if (units_per_cta > 0) {
+        const long long g = std::min<long long>(num_sms, (pl.units + units_per_cta - 1) / units_per_cta);
+        pl = make_plan(mtot, ktot_seg, kseg, tf32, (int)std::max<long long>(1, g), kgroup);
+    }
     const int ke = tf32 ? 32 : 64;  // K elements per 128-byte row
     const int nb = nparts * (int)ellp;
-    TcParams p{};
+    TcParams& p = out.p;
+    p = TcParams{};
     p.units = pl.units;
     p.kchunks = pl.kc;
     p.kc_seg = (int)(pl.kc / kseg);
@@ -959,8 +1012,7 @@ cudaError_t tc_launch_cfg(const void* a, bool tf32, long long mtot, long long kt
         return cudaErrorInvalidValue;
     p.b_boxes = nb > 256 ? 2 : 1;
     p.b_box_rows = nb / p.b_boxes;
-    CUtensorMap map_b;
-    cudaError_t e = encode_2d(&map_b, b, tf32, brows_k, nb, ldb, (uint32_t)ke, (uint32_t)p.b_box_rows,
+    cudaError_t e = encode_2d(&out.map_b, b, tf32, brows_k, nb, ldb, (uint32_t)ke, (uint32_t)p.b_box_rows,
                               CU_TENSOR_MAP_SWIZZLE_128B);
     if (e != cudaSuccess) return e;
     // MMA N chunks: one if nb <= 256, else two multiples of 16
@@ -975,21 +1027,50 @@ cudaError_t tc_launch_cfg(const void* a, bool tf32, long long mtot, long long kt
     p.idesc1 = p.n1 ? make_idesc(tf32, trans != 0, p.n1) : 0;
     p.a_bytes = kTileM * 128;
     p.stage_bytes = (uint32_t)kgroup * (p.a_bytes + (uint32_t)nb * 128);
-    p.stages = std::min<int>(kMaxStages, (int)((200 * 1024) / p.stage_bytes));
+    // a problem of a grouped launch: a ring of at most 100 KB and 256 tensor-memory
+    // columns (two CTAs per SM), unless two stages need more (the widest split
+    // projections: then one CTA per SM, as a one-problem launch)
+    bool shared_sm = units_per_cta > 0 && 2 * (int)p.stage_bytes <= 100 * 1024;
+    const int budget = shared_sm ? 100 * 1024 : 200 * 1024;
+    p.stages = std::min<int>(kMaxStages, budget / (int)p.stage_bytes);
     if (stages_req > 0) p.stages = std::min(p.stages, stages_req);
     if (p.stages < 2) return cudaErrorInvalidValue;
     uint32_t cols = 32;
     while (cols < (uint32_t)nb) cols <<= 1;
-    p.nacc = (2 * cols <= 512) ? 2 : 1;
+    const uint32_t tmem_cap = shared_sm ? 256u : 512u;
+    p.nacc = (2 * cols <= tmem_cap) ? 2 : 1;
     p.acc_cols = cols;
     p.tmem_cols = p.nacc * cols;
-    const size_t smem = (size_t)p.stages * p.stage_bytes + 1024;
+    if (p.tmem_cols > tmem_cap) return cudaErrorInvalidValue;
+    out.smem = (size_t)p.stages * p.stage_bytes + 1024;
+    return cudaSuccess;
+}
+
+// Shared launcher. A: rows x cols row-major (K-major for trans = 0, MN-major
+// for trans = 1) with `kseg` K segments `seg_stride` columns apart; B: panel
+// with nparts * ellp rows of the K-major operand (ldb); output: the panel c
+// (ell columns, type tcout) = sum over the nparts column groups.
+// One launch of the product with kgroup K boxes per stage and `stages_req`
+// ring stages (0: as many as fit 200 KB).
+cudaError_t tc_launch_cfg(const void* a, bool tf32, long long mtot, long long ktot_seg, int kseg, long long seg_stride,
+                          const CUtensorMap& map_a, int a_boxes, int a_box_cols, const void* b, long long ldb,
+                          long long brows_k, int nparts, int trans, int64_t ell, int64_t ellp, void* part,
+                          int* tile_cnt, void* c,
+                          ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel, cudaStream_t st,
+                          int kgroup, int stages_req, TcPieces* pieces, const uint8_t* a_tiles, long long a_ntp,
+                          long long a_seg_bytes) {
+    (void)a;
+    TcBuilt tb;
+    cudaError_t e = tc_build(tb, tf32, mtot, ktot_seg, kseg, seg_stride, a_boxes, a_box_cols, b, ldb, brows_k, nparts,
+                             trans, ell, ellp, part, tile_cnt, c, tcout, ldc, num_sms, flags, cancel, kgroup,
+                             stages_req, pieces, a_tiles, a_ntp, a_seg_bytes);
+    if (e != cudaSuccess) return e;
     auto kern = tf32 ? sketch_tc_kernel<true> : sketch_tc_kernel<false>;
     e = allow_max_dynamic_smem(reinterpret_cast<const void*>(kern));
     if (e != cudaSuccess) return e;
     count_launch();
     {
-        cudaError_t pe_ = launch_pdl(kern, dim3(pl.grid), dim3(kThreads), (size_t)(smem), st, map_a, map_b, p);
+        cudaError_t pe_ = launch_pdl(kern, dim3(tb.p.grid), dim3(kThreads), tb.smem, st, map_a, tb.map_b, tb.p);
         if (pe_ != cudaSuccess) return pe_;
     }
     return cudaGetLastError();
@@ -1214,6 +1295,118 @@ cudaError_t launch_project_split_tc_tiled(const void* a3, int64_t m, int64_t n, 
     return tc_launch(a3, false, m, n, 3, 0, unused, 1, 0, q3, ldq, n, 3, 0, ell, ellp, part, tile_cnt, w, tw, ldw,
                      num_sms, flags, cancel, st, kgroup, pieces, static_cast<const uint8_t*>(a3), tiled_ntp(n),
                      tiled_part_bytes(m, n));
+}
+
+// ---------------------------------------------------------------------------
+// Grouped products (the problems of a batch in one launch)
+// ---------------------------------------------------------------------------
+namespace {
+// stream-K units (128 rows by one 128-byte K box) per CTA of a grouped product; one K box per stage
+constexpr int kGroupUnitsPerCta = 16;
+
+// (the host record may sit anywhere: it is assembled aligned and copied in)
+cudaError_t group_fill(void* item, const TcBuilt& tb, int* grid, size_t* smem, int64_t* part_floats) {
+    TcGroupItem it;
+    it.map_b = tb.map_b;
+    it.p = tb.p;
+    std::memcpy(item, &it, sizeof(it));
+    *grid = tb.p.grid;
+    *smem = tb.smem;
+    const long long mtiles = (tb.p.mtot + kTileM - 1) / kTileM;
+    *part_floats = mtiles * tb.p.maxp * (long long)tb.p.ellp * kTileM;
+    return cudaSuccess;
+}
+}  // namespace
+
+size_t tc_group_item_bytes() { return sizeof(TcGroupItem); }
+
+cudaError_t tc_group_sketch_item(void* item, const void* a_tiles, int64_t m, int64_t n, int trans, const void* x,
+                                 int64_t ldx, int64_t ell, int64_t ellp, void* part, int* tile_cnt, void* c,
+                                 ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel, int* grid,
+                                 size_t* smem, int64_t* part_floats) {
+    if (ellp % 16 != 0 || ellp < 16 || ellp > 128 || ell > ellp) return cudaErrorInvalidValue;
+    cudaError_t e = get_encoder();
+    if (e != cudaSuccess) return e;
+    TcBuilt tb;
+    e = tc_build(tb, false, trans ? n : m, trans ? m : n, 1, 0, 1, 0, x, ldx, trans ? m : n, 1, trans, ell, ellp, part,
+                 tile_cnt, c, tcout, ldc, num_sms, flags, cancel, 1, 0, nullptr,
+                 static_cast<const uint8_t*>(a_tiles), tiled_ntp(n), tiled_part_bytes(m, n), kGroupUnitsPerCta);
+    if (e != cudaSuccess) return e;
+    return group_fill(item, tb, grid, smem, part_floats);
+}
+
+cudaError_t tc_group_project_item(void* item, const void* a3, int64_t m, int64_t n, const void* q3, int64_t ldq,
+                                  int64_t ell, int64_t ellp, void* part, int* tile_cnt, void* w, ElemType tw,
+                                  int64_t ldw, int num_sms, int* flags, const int* cancel, int* grid, size_t* smem,
+                                  int64_t* part_floats) {
+    if (ellp % 16 != 0 || ellp < 16 || ellp > 128 || ell > ellp) return cudaErrorInvalidValue;
+    cudaError_t e = get_encoder();
+    if (e != cudaSuccess) return e;
+    TcBuilt tb;
+    e = tc_build(tb, false, m, n, 3, 0, 1, 0, q3, ldq, n, 3, 0, ell, ellp, part, tile_cnt, w, tw, ldw, num_sms, flags,
+                 cancel, 1, 0, nullptr, static_cast<const uint8_t*>(a3), tiled_ntp(n), tiled_part_bytes(m, n),
+                 kGroupUnitsPerCta);
+    if (e != cudaSuccess) return e;
+    return group_fill(item, tb, grid, smem, part_floats);
+}
+
+cudaError_t launch_sketch_tc_grouped(const void* items, int count, int max_grid, size_t max_smem, cudaStream_t st) {
+    if (count < 1) return cudaSuccess;
+    if (max_grid < 1 || count > 65535 || (reinterpret_cast<uintptr_t>(items) & 127) != 0) return cudaErrorInvalidValue;
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(sketch_tc_grouped_kernel));
+    if (e != cudaSuccess) return e;
+    count_launch();
+    e = launch_pdl(sketch_tc_grouped_kernel, dim3((unsigned)max_grid, (unsigned)count), dim3(kThreads), max_smem, st,
+                   static_cast<const TcGroupItem*>(items));
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// Grouped three-part cast and panel splits.
+namespace {
+// tiled_ntp / tiled_part_bytes on the device
+__device__ __forceinline__ long long tiled_ntp_dev(long long n) { return ((n + 63) / 64 + 1) / 2 * 2; }
+__device__ __forceinline__ long long tiled_part_bytes_dev(long long m, long long n) {
+    return ((m + kTileM - 1) / kTileM) * tiled_ntp_dev(n) * 16384;
+}
+__device__ __forceinline__ void cast3_body(const CastArgs& a) {
+    cast_tiled_body<float, 3>(a.a, a.m, a.n, a.lda, static_cast<uint8_t*>(a.out), tiled_ntp_dev(a.n),
+                              tiled_part_bytes_dev(a.m, a.n), 0, a.cancel);
+}
+__device__ __forceinline__ void split_body(const SplitArgs& a) {
+    split_panel_body(a.q, a.ldq, a.rows, a.ell, a.ellp, static_cast<__nv_bfloat16*>(a.q3), a.ldq3, a.cancel);
+}
+}  // namespace
+
+GroupItem<CastArgs> cast3_item(const CastArgs& a) {
+    GroupItem<CastArgs> it;
+    it.a = a;
+    it.gx = (unsigned)((tiled_ntp(a.n) + 7) / 8);
+    it.gy = (unsigned)((a.m + kTileM - 1) / kTileM);
+    return it;
+}
+
+GroupItem<SplitArgs> split_item(const SplitArgs& a) {
+    GroupItem<SplitArgs> it;
+    it.a = a;
+    it.gx = kAnyGrid;
+    it.gy = 1;
+    return it;
+}
+
+cudaError_t launch_cast3_grouped(const GroupItem<CastArgs>* it, int count, unsigned gx, unsigned gy, cudaStream_t st) {
+    if (count < 1) return cudaSuccess;
+    count_launch();
+    cudaError_t e = launch_pdl(grouped_kernel<CastArgs, cast3_body, 256>, dim3(gx, gy, (unsigned)count), dim3(256),
+                               (size_t)0, st, it);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_split_grouped(const GroupItem<SplitArgs>* it, int count, unsigned gx, cudaStream_t st) {
+    if (count < 1) return cudaSuccess;
+    count_launch();
+    cudaError_t e = launch_pdl(grouped_kernel<SplitArgs, split_body, 256>, dim3(gx, 1, (unsigned)count), dim3(256),
+                               (size_t)0, st, it);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_wait_probe(int* flags, unsigned long long limit_ns, cudaStream_t st) {

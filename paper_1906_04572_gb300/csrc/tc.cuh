@@ -88,6 +88,28 @@ cudaError_t launch_prep_f32(const float* a, int64_t m, int64_t n, int64_t lda, f
 cudaError_t launch_split_panel(const float* q, int64_t ldq, int64_t rows, int64_t ell, int64_t ellp, void* q3,
                                int64_t ldq3, const int* cancel, cudaStream_t st);
 
+// Grouped products: one launch over the problems of a batch. Each problem is
+// a record of tc_group_item_bytes() bytes (any host address; 128-byte aligned
+// in device memory when launched) filled on the host by one of the two calls below, with the
+// arguments of launch_sketch_tc_tiled (a product on the tiled bf16 copy) or
+// of launch_project_split_tc_tiled (the split projection). A problem's grid
+// is its own (about 16 stream-K units per CTA), so its sums do not depend on
+// the other problems; its split tiles are added by the product itself (the
+// counters must be zero). Out: the problem's grid, the dynamic shared memory
+// it needs and the partial floats it may use.
+size_t tc_group_item_bytes();
+cudaError_t tc_group_sketch_item(void* item, const void* a_tiles, int64_t m, int64_t n, int trans, const void* x,
+                                 int64_t ldx, int64_t ell, int64_t ellp, void* part, int* tile_cnt, void* c,
+                                 ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel, int* grid,
+                                 size_t* smem, int64_t* part_floats);
+cudaError_t tc_group_project_item(void* item, const void* a3, int64_t m, int64_t n, const void* q3, int64_t ldq,
+                                  int64_t ell, int64_t ellp, void* part, int* tile_cnt, void* w, ElemType tw,
+                                  int64_t ldw, int num_sms, int* flags, const int* cancel, int* grid, size_t* smem,
+                                  int64_t* part_floats);
+// count records from `items` (device); max_grid / max_smem: the largest grid
+// and shared memory of those records.
+cudaError_t launch_sketch_tc_grouped(const void* items, int count, int max_grid, size_t max_smem, cudaStream_t st);
+
 // Stage-shape autotuner of the tensor-core products (process-wide).
 void tc_set_autotune(bool on);
 // Number of tuned shapes; for 0 <= index < that number, its extents and choice.
