@@ -396,11 +396,13 @@ def concurrent_factorisations(device_index, A, k, p, q, prec, flops, counts=(1, 
     return out
 
 
-def serving_c5(device_index, nreq, rate, prec, slots):
+def serving_c5(device_index, nreq, rate, prec, slots, batch=0):
     """The serving stream (independent requests with Poisson arrivals, m, n ~
     U[256, 4096], k ~ U[5, 64], ell = k + 10, q ~ U{0, 1, 2}, FP32 inputs with
     sigma_i = i^-1.5 on the first 256 directions) through corutv_submit /
-    corutv_poll: per-request latency from submission to completion."""
+    corutv_poll: per-request latency from submission to completion. batch > 0:
+    continuous batching (corutv_set_batching) with batches of up to `batch`
+    requests on grouped launches."""
     import torch
     import synth
     from paper_1906_04572_gb300 import Context, corutv
@@ -417,6 +419,8 @@ def serving_c5(device_index, nreq, rate, prec, slots):
     torch.cuda.synchronize()
     flops = sum(flops_per_factor(r.m, r.n, r.k + r.p, r.q) for r in reqs)
     with Context(device_index, max_slots=slots) as sctx:
+        if batch:
+            corutv.corutv_set_batching(sctx.handle, batch)
         # warm-up: the first few requests once, outside the measurement
         warm = [corutv.corutv_submit(sctx.handle, corutv.make_request(mats[i], reqs[i].k, reqs[i].p, reqs[i].q,
                                                                       prec, *outs[i], seed=reqs[i].seed))
@@ -439,19 +443,21 @@ def serving_c5(device_index, nreq, rate, prec, slots):
             lats.append(lat)
         wall = time.perf_counter() - t0
     lats = np.array(lats) * 1e3
-    return {"requests": nreq, "rate_per_s": rate, "slots": slots, "prec": prec,
+    return {"requests": nreq, "rate_per_s": rate, "slots": slots, "prec": prec, "max_batch": batch,
             "p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99)),
             "solves_per_s": nreq / wall, "tflops": flops / wall / 1e12, "wall_s": wall,
             "inputs": "m, n ~ U[256, 4096], k ~ U[5, 64], ell = k + 10, q ~ U{0,1,2}, sigma_i = i^-1.5 (256 "
                       "directions), FP32, seed 0; product formed on the device from the seeded factors"}
 
 
-def serving_capacity(device_index, nreq, slots, nerr=64):
+def serving_capacity(device_index, nreq, slots, nerr=64, batch=256):
     """The first nreq requests of the serving stream submitted at once, in the
-    mixed-precision form (FP32 data, bf16 sketches) and on the plain FP64 path
-    (FP64 data and arithmetic): completed requests per second, and the
-    reconstruction error ||A - U T V^T|| / ||A|| of the first nerr requests in
-    both forms ("equal error": the mixed error within 1 % of the FP64 one)."""
+    mixed-precision form (FP32 data, bf16 sketches) one request per slot, the
+    same with continuous batching on grouped launches (up to `batch` requests
+    a batch), and on the plain FP64 path (FP64 data and arithmetic): completed
+    requests per second, and the reconstruction error ||A - U T V^T|| / ||A||
+    of the first nerr requests in each form ("equal error": the mixed error
+    within 1 % of the FP64 one)."""
     import torch
     import synth
     from paper_1906_04572_gb300 import Context, corutv
@@ -459,7 +465,9 @@ def serving_capacity(device_index, nreq, slots, nerr=64):
     dev = torch.device("cuda", device_index)
     res = {}
     errs = {}
-    for form, dt, prec in (("mixed_bf16", torch.float32, "bf16"), ("fp64", torch.float64, "f64")):
+    for form, dt, prec, nb in (("mixed_bf16", torch.float32, "bf16", 0),
+                               ("mixed_bf16_batched", torch.float32, "bf16", batch),
+                               ("fp64", torch.float64, "f64", 0)):
         mats, outs = [], []
         for r in reqs:
             u, sig, v = synth.serving_factors(r)
@@ -469,6 +477,8 @@ def serving_capacity(device_index, nreq, slots, nerr=64):
             mats.append(a)
         torch.cuda.synchronize()
         with Context(device_index, max_slots=slots) as sctx:
+            if nb:
+                corutv.corutv_set_batching(sctx.handle, nb)
             warm = [corutv.corutv_submit(sctx.handle, corutv.make_request(mats[i], reqs[i].k, reqs[i].p, reqs[i].q,
                                                                           prec, *outs[i], seed=reqs[i].seed))
                     for i in range(min(slots, nreq))]
@@ -493,10 +503,14 @@ def serving_capacity(device_index, nreq, slots, nerr=64):
         del mats, outs
         torch.cuda.empty_cache()
     ratio = errs["mixed_bf16"] / errs["fp64"]
-    res.update({"requests": nreq, "slots": slots, "errors_compared": int(len(ratio)),
+    ratio_b = errs["mixed_bf16_batched"] / errs["fp64"]
+    res.update({"requests": nreq, "slots": slots, "max_batch": batch, "errors_compared": int(len(ratio)),
                 "error_ratio_max": float(ratio.max()), "error_ratio_median": float(np.median(ratio)),
                 "equal_error": bool(ratio.max() <= 1.01),
+                "batched_error_ratio_max": float(ratio_b.max()),
+                "batched_equal_error": bool(ratio_b.max() <= 1.01),
                 "speedup": res["mixed_bf16"]["solves_per_s"] / res["fp64"]["solves_per_s"],
+                "batched_speedup": res["mixed_bf16_batched"]["solves_per_s"] / res["fp64"]["solves_per_s"],
                 "kind": "all requests submitted at once (capacity); same seeded requests and Psi in both forms"})
     return res
 
@@ -781,6 +795,11 @@ def run_ours(args):
         extra["c2"] = c2_lines(ctx, device, args.steps)
         extra["concurrent"] = concurrent_factorisations(local, A, k, p, q, prec, flops)
         extra["serving"] = serving_c5(local, args.serve_requests, args.serve_rate, "bf16", 8)
+        extra["serving_batched"] = serving_c5(local, args.serve_requests, args.serve_rate, "bf16", 8,
+                                              batch=args.serve_batch)
+        # four times the offered rate: beyond what one request per slot sustains
+        extra["serving_batched_4x_rate"] = serving_c5(local, args.serve_requests, 4 * args.serve_rate, "bf16", 8,
+                                                      batch=args.serve_batch)
         extra["serving"]["capacity_vs_fp64"] = serving_capacity(local, args.serve_capacity, 8)
         extra["rpca"] = rpca_c4(ctx, device)
         # the single-pass core (Sec. 3.1, d_mode 1): 2q+2 passes over A instead of 2q+3
@@ -857,6 +876,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary lines (C1 latency, C2, serving, RPCA, variants)")
     ap.add_argument("--serve-requests", type=int, default=1024)
+    ap.add_argument("--serve-batch", type=int, default=256,
+                    help="largest batch of the continuously batched serving run (grouped launches)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-capacity", type=int, default=128,
                     help="requests of the serving stream timed at once in the mixed and the FP64 form")

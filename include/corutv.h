@@ -213,6 +213,20 @@ typedef struct {
  * synchronisation needed). Host inputs must be complete at submit. */
 corutv_status corutv_submit(corutv_ctx* ctx, const corutv_request* req, uint64_t* ticket);
 
+/* Continuous batching of the serving stream. With max_batch > 0, queued
+ * requests that the grouped path takes (device FP32 A, BF16 sketches,
+ * d_mode / t_lower / power_form / bf16_last_round 0, psi NULL, ell <= 128:
+ * see corutv_factor_batch) are admitted as batches instead of one per slot:
+ * whenever one of two batch lanes is free, it takes the batchable requests at
+ * the head of the queue (arrival order, up to max_batch, as many as the
+ * memory budget allows) and runs them with grouped launches, while requests
+ * that arrive meanwhile queue for the other lane. Each result is bitwise the
+ * one the same request gives alone through corutv_factor_batch. A batch's
+ * device status words are shared: a breakdown or timeout in one problem is
+ * reported for every request of its batch. Other requests keep the slots.
+ * max_batch = 0 (the default) returns to one request per slot; 0 .. 4096. */
+corutv_status corutv_set_batching(corutv_ctx* ctx, int max_batch);
+
 /* Wait up to timeout_us (0 = do not wait, < 0 = forever) for a ticket.
  * CORUTV_EPENDING / CORUTV_ETIMEDOUT while unfinished; otherwise the
  * request's own status, with latency_s (optional) = completion - submit. */

@@ -71,6 +71,7 @@ _SIGS = {
                             ctypes.c_void_p], ctypes.c_int),
     "corutv_submit": ([ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "corutv_factor_batch": ([ctypes.c_void_p, ctypes.POINTER(Request), ctypes.c_int], ctypes.c_int),
+    "corutv_set_batching": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "corutv_poll": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)],
                     ctypes.c_int),
     "corutv_profile_enable": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
@@ -328,6 +329,10 @@ def corutv_factor_batch(ctx, reqs) -> int:
     if s is not None:
         _check(ctx, load().corutv_set_stream(ctx, ctypes.c_void_p(s)))
     return _check(ctx, load().corutv_factor_batch(ctx, arr, len(reqs)))
+
+
+def corutv_set_batching(ctx, max_batch: int) -> int:
+    return _check(ctx, load().corutv_set_batching(ctx, int(max_batch)))
 
 
 def corutv_poll(ctx, ticket: int, timeout_us: int = -1):

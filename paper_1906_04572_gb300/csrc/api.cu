@@ -786,6 +786,7 @@ struct ReqResult {
     corutv_status status = CORUTV_EPENDING;
     double latency = 0.0;
     std::chrono::steady_clock::time_point t0;
+    std::string msg;  // the dispatcher's message for a failed request
 };
 
 // State of the grouped executor (corutv_factor_batch): the problems'
@@ -796,6 +797,18 @@ struct BatchState {
     size_t hcap = 0;
     cudaEvent_t copied = nullptr;  // recorded after the records' copy: `host` may be rewritten
     std::vector<char> rec;        // records being built
+};
+
+// A serving lane of the batching dispatcher (corutv_set_batching): runs one
+// batch of admitted requests at a time with grouped launches on its stream.
+struct BatchLane {
+    cudaStream_t st = nullptr;
+    BatchState bs;
+    int* flags = nullptr;   // device
+    int* hflags = nullptr;  // pinned host mirror
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    std::vector<uint64_t> tickets;
 };
 
 struct corutv_ctx {
@@ -836,6 +849,8 @@ struct corutv_ctx {
     cudaStream_t side = nullptr;         // the A_m, A_l cast chunks (CastOverlap)
     cudaEvent_t ov_ev[2 * kMaxCastChunks + 4] = {};  // chunk fork / done, the test matrix's, the outputs'
     BatchState batch;                    // corutv_factor_batch
+    int batch_max = 0;                   // serving: largest batch (0: one request per slot)
+    std::vector<BatchLane> lanes;        // serving: batch lanes (corutv_set_batching)
 };
 
 namespace {
@@ -1036,6 +1051,9 @@ corutv_status run_batch(corutv_ctx* ctx, BatchState& bs, const corutv_request* r
         CKS(make_plan(P[i].pl, T_F32, r.m, r.n, r.lda, r.opts.k, r.opts.p, r.opts.q, CORUTV_P_BF16, num_sms,
                       reinterpret_cast<uintptr_t>(r.A) % 16 == 0));
         if (!P[i].pl.split) return fail(CORUTV_EINVAL, "batch request %d: the grouped path needs FP32 A", order[i]);
+        // the grouped products' own stream-K grids may split a tile into more pieces
+        P[i].pl.part_elems = std::max(P[i].pl.part_elems,
+                                      tc_group_partial_elems(P[i].pl.m, P[i].pl.n, P[i].pl.ellp, num_sms));
         bytes += factor_bytes(P[i].pl);
     }
     CKS(ensure_ws(ctx, bs.ws, bytes, st));
@@ -1299,6 +1317,17 @@ corutv_status corutv_destroy(corutv_ctx* ctx) {
         if (s.hflags) cudaFreeHost(s.hflags);
         if (s.done) cudaEventDestroy(s.done);
         if (s.st) cudaStreamDestroy(s.st);
+    }
+    for (auto& l : ctx->lanes) {
+        if (l.st) cudaStreamSynchronize(l.st);
+        if (l.bs.ws.ptr) cudaFree(l.bs.ws.ptr);
+        if (l.bs.desc.ptr) cudaFree(l.bs.desc.ptr);
+        if (l.bs.host) cudaFreeHost(l.bs.host);
+        if (l.bs.copied) cudaEventDestroy(l.bs.copied);
+        if (l.flags) cudaFree(l.flags);
+        if (l.hflags) cudaFreeHost(l.hflags);
+        if (l.done) cudaEventDestroy(l.done);
+        if (l.st) cudaStreamDestroy(l.st);
     }
     for (auto ev : ctx->ev_pool) cudaEventDestroy(ev);
     cudaStreamSynchronize(ctx->stream);
@@ -2073,11 +2102,51 @@ corutv_status launch_request(corutv_ctx* ctx, ServingSlot& s, const PendingReq& 
     return CORUTV_OK;
 }
 
+// A request the batch lanes take: device FP32 input, BF16 sketches on the
+// split path, a seeded test matrix and none of the variants (the grouped
+// path's scope); the others run one per slot.
+bool batchable(const PendingReq& pr) {
+    const corutv_request& r = pr.req;
+    const corutv_opts& o = r.opts;
+    return !pr.host && r.dtype == CORUTV_F32 && o.sketch_prec == CORUTV_P_BF16 && o.d_mode == 0 &&
+           o.t_lower == 0 && o.power_form == 0 && o.bf16_last_round == 0 && !o.psi && o.k + o.p <= 128;
+}
+
+// One batch on a lane: its requests' producers first, then the grouped
+// launches, the lane's status words to the host and the completion event.
+corutv_status launch_batch(corutv_ctx* ctx, BatchLane& l, const std::vector<PendingReq>& prs) {
+    for (auto& pr : prs)
+        if (pr.ready) CK(cudaStreamWaitEvent(l.st, pr.ready, 0));
+    std::vector<corutv_request> reqs;
+    reqs.reserve(prs.size());
+    for (auto& pr : prs) reqs.push_back(pr.req);
+    CK(cudaMemsetAsync(l.flags, 0, sizeof(int) * FLAG_COUNT, l.st));
+    CKS(run_batch(ctx, l.bs, reqs.data(), (int)reqs.size(), l.st, l.flags));
+    CK(cudaMemcpyAsync(l.hflags, l.flags, sizeof(int) * FLAG_COUNT, cudaMemcpyDeviceToHost, l.st));
+    CK(cudaEventRecord(l.done, l.st));
+    return CORUTV_OK;
+}
+
+void finish_lane(corutv_ctx* ctx, BatchLane& l, corutv_status st) {
+    const auto now = std::chrono::steady_clock::now();
+    for (uint64_t t : l.tickets) {
+        auto it = ctx->results.find(t);
+        if (it == ctx->results.end()) continue;
+        it->second.done = true;
+        it->second.status = st;
+        if (st != CORUTV_OK) it->second.msg = g_last_error;
+        it->second.latency = std::chrono::duration<double>(now - it->second.t0).count();
+    }
+    l.tickets.clear();
+    l.busy = false;
+}
+
 void finish_slot(corutv_ctx* ctx, ServingSlot& s, corutv_status st) {
     auto it = ctx->results.find(s.ticket);
     if (it != ctx->results.end()) {
         it->second.done = true;
         it->second.status = st;
+        if (st != CORUTV_OK) it->second.msg = g_last_error;
         it->second.latency =
             std::chrono::duration<double>(std::chrono::steady_clock::now() - it->second.t0).count();
     }
@@ -2105,9 +2174,59 @@ void worker_main(corutv_ctx* ctx) {
                 progressed = true;
             }
         }
+        for (auto& l : ctx->lanes) {
+            if (!l.busy) continue;
+            const cudaError_t q = cudaEventQuery(l.done);
+            if (q == cudaSuccess) {
+                corutv_status st = CORUTV_OK;
+                if (l.hflags[FLAG_BREAKDOWN]) st = fail(CORUTV_EBREAKDOWN, "a Cholesky of the batch broke down");
+                else if (l.hflags[FLAG_TIMEOUT]) st = fail(CORUTV_ETIMEDOUT, "a device wait of the batch timed out");
+                finish_lane(ctx, l, st);
+                progressed = true;
+            } else if (q != cudaErrorNotReady) {
+                cudaGetLastError();
+                fail(CORUTV_ECUDA, "batch lane: %s", cudaGetErrorString(q));
+                finish_lane(ctx, l, CORUTV_ECUDA);
+                progressed = true;
+            }
+        }
         // admit in arrival order
         while (!ctx->queue.empty()) {
             PendingReq& head = ctx->queue.front();
+            if (ctx->batch_max > 0 && batchable(head)) {
+                // continuous batching: a free lane takes the queued batchable
+                // requests at the head, up to batch_max and what memory allows
+                BatchLane* lane = nullptr;
+                for (auto& l : ctx->lanes)
+                    if (!l.busy) { lane = &l; break; }
+                if (!lane) break;
+                const size_t held = lane->bs.ws.cap + lane->bs.desc.cap;
+                const size_t others = ctx->serving_bytes - held;
+                const size_t avail = ctx->budget > others ? ctx->budget - others : 0;
+                std::vector<PendingReq> take;
+                size_t sum = 0;
+                for (auto it = ctx->queue.begin(); it != ctx->queue.end() && (int)take.size() < ctx->batch_max &&
+                                                   batchable(*it);
+                     ++it) {
+                    if (sum + it->bytes + (size_t)(1 << 20) > avail) break;  // (records: well under 1 MB)
+                    sum += it->bytes;
+                    take.push_back(*it);
+                }
+                if (take.empty()) break;  // waits for memory
+                ctx->queue.erase(ctx->queue.begin(), ctx->queue.begin() + (std::ptrdiff_t)take.size());
+                lane->busy = true;
+                lane->tickets.clear();
+                for (auto& pr : take) lane->tickets.push_back(pr.ticket);
+                lk.unlock();
+                const corutv_status st = launch_batch(ctx, *lane, take);
+                lk.lock();
+                ctx->serving_bytes = others + lane->bs.ws.cap + lane->bs.desc.cap;
+                for (auto& pr : take)
+                    if (pr.ready) ctx->ev_pool.push_back(pr.ready);
+                if (st != CORUTV_OK) finish_lane(ctx, *lane, st);
+                progressed = true;
+                continue;
+            }
             ServingSlot* pick = nullptr;
             for (auto& s : ctx->slots)
                 if (!s.busy && s.ws.cap >= head.bytes) { pick = &s; break; }
@@ -2151,6 +2270,7 @@ void worker_main(corutv_ctx* ctx) {
         if (ctx->stop) {
             bool any_busy = false;
             for (auto& s : ctx->slots) any_busy |= s.busy;
+            for (auto& l : ctx->lanes) any_busy |= l.busy;
             if (!any_busy) break;
         }
         ctx->scv.wait_for(lk, std::chrono::microseconds(progressed ? 0 : 20));
@@ -2217,6 +2337,24 @@ extern "C" corutv_status corutv_submit(corutv_ctx* ctx, const corutv_request* re
     return CORUTV_OK;
 }
 
+extern "C" corutv_status corutv_set_batching(corutv_ctx* ctx, int max_batch) {
+    CKS(check_ctx(ctx));
+    if (max_batch < 0 || max_batch > 4096) return fail(CORUTV_EINVAL, "max_batch must be in 0 .. 4096");
+    DeviceGuard guard(ctx->device);
+    std::lock_guard<std::mutex> lk(ctx->smu);
+    if (max_batch > 0 && ctx->lanes.empty()) {
+        ctx->lanes.resize(2);
+        for (auto& l : ctx->lanes) {
+            CK(cudaStreamCreateWithFlags(&l.st, cudaStreamNonBlocking));
+            CK(cudaMalloc(&l.flags, sizeof(int) * FLAG_COUNT));
+            CK(cudaMallocHost(&l.hflags, sizeof(int) * FLAG_COUNT));
+            CK(cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming));
+        }
+    }
+    ctx->batch_max = max_batch;
+    return CORUTV_OK;
+}
+
 extern "C" corutv_status corutv_poll(corutv_ctx* ctx, uint64_t ticket, int64_t timeout_us, double* latency_s) {
     CKS(check_ctx(ctx));
     std::unique_lock<std::mutex> lk(ctx->smu);
@@ -2234,6 +2372,7 @@ extern "C" corutv_status corutv_poll(corutv_ctx* ctx, uint64_t ticket, int64_t t
     ctx->results.erase(ticket);
     if (latency_s) *latency_s = rr.latency;
     if (rr.status != CORUTV_OK && rr.status != CORUTV_EPENDING)
-        return fail(rr.status, "request %llu failed with status %d", (unsigned long long)ticket, (int)rr.status);
+        return fail(rr.status, "request %llu failed with status %d: %s", (unsigned long long)ticket, (int)rr.status,
+                    rr.msg.c_str());
     return rr.status;
 }

@@ -2169,7 +2169,7 @@ cudaError_t launch_group(const GroupItem<A>* it, int count, dim3 grid, dim3 bloc
     if (count < 1) return cudaSuccess;
     if (count > 65535) return cudaErrorInvalidValue;
     auto kern = grouped_kernel<A, F, kT>;
-    if (smem > 48 * 1024) {
+    if (smem > 0) {  // (the 48 KB default covers static and dynamic shared memory together)
         const cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(kern));
         if (e != cudaSuccess) return e;
     }

@@ -1320,6 +1320,18 @@ cudaError_t group_fill(void* item, const TcBuilt& tb, int* grid, size_t* smem, i
 
 size_t tc_group_item_bytes() { return sizeof(TcGroupItem); }
 
+int64_t tc_group_partial_elems(int64_t m, int64_t n, int64_t ellp, int num_sms) {
+    int64_t best = 0;
+    const long long ext[3][3] = {{m, n, 1}, {n, m, 1}, {m, n, 3}};  // A X, A^T Y, the split projection
+    for (const auto& e : ext) {
+        Plan pl = make_plan(e[0], e[1], (int)e[2], false, num_sms, 1);
+        const long long g = std::min<long long>(num_sms, (pl.units + kGroupUnitsPerCta - 1) / kGroupUnitsPerCta);
+        pl = make_plan(e[0], e[1], (int)e[2], false, (int)std::max<long long>(1, g), 1);
+        best = std::max<int64_t>(best, pl.mtiles * pl.maxp * ellp * kTileM);
+    }
+    return best;
+}
+
 cudaError_t tc_group_sketch_item(void* item, const void* a_tiles, int64_t m, int64_t n, int trans, const void* x,
                                  int64_t ldx, int64_t ell, int64_t ellp, void* part, int* tile_cnt, void* c,
                                  ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel, int* grid,

@@ -89,15 +89,17 @@ cudaError_t launch_split_panel(const float* q, int64_t ldq, int64_t rows, int64_
                                int64_t ldq3, const int* cancel, cudaStream_t st);
 
 // Grouped products: one launch over the problems of a batch. Each problem is
-// a record of tc_group_item_bytes() bytes (any host address; 128-byte aligned
-// in device memory when launched) filled on the host by one of the two calls below, with the
-// arguments of launch_sketch_tc_tiled (a product on the tiled bf16 copy) or
+// a record of tc_group_item_bytes() bytes (any host address; 128-byte
+// aligned in device memory when launched) filled on the host by one of the
+// two calls below, with the arguments of launch_sketch_tc_tiled (a product on the tiled bf16 copy) or
 // of launch_project_split_tc_tiled (the split projection). A problem's grid
 // is its own (about 16 stream-K units per CTA), so its sums do not depend on
 // the other problems; its split tiles are added by the product itself (the
 // counters must be zero). Out: the problem's grid, the dynamic shared memory
 // it needs and the partial floats it may use.
 size_t tc_group_item_bytes();
+// Partial floats the three grouped products of an m x n problem may use.
+int64_t tc_group_partial_elems(int64_t m, int64_t n, int64_t ellp, int num_sms);
 cudaError_t tc_group_sketch_item(void* item, const void* a_tiles, int64_t m, int64_t n, int trans, const void* x,
                                  int64_t ldx, int64_t ell, int64_t ellp, void* part, int* tile_cnt, void* c,
                                  ElemType tcout, int64_t ldc, int num_sms, int* flags, const int* cancel, int* grid,

@@ -159,3 +159,39 @@ def test_batch_of_many_small_problems(ctx):
         e_or = np.linalg.norm(a64 - ref["U"] @ ref["T"] @ ref["V"].T) / na
         budget = 4 * U_BF16 * np.sqrt(ell) * np.linalg.norm(a64, 2) / na
         assert e_gpu <= e_or + budget, (m, n, k, q, e_gpu, e_or, budget)
+
+
+def test_batched_serving_results_equal_the_grouped_path_alone(ctx):
+    """Continuous batching (corutv_set_batching): requests submitted in two
+    waves with a host pause between them are admitted as batches on the two
+    lanes; every result is bitwise that of the request alone through
+    corutv_factor_batch, and a request the grouped path does not take (FP64
+    sketches) runs in a slot meanwhile and matches its corutv_factor call."""
+    shapes = SHAPES + [(520, 610, 12, 10, 1, 7), (900, 300, 40, 10, 2, 8)]
+    mats = [torch.from_numpy(matrix(m, n, s)).cuda() for (m, n, k, p, q, s) in shapes]
+    alone = [run_batch(ctx, [a], [sh])[0] for a, sh in zip(mats, shapes)]
+    a64 = torch.from_numpy(matrix(400, 350, 9).astype(np.float64)).cuda()
+    ref64 = ctx.factor(a64, 10, 5, 1, "f64", seed=3)
+    assert ctx.sync() == 0
+    ref64 = {x: host(ref64[x]) for x in ("U", "T", "V")}
+    with Context(0, max_slots=4) as sctx:
+        corutv.corutv_set_batching(sctx.handle, 64)
+        tickets, outs = [], []
+        for i, (a, (m, n, k, p, q, seed)) in enumerate(zip(mats, shapes)):
+            rq, out = request(a, k, p, q, seed)
+            tickets.append(corutv.corutv_submit(sctx.handle, rq))
+            outs.append(out)
+            if i == 3:
+                torch.cuda.synchronize()
+        u = torch.empty((400, 15), dtype=torch.float64, device="cuda")
+        t = torch.empty((15, 15), dtype=torch.float64, device="cuda")
+        v = torch.empty((350, 15), dtype=torch.float64, device="cuda")
+        t64 = corutv.corutv_submit(sctx.handle, corutv.make_request(a64, 10, 5, 1, "f64", u, t, v, seed=3))
+        for tk in tickets + [t64]:
+            st, _ = corutv.corutv_poll(sctx.handle, tk, timeout_us=120_000_000)
+            assert st == corutv.OK
+        for o, want in zip(outs, alone):
+            for x in ("U", "T", "V", "perm"):
+                assert np.array_equal(host(o[x]), want[x]), x
+        for x, got in (("U", u), ("T", t), ("V", v)):
+            assert np.array_equal(host(got), ref64[x]), x
