@@ -515,6 +515,54 @@ def serving_capacity(device_index, nreq, slots, nerr=64, batch=256):
     return res
 
 
+def batch_c5(device_index, nreq, reps=5):
+    """The first nreq requests of the serving stream as one corutv_factor_batch
+    call (every step one grouped launch over all of them): device time per
+    batch (CUDA events, `reps` batches after three warm-ups), solves/s and
+    TFLOP/s, and the library kernels one batch launches."""
+    import torch
+    import synth
+    from paper_1906_04572_gb300 import Context, corutv
+    reqs = synth.serving_requests(count=nreq, rate_per_s=1.0, seed=0)
+    dev = torch.device("cuda", device_index)
+    mats, outs = [], []
+    for r in reqs:
+        u, sig, v = synth.serving_factors(r)
+        mats.append((torch.from_numpy(u * sig).to(dev) @ torch.from_numpy(v).to(dev).T).float().contiguous())
+        ell = r.k + r.p
+        outs.append(tuple(torch.empty(sh, device=dev, dtype=torch.float32)
+                          for sh in ((r.m, ell), (ell, ell), (r.n, ell))))
+    torch.cuda.synchronize()
+    flops = sum(flops_per_factor(r.m, r.n, r.k + r.p, r.q) for r in reqs)
+    with Context(device_index) as bctx:
+        rq = [corutv.make_request(a, r.k, r.p, r.q, "bf16", *o, seed=r.seed) for r, a, o in zip(reqs, mats, outs)]
+        for _ in range(3):
+            corutv.corutv_factor_batch(bctx.handle, rq)
+        if bctx.sync() != 0:
+            raise RuntimeError("batched factorisation reported a device status")
+        s = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        corutv.corutv_profile_enable(bctx.handle, True)  # (the batch path records no stage events)
+        e0.record(s)
+        for _ in range(reps):
+            corutv.corutv_factor_batch(bctx.handle, rq)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        launches = corutv.corutv_profile_read(bctx.handle, corutv.STAGE_ALL)[1] / reps
+        corutv.corutv_profile_enable(bctx.handle, False)
+        if bctx.sync() != 0:
+            raise RuntimeError("batched factorisation reported a device status")
+    e = []
+    for a, (U, T, V) in list(zip(mats, outs))[:32]:
+        a64 = a.double()
+        e.append(float(torch.linalg.norm(a64 - (U.double() @ T.double()) @ V.double().T) / torch.linalg.norm(a64)))
+    return {"requests": nreq, "ms_per_batch": ms, "solves_per_s": nreq / (ms / 1e3),
+            "tflops": flops / (ms / 1e3) / 1e12, "e_rel_median_first32": float(np.median(e)),
+            "gpu_launches_per_batch": launches,
+            "kind": "corutv_factor_batch: the requests of the serving stream at once, each step one grouped launch"}
+
+
 def rpca_c4(ctx, device, prec="f32"):
     """ALM-CoRUTV on the RPCA workload (4800 x 1200, rank 5, 10 % uniform
     +-50 outliers, FP32), 50 iterations."""
@@ -801,6 +849,7 @@ def run_ours(args):
         extra["serving_batched_4x_rate"] = serving_c5(local, args.serve_requests, 4 * args.serve_rate, "bf16", 8,
                                                       batch=args.serve_batch)
         extra["serving"]["capacity_vs_fp64"] = serving_capacity(local, args.serve_capacity, 8)
+        extra["batch"] = batch_c5(local, args.serve_capacity)
         extra["rpca"] = rpca_c4(ctx, device)
         # the single-pass core (Sec. 3.1, d_mode 1): 2q+2 passes over A instead of 2q+3
         sp = {}
@@ -881,8 +930,13 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-capacity", type=int, default=128,
                     help="requests of the serving stream timed at once in the mixed and the FP64 form")
+    ap.add_argument("--batch-only", type=int, default=0,
+                    help="only time N serving-stream requests as one corutv_factor_batch call (profiling aid)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    if args.batch_only:
+        print(json.dumps(batch_c5(0, args.batch_only, reps=args.steps)))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
