@@ -1080,7 +1080,7 @@ corutv_status run_batch(corutv_ctx* ctx, BatchState& bs, const corutv_request* r
     std::vector<GroupItem<SplitArgs>> si;
     std::vector<GroupItem<GramArgs>> di;
     std::vector<GroupItem<QrcpArgs>> qi;
-    std::vector<GroupItem<ReflArgs>> ui;
+    std::vector<GroupItem<ReflArgs>> ui, ur;
     std::vector<GroupItem<GatherArgs>> vi;
     std::vector<GroupItem<EmitArgs>> ei;
     int64_t gmax = 0, smax = 0;
@@ -1101,14 +1101,19 @@ corutv_status run_batch(corutv_ctx* ctx, BatchState& bs, const corutv_request* r
         qi.push_back(qrcp_item(QrcpArgs{b.d, ell, b.refl, b.rt, b.perm, nullptr}));
         if (r.U) want_u = true;
         if (r.V) want_v = true;
-        ui.push_back(refl_item(ReflArgs{static_cast<const float*>(b.q1), pl.ldm, r.U ? pl.m : 0, ell, b.refl,
-                                        static_cast<float*>(r.U), r.ldu, nullptr}));
+        const ReflArgs ra{static_cast<const float*>(b.q1), pl.ldm, r.U ? pl.m : 0, ell, b.refl,
+                          static_cast<float*>(r.U), r.ldu, nullptr};
+        // U = Q1 Qt from the reflectors: one row per thread up to ell = 64, else the shared-memory form
+        ur.push_back(refl_rows_item(ra));
+        ui.push_back(refl_item(ra));
+        if (ell <= 64) ui.back().gx = 0;
         vi.push_back(gather_item(GatherArgs{static_cast<const float*>(b.q2), pl.ldn, r.V ? pl.n : 0, ell, b.perm,
                                             static_cast<float*>(r.V), r.ldv, nullptr}));
         ei.push_back(emit_item(EmitArgs{b.rt, ell, static_cast<float*>(r.T), b.perm, r.perm, nullptr}));
     }
     const RecArr rg = rb.add(gi, ells, gmax), rc = rb.add(ci, ells), rs = rb.add(si, ells, smax);
-    const RecArr rd = rb.add(di, ells), rq = rb.add(qi, ells), ru = rb.add(ui, ells), rvv = rb.add(vi, ells);
+    const RecArr rd = rb.add(di, ells), rq = rb.add(qi, ells), ru = rb.add(ui, ells), rur = rb.add(ur, ells);
+    const RecArr rvv = rb.add(vi, ells);
     const RecArr re = rb.add(ei, ells, (int64_t)128 * 129);
     ProdRecs pax, paty, pproj;
     CKS(build_products(rb, P, 0, flags, num_sms, pax));
@@ -1179,7 +1184,8 @@ corutv_status run_batch(corutv_ctx* ctx, BatchState& bs, const corutv_request* r
     CK(launch_gram_grouped(items(rd, GramArgs{}), count, rd.gx, rd.gy, st));
     // eq. 8, then eq. 9: U = Q1 Qt, T = Rt, V = Q2 P
     CK(launch_qrcp_grouped(items(rq, QrcpArgs{}), count, rq.max_ell, st));
-    if (want_u) CK(launch_refl_grouped(items(ru, ReflArgs{}), count, ru.gx, ru.max_ell, st));
+    if (want_u && rur.gx) CK(launch_refl_rows_grouped(items(rur, ReflArgs{}), count, rur.gx, st));
+    if (want_u && ru.gx) CK(launch_refl_grouped(items(ru, ReflArgs{}), count, ru.gx, ru.max_ell, st));
     if (want_v) CK(launch_gather_grouped(items(rvv, GatherArgs{}), count, rvv.gx, st));
     CK(launch_emit_grouped(items(re, EmitArgs{}), count, stride_grid(re.stride_total), st));
     return CORUTV_OK;

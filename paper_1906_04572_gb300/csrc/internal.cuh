@@ -352,6 +352,8 @@ GroupItem<RinvArgs> rinv_item(const RinvArgs& a);
 GroupItem<TrsmArgs> trsm_item(const TrsmArgs& a);
 GroupItem<QrcpArgs> qrcp_item(const QrcpArgs& a);
 GroupItem<ReflArgs> refl_item(const ReflArgs& a);
+// the register-row form for ell <= 64 (gx = 0 for wider problems: refl_item's launch takes those)
+GroupItem<ReflArgs> refl_rows_item(const ReflArgs& a);
 GroupItem<GatherArgs> gather_item(const GatherArgs& a);
 GroupItem<EmitArgs> emit_item(const EmitArgs& a);
 // The Gram's plan for a problem of a batch: about 256 rows per CTA, from the
@@ -371,6 +373,7 @@ cudaError_t launch_trsm_grouped(const GroupItem<TrsmArgs>* it, int count, unsign
                                 cudaStream_t st);
 cudaError_t launch_qrcp_grouped(const GroupItem<QrcpArgs>* it, int count, int max_ell, cudaStream_t st);
 cudaError_t launch_refl_grouped(const GroupItem<ReflArgs>* it, int count, unsigned gx, int max_ell, cudaStream_t st);
+cudaError_t launch_refl_rows_grouped(const GroupItem<ReflArgs>* it, int count, unsigned gx, cudaStream_t st);
 cudaError_t launch_gather_grouped(const GroupItem<GatherArgs>* it, int count, unsigned gx, cudaStream_t st);
 cudaError_t launch_emit_grouped(const GroupItem<EmitArgs>* it, int count, unsigned gx, cudaStream_t st);
 cudaError_t launch_gram_grouped(const GroupItem<GramArgs>* it, int count, unsigned gx, unsigned gy, cudaStream_t st);

@@ -279,8 +279,14 @@ gram_f32_kernel(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_
     gram_f32_body(x, ldx, y, ldy, len, ell, out, cpart, cnt, pl, cancel, pieces_x, pieces_y, writeback);
 }
 
-// One problem of a grouped Gram launch (complete panels: no pieces)
-__device__ __forceinline__ void gram_group_body(const GramArgs& a) {
+// One problem of a grouped Gram launch (complete panels: no pieces), four
+// CTAs per SM: a batch's Grams are many short CTAs, and the per-CTA reduction
+// and staging latencies want more of them resident than the one-problem
+// kernel's two (at most 64 registers a thread).
+__global__ void __launch_bounds__(kGThreads, 3) gram_grouped_kernel(const GroupItem<GramArgs>* items) {
+    const GroupItem<GramArgs>& it = items[blockIdx.z];
+    if (blockIdx.x >= it.gx || blockIdx.y >= it.gy) return;  // whole clusters (gx a multiple of 8)
+    const GramArgs& a = it.a;
     GramPlan pl;
     pl.ntile = a.ntile;
     pl.tiles = a.tiles;
@@ -361,7 +367,7 @@ cudaError_t launch_gram_grouped(const GroupItem<GramArgs>* it, int count, unsign
     cfg.attrs = attr;
     cfg.numAttrs = 2;
     count_launch();
-    auto kern = grouped_kernel<GramArgs, gram_group_body, kGThreads>;
+    auto kern = gram_grouped_kernel;
     prefer_max_shared(reinterpret_cast<const void*>(kern));
     cudaError_t e = cudaLaunchKernelEx(&cfg, kern, it);
     return e != cudaSuccess ? e : cudaGetLastError();

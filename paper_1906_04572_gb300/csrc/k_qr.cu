@@ -1956,9 +1956,9 @@ cudaError_t launch_qrcp(const double* d, int64_t ell, double* qt, double* rt, in
 // that reflector j touches only the blocks at or after j's own.
 constexpr int kRrThreads = 128;   // rows per block
 template <typename TI, typename TO>
-__global__ void __launch_bounds__(kRrThreads)
-apply_refl_rows_kernel(const TI* x, int64_t ldx, int64_t rows, int ell, const double* refl, TO* out, int64_t ldo,
-                       int out_panel, const int* cancel) {
+__device__ __forceinline__ void apply_refl_rows_body(const TI* x, int64_t ldx, int64_t rows, int ell,
+                                                     const double* refl, TO* out, int64_t ldo, int out_panel,
+                                                     const int* cancel) {
     constexpr int kE = 64, kLdv = 64;  // v_j at Vs + j * kLdv (16-byte aligned columns)
     pdl_wait();
     if (cancel && *cancel) return;
@@ -2036,6 +2036,13 @@ apply_refl_rows_kernel(const TI* x, int64_t ldx, int64_t rows, int ell, const do
             if (r0 + r < rows) out[(r0 + r) * ldo + cb + i] = (TO)Os[r * 33 + i];
         }
     }
+}
+
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(kRrThreads)
+apply_refl_rows_kernel(const TI* x, int64_t ldx, int64_t rows, int ell, const double* refl, TO* out, int64_t ldo,
+                       int out_panel, const int* cancel) {
+    apply_refl_rows_body<TI, TO>(x, ldx, rows, ell, refl, out, ldo, out_panel, cancel);
 }
 
 cudaError_t launch_apply_reflectors(const void* q1, ElemType tp, int64_t ldq, int64_t rows, int64_t ell,
@@ -2140,6 +2147,10 @@ __device__ __forceinline__ void qrcp_g(const QrcpArgs& a) { qrcp_body(a.d, a.ell
 __device__ __forceinline__ void refl_g(const ReflArgs& a) {
     apply_refl_body<float, float, float>(a.x, a.ldx, a.rows, a.ell, a.refl, a.out, a.ldo, 0, a.cancel);
 }
+// ell <= 64: one row of Q1 per thread, in registers
+__device__ __forceinline__ void refl_rows_g(const ReflArgs& a) {
+    apply_refl_rows_body<float, float>(a.x, a.ldx, a.rows, a.ell, a.refl, a.out, a.ldo, 0, a.cancel);
+}
 __device__ __forceinline__ void gather_g(const GatherArgs& a) {
     gather_v_body<float, float>(a.q2, a.ldq2, a.n, a.ell, a.perm, a.v, a.ldv, a.cancel);
 }
@@ -2202,6 +2213,9 @@ GroupItem<QrcpArgs> qrcp_item(const QrcpArgs& a) { return item_of(a, 1); }
 GroupItem<ReflArgs> refl_item(const ReflArgs& a) {
     return item_of(a, (unsigned)((a.rows + kTrsmRows - 1) / kTrsmRows));
 }
+GroupItem<ReflArgs> refl_rows_item(const ReflArgs& a) {
+    return item_of(a, a.ell <= 64 ? (unsigned)((a.rows + kRrThreads - 1) / kRrThreads) : 0u);
+}
 GroupItem<GatherArgs> gather_item(const GatherArgs& a) { return item_of(a, (unsigned)((a.n + 31) / 32)); }
 GroupItem<EmitArgs> emit_item(const EmitArgs& a) { return item_of(a, kAnyGrid); }
 
@@ -2239,6 +2253,10 @@ cudaError_t launch_refl_grouped(const GroupItem<ReflArgs>* it, int count, unsign
     if (max_ell < 1 || max_ell > 128) return cudaErrorInvalidValue;
     return launch_group<ReflArgs, refl_g, kTrsmThreads>(it, count, dim3(gx), dim3(kTrsmThreads), refl_smem(max_ell),
                                                         st);
+}
+
+cudaError_t launch_refl_rows_grouped(const GroupItem<ReflArgs>* it, int count, unsigned gx, cudaStream_t st) {
+    return launch_group<ReflArgs, refl_rows_g, kRrThreads>(it, count, dim3(gx), dim3(kRrThreads), 0, st);
 }
 
 cudaError_t launch_gather_grouped(const GroupItem<GatherArgs>* it, int count, unsigned gx, cudaStream_t st) {
