@@ -1302,7 +1302,7 @@ cudaError_t launch_project_split_tc_tiled(const void* a3, int64_t m, int64_t n, 
 // ---------------------------------------------------------------------------
 namespace {
 // stream-K units (128 rows by one 128-byte K box) per CTA of a grouped product; one K box per stage
-constexpr int kGroupUnitsPerCta = 32;
+constexpr int kGroupUnitsPerCta = 64;
 
 // (the host record may sit anywhere: it is assembled aligned and copied in)
 cudaError_t group_fill(void* item, const TcBuilt& tb, int* grid, size_t* smem, int64_t* part_floats) {

@@ -93,7 +93,7 @@ cudaError_t launch_split_panel(const float* q, int64_t ldq, int64_t rows, int64_
 // aligned in device memory when launched) filled on the host by one of the
 // two calls below, with the arguments of launch_sketch_tc_tiled (a product on the tiled bf16 copy) or
 // of launch_project_split_tc_tiled (the split projection). A problem's grid
-// is its own (about 16 stream-K units per CTA), so its sums do not depend on
+// is its own (about 64 stream-K units per CTA), so its sums do not depend on
 // the other problems; its split tiles are added by the product itself (the
 // counters must be zero). Out: the problem's grid, the dynamic shared memory
 // it needs and the partial floats it may use.
