@@ -279,11 +279,11 @@ gram_f32_kernel(const float* x, int64_t ldx, const float* y, int64_t ldy, int64_
     gram_f32_body(x, ldx, y, ldy, len, ell, out, cpart, cnt, pl, cancel, pieces_x, pieces_y, writeback);
 }
 
-// One problem of a grouped Gram launch (complete panels: no pieces), four
-// CTAs per SM: a batch's Grams are many short CTAs, and the per-CTA reduction
-// and staging latencies want more of them resident than the one-problem
-// kernel's two (at most 64 registers a thread).
-__global__ void __launch_bounds__(kGThreads, 3) gram_grouped_kernel(const GroupItem<GramArgs>* items) {
+// One problem of a grouped Gram launch (complete panels: no pieces); blocks
+// beyond the problem's own grid return as whole clusters (gx is a multiple
+// of 8). Two CTAs per SM as in the one-problem kernel (three measured the
+// same and spill).
+__global__ void __launch_bounds__(kGThreads) gram_grouped_kernel(const GroupItem<GramArgs>* items) {
     const GroupItem<GramArgs>& it = items[blockIdx.z];
     if (blockIdx.x >= it.gx || blockIdx.y >= it.gy) return;  // whole clusters (gx a multiple of 8)
     const GramArgs& a = it.a;
