@@ -684,15 +684,18 @@ def sketch_roofline(prof, psteps, m, n, ell, prec, peaks, peaks_kind, workload):
 def step_bytes(m, n, q, prec, input_es):
     """HBM bytes of one factorisation: the algorithmic budget (the passes over
     A at the sketch precision, the projection at the input precision, one
-    cast for bf16) and what this implementation moves (its bf16 cast writes
-    the three exact splits of A, which the projection reads)."""
+    cast for bf16) and what this implementation moves: the bf16 path casts
+    A_h on the critical path (A read, 2 bytes written per element) and A_m,
+    A_l in row chunks beside the thin QRs (A read again, 4 bytes written),
+    and the projection reads the three parts; the TF32 path writes A^T in
+    one pass and the three parts in another."""
     passes = 2 * q + 2
     if prec == "bf16" and input_es == 4:
         alg = 4 * m * n + 2 * m * n + passes * 2 * m * n + 4 * m * n
-        impl = 4 * m * n + 6 * m * n + passes * 2 * m * n + 6 * m * n
+        impl = (4 + 2) * m * n + (4 + 4) * m * n + passes * 2 * m * n + 6 * m * n
     elif prec == "tf32":
         alg = (passes + 1) * 4 * m * n
-        impl = 4 * m * n + (4 + 6) * m * n + passes * 4 * m * n + 6 * m * n
+        impl = (4 + 4) * m * n + (4 + 6) * m * n + passes * 4 * m * n + 6 * m * n
     else:
         es = 8 if prec == "f64" else 4
         alg = impl = (passes + 1) * es * m * n
