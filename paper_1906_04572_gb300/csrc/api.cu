@@ -2159,6 +2159,35 @@ void finish_slot(corutv_ctx* ctx, ServingSlot& s, corutv_status st) {
     s.busy = false;
 }
 
+// Memory held by idle slots and idle batch lanes (other than `keep`) given
+// back, so that a request too large for what is left can be admitted; true
+// if anything was freed. Slot workspaces are freed in their stream's order,
+// a lane's buffers with cudaFree (its stream has no pending work).
+bool release_idle(corutv_ctx* ctx, const BatchLane* keep) {
+    bool freed = false;
+    for (auto& s : ctx->slots) {
+        if (s.busy || !s.ws.ptr) continue;
+        cudaFreeAsync(s.ws.ptr, s.st);
+        ctx->serving_bytes -= s.ws.cap;
+        s.ws.ptr = nullptr;
+        s.ws.cap = 0;
+        freed = true;
+    }
+    for (auto& l : ctx->lanes) {
+        if (l.busy || &l == keep) continue;
+        for (DeviceBuffer* b : {&l.bs.ws, &l.bs.desc}) {
+            if (!b->ptr) continue;
+            cudaFree(b->ptr);
+            ctx->serving_bytes -= b->cap;
+            b->ptr = nullptr;
+            b->cap = 0;
+            freed = true;
+        }
+    }
+    cudaGetLastError();
+    return freed;
+}
+
 void worker_main(corutv_ctx* ctx) {
     DeviceGuard guard(ctx->device);
     std::unique_lock<std::mutex> lk(ctx->smu);
@@ -2218,7 +2247,10 @@ void worker_main(corutv_ctx* ctx) {
                     sum += it->bytes;
                     take.push_back(*it);
                 }
-                if (take.empty()) break;  // waits for memory
+                if (take.empty()) {
+                    if (release_idle(ctx, lane)) continue;  // retry with the idle memory given back
+                    break;                                   // waits for running work to free memory
+                }
                 ctx->queue.erase(ctx->queue.begin(), ctx->queue.begin() + (std::ptrdiff_t)take.size());
                 lane->busy = true;
                 lane->tickets.clear();
@@ -2259,7 +2291,10 @@ void worker_main(corutv_ctx* ctx) {
                     }
                 }
             }
-            if (!pick) break;
+            if (!pick) {
+                if (release_idle(ctx, nullptr)) continue;  // retry with the idle memory given back
+                break;
+            }
             PendingReq pr = head;
             ctx->queue.pop_front();
             pick->busy = true;
