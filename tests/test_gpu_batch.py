@@ -195,3 +195,34 @@ def test_batched_serving_results_equal_the_grouped_path_alone(ctx):
                 assert np.array_equal(host(o[x]), want[x]), x
         for x, got in (("U", u), ("T", t), ("V", v)):
             assert np.array_equal(host(got), ref64[x]), x
+
+
+def test_batch_at_the_widest_sketch(ctx):
+    """ell = 128 (the widest tensor-core sketch) beside a narrow problem: the
+    projection's B panel then needs two TMA boxes and two MMA N chunks, its
+    ring the one-CTA-per-SM budget, and the Cholesky, QRCP and R^-1 their
+    largest shared memory; both problems within the BF16 budget of the
+    oracle and bitwise equal to their batches of one."""
+    shapes = [(700, 650, 118, 10, 1, 31), (400, 380, 9, 10, 2, 32)]
+    mats = [torch.from_numpy(matrix(m, n, s)).cuda() for (m, n, k, p, q, s) in shapes]
+    res = run_batch(ctx, mats, shapes)
+    for i, (a, got, (m, n, k, p, q, s)) in enumerate(zip(mats, res, shapes)):
+        a64 = a.cpu().numpy().astype(np.float64)
+        ell = k + p
+        ref = oracle.corutv(a64, k, p, q, seed=s, stream=7)
+        na = np.linalg.norm(a64)
+        e_gpu = np.linalg.norm(a64 - got["U"] @ got["T"] @ got["V"].T) / na
+        e_or = np.linalg.norm(a64 - ref["U"] @ ref["T"] @ ref["V"].T) / na
+        budget = 4 * U_BF16 * np.sqrt(ell) * np.linalg.norm(a64, 2) / na
+        assert e_gpu <= e_or + budget, (m, n, k, q, e_gpu, e_or, budget)
+        alone = run_batch(ctx, [a], [shapes[i]])[0]
+        for x in ("U", "T", "V", "perm"):
+            assert np.array_equal(alone[x], got[x]), (i, x)
+
+
+def test_set_batching_rejects_out_of_range(ctx):
+    for bad in (-1, 4097):
+        with pytest.raises(corutv.CorutvError) as ei:
+            corutv.corutv_set_batching(ctx.handle, bad)
+        assert ei.value.status == corutv.EINVAL
+    corutv.corutv_set_batching(ctx.handle, 0)
