@@ -27,3 +27,20 @@ def test_reference_arm_prints_the_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_step_byte_model():
+    """The whole-step byte figures the bench reports: at q = 2 the mixed
+    path's algorithmic budget is 22 m n bytes (FP32 A read once and written
+    as bf16, six bf16 passes, the projection reading FP32 A), and this
+    implementation moves 32 m n (A read by both casts, the three bf16 parts
+    written and read by the projection); the FP64 path reads A 2q+3 times."""
+    sys.path.insert(0, ROOT)
+    import bench
+    m, n = 1000, 700
+    alg, impl = bench.step_bytes(m, n, 2, "bf16", 4)
+    assert alg == 22 * m * n and impl == 32 * m * n
+    alg, impl = bench.step_bytes(m, n, 2, "f64", 8)
+    assert alg == impl == 7 * 8 * m * n
+    alg, impl = bench.step_bytes(m, n, 1, "bf16", 4)
+    assert alg == 18 * m * n and impl == 28 * m * n
