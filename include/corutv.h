@@ -205,8 +205,10 @@ typedef struct {
 /* Queue one corutv_factor request; the descriptor is copied, the buffers
  * are borrowed until corutv_poll returns something other than
  * CORUTV_EPENDING. Requests are admitted in arrival order as slots and
- * workspace memory free up, and run concurrently on the device. Returns
- * CORUTV_ENOMEM only if the request could never fit the budget.
+ * workspace memory free up, and run concurrently on the device; the memory
+ * idle slots and idle batch lanes hold is given back when the request at the
+ * head would not fit beside it. Returns CORUTV_ENOMEM only if the request
+ * could never fit the budget.
  * Device inputs: submit records an event on the context's stream
  * (corutv_set_stream) and the request's work waits for it, so A and psi may
  * still be in production on that stream when the caller submits (no host
